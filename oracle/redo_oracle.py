@@ -1,0 +1,455 @@
+"""CPU FP64 oracle for REDO -- TEST INFRASTRUCTURE ONLY.
+
+Rapid Exponentiation using Discrete Operators (Bhole & Mahesh,
+arXiv:1707.02162).  This module is a plain, slow, obviously-correct numpy
+restatement of what the GPU library computes.  It exists to check the CUDA
+path; nothing in the product imports it.  Only the test-suite, the smoke check
+and the benchmark's CPU-baseline arm may call it.  It shares no code with the
+CUDA path (no kernels, headers, tables or helpers) and never imports the
+product package.
+
+All arithmetic is IEEE float64 / complex128.  Library primitives used as single
+steps: matrix product (``@``), ``numpy.linalg.solve`` (Pade denominator),
+``numpy.linalg.eigh`` (Hermitian eigen-decomposition).
+
+Functions and the passage each one follows:
+
+* :func:`quantize` / :func:`level_digits` -- Eq. (cgrain), Section II: the
+  coefficient is coarse-grained to ``sum_j c_j b^j`` times the grain epsilon.
+* :func:`expm_pade13` -- the scaling-and-squaring Pade-13 matrix exponential of
+  Higham (2005) ("Pade ME", the paper's comparison method, Section II).
+* :func:`expm_hermitian` -- ``exp(-i t H)`` by eigen-decomposition ("ED").
+* :func:`build_table` -- the one-time discrete-operator table, process 1 of
+  Section II (Eq. redoform, read with the ``c b^j dt`` scaling of the worked
+  example that precedes it) plus the drift step ``D = exp(-i dt H0)``.
+* :func:`step_factors` / :func:`step_propagator` / :func:`propagate` -- process
+  2 (Eq. exp2prod) applied per control term, composed with the drift as in the
+  Dirac-frame step of Section III (Eqs. vnd and the step formula after it) and
+  chained ``U = U_M ... U_1`` (Section III).
+* :func:`fidelity` -- the unitary fidelity ``F_U`` of Section III.
+* :func:`grape_gradient` -- the GRAPE gradient ``dF/du_kn`` of the REDO split
+  model (Section III, flowchart Fig. fc; the paper gives no formula, the
+  derivative is taken from the definitions, see its docstring).
+* :func:`polar_unitary` -- polar factor ``P (P^dag P)^(-1/2)``.
+* :func:`simulate_expectation` -- ``<M> = Tr[M rho(t)]`` of Section IV for a
+  pure initial state.
+* :func:`mlp_*` -- an FP64 multilayer perceptron with exact (erf) GELU and Adam,
+  the learned warm start of the control problem (no counterpart in the paper).
+
+Pins (tests/test_oracle_pins.py) tie every function to closed forms, library
+routines used as independent checks (scipy), invariants and brute force.
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+
+__all__ = [
+    "quantize", "level_digits", "level_values", "table_thetas", "expm_pade13", "expm_hermitian",
+    "build_table", "step_factors", "step_propagator", "propagate", "fidelity", "trace_overlap",
+    "grape_gradient", "polar_unitary", "simulate_expectation", "exact_step", "split_step",
+    "plan_digits", "mlp_init", "mlp_forward", "mlp_backward", "adam_step", "gelu", "gelu_grad",
+]
+
+
+# ---------------------------------------------------------------------------
+# Eq. (cgrain): coarse graining to integer levels
+# ---------------------------------------------------------------------------
+
+def quantize(u, lo, hi, levels):
+    """Coarse-grain coefficients to level indices (Eq. cgrain, Section II).
+
+    Reading adopted: the grid has ``levels`` points ``lo + q*delta``,
+    ``delta = (hi - lo)/(levels - 1)``, both ends included, and a coefficient
+    goes to the nearest grid point, ties to even ("floor-ceil" bracket of the
+    paper, rounding mode unstated).  Arithmetic: one IEEE subtract, one IEEE
+    divide (no fused multiply-add), then round-half-even.
+
+    Returns ``(q, n_nonfinite, n_saturated)``: ``q`` int32 of the shape of u
+    (trailing axis = term k), with non-finite inputs mapped to level 0 and
+    out-of-range inputs clamped to [0, levels-1].
+    """
+    u = np.asarray(u, dtype=np.float64)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    delta = (hi - lo) / np.float64(levels - 1)
+    with np.errstate(invalid="ignore", over="ignore", divide="ignore"):
+        x = np.subtract(u, lo)
+        x = np.divide(x, delta)
+        r = np.rint(x)
+    finite = np.isfinite(u)
+    low = finite & (r < 0)
+    high = finite & (r > levels - 1)
+    r = np.where(low, 0.0, r)
+    r = np.where(high, levels - 1, r)
+    r = np.where(finite, r, 0.0)
+    q = r.astype(np.int32)
+    return q, int((~finite).sum()), int(low.sum() + high.sum())
+
+
+def level_digits(q, base, digits):
+    """Base-b digits ``c_j = floor(q / b^j) mod b`` for j = 0..digits-1 (Eq. cgrain).
+
+    The paper's digit range j = l..m maps to 0..digits-1 with the grain
+    epsilon = delta, so ``q = sum_j c_j b^j``.  Shape: q.shape + (digits,).
+    """
+    q = np.asarray(q, dtype=np.int64)
+    return np.stack([(q // (base ** j)) % base for j in range(digits)], axis=-1).astype(np.int32)
+
+
+def level_values(q, lo, hi, levels):
+    """Quantised coefficient ``u_hat = lo + q*delta`` (the coarse-grained value)."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    delta = (hi - lo) / np.float64(levels - 1)
+    return lo + np.asarray(q, dtype=np.float64) * delta
+
+
+def table_thetas(lo_k, hi_k, levels, base, digits):
+    """Coefficients of the discrete operators of one term: ``theta[j][c]``.
+
+    Digit 0 carries the offset of the grid (reading for signed ranges):
+    ``theta[0][c] = lo + c*delta``; digit j >= 1: ``theta[j][c] = c * b^j * delta``
+    (Eq. redoform read with the ``c b^j`` scaling of the worked example).
+    Summing one entry per digit gives ``lo + q*delta`` for ``q = sum_j c_j b^j``.
+    """
+    delta = (np.float64(hi_k) - np.float64(lo_k)) / np.float64(levels - 1)
+    th = np.empty((digits, base), dtype=np.float64)
+    for c in range(base):
+        th[0, c] = np.float64(lo_k) + np.float64(c) * delta
+    for j in range(1, digits):
+        for c in range(base):
+            th[j, c] = np.float64(c * base ** j) * delta
+    return th
+
+
+def plan_digits(omega_max, eps, base):
+    """Cost model of Section II: smallest l with b^l <= eps and m with b^(m+1) > omega_max;
+    returns ``(l, m, p, s)`` with ``p = m - l`` products and ``s = (b-1)(p+1)`` stored operators."""
+    l = int(math.floor(math.log(eps, base) + 1e-12))
+    m = int(math.ceil(math.log(omega_max, base) - 1.0 - 1e-12))
+    while base ** (m + 1) <= omega_max:
+        m += 1
+    p = m - l
+    s = (base - 1) * (p + 1)
+    return l, m, p, s
+
+
+# ---------------------------------------------------------------------------
+# Matrix exponentials
+# ---------------------------------------------------------------------------
+
+def _pade13_coefficients():
+    # [13/13] Pade approximant of exp: b_j = (26 - j)! 13! / (26! j! (13 - j)!)
+    m = 13
+    out = []
+    for j in range(m + 1):
+        f = Fraction(math.factorial(2 * m - j) * math.factorial(m),
+                     math.factorial(2 * m) * math.factorial(j) * math.factorial(m - j))
+        out.append(float(f))
+    return out
+
+
+_B13 = _pade13_coefficients()
+# Higham (2005), Table 2.3: largest 1-norm for which the degree-13 Pade
+# approximant meets unit roundoff in double precision.
+_THETA13 = 5.371920351148152
+
+
+def expm_pade13(A):
+    """``exp(A)`` by scaling and squaring with the [13/13] Pade approximant (Higham 2005).
+
+    Steps: choose s with ||A/2^s||_1 <= theta_13; evaluate the even/odd parts
+    U, V of the approximant at A/2^s; solve (V - U) R = (V + U); square s times.
+    """
+    A = np.asarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    norm1 = np.abs(A).sum(axis=0).max() if n else 0.0
+    s = 0
+    if norm1 > _THETA13:
+        s = int(math.ceil(math.log2(norm1 / _THETA13)))
+    A = A / (2.0 ** s)
+    I = np.eye(n, dtype=np.complex128)
+    A2 = A @ A
+    A4 = A2 @ A2
+    A6 = A4 @ A2
+    b = _B13
+    Uin = A6 @ (b[13] * A6 + b[11] * A4 + b[9] * A2) + b[7] * A6 + b[5] * A4 + b[3] * A2 + b[1] * I
+    U = A @ Uin
+    V = A6 @ (b[12] * A6 + b[10] * A4 + b[8] * A2) + b[6] * A6 + b[4] * A4 + b[2] * A2 + b[0] * I
+    R = np.linalg.solve(V - U, V + U)
+    for _ in range(s):
+        R = R @ R
+    return R
+
+
+def expm_hermitian(H, t):
+    """``exp(-i t H)`` for Hermitian H by eigen-decomposition ``H = V diag(w) V^dag``."""
+    H = np.asarray(H, dtype=np.complex128)
+    w, V = np.linalg.eigh(H)
+    return (V * np.exp(-1j * t * w)[None, :]) @ V.conj().T
+
+
+# ---------------------------------------------------------------------------
+# Process 1: the one-time table
+# ---------------------------------------------------------------------------
+
+def build_table(H0, Hk, dt, lo, hi, levels, base, digits, method="pade"):
+    """Discrete-operator table and drift step (Section II process 1; Section III).
+
+    ``T[k][j][c] = exp(-i dt theta_kjc H_k)`` with ``theta`` from
+    :func:`table_thetas`, and ``D = exp(-i dt H0)``.  ``method`` picks the
+    exponential: ``"pade"`` (:func:`expm_pade13`) or ``"eig"``
+    (:func:`expm_hermitian`).  Returns ``(T, D)`` with T of shape
+    (K, digits, base, N, N).  The table is NOT folded with D.
+    """
+    Hk = np.asarray(Hk, dtype=np.complex128)
+    K, N, _ = Hk.shape
+    T = np.empty((K, digits, base, N, N), dtype=np.complex128)
+    for k in range(K):
+        th = table_thetas(lo[k], hi[k], levels, base, digits)
+        for j in range(digits):
+            for c in range(base):
+                if method == "pade":
+                    T[k, j, c] = expm_pade13(-1j * dt * th[j, c] * Hk[k])
+                else:
+                    T[k, j, c] = expm_hermitian(Hk[k], dt * th[j, c])
+    if method == "pade":
+        D = expm_pade13(-1j * dt * np.asarray(H0, dtype=np.complex128))
+    else:
+        D = expm_hermitian(H0, dt)
+    return T, D
+
+
+# ---------------------------------------------------------------------------
+# Process 2: products of discrete operators, the step and the chain
+# ---------------------------------------------------------------------------
+
+def step_factors(T, D, digit_row):
+    """Per-term products ``E_k = T[k][d-1][c_{d-1}] ... T[k][0][c_0]`` (Eq. exp2prod).
+
+    ``digit_row`` has shape (K, digits).  Returns the list [E_0, ..., E_{K-1}].
+    """
+    K, d = digit_row.shape
+    out = []
+    for k in range(K):
+        E = T[k, 0, digit_row[k, 0]]
+        for j in range(1, d):
+            E = T[k, j, digit_row[k, j]] @ E
+        out.append(E)
+    return out
+
+
+def step_propagator(T, D, digit_row):
+    """One step ``U_n = E_{K-1} ... E_0 D`` (Section III step formula with the drift
+    applied first in time; Lie-Trotter reading of the Dirac-frame product)."""
+    U = D
+    for E in step_factors(T, D, digit_row):
+        U = E @ U
+    return U
+
+
+def propagate(T, D, digits_bm):
+    """Chained propagator ``U = U_M ... U_2 U_1`` (Section III) for one pulse.
+
+    ``digits_bm`` has shape (M, K, digits).  Returns the N x N product.
+    """
+    N = D.shape[0]
+    U = np.eye(N, dtype=np.complex128)
+    for n in range(digits_bm.shape[0]):
+        U = step_propagator(T, D, digits_bm[n]) @ U
+    return U
+
+
+def exact_step(H0, Hk, dt, u_row):
+    """Unsplit, unquantised step ``exp(-i dt (H0 + sum_k u_k H_k))`` (Eq. propUn)."""
+    H = np.asarray(H0, dtype=np.complex128) + np.tensordot(np.asarray(u_row, dtype=np.float64), Hk, axes=1)
+    return expm_pade13(-1j * dt * H)
+
+
+def split_step(H0, Hk, dt, u_row):
+    """Split but unquantised step ``exp(-i dt u_{K-1} H_{K-1}) ... exp(-i dt u_0 H_0) exp(-i dt H0)``."""
+    U = expm_pade13(-1j * dt * np.asarray(H0, dtype=np.complex128))
+    for k in range(Hk.shape[0]):
+        U = expm_pade13(-1j * dt * u_row[k] * Hk[k]) @ U
+    return U
+
+
+# ---------------------------------------------------------------------------
+# Fidelity (Section III, F_U)
+# ---------------------------------------------------------------------------
+
+def trace_overlap(U_target, U):
+    """``tau = Tr(U_T^dag U) = sum_ab conj(U_T[a,b]) U[a,b]``."""
+    return complex(np.sum(np.conj(U_target) * U))
+
+
+def fidelity(U_target, U):
+    """``F_U = |Tr(U_T^dag U)|^2 / N^2`` (``Tr(U_T^dag U_T) = N`` for unitary U_T)."""
+    N = U.shape[0]
+    tau = trace_overlap(U_target, U)
+    return (tau.real * tau.real + tau.imag * tau.imag) / float(N * N)
+
+
+# ---------------------------------------------------------------------------
+# GRAPE gradient of the REDO split model
+# ---------------------------------------------------------------------------
+
+def grape_gradient(T, D, Hk, dt, digits_bm, U_target):
+    """``(F, g)`` with ``g[n][k] = dF/du_kn`` of the split model at the quantised point.
+
+    The paper's GRAPE (Section III, Fig. fc) ascends F with REDO propagators but
+    prints no gradient; this one is derived from the definitions.  With
+    ``U = U_M ... U_1``, ``X_{n-1} = U_{n-1} ... U_1``, ``L_n = U_M ... U_{n+1}``,
+    ``A_k = E_{K-1} ... E_{k+1}`` and ``B_k = E_k ... E_0 D`` (all at the
+    quantised coefficients), ``dU_n/du_kn = A_k (-i dt H_k) B_k`` exactly because
+    H_k commutes with its own exponential.  Hence
+    ``d tau/du_kn = -i dt Tr(H_k B_k X_{n-1} U_T^dag L_n A_k)`` and
+    ``dF/du_kn = (2/N^2) Re(conj(tau) d tau/du_kn)``.
+
+    Everything is formed explicitly from these definitions (no recursion).
+    ``g`` has shape (M, K), units 1/(rad/s).
+    """
+    M, K, _ = digits_bm.shape
+    N = D.shape[0]
+    I = np.eye(N, dtype=np.complex128)
+    steps = [step_propagator(T, D, digits_bm[n]) for n in range(M)]
+    X = [I]                                  # X[n] = U_n ... U_1, X[0] = I
+    for n in range(M):
+        X.append(steps[n] @ X[-1])
+    Lsuf = [None] * (M + 1)                  # Lsuf[n] = U_M ... U_{n+1}
+    Lsuf[M] = I
+    for n in range(M - 1, -1, -1):
+        Lsuf[n] = Lsuf[n + 1] @ steps[n]
+    U = X[M]
+    tau = trace_overlap(U_target, U)
+    F = (abs(tau) ** 2) / float(N * N)
+    g = np.zeros((M, K), dtype=np.float64)
+    UTd = U_target.conj().T
+    for n in range(M):
+        E = step_factors(T, D, digits_bm[n])
+        # B_k = E_k ... E_0 D ; A_k = E_{K-1} ... E_{k+1}
+        Bk = []
+        acc = D
+        for k in range(K):
+            acc = E[k] @ acc
+            Bk.append(acc)
+        Ak = [None] * K
+        acc = I
+        for k in range(K - 1, -1, -1):
+            Ak[k] = acc
+            acc = acc @ E[k]
+        Y = X[n] @ UTd @ Lsuf[n + 1]         # X_{n-1} U_T^dag L_n  (0-based step n is step n+1)
+        for k in range(K):
+            W = Bk[k] @ Y @ Ak[k]
+            dtau = -1j * dt * np.trace(Hk[k] @ W)
+            g[n, k] = 2.0 / (N * N) * (np.conj(tau) * dtau).real
+    return F, g
+
+
+# ---------------------------------------------------------------------------
+# Re-unitarisation
+# ---------------------------------------------------------------------------
+
+def polar_unitary(P):
+    """Unitary polar factor ``P (P^dag P)^(-1/2)`` via eigen-decomposition of P^dag P."""
+    P = np.asarray(P, dtype=np.complex128)
+    w, V = np.linalg.eigh(P.conj().T @ P)
+    return P @ ((V * (1.0 / np.sqrt(w))[None, :]) @ V.conj().T)
+
+
+# ---------------------------------------------------------------------------
+# Section IV: expectation values along the chain
+# ---------------------------------------------------------------------------
+
+def simulate_expectation(T, D, digits_bm, psi0, obs_diag):
+    """``<O>(t_n) = <psi_n| O |psi_n>`` for diagonal O, ``psi_n = U_n ... U_1 psi0``,
+    n = 0..M (Section IV, ``Tr[M rho(t)]`` with ``rho = |psi><psi|``).
+
+    Returns ``(expect[M+1], U_final)`` where ``U_final = U_M ... U_1``.
+    """
+    N = D.shape[0]
+    X = np.eye(N, dtype=np.complex128)
+    out = np.empty(digits_bm.shape[0] + 1, dtype=np.float64)
+    psi = X @ psi0
+    out[0] = float(np.sum(obs_diag * (psi.real ** 2 + psi.imag ** 2)))
+    for n in range(digits_bm.shape[0]):
+        X = step_propagator(T, D, digits_bm[n]) @ X
+        psi = X @ psi0
+        out[n + 1] = float(np.sum(obs_diag * (psi.real ** 2 + psi.imag ** 2)))
+    return out, X
+
+
+# ---------------------------------------------------------------------------
+# Learned warm start: FP64 MLP (no counterpart in the paper)
+# ---------------------------------------------------------------------------
+
+def gelu(x):
+    """Exact GELU ``0.5 x (1 + erf(x / sqrt 2))``."""
+    from math import erf
+    v = np.vectorize(erf, otypes=[np.float64])
+    return 0.5 * x * (1.0 + v(x / math.sqrt(2.0)))
+
+
+def gelu_grad(x):
+    """Derivative of the exact GELU: ``Phi(x) + x phi(x)``."""
+    from math import erf
+    v = np.vectorize(erf, otypes=[np.float64])
+    Phi = 0.5 * (1.0 + v(x / math.sqrt(2.0)))
+    phi = np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+    return Phi + x * phi
+
+
+def mlp_init(sizes, rng):
+    """Weights ``W_l`` (out, in) ~ U[-1/sqrt(in), 1/sqrt(in)], biases zero."""
+    params = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        lim = 1.0 / math.sqrt(a)
+        params.append((rng.uniform(-lim, lim, size=(b, a)), np.zeros(b)))
+    return params
+
+
+def mlp_forward(params, x):
+    """Hidden layers ``h = GELU(W h + b)``, output ``tanh(W h + b)``; x is (batch, in).
+
+    Returns ``(y, cache)`` with the pre-activations needed by :func:`mlp_backward`.
+    """
+    h = np.asarray(x, dtype=np.float64)
+    cache = [h]
+    for li, (W, b) in enumerate(params):
+        z = h @ W.T + b
+        cache.append(z)
+        h = np.tanh(z) if li == len(params) - 1 else gelu(z)
+        cache.append(h)
+    return h, cache
+
+
+def mlp_backward(params, cache, y_target):
+    """Gradients of the loss ``mean((y - y_target)^2)`` (mean over all entries)."""
+    nl = len(params)
+    y = cache[-1]
+    dh = 2.0 * (y - y_target) / y.size
+    grads = [None] * nl
+    for li in range(nl - 1, -1, -1):
+        z = cache[2 * li + 1]
+        h_in = cache[2 * li]
+        if li == nl - 1:
+            dz = dh * (1.0 - np.tanh(z) ** 2)
+        else:
+            dz = dh * gelu_grad(z)
+        W, _ = params[li]
+        grads[li] = (dz.T @ h_in, dz.sum(axis=0))
+        dh = dz @ W
+    loss = float(np.mean((y - y_target) ** 2))
+    return loss, grads
+
+
+def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015) with bias correction; returns (p, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -1,0 +1,412 @@
+"""Pins for the CPU oracle: closed forms, printed values, invariants, brute force.
+
+Each test ties an oracle function to something other than itself, chosen so
+that a dropped term, a wrong sign or index, or a transposed operand fails.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import redo_oracle as O
+from paper_1707_02162_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+SX = np.array([[0, 1], [1, 0]], dtype=complex)
+SY = np.array([[0, -1j], [1j, 0]], dtype=complex)
+SZ = np.array([[1, 0], [0, -1]], dtype=complex)
+I2 = np.eye(2, dtype=complex)
+
+
+def _rand_herm(rng, N, scale=1.0):
+    A = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    return scale * (A + A.conj().T) / 2
+
+
+# ---------------------------------------------------------------- quantizer
+
+def test_quantize_grid_points_exact():
+    L = 4096
+    lo, hi = np.array([-2 * np.pi * 1e4]), np.array([2 * np.pi * 1e4])
+    delta = (hi[0] - lo[0]) / (L - 1)
+    q = np.arange(L)
+    u = (lo[0] + q * delta)[:, None]
+    qq, nn, ns = O.quantize(u, lo, hi, L)
+    assert nn == 0 and ns == 0
+    assert np.array_equal(qq[:, 0], q)
+
+
+def test_quantize_ties_half_even_and_clamp():
+    # lo=0, delta=1 makes (u-lo)/delta exact, so u=q+0.5 is an exact tie.
+    L = 16
+    lo, hi = np.array([0.0]), np.array([15.0])
+    u = np.array([0.5, 1.5, 2.5, 3.5, 14.5, -0.4, -0.6, 15.4, 15.6, -1e300, 1e300,
+                  np.nan, np.inf, -np.inf])[:, None]
+    q, nn, ns = O.quantize(u, lo, hi, L)
+    assert list(q[:, 0]) == [0, 2, 2, 4, 14, 0, 0, 15, 15, 0, 15, 0, 0, 0]
+    assert nn == 3
+    # -0.6 -> -1, 15.6 -> 16, -1e300, 1e300 saturate; -0.4 -> -0 and 15.4 -> 15 do not
+    assert ns == 4
+
+
+def test_quantize_matches_python_scalar_brute_force():
+    # Independent scalar restatement with Python floats (IEEE double) and
+    # Python's round() (ties to even).
+    rng = np.random.default_rng(11)
+    L = 4096
+    lo = np.array([-3.7, 0.0, -1e4])
+    hi = np.array([5.1, 2.0, 2e4])
+    u = rng.uniform(lo - 0.1 * (hi - lo), hi + 0.1 * (hi - lo), size=(2000, 3))
+    # also points within +-1 ulp of midpoints
+    delta = (hi - lo) / (L - 1)
+    mids = lo + (np.arange(100)[:, None] + 0.5) * delta
+    u = np.concatenate([u, mids, np.nextafter(mids, np.inf), np.nextafter(mids, -np.inf)])
+    q, _, _ = O.quantize(u, lo, hi, L)
+    for i in range(u.shape[0]):
+        for k in range(3):
+            d = (float(hi[k]) - float(lo[k])) / float(L - 1)
+            x = (float(u[i, k]) - float(lo[k])) / d
+            r = min(max(round(x), 0), L - 1)
+            assert q[i, k] == r
+
+
+def test_digits_worked_example():
+    g = json.load(open(GOLDEN))["coarse_grain_example"]
+    d = O.level_digits(np.array([g["max_level"]]), g["base"], 3)
+    assert list(d[0]) == g["max_level_digits"]
+    rng = np.random.default_rng(0)
+    q = rng.integers(0, 64 ** 3, size=1000)
+    dd = O.level_digits(q, 64, 3)
+    assert np.array_equal(dd[:, 0] + 64 * dd[:, 1] + 4096 * dd[:, 2], q)
+    assert dd.min() >= 0 and dd.max() <= 63
+
+
+@pytest.mark.parametrize("key", ["coarse_grain_example", "freezing_grain"])
+def test_cost_model_printed_values(key):
+    g = json.load(open(GOLDEN))[key]
+    l, m, p, s = O.plan_digits(g["omega_max"], g["eps"], g["base"])
+    assert (l, m, p, s) == (g["l"], g["m"], g["p"], g["s"])
+
+
+def test_table_thetas_sum_to_level_value():
+    lo, hi, L, b, d = -7.0, 11.0, 4096, 64, 2
+    th = O.table_thetas(lo, hi, L, b, d)
+    q = np.arange(L)
+    dig = O.level_digits(q, b, d)
+    s = th[0, dig[:, 0]] + th[1, dig[:, 1]]
+    assert np.allclose(s, O.level_values(q, np.array(lo), np.array(hi), L), rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- expm
+
+@pytest.mark.parametrize("theta", [0.0, 1e-3, 0.3, 1.7, 12.0, 250.0])
+def test_expm_pauli_closed_form(theta):
+    ref = math.cos(theta) * I2 - 1j * math.sin(theta) * SX
+    assert np.abs(O.expm_pade13(-1j * theta * SX) - ref).max() < 1e-13 * max(1, theta)
+    assert np.abs(O.expm_hermitian(SX, theta) - ref).max() < 1e-13 * max(1, theta)
+    refy = math.cos(theta) * I2 - 1j * math.sin(theta) * SY
+    assert np.abs(O.expm_pade13(-1j * theta * SY) - refy).max() < 1e-13 * max(1, theta)
+
+
+def test_expm_collective_x_is_tensor_power():
+    n, th = 3, 0.77
+    Hx = inputs.controls_global_xy(n)[0]
+    one = math.cos(th / 2) * I2 - 1j * math.sin(th / 2) * SX
+    ref = np.kron(np.kron(one, one), one)
+    assert np.abs(O.expm_pade13(-1j * th * Hx) - ref).max() < 1e-14
+
+
+def test_expm_diagonal_drift_exact():
+    w = inputs.config(0)
+    dt = w.dt
+    ref = np.diag(np.exp(-1j * dt * np.real(np.diag(w.H0))))
+    assert np.abs(O.expm_pade13(-1j * dt * w.H0) - ref).max() < 1e-15
+    assert np.abs(O.expm_hermitian(w.H0, dt) - ref).max() < 1e-15
+
+
+def test_expm_against_scipy_and_eig():
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(5)
+    for N, scale in [(4, 0.1), (8, 1.0), (16, 3.0), (32, 20.0)]:
+        H = _rand_herm(rng, N, scale)
+        A = -1j * H
+        E1 = O.expm_pade13(A)
+        E2 = O.expm_hermitian(H, 1.0)
+        E3 = scipy_linalg.expm(A)
+        tol = 1e-13 * max(1.0, scale * N)
+        assert np.abs(E1 - E3).max() < tol
+        assert np.abs(E1 - E2).max() < tol
+        assert np.abs(E1.conj().T @ E1 - np.eye(N)).max() < tol
+
+
+def test_expm_group_property():
+    rng = np.random.default_rng(6)
+    H = _rand_herm(rng, 8)
+    a, b = 0.37, -1.21
+    lhs = O.expm_pade13(-1j * a * H) @ O.expm_pade13(-1j * b * H)
+    assert np.abs(lhs - O.expm_pade13(-1j * (a + b) * H)).max() < 1e-13
+
+
+def test_expm_nonhermitian_general():
+    # Pade path is for general matrices: nilpotent Jordan block has exp = I + A + A^2/2
+    A = np.array([[0, 2.0, 0], [0, 0, 3.0], [0, 0, 0]], dtype=complex)
+    ref = np.eye(3) + A + A @ A / 2
+    assert np.abs(O.expm_pade13(A) - ref).max() < 1e-14
+
+
+# ---------------------------------------------------------------- table & product
+
+def _small_workload(idx=0, M=12, B=1, n=None, L_base=64, digits=2):
+    return inputs.config(idx, M=M, B=B, n_qubits=n, base=L_base, digits=digits)
+
+
+def test_table_group_property_and_methods_agree():
+    w = _small_workload(0)
+    T, D = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
+    T2, D2 = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits, method="eig")
+    assert np.abs(T - T2).max() < 1e-13 and np.abs(D - D2).max() < 1e-14
+    rng = np.random.default_rng(1)
+    for q in rng.integers(0, w.levels, size=20):
+        c = O.level_digits(np.array([q]), w.base, w.digits)[0]
+        for k in range(w.K):
+            prod = T[k, 1, c[1]] @ T[k, 0, c[0]]
+            uh = O.level_values(q, w.lo[k], w.hi[k], w.levels)
+            assert np.abs(prod - O.expm_hermitian(w.Hk[k], w.dt * uh)).max() < 1e-13
+
+
+def test_commuting_case_has_no_splitting_error():
+    # Z-only controls commute with a diagonal drift: the REDO product equals the
+    # unsplit exponential of the quantised Hamiltonian.
+    n = 2
+    rng = np.random.default_rng(2)
+    H0 = inputs.drift_zz(n, rng.uniform(-5e3, 5e3, n), np.array([[0, 150.0], [0, 0]]))
+    Hk = np.stack([inputs.embed({0: SZ / 2}, n), inputs.embed({1: SZ / 2}, n)])
+    lo, hi, L, b, d, dt = np.array([-6e4, -6e4]), np.array([6e4, 6e4]), 4096, 64, 2, 1e-6
+    T, D = O.build_table(H0, Hk, dt, lo, hi, L, b, d)
+    u = rng.uniform(-6e4, 6e4, size=(1, 30, 2))
+    q, _, _ = O.quantize(u, lo, hi, L)
+    dig = O.level_digits(q, b, d)
+    U = O.propagate(T, D, dig[0])
+    uh = O.level_values(q[0], lo, hi, L)
+    Htot = 30 * H0 + np.tensordot(uh.sum(axis=0), Hk, axes=1)
+    assert np.abs(U - O.expm_hermitian(Htot, dt)).max() < 1e-12
+
+
+def test_dirac_frame_step_equals_split_step():
+    # Section III: U_n = V(dt) exp(-i Omega dt S~), S~ = V^dag(dt) S V(dt)
+    rng = np.random.default_rng(3)
+    n = 2
+    H0 = inputs.drift_zz(n, rng.uniform(-5e3, 5e3, n), np.array([[0, 180.0], [0, 0]]))
+    S = inputs.controls_global_xy(n)[0]
+    dt, Om = 5e-6, 4.3e4
+    V = O.expm_hermitian(H0, dt)
+    Stil = V.conj().T @ S @ V
+    paper = V @ O.expm_pade13(-1j * Om * dt * Stil)
+    ours = O.split_step(H0, S[None], dt, np.array([Om]))
+    assert np.abs(paper - ours).max() < 1e-13
+
+
+def test_splitting_error_is_first_order():
+    rng = np.random.default_rng(4)
+    n = 1
+    H0 = 2 * np.pi * 3e3 * SZ / 2
+    Hk = np.stack([SX / 2, SY / 2])
+    errs = []
+    for dt in [4e-6, 2e-6, 1e-6]:
+        u = np.array([5e4, -3e4])
+        errs.append(np.abs(O.split_step(H0, Hk, dt, u) - O.exact_step(H0, Hk, dt, u)).max())
+    # local error of Lie-Trotter is O(dt^2): halving dt quarters it
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_chain_time_order():
+    # Step 1 is applied first: U = U_2 U_1.  pi/2 about x then pi/2 about y.
+    n = 1
+    H0 = np.zeros((2, 2), dtype=complex)
+    Hk = np.stack([SX / 2, SY / 2])
+    dt = 1.0
+    L = 3
+    lo, hi = np.array([0.0, 0.0]), np.array([math.pi, math.pi])   # levels 0, pi/2, pi
+    T, D = O.build_table(H0, Hk, dt, lo, hi, L, L, 1)
+    dig = np.array([[[1], [0]], [[0], [1]]])        # step1: x by pi/2; step2: y by pi/2
+    U = O.propagate(T, D, dig)
+    Rx = O.expm_hermitian(SX / 2, math.pi / 2)
+    Ry = O.expm_hermitian(SY / 2, math.pi / 2)
+    assert np.abs(U - Ry @ Rx).max() < 1e-15
+    assert np.abs(U - Rx @ Ry).max() > 0.1
+
+
+def test_redo_error_bound_vs_quantization():
+    # Per step ||E(u_hat) - E(u)||_2 <= dt |u - u_hat| ||H||_2; the chain error grows at most linearly.
+    w = _small_workload(0, M=50)
+    T, D = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
+    q, _, _ = O.quantize(w.u, w.lo, w.hi, w.levels)
+    dig = O.level_digits(q, w.base, w.digits)
+    U_redo = O.propagate(T, D, dig[0])
+    U_split = np.eye(w.N, dtype=complex)
+    for n in range(w.M):
+        U_split = O.split_step(w.H0, w.Hk, w.dt, w.u[0, n]) @ U_split
+    uh = O.level_values(q[0], w.lo, w.hi, w.levels)
+    hnorm = [np.linalg.norm(w.Hk[k], 2) for k in range(w.K)]
+    bound = sum(w.dt * abs(w.u[0, n, k] - uh[n, k]) * hnorm[k] for n in range(w.M) for k in range(w.K))
+    err = np.linalg.norm(U_redo - U_split, 2)
+    assert err <= bound * (1 + 1e-9) + 1e-13
+    assert err > 0
+
+
+@pytest.mark.parametrize("n", [1, 3])
+def test_fidelity_closed_form_coarse_grain(n):
+    # Section II: F = |Tr[e^{i Om dt S} e^{-i Om_hat dt S}]/N|^2; for S = sum X_i/2
+    # this is cos^{2n}(dt (Om - Om_hat)/2).
+    S = inputs.controls_global_xy(n)[0]
+    dt, Om, Omh = 5e-6, 123456.789, 23456.0
+    Ua = O.expm_hermitian(S, Om * dt)
+    Ub = O.expm_hermitian(S, Omh * dt)
+    F = O.fidelity(Ua, Ub)
+    assert abs(F - math.cos(dt * (Om - Omh) / 2) ** (2 * n)) < 1e-14
+    assert 1 - F > 1e-3
+
+
+def test_fidelity_invariants():
+    rng = np.random.default_rng(7)
+    U = inputs.haar_unitary(rng, 8)
+    V = inputs.haar_unitary(rng, 8)
+    assert abs(O.fidelity(U, U) - 1) < 1e-14
+    assert abs(O.fidelity(U, np.exp(0.7j) * U) - 1) < 1e-14
+    f = O.fidelity(U, V)
+    assert 0 <= f <= 1
+    # tau is conjugate-linear in the target, linear in U
+    assert abs(O.trace_overlap(U, 1j * V) - 1j * O.trace_overlap(U, V)) < 1e-14
+    assert abs(O.trace_overlap(U, V) - np.trace(U.conj().T @ V)) < 1e-13
+
+
+# ---------------------------------------------------------------- gradient
+
+def _split_fidelity(H0, Hk, dt, u, UT):
+    U = np.eye(H0.shape[0], dtype=complex)
+    for n in range(u.shape[0]):
+        U = O.split_step(H0, Hk, dt, u[n]) @ U
+    return O.fidelity(UT, U)
+
+
+def test_gradient_matches_central_differences():
+    w = inputs.config(0, M=8)
+    T, D = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
+    q, _, _ = O.quantize(w.u, w.lo, w.hi, w.levels)
+    dig = O.level_digits(q, w.base, w.digits)
+    F, g = O.grape_gradient(T, D, w.Hk, w.dt, dig[0], w.target)
+    uh = O.level_values(q[0], w.lo, w.hi, w.levels)
+    assert abs(F - _split_fidelity(w.H0, w.Hk, w.dt, uh, w.target)) < 1e-13
+    Om = w.extra["Omega"]
+    h = 1e-6 * Om        # h = 1e-6 in normalised amplitude
+    for n in range(w.M):
+        for k in range(w.K):
+            up, um = uh.copy(), uh.copy()
+            up[n, k] += h
+            um[n, k] -= h
+            fd = (_split_fidelity(w.H0, w.Hk, w.dt, up, w.target)
+                  - _split_fidelity(w.H0, w.Hk, w.dt, um, w.target)) / (2 * h)
+            assert abs(fd - g[n, k]) < 1e-9 * max(1.0, abs(g).max()) + 2e-12 / h
+
+
+def test_gradient_single_qubit_closed_form():
+    # H0 = 0, control Z/2, target I: F = cos^2(phi/2), phi = dt sum u; dF/du_n = -(dt/2) sin(phi)
+    H0 = np.zeros((2, 2), dtype=complex)
+    Hk = np.stack([SZ / 2])
+    dt, L = 1e-4, 4096
+    lo, hi = np.array([-1e4]), np.array([1e4])
+    T, D = O.build_table(H0, Hk, dt, lo, hi, L, 64, 2)
+    rng = np.random.default_rng(9)
+    q, _, _ = O.quantize(rng.uniform(-1e4, 1e4, size=(5, 1)), lo, hi, L)
+    dig = O.level_digits(q, 64, 2)
+    F, g = O.grape_gradient(T, D, Hk, dt, dig, np.eye(2, dtype=complex))
+    phi = dt * O.level_values(q, lo, hi, L).sum()
+    assert abs(F - math.cos(phi / 2) ** 2) < 1e-14
+    assert np.abs(g[:, 0] + dt / 2 * math.sin(phi)).max() < 1e-16
+
+
+def test_gradient_vanishes_at_reached_target():
+    w = inputs.config(0, M=6)
+    T, D = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
+    q, _, _ = O.quantize(w.u, w.lo, w.hi, w.levels)
+    dig = O.level_digits(q, w.base, w.digits)
+    UT = O.propagate(T, D, dig[0]) * np.exp(0.3j)
+    F, g = O.grape_gradient(T, D, w.Hk, w.dt, dig[0], UT)
+    assert abs(F - 1) < 1e-13
+    assert np.abs(g).max() < 1e-12
+
+
+# ---------------------------------------------------------------- polar, simulate
+
+def test_polar_factor():
+    rng = np.random.default_rng(8)
+    U = inputs.haar_unitary(rng, 16)
+    assert np.abs(O.polar_unitary(U) - U).max() < 1e-13
+    Hp = _rand_herm(rng, 16, 0.01) + np.eye(16)          # positive definite
+    P = U @ Hp
+    Q = O.polar_unitary(P)
+    assert np.abs(Q - U).max() < 1e-12
+    assert np.abs(Q.conj().T @ Q - np.eye(16)).max() < 1e-14
+
+
+def test_expectation_rabi_closed_form():
+    # 1 qubit, H0 = 0, constant drive Omega X/2: <Z>(t) = cos(Omega_hat t) exactly.
+    H0 = np.zeros((2, 2), dtype=complex)
+    Hk = np.stack([SX / 2])
+    dt, L, M = 1e-6, 4096, 200
+    lo, hi = np.array([0.0]), np.array([2 * 2 * np.pi * 5e3])
+    T, D = O.build_table(H0, Hk, dt, lo, hi, L, 64, 2)
+    u = np.full((1, M, 1), 2 * np.pi * 5e3 * 1.013)
+    q, _, _ = O.quantize(u, lo, hi, L)
+    dig = O.level_digits(q, 64, 2)
+    psi0 = np.array([1, 0], dtype=complex)
+    ex, U = O.simulate_expectation(T, D, dig[0], psi0, np.array([1.0, -1.0]))
+    omh = O.level_values(q[0, 0, 0], lo[0], hi[0], L)
+    t = dt * np.arange(M + 1)
+    assert np.abs(ex - np.cos(omh * t)).max() < 1e-12
+    assert ex[0] == 1.0
+
+
+# ---------------------------------------------------------------- MLP
+
+def test_gelu_values():
+    # GELU(x) = x Phi(x); Phi(1) = 0.8413447460685429, Phi(-1) = 0.15865525393145707
+    v = O.gelu(np.array([0.0, 1.0, -1.0, 8.0]))
+    assert v[0] == 0.0
+    assert abs(v[1] - 0.8413447460685429) < 1e-15
+    assert abs(v[2] + 0.15865525393145707) < 1e-15
+    assert abs(v[3] - 8.0) < 1e-12
+
+
+def test_mlp_gradient_finite_difference():
+    rng = np.random.default_rng(10)
+    params = O.mlp_init([5, 7, 6, 4], rng)
+    x = rng.standard_normal((3, 5))
+    yt = rng.uniform(-1, 1, size=(3, 4))
+    y, cache = O.mlp_forward(params, x)
+    loss, grads = O.mlp_backward(params, cache, yt)
+    h = 1e-6
+    for li, (W, b) in enumerate(params):
+        for (i, j) in [(0, 0), (W.shape[0] - 1, W.shape[1] - 1), (1, 2)]:
+            Wp = [(w.copy(), bb.copy()) for w, bb in params]
+            Wm = [(w.copy(), bb.copy()) for w, bb in params]
+            Wp[li][0][i, j] += h
+            Wm[li][0][i, j] -= h
+            lp = np.mean((O.mlp_forward(Wp, x)[0] - yt) ** 2)
+            lm = np.mean((O.mlp_forward(Wm, x)[0] - yt) ** 2)
+            assert abs((lp - lm) / (2 * h) - grads[li][0][i, j]) < 1e-8
+        bp = [(w.copy(), bb.copy()) for w, bb in params]
+        bp[li][1][0] += h
+        bm = [(w.copy(), bb.copy()) for w, bb in params]
+        bm[li][1][0] -= h
+        fd = (np.mean((O.mlp_forward(bp, x)[0] - yt) ** 2) - np.mean((O.mlp_forward(bm, x)[0] - yt) ** 2)) / (2 * h)
+        assert abs(fd - grads[li][1][0]) < 1e-8
+
+
+def test_adam_first_step_is_signed_lr():
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    p2, m, v = O.adam_step(p, g, np.zeros(3), np.zeros(3), 1, 0.01)
+    assert np.allclose(p2, p - 0.01 * np.sign(g), atol=1e-7)
