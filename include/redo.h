@@ -1,0 +1,197 @@
+/*
+ * redo.h -- C ABI of libredo, a GB300 (sm_103a) implementation of REDO,
+ * "Rapid Exponentiation using Discrete Operators" (Bhole & Mahesh,
+ * arXiv:1707.02162).
+ *
+ * The library evaluates piecewise-constant quantum propagators
+ *     U = U_M ... U_2 U_1,   U_n = E_{K-1,n} ... E_{0,n} D,   D = exp(-i dt H0)
+ * (Section III, Eq. propUn, with the drift split off as in the Dirac-frame
+ * step formula), where every per-term factor
+ *     E_{k,n} = exp(-i dt u_hat_{kn} H_k)
+ * is not exponentiated but assembled as a product of precomputed discrete
+ * operators (Section II, processes 1 and 2, Eqs. cgrain, redoform, exp2prod).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Complex matrices are interleaved complex128 (re, im pairs of double),
+ *    row-major N x N, contiguous; batches are outermost.  This is the memory
+ *    layout of a contiguous torch.complex128 tensor.
+ *  - Unless stated otherwise every array argument is DEVICE memory owned by the
+ *    caller.  The only library-owned object is the opaque redo_table.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls enqueue work on it and return without synchronising, except
+ *    redo_build_table and redo_table_free, which synchronise `stream`.
+ *  - Host-detectable errors (null pointers, bad sizes, non-Hermitian input,
+ *    unsupported precision for a size) return a nonzero redo_status before
+ *    anything is enqueued; redo_last_error() then describes the error
+ *    (thread-local string, valid until the next call on the same thread).
+ *  - Device-detected conditions are accumulated into a caller-provided device
+ *    array `dev_status` of REDO_STATUS_WORDS int64 counters (see
+ *    redo_status_word); the caller zeroes it and reads it after the stream
+ *    has been synchronised.  Kernels never trap or assert.
+ *  - Index conventions: the control array u and the level array q have shape
+ *    [B][M][K] (pulse, time step, control term), row-major.  Time step 0 is
+ *    applied first, i.e. it is the rightmost factor of the chain.
+ */
+#ifndef REDO_H
+#define REDO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  REDO_OK = 0,
+  REDO_ERR_INVALID = 1,        /* bad argument: null pointer, size, range        */
+  REDO_ERR_NOT_HERMITIAN = 2,  /* H0 or some H_k is not Hermitian                */
+  REDO_ERR_OOM = 3,            /* device allocation failed (build_table only)    */
+  REDO_ERR_CUDA = 4,           /* a CUDA runtime call failed                     */
+  REDO_ERR_UNSUPPORTED = 5     /* valid request this build does not implement    */
+} redo_status;
+
+/* Arithmetic of the product chain.  The table master copy, the quantizer and
+ * the fidelity reduction are always FP64. */
+typedef enum {
+  REDO_FP64 = 0,     /* complex FP64 products (plain REDO)                       */
+  REDO_FP32 = 1,     /* complex FP32 products on the FP32 pipes                  */
+  REDO_FP16X3 = 4    /* tensor cores: each operand split hi + 2^-11-scaled lo in
+                        FP16, three products hi*hi + (hi*lo + lo*hi) with FP32
+                        accumulation                                            */
+} redo_precision;
+
+/* Device status counters (int64 each), indices into dev_status. */
+typedef enum {
+  REDO_STATUS_NONFINITE = 0,   /* control coefficients that were NaN or +-Inf    */
+  REDO_STATUS_SATURATED = 1,   /* coefficients clamped to the ends of the grid   */
+  REDO_STATUS_TIMEOUT = 2,     /* a bounded device wait gave up (should be 0)    */
+  REDO_STATUS_BADINDEX = 3,    /* a level index outside [0, levels) was seen     */
+  REDO_STATUS_WORDS = 4
+} redo_status_word;
+
+typedef struct redo_table redo_table;
+
+/*
+ * redo_build_table -- one-time discrete-operator table (Section II, process 1).
+ *
+ * Stores, for every control term k < K, digit j < digits and digit value
+ * c < base, the operator
+ *     T[k][j][c] = exp(-i dt theta_kjc H_k),
+ *     theta_k0c = lo[k] + c delta_k,   theta_kjc = c base^j delta_k  (j >= 1),
+ *     delta_k   = (hi[k] - lo[k]) / (base^digits - 1),
+ * i.e. Eq. (redoform) with the c b^j dt scaling of the worked example of
+ * Section II and the grid offset lo[k] carried by digit 0, so that
+ *     prod_j T[k][j][c_j] = exp(-i dt (lo[k] + q delta_k) H_k)
+ * for the level q = sum_j c_j base^j.  The drift step D = exp(-i dt H0) is
+ * folded into the digit-0 operators of term 0 (T[0][0][c] <- T[0][0][c] D).
+ * Exponentials are FP64 scaling-and-squaring Taylor series on the GPU.
+ *
+ *  N        Hilbert-space dimension, 2 <= N <= 64.
+ *  K        number of control terms, 1 <= K <= 64.
+ *  dt       time step in seconds (> 0).
+ *  H0       device, complex128 [N][N], Hermitian drift (rad/s).
+ *  Hk       device, complex128 [K][N][N], Hermitian control operators.
+ *  lo, hi   HOST double [K], ends of each coefficient's level grid (lo < hi).
+ *  base     digit base b >= 2;  digits d >= 1;  base^digits <= 2^24 levels.
+ *  flags    REDO_TABLE_FP32 also builds the FP32 copy used by REDO_FP32;
+ *           REDO_TABLE_FP16X3 also builds the split-FP16 operand planes used
+ *           by REDO_FP16X3 (N = 64 only).  The FP64 copy is always built.
+ *  stream   stream for the build; synchronised before returning.
+ *  out      receives the handle; free with redo_table_free.
+ * Errors: REDO_ERR_INVALID, REDO_ERR_NOT_HERMITIAN (relative tolerance 1e-12
+ * on max |H - H^dag|), REDO_ERR_OOM, REDO_ERR_CUDA.
+ */
+#define REDO_TABLE_FP32 0x1u
+#define REDO_TABLE_FP16X3 0x2u
+redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, const void* Hk,
+                             const double* lo, const double* hi, int32_t base, int32_t digits,
+                             uint32_t flags, void* stream, redo_table** out);
+
+/* Releases the table's device memory (synchronises the build stream). */
+redo_status redo_table_free(redo_table* t);
+
+/*
+ * redo_table_info -- sizes of a table (host call, no device work).
+ * Any output pointer may be NULL.  `entries` = K*digits*base operators.
+ */
+redo_status redo_table_info(const redo_table* t, int32_t* N, int32_t* K, int32_t* base,
+                            int32_t* digits, int64_t* levels, int64_t* entries);
+
+/*
+ * redo_table_copy -- copy the FP64 table (device, complex128 [K][digits][base][N][N],
+ * drift folded into term 0 digit 0) and/or the drift D (device, complex128 [N][N])
+ * into caller buffers.  Either destination may be NULL.  Asynchronous on stream.
+ */
+redo_status redo_table_copy(const redo_table* t, void* table_out, void* drift_out, void* stream);
+
+/*
+ * redo_quantize -- coarse-grain coefficients to level indices (Eq. cgrain).
+ *
+ * q[b][n][k] = clamp(rint((u[b][n][k] - lo[k]) / delta_k), 0, levels - 1),
+ * computed with one IEEE FP64 subtract and one IEEE FP64 divide (no fused
+ * multiply-add) and round-half-to-even, so the result is bit-identical to any
+ * IEEE implementation of the same formula.  NaN/Inf coefficients give q = 0
+ * and count in dev_status[REDO_STATUS_NONFINITE]; out-of-range coefficients
+ * are clamped and counted in dev_status[REDO_STATUS_SATURATED].
+ *
+ *  u    device double [B][M][K];  q  device int32 [B][M][K] (may not alias u).
+ *  dev_status  device int64 [REDO_STATUS_WORDS] or NULL.
+ */
+redo_status redo_quantize(const redo_table* t, const double* u, int64_t B, int64_t M, int32_t* q,
+                          int64_t* dev_status, void* stream);
+
+/*
+ * redo_propagate -- REDO propagators of B pulses (Section II process 2,
+ * Section III chain U = U_M ... U_1).
+ *
+ * For each pulse b, multiplies the M*K*digits gathered table operators in time
+ * order.  The chain is cut into segments whose products are formed in
+ * parallel and then multiplied in order (association changes only rounding).
+ *
+ *  q           device int32 [B][M][K] level indices (from redo_quantize).
+ *  prec        REDO_FP64, REDO_FP32 or REDO_FP16X3 (the last needs the table
+ *              built with REDO_TABLE_FP16X3).
+ *  reunit_every  reserved, must be 0.
+ *  U_out       device complex128 [B][N][N]; receives U_b.  May be NULL if F is wanted only.
+ *  U_target    device complex128 [N][N] or NULL.
+ *  F_out       device double [B]: |Tr(U_target^dag U_b)|^2 / N^2 (FP64 reduction);
+ *              required iff U_target is given.
+ *  tau_out     device complex128 [B] (Tr(U_target^dag U_b)) or NULL.
+ *  workspace   device scratch of at least redo_propagate_workspace() bytes,
+ *              256-byte aligned; contents are overwritten.
+ *  dev_status  device int64 [REDO_STATUS_WORDS] or NULL.
+ * Level indices outside [0, levels) are counted in REDO_STATUS_BADINDEX and
+ * replaced by 0.
+ */
+redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                           redo_precision prec, int32_t reunit_every, void* U_out,
+                           const void* U_target, double* F_out, void* tau_out, void* workspace,
+                           size_t workspace_bytes, int64_t* dev_status, void* stream);
+
+/* Scratch bytes redo_propagate needs for (B, M, prec) on this table. */
+redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
+                                     redo_precision prec, size_t* bytes);
+
+/*
+ * Kernel timing for measurement.  While enabled, the library brackets each of
+ * its kernel launches with CUDA events on the launching stream.  Phases:
+ *   0 quantize, 1 table, 2 chain segments, 3 chain combine, 4 finalize,
+ *   5 tensor-core chain, 6 reserved, 7 reserved.
+ * redo_profile_read synchronises on the recorded events, adds each phase's
+ * elapsed milliseconds and launch count into ms_out[p] / launches_out[p]
+ * (arrays of n <= REDO_PROFILE_PHASES entries, either may be NULL) and clears
+ * the record.  Not thread-safe; meant for benchmarks, not production.
+ */
+#define REDO_PROFILE_PHASES 8
+redo_status redo_profile_enable(int32_t enable);
+redo_status redo_profile_read(double* ms_out, int64_t* launches_out, int32_t n);
+
+/* Thread-local description of the last error returned on this thread. */
+const char* redo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REDO_H */

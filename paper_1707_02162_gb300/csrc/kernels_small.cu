@@ -1,0 +1,643 @@
+// SIMT kernels of libredo for N <= 64: quantizer, FP64 operator table,
+// segmented product chains (FP64 / FP32) and the FP64 fidelity epilogue.
+//
+// Every product here is a complex N x N matrix product held in shared memory;
+// table operators are streamed in with bulk asynchronous copies
+// (cp.async.bulk + mbarrier), several stages ahead of the product that uses
+// them.  All device waits are bounded and report through the status words.
+#include <cstdio>
+#include <type_traits>
+
+#include "redo_internal.cuh"
+#include "device_sync.cuh"
+
+namespace redo {
+
+// ============================================================================
+// Quantizer -- Eq. (cgrain): level q = clamp(rint((u - lo_k) / delta_k))
+// ============================================================================
+__global__ void quantize_kernel(const double* __restrict__ u, int64_t count, int K,
+                                const double* __restrict__ lo, const double* __restrict__ delta,
+                                int64_t levels, int32_t* __restrict__ q, int64_t* status) {
+  unsigned nonfinite = 0, saturated = 0;
+  const double top = (double)(levels - 1);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % K);
+    const double v = u[i];
+    int32_t r = 0;
+    if (!isfinite(v)) {
+      ++nonfinite;
+    } else {
+      // one IEEE subtract, one IEEE divide (no contraction), round half to even
+      const double x = rint(__ddiv_rn(__dsub_rn(v, lo[k]), delta[k]));
+      if (x < 0.0) {
+        ++saturated;
+        r = 0;
+      } else if (x > top) {
+        ++saturated;
+        r = (int32_t)(levels - 1);
+      } else {
+        r = (int32_t)x;
+      }
+    }
+    q[i] = r;
+  }
+  if (status) {
+    // warp-aggregate the counters, one atomic per warp and word
+    for (int off = 16; off > 0; off >>= 1) {
+      nonfinite += __shfl_down_sync(0xffffffffu, nonfinite, off);
+      saturated += __shfl_down_sync(0xffffffffu, saturated, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (nonfinite) atomicAdd((unsigned long long*)&status[REDO_STATUS_NONFINITE], nonfinite);
+      if (saturated) atomicAdd((unsigned long long*)&status[REDO_STATUS_SATURATED], saturated);
+    }
+  }
+}
+
+cudaError_t launch_quantize(const double* u, int64_t count, int K, const double* lo,
+                            const double* delta, int64_t levels, int32_t* q, int64_t* status,
+                            cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  quantize_kernel<<<(unsigned)blocks, 256, 0, s>>>(u, count, K, lo, delta, levels, q, status);
+  return cudaGetLastError();
+}
+
+// ============================================================================
+// Shared-memory complex matrix product  Y = A * X  (N x N, row-major)
+// Thread lt of a chain owns rows ty + TY*a and columns tx + TX*c.
+// ============================================================================
+template <typename R, int N, int TM, int TN>
+struct SmemMM {
+  static constexpr int TY = N / TM, TX = N / TN, THREADS = TY * TX;
+  static_assert(TY * TM == N && TX * TN == N, "tile must divide N");
+  __device__ __forceinline__ static void run(const cplx<R>* __restrict__ A,
+                                             const cplx<R>* __restrict__ X, int lt,
+                                             cplx<R> (&Y)[TM][TN]) {
+    const int ty = lt / TX, tx = lt % TX;
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int c = 0; c < TN; ++c) Y[a][c] = cmake<R>(R(0), R(0));
+#pragma unroll 4
+    for (int k = 0; k < N; ++k) {
+      cplx<R> av[TM], xv[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) av[a] = A[(ty + TY * a) * N + k];
+#pragma unroll
+      for (int c = 0; c < TN; ++c) xv[c] = X[k * N + tx + TX * c];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) cfma<R>(Y[a][c], av[a], xv[c]);
+    }
+  }
+  __device__ __forceinline__ static void store(cplx<R>* __restrict__ X, int lt,
+                                               const cplx<R> (&Y)[TM][TN]) {
+    const int ty = lt / TX, tx = lt % TX;
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int c = 0; c < TN; ++c) X[(ty + TY * a) * N + tx + TX * c] = Y[a][c];
+  }
+};
+
+// Per-N tiling: 256 threads per chain for N >= 16; smaller N packs several
+// independent chains into one CTA.
+template <int N> struct Tiling;
+template <> struct Tiling<64> { static constexpr int TM = 4, TN = 4, CH = 1; };
+template <> struct Tiling<32> { static constexpr int TM = 2, TN = 2, CH = 1; };
+template <> struct Tiling<16> { static constexpr int TM = 1, TN = 1, CH = 1; };
+template <> struct Tiling<8> { static constexpr int TM = 1, TN = 1, CH = 4; };
+template <> struct Tiling<4> { static constexpr int TM = 1, TN = 1, CH = 16; };
+template <> struct Tiling<2> { static constexpr int TM = 1, TN = 1, CH = 64; };
+
+// ============================================================================
+// FP64 operator table: scaling-and-squaring Taylor exponential, one CTA per
+// operator.  exp(A) with A = -i dt theta H: halve A until ||A||_1 <= 1/2,
+// sum the Taylor series by Horner's rule to the first degree m whose
+// remainder bound ||A||^(m+1)/(m+1)! is below 1e-18, then square back.
+// ============================================================================
+template <int N>
+__global__ void __launch_bounds__(SmemMM<double, N, (N >= 64 ? 4 : (N >= 32 ? 2 : 1)),
+                                         (N >= 64 ? 4 : (N >= 32 ? 2 : 1))>::THREADS)
+table_expm_kernel(const double2* __restrict__ H0, const double2* __restrict__ Hk, int K,
+                  int digits, int base, double dt, const double* __restrict__ lo,
+                  const double* __restrict__ delta, int64_t entries, double2* __restrict__ T,
+                  double2* __restrict__ D) {
+  constexpr int TM = (N >= 64 ? 4 : (N >= 32 ? 2 : 1));
+  using MM = SmemMM<double, N, TM, TM>;
+  constexpr int N2 = N * N;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* P = A + N2;
+  __shared__ double colsum[N];
+  const int lt = threadIdx.x;
+  const int64_t e = blockIdx.x;
+  const double2* H;
+  double theta;
+  double2* out;
+  if (e == entries) {
+    H = H0;
+    theta = 1.0;
+    out = D;
+  } else {
+    const int c = (int)(e % base);
+    const int j = (int)((e / base) % digits);
+    const int k = (int)(e / ((int64_t)base * digits));
+    H = Hk + (int64_t)k * N2;
+    if (j == 0) {
+      theta = __dadd_rn(lo[k], __dmul_rn((double)c, delta[k]));  // no contraction
+    } else {
+      double bj = 1.0;
+      for (int i = 0; i < j; ++i) bj *= (double)base;
+      theta = __dmul_rn((double)c * bj, delta[k]);
+    }
+    out = T + e * N2;
+  }
+  const double sc = dt * theta;
+  for (int i = lt; i < N2; i += MM::THREADS) {
+    const double2 h = H[i];
+    A[i] = make_double2(sc * h.y, -sc * h.x);   // -i sc (h.x + i h.y)
+  }
+  __syncthreads();
+  if (lt < N) {
+    double s = 0.0;
+    for (int r = 0; r < N; ++r) s += hypot(A[r * N + lt].x, A[r * N + lt].y);
+    colsum[lt] = s;
+  }
+  __syncthreads();
+  double nrm = 0.0;
+  for (int i = 0; i < N; ++i) nrm = fmax(nrm, colsum[i]);
+  int sq = 0;
+  while (nrm > 0.5 && sq < 1000) {
+    nrm *= 0.5;
+    ++sq;
+  }
+  int m = 0;
+  if (nrm > 0.0) {
+    double term = nrm;  // nrm^(m+1)/(m+1)! for m = 0
+    m = 1;
+    term = term * nrm / 2.0;
+    while (term > 1e-18 && m < 30) {
+      ++m;
+      term = term * nrm / (double)(m + 1);
+    }
+  }
+  const double scale = ldexp(1.0, -sq);
+  for (int i = lt; i < N2; i += MM::THREADS) {
+    const double2 a = A[i];
+    A[i] = make_double2(a.x * scale, a.y * scale);
+    P[i] = make_double2((i / N == i % N) ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  double2 Y[TM][TM];
+  for (int it = m; it >= 1; --it) {
+    MM::run(A, P, lt, Y);
+    __syncthreads();
+    const double inv = 1.0 / (double)it;
+    const int ty = lt / MM::TX, tx = lt % MM::TX;
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int c = 0; c < TM; ++c) {
+        const int r = ty + MM::TY * a, col = tx + MM::TX * c;
+        P[r * N + col] = make_double2(Y[a][c].x * inv + (r == col ? 1.0 : 0.0), Y[a][c].y * inv);
+      }
+    __syncthreads();
+  }
+  for (int it = 0; it < sq; ++it) {
+    MM::run(P, P, lt, Y);
+    __syncthreads();
+    MM::store(P, lt, Y);
+    __syncthreads();
+  }
+  for (int i = lt; i < N2; i += MM::THREADS) out[i] = P[i];
+}
+
+// T[0][0][c] <- T[0][0][c] * D  (drift applied first in time)
+template <int N>
+__global__ void __launch_bounds__(SmemMM<double, N, (N >= 64 ? 4 : (N >= 32 ? 2 : 1)),
+                                         (N >= 64 ? 4 : (N >= 32 ? 2 : 1))>::THREADS)
+table_fold_kernel(double2* __restrict__ T, const double2* __restrict__ D) {
+  constexpr int TM = (N >= 64 ? 4 : (N >= 32 ? 2 : 1));
+  using MM = SmemMM<double, N, TM, TM>;
+  constexpr int N2 = N * N;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* X = A + N2;
+  double2* Tc = T + (int64_t)blockIdx.x * N2;
+  for (int i = threadIdx.x; i < N2; i += MM::THREADS) {
+    A[i] = Tc[i];
+    X[i] = D[i];
+  }
+  __syncthreads();
+  double2 Y[TM][TM];
+  MM::run(A, X, threadIdx.x, Y);
+  __syncthreads();
+  MM::store(A, threadIdx.x, Y);
+  __syncthreads();
+  for (int i = threadIdx.x; i < N2; i += MM::THREADS) Tc[i] = A[i];
+}
+
+template <int N>
+static cudaError_t table_expm_n(const redo_table* t, const double2* H0, const double2* Hk,
+                                cudaStream_t s) {
+  constexpr int TM = (N >= 64 ? 4 : (N >= 32 ? 2 : 1));
+  using MM = SmemMM<double, N, TM, TM>;
+  const size_t smem = 2 * sizeof(double2) * N * N;
+  cudaError_t e = cudaFuncSetAttribute(table_expm_kernel<N>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  table_expm_kernel<N><<<(unsigned)(t->entries + 1), MM::THREADS, smem, s>>>(
+      H0, Hk, t->K, t->digits, t->base, t->dt, t->d_lo, t->d_delta, t->entries, t->T64, t->D64);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t table_fold_n(const redo_table* t, cudaStream_t s) {
+  constexpr int TM = (N >= 64 ? 4 : (N >= 32 ? 2 : 1));
+  using MM = SmemMM<double, N, TM, TM>;
+  const size_t smem = 2 * sizeof(double2) * N * N;
+  cudaError_t e = cudaFuncSetAttribute(table_fold_kernel<N>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  table_fold_kernel<N><<<(unsigned)t->base, MM::THREADS, smem, s>>>(t->T64, t->D64);
+  return cudaGetLastError();
+}
+
+#define REDO_DISPATCH_N(N_, CALL)          \
+  switch (N_) {                            \
+    case 2: return CALL<2>;                \
+    case 4: return CALL<4>;                \
+    case 8: return CALL<8>;                \
+    case 16: return CALL<16>;              \
+    case 32: return CALL<32>;              \
+    case 64: return CALL<64>;              \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_table_expm(const redo_table* t, const double2* H0, const double2* Hk,
+                              cudaStream_t s) {
+  switch (t->N) {
+    case 2: return table_expm_n<2>(t, H0, Hk, s);
+    case 4: return table_expm_n<4>(t, H0, Hk, s);
+    case 8: return table_expm_n<8>(t, H0, Hk, s);
+    case 16: return table_expm_n<16>(t, H0, Hk, s);
+    case 32: return table_expm_n<32>(t, H0, Hk, s);
+    case 64: return table_expm_n<64>(t, H0, Hk, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_table_fold_drift(const redo_table* t, cudaStream_t s) {
+  switch (t->N) {
+    case 2: return table_fold_n<2>(t, s);
+    case 4: return table_fold_n<4>(t, s);
+    case 8: return table_fold_n<8>(t, s);
+    case 16: return table_fold_n<16>(t, s);
+    case 32: return table_fold_n<32>(t, s);
+    case 64: return table_fold_n<64>(t, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+__global__ void to_fp32_kernel(const double2* __restrict__ src, float2* __restrict__ dst,
+                               int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = src[i];
+    dst[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+cudaError_t launch_to_fp32(const double2* src, float2* dst, int64_t count, cudaStream_t s) {
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  to_fp32_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+// ============================================================================
+// Segmented product chains (Eq. exp2prod per term, chained over time)
+// ============================================================================
+
+// Factor f of pulse b is table operator (k, j, c) with
+//   n = f / (K d), k = (f mod K d) / d, j = f mod d, c = floor(q[b][n][k] / base^j) mod base.
+// Factor 0 (drift-folded digit 0 of term 0, step 0) is applied first.
+template <typename R>
+struct GatherSrc {
+  const cplx<R>* T;
+  const int32_t* q;
+  int64_t M;
+  int K, d, base;
+  int64_t levels;
+  int64_t* status;
+  __device__ __forceinline__ const cplx<R>* addr(int64_t b, int64_t f, int N2) const {
+    const int64_t kd = (int64_t)K * d;
+    const int64_t n = f / kd;
+    const int r = (int)(f - n * kd);
+    const int k = r / d, j = r - k * d;
+    int32_t qv = q[(b * M + n) * K + k];
+    if (qv < 0 || qv >= levels) {
+      if (status) atomicAdd((unsigned long long*)&status[REDO_STATUS_BADINDEX], 1ull);
+      qv = 0;
+    }
+    for (int i = 0; i < j; ++i) qv /= base;
+    const int c = qv % base;
+    return T + ((int64_t)(k * d + j) * base + c) * N2;
+  }
+};
+
+// Factor f of unit b is P[b][f] (an ordered list of earlier segment products).
+template <typename R>
+struct DenseSrc {
+  const cplx<R>* P;
+  int64_t per_unit;
+  __device__ __forceinline__ const cplx<R>* addr(int64_t b, int64_t f, int N2) const {
+    return P + (b * per_unit + f) * N2;
+  }
+};
+
+template <typename R, int N, int STAGES, class Src>
+__global__ void __launch_bounds__(SmemMM<R, N, Tiling<N>::TM, Tiling<N>::TN>::THREADS * Tiling<N>::CH)
+chain_kernel(Src src, int64_t units, int64_t segs_per_unit, int64_t seg_len, int64_t total_len,
+             cplx<R>* __restrict__ out, int64_t* status) {
+  using TL = Tiling<N>;
+  using MM = SmemMM<R, N, TL::TM, TL::TN>;
+  constexpr int CH = TL::CH;
+  constexpr int N2 = N * N;
+  constexpr uint32_t BYTES = (uint32_t)(N2 * sizeof(cplx<R>));
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cplx<R>* Xall = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* Aall = Xall + CH * N2;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Aall + CH * STAGES * N2);
+  __shared__ int abort_flag;
+
+  const int ch = threadIdx.x / MM::THREADS;
+  const int lt = threadIdx.x - ch * MM::THREADS;
+  const int64_t G = units * segs_per_unit;
+
+  // every thread derives the lengths of all chains of the CTA (uniform loop bound)
+  int64_t maxlen = 0, my_len = 0, my_f0 = 0, my_unit = 0;
+  for (int c = 0; c < CH; ++c) {
+    const int64_t g = (int64_t)blockIdx.x * CH + c;
+    int64_t len = 0, f0 = 0;
+    if (g < G) {
+      const int64_t s = g % segs_per_unit;
+      f0 = s * seg_len;
+      int64_t f1 = f0 + seg_len;
+      if (f1 > total_len) f1 = total_len;
+      len = f1 > f0 ? f1 - f0 : 0;
+    }
+    if (len > maxlen) maxlen = len;
+    if (c == ch) {
+      my_len = len;
+      my_f0 = f0;
+      my_unit = g / segs_per_unit;
+    }
+  }
+  const int64_t my_g = (int64_t)blockIdx.x * CH + ch;
+  cplx<R>* X = Xall + ch * N2;
+  cplx<R>* A = Aall + ch * STAGES * N2;
+  uint64_t* bar = bars + ch * STAGES;
+
+  if (threadIdx.x == 0) abort_flag = 0;
+  if (lt < STAGES) mbar_init(&bar[lt], 1);
+  fence_mbarrier_init();
+  for (int i = lt; i < N2; i += MM::THREADS)
+    X[i] = cmake<R>((i / N == i % N) ? R(1) : R(0), R(0));
+  __syncthreads();
+  if (lt == 0) {
+    for (int s = 0; s < STAGES && s < my_len; ++s) {
+      mbar_arrive_expect_tx(&bar[s], BYTES);
+      bulk_load(A + s * N2, src.addr(my_unit, my_f0 + s, N2), BYTES, &bar[s]);
+    }
+  }
+  cplx<R> Y[TL::TM][TL::TN];
+  for (int64_t t = 0; t < maxlen; ++t) {
+    const int stage = (int)(t % STAGES);
+    const uint32_t parity = (uint32_t)((t / STAGES) & 1);
+    const bool active = t < my_len;
+    if (active) {
+      if (!mbar_wait_bounded(&bar[stage], parity)) {
+        abort_flag = 1;
+      } else {
+        MM::run(A + stage * N2, X, lt, Y);
+      }
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    if (active) {
+      MM::store(X, lt, Y);
+      if (lt == 0 && t + STAGES < my_len) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[stage], BYTES);
+        bulk_load(A + stage * N2, src.addr(my_unit, my_f0 + t + STAGES, N2), BYTES, &bar[stage]);
+      }
+    }
+    __syncthreads();
+  }
+  if (abort_flag) {
+    if (threadIdx.x == 0 && status)
+      atomicAdd((unsigned long long*)&status[REDO_STATUS_TIMEOUT], 1ull);
+    return;
+  }
+  if (my_g < G) {
+    cplx<R>* o = out + my_g * N2;
+    for (int i = lt; i < N2; i += MM::THREADS) o[i] = X[i];
+  }
+}
+
+template <typename R, int N>
+struct ChainCfg {
+  static constexpr int STAGES = (N >= 64) ? 2 : ((N >= 32) ? 3 : 4);
+  static constexpr int THREADS = SmemMM<R, N, Tiling<N>::TM, Tiling<N>::TN>::THREADS * Tiling<N>::CH;
+  static constexpr size_t SMEM =
+      (size_t)Tiling<N>::CH * (1 + STAGES) * N * N * sizeof(cplx<R>) +
+      (size_t)Tiling<N>::CH * STAGES * sizeof(uint64_t);
+};
+
+template <typename R, int N, class Src>
+static cudaError_t launch_chain_n(Src src, int64_t units, int64_t segs, int64_t seg_len,
+                                  int64_t total_len, cplx<R>* out, int64_t* status,
+                                  cudaStream_t s) {
+  using C = ChainCfg<R, N>;
+  auto kern = chain_kernel<R, N, C::STAGES, Src>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::SMEM);
+  if (e != cudaSuccess) return e;
+  const int64_t G = units * segs;
+  const int64_t blocks = (G + Tiling<N>::CH - 1) / Tiling<N>::CH;
+  if (blocks == 0) return cudaSuccess;
+  kern<<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(src, units, segs, seg_len, total_len, out,
+                                                      status);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static int chain_slots(int N, int num_sms) {
+  size_t smem = 0;
+  int ch = 1;
+  switch (N) {
+#define CASE(n)                         \
+  case n:                               \
+    smem = ChainCfg<R, n>::SMEM;        \
+    ch = Tiling<n>::CH;                 \
+    break;
+    CASE(2) CASE(4) CASE(8) CASE(16) CASE(32) CASE(64)
+#undef CASE
+    default: break;
+  }
+  int per_sm = smem ? (int)((220 * 1024) / smem) : 1;
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 8) per_sm = 8;
+  return num_sms * per_sm * ch;
+}
+
+ChainPlan plan_chain(const redo_table* t, int64_t B, int64_t M, int prec) {
+  ChainPlan p;
+  p.B = B;
+  p.M = M;
+  p.F = M * (int64_t)t->K * t->digits;
+  const int slots = prec == REDO_FP64 ? chain_slots<double>(t->N, t->num_sms)
+                                      : chain_slots<float>(t->N, t->num_sms);
+  // about two segments per resident chain, each at least 16 factors long
+  int64_t S = (2 * (int64_t)slots + B - 1) / (B > 0 ? B : 1);
+  const int64_t max_s = (p.F + 15) / 16;
+  if (S > max_s) S = max_s;
+  if (S > 1024) S = 1024;
+  if (S < 1) S = 1;
+  p.seg_len = p.F > 0 ? (p.F + S - 1) / S : 0;
+  p.S = p.seg_len > 0 ? (p.F + p.seg_len - 1) / p.seg_len : 1;
+  return p;
+}
+
+size_t chain_workspace_bytes(const redo_table* t, const ChainPlan& p, int prec) {
+  const size_t el = prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t n2 = (size_t)t->N * t->N;
+  const size_t seg = (size_t)p.B * p.S * n2 * el;
+  const size_t prod = (size_t)p.B * n2 * el;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return up(seg) + up(prod);
+}
+
+template <typename R>
+static cudaError_t chain_segments_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
+                                    void* seg_out, int64_t* status, cudaStream_t s) {
+  GatherSrc<R> src;
+  src.T = std::is_same<R, double>::value ? (const cplx<R>*)t->T64 : (const cplx<R>*)t->T32;
+  src.q = q;
+  src.M = p.M;
+  src.K = t->K;
+  src.d = t->digits;
+  src.base = t->base;
+  src.levels = t->levels;
+  src.status = status;
+  cplx<R>* out = (cplx<R>*)seg_out;
+  switch (t->N) {
+    case 2: return launch_chain_n<R, 2>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
+    case 4: return launch_chain_n<R, 4>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
+    case 8: return launch_chain_n<R, 8>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
+    case 16: return launch_chain_n<R, 16>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
+    case 32: return launch_chain_n<R, 32>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
+    case 64: return launch_chain_n<R, 64>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_chain_segments(const redo_table* t, const int32_t* q, const ChainPlan& p,
+                                  int prec, void* seg_out, int64_t* status, cudaStream_t s) {
+  if (prec == REDO_FP64) return chain_segments_t<double>(t, q, p, seg_out, status, s);
+  return chain_segments_t<float>(t, q, p, seg_out, status, s);
+}
+
+template <typename R>
+static cudaError_t chain_combine_t(const redo_table* t, const ChainPlan& p, const void* seg_in,
+                                   void* prod_out, int64_t* status, cudaStream_t s) {
+  DenseSrc<R> src;
+  src.P = (const cplx<R>*)seg_in;
+  src.per_unit = p.S;
+  cplx<R>* out = (cplx<R>*)prod_out;
+  const int64_t L = p.F > 0 ? p.S : 0;
+  switch (t->N) {
+    case 2: return launch_chain_n<R, 2>(src, p.B, 1, L, L, out, status, s);
+    case 4: return launch_chain_n<R, 4>(src, p.B, 1, L, L, out, status, s);
+    case 8: return launch_chain_n<R, 8>(src, p.B, 1, L, L, out, status, s);
+    case 16: return launch_chain_n<R, 16>(src, p.B, 1, L, L, out, status, s);
+    case 32: return launch_chain_n<R, 32>(src, p.B, 1, L, L, out, status, s);
+    case 64: return launch_chain_n<R, 64>(src, p.B, 1, L, L, out, status, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_chain_combine(const redo_table* t, const ChainPlan& p, int prec,
+                                 const void* seg_in, void* prod_out, int64_t* status,
+                                 cudaStream_t s) {
+  if (prec == REDO_FP64) return chain_combine_t<double>(t, p, seg_in, prod_out, status, s);
+  return chain_combine_t<float>(t, p, seg_in, prod_out, status, s);
+}
+
+// ============================================================================
+// Epilogue: U_out (complex128), tau = Tr(U_T^dag U) and F = |tau|^2 / N^2,
+// reduced in FP64 in a fixed order (deterministic).
+// ============================================================================
+template <typename R>
+__global__ void __launch_bounds__(256)
+finalize_kernel(int N, const cplx<R>* __restrict__ prod, double2* __restrict__ U_out,
+                const double2* __restrict__ U_target, double* __restrict__ F_out,
+                double2* __restrict__ tau_out) {
+  const int64_t b = blockIdx.x;
+  const int N2 = N * N;
+  const cplx<R>* P = prod + b * N2;
+  double re = 0.0, im = 0.0;
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+    const cplx<R> v = P[i];
+    const double2 u = make_double2((double)v.x, (double)v.y);
+    if (U_out) U_out[b * N2 + i] = u;
+    if (U_target) {
+      const double2 g = U_target[i];
+      // conj(g) * u
+      re = fma(g.x, u.x, re);
+      re = fma(g.y, u.y, re);
+      im = fma(g.x, u.y, im);
+      im = fma(-g.y, u.x, im);
+    }
+  }
+  if (!U_target) return;
+  __shared__ double sre[256], sim[256];
+  sre[threadIdx.x] = re;
+  sim[threadIdx.x] = im;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sre[threadIdx.x] += sre[threadIdx.x + w];
+      sim[threadIdx.x] += sim[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double tr = sre[0], ti = sim[0];
+    if (F_out) F_out[b] = (tr * tr + ti * ti) / ((double)N * (double)N);
+    if (tau_out) tau_out[b] = make_double2(tr, ti);
+  }
+}
+
+cudaError_t launch_finalize(const redo_table* t, int64_t B, int prec, const void* prod,
+                            void* U_out, const double2* U_target, double* F_out, double2* tau_out,
+                            cudaStream_t s) {
+  if (B == 0) return cudaSuccess;
+  if (prec == REDO_FP64)
+    finalize_kernel<double><<<(unsigned)B, 256, 0, s>>>(t->N, (const double2*)prod,
+                                                         (double2*)U_out, U_target, F_out, tau_out);
+  else
+    finalize_kernel<float><<<(unsigned)B, 256, 0, s>>>(t->N, (const float2*)prod,
+                                                        (double2*)U_out, U_target, F_out, tau_out);
+  return cudaGetLastError();
+}
+
+}  // namespace redo

@@ -1,0 +1,310 @@
+// Host side of the libredo C ABI: argument checks, table ownership, launch order.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "redo_internal.cuh"
+
+namespace redo {
+
+static thread_local char g_err[512] = "";
+
+redo_status set_error(redo_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+redo_status cuda_error(cudaError_t e, const char* what) {
+  return set_error(REDO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// Optional event timing of the library's own launches (benchmarks only)
+// ---------------------------------------------------------------------------
+struct ProfRecord {
+  int phase;
+  cudaEvent_t a, b;
+};
+static bool g_prof_on = false;
+static std::vector<ProfRecord> g_prof;
+
+struct ProfScope {
+  ProfRecord r{-1, nullptr, nullptr};
+  cudaStream_t s;
+  ProfScope(int phase, cudaStream_t st) : s(st) {
+    if (!g_prof_on) return;
+    r.phase = phase;
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+      r.phase = -1;
+      return;
+    }
+    cudaEventRecord(r.a, s);
+  }
+  ~ProfScope() {
+    if (r.phase < 0) return;
+    cudaEventRecord(r.b, s);
+    g_prof.push_back(r);
+  }
+};
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+static redo_status check_hermitian(const std::vector<double>& h, int N, const char* name, int k) {
+  double mx = 0.0, dev = 0.0;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      const double ar = h[2 * (i * N + j)], ai = h[2 * (i * N + j) + 1];
+      const double br = h[2 * (j * N + i)], bi = h[2 * (j * N + i) + 1];
+      mx = std::fmax(mx, std::hypot(ar, ai));
+      dev = std::fmax(dev, std::hypot(ar - br, ai + bi));
+      if (!std::isfinite(ar) || !std::isfinite(ai))
+        return set_error(REDO_ERR_INVALID, "%s[%d] has a non-finite entry", name, k);
+    }
+  if (dev > 1e-12 * (mx > 0 ? mx : 1.0))
+    return set_error(REDO_ERR_NOT_HERMITIAN, "%s[%d] is not Hermitian (max |H-H^dag| = %g)", name,
+                     k, dev);
+  return REDO_OK;
+}
+
+}  // namespace redo
+
+using namespace redo;
+
+extern "C" {
+
+const char* redo_last_error(void) { return g_err; }
+
+redo_status redo_profile_enable(int32_t enable) {
+  g_prof_on = enable != 0;
+  return REDO_OK;
+}
+
+redo_status redo_profile_read(double* ms_out, int64_t* launches_out, int32_t n) {
+  if (n < 0 || n > REDO_PROFILE_PHASES) return set_error(REDO_ERR_INVALID, "n out of range");
+  for (auto& r : g_prof) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess &&
+        r.phase < n) {
+      if (ms_out) ms_out[r.phase] += ms;
+      if (launches_out) launches_out[r.phase] += 1;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof.clear();
+  return REDO_OK;
+}
+
+redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, const void* Hk,
+                             const double* lo, const double* hi, int32_t base, int32_t digits,
+                             uint32_t flags, void* stream, redo_table** out) {
+  if (!out) return set_error(REDO_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!H0 || !Hk || !lo || !hi) return set_error(REDO_ERR_INVALID, "null input pointer");
+  if (N < 2 || N > kMaxN || !is_pow2(N))
+    return set_error(REDO_ERR_UNSUPPORTED, "N=%d: this build supports N in {2,4,...,64}", N);
+  if (K < 1 || K > kMaxK) return set_error(REDO_ERR_INVALID, "K=%d out of [1, %d]", K, kMaxK);
+  if (!(dt > 0) || !std::isfinite(dt)) return set_error(REDO_ERR_INVALID, "dt must be > 0");
+  if (base < 2 || digits < 1) return set_error(REDO_ERR_INVALID, "base >= 2 and digits >= 1");
+  double lv = 1.0;
+  for (int j = 0; j < digits; ++j) lv *= base;
+  if (lv > (double)(1 << 24)) return set_error(REDO_ERR_INVALID, "base^digits > 2^24 levels");
+  for (int k = 0; k < K; ++k)
+    if (!(hi[k] > lo[k]) || !std::isfinite(lo[k]) || !std::isfinite(hi[k]))
+      return set_error(REDO_ERR_INVALID, "term %d: need finite lo < hi", k);
+  if ((flags & REDO_TABLE_FP16X3) && N != 64)
+    return set_error(REDO_ERR_UNSUPPORTED, "REDO_TABLE_FP16X3 needs N = 64");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // Hermitian check on the host (one synchronous copy, build time only)
+  const size_t n2 = (size_t)N * N;
+  std::vector<double> h(2 * n2 * (K + 1));
+  REDO_CUDA_TRY(cudaMemcpyAsync(h.data(), H0, 2 * n2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  REDO_CUDA_TRY(cudaMemcpyAsync(h.data() + 2 * n2, Hk, 2 * n2 * K * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+  REDO_CUDA_TRY(cudaStreamSynchronize(s));
+  {
+    std::vector<double> one(2 * n2);
+    for (int k = -1; k < K; ++k) {
+      std::memcpy(one.data(), h.data() + 2 * n2 * (k + 1), 2 * n2 * sizeof(double));
+      redo_status st = check_hermitian(one, N, k < 0 ? "H0" : "Hk", k < 0 ? 0 : k);
+      if (st != REDO_OK) return st;
+    }
+  }
+
+  redo_table* t = (redo_table*)std::calloc(1, sizeof(redo_table));
+  if (!t) return set_error(REDO_ERR_OOM, "host allocation failed");
+  t->N = N;
+  t->K = K;
+  t->base = base;
+  t->digits = digits;
+  t->levels = (int64_t)lv;
+  t->entries = (int64_t)K * digits * base;
+  t->dt = dt;
+  t->build_stream = s;
+  for (int k = 0; k < K; ++k) {
+    t->lo[k] = lo[k];
+    t->hi[k] = hi[k];
+    t->delta[k] = (hi[k] - lo[k]) / (double)(t->levels - 1);
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (t->num_sms <= 0) t->num_sms = 148;
+
+  auto fail = [&](redo_status st) {
+    redo_table_free(t);
+    return st;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&t->d_lo, sizeof(double) * K)) != cudaSuccess ||
+      (e = cudaMalloc(&t->d_delta, sizeof(double) * K)) != cudaSuccess ||
+      (e = cudaMalloc(&t->T64, sizeof(double2) * n2 * t->entries)) != cudaSuccess ||
+      (e = cudaMalloc(&t->D64, sizeof(double2) * n2)) != cudaSuccess)
+    return fail(set_error(REDO_ERR_OOM, "table allocation: %s", cudaGetErrorString(e)));
+  if ((flags & (REDO_TABLE_FP32 | REDO_TABLE_FP16X3)) &&
+      (e = cudaMalloc(&t->T32, sizeof(float2) * n2 * t->entries)) != cudaSuccess)
+    return fail(set_error(REDO_ERR_OOM, "FP32 table allocation: %s", cudaGetErrorString(e)));
+  if ((e = cudaMemcpyAsync(t->d_lo, t->lo, sizeof(double) * K, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(t->d_delta, t->delta, sizeof(double) * K, cudaMemcpyHostToDevice, s)))
+    return fail(cuda_error(e, "copy lo/delta"));
+  if ((e = launch_table_expm(t, (const double2*)H0, (const double2*)Hk, s)) != cudaSuccess)
+    return fail(cuda_error(e, "table exponentials"));
+  if ((e = launch_table_fold_drift(t, s)) != cudaSuccess)
+    return fail(cuda_error(e, "drift fold"));
+  if (t->T32 && (e = launch_to_fp32(t->T64, t->T32, (int64_t)n2 * t->entries, s)) != cudaSuccess)
+    return fail(cuda_error(e, "FP32 copy"));
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_error(e, "table build"));
+  *out = t;
+  return REDO_OK;
+}
+
+redo_status redo_table_free(redo_table* t) {
+  if (!t) return REDO_OK;
+  if (t->build_stream) cudaStreamSynchronize(t->build_stream);
+  cudaFree(t->d_lo);
+  cudaFree(t->d_delta);
+  cudaFree(t->T64);
+  cudaFree(t->D64);
+  cudaFree(t->T32);
+  cudaFree(t->tc_planes);
+  std::free(t);
+  return REDO_OK;
+}
+
+redo_status redo_table_info(const redo_table* t, int32_t* N, int32_t* K, int32_t* base,
+                            int32_t* digits, int64_t* levels, int64_t* entries) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (N) *N = t->N;
+  if (K) *K = t->K;
+  if (base) *base = t->base;
+  if (digits) *digits = t->digits;
+  if (levels) *levels = t->levels;
+  if (entries) *entries = t->entries;
+  return REDO_OK;
+}
+
+redo_status redo_table_copy(const redo_table* t, void* table_out, void* drift_out, void* stream) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  const size_t n2 = (size_t)t->N * t->N;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (table_out)
+    REDO_CUDA_TRY(cudaMemcpyAsync(table_out, t->T64, sizeof(double2) * n2 * t->entries,
+                                  cudaMemcpyDeviceToDevice, s));
+  if (drift_out)
+    REDO_CUDA_TRY(
+        cudaMemcpyAsync(drift_out, t->D64, sizeof(double2) * n2, cudaMemcpyDeviceToDevice, s));
+  return REDO_OK;
+}
+
+redo_status redo_quantize(const redo_table* t, const double* u, int64_t B, int64_t M, int32_t* q,
+                          int64_t* dev_status, void* stream) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
+  const int64_t count = B * M * t->K;
+  if (count == 0) return REDO_OK;
+  if (!u || !q) return set_error(REDO_ERR_INVALID, "null u or q");
+  ProfScope ps(0, (cudaStream_t)stream);
+  cudaError_t e = launch_quantize(u, count, t->K, t->d_lo, t->d_delta, t->levels, q, dev_status,
+                                  (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "quantize");
+  return REDO_OK;
+}
+
+static redo_status check_prec(const redo_table* t, redo_precision prec) {
+  if (prec == REDO_FP64) return REDO_OK;
+  if (prec == REDO_FP32) {
+    if (!t->T32) return set_error(REDO_ERR_INVALID, "REDO_FP32 needs a table built with REDO_TABLE_FP32");
+    return REDO_OK;
+  }
+  if (prec == REDO_FP16X3) {
+    if (!t->tc_planes)
+      return set_error(REDO_ERR_INVALID, "REDO_FP16X3 needs a table built with REDO_TABLE_FP16X3");
+    return REDO_OK;
+  }
+  return set_error(REDO_ERR_INVALID, "unknown precision %d", (int)prec);
+}
+
+redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
+                                     redo_precision prec, size_t* bytes) {
+  if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
+  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
+  redo_status st = check_prec(t, prec);
+  if (st != REDO_OK) return st;
+  ChainPlan p = plan_chain(t, B, M, prec);
+  *bytes = chain_workspace_bytes(t, p, prec);
+  return REDO_OK;
+}
+
+redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                           redo_precision prec, int32_t reunit_every, void* U_out,
+                           const void* U_target, double* F_out, void* tau_out, void* workspace,
+                           size_t workspace_bytes, int64_t* dev_status, void* stream) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
+  if (reunit_every != 0) return set_error(REDO_ERR_UNSUPPORTED, "reunit_every must be 0");
+  redo_status st = check_prec(t, prec);
+  if (st != REDO_OK) return st;
+  if (B == 0) return REDO_OK;
+  if (M > 0 && !q) return set_error(REDO_ERR_INVALID, "q is NULL");
+  if (U_target && !F_out && !tau_out)
+    return set_error(REDO_ERR_INVALID, "U_target given without F_out or tau_out");
+  if (!U_out && !U_target) return set_error(REDO_ERR_INVALID, "nothing to compute");
+  const int eff_prec = prec == REDO_FP16X3 ? REDO_FP32 : prec;  // tensor path lands later
+  ChainPlan p = plan_chain(t, B, M, eff_prec);
+  const size_t need = chain_workspace_bytes(t, p, eff_prec);
+  if (!workspace || workspace_bytes < need)
+    return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", need);
+  if (((uintptr_t)workspace & 255) != 0) return set_error(REDO_ERR_INVALID, "workspace not 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t el = eff_prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t n2 = (size_t)t->N * t->N;
+  char* seg = (char*)workspace;
+  char* prod = seg + (((size_t)p.B * p.S * n2 * el + 255) & ~(size_t)255);
+  cudaError_t e;
+  {
+    ProfScope ps(2, s);
+    if ((e = launch_chain_segments(t, q, p, eff_prec, seg, dev_status, s)) != cudaSuccess)
+      return cuda_error(e, "chain segments");
+  }
+  {
+    ProfScope ps(3, s);
+    if ((e = launch_chain_combine(t, p, eff_prec, seg, prod, dev_status, s)) != cudaSuccess)
+      return cuda_error(e, "chain combine");
+  }
+  {
+    ProfScope ps(4, s);
+    if ((e = launch_finalize(t, B, eff_prec, prod, U_out, (const double2*)U_target, F_out,
+                             (double2*)tau_out, s)) != cudaSuccess)
+      return cuda_error(e, "finalize");
+  }
+  return REDO_OK;
+}
+
+}  // extern "C"

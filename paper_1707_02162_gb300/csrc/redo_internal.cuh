@@ -1,0 +1,103 @@
+// Internal declarations shared by the libredo translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/redo.h"
+
+namespace redo {
+
+// ----------------------------------------------------------------------------
+// Complex arithmetic on interleaved pairs (double2 / float2)
+// ----------------------------------------------------------------------------
+template <typename R> struct C2;
+template <> struct C2<double> { using T = double2; };
+template <> struct C2<float> { using T = float2; };
+template <typename R> using cplx = typename C2<R>::T;
+
+template <typename R> __host__ __device__ __forceinline__ cplx<R> cmake(R re, R im) {
+  cplx<R> z; z.x = re; z.y = im; return z;
+}
+// acc += a * b
+template <typename R> __device__ __forceinline__ void cfma(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// ----------------------------------------------------------------------------
+// Table handle
+// ----------------------------------------------------------------------------
+constexpr int kMaxK = 64;
+constexpr int kMaxN = 64;
+
+struct Fp16x3Planes;  // tensor-core operand planes, defined in kernels_tc.cu
+
+}  // namespace redo
+
+struct redo_table {
+  int32_t N, K, base, digits;
+  int64_t levels;
+  int64_t entries;            // K * digits * base
+  double dt;
+  double lo[redo::kMaxK], hi[redo::kMaxK], delta[redo::kMaxK];
+  double* d_lo;               // device copies [K]
+  double* d_delta;            // [K]
+  double2* T64;               // [entries][N][N], term 0 digit 0 folded with D
+  double2* D64;               // [N][N]
+  float2* T32;                // [entries][N][N] or nullptr
+  void* tc_planes;            // tensor-core planes or nullptr
+  size_t tc_bytes;
+  cudaStream_t build_stream;
+  int num_sms;
+};
+
+namespace redo {
+
+// ----------------------------------------------------------------------------
+// Error plumbing
+// ----------------------------------------------------------------------------
+redo_status set_error(redo_status s, const char* fmt, ...);
+redo_status cuda_error(cudaError_t e, const char* what);
+#define REDO_CUDA_TRY(call)                                   \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return ::redo::cuda_error(_e, #call); \
+  } while (0)
+
+// ----------------------------------------------------------------------------
+// Launchers (each defined in the translation unit that holds its kernels)
+// ----------------------------------------------------------------------------
+
+// Quantizer (kernels_small.cu).
+cudaError_t launch_quantize(const double* u, int64_t count, int K, const double* lo,
+                            const double* delta, int64_t levels, int32_t* q, int64_t* status,
+                            cudaStream_t s);
+
+// Table: entries e = (k*digits + j)*base + c, plus the drift (entry index -1).
+cudaError_t launch_table_expm(const redo_table* t, const double2* H0, const double2* Hk,
+                              cudaStream_t s);
+cudaError_t launch_table_fold_drift(const redo_table* t, cudaStream_t s);
+cudaError_t launch_to_fp32(const double2* src, float2* dst, int64_t count, cudaStream_t s);
+
+// Segmented chain products for N <= 64 (SIMT, FP64 or FP32).
+struct ChainPlan {
+  int64_t B, M;
+  int64_t F;          // factors per pulse = M*K*digits
+  int64_t seg_len;    // factors per segment
+  int64_t S;          // segments per pulse
+};
+ChainPlan plan_chain(const redo_table* t, int64_t B, int64_t M, int prec);
+size_t chain_workspace_bytes(const redo_table* t, const ChainPlan& p, int prec);
+cudaError_t launch_chain_segments(const redo_table* t, const int32_t* q, const ChainPlan& p,
+                                  int prec, void* seg_out, int64_t* status, cudaStream_t s);
+cudaError_t launch_chain_combine(const redo_table* t, const ChainPlan& p, int prec,
+                                 const void* seg_in, void* prod_out, int64_t* status,
+                                 cudaStream_t s);
+cudaError_t launch_finalize(const redo_table* t, int64_t B, int prec, const void* prod,
+                            void* U_out, const double2* U_target, double* F_out, double2* tau_out,
+                            cudaStream_t s);
+
+}  // namespace redo

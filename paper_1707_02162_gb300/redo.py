@@ -1,0 +1,224 @@
+"""Thin ctypes binding of libredo (argument marshalling only).
+
+Every function here forwards to the C entry point of the same name declared in
+``include/redo.h``; torch is used only to own device memory and to name the
+current CUDA stream.  There is no CPU fallback: if ``libredo.so`` is missing or
+no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libredo.so")
+
+REDO_OK = 0
+REDO_FP64, REDO_FP32, REDO_FP16X3 = 0, 1, 4
+PRECISIONS = {"fp64": REDO_FP64, "fp32": REDO_FP32, "fp16x3": REDO_FP16X3}
+REDO_TABLE_FP32, REDO_TABLE_FP16X3 = 0x1, 0x2
+STATUS_WORDS = 4
+STATUS_NONFINITE, STATUS_SATURATED, STATUS_TIMEOUT, STATUS_BADINDEX = range(4)
+
+EXPORTS = [
+    "redo_build_table", "redo_table_free", "redo_table_info", "redo_table_copy", "redo_quantize",
+    "redo_propagate", "redo_propagate_workspace", "redo_last_error", "redo_profile_enable",
+    "redo_profile_read",
+]
+PROFILE_PHASES = 8
+PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "r6", "r7"]
+
+
+class RedoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libredo status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libredo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with paper_1707_02162_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint32
+    L.redo_build_table.argtypes = [i32, i32, dbl, vp, vp, vp, vp, i32, i32, u32, vp, ctypes.POINTER(vp)]
+    L.redo_table_free.argtypes = [vp]
+    L.redo_table_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4 + [ctypes.POINTER(i64)] * 2
+    L.redo_table_copy.argtypes = [vp, vp, vp, vp]
+    L.redo_quantize.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+    L.redo_propagate.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
+    L.redo_propagate_workspace.argtypes = [vp, i64, i64, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_profile_enable.argtypes = [i32]
+    L.redo_profile_read.argtypes = [vp, vp, i32]
+    L.redo_last_error.restype = ctypes.c_char_p
+    L.redo_last_error.argtypes = []
+    for name in EXPORTS:
+        if name != "redo_last_error":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != REDO_OK:
+        raise RedoError(status, load_library().redo_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def redo_build_table(H0: torch.Tensor, Hk: torch.Tensor, dt: float, lo, hi, base: int, digits: int,
+                     flags: int = REDO_TABLE_FP32, stream=None) -> int:
+    """Build the discrete-operator table; returns the opaque handle (an int)."""
+    L = load_library()
+    N = H0.shape[0]
+    K = Hk.shape[0]
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    out = ctypes.c_void_p()
+    _check(L.redo_build_table(N, K, float(dt), _ptr(H0), _ptr(Hk), lo.ctypes.data_as(ctypes.c_void_p),
+                              hi.ctypes.data_as(ctypes.c_void_p), base, digits, flags, _stream(stream),
+                              ctypes.byref(out)))
+    return out.value
+
+
+def redo_table_free(handle: int):
+    _check(load_library().redo_table_free(ctypes.c_void_p(handle)))
+
+
+def redo_table_info(handle: int) -> dict:
+    i = [ctypes.c_int32() for _ in range(4)]
+    j = [ctypes.c_int64() for _ in range(2)]
+    _check(load_library().redo_table_info(ctypes.c_void_p(handle), *[ctypes.byref(x) for x in i],
+                                          *[ctypes.byref(x) for x in j]))
+    return dict(N=i[0].value, K=i[1].value, base=i[2].value, digits=i[3].value, levels=j[0].value,
+                entries=j[1].value)
+
+
+def redo_table_copy(handle: int, table_out: torch.Tensor | None, drift_out: torch.Tensor | None, stream=None):
+    _check(load_library().redo_table_copy(ctypes.c_void_p(handle), _ptr(table_out), _ptr(drift_out),
+                                          _stream(stream)))
+
+
+def redo_quantize(handle: int, u: torch.Tensor, q: torch.Tensor, status: torch.Tensor | None = None, stream=None):
+    B, M = u.shape[0], u.shape[1]
+    _check(load_library().redo_quantize(ctypes.c_void_p(handle), _ptr(u), B, M, _ptr(q), _ptr(status),
+                                        _stream(stream)))
+
+
+def redo_propagate_workspace(handle: int, B: int, M: int, prec) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().redo_propagate_workspace(ctypes.c_void_p(handle), B, M, _prec(prec), ctypes.byref(n)))
+    return n.value
+
+
+def redo_propagate(handle: int, q: torch.Tensor, prec, U_out: torch.Tensor | None, U_target: torch.Tensor | None,
+                   F_out: torch.Tensor | None, tau_out: torch.Tensor | None, workspace: torch.Tensor,
+                   status: torch.Tensor | None = None, reunit_every: int = 0, stream=None):
+    B, M = q.shape[0], q.shape[1]
+    _check(load_library().redo_propagate(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), reunit_every,
+                                         _ptr(U_out), _ptr(U_target), _ptr(F_out), _ptr(tau_out),
+                                         _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                         _ptr(status), _stream(stream)))
+
+
+def redo_profile_enable(enable: bool):
+    _check(load_library().redo_profile_enable(1 if enable else 0))
+
+
+def redo_profile_read() -> dict:
+    """Per-phase (milliseconds, launches) recorded since the last read."""
+    ms = (ctypes.c_double * PROFILE_PHASES)()
+    n = (ctypes.c_int64 * PROFILE_PHASES)()
+    _check(load_library().redo_profile_read(ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(n, ctypes.c_void_p),
+                                            PROFILE_PHASES))
+    return {PHASE_NAMES[i]: (ms[i], n[i]) for i in range(PROFILE_PHASES) if n[i]}
+
+
+class Table:
+    """Owning wrapper of a redo_table built from torch tensors on the current device."""
+
+    def __init__(self, H0, Hk, dt, lo, hi, base=64, digits=2, fp32=True, fp16x3=False, device="cuda"):
+        H0 = torch.as_tensor(H0, dtype=torch.complex128, device=device).contiguous()
+        Hk = torch.as_tensor(Hk, dtype=torch.complex128, device=device).contiguous()
+        flags = (REDO_TABLE_FP32 if fp32 else 0) | (REDO_TABLE_FP16X3 if fp16x3 else 0)
+        self.handle = redo_build_table(H0, Hk, dt, lo, hi, base, digits, flags)
+        self.info = redo_table_info(self.handle)
+        self.N, self.K = self.info["N"], self.info["K"]
+        self.device = H0.device
+        self._ws = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            redo_table_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def operators(self):
+        """(T, D): the FP64 table [K][digits][base][N][N] (term 0 digit 0 folded with D) and D."""
+        i = self.info
+        T = torch.empty((i["K"], i["digits"], i["base"], i["N"], i["N"]), dtype=torch.complex128, device=self.device)
+        D = torch.empty((i["N"], i["N"]), dtype=torch.complex128, device=self.device)
+        redo_table_copy(self.handle, T, D)
+        return T, D
+
+    def quantize(self, u, status=None):
+        u = torch.as_tensor(u, dtype=torch.float64, device=self.device).contiguous()
+        q = torch.empty(u.shape, dtype=torch.int32, device=self.device)
+        redo_quantize(self.handle, u, q, status)
+        return q
+
+    def workspace(self, B, M, prec):
+        nbytes = redo_propagate_workspace(self.handle, B, M, prec)
+        key = (B, M, _prec(prec))
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+            self._ws[key] = ws
+        return ws
+
+    def propagate(self, q, prec="fp64", target=None, want_U=True, status=None):
+        B = q.shape[0]
+        U = torch.empty((B, self.N, self.N), dtype=torch.complex128, device=self.device) if want_U else None
+        F = tau = None
+        if target is not None:
+            target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
+            F = torch.empty(B, dtype=torch.float64, device=self.device)
+            tau = torch.empty(B, dtype=torch.complex128, device=self.device)
+        ws = self.workspace(B, q.shape[1], prec)
+        redo_propagate(self.handle, q, prec, U, target, F, tau, ws, status)
+        return U, F, tau
+
+
+def new_status(device="cuda") -> torch.Tensor:
+    return torch.zeros(STATUS_WORDS, dtype=torch.int64, device=device)
