@@ -170,6 +170,37 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
                            const void* U_target, double* F_out, void* tau_out, void* workspace,
                            size_t workspace_bytes, int64_t* dev_status, void* stream);
 
+/*
+ * redo_propagate_noalloc -- redo_propagate for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this is a deployment variant.
+ *
+ * Some callers may not call cudaMalloc at all: code running inside a custom
+ * allocator's callback, plug-ins whose host application owns the whole device
+ * memory pool, or real-time control loops that forbid allocation after
+ * start-up.  This entry point needs no workspace: its
+ * scratch is a fixed array of REDO_NOALLOC_SCRATCH_BYTES bytes compiled into
+ * the library as a device global, which every GPU that loads libredo holds
+ * until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The caller still passes inputs and outputs, with the
+ * same meaning, layout and status words as redo_propagate (REDO_FP64 and
+ * REDO_FP32 only).
+ *
+ *  - Requests whose segment and pulse products cannot fit the array even with
+ *    one segment per pulse (about B*N*N*16 bytes for FP64, half for FP32)
+ *    return REDO_ERR_INVALID with a message naming the limit.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the one array and it keeps the previous
+ *    call's contents (nothing in it needs to start at zero).  Calls whose
+ *    kernels overlap on the GPU -- on different streams or from different host
+ *    threads -- race on it; serialise them.
+ */
+#define REDO_NOALLOC_SCRATCH_BYTES (32u << 20)
+redo_status redo_propagate_noalloc(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                                   redo_precision prec, void* U_out, const void* U_target,
+                                   double* F_out, void* tau_out, int64_t* dev_status, void* stream);
+
 /* Scratch bytes redo_propagate needs for (B, M, prec) on this table. */
 redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
                                      redo_precision prec, size_t* bytes);

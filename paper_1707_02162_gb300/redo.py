@@ -26,7 +26,7 @@ STATUS_NONFINITE, STATUS_SATURATED, STATUS_TIMEOUT, STATUS_BADINDEX = range(4)
 EXPORTS = [
     "redo_build_table", "redo_table_free", "redo_table_info", "redo_table_copy", "redo_quantize",
     "redo_propagate", "redo_propagate_workspace", "redo_last_error", "redo_profile_enable",
-    "redo_profile_read",
+    "redo_profile_read", "redo_propagate_noalloc",
 ]
 PROFILE_PHASES = 8
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "r6", "r7"]
@@ -57,6 +57,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_quantize.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.redo_propagate.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_propagate_workspace.argtypes = [vp, i64, i64, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_propagate_noalloc.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
     L.redo_profile_enable.argtypes = [i32]
     L.redo_profile_read.argtypes = [vp, vp, i32]
     L.redo_last_error.restype = ctypes.c_char_p
@@ -145,6 +146,17 @@ def redo_propagate(handle: int, q: torch.Tensor, prec, U_out: torch.Tensor | Non
                                          _ptr(U_out), _ptr(U_target), _ptr(F_out), _ptr(tau_out),
                                          _ptr(workspace), workspace.numel() * workspace.element_size(),
                                          _ptr(status), _stream(stream)))
+
+
+def redo_propagate_noalloc(handle: int, q: torch.Tensor, prec, U_out: torch.Tensor | None,
+                           U_target: torch.Tensor | None, F_out: torch.Tensor | None, tau_out: torch.Tensor | None,
+                           status: torch.Tensor | None = None, stream=None):
+    """redo_propagate without a workspace: scratch is the library's fixed device array
+    (for callers that cannot allocate device memory)."""
+    B, M = q.shape[0], q.shape[1]
+    _check(load_library().redo_propagate_noalloc(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), _ptr(U_out),
+                                                 _ptr(U_target), _ptr(F_out), _ptr(tau_out), _ptr(status),
+                                                 _stream(stream)))
 
 
 def redo_profile_enable(enable: bool):
