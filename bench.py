@@ -31,7 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "REDO prop steps/s & GRAPE iters/s vs FP64 plain REDO, same GB300, |ΔF|≤1e-6"
 UNIT = "pulse-steps/s"
 B_FULL, M_FULL, N_QUBITS = 256, 2000, 6
-MAIN_PREC = os.environ.get("REDO_BENCH_PREC", "fp32")
+MAIN_PREC = os.environ.get("REDO_BENCH_PREC", "fp16x3")
+REUNIT = 64          # re-unitarisation period (steps) of the reduced-precision forms
 
 
 def _workload_config(extra=None):
@@ -163,7 +164,7 @@ def run_gpu(args):
         peaks = _json.load(open(pk))
 
     # Each rank runs an independent replica batch (weak scaling, no collective on the data path).
-    w = inputs.config(1, seed=1)
+    w = inputs.config(1, seed=1, B=args.B, M=args.M)
     if rank:
         w.u = np.random.default_rng(1 + 7919 * rank).uniform(w.lo[0], w.hi[0], size=w.u.shape)
     dev = torch.device("cuda", local)
@@ -178,13 +179,14 @@ def run_gpu(args):
     F = torch.empty(B, dtype=torch.float64, device=dev)
     tau = torch.empty(B, dtype=torch.complex128, device=dev)
     status = redo.new_status(dev)
-    ws = table.workspace(B, M, MAIN_PREC)
+    reunit_main = 0 if MAIN_PREC == "fp64" else REUNIT
+    ws = table.workspace(B, M, MAIN_PREC, reunit_main)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)      # > 129 MB L2
     stream = torch.cuda.current_stream()
 
-    def step(prec=MAIN_PREC, qq=q, UU=U, FF=F, tt=tau, uu=u_dev, wsp=ws):
+    def step(prec=MAIN_PREC, qq=q, UU=U, FF=F, tt=tau, uu=u_dev, wsp=ws, reunit=reunit_main):
         redo.redo_quantize(table.handle, uu, qq, status)
-        redo.redo_propagate(table.handle, qq, prec, UU, target, FF, tt, wsp, status)
+        redo.redo_propagate(table.handle, qq, prec, UU, target, FF, tt, wsp, status, reunit_every=reunit)
 
     for _ in range(args.warmup):
         step()
@@ -262,13 +264,13 @@ def run_gpu(args):
         ts = torch.empty(Bs, dtype=torch.complex128, device=dev)
         ws64 = table.workspace(Bs, M, "fp64")
         us = u_dev[:Bs].contiguous()
-        step("fp64", qs, Us, Fs, ts, us, ws64)
+        step("fp64", qs, Us, Fs, ts, us, ws64, 0)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 2
         a.record(stream)
         for _ in range(reps):
-            step("fp64", qs, Us, Fs, ts, us, ws64)
+            step("fp64", qs, Us, Fs, ts, us, ws64, 0)
         b.record(stream)
         torch.cuda.synchronize()
         ms64 = a.elapsed_time(b) / reps
@@ -306,7 +308,7 @@ def run_gpu(args):
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "fp16x3": "f16x3 (f32 accumulate)"}[MAIN_PREC],
            "data": "synthetic (seeded NMR-like Hamiltonian, uniform random controls, Haar target)",
-           "config": _workload_config({"precision": MAIN_PREC,
+           "config": _workload_config({"precision": MAIN_PREC, "B": B, "M": M, "reunit_every": reunit_main,
                                        "l2": "flushed between timed steps (256 MB write outside the events)"}),
            "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
@@ -351,6 +353,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--B", type=int, default=B_FULL, help="pulses (smaller only for profiling captures)")
+    ap.add_argument("--M", type=int, default=M_FULL, help="steps per pulse (smaller only for profiling captures)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")

@@ -153,7 +153,13 @@ redo_status redo_quantize(const redo_table* t, const double* u, int64_t B, int64
  *  q           device int32 [B][M][K] level indices (from redo_quantize).
  *  prec        REDO_FP64, REDO_FP32 or REDO_FP16X3 (the last needs the table
  *              built with REDO_TABLE_FP16X3).
- *  reunit_every  reserved, must be 0.
+ *  reunit_every  R >= 0.  R = 0: no re-unitarisation.  R > 0: segments are cut
+ *              at every R-th time step and each segment product -- the
+ *              propagator of R consecutive steps -- is replaced by its unitary
+ *              polar factor (one Newton-Schulz step P <- P(3I - P^dag P)/2 in
+ *              the chain precision), and each pulse product gets one more
+ *              Newton-Schulz step in FP64 before the fidelity.  This removes
+ *              the norm drift of reduced-precision chains; R > M acts as R = M.
  *  U_out       device complex128 [B][N][N]; receives U_b.  May be NULL if F is wanted only.
  *  U_target    device complex128 [N][N] or NULL.
  *  F_out       device double [B]: |Tr(U_target^dag U_b)|^2 / N^2 (FP64 reduction);
@@ -201,15 +207,15 @@ redo_status redo_propagate_noalloc(const redo_table* t, const int32_t* q, int64_
                                    redo_precision prec, void* U_out, const void* U_target,
                                    double* F_out, void* tau_out, int64_t* dev_status, void* stream);
 
-/* Scratch bytes redo_propagate needs for (B, M, prec) on this table. */
+/* Scratch bytes redo_propagate needs for (B, M, prec, reunit_every) on this table. */
 redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
-                                     redo_precision prec, size_t* bytes);
+                                     redo_precision prec, int32_t reunit_every, size_t* bytes);
 
 /*
  * Kernel timing for measurement.  While enabled, the library brackets each of
  * its kernel launches with CUDA events on the launching stream.  Phases:
  *   0 quantize, 1 table, 2 chain segments, 3 chain combine, 4 finalize,
- *   5 tensor-core chain, 6 reserved, 7 reserved.
+ *   5 tensor-core chain, 6 re-unitarisation, 7 gradient.
  * redo_profile_read synchronises on the recorded events, adds each phase's
  * elapsed milliseconds and launch count into ms_out[p] / launches_out[p]
  * (arrays of n <= REDO_PROFILE_PHASES entries, either may be NULL) and clears

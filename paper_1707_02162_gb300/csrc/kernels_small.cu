@@ -583,6 +583,103 @@ cudaError_t launch_chain_combine(const redo_table* t, const ChainPlan& p, int pr
 }
 
 // ============================================================================
+// Re-unitarisation: Newton-Schulz polar iteration  P <- P (3I - P^dag P) / 2,
+// one CTA per matrix.  Converges quadratically to the unitary polar factor
+// P (P^dag P)^(-1/2) when ||P^dag P - I|| < 1; the product chains hand it
+// matrices within ~1e-3 of unitary, so one step leaves ~1e-6 of that.
+// ============================================================================
+template <typename Rin, typename Rc, int N>
+__global__ void __launch_bounds__(SmemMM<Rc, N, (N >= 64 ? 4 : (N >= 32 ? 2 : 1)),
+                                         (N >= 64 ? 4 : (N >= 32 ? 2 : 1))>::THREADS)
+polar_ns_kernel(const cplx<Rin>* __restrict__ in, cplx<Rc>* __restrict__ out, int iters) {
+  constexpr int TM = (N >= 64 ? 4 : (N >= 32 ? 2 : 1));
+  using MM = SmemMM<Rc, N, TM, TM>;
+  constexpr int N2 = N * N;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cplx<Rc>* P = reinterpret_cast<cplx<Rc>*>(smem_raw);
+  cplx<Rc>* Q = P + N2;
+  const int lt = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  for (int i = lt; i < N2; i += MM::THREADS) {
+    const cplx<Rin> v = in[b * N2 + i];
+    P[i] = cmake<Rc>((Rc)v.x, (Rc)v.y);
+  }
+  __syncthreads();
+  cplx<Rc> Y[TM][TM];
+  const int ty = lt / MM::TX, tx = lt % MM::TX;
+  for (int it = 0; it < iters; ++it) {
+    for (int i = lt; i < N2; i += MM::THREADS) {
+      const int r = i / N, c = i % N;
+      const cplx<Rc> v = P[c * N + r];
+      Q[i] = cmake<Rc>(v.x, -v.y);                       // Q = P^dag
+    }
+    __syncthreads();
+    MM::run(Q, P, lt, Y);                                // G = P^dag P
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int c = 0; c < TM; ++c) {
+        const int r = ty + MM::TY * a, col = tx + MM::TX * c;
+        Q[r * N + col] = cmake<Rc>((r == col ? Rc(1.5) : Rc(0)) - Rc(0.5) * Y[a][c].x,
+                                   -Rc(0.5) * Y[a][c].y);
+      }
+    __syncthreads();
+    MM::run(P, Q, lt, Y);                                // P (3I - G) / 2
+    __syncthreads();
+    MM::store(P, lt, Y);
+    __syncthreads();
+  }
+  for (int i = lt; i < N2; i += MM::THREADS) out[b * N2 + i] = P[i];
+}
+
+template <typename Rin, typename Rc, int N>
+static cudaError_t polar_n(const void* in, void* out, int64_t count, int iters, cudaStream_t s) {
+  constexpr int TM = (N >= 64 ? 4 : (N >= 32 ? 2 : 1));
+  using MM = SmemMM<Rc, N, TM, TM>;
+  const size_t smem = 2 * sizeof(cplx<Rc>) * N * N;
+  auto kern = polar_ns_kernel<Rin, Rc, N>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (count == 0) return cudaSuccess;
+  kern<<<(unsigned)count, MM::THREADS, smem, s>>>((const cplx<Rin>*)in, (cplx<Rc>*)out, iters);
+  return cudaGetLastError();
+}
+
+template <typename Rin, typename Rc>
+static cudaError_t polar_t(int N, const void* in, void* out, int64_t count, int iters,
+                           cudaStream_t s) {
+  switch (N) {
+    case 2: return polar_n<Rin, Rc, 2>(in, out, count, iters, s);
+    case 4: return polar_n<Rin, Rc, 4>(in, out, count, iters, s);
+    case 8: return polar_n<Rin, Rc, 8>(in, out, count, iters, s);
+    case 16: return polar_n<Rin, Rc, 16>(in, out, count, iters, s);
+    case 32: return polar_n<Rin, Rc, 32>(in, out, count, iters, s);
+    case 64: return polar_n<Rin, Rc, 64>(in, out, count, iters, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_polar(const redo_table* t, int prec_in, int prec_out, const void* in, void* out,
+                         int64_t count, int iters, cudaStream_t s) {
+  const bool din = prec_in == REDO_FP64, dout = prec_out == REDO_FP64;
+  if (din && dout) return polar_t<double, double>(t->N, in, out, count, iters, s);
+  if (!din && dout) return polar_t<float, double>(t->N, in, out, count, iters, s);
+  if (!din && !dout) return polar_t<float, float>(t->N, in, out, count, iters, s);
+  return cudaErrorInvalidValue;
+}
+
+ChainPlan plan_chain_aligned(const redo_table* t, int64_t B, int64_t M, int64_t steps_per_segment) {
+  ChainPlan p;
+  p.B = B;
+  p.M = M;
+  p.F = M * (int64_t)t->K * t->digits;
+  p.seg_len = steps_per_segment * (int64_t)t->K * t->digits;
+  p.S = p.F > 0 ? (p.F + p.seg_len - 1) / p.seg_len : 1;
+  return p;
+}
+
+// ============================================================================
 // Epilogue: U_out (complex128), tau = Tr(U_T^dag U) and F = |tau|^2 / N^2,
 // reduced in FP64 in a fixed order (deterministic).
 // ============================================================================

@@ -1,0 +1,502 @@
+// Tensor-core (tcgen05) product chains for N = 64 in split-FP16 arithmetic.
+//
+// One chain multiplies a segment of gathered table operators,
+//     X <- A_f X,   f = f0 .. f0+len-1,
+// kept on chip as Y = X^T so that the running state is the M-side operand:
+//     Y <- Y A_f^T.
+// With the real embedding of a complex product,
+//     [Zr; Zi] = [[Yr, -Yi], [Yi, Yr]] [Cr; Ci],   C = A_f^T,
+// one step is a real 128 x 64 x 128 product: the state operand (128 x 128)
+// lives in shared memory, the table operand B^T (64 x 128, row n =
+// [Re A_f[n,:], Im A_f[n,:]]) is streamed from the L2-resident table by bulk
+// copies, and the accumulator D = [Zr; Zi] lives in tensor memory.  A table
+// entry stores its hi and lo planes as one 128-row tile (rows 0-63 hi, 64-127
+// lo), so  A_hi [B_hi; B_lo]^T  is a single N = 128 product.
+//
+// Split-FP16 arithmetic: every operand value v (|v| <= 1 for unitary
+// factors) is held as hi = fp16(v) and lo = fp16((v - hi) * 2^11); a step
+// accumulates  D1 = sum hi*hi'  and  D2 = sum (hi*lo' + lo*hi')  in FP32 and
+// the epilogue forms Z = D1 + 2^-11 D2 (the lo*lo' term, ~2^-22 relative, is
+// dropped).  Both operands of one MMA have the same type (fp16).  The
+// accumulation shrinks the norm by ~3e-8 per product; redo_propagate's
+// periodic re-unitarisation removes that drift.
+//
+// Warp roles per CTA (CH chains, EW epilogue warps per chain): warps
+// 0..CH*EW-1 epilogue -- warp w serves TMEM lanes 32(w mod 4).. and, when
+// EW = 8, one 32-column half of the accumulator -- then one bulk-copy
+// producer warp and one MMA-issuing warp.  Two chains per CTA let one
+// chain's MMAs run while the other chain's epilogue rewrites its state.
+// Every wait is bounded; a timeout sets REDO_STATUS_TIMEOUT and the CTA
+// drains, frees its tensor memory and exits.
+#include <cuda_fp16.h>
+
+#include "redo_internal.cuh"
+#include "device_sync.cuh"
+
+namespace redo {
+namespace tc {
+
+constexpr int kN = 64;
+constexpr uint32_t kTablePlane = 64 * 128 * 2;       // 16 KB: one 64 x 128 fp16 operand plane
+constexpr uint32_t kEntryBytes = 2 * kTablePlane;    // hi + lo planes of one table operator
+constexpr uint32_t kEntryAtom = 128 * 128;           // one 64-wide K column of the 128-row entry tile
+constexpr uint32_t kStateAtom = 128 * 128;           // 16 KB: one 64-wide K column of the 128-row state
+constexpr uint32_t kStatePlane = 2 * kStateAtom;     // 32 KB
+constexpr uint32_t kStateBytes = 2 * kStatePlane;    // hi + lo
+constexpr uint32_t kTcWaitLimit = 1u << 24;
+constexpr float kLoScale = 2048.0f;                  // 2^11
+constexpr float kLoInv = 1.0f / 2048.0f;
+
+// Byte offset of 16-bit element (row, k), k < 128, in a K-major tile with
+// 128-byte swizzling: 64-element K columns of `rows` x 128 B, 8-row groups
+// 1024 B apart, 16-byte granule g of row r stored at granule g ^ (r mod 8).
+__host__ __device__ __forceinline__ uint32_t sw128(uint32_t row, uint32_t k, uint32_t rows) {
+  const uint32_t atom = k >> 6, kk = k & 63, g = kk >> 3, w = kk & 7;
+  return atom * rows * 128u + row * 128u + (((g ^ (row & 7u)) << 4) | (w << 1));
+}
+
+// --------------------------------------------------------------------------
+// tcgen05 / TMEM primitives (inline PTX)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;          // stride byte offset: 8-row groups
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptors: D f32, A/B f16, both K-major, M = 128, N = 64 or 128.
+constexpr uint32_t idesc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+constexpr uint32_t kIdesc64 = idesc_f16(64);
+constexpr uint32_t kIdesc128 = idesc_f16(128);
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+#define REDO_R8(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), "=r"(r[i + 4]), \
+                   "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : REDO_R8(0), REDO_R8(8), REDO_R8(16), REDO_R8(24)
+      : "r"(taddr));
+}
+#undef REDO_R8
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// --------------------------------------------------------------------------
+// Table operand planes: entry e -> one 128 x 128 K-major swizzled tile whose
+// rows 0-63 are hi(B^T) and rows 64-127 lo(B^T), B^T row n = [Re T_e[n,:], Im T_e[n,:]].
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack_half2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+__global__ void __launch_bounds__(256) build_planes_kernel(const double2* __restrict__ T,
+                                                           uint8_t* __restrict__ planes) {
+  const int64_t e = blockIdx.x;
+  const double2* Te = T + e * (kN * kN);
+  uint8_t* tile = planes + e * kEntryBytes;
+  // 64 rows x 16 granules of 8 elements
+  for (int gi = threadIdx.x; gi < 64 * 16; gi += blockDim.x) {
+    const int n = gi >> 4, g = gi & 15;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      __half hh[2], ll[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int k = 8 * g + 2 * p + q;           // 0..127
+        const double2 z = Te[n * kN + (k & 63)];
+        const double v = k < 64 ? z.x : z.y;
+        hh[q] = __double2half(v);
+        ll[q] = __double2half((v - (double)__half2float(hh[q])) * 2048.0);
+      }
+      h[p] = pack_half2(hh[0], hh[1]);
+      l[p] = pack_half2(ll[0], ll[1]);
+    }
+    *reinterpret_cast<uint4*>(tile + sw128(n, 8 * g, 128)) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(tile + sw128(64 + n, 8 * g, 128)) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// --------------------------------------------------------------------------
+// The chain kernel
+// --------------------------------------------------------------------------
+struct TcArgs {
+  const uint8_t* planes;
+  const int32_t* q;
+  int64_t M;
+  int K, d, base;
+  int64_t levels;
+  int64_t units, segs, seg_len, F;
+  float2* out;
+  int64_t* status;
+};
+
+template <int CH, int EW, int STAGES>
+struct TcLayout {
+  static constexpr uint32_t kState = 0;
+  static constexpr uint32_t kRing = CH * kStateBytes;
+  static constexpr uint32_t kBars = kRing + STAGES * kEntryBytes;
+  // full[STAGES], empty[STAGES], mma_done[CH], state_ready[CH]
+  static constexpr uint32_t kMisc = kBars + (2 * STAGES + 2 * CH) * 8;
+  static constexpr uint32_t kBytes = kMisc + 16;
+  static constexpr uint32_t kAlloc = kBytes + 1024;   // slack for 1024-byte alignment
+  static constexpr int kEpiThreads = 32 * EW;         // per chain
+  static constexpr int kThreads = 32 * (EW * CH + 2);
+  static constexpr int kCols = 128 / (EW / 4);        // accumulator columns per epilogue thread (x2 halves)
+  static constexpr uint32_t kTmemCols = CH == 1 ? 128 : (CH == 2 ? 256 : 512);
+  static_assert(EW == 4 || EW == 8, "4 or 8 epilogue warps per chain");
+  static_assert(kAlloc <= 232448, "shared memory budget");
+};
+
+__device__ __forceinline__ int64_t tc_entry(const TcArgs& a, int64_t unit, int64_t f) {
+  const int64_t kd = (int64_t)a.K * a.d;
+  const int64_t n = f / kd;
+  const int r = (int)(f - n * kd);
+  const int k = r / a.d, j = r - k * a.d;
+  int32_t qv = a.q[(unit * a.M + n) * a.K + k];
+  if (qv < 0 || qv >= a.levels) {
+    if (a.status) atomicAdd((unsigned long long*)&a.status[REDO_STATUS_BADINDEX], 1ull);
+    qv = 0;
+  }
+  for (int i = 0; i < j; ++i) qv /= a.base;
+  return (int64_t)(k * a.d + j) * a.base + qv % a.base;
+}
+
+// Split 8 consecutive accumulator values into hi / lo fp16 granules.
+__device__ __forceinline__ void split8(const float* z, uint4& h, uint4& l) {
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const float x0 = z[2 * p], x1 = z[2 * p + 1];
+    const __half2 hh = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(hh);
+    const __half2 ll = __floats2half2_rn((x0 - hf.x) * kLoScale, (x1 - hf.y) * kLoScale);
+    hw[p] = *reinterpret_cast<const uint32_t*>(&hh);
+    lw[p] = *reinterpret_cast<const uint32_t*>(&ll);
+  }
+  h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
+template <int CH, int EW, int STAGES>
+__global__ void __launch_bounds__(TcLayout<CH, EW, STAGES>::kThreads, 1)
+chain_tc_kernel(TcArgs a) {
+  using L = TcLayout<CH, EW, STAGES>;
+  constexpr int HALVES = EW / 4;                  // column groups per TMEM lane quarter
+  constexpr int COLS = 64 / HALVES;               // accumulator columns per epilogue thread
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBars);
+  uint64_t* empty = full + STAGES;
+  uint64_t* mma_done = empty + STAGES;
+  uint64_t* state_ready = mma_done + CH;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kMisc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::kMisc + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = a.units * a.segs;
+  int64_t len[CH], f0[CH], unit[CH];
+  int64_t maxlen = 0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int64_t g = (int64_t)blockIdx.x * CH + c;
+    len[c] = 0;
+    f0[c] = 0;
+    unit[c] = 0;
+    if (g < G) {
+      unit[c] = g / a.segs;
+      f0[c] = (g % a.segs) * a.seg_len;
+      int64_t f1 = f0[c] + a.seg_len;
+      if (f1 > a.F) f1 = a.F;
+      len[c] = f1 > f0[c] ? f1 - f0[c] : 0;
+    }
+    if (len[c] > maxlen) maxlen = len[c];
+  }
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int c = 0; c < CH; ++c) {
+      mbar_init(&mma_done[c], 1);
+      mbar_init(&state_ready[c], L::kEpiThreads);
+    }
+    *abort_flag = 0;
+    fence_mbarrier_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, L::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp < EW * CH) {
+    // ------------------------------------------------------------ epilogue
+    const int c = warp / EW;
+    const int ew = warp % EW;
+    const int quarter = ew & 3, half = ew >> 2;
+    const int row = 32 * quarter + lane;                 // TMEM lane = state row, 0..127
+    const int col0 = COLS * half;                        // first accumulator column of this thread
+    uint8_t* st_hi = smem + L::kState + c * kStateBytes;
+    uint8_t* st_lo = st_hi + kStatePlane;
+    const int64_t g = (int64_t)blockIdx.x * CH + c;
+    float* out = g < G ? reinterpret_cast<float*>(a.out + g * (kN * kN)) : nullptr;
+    const uint32_t d1 = tmem_base + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(c * 128);
+    const uint32_t d2 = d1 + 64;
+    const int mrow = row < 64 ? row + 64 : row - 64;     // mirror row of the embedding
+    const uint32_t negmask = row < 64 ? 0u : 0x80008000u;
+    const int m = row & 63, comp = row >> 6;
+    if (len[c] == 0) {
+      if (out)
+        for (int n = col0; n < col0 + COLS; ++n)
+          out[(n * kN + m) * 2 + comp] = (comp == 0 && n == m) ? 1.f : 0.f;
+    } else {
+      // initial state Y = I: embedded 128 x 128 identity, lo = 0; this thread
+      // writes K granules [16*half/HALVES, ...) of its row
+      for (int gi = 16 * half / HALVES; gi < 16 * (half + 1) / HALVES; ++gi) {
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        const int k0 = 8 * gi;
+        if (row >= k0 && row < k0 + 8) {
+          const int p = (row - k0) >> 1, hp = (row - k0) & 1;
+          w[p] = (uint32_t)0x3C00u << (16 * hp);         // fp16 1.0
+        }
+        const uint32_t off = sw128(row, k0, 128);
+        *reinterpret_cast<uint4*>(st_hi + off) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(st_lo + off) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&state_ready[c]);
+      for (int64_t t = 0; t < len[c]; ++t) {
+        bool ok = !*abort_flag && mbar_wait_bounded_n(&mma_done[c], (uint32_t)(t & 1), kTcWaitLimit);
+        ok = __all_sync(0xffffffffu, ok);                // keep the warp converged for tcgen05.ld
+        if (!ok) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const bool last = (t == len[c] - 1);
+#pragma unroll
+        for (int j = 0; j < COLS / 32; ++j) {
+          const int cb = col0 + 32 * j;                  // 32 accumulator columns
+          uint32_t ra[32], rb[32];
+          tmem_ld32(d1 + cb, ra);
+          tmem_ld32(d2 + cb, rb);
+          tmem_wait_ld();
+          float z[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            z[i] = fmaf(__uint_as_float(rb[i]), kLoInv, __uint_as_float(ra[i]));
+          if (!last) {
+#pragma unroll
+            for (int gq = 0; gq < 4; ++gq) {
+              uint4 h, l;
+              split8(z + 8 * gq, h, l);
+              const uint32_t kcol = (uint32_t)(cb + 8 * gq);
+              const uint32_t od = sw128((uint32_t)row, kcol, 128);
+              const uint32_t om = sw128((uint32_t)mrow, 64u + kcol, 128);
+              *reinterpret_cast<uint4*>(st_hi + od) = h;
+              *reinterpret_cast<uint4*>(st_lo + od) = l;
+              *reinterpret_cast<uint4*>(st_hi + om) =
+                  make_uint4(h.x ^ negmask, h.y ^ negmask, h.z ^ negmask, h.w ^ negmask);
+              *reinterpret_cast<uint4*>(st_lo + om) =
+                  make_uint4(l.x ^ negmask, l.y ^ negmask, l.z ^ negmask, l.w ^ negmask);
+            }
+          } else if (out) {
+            // row < 64 holds Re Y[row, :] = Re X[:, row]; row >= 64 holds Im X[:, row-64]
+#pragma unroll
+            for (int i = 0; i < 32; ++i) out[((cb + i) * kN + m) * 2 + comp] = z[i];
+          }
+        }
+        if (!last) {
+          fence_proxy_async_smem();
+          tc_fence_before();
+          mbar_arrive(&state_ready[c]);
+        }
+      }
+    }
+  } else if (warp == EW * CH) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t idx = 0;
+      for (int64_t t = 0; t < maxlen && !*abort_flag; ++t) {
+        for (int c = 0; c < CH; ++c) {
+          if (t >= len[c]) continue;
+          const uint32_t s = idx % STAGES, u = idx / STAGES;
+          if (u > 0 && !mbar_wait_bounded_n(&empty[s], (u - 1) & 1, kTcWaitLimit)) {
+            *abort_flag = 1;
+            break;
+          }
+          const int64_t e = tc_entry(a, unit[c], f0[c] + t);
+          uint8_t* dst = smem + L::kRing + s * kEntryBytes;
+          const uint8_t* src = a.planes + e * kEntryBytes;
+          mbar_arrive_expect_tx(&full[s], kEntryBytes);
+          bulk_load(dst, src, kEntryBytes / 2, &full[s]);
+          bulk_load(dst + kEntryBytes / 2, src + kEntryBytes / 2, kEntryBytes / 2, &full[s]);
+          ++idx;
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t idx = 0;
+      for (int64_t t = 0; t < maxlen && !*abort_flag; ++t) {
+        for (int c = 0; c < CH; ++c) {
+          if (t >= len[c]) continue;
+          const uint32_t s = idx % STAGES, u = idx / STAGES;
+          if (!mbar_wait_bounded_n(&full[s], u & 1, kTcWaitLimit) ||
+              !mbar_wait_bounded_n(&state_ready[c], (uint32_t)(t & 1), kTcWaitLimit)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_hi = smem_u32(smem + L::kState + c * kStateBytes);
+          const uint32_t a_lo = a_hi + kStatePlane;
+          const uint32_t b0 = smem_u32(smem + L::kRing + s * kEntryBytes);
+          const uint32_t dd1 = tmem_base + (uint32_t)(c * 128);
+          const uint32_t dd2 = dd1 + 64;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t ko = (uint32_t)(kk >> 2) * kStateAtom + (uint32_t)(kk & 3) * 32u;
+            const uint32_t bo = (uint32_t)(kk >> 2) * kEntryAtom + (uint32_t)(kk & 3) * 32u;
+            const uint64_t ah = smem_desc_sw128(a_hi + ko), al = smem_desc_sw128(a_lo + ko);
+            const uint64_t bb = smem_desc_sw128(b0 + bo);    // rows 0-63 hi, 64-127 lo
+            // [D1 | D2] (+)= A_hi [B_hi; B_lo]^T ;  D2 += A_lo B_hi^T
+            mma_f16(dd1, ah, bb, kIdesc128, kk > 0 ? 1u : 0u);
+            mma_f16(dd2, al, bb, kIdesc64, 1u);
+          }
+          mma_commit(&empty[s]);
+          mma_commit(&mma_done[c]);
+          ++idx;
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (*abort_flag && threadIdx.x == 0 && a.status)
+    atomicAdd((unsigned long long*)&a.status[REDO_STATUS_TIMEOUT], 1ull);
+  if (warp == 0) tmem_dealloc(tmem_base, L::kTmemCols);
+}
+
+}  // namespace tc
+
+// ============================================================================
+// Host launchers
+// ============================================================================
+size_t tc_planes_bytes(const redo_table* t) { return (size_t)t->entries * tc::kEntryBytes; }
+
+cudaError_t launch_build_tc_planes(const redo_table* t, cudaStream_t s) {
+  if (t->N != tc::kN) return cudaErrorInvalidValue;
+  tc::build_planes_kernel<<<(unsigned)t->entries, 256, 0, s>>>(t->T64, (uint8_t*)t->tc_planes);
+  return cudaGetLastError();
+}
+
+constexpr int kTcChains = 2;
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcStages = 3;
+
+ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M) {
+  ChainPlan p;
+  p.B = B;
+  p.M = M;
+  p.F = M * (int64_t)t->K * t->digits;
+  const int64_t slots = (int64_t)t->num_sms * kTcChains;
+  // pick the segment count minimising (waves x segment length) + combine cost
+  int64_t bestS = 1;
+  double best = 1e300;
+  for (int64_t S = 1; S <= 256; ++S) {
+    const int64_t seg_len = p.F > 0 ? (p.F + S - 1) / S : 0;
+    if (S > 1 && seg_len < 64) break;
+    const int64_t segs = seg_len > 0 ? (p.F + seg_len - 1) / seg_len : 1;
+    const int64_t waves = (B * segs + slots - 1) / slots;
+    const double cost = (double)waves * (double)seg_len + 8.0 * (double)segs;
+    if (cost < best) {
+      best = cost;
+      bestS = S;
+    }
+  }
+  p.seg_len = p.F > 0 ? (p.F + bestS - 1) / bestS : 0;
+  p.S = p.seg_len > 0 ? (p.F + p.seg_len - 1) / p.seg_len : 1;
+  return p;
+}
+
+cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPlan& p,
+                            void* seg_out, int64_t* status, cudaStream_t s) {
+  using L = tc::TcLayout<kTcChains, kTcEpiWarps, kTcStages>;
+  auto kern = tc::chain_tc_kernel<kTcChains, kTcEpiWarps, kTcStages>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L::kAlloc);
+  if (e != cudaSuccess) return e;
+  tc::TcArgs a;
+  a.planes = (const uint8_t*)t->tc_planes;
+  a.q = q;
+  a.M = p.M;
+  a.K = t->K;
+  a.d = t->digits;
+  a.base = t->base;
+  a.levels = t->levels;
+  a.units = p.B;
+  a.segs = p.S;
+  a.seg_len = p.seg_len;
+  a.F = p.F;
+  a.out = (float2*)seg_out;
+  a.status = status;
+  const int64_t G = p.B * p.S;
+  const int64_t blocks = (G + kTcChains - 1) / kTcChains;
+  if (blocks == 0) return cudaSuccess;
+  kern<<<(unsigned)blocks, L::kThreads, L::kAlloc, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace redo

@@ -180,6 +180,13 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
     return fail(cuda_error(e, "drift fold"));
   if (t->T32 && (e = launch_to_fp32(t->T64, t->T32, (int64_t)n2 * t->entries, s)) != cudaSuccess)
     return fail(cuda_error(e, "FP32 copy"));
+  if (flags & REDO_TABLE_FP16X3) {
+    t->tc_bytes = tc_planes_bytes(t);
+    if ((e = cudaMalloc(&t->tc_planes, t->tc_bytes)) != cudaSuccess)
+      return fail(set_error(REDO_ERR_OOM, "FP16x3 planes allocation: %s", cudaGetErrorString(e)));
+    if ((e = launch_build_tc_planes(t, s)) != cudaSuccess)
+      return fail(cuda_error(e, "FP16x3 planes"));
+  }
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_error(e, "table build"));
   *out = t;
   return REDO_OK;
@@ -251,14 +258,40 @@ static redo_status check_prec(const redo_table* t, redo_precision prec) {
   return set_error(REDO_ERR_INVALID, "unknown precision %d", (int)prec);
 }
 
+// Plan and workspace layout shared by redo_propagate and redo_propagate_workspace.
+struct PropLayout {
+  ChainPlan p;
+  int eff_prec;       // precision of segment and pulse products
+  size_t seg_off, prod_off, prod64_off, total;
+};
+
+static PropLayout prop_layout(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                              int32_t reunit_every) {
+  PropLayout L;
+  // the tensor-core path forms segment products in split FP16 and combines them in FP32
+  L.eff_prec = prec == REDO_FP16X3 ? REDO_FP32 : prec;
+  if (reunit_every > 0)
+    L.p = plan_chain_aligned(t, B, M, reunit_every);
+  else
+    L.p = prec == REDO_FP16X3 ? plan_chain_tc(t, B, M) : plan_chain(t, B, M, L.eff_prec);
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t el = L.eff_prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t n2 = (size_t)t->N * t->N;
+  L.seg_off = 0;
+  L.prod_off = up((size_t)L.p.B * L.p.S * n2 * el);
+  L.prod64_off = L.prod_off + up((size_t)L.p.B * n2 * el);
+  L.total = L.prod64_off + (reunit_every > 0 ? up((size_t)L.p.B * n2 * sizeof(double2)) : 0);
+  return L;
+}
+
 redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
-                                     redo_precision prec, size_t* bytes) {
+                                     redo_precision prec, int32_t reunit_every, size_t* bytes) {
   if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
-  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
+  if (B < 0 || M < 0 || reunit_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
   redo_status st = check_prec(t, prec);
   if (st != REDO_OK) return st;
-  ChainPlan p = plan_chain(t, B, M, prec);
-  *bytes = chain_workspace_bytes(t, p, prec);
+  if (reunit_every > M) reunit_every = M > 0 ? (int32_t)M : 0;
+  *bytes = prop_layout(t, B, M, prec, reunit_every).total;
   return REDO_OK;
 }
 
@@ -268,7 +301,7 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
                            size_t workspace_bytes, int64_t* dev_status, void* stream) {
   if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
   if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
-  if (reunit_every != 0) return set_error(REDO_ERR_UNSUPPORTED, "reunit_every must be 0");
+  if (reunit_every < 0) return set_error(REDO_ERR_INVALID, "reunit_every must be >= 0");
   redo_status st = check_prec(t, prec);
   if (st != REDO_OK) return st;
   if (B == 0) return REDO_OK;
@@ -276,31 +309,49 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
   if (U_target && !F_out && !tau_out)
     return set_error(REDO_ERR_INVALID, "U_target given without F_out or tau_out");
   if (!U_out && !U_target) return set_error(REDO_ERR_INVALID, "nothing to compute");
-  const int eff_prec = prec == REDO_FP16X3 ? REDO_FP32 : prec;  // tensor path lands later
-  ChainPlan p = plan_chain(t, B, M, eff_prec);
-  const size_t need = chain_workspace_bytes(t, p, eff_prec);
-  if (!workspace || workspace_bytes < need)
-    return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", need);
+  if (reunit_every > M) reunit_every = M > 0 ? (int32_t)M : 0;
+  const PropLayout L = prop_layout(t, B, M, prec, reunit_every);
+  if (!workspace || workspace_bytes < L.total)
+    return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", L.total);
   if (((uintptr_t)workspace & 255) != 0) return set_error(REDO_ERR_INVALID, "workspace not 256-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t el = eff_prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
-  const size_t n2 = (size_t)t->N * t->N;
-  char* seg = (char*)workspace;
-  char* prod = seg + (((size_t)p.B * p.S * n2 * el + 255) & ~(size_t)255);
+  const ChainPlan& p = L.p;
+  const int eff = L.eff_prec;
+  char* seg = (char*)workspace + L.seg_off;
+  char* prod = (char*)workspace + L.prod_off;
+  char* prod64 = (char*)workspace + L.prod64_off;
   cudaError_t e;
-  {
+  if (prec == REDO_FP16X3) {
+    ProfScope ps(5, s);
+    if ((e = launch_chain_tc(t, q, p, seg, dev_status, s)) != cudaSuccess)
+      return cuda_error(e, "tensor-core chain segments");
+  } else {
     ProfScope ps(2, s);
-    if ((e = launch_chain_segments(t, q, p, eff_prec, seg, dev_status, s)) != cudaSuccess)
+    if ((e = launch_chain_segments(t, q, p, eff, seg, dev_status, s)) != cudaSuccess)
       return cuda_error(e, "chain segments");
+  }
+  if (reunit_every > 0 && M > 0) {
+    ProfScope ps(6, s);
+    if ((e = launch_polar(t, eff, eff, seg, seg, p.B * p.S, 1, s)) != cudaSuccess)
+      return cuda_error(e, "segment re-unitarisation");
   }
   {
     ProfScope ps(3, s);
-    if ((e = launch_chain_combine(t, p, eff_prec, seg, prod, dev_status, s)) != cudaSuccess)
+    if ((e = launch_chain_combine(t, p, eff, seg, prod, dev_status, s)) != cudaSuccess)
       return cuda_error(e, "chain combine");
+  }
+  const void* fin = prod;
+  int fin_prec = eff;
+  if (reunit_every > 0 && M > 0) {
+    ProfScope ps(6, s);
+    if ((e = launch_polar(t, eff, REDO_FP64, prod, prod64, B, 1, s)) != cudaSuccess)
+      return cuda_error(e, "final re-unitarisation");
+    fin = prod64;
+    fin_prec = REDO_FP64;
   }
   {
     ProfScope ps(4, s);
-    if ((e = launch_finalize(t, B, eff_prec, prod, U_out, (const double2*)U_target, F_out,
+    if ((e = launch_finalize(t, B, fin_prec, fin, U_out, (const double2*)U_target, F_out,
                              (double2*)tau_out, s)) != cudaSuccess)
       return cuda_error(e, "finalize");
   }

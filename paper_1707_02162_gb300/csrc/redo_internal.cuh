@@ -33,7 +33,6 @@ template <typename R> __device__ __forceinline__ void cfma(cplx<R>& acc, cplx<R>
 constexpr int kMaxK = 64;
 constexpr int kMaxN = 64;
 
-struct Fp16x3Planes;  // tensor-core operand planes, defined in kernels_tc.cu
 
 }  // namespace redo
 
@@ -96,6 +95,20 @@ cudaError_t launch_chain_segments(const redo_table* t, const int32_t* q, const C
 cudaError_t launch_chain_combine(const redo_table* t, const ChainPlan& p, int prec,
                                  const void* seg_in, void* prod_out, int64_t* status,
                                  cudaStream_t s);
+// Segments of exactly `steps_per_segment` time steps (re-unitarisation period).
+ChainPlan plan_chain_aligned(const redo_table* t, int64_t B, int64_t M, int64_t steps_per_segment);
+// One or more Newton-Schulz polar steps on `count` N x N matrices (in may equal out
+// when the precisions match); prec_in/prec_out are REDO_FP64 or REDO_FP32.
+cudaError_t launch_polar(const redo_table* t, int prec_in, int prec_out, const void* in, void* out,
+                         int64_t count, int iters, cudaStream_t s);
+
+// Tensor-core chains (kernels_tc.cu), N = 64, split-FP16.
+size_t tc_planes_bytes(const redo_table* t);
+cudaError_t launch_build_tc_planes(const redo_table* t, cudaStream_t s);
+ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M);
+cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPlan& p,
+                            void* seg_out, int64_t* status, cudaStream_t s);
+
 cudaError_t launch_finalize(const redo_table* t, int64_t B, int prec, const void* prod,
                             void* U_out, const double2* U_target, double* F_out, double2* tau_out,
                             cudaStream_t s);

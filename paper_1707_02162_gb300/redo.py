@@ -29,7 +29,8 @@ EXPORTS = [
     "redo_profile_read", "redo_propagate_noalloc",
 ]
 PROFILE_PHASES = 8
-PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "r6", "r7"]
+PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
+               "gradient"]
 
 
 class RedoError(RuntimeError):
@@ -56,7 +57,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_table_copy.argtypes = [vp, vp, vp, vp]
     L.redo_quantize.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.redo_propagate.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
-    L.redo_propagate_workspace.argtypes = [vp, i64, i64, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_propagate_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_noalloc.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
     L.redo_profile_enable.argtypes = [i32]
     L.redo_profile_read.argtypes = [vp, vp, i32]
@@ -132,9 +133,10 @@ def redo_quantize(handle: int, u: torch.Tensor, q: torch.Tensor, status: torch.T
                                         _stream(stream)))
 
 
-def redo_propagate_workspace(handle: int, B: int, M: int, prec) -> int:
+def redo_propagate_workspace(handle: int, B: int, M: int, prec, reunit_every: int = 0) -> int:
     n = ctypes.c_size_t()
-    _check(load_library().redo_propagate_workspace(ctypes.c_void_p(handle), B, M, _prec(prec), ctypes.byref(n)))
+    _check(load_library().redo_propagate_workspace(ctypes.c_void_p(handle), B, M, _prec(prec), reunit_every,
+                                                   ctypes.byref(n)))
     return n.value
 
 
@@ -210,16 +212,16 @@ class Table:
         redo_quantize(self.handle, u, q, status)
         return q
 
-    def workspace(self, B, M, prec):
-        nbytes = redo_propagate_workspace(self.handle, B, M, prec)
-        key = (B, M, _prec(prec))
+    def workspace(self, B, M, prec, reunit_every=0):
+        nbytes = redo_propagate_workspace(self.handle, B, M, prec, reunit_every)
+        key = (B, M, _prec(prec), reunit_every)
         ws = self._ws.get(key)
         if ws is None or ws.numel() < nbytes:
             ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
             self._ws[key] = ws
         return ws
 
-    def propagate(self, q, prec="fp64", target=None, want_U=True, status=None):
+    def propagate(self, q, prec="fp64", target=None, want_U=True, status=None, reunit_every=0):
         B = q.shape[0]
         U = torch.empty((B, self.N, self.N), dtype=torch.complex128, device=self.device) if want_U else None
         F = tau = None
@@ -227,8 +229,8 @@ class Table:
             target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
             F = torch.empty(B, dtype=torch.float64, device=self.device)
             tau = torch.empty(B, dtype=torch.complex128, device=self.device)
-        ws = self.workspace(B, q.shape[1], prec)
-        redo_propagate(self.handle, q, prec, U, target, F, tau, ws, status)
+        ws = self.workspace(B, q.shape[1], prec, reunit_every)
+        redo_propagate(self.handle, q, prec, U, target, F, tau, ws, status, reunit_every=reunit_every)
         return U, F, tau
 
 

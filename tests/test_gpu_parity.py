@@ -157,6 +157,23 @@ def test_propagate_fp32_n6():
     _check_prop(w, "fp32", FP32_TOL)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_propagate_reunitarized_matches_oracle_polar(prec, tol):
+    # re-unitarisation every R steps replaces each R-step block product by its
+    # polar factor; for an exact (FP64) chain that is the identity map up to rounding
+    w = inputs.config(1, B=3, M=50)
+    t = _table(w)
+    q = t.quantize(w.u)
+    U, F, _ = t.propagate(q, prec, target=w.target, reunit_every=16)
+    q_ref, dig, _, _ = _ref.oracle_levels(w)
+    T, D = _ref.oracle_table(w)
+    Uo = _ref.oracle_propagators(w, T, D, dig, range(w.B))
+    assert np.abs(U.cpu().numpy() - Uo).max() < tol
+    Ug = U.cpu().numpy()
+    G = np.einsum("bji,bjk->bik", Ug.conj(), Ug)
+    assert np.abs(G - np.eye(w.N)).max() < 1e-11
+
+
 def test_propagate_zero_steps_is_identity():
     w = inputs.config(1, B=2, M=0)
     t = _table(w)
