@@ -207,6 +207,49 @@ redo_status redo_propagate_noalloc(const redo_table* t, const int32_t* q, int64_
                                    redo_precision prec, void* U_out, const void* U_target,
                                    double* F_out, void* tau_out, int64_t* dev_status, void* stream);
 
+/*
+ * redo_fidelity_grad -- fidelity and its GRAPE gradient (Section III, the
+ * gradient ascent of Fig. fc with REDO propagators; the paper prints no
+ * gradient formula).
+ *
+ * F_b = |tau_b|^2 / N^2, tau_b = Tr(U_T^dag U_b), and for every step n and term k
+ *     grad[b][n][k] = dF_b/du_kn = (2 dt / N^2) Im( conj(tau_b) Tr(H_k W_nk) ),
+ *     W_nk = (E_k ... E_0 D  U_{n-1} ... U_1) U_T^dag (U_M ... U_{n+1} E_{K-1} ... E_{k+1}),
+ * the exact derivative of the split model U_n = E_{K-1} ... E_0 D with
+ * E_k = exp(-i dt u_kn H_k), evaluated at the quantised coefficients (the
+ * quantizer itself is piecewise constant; its derivative is taken as 1).
+ * Units: 1/(rad/s) (multiply by Omega for a normalised amplitude).
+ *
+ *  q, B, M       as for redo_propagate.
+ *  U_target      device complex128 [N][N], or [B][N][N] if target_batched != 0.
+ *  prec          REDO_FP64 or REDO_FP32 (products; traces and tau in FP64).
+ *  checkpoint_every  C > 0: forward checkpoints every C steps; 0: automatic.
+ *  F_out         device double [B] or NULL;  grad  device double [B][M][K].
+ *  workspace     >= redo_fidelity_grad_workspace() bytes, 256-byte aligned.
+ * Method: segment products (one per C steps), prefix checkpoints and suffix
+ * costates per segment, then one backward sweep per segment that undoes each
+ * factor with its adjoint (the table operators are unitary) and evaluates the
+ * traces with the sparse (CSR) form of H_k captured at table build time.
+ */
+redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                               const void* U_target, int32_t target_batched, redo_precision prec,
+                               int32_t checkpoint_every, double* F_out, double* grad,
+                               void* workspace, size_t workspace_bytes, int64_t* dev_status,
+                               void* stream);
+redo_status redo_fidelity_grad_workspace(const redo_table* t, int64_t B, int64_t M,
+                                         redo_precision prec, int32_t checkpoint_every,
+                                         size_t* bytes);
+
+/*
+ * redo_grape_step -- one GRAPE ascent update in place (Section III, Fig. fc):
+ *     u[b][n][k] <- clamp(u[b][n][k] + step * s_b * grad[b][n][k], lo[k], hi[k]).
+ * `step` is in (rad/s)^2 when grad is dF/du from redo_fidelity_grad.
+ *  u device double [B][M][K] (in/out);  grad device double [B][M][K];
+ *  step_scale device double [B] (per-pulse factor s_b) or NULL (s_b = 1).
+ */
+redo_status redo_grape_step(const redo_table* t, double* u, const double* grad, int64_t B,
+                            int64_t M, double step, const double* step_scale, void* stream);
+
 /* Scratch bytes redo_propagate needs for (B, M, prec, reunit_every) on this table. */
 redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
                                      redo_precision prec, int32_t reunit_every, size_t* bytes);

@@ -10,6 +10,7 @@
 
 #include "redo_internal.cuh"
 #include "device_sync.cuh"
+#include "smem_mm.cuh"
 
 namespace redo {
 
@@ -67,43 +68,33 @@ cudaError_t launch_quantize(const double* u, int64_t count, int K, const double*
 }
 
 // ============================================================================
-// Shared-memory complex matrix product  Y = A * X  (N x N, row-major)
-// Thread lt of a chain owns rows ty + TY*a and columns tx + TX*c.
+// GRAPE update (Section III, Fig. fc): u <- clamp(u + step * dF/du, lo_k, hi_k)
 // ============================================================================
-template <typename R, int N, int TM, int TN>
-struct SmemMM {
-  static constexpr int TY = N / TM, TX = N / TN, THREADS = TY * TX;
-  static_assert(TY * TM == N && TX * TN == N, "tile must divide N");
-  __device__ __forceinline__ static void run(const cplx<R>* __restrict__ A,
-                                             const cplx<R>* __restrict__ X, int lt,
-                                             cplx<R> (&Y)[TM][TN]) {
-    const int ty = lt / TX, tx = lt % TX;
-#pragma unroll
-    for (int a = 0; a < TM; ++a)
-#pragma unroll
-      for (int c = 0; c < TN; ++c) Y[a][c] = cmake<R>(R(0), R(0));
-#pragma unroll 4
-    for (int k = 0; k < N; ++k) {
-      cplx<R> av[TM], xv[TN];
-#pragma unroll
-      for (int a = 0; a < TM; ++a) av[a] = A[(ty + TY * a) * N + k];
-#pragma unroll
-      for (int c = 0; c < TN; ++c) xv[c] = X[k * N + tx + TX * c];
-#pragma unroll
-      for (int a = 0; a < TM; ++a)
-#pragma unroll
-        for (int c = 0; c < TN; ++c) cfma<R>(Y[a][c], av[a], xv[c]);
-    }
+__global__ void grape_step_kernel(double* __restrict__ u, const double* __restrict__ g,
+                                  int64_t count, int64_t per_pulse, int K,
+                                  const double* __restrict__ lo, const double* __restrict__ delta,
+                                  int64_t levels, double step, const double* __restrict__ scale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % K);
+    const double l = lo[k], h = l + delta[k] * (double)(levels - 1);
+    const double st = scale ? step * scale[i / per_pulse] : step;
+    double v = fma(st, g[i], u[i]);
+    v = v < l ? l : (v > h ? h : v);
+    u[i] = v;
   }
-  __device__ __forceinline__ static void store(cplx<R>* __restrict__ X, int lt,
-                                               const cplx<R> (&Y)[TM][TN]) {
-    const int ty = lt / TX, tx = lt % TX;
-#pragma unroll
-    for (int a = 0; a < TM; ++a)
-#pragma unroll
-      for (int c = 0; c < TN; ++c) X[(ty + TY * a) * N + tx + TX * c] = Y[a][c];
-  }
-};
+}
+
+cudaError_t launch_grape_step(double* u, const double* g, int64_t count, int64_t per_pulse, int K,
+                              const double* lo, const double* delta, int64_t levels, double step,
+                              const double* scale, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  grape_step_kernel<<<(unsigned)blocks, 256, 0, s>>>(u, g, count, per_pulse, K, lo, delta, levels,
+                                                     step, scale);
+  return cudaGetLastError();
+}
 
 // Per-N tiling: 256 threads per chain for N >= 16; smaller N packs several
 // independent chains into one CTA.

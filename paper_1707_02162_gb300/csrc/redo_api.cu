@@ -168,6 +168,36 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
       (e = cudaMalloc(&t->T64, sizeof(double2) * n2 * t->entries)) != cudaSuccess ||
       (e = cudaMalloc(&t->D64, sizeof(double2) * n2)) != cudaSuccess)
     return fail(set_error(REDO_ERR_OOM, "table allocation: %s", cudaGetErrorString(e)));
+  {
+    // sparse (CSR) copy of the control operators for the gradient traces Tr(H_k W)
+    std::vector<int32_t> ptr((size_t)K * (N + 1)), col;
+    std::vector<double2> val;
+    for (int k = 0; k < K; ++k) {
+      const double* hk = h.data() + 2 * n2 * (k + 1);
+      for (int r = 0; r < N; ++r) {
+        ptr[(size_t)k * (N + 1) + r] = (int32_t)col.size();
+        for (int c = 0; c < N; ++c) {
+          const double re = hk[2 * (r * N + c)], im = hk[2 * (r * N + c) + 1];
+          if (re != 0.0 || im != 0.0) {
+            col.push_back(c);
+            val.push_back(make_double2(re, im));
+          }
+        }
+      }
+      ptr[(size_t)k * (N + 1) + N] = (int32_t)col.size();
+    }
+    t->hk_nnz = (int64_t)col.size();
+    const size_t nz = col.empty() ? 1 : col.size();
+    if ((e = cudaMalloc(&t->hk_ptr, sizeof(int32_t) * ptr.size())) != cudaSuccess ||
+        (e = cudaMalloc(&t->hk_col, sizeof(int32_t) * nz)) != cudaSuccess ||
+        (e = cudaMalloc(&t->hk_val, sizeof(double2) * nz)) != cudaSuccess)
+      return fail(set_error(REDO_ERR_OOM, "operator CSR allocation: %s", cudaGetErrorString(e)));
+    if ((e = cudaMemcpy(t->hk_ptr, ptr.data(), sizeof(int32_t) * ptr.size(), cudaMemcpyHostToDevice)) ||
+        (!col.empty() &&
+         ((e = cudaMemcpy(t->hk_col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice)) ||
+          (e = cudaMemcpy(t->hk_val, val.data(), sizeof(double2) * val.size(), cudaMemcpyHostToDevice)))))
+      return fail(cuda_error(e, "operator CSR upload"));
+  }
   if ((flags & (REDO_TABLE_FP32 | REDO_TABLE_FP16X3)) &&
       (e = cudaMalloc(&t->T32, sizeof(float2) * n2 * t->entries)) != cudaSuccess)
     return fail(set_error(REDO_ERR_OOM, "FP32 table allocation: %s", cudaGetErrorString(e)));
@@ -201,6 +231,9 @@ redo_status redo_table_free(redo_table* t) {
   cudaFree(t->D64);
   cudaFree(t->T32);
   cudaFree(t->tc_planes);
+  cudaFree(t->hk_ptr);
+  cudaFree(t->hk_col);
+  cudaFree(t->hk_val);
   std::free(t);
   return REDO_OK;
 }
@@ -355,6 +388,94 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
                              (double2*)tau_out, s)) != cudaSuccess)
       return cuda_error(e, "finalize");
   }
+  return REDO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// GRAPE gradient
+// ---------------------------------------------------------------------------
+struct GradLayout {
+  ChainPlan p;
+  size_t seg_off, pck_off, rck_off, tau_off, total;
+};
+
+static GradLayout grad_layout(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                              int32_t checkpoint_every) {
+  GradLayout L;
+  L.p = checkpoint_every > 0 ? plan_chain_aligned(t, B, M, checkpoint_every)
+                             : plan_chain(t, B, M, prec);
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t el = prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t mats = up((size_t)L.p.B * L.p.S * t->N * t->N * el);
+  L.seg_off = 0;
+  L.pck_off = mats;
+  L.rck_off = 2 * mats;
+  L.tau_off = 3 * mats;
+  L.total = L.tau_off + up((size_t)B * sizeof(double2));
+  return L;
+}
+
+redo_status redo_fidelity_grad_workspace(const redo_table* t, int64_t B, int64_t M,
+                                         redo_precision prec, int32_t checkpoint_every,
+                                         size_t* bytes) {
+  if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
+  if (B < 0 || M < 0 || checkpoint_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  if (prec != REDO_FP64 && prec != REDO_FP32)
+    return set_error(REDO_ERR_UNSUPPORTED, "the gradient supports REDO_FP64 and REDO_FP32");
+  redo_status st = check_prec(t, prec);
+  if (st != REDO_OK) return st;
+  if (checkpoint_every > M) checkpoint_every = M > 0 ? (int32_t)M : 0;
+  *bytes = grad_layout(t, B, M, prec, checkpoint_every).total;
+  return REDO_OK;
+}
+
+redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                               const void* U_target, int32_t target_batched, redo_precision prec,
+                               int32_t checkpoint_every, double* F_out, double* grad,
+                               void* workspace, size_t workspace_bytes, int64_t* dev_status,
+                               void* stream) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (B < 0 || M < 0 || checkpoint_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  if (prec != REDO_FP64 && prec != REDO_FP32)
+    return set_error(REDO_ERR_UNSUPPORTED, "the gradient supports REDO_FP64 and REDO_FP32");
+  redo_status st = check_prec(t, prec);
+  if (st != REDO_OK) return st;
+  if (B == 0) return REDO_OK;
+  if (!U_target) return set_error(REDO_ERR_INVALID, "U_target is NULL");
+  if (M > 0 && (!q || !grad)) return set_error(REDO_ERR_INVALID, "q or grad is NULL");
+  if (checkpoint_every > M) checkpoint_every = M > 0 ? (int32_t)M : 0;
+  const GradLayout L = grad_layout(t, B, M, prec, checkpoint_every);
+  if (!workspace || workspace_bytes < L.total)
+    return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", L.total);
+  if (((uintptr_t)workspace & 255) != 0) return set_error(REDO_ERR_INVALID, "workspace not 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  double2* tau = (double2*)(w + L.tau_off);
+  cudaError_t e;
+  ProfScope ps(7, s);
+  if ((e = launch_chain_segments(t, q, L.p, prec, w + L.seg_off, dev_status, s)) != cudaSuccess)
+    return cuda_error(e, "gradient segments");
+  if ((e = launch_grad_scan(t, B, L.p.S, prec, w + L.seg_off, (const double2*)U_target,
+                            target_batched, w + L.pck_off, w + L.rck_off, tau, F_out, s)) !=
+      cudaSuccess)
+    return cuda_error(e, "gradient checkpoints");
+  if (M > 0 && (e = launch_grad_sweep(t, q, L.p, prec, w + L.pck_off, w + L.rck_off, tau, grad,
+                                      dev_status, s)) != cudaSuccess)
+    return cuda_error(e, "gradient sweep");
+  return REDO_OK;
+}
+
+redo_status redo_grape_step(const redo_table* t, double* u, const double* grad, int64_t B,
+                            int64_t M, double step, const double* step_scale, void* stream) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
+  if (!std::isfinite(step)) return set_error(REDO_ERR_INVALID, "step must be finite");
+  const int64_t count = B * M * t->K;
+  if (count == 0) return REDO_OK;
+  if (!u || !grad) return set_error(REDO_ERR_INVALID, "null u or grad");
+  cudaError_t e = launch_grape_step(u, grad, count, M * t->K, t->K, t->d_lo, t->d_delta,
+                                    t->levels, step, step_scale, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "grape step");
   return REDO_OK;
 }
 

@@ -47,6 +47,10 @@ struct redo_table {
   double2* T64;               // [entries][N][N], term 0 digit 0 folded with D
   double2* D64;               // [N][N]
   float2* T32;                // [entries][N][N] or nullptr
+  int32_t* hk_ptr;            // CSR of the control operators: row pointers [K][N+1]
+  int32_t* hk_col;            // column indices [nnz]
+  double2* hk_val;            // values [nnz]
+  int64_t hk_nnz;
   void* tc_planes;            // tensor-core planes or nullptr
   size_t tc_bytes;
   cudaStream_t build_stream;
@@ -108,6 +112,18 @@ cudaError_t launch_build_tc_planes(const redo_table* t, cudaStream_t s);
 ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M);
 cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPlan& p,
                             void* seg_out, int64_t* status, cudaStream_t s);
+
+cudaError_t launch_grape_step(double* u, const double* g, int64_t count, int64_t per_pulse, int K,
+                              const double* lo, const double* delta, int64_t levels, double step,
+                              const double* scale, cudaStream_t s);
+
+// GRAPE gradient (kernels_grad.cu).
+cudaError_t launch_grad_scan(const redo_table* t, int64_t B, int64_t S, int prec, const void* seg,
+                             const double2* U_target, int target_batched, void* Pck, void* Rck,
+                             double2* tau, double* F_out, cudaStream_t s);
+cudaError_t launch_grad_sweep(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
+                              const void* Pck, const void* Rck, const double2* tau, double* grad,
+                              int64_t* status, cudaStream_t s);
 
 cudaError_t launch_finalize(const redo_table* t, int64_t B, int prec, const void* prod,
                             void* U_out, const double2* U_target, double* F_out, double2* tau_out,

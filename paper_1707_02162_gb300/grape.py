@@ -1,0 +1,86 @@
+"""GRAPE with REDO propagators on the GPU (Section III, Fig. fc).
+
+* :class:`RedoFidelity` -- ``torch.autograd.Function``: the fidelity of every
+  pulse against a target, differentiable with respect to the control
+  coefficients through libredo's gradient entry point (the derivative of the
+  split model at the quantised point; the quantizer is passed straight through).
+* :func:`grape` -- the ascent loop: quantise, fidelity + gradient, update in
+  place; the table is built once outside the loop as the method prescribes.
+  Every step of an iteration runs in libredo kernels; the only host read per
+  iteration is the fidelity vector.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import redo
+
+
+class RedoFidelity(torch.autograd.Function):
+    """F = |Tr(U_T^dag U(u))|^2 / N^2 for u of shape [B][M][K] (float64, device)."""
+
+    @staticmethod
+    def forward(ctx, u, table: redo.Table, target, prec="fp64", checkpoint_every=0):
+        q = table.quantize(u.detach())
+        F, g = table.fidelity_grad(q, target, prec, checkpoint_every)
+        ctx.save_for_backward(g)
+        return F
+
+    @staticmethod
+    def backward(ctx, grad_F):
+        (g,) = ctx.saved_tensors
+        return grad_F[:, None, None] * g, None, None, None, None
+
+
+@dataclass
+class GrapeResult:
+    u: torch.Tensor
+    F_history: list = field(default_factory=list)
+    iterations: int = 0
+    reached: torch.Tensor | None = None        # per pulse: first iteration with F >= threshold (-1 if never)
+
+
+def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, prec="fp64",
+          checkpoint_every=0, threshold: float | None = None, adaptive: bool = True) -> GrapeResult:
+    """Fixed-step gradient ascent on the fidelity, ``u <- clamp(u + step * dF/du)``.
+
+    With ``adaptive`` the step of a pulse is halved whenever its fidelity
+    decreased and grown by 1.1 otherwise (a cheap stand-in for a line search;
+    the paper does not specify the update rule).  Stops early once every
+    pulse reached ``threshold``.
+    """
+    u = u0.clone().contiguous()
+    B, M, K = u.shape
+    scale_h = torch.ones(B, dtype=torch.float64)               # per-pulse step factors (host)
+    scale_d = torch.ones(B, dtype=torch.float64, device=u.device)
+    prev_F = None
+    reached = torch.full((B,), -1, dtype=torch.int64)
+    res = GrapeResult(u=u)
+    nbytes = redo.redo_fidelity_grad_workspace(table.handle, B, M, prec, checkpoint_every)
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=u.device)
+    target = torch.as_tensor(target, dtype=torch.complex128, device=u.device).contiguous()
+    q = torch.empty(u.shape, dtype=torch.int32, device=u.device)
+    F = torch.empty(B, dtype=torch.float64, device=u.device)
+    g = torch.empty(u.shape, dtype=torch.float64, device=u.device)
+    for it in range(iters):
+        redo.redo_quantize(table.handle, u, q)
+        redo.redo_fidelity_grad(table.handle, q, target, prec, checkpoint_every, F, g, ws)
+        Fh = F.cpu()
+        res.F_history.append(Fh.clone())
+        if threshold is not None:
+            newly = (Fh >= threshold) & (reached < 0)
+            reached[newly] = it
+            if bool((reached >= 0).all()):
+                break
+        if adaptive and prev_F is not None:
+            worse = Fh < prev_F
+            scale_h = torch.where(worse, scale_h * 0.5, torch.clamp(scale_h * 1.1, max=8.0))
+            scale_d.copy_(scale_h, non_blocking=True)
+        prev_F = Fh
+        redo.redo_grape_step(table.handle, u, g, step, scale_d if adaptive else None)
+        res.iterations = it + 1
+    res.u = u
+    res.reached = reached
+    return res

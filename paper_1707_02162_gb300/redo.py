@@ -26,7 +26,8 @@ STATUS_NONFINITE, STATUS_SATURATED, STATUS_TIMEOUT, STATUS_BADINDEX = range(4)
 EXPORTS = [
     "redo_build_table", "redo_table_free", "redo_table_info", "redo_table_copy", "redo_quantize",
     "redo_propagate", "redo_propagate_workspace", "redo_last_error", "redo_profile_enable",
-    "redo_profile_read", "redo_propagate_noalloc",
+    "redo_profile_read", "redo_propagate_noalloc", "redo_fidelity_grad", "redo_fidelity_grad_workspace",
+    "redo_grape_step",
 ]
 PROFILE_PHASES = 8
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -59,6 +60,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_propagate.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_propagate_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_noalloc.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
+    L.redo_fidelity_grad.argtypes = [vp, vp, i64, i64, vp, i32, i32, i32, vp, vp, vp, ctypes.c_size_t, vp, vp]
+    L.redo_fidelity_grad_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_grape_step.argtypes = [vp, vp, vp, i64, i64, dbl, vp, vp]
     L.redo_profile_enable.argtypes = [i32]
     L.redo_profile_read.argtypes = [vp, vp, i32]
     L.redo_last_error.restype = ctypes.c_char_p
@@ -161,6 +165,32 @@ def redo_propagate_noalloc(handle: int, q: torch.Tensor, prec, U_out: torch.Tens
                                                  _stream(stream)))
 
 
+def redo_fidelity_grad_workspace(handle: int, B: int, M: int, prec, checkpoint_every: int = 0) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().redo_fidelity_grad_workspace(ctypes.c_void_p(handle), B, M, _prec(prec), checkpoint_every,
+                                                       ctypes.byref(n)))
+    return n.value
+
+
+def redo_fidelity_grad(handle: int, q: torch.Tensor, U_target: torch.Tensor, prec, checkpoint_every: int,
+                       F_out: torch.Tensor | None, grad: torch.Tensor, workspace: torch.Tensor,
+                       status: torch.Tensor | None = None, stream=None):
+    B, M = q.shape[0], q.shape[1]
+    batched = 1 if U_target.dim() == 3 else 0
+    _check(load_library().redo_fidelity_grad(ctypes.c_void_p(handle), _ptr(q), B, M, _ptr(U_target), batched,
+                                             _prec(prec), checkpoint_every, _ptr(F_out), _ptr(grad), _ptr(workspace),
+                                             workspace.numel() * workspace.element_size(), _ptr(status),
+                                             _stream(stream)))
+
+
+def redo_grape_step(handle: int, u: torch.Tensor, grad: torch.Tensor, step: float,
+                    step_scale: torch.Tensor | None = None, stream=None):
+    """In place: u <- clamp(u + step * s_b * grad, lo_k, hi_k) (gradient ascent on the fidelity)."""
+    B, M = u.shape[0], u.shape[1]
+    _check(load_library().redo_grape_step(ctypes.c_void_p(handle), _ptr(u), _ptr(grad), B, M, float(step),
+                                          _ptr(step_scale), _stream(stream)))
+
+
 def redo_profile_enable(enable: bool):
     _check(load_library().redo_profile_enable(1 if enable else 0))
 
@@ -232,6 +262,21 @@ class Table:
         ws = self.workspace(B, q.shape[1], prec, reunit_every)
         redo_propagate(self.handle, q, prec, U, target, F, tau, ws, status, reunit_every=reunit_every)
         return U, F, tau
+
+
+def _table_fidelity_grad(self, q, target, prec="fp64", checkpoint_every=0, status=None):
+    """(F [B], grad [B][M][K]) of the fidelity against `target` at levels q."""
+    B, M = q.shape[0], q.shape[1]
+    target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
+    F = torch.empty(B, dtype=torch.float64, device=self.device)
+    g = torch.empty((B, M, self.K), dtype=torch.float64, device=self.device)
+    nbytes = redo_fidelity_grad_workspace(self.handle, B, M, prec, checkpoint_every)
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+    redo_fidelity_grad(self.handle, q, target, prec, checkpoint_every, F, g, ws, status)
+    return F, g
+
+
+Table.fidelity_grad = _table_fidelity_grad
 
 
 def new_status(device="cuda") -> torch.Tensor:
