@@ -241,6 +241,30 @@ redo_status redo_fidelity_grad_workspace(const redo_table* t, int64_t B, int64_t
                                          size_t* bytes);
 
 /*
+ * redo_simulate -- dynamics along REDO chains (Section IV): for each pulse
+ * (noise realisation) b the state psi_n = U_n ... U_1 psi_0 and the expectation
+ *     expect[b][n] = <psi_n| O |psi_n> = sum_a obs_diag[a] |psi_n[a]|^2,  n = 0..M,
+ * of a diagonal observable (Tr[O rho(t)] with rho = |psi><psi|), plus optionally
+ * the final propagator U_M ... U_1.
+ *
+ * The state is advanced by one matrix-vector product per table operator, in
+ * FP64 for REDO_FP64 and FP32 otherwise; U_final, if requested, is computed
+ * exactly as redo_propagate(prec, reunit_every) computes U_out.
+ *  psi0      device complex128 [N] (or [B][N] if psi0_batched != 0).
+ *  obs_diag  device double [N];  expect  device double [B][M+1].
+ *  U_final   device complex128 [B][N][N] or NULL.
+ *  workspace >= redo_simulate_workspace(..., want_U = U_final != NULL) bytes.
+ */
+redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                          redo_precision prec, int32_t reunit_every, const void* psi0,
+                          int32_t psi0_batched, const double* obs_diag, double* expect,
+                          void* U_final, void* workspace, size_t workspace_bytes,
+                          int64_t* dev_status, void* stream);
+redo_status redo_simulate_workspace(const redo_table* t, int64_t B, int64_t M,
+                                    redo_precision prec, int32_t reunit_every, int32_t want_U,
+                                    size_t* bytes);
+
+/*
  * redo_grape_step -- one GRAPE ascent update in place (Section III, Fig. fc):
  *     u[b][n][k] <- clamp(u[b][n][k] + step * s_b * grad[b][n][k], lo[k], hi[k]).
  * `step` is in (rad/s)^2 when grad is dF/du from redo_fidelity_grad.

@@ -465,6 +465,47 @@ redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B,
   return REDO_OK;
 }
 
+redo_status redo_simulate_workspace(const redo_table* t, int64_t B, int64_t M,
+                                    redo_precision prec, int32_t reunit_every, int32_t want_U,
+                                    size_t* bytes) {
+  if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
+  if (!want_U) {
+    redo_status st = check_prec(t, prec);
+    if (st != REDO_OK) return st;
+    *bytes = 0;
+    return REDO_OK;
+  }
+  return redo_propagate_workspace(t, B, M, prec, reunit_every, bytes);
+}
+
+redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                          redo_precision prec, int32_t reunit_every, const void* psi0,
+                          int32_t psi0_batched, const double* obs_diag, double* expect,
+                          void* U_final, void* workspace, size_t workspace_bytes,
+                          int64_t* dev_status, void* stream) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (B < 0 || M < 0 || reunit_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  redo_status st = check_prec(t, prec);
+  if (st != REDO_OK) return st;
+  if (prec == REDO_FP16X3 && !t->T32)
+    return set_error(REDO_ERR_INVALID, "state simulation needs the FP32 table copy");
+  if (B == 0) return REDO_OK;
+  if (!psi0 || !obs_diag || !expect) return set_error(REDO_ERR_INVALID, "null psi0, obs_diag or expect");
+  if (M > 0 && !q) return set_error(REDO_ERR_INVALID, "q is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    ProfScope ps(2, s);
+    cudaError_t e = launch_sim_state(t, q, B, M, prec == REDO_FP64 ? REDO_FP64 : REDO_FP32,
+                                     (const double2*)psi0, psi0_batched, obs_diag, expect,
+                                     dev_status, s);
+    if (e != cudaSuccess) return cuda_error(e, "state simulation");
+  }
+  if (U_final)
+    return redo_propagate(t, q, B, M, prec, reunit_every, U_final, nullptr, nullptr, nullptr,
+                          workspace, workspace_bytes, dev_status, stream);
+  return REDO_OK;
+}
+
 redo_status redo_grape_step(const redo_table* t, double* u, const double* grad, int64_t B,
                             int64_t M, double step, const double* step_scale, void* stream) {
   if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");

@@ -125,6 +125,11 @@ cudaError_t launch_grad_sweep(const redo_table* t, const int32_t* q, const Chain
                               const void* Pck, const void* Rck, const double2* tau, double* grad,
                               int64_t* status, cudaStream_t s);
 
+// State simulation (kernels_sim.cu).
+cudaError_t launch_sim_state(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                             int prec, const double2* psi0, int psi0_batched, const double* obs,
+                             double* expect, int64_t* status, cudaStream_t s);
+
 cudaError_t launch_finalize(const redo_table* t, int64_t B, int prec, const void* prod,
                             void* U_out, const double2* U_target, double* F_out, double2* tau_out,
                             cudaStream_t s);

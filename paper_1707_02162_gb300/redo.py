@@ -27,7 +27,7 @@ EXPORTS = [
     "redo_build_table", "redo_table_free", "redo_table_info", "redo_table_copy", "redo_quantize",
     "redo_propagate", "redo_propagate_workspace", "redo_last_error", "redo_profile_enable",
     "redo_profile_read", "redo_propagate_noalloc", "redo_fidelity_grad", "redo_fidelity_grad_workspace",
-    "redo_grape_step",
+    "redo_grape_step", "redo_simulate", "redo_simulate_workspace",
 ]
 PROFILE_PHASES = 8
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -63,6 +63,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_fidelity_grad.argtypes = [vp, vp, i64, i64, vp, i32, i32, i32, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_fidelity_grad_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_grape_step.argtypes = [vp, vp, vp, i64, i64, dbl, vp, vp]
+    L.redo_simulate.argtypes = [vp, vp, i64, i64, i32, i32, vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
+    L.redo_simulate_workspace.argtypes = [vp, i64, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_profile_enable.argtypes = [i32]
     L.redo_profile_read.argtypes = [vp, vp, i32]
     L.redo_last_error.restype = ctypes.c_char_p
@@ -191,6 +193,24 @@ def redo_grape_step(handle: int, u: torch.Tensor, grad: torch.Tensor, step: floa
                                           _ptr(step_scale), _stream(stream)))
 
 
+def redo_simulate_workspace(handle: int, B: int, M: int, prec, reunit_every: int = 0, want_U: bool = True) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().redo_simulate_workspace(ctypes.c_void_p(handle), B, M, _prec(prec), reunit_every,
+                                                  1 if want_U else 0, ctypes.byref(n)))
+    return n.value
+
+
+def redo_simulate(handle: int, q: torch.Tensor, prec, reunit_every: int, psi0: torch.Tensor, obs_diag: torch.Tensor,
+                  expect: torch.Tensor, U_final: torch.Tensor | None, workspace: torch.Tensor | None,
+                  status: torch.Tensor | None = None, stream=None):
+    B, M = q.shape[0], q.shape[1]
+    batched = 1 if psi0.dim() == 2 else 0
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().redo_simulate(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), reunit_every,
+                                        _ptr(psi0), batched, _ptr(obs_diag), _ptr(expect), _ptr(U_final),
+                                        _ptr(workspace), nbytes, _ptr(status), _stream(stream)))
+
+
 def redo_profile_enable(enable: bool):
     _check(load_library().redo_profile_enable(1 if enable else 0))
 
@@ -277,6 +297,21 @@ def _table_fidelity_grad(self, q, target, prec="fp64", checkpoint_every=0, statu
 
 
 Table.fidelity_grad = _table_fidelity_grad
+
+
+def _table_simulate(self, q, psi0, obs_diag, prec="fp64", reunit_every=0, want_U=True, status=None):
+    """(expect [B][M+1], U_final [B][N][N] or None) along the chains of levels q."""
+    B, M = q.shape[0], q.shape[1]
+    psi0 = torch.as_tensor(psi0, dtype=torch.complex128, device=self.device).contiguous()
+    obs = torch.as_tensor(obs_diag, dtype=torch.float64, device=self.device).contiguous()
+    ex = torch.empty((B, M + 1), dtype=torch.float64, device=self.device)
+    U = torch.empty((B, self.N, self.N), dtype=torch.complex128, device=self.device) if want_U else None
+    ws = self.workspace(B, M, prec, reunit_every) if want_U else None
+    redo_simulate(self.handle, q, prec, reunit_every, psi0, obs, ex, U, ws, status)
+    return ex, U
+
+
+Table.simulate = _table_simulate
 
 
 def new_status(device="cuda") -> torch.Tensor:
