@@ -274,6 +274,39 @@ redo_status redo_simulate_workspace(const redo_table* t, int64_t B, int64_t M,
 redo_status redo_grape_step(const redo_table* t, double* u, const double* grad, int64_t B,
                             int64_t M, double step, const double* step_scale, void* stream);
 
+/*
+ * Learned warm start for GRAPE (no counterpart in the paper): a multilayer
+ * perceptron maps problem parameters to an initial pulse.  FP32 master
+ * weights, FP32 arithmetic, all device memory caller-owned.
+ *
+ * Network with `layers` affine maps of widths sizes[0] -> ... -> sizes[layers]
+ * (host int32 array): h_0 = x, z_l = h_l W_l^T + b_l, h_{l+1} = GELU(z_l)
+ * (exact erf form) for l < layers-1 and y = tanh(z_{layers-1}).  `params` is one
+ * flat array holding W_0 (sizes[1] x sizes[0], row-major), b_0, W_1, b_1, ...
+ *
+ * redo_mlp_sizes: float counts of params, of the activation buffer `acts`
+ *   (z and h of every layer for `batch` samples) and of the backward `work`
+ *   buffer.  Host only.
+ * redo_mlp_forward: x [batch][sizes[0]] -> y [batch][sizes[layers]], filling acts.
+ * redo_mlp_backward: gradients of loss = mean over all entries of
+ *   (y - y_target)^2 into grads (same layout as params), using the acts of the
+ *   preceding forward call; loss (device double [1], may be NULL) receives the loss.
+ * redo_mlp_adam: Adam (bias-corrected, step >= 1) on `count` parameters:
+ *   m <- b1 m + (1-b1) g; v <- b2 v + (1-b2) g^2;
+ *   p <- p - lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
+ */
+redo_status redo_mlp_sizes(int32_t layers, const int32_t* sizes, int64_t batch,
+                           int64_t* params, int64_t* acts, int64_t* work);
+redo_status redo_mlp_forward(int32_t layers, const int32_t* sizes, const float* params,
+                             const float* x, int64_t batch, float* acts, float* y, void* stream);
+redo_status redo_mlp_backward(int32_t layers, const int32_t* sizes, const float* params,
+                              const float* x, int64_t batch, const float* acts,
+                              const float* y_target, float* grads, double* loss, float* work,
+                              void* stream);
+redo_status redo_mlp_adam(int64_t count, float* params, const float* grads, float* m, float* v,
+                          int32_t step, float lr, float beta1, float beta2, float eps,
+                          void* stream);
+
 /* Scratch bytes redo_propagate needs for (B, M, prec, reunit_every) on this table. */
 redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
                                      redo_precision prec, int32_t reunit_every, size_t* bytes);

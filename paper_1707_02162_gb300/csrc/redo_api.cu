@@ -506,6 +506,65 @@ redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int6
   return REDO_OK;
 }
 
+static redo_status check_mlp(int32_t layers, const int32_t* sizes) {
+  if (layers < 1 || layers > 32 || !sizes) return set_error(REDO_ERR_INVALID, "1 <= layers <= 32");
+  for (int l = 0; l <= layers; ++l)
+    if (sizes[l] < 1 || sizes[l] > (1 << 20)) return set_error(REDO_ERR_INVALID, "bad layer width");
+  return REDO_OK;
+}
+
+redo_status redo_mlp_sizes(int32_t layers, const int32_t* sizes, int64_t batch,
+                           int64_t* params, int64_t* acts, int64_t* work) {
+  redo_status st = check_mlp(layers, sizes);
+  if (st != REDO_OK) return st;
+  if (batch < 0) return set_error(REDO_ERR_INVALID, "negative batch");
+  int64_t a = 0, mw = 0;
+  for (int l = 0; l <= layers; ++l) {
+    if (l > 0) a += 2 * batch * sizes[l];
+    if (sizes[l] > mw) mw = sizes[l];
+  }
+  if (params) *params = mlp_param_count(layers, sizes);
+  if (acts) *acts = a;
+  if (work) *work = 2 * batch * mw;
+  return REDO_OK;
+}
+
+redo_status redo_mlp_forward(int32_t layers, const int32_t* sizes, const float* params,
+                             const float* x, int64_t batch, float* acts, float* y, void* stream) {
+  redo_status st = check_mlp(layers, sizes);
+  if (st != REDO_OK) return st;
+  if (batch < 0) return set_error(REDO_ERR_INVALID, "negative batch");
+  if (batch == 0) return REDO_OK;
+  if (!params || !x || !acts || !y) return set_error(REDO_ERR_INVALID, "null pointer");
+  cudaError_t e = mlp_forward(layers, sizes, params, x, batch, acts, y, (cudaStream_t)stream);
+  return e == cudaSuccess ? REDO_OK : cuda_error(e, "mlp forward");
+}
+
+redo_status redo_mlp_backward(int32_t layers, const int32_t* sizes, const float* params,
+                              const float* x, int64_t batch, const float* acts,
+                              const float* y_target, float* grads, double* loss, float* work,
+                              void* stream) {
+  redo_status st = check_mlp(layers, sizes);
+  if (st != REDO_OK) return st;
+  if (batch < 1) return set_error(REDO_ERR_INVALID, "batch must be >= 1");
+  if (!params || !x || !acts || !y_target || !grads || !work)
+    return set_error(REDO_ERR_INVALID, "null pointer");
+  cudaError_t e = mlp_backward(layers, sizes, params, x, batch, acts, y_target, grads, loss, work,
+                               (cudaStream_t)stream);
+  return e == cudaSuccess ? REDO_OK : cuda_error(e, "mlp backward");
+}
+
+redo_status redo_mlp_adam(int64_t count, float* params, const float* grads, float* m, float* v,
+                          int32_t step, float lr, float beta1, float beta2, float eps,
+                          void* stream) {
+  if (count < 0 || step < 1) return set_error(REDO_ERR_INVALID, "count >= 0 and step >= 1");
+  if (count == 0) return REDO_OK;
+  if (!params || !grads || !m || !v) return set_error(REDO_ERR_INVALID, "null pointer");
+  cudaError_t e = mlp_adam(count, params, grads, m, v, step, lr, beta1, beta2, eps,
+                           (cudaStream_t)stream);
+  return e == cudaSuccess ? REDO_OK : cuda_error(e, "adam");
+}
+
 redo_status redo_grape_step(const redo_table* t, double* u, const double* grad, int64_t B,
                             int64_t M, double step, const double* step_scale, void* stream) {
   if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");

@@ -130,6 +130,16 @@ cudaError_t launch_sim_state(const redo_table* t, const int32_t* q, int64_t B, i
                              int prec, const double2* psi0, int psi0_batched, const double* obs,
                              double* expect, int64_t* status, cudaStream_t s);
 
+// Warm-start MLP (kernels_mlp.cu).
+int64_t mlp_param_count(int L, const int32_t* sizes);
+cudaError_t mlp_forward(int L, const int32_t* sizes, const float* params, const float* x,
+                        int64_t batch, float* acts, float* y, cudaStream_t s);
+cudaError_t mlp_backward(int L, const int32_t* sizes, const float* params, const float* x,
+                         int64_t batch, const float* acts, const float* y_target, float* grads,
+                         double* loss, float* work, cudaStream_t s);
+cudaError_t mlp_adam(int64_t count, float* p, const float* g, float* m, float* v, int step, float lr,
+                     float b1, float b2, float eps, cudaStream_t s);
+
 cudaError_t launch_finalize(const redo_table* t, int64_t B, int prec, const void* prod,
                             void* U_out, const double2* U_target, double* F_out, double2* tau_out,
                             cudaStream_t s);

@@ -27,7 +27,8 @@ EXPORTS = [
     "redo_build_table", "redo_table_free", "redo_table_info", "redo_table_copy", "redo_quantize",
     "redo_propagate", "redo_propagate_workspace", "redo_last_error", "redo_profile_enable",
     "redo_profile_read", "redo_propagate_noalloc", "redo_fidelity_grad", "redo_fidelity_grad_workspace",
-    "redo_grape_step", "redo_simulate", "redo_simulate_workspace",
+    "redo_grape_step", "redo_simulate", "redo_simulate_workspace", "redo_mlp_sizes", "redo_mlp_forward",
+    "redo_mlp_backward", "redo_mlp_adam",
 ]
 PROFILE_PHASES = 8
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -65,6 +66,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_grape_step.argtypes = [vp, vp, vp, i64, i64, dbl, vp, vp]
     L.redo_simulate.argtypes = [vp, vp, i64, i64, i32, i32, vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_simulate_workspace.argtypes = [vp, i64, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_mlp_sizes.argtypes = [i32, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.redo_mlp_forward.argtypes = [i32, vp, vp, vp, i64, vp, vp, vp]
+    L.redo_mlp_backward.argtypes = [i32, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp]
+    L.redo_mlp_adam.argtypes = [i64, vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, vp]
     L.redo_profile_enable.argtypes = [i32]
     L.redo_profile_read.argtypes = [vp, vp, i32]
     L.redo_last_error.restype = ctypes.c_char_p
@@ -209,6 +215,37 @@ def redo_simulate(handle: int, q: torch.Tensor, prec, reunit_every: int, psi0: t
     _check(load_library().redo_simulate(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), reunit_every,
                                         _ptr(psi0), batched, _ptr(obs_diag), _ptr(expect), _ptr(U_final),
                                         _ptr(workspace), nbytes, _ptr(status), _stream(stream)))
+
+
+def _sizes_arg(sizes):
+    arr = (ctypes.c_int32 * len(sizes))(*[int(x) for x in sizes])
+    return arr, len(sizes) - 1
+
+
+def redo_mlp_sizes(sizes, batch: int) -> tuple[int, int, int]:
+    arr, L = _sizes_arg(sizes)
+    p, a, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().redo_mlp_sizes(L, ctypes.cast(arr, ctypes.c_void_p), batch, ctypes.byref(p),
+                                         ctypes.byref(a), ctypes.byref(w)))
+    return p.value, a.value, w.value
+
+
+def redo_mlp_forward(sizes, params, x, acts, y, stream=None):
+    arr, L = _sizes_arg(sizes)
+    _check(load_library().redo_mlp_forward(L, ctypes.cast(arr, ctypes.c_void_p), _ptr(params), _ptr(x), x.shape[0],
+                                           _ptr(acts), _ptr(y), _stream(stream)))
+
+
+def redo_mlp_backward(sizes, params, x, acts, y_target, grads, loss, work, stream=None):
+    arr, L = _sizes_arg(sizes)
+    _check(load_library().redo_mlp_backward(L, ctypes.cast(arr, ctypes.c_void_p), _ptr(params), _ptr(x), x.shape[0],
+                                            _ptr(acts), _ptr(y_target), _ptr(grads), _ptr(loss), _ptr(work),
+                                            _stream(stream)))
+
+
+def redo_mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load_library().redo_mlp_adam(params.numel(), _ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(step),
+                                        float(lr), float(beta1), float(beta2), float(eps), _stream(stream)))
 
 
 def redo_profile_enable(enable: bool):
