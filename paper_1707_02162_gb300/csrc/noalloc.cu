@@ -58,6 +58,7 @@ extern "C" redo_status redo_propagate_noalloc(const redo_table* t, const int32_t
   if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
   if (prec != REDO_FP64 && prec != REDO_FP32)
     return set_error(REDO_ERR_UNSUPPORTED, "redo_propagate_noalloc supports REDO_FP64 and REDO_FP32");
+  if (t->N > kSmallN) return set_error(REDO_ERR_UNSUPPORTED, "redo_propagate_noalloc supports N <= 64");
   if (prec == REDO_FP32 && !t->T32)
     return set_error(REDO_ERR_INVALID, "REDO_FP32 needs a table built with REDO_TABLE_FP32");
   if (B == 0) return REDO_OK;

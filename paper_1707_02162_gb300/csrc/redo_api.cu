@@ -108,7 +108,7 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
   *out = nullptr;
   if (!H0 || !Hk || !lo || !hi) return set_error(REDO_ERR_INVALID, "null input pointer");
   if (N < 2 || N > kMaxN || !is_pow2(N))
-    return set_error(REDO_ERR_UNSUPPORTED, "N=%d: this build supports N in {2,4,...,64}", N);
+    return set_error(REDO_ERR_UNSUPPORTED, "N=%d: this build supports N in {2,4,...,1024}", N);
   if (K < 1 || K > kMaxK) return set_error(REDO_ERR_INVALID, "K=%d out of [1, %d]", K, kMaxK);
   if (!(dt > 0) || !std::isfinite(dt)) return set_error(REDO_ERR_INVALID, "dt must be > 0");
   if (base < 2 || digits < 1) return set_error(REDO_ERR_INVALID, "base >= 2 and digits >= 1");
@@ -204,10 +204,28 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
   if ((e = cudaMemcpyAsync(t->d_lo, t->lo, sizeof(double) * K, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(t->d_delta, t->delta, sizeof(double) * K, cudaMemcpyHostToDevice, s)))
     return fail(cuda_error(e, "copy lo/delta"));
-  if ((e = launch_table_expm(t, (const double2*)H0, (const double2*)Hk, s)) != cudaSuccess)
-    return fail(cuda_error(e, "table exponentials"));
-  if ((e = launch_table_fold_drift(t, s)) != cudaSuccess)
-    return fail(cuda_error(e, "drift fold"));
+  if (N <= kSmallN) {
+    if ((e = launch_table_expm(t, (const double2*)H0, (const double2*)Hk, s)) != cudaSuccess)
+      return fail(cuda_error(e, "table exponentials"));
+    if ((e = launch_table_fold_drift(t, s)) != cudaSuccess)
+      return fail(cuda_error(e, "drift fold"));
+  } else {
+    // 1-norms (max column sum) of the generators bound the Taylor scaling
+    std::vector<double> hn(K);
+    double h0n = 0.0;
+    for (int k = -1; k < K; ++k) {
+      const double* hk = h.data() + 2 * n2 * (k + 1);
+      double mx = 0.0;
+      for (int c = 0; c < N; ++c) {
+        double sum = 0.0;
+        for (int r = 0; r < N; ++r) sum += std::hypot(hk[2 * (r * N + c)], hk[2 * (r * N + c) + 1]);
+        mx = std::fmax(mx, sum);
+      }
+      if (k < 0) h0n = mx; else hn[k] = mx;
+    }
+    if ((e = large_table_build(t, (const double2*)H0, (const double2*)Hk, hn, h0n, s)) != cudaSuccess)
+      return fail(cuda_error(e, "large-N table"));
+  }
   if (t->T32 && (e = launch_to_fp32(t->T64, t->T32, (int64_t)n2 * t->entries, s)) != cudaSuccess)
     return fail(cuda_error(e, "FP32 copy"));
   if (flags & REDO_TABLE_FP16X3) {
@@ -301,6 +319,13 @@ struct PropLayout {
 static PropLayout prop_layout(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
                               int32_t reunit_every) {
   PropLayout L;
+  if (t->N > kSmallN) {
+    L.eff_prec = prec;
+    L.p = reunit_every > 0 ? plan_chain_aligned(t, B, M, reunit_every) : plan_chain_large(t, B, M);
+    L.seg_off = L.prod_off = L.prod64_off = 0;
+    L.total = large_prop_workspace(t, L.p, prec, reunit_every > 0);
+    return L;
+  }
   // the tensor-core path forms segment products in split FP16 and combines them in FP32
   L.eff_prec = prec == REDO_FP16X3 ? REDO_FP32 : prec;
   if (reunit_every > 0)
@@ -354,6 +379,21 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
   char* prod = (char*)workspace + L.prod_off;
   char* prod64 = (char*)workspace + L.prod64_off;
   cudaError_t e;
+  if (t->N > kSmallN) {
+    void* res = nullptr;
+    int res_prec = eff;
+    {
+      ProfScope ps(2, s);
+      if ((e = large_propagate(t, q, p, eff, reunit_every > 0, workspace, &res, &res_prec,
+                               dev_status, s)) != cudaSuccess)
+        return cuda_error(e, "large-N chains");
+    }
+    ProfScope ps(4, s);
+    if ((e = launch_finalize(t, B, res_prec, res, U_out, (const double2*)U_target, F_out,
+                             (double2*)tau_out, s)) != cudaSuccess)
+      return cuda_error(e, "finalize");
+    return REDO_OK;
+  }
   if (prec == REDO_FP16X3) {
     ProfScope ps(5, s);
     if ((e = launch_chain_tc(t, q, p, seg, dev_status, s)) != cudaSuccess)
@@ -402,6 +442,13 @@ struct GradLayout {
 static GradLayout grad_layout(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
                               int32_t checkpoint_every) {
   GradLayout L;
+  if (t->N > kSmallN) {
+    L.p = checkpoint_every > 0 ? plan_chain_aligned(t, B, M, checkpoint_every)
+                               : plan_chain_large(t, B, M);
+    L.seg_off = L.pck_off = L.rck_off = L.tau_off = 0;
+    L.total = large_grad_workspace(t, L.p, prec);
+    return L;
+  }
   L.p = checkpoint_every > 0 ? plan_chain_aligned(t, B, M, checkpoint_every)
                              : plan_chain(t, B, M, prec);
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -453,6 +500,12 @@ redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B,
   double2* tau = (double2*)(w + L.tau_off);
   cudaError_t e;
   ProfScope ps(7, s);
+  if (t->N > kSmallN) {
+    if ((e = large_grad(t, q, L.p, prec, (const double2*)U_target, target_batched, F_out, grad,
+                        workspace, dev_status, s)) != cudaSuccess)
+      return cuda_error(e, "large-N gradient");
+    return REDO_OK;
+  }
   if ((e = launch_chain_segments(t, q, L.p, prec, w + L.seg_off, dev_status, s)) != cudaSuccess)
     return cuda_error(e, "gradient segments");
   if ((e = launch_grad_scan(t, B, L.p.S, prec, w + L.seg_off, (const double2*)U_target,
@@ -469,13 +522,16 @@ redo_status redo_simulate_workspace(const redo_table* t, int64_t B, int64_t M,
                                     redo_precision prec, int32_t reunit_every, int32_t want_U,
                                     size_t* bytes) {
   if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
-  if (!want_U) {
-    redo_status st = check_prec(t, prec);
+  redo_status st = check_prec(t, prec);
+  if (st != REDO_OK) return st;
+  const size_t state = t->N > kSmallN ? large_sim_workspace(t, B) : 0;
+  size_t prop = 0;
+  if (want_U) {
+    st = redo_propagate_workspace(t, B, M, prec, reunit_every, &prop);
     if (st != REDO_OK) return st;
-    *bytes = 0;
-    return REDO_OK;
   }
-  return redo_propagate_workspace(t, B, M, prec, reunit_every, bytes);
+  *bytes = state > prop ? state : prop;   // the two phases run one after the other
+  return REDO_OK;
 }
 
 redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
@@ -495,9 +551,17 @@ redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int6
   cudaStream_t s = (cudaStream_t)stream;
   {
     ProfScope ps(2, s);
-    cudaError_t e = launch_sim_state(t, q, B, M, prec == REDO_FP64 ? REDO_FP64 : REDO_FP32,
-                                     (const double2*)psi0, psi0_batched, obs_diag, expect,
-                                     dev_status, s);
+    cudaError_t e;
+    if (t->N > kSmallN) {
+      const size_t need = large_sim_workspace(t, B);
+      if (!workspace || workspace_bytes < need)
+        return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", need);
+      e = large_sim(t, q, B, M, prec == REDO_FP64 ? REDO_FP64 : REDO_FP32, (const double2*)psi0,
+                    psi0_batched, obs_diag, expect, workspace, s);
+    } else {
+      e = launch_sim_state(t, q, B, M, prec == REDO_FP64 ? REDO_FP64 : REDO_FP32,
+                           (const double2*)psi0, psi0_batched, obs_diag, expect, dev_status, s);
+    }
     if (e != cudaSuccess) return cuda_error(e, "state simulation");
   }
   if (U_final)

@@ -31,7 +31,8 @@ template <typename R> __device__ __forceinline__ void cfma(cplx<R>& acc, cplx<R>
 // Table handle
 // ----------------------------------------------------------------------------
 constexpr int kMaxK = 64;
-constexpr int kMaxN = 64;
+constexpr int kMaxN = 1024;     // N > 64 takes the global-memory (large-N) path
+constexpr int kSmallN = 64;
 
 
 }  // namespace redo
@@ -139,6 +140,26 @@ cudaError_t mlp_backward(int L, const int32_t* sizes, const float* params, const
                          double* loss, float* work, cudaStream_t s);
 cudaError_t mlp_adam(int64_t count, float* p, const float* g, float* m, float* v, int step, float lr,
                      float b1, float b2, float eps, cudaStream_t s);
+
+// Large-N path (kernels_large.cu), 64 < N <= 1024.
+}  // namespace redo
+#include <vector>
+namespace redo {
+cudaError_t large_table_build(redo_table* t, const double2* H0, const double2* Hk,
+                              const std::vector<double>& hnorm1, double h0norm1, cudaStream_t s);
+ChainPlan plan_chain_large(const redo_table* t, int64_t B, int64_t M);
+size_t large_prop_workspace(const redo_table* t, const ChainPlan& p, int prec, bool reunit);
+cudaError_t large_propagate(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
+                            bool reunit, void* ws, void** result, int* result_prec,
+                            int64_t* status, cudaStream_t s);
+size_t large_grad_workspace(const redo_table* t, const ChainPlan& p, int prec);
+cudaError_t large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
+                       const double2* UT, int tb, double* F_out, double* grad, void* ws,
+                       int64_t* status, cudaStream_t s);
+size_t large_sim_workspace(const redo_table* t, int64_t B);
+cudaError_t large_sim(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
+                      const double2* psi0, int pb, const double* obs, double* expect, void* ws,
+                      cudaStream_t s);
 
 cudaError_t launch_finalize(const redo_table* t, int64_t B, int prec, const void* prod,
                             void* U_out, const double2* U_target, double* F_out, double2* tau_out,

@@ -1,0 +1,95 @@
+"""Large-N path (N = 128 ... 1024): table, propagation, gradient and simulation
+against the oracle on reduced control sets (the oracle's Pade table is the slow part)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import redo_oracle as O
+from paper_1707_02162_gb300 import inputs
+from tests import _ref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_02162_gb300 import build
+    build.build()
+
+
+def _reduced(idx, n, K, B, M, base=64, digits=2):
+    w = inputs.config(idx, n_qubits=n, B=B, M=M, base=base, digits=digits)
+    w.Hk = w.Hk[:K].copy()
+    w.lo, w.hi = w.lo[:K].copy(), w.hi[:K].copy()
+    w.u = w.u[:, :, :K].copy()
+    return w
+
+
+def _table(w):
+    from paper_1707_02162_gb300 import redo
+    return redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+
+
+def test_large_table_matches_oracle_n7():
+    w = _reduced(2, 7, 2, 1, 4)                       # N=128, K=2, b=64, d=2
+    t = _table(w)
+    T, D = t.operators()
+    To, Do = _ref.oracle_table(w)
+    assert np.abs(D.cpu().numpy() - Do).max() < 1e-14
+    assert np.abs(T.cpu().numpy() - _ref.folded(To, Do)).max() < 1e-13
+
+
+@pytest.mark.parametrize("prec,tol,reunit", [("fp64", 1e-12, 0), ("fp32", 2e-4, 0), ("fp32", 2e-4, 8),
+                                             ("fp64", 1e-12, 8)])
+def test_large_propagate_matches_oracle_n7(prec, tol, reunit):
+    w = _reduced(2, 7, 2, 3, 21)                      # ragged against 8-step segments
+    t = _table(w)
+    q = t.quantize(w.u)
+    U, F, _ = t.propagate(q, prec, target=w.target, reunit_every=reunit)
+    To, Do = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    Uo = _ref.oracle_propagators(w, To, Do, dig, range(w.B))
+    assert np.abs(U.cpu().numpy() - Uo).max() < tol
+    Fo = np.array([O.fidelity(w.target, Uo[b]) for b in range(w.B)])
+    assert np.abs(F.cpu().numpy() - Fo).max() < 1e-6
+
+
+def test_large_propagate_n8_other_base():
+    w = _reduced(2, 8, 1, 2, 30, base=16, digits=2)   # N=256, 256 levels
+    t = _table(w)
+    q = t.quantize(w.u)
+    U, F, _ = t.propagate(q, "fp64", target=w.target)
+    To, Do = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    Uo = _ref.oracle_propagators(w, To, Do, dig, range(w.B))
+    assert np.abs(U.cpu().numpy() - Uo).max() < 1e-12
+
+
+@pytest.mark.parametrize("prec,tol,ck", [("fp64", 1e-10, 0), ("fp64", 1e-10, 4), ("fp32", 2e-4, 0)])
+def test_large_gradient_matches_oracle_n7(prec, tol, ck):
+    w = _reduced(2, 7, 2, 2, 9)
+    t = _table(w)
+    q = t.quantize(w.u)
+    F, g = t.fidelity_grad(q, w.target, prec, checkpoint_every=ck)
+    To, Do = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    for b in range(w.B):
+        Fo, go = O.grape_gradient(To, Do, w.Hk, w.dt, dig[b], w.target)
+        assert np.abs(g.cpu().numpy()[b] - go).max() <= tol * np.abs(go).max()
+        assert abs(F.cpu().numpy()[b] - Fo) < 1e-10
+
+
+@pytest.mark.parametrize("n,M", [(7, 40), (9, 12)])
+def test_large_simulate_matches_oracle(n, M):
+    w = inputs.config(3, n_qubits=n, B=2, M=M, base=16, digits=2)   # N=128 / 512, K=1
+    t = _table(w)
+    q = t.quantize(w.u)
+    ex, U = t.simulate(q, w.psi0, w.obs_diag, "fp64")
+    To, Do = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    for b in range(w.B):
+        eo, Uo = O.simulate_expectation(To, Do, dig[b], w.psi0, w.obs_diag)
+        assert np.abs(ex.cpu().numpy()[b] - eo).max() < 1e-12
+        assert np.abs(U.cpu().numpy()[b] - Uo).max() < 1e-12
