@@ -169,7 +169,8 @@ def run_gpu(args):
         w.u = np.random.default_rng(1 + 7919 * rank).uniform(w.lo[0], w.hi[0], size=w.u.shape)
     dev = torch.device("cuda", local)
     table = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True,
-                       fp16x3=(MAIN_PREC == "fp16x3"))
+                       fp16x3=(MAIN_PREC == "fp16x3"), levels=args.levels)
+    prods_per_step = w.K * (1 if args.levels else w.digits)
     u_host = torch.from_numpy(w.u).pin_memory()
     u_dev = u_host.to(dev)
     target = torch.as_tensor(w.target, device=dev)
@@ -233,7 +234,7 @@ def run_gpu(args):
         dom_ms, dom_n, dom_name = tc_ms, tc_n, "chain_tc"
     else:
         dom_ms, dom_n, dom_name = seg_ms, seg_n, "chain_segments"
-    flops_per_launch = B * M * w.K * w.digits * 8.0 * N ** 3        # algorithmic: K*d complex products / step
+    flops_per_launch = B * M * prods_per_step * 8.0 * N ** 3       # algorithmic: complex products per step
     avg_s = (dom_ms / max(dom_n, 1)) / 1e3
     achieved_tf = flops_per_launch / avg_s / 1e12
     if MAIN_PREC == "fp16x3":
@@ -252,7 +253,8 @@ def run_gpu(args):
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom_name
     roof["traffic"] = None
-    roof["algorithmic_per_launch"] = f"{flops_per_launch:.4g} flop (B*M*K*d complex {N}x{N} products, 8N^3 each)"
+    roof["algorithmic_per_launch"] = (f"{flops_per_launch:.4g} flop (B*M*{prods_per_step} complex {N}x{N} "
+                                      f"products, 8N^3 each)")
 
     # ---- FP64 plain REDO on the same GPU (subset of pulses, same steps)
     fp64 = None
@@ -309,6 +311,8 @@ def run_gpu(args):
            "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "fp16x3": "f16x3 (f32 accumulate)"}[MAIN_PREC],
            "data": "synthetic (seeded NMR-like Hamiltonian, uniform random controls, Haar target)",
            "config": _workload_config({"precision": MAIN_PREC, "B": B, "M": M, "reunit_every": reunit_main,
+                                       "table": ("level table (process 3): K products per step" if args.levels
+                                                 else "digit table: K*d products per step"),
                                        "l2": "flushed between timed steps (256 MB write outside the events)"}),
            "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
@@ -355,12 +359,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--B", type=int, default=B_FULL, help="pulses (smaller only for profiling captures)")
     ap.add_argument("--M", type=int, default=M_FULL, help="steps per pulse (smaller only for profiling captures)")
+    ap.add_argument("--digit-table", action="store_true",
+                    help="multiply digit operators every step instead of using the level table "
+                         "(process 3: every level's operator evaluated once, the default)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    args.levels = not args.digit_table
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -98,6 +98,13 @@ typedef struct redo_table redo_table;
  *  flags    REDO_TABLE_FP32 also builds the FP32 copy used by REDO_FP32;
  *           REDO_TABLE_FP16X3 also builds the split-FP16 operand planes used
  *           by REDO_FP16X3 (N = 64 only).  The FP64 copy is always built.
+ *           REDO_TABLE_LEVELS applies process 3 of Section II to every level:
+ *           after the digit table is built, each level's operator
+ *           E[k][q] = T[k][d-1][c_{d-1}] ... T[k][0][c_0] is evaluated once and
+ *           stored, and the table then holds K x levels operators (reported by
+ *           redo_table_info as base = levels, digits = 1), so a time step costs
+ *           K products instead of K*digits.  N <= 64; K * levels * N^2 * 16
+ *           bytes must stay below 64 GiB.
  *  stream   stream for the build; synchronised before returning.
  *  out      receives the handle; free with redo_table_free.
  * Errors: REDO_ERR_INVALID, REDO_ERR_NOT_HERMITIAN (relative tolerance 1e-12
@@ -105,6 +112,7 @@ typedef struct redo_table redo_table;
  */
 #define REDO_TABLE_FP32 0x1u
 #define REDO_TABLE_FP16X3 0x2u
+#define REDO_TABLE_LEVELS 0x4u
 redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, const void* Hk,
                              const double* lo, const double* hi, int32_t base, int32_t digits,
                              uint32_t flags, void* stream, redo_table** out);

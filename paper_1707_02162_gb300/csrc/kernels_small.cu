@@ -234,6 +234,63 @@ table_fold_kernel(double2* __restrict__ T, const double2* __restrict__ D) {
   for (int i = threadIdx.x; i < N2; i += MM::THREADS) Tc[i] = A[i];
 }
 
+// Process 3 of Section II: the operator of every level q, evaluated once as the
+// product of its digit operators, E[k][q] = T[k][d-1][c_{d-1}] ... T[k][0][c_0].
+template <int N>
+__global__ void __launch_bounds__(SmemMM<double, N, SqTile<N>::TM, SqTile<N>::TM>::THREADS)
+table_expand_kernel(const double2* __restrict__ T, int d, int base, int64_t levels,
+                    double2* __restrict__ E) {
+  constexpr int TM = SqTile<N>::TM;
+  using MM = SmemMM<double, N, TM, TM>;
+  constexpr int N2 = N * N;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* X = A + N2;
+  const int64_t e = blockIdx.x;
+  const int64_t k = e / levels, q = e % levels;
+  const int lt = threadIdx.x;
+  int64_t qq = q;
+  const double2* T0 = T + ((k * d + 0) * base + qq % base) * N2;
+  for (int i = lt; i < N2; i += MM::THREADS) X[i] = T0[i];
+  double2 Y[TM][TM];
+  for (int j = 1; j < d; ++j) {
+    qq /= base;
+    const double2* Tj = T + ((k * d + j) * base + qq % base) * N2;
+    __syncthreads();
+    for (int i = lt; i < N2; i += MM::THREADS) A[i] = Tj[i];
+    __syncthreads();
+    MM::run(A, X, lt, Y);
+    __syncthreads();
+    MM::store(X, lt, Y);
+  }
+  __syncthreads();
+  for (int i = lt; i < N2; i += MM::THREADS) E[e * N2 + i] = X[i];
+}
+
+template <int N>
+static cudaError_t table_expand_n(const double2* T, int K, int d, int base, int64_t levels,
+                                  double2* E, cudaStream_t s) {
+  using MM = SmemMM<double, N, SqTile<N>::TM, SqTile<N>::TM>;
+  const size_t smem = 2 * sizeof(double2) * N * N;
+  cudaError_t e = cudaFuncSetAttribute(table_expand_kernel<N>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  table_expand_kernel<N><<<(unsigned)((int64_t)K * levels), MM::THREADS, smem, s>>>(T, d, base, levels, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table_expand(const redo_table* t, double2* E, cudaStream_t s) {
+  switch (t->N) {
+    case 2: return table_expand_n<2>(t->T64, t->K, t->digits, t->base, t->levels, E, s);
+    case 4: return table_expand_n<4>(t->T64, t->K, t->digits, t->base, t->levels, E, s);
+    case 8: return table_expand_n<8>(t->T64, t->K, t->digits, t->base, t->levels, E, s);
+    case 16: return table_expand_n<16>(t->T64, t->K, t->digits, t->base, t->levels, E, s);
+    case 32: return table_expand_n<32>(t->T64, t->K, t->digits, t->base, t->levels, E, s);
+    case 64: return table_expand_n<64>(t->T64, t->K, t->digits, t->base, t->levels, E, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int N>
 static cudaError_t table_expm_n(const redo_table* t, const double2* H0, const double2* Hk,
                                 cudaStream_t s) {

@@ -120,6 +120,11 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
       return set_error(REDO_ERR_INVALID, "term %d: need finite lo < hi", k);
   if ((flags & REDO_TABLE_FP16X3) && N != 64)
     return set_error(REDO_ERR_UNSUPPORTED, "REDO_TABLE_FP16X3 needs N = 64");
+  if ((flags & REDO_TABLE_LEVELS) && N > kSmallN)
+    return set_error(REDO_ERR_UNSUPPORTED, "REDO_TABLE_LEVELS needs N <= 64");
+  if ((flags & REDO_TABLE_LEVELS) &&
+      (double)K * lv * (double)N * N * 16.0 > 64.0 * 1024 * 1024 * 1024)
+    return set_error(REDO_ERR_INVALID, "level table above 64 GiB (K * levels * N^2 * 16 bytes)");
   cudaStream_t s = (cudaStream_t)stream;
 
   // Hermitian check on the host (one synchronous copy, build time only)
@@ -144,6 +149,8 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
   t->K = K;
   t->base = base;
   t->digits = digits;
+  t->digit_base = base;
+  t->digit_count = digits;
   t->levels = (int64_t)lv;
   t->entries = (int64_t)K * digits * base;
   t->dt = dt;
@@ -225,6 +232,28 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
     }
     if ((e = large_table_build(t, (const double2*)H0, (const double2*)Hk, hn, h0n, s)) != cudaSuccess)
       return fail(cuda_error(e, "large-N table"));
+  }
+  if (flags & REDO_TABLE_LEVELS) {
+    // process 3: evaluate each level's operator once as the product of its digit operators
+    double2* E = nullptr;
+    const int64_t ne = (int64_t)K * t->levels;
+    if ((e = cudaMalloc(&E, sizeof(double2) * n2 * ne)) != cudaSuccess)
+      return fail(set_error(REDO_ERR_OOM, "level table allocation: %s", cudaGetErrorString(e)));
+    if ((e = launch_table_expand(t, E, s)) != cudaSuccess || (e = cudaStreamSynchronize(s))) {
+      cudaFree(E);
+      return fail(cuda_error(e, "level table"));
+    }
+    cudaFree(t->T64);
+    t->T64 = E;
+    t->entries = ne;
+    t->base = (int32_t)t->levels;
+    t->digits = 1;
+    if (t->T32) {
+      cudaFree(t->T32);
+      t->T32 = nullptr;
+      if ((e = cudaMalloc(&t->T32, sizeof(float2) * n2 * ne)) != cudaSuccess)
+        return fail(set_error(REDO_ERR_OOM, "FP32 level table allocation: %s", cudaGetErrorString(e)));
+    }
   }
   if (t->T32 && (e = launch_to_fp32(t->T64, t->T32, (int64_t)n2 * t->entries, s)) != cudaSuccess)
     return fail(cuda_error(e, "FP32 copy"));

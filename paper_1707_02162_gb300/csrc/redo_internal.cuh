@@ -38,7 +38,8 @@ constexpr int kSmallN = 64;
 }  // namespace redo
 
 struct redo_table {
-  int32_t N, K, base, digits;
+  int32_t N, K, base, digits;      // as stored: a level table has base = levels, digits = 1
+  int32_t digit_base, digit_count; // the digit decomposition the operators were built from
   int64_t levels;
   int64_t entries;            // K * digits * base
   double dt;
@@ -85,6 +86,8 @@ cudaError_t launch_table_expm(const redo_table* t, const double2* H0, const doub
                               cudaStream_t s);
 cudaError_t launch_table_fold_drift(const redo_table* t, cudaStream_t s);
 cudaError_t launch_to_fp32(const double2* src, float2* dst, int64_t count, cudaStream_t s);
+// Level operators E[k][q] (process 3) from the digit table; E has K*levels entries.
+cudaError_t launch_table_expand(const redo_table* t, double2* E, cudaStream_t s);
 
 // Segmented chain products for N <= 64 (SIMT, FP64 or FP32).
 struct ChainPlan {

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libredo.so")
 REDO_OK = 0
 REDO_FP64, REDO_FP32, REDO_FP16X3 = 0, 1, 4
 PRECISIONS = {"fp64": REDO_FP64, "fp32": REDO_FP32, "fp16x3": REDO_FP16X3}
-REDO_TABLE_FP32, REDO_TABLE_FP16X3 = 0x1, 0x2
+REDO_TABLE_FP32, REDO_TABLE_FP16X3, REDO_TABLE_LEVELS = 0x1, 0x2, 0x4
 STATUS_WORDS = 4
 STATUS_NONFINITE, STATUS_SATURATED, STATUS_TIMEOUT, STATUS_BADINDEX = range(4)
 
@@ -264,10 +264,12 @@ def redo_profile_read() -> dict:
 class Table:
     """Owning wrapper of a redo_table built from torch tensors on the current device."""
 
-    def __init__(self, H0, Hk, dt, lo, hi, base=64, digits=2, fp32=True, fp16x3=False, device="cuda"):
+    def __init__(self, H0, Hk, dt, lo, hi, base=64, digits=2, fp32=True, fp16x3=False, levels=False,
+                 device="cuda"):
         H0 = torch.as_tensor(H0, dtype=torch.complex128, device=device).contiguous()
         Hk = torch.as_tensor(Hk, dtype=torch.complex128, device=device).contiguous()
-        flags = (REDO_TABLE_FP32 if fp32 else 0) | (REDO_TABLE_FP16X3 if fp16x3 else 0)
+        flags = ((REDO_TABLE_FP32 if fp32 else 0) | (REDO_TABLE_FP16X3 if fp16x3 else 0)
+                 | (REDO_TABLE_LEVELS if levels else 0))
         self.handle = redo_build_table(H0, Hk, dt, lo, hi, base, digits, flags)
         self.info = redo_table_info(self.handle)
         self.N, self.K = self.info["N"], self.info["K"]

@@ -226,3 +226,28 @@ def test_propagate_full_size_batched_sampled_fp64_fp32():
         assert ((Fg >= 0) & (Fg <= 1 + 1e-9)).all()
         for i, b in enumerate(pulses):
             assert abs(Fg[b] - O.fidelity(w.target, Uo[i])) < F_TOL
+
+
+def test_level_table_operators_are_digit_products():
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(0, B=2, M=50)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, levels=True)
+    E, D = t.operators()                     # [K][1][levels][N][N]
+    To, Do = _ref.oracle_table(w)
+    Tf = _ref.folded(To, Do)
+    Eg = E.cpu().numpy()
+    rng = np.random.default_rng(3)
+    for qv in list(rng.integers(0, w.levels, size=30)) + [0, w.levels - 1]:
+        c = O.level_digits(np.array([qv]), w.base, w.digits)[0]
+        for k in range(w.K):
+            assert np.abs(Eg[k, 0, qv] - Tf[k, 1, c[1]] @ Tf[k, 0, c[0]]).max() < 1e-14
+    q = t.quantize(w.u)
+    for prec, tol in (("fp64", FP64_TOL), ("fp32", FP32_TOL)):
+        U, F, _ = t.propagate(q, prec, target=w.target)
+        _, dig, _, _ = _ref.oracle_levels(w)
+        Uo = _ref.oracle_propagators(w, To, Do, dig, range(w.B))
+        assert np.abs(U.cpu().numpy() - Uo).max() < tol
+    # the gradient works on a level table too
+    Fg, g = t.fidelity_grad(q, w.target, "fp64")
+    Fo, go = O.grape_gradient(To, Do, w.Hk, w.dt, O.level_digits(q.cpu().numpy(), w.base, w.digits)[0], w.target)
+    assert np.abs(g.cpu().numpy()[0] - go).max() <= 1e-10 * np.abs(go).max()

@@ -110,3 +110,20 @@ def test_tc_requires_planes():
     q = t.quantize(w.u)
     with pytest.raises(redo.RedoError):
         t.propagate(q, "fp16x3")
+
+
+def test_tc_level_table_matches_oracle():
+    # process 3: every level's operator evaluated once; a step costs K products
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(1, B=4, M=120)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True, levels=True)
+    assert t.info["digits"] == 1 and t.info["base"] == w.levels and t.info["entries"] == w.K * w.levels
+    q = t.quantize(w.u)
+    U, F, _ = t.propagate(q, "fp16x3", target=w.target, reunit_every=64)
+    U64, F64, _ = t.propagate(q, "fp64", target=w.target)
+    T, D = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    Uo = _ref.oracle_propagators(w, T, D, dig, range(w.B))
+    assert np.abs(U64.cpu().numpy() - Uo).max() < 1e-12
+    assert np.abs(U.cpu().numpy() - Uo).max() < TC_TOL
+    assert (F - F64).abs().max().item() < F_TOL
