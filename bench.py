@@ -351,12 +351,153 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------------------- other workloads
+# One JSON line each; the driver's default run is the batched-propagation line above.
+
+def _events_time(fn, reps):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_workload(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1707_02162_gb300 import build as _b
+    _b.build()
+    from paper_1707_02162_gb300 import inputs, redo
+    out = {"workload": args.workload, "n_gpus": 1, "data": "synthetic"}
+    if args.workload == "grape":
+        # 8 qubits (N=256), K=16, M=1000, dt=2 us, Haar target; forward checkpoints every 32 steps
+        w = inputs.config(2)
+        t0 = time.time()
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+        build_s = time.time() - t0
+        u = torch.tensor(w.u, device="cuda")
+        target = torch.as_tensor(w.target, device="cuda")
+        q = torch.empty(u.shape, dtype=torch.int32, device="cuda")
+        F = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = torch.empty(u.shape, dtype=torch.float64, device="cuda")
+        res = {}
+        for prec, reps in (("fp32", args.steps), ("fp64", 1)):
+            ws = torch.empty(redo.redo_fidelity_grad_workspace(t.handle, 1, w.M, prec, 32), dtype=torch.uint8,
+                             device="cuda")
+
+            def it():
+                redo.redo_quantize(t.handle, u, q)
+                redo.redo_fidelity_grad(t.handle, q, target, prec, 32, F, g, ws)
+                redo.redo_grape_step(t.handle, u, g, 1e9)
+            it()
+            ms = _events_time(it, reps)
+            res[prec] = {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "timed_iterations": reps}
+        flop = 3 * w.M * w.K * w.digits * 8.0 * w.N ** 3
+        out.update({"metric": "GRAPE iters/s", "unit": "iterations/s", "value": res["fp32"]["iters_per_s"],
+                    "precision": "fp32 (SIMT, large-N lockstep GEMMs)", "fp64_plain_redo": res["fp64"],
+                    "speedup_vs_fp64": res["fp32"]["iters_per_s"] / res["fp64"]["iters_per_s"],
+                    "algorithmic_flop_per_iter": flop,
+                    "achieved_tflops_fp32": flop / (res["fp32"]["ms_per_iter"] / 1e3) / 1e12,
+                    "table_build_s": build_s,
+                    "config": {"N": w.N, "K": w.K, "M": w.M, "dt": w.dt, "checkpoint_every": 32, "B": 1}})
+    elif args.workload == "sim":
+        # 10-qubit ZZ chain (N=1024), global X drive with OU noise, 64 realisations; M_sample steps timed
+        Ms = args.M if args.M != M_FULL else 40
+        w = inputs.config(3, M=Ms)
+        t0 = time.time()
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+        build_s = time.time() - t0
+        q = t.quantize(w.u)
+        psi0 = torch.as_tensor(w.psi0, device="cuda")
+        obs = torch.as_tensor(w.obs_diag, device="cuda")
+        ex = torch.empty((w.B, Ms + 1), dtype=torch.float64, device="cuda")
+        Uf = torch.empty((w.B, w.N, w.N), dtype=torch.complex128, device="cuda")
+        res = {}
+        for prec, want in (("fp32", False), ("fp32", True), ("fp64", False)):
+            nb = redo.redo_simulate_workspace(t.handle, w.B, Ms, prec, 0, want)
+            ws = torch.empty(max(nb, 256), dtype=torch.uint8, device="cuda")
+
+            def it():
+                redo.redo_simulate(t.handle, q, prec, 0, psi0, obs, ex, Uf if want else None, ws)
+            it()
+            ms = _events_time(it, 1)
+            res[f"{prec}{'_with_U' if want else '_state_only'}"] = {
+                "realisation_steps_per_s": w.B * Ms / (ms / 1e3), "ms": ms}
+        out.update({"metric": "REDO prop steps/s (noisy-drive ensemble)", "unit": "realisation-steps/s",
+                    "value": res["fp32_with_U"]["realisation_steps_per_s"], "results": res,
+                    "sample": f"{Ms} of the 2000 steps, all 64 realisations", "table_build_s": build_s,
+                    "config": {"N": w.N, "K": w.K, "B": w.B, "M_timed": Ms}})
+    elif args.workload == "plain":
+        # 3 qubits (N=8), M=1000: latency of one pulse and throughput of 4096 replicas
+        res = {}
+        for B in (1, 4096):
+            w = inputs.config(0, B=B)
+            t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+            u = torch.tensor(w.u, device="cuda")
+            target = torch.as_tensor(w.target, device="cuda")
+            for prec in ("fp64", "fp32"):
+                q = t.quantize(u)
+                U, F, tau = (torch.empty((B, 8, 8), dtype=torch.complex128, device="cuda"),
+                             torch.empty(B, dtype=torch.float64, device="cuda"),
+                             torch.empty(B, dtype=torch.complex128, device="cuda"))
+                ws = t.workspace(B, w.M, prec)
+
+                def it():
+                    redo.redo_quantize(t.handle, u, q)
+                    redo.redo_propagate(t.handle, q, prec, U, target, F, tau, ws)
+                it()
+                ms = _events_time(it, args.steps)
+                res[f"B{B}_{prec}"] = {"ms_per_call": ms, "pulse_steps_per_s": B * w.M / (ms / 1e3)}
+        out.update({"metric": "REDO prop steps/s (plain REDO, N=8)", "unit": "pulse-steps/s",
+                    "value": res["B4096_fp64"]["pulse_steps_per_s"], "results": res})
+    elif args.workload == "warmstart":
+        # 5 qubits (N=32), K=10, M=500: batched GRAPE iterations and MLP training throughput
+        B = 256
+        w = inputs.config(4, B=B)
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+        rng = np.random.default_rng(0)
+        targets = torch.as_tensor(np.stack([inputs.haar_unitary(rng, w.N) for _ in range(B)]), device="cuda")
+        u = torch.tensor(w.u, device="cuda")
+        q = torch.empty(u.shape, dtype=torch.int32, device="cuda")
+        F = torch.empty(B, dtype=torch.float64, device="cuda")
+        g = torch.empty(u.shape, dtype=torch.float64, device="cuda")
+        res = {}
+        for prec in ("fp32", "fp64"):
+            ws = torch.empty(redo.redo_fidelity_grad_workspace(t.handle, B, w.M, prec, 0), dtype=torch.uint8,
+                             device="cuda")
+
+            def it():
+                redo.redo_quantize(t.handle, u, q)
+                redo.redo_fidelity_grad(t.handle, q, targets, prec, 0, F, g, ws)
+                redo.redo_grape_step(t.handle, u, g, 1e9)
+            it()
+            ms = _events_time(it, args.steps if prec == "fp32" else 1)
+            res[prec] = {"instance_iters_per_s": B * 1e3 / ms, "ms_per_batched_iter": ms}
+        from paper_1707_02162_gb300.warmstart import MLP
+        net = MLP([23, 512, 512, 512, w.M * w.K])
+        x = torch.randn(1024, 23)
+        y = torch.rand(1024, w.M * w.K) * 2 - 1
+        net.train_step(x, y, 1e-3)
+        ms = _events_time(lambda: net.train_step(x, y, 1e-3), 5)
+        out.update({"metric": "GRAPE iters/s (batched instances, N=32)", "unit": "instance-iterations/s",
+                    "value": res["fp32"]["instance_iters_per_s"], "results": res,
+                    "mlp_train_samples_per_s": 1024 / (ms / 1e3),
+                    "config": {"N": w.N, "K": w.K, "M": w.M, "instances": B, "mlp": "23-512-512-512-5000"}})
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="prop", choices=["prop", "grape", "sim", "plain", "warmstart"],
+                    help="prop (default): the batched propagation line; others: auxiliary measurements")
     ap.add_argument("--B", type=int, default=B_FULL, help="pulses (smaller only for profiling captures)")
     ap.add_argument("--M", type=int, default=M_FULL, help="steps per pulse (smaller only for profiling captures)")
     ap.add_argument("--digit-table", action="store_true",
@@ -371,6 +512,8 @@ def main():
     args.levels = not args.digit_table
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "prop":
+        run_workload(args)
     else:
         run_gpu(args)
 

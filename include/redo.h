@@ -88,7 +88,8 @@ typedef struct redo_table redo_table;
  * folded into the digit-0 operators of term 0 (T[0][0][c] <- T[0][0][c] D).
  * Exponentials are FP64 scaling-and-squaring Taylor series on the GPU.
  *
- *  N        Hilbert-space dimension, 2 <= N <= 64.
+ *  N        Hilbert-space dimension, a power of two, 2 <= N <= 1024 (N > 64 uses
+ *           the global-memory path: batched GEMMs, one launch per chain step).
  *  K        number of control terms, 1 <= K <= 64.
  *  dt       time step in seconds (> 0).
  *  H0       device, complex128 [N][N], Hermitian drift (rad/s).
@@ -97,7 +98,8 @@ typedef struct redo_table redo_table;
  *  base     digit base b >= 2;  digits d >= 1;  base^digits <= 2^24 levels.
  *  flags    REDO_TABLE_FP32 also builds the FP32 copy used by REDO_FP32;
  *           REDO_TABLE_FP16X3 also builds the split-FP16 operand planes used
- *           by REDO_FP16X3 (N = 64 only).  The FP64 copy is always built.
+ *           by REDO_FP16X3 (N = 64, or 128 <= N <= 1024 where two plane sets,
+ *           for left and right products, are stored).  The FP64 copy is always built.
  *           REDO_TABLE_LEVELS applies process 3 of Section II to every level:
  *           after the digit table is built, each level's operator
  *           E[k][q] = T[k][d-1][c_{d-1}] ... T[k][0][c_0] is evaluated once and
@@ -230,7 +232,8 @@ redo_status redo_propagate_noalloc(const redo_table* t, const int32_t* q, int64_
  *
  *  q, B, M       as for redo_propagate.
  *  U_target      device complex128 [N][N], or [B][N][N] if target_batched != 0.
- *  prec          REDO_FP64 or REDO_FP32 (products; traces and tau in FP64).
+ *  prec          REDO_FP64 or REDO_FP32, or REDO_FP16X3 for N >= 128 (products;
+ *                traces and tau in FP64).
  *  checkpoint_every  C > 0: forward checkpoints every C steps; 0: automatic.
  *  F_out         device double [B] or NULL;  grad  device double [B][M][K].
  *  workspace     >= redo_fidelity_grad_workspace() bytes, 256-byte aligned.

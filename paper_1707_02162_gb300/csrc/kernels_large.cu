@@ -533,10 +533,11 @@ size_t large_prop_workspace(const redo_table* t, const ChainPlan& p, int prec, b
          (reunit ? up(p.B * n2 * sizeof(double2)) + up(2 * p.B * n2 * sizeof(double2)) : 0);
 }
 
+// After the segment products sit in the first region of the workspace: optional FP32/FP64
+// re-unitarisation of segments, ordered combine, optional FP64 polar step of pulse products.
 template <typename R>
-static cudaError_t large_propagate_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
-                                     bool reunit, char* ws, void** result, int* result_prec,
-                                     int64_t* status, cudaStream_t s) {
+static cudaError_t large_finish_t(const redo_table* t, const ChainPlan& p, bool reunit, char* ws,
+                                  void** result, int* result_prec, cudaStream_t s) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int N = t->N;
   const size_t n2 = (size_t)N * N, G = (size_t)p.B * p.S;
@@ -545,8 +546,7 @@ static cudaError_t large_propagate_t(const redo_table* t, const int32_t* q, cons
   cplx<R>* prod = (cplx<R>*)((char*)ping + up(G * n2 * sizeof(cplx<R>)));
   cplx<R>* nsbuf = (cplx<R>*)((char*)prod + up(p.B * n2 * sizeof(cplx<R>)));
   char* tail = (char*)nsbuf + up(2 * G * n2 * sizeof(cplx<R>));
-  cudaError_t e = large_chain_t<R>(t, q, p, seg, ping, status, s);
-  if (e) return e;
+  cudaError_t e = cudaSuccess;
   if (reunit && p.M > 0 && (e = large_polar_t<R>(N, seg, G, nsbuf, s))) return e;
   if ((e = large_combine_t<R>(N, p, seg, prod, ping, s))) return e;
   *result = prod;
@@ -560,6 +560,24 @@ static cudaError_t large_propagate_t(const redo_table* t, const int32_t* q, cons
     *result_prec = REDO_FP64;
   }
   return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t large_propagate_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
+                                     bool reunit, char* ws, void** result, int* result_prec,
+                                     int64_t* status, cudaStream_t s) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t n2 = (size_t)t->N * t->N, G = (size_t)p.B * p.S;
+  cplx<R>* seg = (cplx<R>*)ws;
+  cplx<R>* ping = (cplx<R>*)(ws + up(G * n2 * sizeof(cplx<R>)));
+  cudaError_t e = large_chain_t<R>(t, q, p, seg, ping, status, s);
+  if (e) return e;
+  return large_finish_t<R>(t, p, reunit, ws, result, result_prec, s);
+}
+
+cudaError_t large_finish_fp32(const redo_table* t, const ChainPlan& p, bool reunit, void* ws,
+                              void** result, int* result_prec, cudaStream_t s) {
+  return large_finish_t<float>(t, p, reunit, (char*)ws, result, result_prec, s);
 }
 
 cudaError_t large_propagate(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
@@ -716,10 +734,12 @@ size_t large_grad_workspace(const redo_table* t, const ChainPlan& p, int prec) {
   return 5 * up(G * n2 * el) + 2 * up(p.B * n2 * el) + up(p.B * sizeof(double2));
 }
 
+// Prefix checkpoints, tau/F and suffix costates from the segment products in the first
+// workspace region.
 template <typename R>
-static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
-                                const double2* UT, int tb, double* F_out, double* grad, char* ws,
-                                int64_t* status, cudaStream_t s) {
+static cudaError_t large_scans_t(const redo_table* t, const ChainPlan& p, const double2* UT, int tb,
+                                 double* F_out, char* ws, cplx<R>** Pck_out, cplx<R>** Rck_out,
+                                 double2** tau_out, cudaStream_t s) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int N = t->N;
   const int64_t n2 = (int64_t)N * N, G = p.B * p.S;
@@ -727,14 +747,10 @@ static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const Cha
   cplx<R>* seg = (cplx<R>*)ws;
   cplx<R>* Pck = (cplx<R>*)(ws + mat);
   cplx<R>* Rck = (cplx<R>*)(ws + 2 * mat);
-  cplx<R>* pA = (cplx<R>*)(ws + 3 * mat);
-  cplx<R>* pB = (cplx<R>*)(ws + 4 * mat);
   cplx<R>* run = (cplx<R>*)(ws + 5 * mat);
   cplx<R>* run2 = (cplx<R>*)(ws + 5 * mat + up(p.B * n2 * sizeof(cplx<R>)));
   double2* tau = (double2*)(ws + 5 * mat + 2 * up(p.B * n2 * sizeof(cplx<R>)));
-  cudaError_t e = large_chain_t<R>(t, q, p, seg, pA, status, s);
-  if (e) return e;
-  // prefix checkpoints Pck[u][s] = S_s ... S_0 and tau from the last
+  cudaError_t e;
   if ((e = set_identity<R>(run, p.B, N, s))) return e;
   for (int64_t ss = 0; ss < p.S; ++ss) {
     ListStepOps<R> op{seg, p.S, ss, false, run, run2, n2};
@@ -744,7 +760,6 @@ static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const Cha
     if ((e = cgemm<R, false>(cp, p.B, N, R(1), R(0), s))) return e;
   }
   tau_kernel<R><<<(unsigned)p.B, 256, 0, s>>>(run, UT, tb, N, tau, F_out);
-  // suffix costates Rck[u][s] = U_T^dag S_{S-1} ... S_{s+1}
   adjoint_target_kernel<R><<<blocks_for(p.B * n2), 256, 0, s>>>(UT, tb, N, p.B, run);
   for (int64_t ss = p.S - 1; ss >= 0; --ss) {
     DenseOps<R> cp{nullptr, run, Rck + ss * n2, 0, n2, p.S * n2};
@@ -754,6 +769,35 @@ static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const Cha
     if ((e = cgemm<R, false>(op, p.B, N, R(1), R(0), s))) return e;
     std::swap(run, run2);
   }
+  *Pck_out = Pck;
+  *Rck_out = Rck;
+  *tau_out = tau;
+  return cudaGetLastError();
+}
+
+cudaError_t large_grad_scans_fp32(const redo_table* t, const ChainPlan& p, const double2* UT, int tb,
+                                  double* F_out, void* ws, float2** Pck, float2** Rck, double2** tau,
+                                  cudaStream_t s) {
+  return large_scans_t<float>(t, p, UT, tb, F_out, (char*)ws, Pck, Rck, tau, s);
+}
+
+template <typename R>
+static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
+                                const double2* UT, int tb, double* F_out, double* grad, char* ws,
+                                int64_t* status, cudaStream_t s) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int N = t->N;
+  const int64_t n2 = (int64_t)N * N, G = p.B * p.S;
+  const size_t mat = up((size_t)G * n2 * sizeof(cplx<R>));
+  cplx<R>* seg = (cplx<R>*)ws;
+  cplx<R>* pA = (cplx<R>*)(ws + 3 * mat);
+  cplx<R>* pB = (cplx<R>*)(ws + 4 * mat);
+  cudaError_t e = large_chain_t<R>(t, q, p, seg, pA, status, s);
+  if (e) return e;
+  cplx<R>* Pck;
+  cplx<R>* Rck;
+  double2* tau;
+  if ((e = large_scans_t<R>(t, p, UT, tb, F_out, ws, &Pck, &Rck, &tau, s))) return e;
   if (p.M == 0) return cudaGetLastError();
   // reverse sweep: traces, then P <- A^dag P, R <- R A
   GatherStepOps<R> left{}, right{};

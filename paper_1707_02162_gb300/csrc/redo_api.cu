@@ -118,8 +118,8 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
   for (int k = 0; k < K; ++k)
     if (!(hi[k] > lo[k]) || !std::isfinite(lo[k]) || !std::isfinite(hi[k]))
       return set_error(REDO_ERR_INVALID, "term %d: need finite lo < hi", k);
-  if ((flags & REDO_TABLE_FP16X3) && N != 64)
-    return set_error(REDO_ERR_UNSUPPORTED, "REDO_TABLE_FP16X3 needs N = 64");
+  if ((flags & REDO_TABLE_FP16X3) && N != 64 && N < 128)
+    return set_error(REDO_ERR_UNSUPPORTED, "REDO_TABLE_FP16X3 needs N = 64 or N >= 128");
   if ((flags & REDO_TABLE_LEVELS) && N > kSmallN)
     return set_error(REDO_ERR_UNSUPPORTED, "REDO_TABLE_LEVELS needs N <= 64");
   if ((flags & REDO_TABLE_LEVELS) &&
@@ -258,11 +258,11 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
   if (t->T32 && (e = launch_to_fp32(t->T64, t->T32, (int64_t)n2 * t->entries, s)) != cudaSuccess)
     return fail(cuda_error(e, "FP32 copy"));
   if (flags & REDO_TABLE_FP16X3) {
-    t->tc_bytes = tc_planes_bytes(t);
+    t->tc_bytes = N > kSmallN ? tc_large_planes_bytes(t) : tc_planes_bytes(t);
     if ((e = cudaMalloc(&t->tc_planes, t->tc_bytes)) != cudaSuccess)
       return fail(set_error(REDO_ERR_OOM, "FP16x3 planes allocation: %s", cudaGetErrorString(e)));
-    if ((e = launch_build_tc_planes(t, s)) != cudaSuccess)
-      return fail(cuda_error(e, "FP16x3 planes"));
+    e = N > kSmallN ? launch_build_tc_large_planes(t, s) : launch_build_tc_planes(t, s);
+    if (e != cudaSuccess) return fail(cuda_error(e, "FP16x3 planes"));
   }
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_error(e, "table build"));
   *out = t;
@@ -349,10 +349,11 @@ static PropLayout prop_layout(const redo_table* t, int64_t B, int64_t M, redo_pr
                               int32_t reunit_every) {
   PropLayout L;
   if (t->N > kSmallN) {
-    L.eff_prec = prec;
+    L.eff_prec = prec == REDO_FP16X3 ? REDO_FP32 : prec;
     L.p = reunit_every > 0 ? plan_chain_aligned(t, B, M, reunit_every) : plan_chain_large(t, B, M);
     L.seg_off = L.prod_off = L.prod64_off = 0;
-    L.total = large_prop_workspace(t, L.p, prec, reunit_every > 0);
+    L.total = prec == REDO_FP16X3 ? tc_large_prop_workspace(t, L.p, reunit_every > 0)
+                                  : large_prop_workspace(t, L.p, prec, reunit_every > 0);
     return L;
   }
   // the tensor-core path forms segment products in split FP16 and combines them in FP32
@@ -413,9 +414,11 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
     int res_prec = eff;
     {
       ProfScope ps(2, s);
-      if ((e = large_propagate(t, q, p, eff, reunit_every > 0, workspace, &res, &res_prec,
-                               dev_status, s)) != cudaSuccess)
-        return cuda_error(e, "large-N chains");
+      e = prec == REDO_FP16X3
+              ? tc_large_propagate(t, q, p, reunit_every > 0, workspace, &res, &res_prec, dev_status, s)
+              : large_propagate(t, q, p, eff, reunit_every > 0, workspace, &res, &res_prec,
+                                dev_status, s);
+      if (e != cudaSuccess) return cuda_error(e, "large-N chains");
     }
     ProfScope ps(4, s);
     if ((e = launch_finalize(t, B, res_prec, res, U_out, (const double2*)U_target, F_out,
@@ -475,7 +478,7 @@ static GradLayout grad_layout(const redo_table* t, int64_t B, int64_t M, redo_pr
     L.p = checkpoint_every > 0 ? plan_chain_aligned(t, B, M, checkpoint_every)
                                : plan_chain_large(t, B, M);
     L.seg_off = L.pck_off = L.rck_off = L.tau_off = 0;
-    L.total = large_grad_workspace(t, L.p, prec);
+    L.total = prec == REDO_FP16X3 ? tc_large_grad_workspace(t, L.p) : large_grad_workspace(t, L.p, prec);
     return L;
   }
   L.p = checkpoint_every > 0 ? plan_chain_aligned(t, B, M, checkpoint_every)
@@ -496,8 +499,9 @@ redo_status redo_fidelity_grad_workspace(const redo_table* t, int64_t B, int64_t
                                          size_t* bytes) {
   if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
   if (B < 0 || M < 0 || checkpoint_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
-  if (prec != REDO_FP64 && prec != REDO_FP32)
-    return set_error(REDO_ERR_UNSUPPORTED, "the gradient supports REDO_FP64 and REDO_FP32");
+  if (prec != REDO_FP64 && prec != REDO_FP32 && !(prec == REDO_FP16X3 && t->N > kSmallN))
+    return set_error(REDO_ERR_UNSUPPORTED,
+                     "the gradient supports REDO_FP64, REDO_FP32 and, for N >= 128, REDO_FP16X3");
   redo_status st = check_prec(t, prec);
   if (st != REDO_OK) return st;
   if (checkpoint_every > M) checkpoint_every = M > 0 ? (int32_t)M : 0;
@@ -512,8 +516,9 @@ redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B,
                                void* stream) {
   if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
   if (B < 0 || M < 0 || checkpoint_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
-  if (prec != REDO_FP64 && prec != REDO_FP32)
-    return set_error(REDO_ERR_UNSUPPORTED, "the gradient supports REDO_FP64 and REDO_FP32");
+  if (prec != REDO_FP64 && prec != REDO_FP32 && !(prec == REDO_FP16X3 && t->N > kSmallN))
+    return set_error(REDO_ERR_UNSUPPORTED,
+                     "the gradient supports REDO_FP64, REDO_FP32 and, for N >= 128, REDO_FP16X3");
   redo_status st = check_prec(t, prec);
   if (st != REDO_OK) return st;
   if (B == 0) return REDO_OK;
@@ -530,9 +535,12 @@ redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B,
   cudaError_t e;
   ProfScope ps(7, s);
   if (t->N > kSmallN) {
-    if ((e = large_grad(t, q, L.p, prec, (const double2*)U_target, target_batched, F_out, grad,
-                        workspace, dev_status, s)) != cudaSuccess)
-      return cuda_error(e, "large-N gradient");
+    e = prec == REDO_FP16X3
+            ? tc_large_grad(t, q, L.p, (const double2*)U_target, target_batched, F_out, grad,
+                            workspace, dev_status, s)
+            : large_grad(t, q, L.p, prec, (const double2*)U_target, target_batched, F_out, grad,
+                         workspace, dev_status, s);
+    if (e != cudaSuccess) return cuda_error(e, "large-N gradient");
     return REDO_OK;
   }
   if ((e = launch_chain_segments(t, q, L.p, prec, w + L.seg_off, dev_status, s)) != cudaSuccess)

@@ -160,6 +160,22 @@ cudaError_t large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p
                        const double2* UT, int tb, double* F_out, double* grad, void* ws,
                        int64_t* status, cudaStream_t s);
 size_t large_sim_workspace(const redo_table* t, int64_t B);
+cudaError_t large_finish_fp32(const redo_table* t, const ChainPlan& p, bool reunit, void* ws,
+                              void** result, int* result_prec, cudaStream_t s);
+cudaError_t large_grad_scans_fp32(const redo_table* t, const ChainPlan& p, const double2* UT, int tb,
+                                  double* F_out, void* ws, float2** Pck, float2** Rck, double2** tau,
+                                  cudaStream_t s);
+// Tensor-core large-N path (kernels_tc_large.cu), split FP16, 128 <= N <= 1024.
+size_t tc_large_planes_bytes(const redo_table* t);
+cudaError_t launch_build_tc_large_planes(const redo_table* t, cudaStream_t s);
+size_t tc_large_prop_workspace(const redo_table* t, const ChainPlan& p, bool reunit);
+cudaError_t tc_large_propagate(const redo_table* t, const int32_t* q, const ChainPlan& p, bool reunit,
+                               void* ws, void** result, int* result_prec, int64_t* status,
+                               cudaStream_t s);
+size_t tc_large_grad_workspace(const redo_table* t, const ChainPlan& p);
+cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, const double2* UT,
+                          int tb, double* F_out, double* grad, void* ws, int64_t* status,
+                          cudaStream_t s);
 cudaError_t large_sim(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
                       const double2* psi0, int pb, const double* obs, double* expect, void* ws,
                       cudaStream_t s);

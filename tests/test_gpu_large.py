@@ -93,3 +93,52 @@ def test_large_simulate_matches_oracle(n, M):
         eo, Uo = O.simulate_expectation(To, Do, dig[b], w.psi0, w.obs_diag)
         assert np.abs(ex.cpu().numpy()[b] - eo).max() < 1e-12
         assert np.abs(U.cpu().numpy()[b] - Uo).max() < 1e-12
+
+
+def _tc_table(w):
+    from paper_1707_02162_gb300 import redo
+    return redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True)
+
+
+@pytest.mark.parametrize("reunit", [0, 8])
+def test_large_tc_propagate_n7(reunit):
+    w = _reduced(2, 7, 2, 3, 21)
+    t = _tc_table(w)
+    q = t.quantize(w.u)
+    U, F, _ = t.propagate(q, "fp16x3", target=w.target, reunit_every=reunit)
+    To, Do = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    Uo = _ref.oracle_propagators(w, To, Do, dig, range(w.B))
+    assert np.abs(U.cpu().numpy() - Uo).max() < 2e-4
+    Fo = np.array([O.fidelity(w.target, Uo[b]) for b in range(w.B)])
+    assert np.abs(F.cpu().numpy() - Fo).max() < 1e-6
+
+
+def test_large_tc_propagate_n8_and_simulate_n9():
+    w = _reduced(2, 8, 1, 2, 30, base=16, digits=2)
+    t = _tc_table(w)
+    q = t.quantize(w.u)
+    U, _, _ = t.propagate(q, "fp16x3", reunit_every=10)
+    U64, _, _ = t.propagate(q, "fp64")
+    assert (U - U64).abs().max().item() < 2e-4
+    w = inputs.config(3, n_qubits=9, B=2, M=12, base=16, digits=2)
+    t = _tc_table(w)
+    q = t.quantize(w.u)
+    ex, U = t.simulate(q, w.psi0, w.obs_diag, "fp16x3")
+    ex64, U64 = t.simulate(q, w.psi0, w.obs_diag, "fp64")
+    assert (U - U64).abs().max().item() < 2e-4
+    assert (ex - ex64).abs().max().item() < 2e-5
+
+
+@pytest.mark.parametrize("ck", [0, 4])
+def test_large_tc_gradient_n7(ck):
+    w = _reduced(2, 7, 2, 2, 9)
+    t = _tc_table(w)
+    q = t.quantize(w.u)
+    F, g = t.fidelity_grad(q, w.target, "fp16x3", checkpoint_every=ck)
+    To, Do = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    for b in range(w.B):
+        Fo, go = O.grape_gradient(To, Do, w.Hk, w.dt, dig[b], w.target)
+        assert np.abs(g.cpu().numpy()[b] - go).max() <= 1e-3 * np.abs(go).max()
+        assert abs(F.cpu().numpy()[b] - Fo) < 1e-6
