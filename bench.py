@@ -375,9 +375,9 @@ def run_workload(args):
     out = {"workload": args.workload, "n_gpus": 1, "data": "synthetic"}
     if args.workload == "grape":
         # 8 qubits (N=256), K=16, M=1000, dt=2 us, Haar target; forward checkpoints every 32 steps
-        w = inputs.config(2)
+        w = inputs.config(2, M=args.M if args.M != M_FULL else None)
         t0 = time.time()
-        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True)
         build_s = time.time() - t0
         u = torch.tensor(w.u, device="cuda")
         target = torch.as_tensor(w.target, device="cuda")
@@ -385,7 +385,9 @@ def run_workload(args):
         F = torch.empty(1, dtype=torch.float64, device="cuda")
         g = torch.empty(u.shape, dtype=torch.float64, device="cuda")
         res = {}
-        for prec, reps in (("fp32", args.steps), ("fp64", 1)):
+        precs = (("fp16x3", args.steps),) if args.skip_fp64 else (("fp16x3", args.steps), ("fp32", args.steps),
+                                                                 ("fp64", 1))
+        for prec, reps in precs:
             ws = torch.empty(redo.redo_fidelity_grad_workspace(t.handle, 1, w.M, prec, 32), dtype=torch.uint8,
                              device="cuda")
 
@@ -397,11 +399,15 @@ def run_workload(args):
             ms = _events_time(it, reps)
             res[prec] = {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "timed_iterations": reps}
         flop = 3 * w.M * w.K * w.digits * 8.0 * w.N ** 3
-        out.update({"metric": "GRAPE iters/s", "unit": "iterations/s", "value": res["fp32"]["iters_per_s"],
-                    "precision": "fp32 (SIMT, large-N lockstep GEMMs)", "fp64_plain_redo": res["fp64"],
-                    "speedup_vs_fp64": res["fp32"]["iters_per_s"] / res["fp64"]["iters_per_s"],
+        out.update({"metric": "GRAPE iters/s", "unit": "iterations/s", "value": res["fp16x3"]["iters_per_s"],
+                    "precision": "fp16x3 (tcgen05 lockstep chains, FP32 accumulate)", "fp32_simt": res.get("fp32"),
+                    "fp64_plain_redo": res.get("fp64"),
+                    "speedup_vs_fp64": (res["fp16x3"]["iters_per_s"] / res["fp64"]["iters_per_s"]
+                                        if "fp64" in res else None),
                     "algorithmic_flop_per_iter": flop,
-                    "achieved_tflops_fp32": flop / (res["fp32"]["ms_per_iter"] / 1e3) / 1e12,
+                    "achieved_tensor_tflops_fp16x3": 3 * flop / (res["fp16x3"]["ms_per_iter"] / 1e3) / 1e12,
+                    "achieved_tflops_fp32": (flop / (res["fp32"]["ms_per_iter"] / 1e3) / 1e12
+                                             if "fp32" in res else None),
                     "table_build_s": build_s,
                     "config": {"N": w.N, "K": w.K, "M": w.M, "dt": w.dt, "checkpoint_every": 32, "B": 1}})
     elif args.workload == "sim":
@@ -409,7 +415,7 @@ def run_workload(args):
         Ms = args.M if args.M != M_FULL else 40
         w = inputs.config(3, M=Ms)
         t0 = time.time()
-        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True)
         build_s = time.time() - t0
         q = t.quantize(w.u)
         psi0 = torch.as_tensor(w.psi0, device="cuda")
@@ -417,7 +423,7 @@ def run_workload(args):
         ex = torch.empty((w.B, Ms + 1), dtype=torch.float64, device="cuda")
         Uf = torch.empty((w.B, w.N, w.N), dtype=torch.complex128, device="cuda")
         res = {}
-        for prec, want in (("fp32", False), ("fp32", True), ("fp64", False)):
+        for prec, want in (("fp16x3", True), ("fp32", False), ("fp32", True), ("fp64", False)):
             nb = redo.redo_simulate_workspace(t.handle, w.B, Ms, prec, 0, want)
             ws = torch.empty(max(nb, 256), dtype=torch.uint8, device="cuda")
 
@@ -427,8 +433,10 @@ def run_workload(args):
             ms = _events_time(it, 1)
             res[f"{prec}{'_with_U' if want else '_state_only'}"] = {
                 "realisation_steps_per_s": w.B * Ms / (ms / 1e3), "ms": ms}
+        flop_step = 3 * w.K * w.digits * 8.0 * w.N ** 3
         out.update({"metric": "REDO prop steps/s (noisy-drive ensemble)", "unit": "realisation-steps/s",
-                    "value": res["fp32_with_U"]["realisation_steps_per_s"], "results": res,
+                    "value": res["fp16x3_with_U"]["realisation_steps_per_s"], "results": res,
+                    "achieved_tensor_tflops_fp16x3": flop_step * res["fp16x3_with_U"]["realisation_steps_per_s"] / 1e12,
                     "sample": f"{Ms} of the 2000 steps, all 64 realisations", "table_build_s": build_s,
                     "config": {"N": w.N, "K": w.K, "B": w.B, "M_timed": Ms}})
     elif args.workload == "plain":

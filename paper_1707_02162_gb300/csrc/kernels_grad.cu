@@ -117,6 +117,7 @@ struct GradArgs {
   const double2* tau;
   const int32_t* hk_ptr;
   const int32_t* hk_col;
+  const int32_t* hk_row;
   const double2* hk_val;
   double scale;              // 2 dt / N^2
   double* grad;              // [B][M][K]
@@ -197,13 +198,7 @@ grad_sweep_kernel(GradArgs<R> a) {
       const int p1 = a.hk_ptr[k * (N + 1) + N];
       double re = 0.0, im = 0.0;
       for (int e = p0 + lt; e < p1; e += MM::THREADS) {
-        // row of nonzero e: largest i with hk_ptr[k*(N+1)+i] <= e
-        int lo_i = 0, hi_i = N;
-        while (hi_i - lo_i > 1) {
-          const int mid = (lo_i + hi_i) >> 1;
-          if (a.hk_ptr[k * (N + 1) + mid] <= e) lo_i = mid; else hi_i = mid;
-        }
-        const int i = lo_i, c = a.hk_col[e];
+        const int i = a.hk_row[e], c = a.hk_col[e];
         R dr = 0, di = 0;
         for (int x = 0; x < N; ++x) {
           const cplx<R> pv = P[c * N + x], rv = Rm[x * N + i];
@@ -329,6 +324,7 @@ static cudaError_t grad_sweep_t(const redo_table* t, const int32_t* q, const Cha
   a.tau = tau;
   a.hk_ptr = t->hk_ptr;
   a.hk_col = t->hk_col;
+  a.hk_row = t->hk_row;
   a.hk_val = t->hk_val;
   a.scale = 2.0 * t->dt / ((double)t->N * (double)t->N);
   a.grad = grad;

@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const cplx<R>* __restrict__ 
                                                     int64_t S, int64_t seg_len, int64_t F,
                                                     int64_t t, int K, int d,
                                                     const int32_t* __restrict__ hk_ptr,
-                                                    const int32_t* __restrict__ hk_col,
+                                                    const int32_t* __restrict__ hk_col, const int32_t* __restrict__ hk_row,
                                                     const double2* __restrict__ hk_val,
                                                     const double2* __restrict__ tau, double scale,
                                                     int64_t M, double* __restrict__ grad) {
@@ -640,12 +640,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const cplx<R>* __restrict__ 
   // one warp per nonzero: (row i, col c): H[i][c] * sum_x P[c][x] R[x][i]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = p0 + warp; e < p1; e += 8) {
-    int lo_i = 0, hi_i = N;
-    while (hi_i - lo_i > 1) {
-      const int mid = (lo_i + hi_i) >> 1;
-      if (hk_ptr[k * (N + 1) + mid] <= e) lo_i = mid; else hi_i = mid;
-    }
-    const int i = lo_i, c = hk_col[e];
+    const int i = hk_row[e], c = hk_col[e];
     double dr = 0.0, di = 0.0;
     for (int x = lane; x < N; x += 32) {
       const cplx<R> pv = Pg[(int64_t)c * N + x], rv = Rg[(int64_t)x * N + i];
@@ -825,7 +820,7 @@ static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const Cha
   const double scale = 2.0 * t->dt / ((double)N * (double)N);
   for (int64_t tt = 0; tt < p.seg_len; ++tt) {
     trace_kernel<R><<<(unsigned)G, 256, 0, s>>>(P, Rr, N, p.S, p.seg_len, p.F, tt, t->K, t->digits,
-                                                t->hk_ptr, t->hk_col, t->hk_val, tau, scale, p.M,
+                                                t->hk_ptr, t->hk_col, t->hk_row, t->hk_val, tau, scale, p.M,
                                                 grad);
     left.t = tt;
     left.X = P;

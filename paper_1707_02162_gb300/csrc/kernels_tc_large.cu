@@ -350,17 +350,48 @@ __global__ void __launch_bounds__(192, 1) tc_large_step_kernel(StepArgs a) {
 constexpr uint32_t kStepSmem = kStages * 2 * kTile + 1024 + 128;
 
 // ---------------------------------------------------------------------------- gradient traces
-// Tr(H_k V^dag R) for chain g, V and R embedded (V = P^dag): one CTA per chain.
+// Tr(H_k V^dag R) = sum_x sum_{(i,c) in nz(H_k)} H[i][c] conj(V[x][c]) R[x][i]  (V = P^dag):
+// a sum over rows x of V and R, read straight from their embeddings (row x of Emb
+// holds Re(row x) in K columns 0..N-1; row N+x holds Im(row x)).  Grid (chain, row block):
+// each warp stages one row of V and of R in shared memory, its lanes walk the
+// nonzeros, and block partials are added into acc[g]; trace_finish_kernel turns
+// acc into dF/du and clears it.
+__device__ __forceinline__ void emb_row_to_smem(const uint8_t* st, int N, int x, float* re, float* im,
+                                                int lane) {
+  for (int g = lane; g < N / 8; g += 32) {
+    const uint32_t orr = emb_off(N, x, 8 * g), oi = emb_off(N, N + x, 8 * g);
+    const uint4 hr = *reinterpret_cast<const uint4*>(st + orr);
+    const uint4 lr = *reinterpret_cast<const uint4*>(st + orr + kHalf);
+    const uint4 hi = *reinterpret_cast<const uint4*>(st + oi);
+    const uint4 li = *reinterpret_cast<const uint4*>(st + oi + kHalf);
+    const uint32_t hrw[4] = {hr.x, hr.y, hr.z, hr.w}, lrw[4] = {lr.x, lr.y, lr.z, lr.w};
+    const uint32_t hiw[4] = {hi.x, hi.y, hi.z, hi.w}, liw[4] = {li.x, li.y, li.z, li.w};
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hrw[p]));
+      const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&lrw[p]));
+      const float2 c = __half22float2(*reinterpret_cast<const __half2*>(&hiw[p]));
+      const float2 d = __half22float2(*reinterpret_cast<const __half2*>(&liw[p]));
+      re[8 * g + 2 * p] = fmaf(b.x, kInv, a.x);
+      re[8 * g + 2 * p + 1] = fmaf(b.y, kInv, a.y);
+      im[8 * g + 2 * p] = fmaf(d.x, kInv, c.x);
+      im[8 * g + 2 * p + 1] = fmaf(d.y, kInv, c.y);
+    }
+  }
+}
+
+constexpr int kTraceRows = 8;   // rows per block (one per warp)
+
 __global__ void __launch_bounds__(256) trace_emb_kernel(const uint8_t* __restrict__ V,
-                                                        const uint8_t* __restrict__ Rs, int N, int64_t G,
-                                                        int64_t S, int64_t seg_len, int64_t F, int64_t t,
-                                                        int K, int d, const int32_t* __restrict__ hk_ptr,
+                                                        const uint8_t* __restrict__ Rs, int N, int64_t S,
+                                                        int64_t seg_len, int64_t F, int64_t t, int K, int d,
+                                                        const int32_t* __restrict__ hk_ptr,
                                                         const int32_t* __restrict__ hk_col,
+                                                        const int32_t* __restrict__ hk_row,
                                                         const double2* __restrict__ hk_val,
-                                                        const double2* __restrict__ tau, double scale,
-                                                        int64_t M, double* __restrict__ grad) {
+                                                        double2* __restrict__ acc) {
   const int64_t g = blockIdx.x;
-  const int64_t u = g / S, s = g % S;
+  const int64_t s = g % S;
   const int64_t f0 = s * seg_len;
   int64_t f1 = f0 + seg_len;
   if (f1 > F) f1 = F;
@@ -371,34 +402,32 @@ __global__ void __launch_bounds__(256) trace_emb_kernel(const uint8_t* __restric
   const int rr = (int)(f - n * kd);
   const int k = rr / d, j = rr - k * d;
   if (j != d - 1) return;
+  extern __shared__ float rows[];            // per warp: Vre, Vim, Rre, Rim (N floats each)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* vre = rows + (size_t)warp * 4 * N;
+  float* vim = vre + N;
+  float* rre = vim + N;
+  float* rim = rre + N;
+  const int x = blockIdx.y * kTraceRows + warp;
   const uint8_t* Vg = V + g * state_bytes(N);
   const uint8_t* Rg = Rs + g * state_bytes(N);
+  emb_row_to_smem(Vg, N, x, vre, vim, lane);
+  emb_row_to_smem(Rg, N, x, rre, rim, lane);
+  __syncwarp();
   const int p0 = hk_ptr[k * (N + 1)], p1 = hk_ptr[k * (N + 1) + N];
   double re = 0.0, im = 0.0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int ee = p0 + warp; ee < p1; ee += 8) {
-    int lo_i = 0, hi_i = N;
-    while (hi_i - lo_i > 1) {
-      const int mid = (lo_i + hi_i) >> 1;
-      if (hk_ptr[k * (N + 1) + mid] <= ee) lo_i = mid; else hi_i = mid;
-    }
-    const int i = lo_i, c = hk_col[ee];
-    // (V^dag R)[c][i] = sum_x conj(V[x][c]) R[x][i]
-    double dr = 0.0, di = 0.0;
-    for (int x = lane; x < N; x += 32) {
-      const float2 v = emb_get(Vg, N, x, c), w = emb_get(Rg, N, x, i);
-      dr += (double)v.x * w.x + (double)v.y * w.y;
-      di += (double)v.x * w.y - (double)v.y * w.x;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      dr += __shfl_down_sync(0xffffffffu, dr, off);
-      di += __shfl_down_sync(0xffffffffu, di, off);
-    }
-    if (lane == 0) {
-      const double2 h = hk_val[ee];
-      re += h.x * dr - h.y * di;
-      im += h.x * di + h.y * dr;
-    }
+  for (int e = p0 + lane; e < p1; e += 32) {
+    const int i = hk_row[e], c = hk_col[e];
+    // conj(V[x][c]) R[x][i]
+    const float a = vre[c], b = vim[c], cr = rre[i], ci = rim[i];
+    const float pr = a * cr + b * ci, pi = a * ci - b * cr;
+    const double2 h = hk_val[e];
+    re += h.x * pr - h.y * pi;
+    im += h.x * pi + h.y * pr;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, off);
+    im += __shfl_down_sync(0xffffffffu, im, off);
   }
   __shared__ double sre[8], sim[8];
   if (lane == 0) {
@@ -412,9 +441,31 @@ __global__ void __launch_bounds__(256) trace_emb_kernel(const uint8_t* __restric
       tr += sre[w];
       ti += sim[w];
     }
-    const double2 tu = tau[u];
-    grad[(u * M + n) * K + k] = scale * (tu.x * ti - tu.y * tr);
+    atomicAdd(&acc[g].x, tr);
+    atomicAdd(&acc[g].y, ti);
   }
+}
+
+__global__ void trace_finish_kernel(double2* __restrict__ acc, int64_t G, int64_t S, int64_t seg_len,
+                                    int64_t F, int64_t t, int K, int d, const double2* __restrict__ tau,
+                                    double scale, int64_t M, double* __restrict__ grad) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int64_t u = g / S, s = g % S;
+  const int64_t f0 = s * seg_len;
+  int64_t f1 = f0 + seg_len;
+  if (f1 > F) f1 = F;
+  const int64_t f = f1 - 1 - t;
+  if (f < f0 || f >= f1) return;
+  const int64_t kd = (int64_t)K * d;
+  const int64_t n = f / kd;
+  const int rr = (int)(f - n * kd);
+  const int k = rr / d, j = rr - k * d;
+  if (j != d - 1) return;
+  const double2 T = acc[g];
+  const double2 tu = tau[u];
+  grad[(u * M + n) * K + k] = scale * (tu.x * T.y - tu.y * T.x);
+  acc[g] = make_double2(0.0, 0.0);
 }
 
 static unsigned blocks_for(int64_t n) {
@@ -504,7 +555,8 @@ cudaError_t tc_large_propagate(const redo_table* t, const int32_t* q, const Chai
 size_t tc_large_grad_workspace(const redo_table* t, const ChainPlan& p) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t G = (size_t)p.B * p.S;
-  return large_grad_workspace(t, p, REDO_FP32) + 4 * up(G * state_bytes(t->N));
+  // + 2G embedded states x 2 (ping-pong) + 2G row-major FP32 transposes for the traces
+  return large_grad_workspace(t, p, REDO_FP32) + 4 * up(G * state_bytes(t->N)) + up(G * sizeof(double2));
 }
 
 // Gradient: tensor-core forward segments, SIMT FP32 checkpoint/costate scans,
@@ -545,11 +597,26 @@ cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan
   emb_from_complex_kernel<float><<<blocks_for(G * N * (N / 8)), 256, 0, s>>>(Rck, N, G, 2, s0 + sb);
   cur = s0;
   nxt = s1;
+  double2* acc = (double2*)(s1 + 2 * sb);      // per-chain trace accumulators
+  if ((e = cudaMemsetAsync(acc, 0, sizeof(double2) * G, s))) return e;
+  const size_t trace_smem = (size_t)kTraceRows * 4 * N * sizeof(float);
+  if ((e = cudaFuncSetAttribute(trace_emb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)trace_smem)))
+    return e;
   const double scale = 2.0 * t->dt / ((double)N * (double)N);
+  const int64_t kd = (int64_t)t->K * t->digits;
+  const bool aligned = (p.seg_len % kd) == 0;
   for (int64_t tt = 0; tt < p.seg_len; ++tt) {
-    trace_emb_kernel<<<(unsigned)G, 256, 0, s>>>(cur, cur + sb, N, G, p.S, p.seg_len, p.F, tt, t->K,
-                                                 t->digits, t->hk_ptr, t->hk_col, t->hk_val, tau, scale,
-                                                 p.M, grad);
+    // traces are needed where the visited factor is a term's last digit; with
+    // segments aligned to whole steps that is every d-th sweep step for all chains
+    if (!aligned || ((p.seg_len - 1 - tt) % t->digits) == (t->digits - 1)) {
+      dim3 grid((unsigned)G, (unsigned)(N / kTraceRows));
+      trace_emb_kernel<<<grid, 256, trace_smem, s>>>(cur, cur + sb, N, p.S, p.seg_len, p.F, tt, t->K,
+                                                     t->digits, t->hk_ptr, t->hk_col, t->hk_row, t->hk_val,
+                                                     acc);
+      trace_finish_kernel<<<(unsigned)((G + 127) / 128), 128, 0, s>>>(acc, G, p.S, p.seg_len, p.F, tt, t->K,
+                                                                      t->digits, tau, scale, p.M, grad);
+    }
     if ((e = step(t, q, p, tt, 1, 2 * G, G, cols, cur, nxt, status, s))) return e;
     std::swap(cur, nxt);
   }

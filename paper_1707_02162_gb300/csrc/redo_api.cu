@@ -177,7 +177,7 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
     return fail(set_error(REDO_ERR_OOM, "table allocation: %s", cudaGetErrorString(e)));
   {
     // sparse (CSR) copy of the control operators for the gradient traces Tr(H_k W)
-    std::vector<int32_t> ptr((size_t)K * (N + 1)), col;
+    std::vector<int32_t> ptr((size_t)K * (N + 1)), col, rowi;
     std::vector<double2> val;
     for (int k = 0; k < K; ++k) {
       const double* hk = h.data() + 2 * n2 * (k + 1);
@@ -187,6 +187,7 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
           const double re = hk[2 * (r * N + c)], im = hk[2 * (r * N + c) + 1];
           if (re != 0.0 || im != 0.0) {
             col.push_back(c);
+            rowi.push_back(r);
             val.push_back(make_double2(re, im));
           }
         }
@@ -197,11 +198,13 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
     const size_t nz = col.empty() ? 1 : col.size();
     if ((e = cudaMalloc(&t->hk_ptr, sizeof(int32_t) * ptr.size())) != cudaSuccess ||
         (e = cudaMalloc(&t->hk_col, sizeof(int32_t) * nz)) != cudaSuccess ||
+        (e = cudaMalloc(&t->hk_row, sizeof(int32_t) * nz)) != cudaSuccess ||
         (e = cudaMalloc(&t->hk_val, sizeof(double2) * nz)) != cudaSuccess)
       return fail(set_error(REDO_ERR_OOM, "operator CSR allocation: %s", cudaGetErrorString(e)));
     if ((e = cudaMemcpy(t->hk_ptr, ptr.data(), sizeof(int32_t) * ptr.size(), cudaMemcpyHostToDevice)) ||
         (!col.empty() &&
          ((e = cudaMemcpy(t->hk_col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice)) ||
+          (e = cudaMemcpy(t->hk_row, rowi.data(), sizeof(int32_t) * rowi.size(), cudaMemcpyHostToDevice)) ||
           (e = cudaMemcpy(t->hk_val, val.data(), sizeof(double2) * val.size(), cudaMemcpyHostToDevice)))))
       return fail(cuda_error(e, "operator CSR upload"));
   }
@@ -280,6 +283,7 @@ redo_status redo_table_free(redo_table* t) {
   cudaFree(t->tc_planes);
   cudaFree(t->hk_ptr);
   cudaFree(t->hk_col);
+  cudaFree(t->hk_row);
   cudaFree(t->hk_val);
   std::free(t);
   return REDO_OK;

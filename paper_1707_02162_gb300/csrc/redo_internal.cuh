@@ -51,6 +51,7 @@ struct redo_table {
   float2* T32;                // [entries][N][N] or nullptr
   int32_t* hk_ptr;            // CSR of the control operators: row pointers [K][N+1]
   int32_t* hk_col;            // column indices [nnz]
+  int32_t* hk_row;            // row index of every nonzero [nnz] (COO view of the same CSR)
   double2* hk_val;            // values [nnz]
   int64_t hk_nnz;
   void* tc_planes;            // tensor-core planes or nullptr
