@@ -164,9 +164,10 @@ def run_gpu(args):
         peaks = _json.load(open(pk))
 
     # Each rank runs an independent replica batch (weak scaling, no collective on the data path).
+    from paper_1707_02162_gb300.replicas import aggregate_throughput, replica_seed
     w = inputs.config(1, seed=1, B=args.B, M=args.M)
     if rank:
-        w.u = np.random.default_rng(1 + 7919 * rank).uniform(w.lo[0], w.hi[0], size=w.u.shape)
+        w.u = np.random.default_rng(replica_seed(1, rank)).uniform(w.lo[0], w.hi[0], size=w.u.shape)
     dev = torch.device("cuda", local)
     table = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True,
                        fp16x3=(MAIN_PREC == "fp16x3"), levels=args.levels)
@@ -214,13 +215,8 @@ def run_gpu(args):
     prof = redo.redo_profile_read()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * B * M / (ms_per_step / 1e3)
+    value, total_s = aggregate_throughput(float(B * M * args.steps), sum(step_ms) / 1e3)
+    ms_per_step = total_s * 1e3 / args.steps
 
     st = status.cpu().numpy()
     # parity guard on the measured run: F of two pulses against FP64 GPU path is checked in tests;
