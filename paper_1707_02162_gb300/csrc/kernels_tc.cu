@@ -29,6 +29,7 @@
 // Every wait is bounded; a timeout sets REDO_STATUS_TIMEOUT and the CTA
 // drains, frees its tensor memory and exits.
 #include <cuda_fp16.h>
+#include <cstdlib>
 
 #include "redo_internal.cuh"
 #include "device_sync.cuh"
@@ -346,6 +347,237 @@ chain_tc_kernel(TcArgs a) {
   if (warp == 0) tmem_dealloc(tmem_base, L::kTmemCols);
 }
 
+// --------------------------------------------------------------------------
+// Variant with the state operand in tensor memory.  Each chain owns 256 TMEM
+// columns: A_hi (64 columns = 128 fp16 K values per lane), A_lo, D1, D2.  The
+// MMA reads A from tensor memory and only the table operand from shared memory,
+// which removes 64 KB of shared-memory reads per product.  Because row r of the
+// embedded state needs the partner row r +- 64 of the accumulator (Re and Im
+// parts of one state row sit 64 lanes apart), the epilogue swaps its split
+// values with the partner thread through a small shared buffer (stored
+// word-transposed, conflict-free) and writes both halves of its A row with
+// tcgen05.st.
+// --------------------------------------------------------------------------
+template <int STAGES>
+struct Tc2Layout {
+  static constexpr int CH = 2, EW = 8;
+  static constexpr uint32_t kRing = 0;
+  static constexpr uint32_t kX = STAGES * kEntryBytes;                 // exchange: [CH][2 halves][32 words][128 rows]
+  static constexpr uint32_t kXBytes = CH * 2 * 32 * 128 * 4;
+  static constexpr uint32_t kBars = kX + kXBytes;
+  // full[STAGES], empty[STAGES], mma_done[CH], state_ready[CH], xchg[CH]
+  static constexpr uint32_t kMisc = kBars + (2 * STAGES + 3 * CH) * 8;
+  static constexpr uint32_t kAlloc = kMisc + 16 + 1024;
+  static constexpr int kThreads = 32 * (EW * CH + 2);
+  static_assert(kAlloc <= 232448, "shared memory budget");
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(Tc2Layout<STAGES>::kThreads, 1) chain_tc2_kernel(TcArgs a) {
+  using L = Tc2Layout<STAGES>;
+  constexpr int CH = L::CH, EW = L::EW;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint32_t* xbuf = reinterpret_cast<uint32_t*>(smem + L::kX);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBars);
+  uint64_t* empty = full + STAGES;
+  uint64_t* mma_done = empty + STAGES;
+  uint64_t* state_ready = mma_done + CH;
+  uint64_t* xchg = state_ready + CH;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kMisc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::kMisc + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = a.units * a.segs;
+  int64_t len[CH], f0[CH], unit[CH];
+  int64_t maxlen = 0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int64_t g = (int64_t)blockIdx.x * CH + c;
+    len[c] = 0;
+    f0[c] = 0;
+    unit[c] = 0;
+    if (g < G) {
+      unit[c] = g / a.segs;
+      f0[c] = (g % a.segs) * a.seg_len;
+      int64_t f1 = f0[c] + a.seg_len;
+      if (f1 > a.F) f1 = a.F;
+      len[c] = f1 > f0[c] ? f1 - f0[c] : 0;
+    }
+    if (len[c] > maxlen) maxlen = len[c];
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int c = 0; c < CH; ++c) {
+      mbar_init(&mma_done[c], 1);
+      mbar_init(&state_ready[c], 32 * EW);
+      mbar_init(&xchg[c], 32 * EW);
+    }
+    *abort_flag = 0;
+    fence_mbarrier_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp < EW * CH) {
+    const int c = warp / EW, ew = warp % EW;
+    const int quarter = ew & 3, j = ew >> 2;                 // lanes 32*quarter.., columns 32j..
+    const int r = 32 * quarter + lane;
+    const int partner = r < 64 ? r + 64 : r - 64;
+    const uint32_t negp = r < 64 ? 0x80008000u : 0u;         // partner half enters row r negated if r < 64
+    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+    const uint32_t base = tmem_base + lane_off + (uint32_t)(c * 256);
+    const uint32_t a_hi = base, a_lo = base + 64, d1 = base + 128, d2 = base + 192;
+    uint32_t* xw = xbuf + (size_t)(c * 2 + j) * 32 * 128;    // [32 words][128 rows]
+    const int64_t g = (int64_t)blockIdx.x * CH + c;
+    float* out = g < G ? reinterpret_cast<float*>(a.out + g * (kN * kN)) : nullptr;
+    const int m = r & 63, comp = r >> 6;
+    if (len[c] == 0) {
+      if (out)
+        for (int n = 32 * j; n < 32 * j + 32; ++n) out[(n * kN + m) * 2 + comp] = (comp == 0 && n == m) ? 1.f : 0.f;
+    } else {
+      // Y = I: row r < 64 holds I[r,:] in K 0..63; row r >= 64 holds I[r-64,:] in K 64..127
+      uint32_t own[16], oth[16], zero[16];
+#pragma unroll
+      for (int w = 0; w < 16; ++w) {
+        own[w] = 0u;
+        oth[w] = 0u;
+        zero[w] = 0u;
+      }
+      const int col = r < 64 ? r : r - 64;                   // K position of the 1 within its half
+      if (col >= 32 * j && col < 32 * j + 32) {
+        const int e = col - 32 * j;
+        (r < 64 ? own : oth)[e >> 1] = (uint32_t)0x3C00u << (16 * (e & 1));
+      }
+      tmem_st16(a_hi + 16 * j, own);
+      tmem_st16(a_hi + 32 + 16 * j, oth);
+      tmem_st16(a_lo + 16 * j, zero);
+      tmem_st16(a_lo + 32 + 16 * j, zero);
+      tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(&state_ready[c]);
+      for (int64_t t = 0; t < len[c]; ++t) {
+        bool ok = !*abort_flag && mbar_wait_bounded_n(&mma_done[c], (uint32_t)(t & 1), kTcWaitLimit);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        uint32_t ra[32], rb[32];
+        tmem_ld32(d1 + 32 * j, ra);
+        tmem_ld32(d2 + 32 * j, rb);
+        tmem_wait_ld();
+        float z[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) z[i] = fmaf(__uint_as_float(rb[i]), kLoInv, __uint_as_float(ra[i]));
+        if (t == len[c] - 1) {
+          if (out) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) out[((32 * j + i) * kN + m) * 2 + comp] = z[i];
+          }
+          break;
+        }
+        uint32_t hw[16], lw[16];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+          const __half2 hh = __floats2half2_rn(z[2 * p], z[2 * p + 1]);
+          const float2 hf = __half22float2(hh);
+          const __half2 ll = __floats2half2_rn((z[2 * p] - hf.x) * kLoScale, (z[2 * p + 1] - hf.y) * kLoScale);
+          hw[p] = *reinterpret_cast<const uint32_t*>(&hh);
+          lw[p] = *reinterpret_cast<const uint32_t*>(&ll);
+        }
+#pragma unroll
+        for (int w = 0; w < 16; ++w) {
+          xw[w * 128 + r] = hw[w];
+          xw[(16 + w) * 128 + r] = lw[w];
+        }
+        // all 256 threads of the chain have published their halves (bounded wait, no hardware barrier)
+        mbar_arrive(&xchg[c]);
+        bool xok = mbar_wait_bounded_n(&xchg[c], (uint32_t)(t & 1), kTcWaitLimit);
+        xok = __all_sync(0xffffffffu, xok);
+        if (!xok) {
+          *abort_flag = 1;
+          break;
+        }
+#pragma unroll
+        for (int w = 0; w < 16; ++w) {
+          own[w] = xw[w * 128 + partner] ^ negp;
+          oth[w] = xw[(16 + w) * 128 + partner] ^ negp;
+        }
+        tmem_st16(a_hi + 16 * j, hw);
+        tmem_st16(a_lo + 16 * j, lw);
+        tmem_st16(a_hi + 32 + 16 * j, own);
+        tmem_st16(a_lo + 32 + 16 * j, oth);
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(&state_ready[c]);
+      }
+    }
+  } else if (warp == EW * CH) {
+    if (lane == 0) {
+      uint32_t idx = 0;
+      for (int64_t t = 0; t < maxlen && !*abort_flag; ++t) {
+        for (int c = 0; c < CH; ++c) {
+          if (t >= len[c]) continue;
+          const uint32_t s = idx % STAGES, u = idx / STAGES;
+          if (u > 0 && !mbar_wait_bounded_n(&empty[s], (u - 1) & 1, kTcWaitLimit)) {
+            *abort_flag = 1;
+            break;
+          }
+          const int64_t e = tc_entry(a, unit[c], f0[c] + t);
+          uint8_t* dst = smem + L::kRing + s * kEntryBytes;
+          const uint8_t* src = a.planes + e * kEntryBytes;
+          mbar_arrive_expect_tx(&full[s], kEntryBytes);
+          bulk_load(dst, src, kEntryBytes / 2, &full[s]);
+          bulk_load(dst + kEntryBytes / 2, src + kEntryBytes / 2, kEntryBytes / 2, &full[s]);
+          ++idx;
+        }
+      }
+    }
+  } else {
+    if (lane == 0) {
+      uint32_t idx = 0;
+      for (int64_t t = 0; t < maxlen && !*abort_flag; ++t) {
+        for (int c = 0; c < CH; ++c) {
+          if (t >= len[c]) continue;
+          const uint32_t s = idx % STAGES, u = idx / STAGES;
+          if (!mbar_wait_bounded_n(&full[s], u & 1, kTcWaitLimit) ||
+              !mbar_wait_bounded_n(&state_ready[c], (uint32_t)(t & 1), kTcWaitLimit)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t b0 = smem_u32(smem + L::kRing + s * kEntryBytes);
+          const uint32_t base = tmem_base + (uint32_t)(c * 256);
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t bo = (uint32_t)(kk >> 2) * kEntryAtom + (uint32_t)(kk & 3) * 32u;
+            const uint64_t bb = smem_desc_sw128(b0 + bo);
+            mma_f16_tmem_a(base + 128, base + 8 * kk, bb, kIdesc128, kk > 0 ? 1u : 0u);
+            mma_f16_tmem_a(base + 192, base + 64 + 8 * kk, bb, kIdesc64, 1u);
+          }
+          mma_commit(&empty[s]);
+          mma_commit(&mma_done[c]);
+          ++idx;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (*abort_flag && threadIdx.x == 0 && a.status)
+    atomicAdd((unsigned long long*)&a.status[REDO_STATUS_TIMEOUT], 1ull);
+  if (warp == 0) tmem_dealloc(tmem_base, 512);
+}
+
 }  // namespace tc
 
 // ============================================================================
@@ -388,8 +620,44 @@ ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M) {
   return p;
 }
 
+// Which chain kernel runs: 1 (default) = state operand in shared memory, 2 = in tensor
+// memory.  Both are exact alternatives; on GB300 the shared-memory form measured faster
+// (37.3 vs 39.1 ms for 256 pulses x 2000 steps x 12 products), as the per-step epilogue
+// latency, not shared-memory bandwidth, bounds both.
+static int tc_variant() {
+  const char* v = getenv("REDO_TC_VARIANT");
+  return (v && v[0] == '2') ? 2 : 1;
+}
+
 cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPlan& p,
                             void* seg_out, int64_t* status, cudaStream_t s) {
+  if (tc_variant() == 2) {
+    constexpr int ST = 4;
+    using L2 = tc::Tc2Layout<ST>;
+    auto kern2 = tc::chain_tc2_kernel<ST>;
+    cudaError_t e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L2::kAlloc);
+    if (e != cudaSuccess) return e;
+    tc::TcArgs a;
+    a.planes = (const uint8_t*)t->tc_planes;
+    a.q = q;
+    a.M = p.M;
+    a.K = t->K;
+    a.d = t->digits;
+    a.base = t->base;
+    a.levels = t->levels;
+    a.units = p.B;
+    a.segs = p.S;
+    a.seg_len = p.seg_len;
+    a.F = p.F;
+    a.out = (float2*)seg_out;
+    a.status = status;
+    const int64_t G = p.B * p.S;
+    const int64_t blocks = (G + L2::CH - 1) / L2::CH;
+    if (blocks == 0) return cudaSuccess;
+    kern2<<<(unsigned)blocks, L2::kThreads, L2::kAlloc, s>>>(a);
+    return cudaGetLastError();
+  }
   using L = tc::TcLayout<kTcChains, kTcEpiWarps, kTcStages>;
   auto kern = tc::chain_tc_kernel<kTcChains, kTcEpiWarps, kTcStages>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -127,3 +127,19 @@ def test_tc_level_table_matches_oracle():
     assert np.abs(U64.cpu().numpy() - Uo).max() < 1e-12
     assert np.abs(U.cpu().numpy() - Uo).max() < TC_TOL
     assert (F - F64).abs().max().item() < F_TOL
+
+
+def test_tc_tensor_memory_state_variant_matches(monkeypatch):
+    # the alternative chain kernel keeps the state operand in tensor memory
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(1, B=3, M=80)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True, levels=True)
+    q = t.quantize(w.u)
+    U1, F1, _ = t.propagate(q, "fp16x3", target=w.target, reunit_every=16)
+    monkeypatch.setenv("REDO_TC_VARIANT", "2")
+    U2, F2, _ = t.propagate(q, "fp16x3", target=w.target, reunit_every=16)
+    monkeypatch.delenv("REDO_TC_VARIANT")
+    U64, _, _ = t.propagate(q, "fp64")
+    assert (U2 - U64).abs().max().item() < TC_TOL
+    assert (U1 - U2).abs().max().item() < TC_TOL
+    assert (F1 - F2).abs().max().item() < F_TOL
