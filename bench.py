@@ -409,7 +409,7 @@ def run_workload(args):
     elif args.workload == "sim":
         # 10-qubit ZZ chain (N=1024), global X drive with OU noise, 64 realisations; M_sample steps timed
         Ms = args.M if args.M != M_FULL else 40
-        w = inputs.config(3, M=Ms)
+        w = inputs.config(3, M=Ms, B=args.B if args.B != B_FULL else None, n_qubits=args.nq)
         t0 = time.time()
         t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True)
         build_s = time.time() - t0
@@ -458,6 +458,19 @@ def run_workload(args):
                 res[f"B{B}_{prec}"] = {"ms_per_call": ms, "pulse_steps_per_s": B * w.M / (ms / 1e3)}
         out.update({"metric": "REDO prop steps/s (plain REDO, N=8)", "unit": "pulse-steps/s",
                     "value": res["B4096_fp64"]["pulse_steps_per_s"], "results": res})
+    elif args.workload == "warmstart_study":
+        # 5 qubits, K=10, M=500, dt=2 us; targets from weight-one Pauli strings (reachable)
+        from paper_1707_02162_gb300 import warmstart
+        w = inputs.config(4, B=1)
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+        t0 = time.time()
+        const = np.concatenate([w.extra["nu"][0] / 5e3, w.extra["J"][0][np.triu_indices(w.n_qubits, 1)] / 200.0])
+        rep = warmstart.study(t, w.n_qubits, w.M, w.K, w.extra["Omega"], const, n_train=args.B if args.B != B_FULL else 512)
+        out.update({"metric": "GRAPE iterations to F>=0.99 (MLP warm start vs random init, Adam ascent)",
+                    "unit": "iterations", "value": rep.summary()["median_iters_mlp_init"],
+                    "summary": rep.summary(), "wall_s": time.time() - t0,
+                    "config": {"N": w.N, "K": w.K, "M": w.M, "dt": w.dt,
+                               "targets": "exp(-i sum theta_k P_k), 8 weight-one Pauli strings, theta ~ U[0, pi/2]"}})
     elif args.workload == "warmstart":
         # 5 qubits (N=32), K=10, M=500: batched GRAPE iterations and MLP training throughput
         B = 256
@@ -500,10 +513,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="prop", choices=["prop", "grape", "sim", "plain", "warmstart"],
+    ap.add_argument("--workload", default="prop",
+                    choices=["prop", "grape", "sim", "plain", "warmstart", "warmstart_study"],
                     help="prop (default): the batched propagation line; others: auxiliary measurements")
     ap.add_argument("--B", type=int, default=B_FULL, help="pulses (smaller only for profiling captures)")
     ap.add_argument("--M", type=int, default=M_FULL, help="steps per pulse (smaller only for profiling captures)")
+    ap.add_argument("--nq", type=int, default=None, help="qubits of the sim workload (profiling captures only)")
     ap.add_argument("--digit-table", action="store_true",
                     help="multiply digit operators every step instead of using the level table "
                          "(process 3: every level's operator evaluated once, the default)")

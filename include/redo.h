@@ -318,6 +318,18 @@ redo_status redo_mlp_adam(int64_t count, float* params, const float* grads, floa
                           int32_t step, float lr, float beta1, float beta2, float eps,
                           void* stream);
 
+/*
+ * redo_grape_adam_step -- GRAPE ascent with Adam moments (the paper leaves the
+ * update rule open): per coefficient
+ *     m <- b1 m + (1-b1) g,  v <- b2 v + (1-b2) g^2,
+ *     u <- clamp(u + lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps), lo[k], hi[k]).
+ * `lr` is in rad/s (the size of a typical coefficient change); m and v are
+ * caller-owned device double [B][M][K], zero before step 1.
+ */
+redo_status redo_grape_adam_step(const redo_table* t, double* u, const double* grad, double* m,
+                                 double* v, int64_t B, int64_t M, int32_t step, double lr, double beta1,
+                                 double beta2, double eps, void* stream);
+
 /* Scratch bytes redo_propagate needs for (B, M, prec, reunit_every) on this table. */
 redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
                                      redo_precision prec, int32_t reunit_every, size_t* bytes);

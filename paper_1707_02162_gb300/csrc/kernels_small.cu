@@ -85,6 +85,40 @@ __global__ void grape_step_kernel(double* __restrict__ u, const double* __restri
   }
 }
 
+// Adam ascent on the coefficients: m, v moments per coefficient, bias-corrected,
+// u <- clamp(u + lr * mhat / (sqrt(vhat) + eps), lo_k, hi_k)
+__global__ void grape_adam_kernel(double* __restrict__ u, const double* __restrict__ g,
+                                  double* __restrict__ m, double* __restrict__ v, int64_t count, int K,
+                                  const double* __restrict__ lo, const double* __restrict__ delta,
+                                  int64_t levels, double lr, double b1, double b2, double eps,
+                                  double c1, double c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % K);
+    const double l = lo[k], h = l + delta[k] * (double)(levels - 1);
+    const double gi = g[i];
+    const double mi = b1 * m[i] + (1.0 - b1) * gi;
+    const double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    double x = u[i] + lr * (mi / c1) / (sqrt(vi / c2) + eps);
+    x = x < l ? l : (x > h ? h : x);
+    u[i] = x;
+  }
+}
+
+cudaError_t launch_grape_adam(double* u, const double* g, double* m, double* v, int64_t count, int K,
+                              const double* lo, const double* delta, int64_t levels, int step, double lr,
+                              double b1, double b2, double eps, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
+  grape_adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(u, g, m, v, count, K, lo, delta, levels, lr, b1,
+                                                     b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_grape_step(double* u, const double* g, int64_t count, int64_t per_pulse, int K,
                               const double* lo, const double* delta, int64_t levels, double step,
                               const double* scale, cudaStream_t s) {

@@ -670,6 +670,22 @@ redo_status redo_mlp_adam(int64_t count, float* params, const float* grads, floa
   return e == cudaSuccess ? REDO_OK : cuda_error(e, "adam");
 }
 
+redo_status redo_grape_adam_step(const redo_table* t, double* u, const double* grad, double* m,
+                                 double* v, int64_t B, int64_t M, int32_t step, double lr, double beta1,
+                                 double beta2, double eps, void* stream) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (B < 0 || M < 0 || step < 1) return set_error(REDO_ERR_INVALID, "B, M >= 0 and step >= 1");
+  if (!std::isfinite(lr) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return set_error(REDO_ERR_INVALID, "bad Adam hyper-parameters");
+  const int64_t count = B * M * t->K;
+  if (count == 0) return REDO_OK;
+  if (!u || !grad || !m || !v) return set_error(REDO_ERR_INVALID, "null pointer");
+  cudaError_t e = launch_grape_adam(u, grad, m, v, count, t->K, t->d_lo, t->d_delta, t->levels, step,
+                                    lr, beta1, beta2, eps, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "grape adam step");
+  return REDO_OK;
+}
+
 redo_status redo_grape_step(const redo_table* t, double* u, const double* grad, int64_t B,
                             int64_t M, double step, const double* step_scale, void* stream) {
   if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");

@@ -122,6 +122,10 @@ cudaError_t launch_grape_step(double* u, const double* g, int64_t count, int64_t
                               const double* lo, const double* delta, int64_t levels, double step,
                               const double* scale, cudaStream_t s);
 
+cudaError_t launch_grape_adam(double* u, const double* g, double* m, double* v, int64_t count, int K,
+                              const double* lo, const double* delta, int64_t levels, int step, double lr,
+                              double b1, double b2, double eps, cudaStream_t s);
+
 // GRAPE gradient (kernels_grad.cu).
 cudaError_t launch_grad_scan(const redo_table* t, int64_t B, int64_t S, int prec, const void* seg,
                              const double2* U_target, int target_batched, void* Pck, void* Rck,

@@ -43,13 +43,15 @@ class GrapeResult:
 
 
 def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, prec="fp64",
-          checkpoint_every=0, threshold: float | None = None, adaptive: bool = True) -> GrapeResult:
-    """Fixed-step gradient ascent on the fidelity, ``u <- clamp(u + step * dF/du)``.
+          checkpoint_every=0, threshold: float | None = None, adaptive: bool = True,
+          optimizer: str = "gd", lr_decay: float = 150.0) -> GrapeResult:
+    """Gradient ascent on the fidelity (the paper does not specify the update rule).
 
-    With ``adaptive`` the step of a pulse is halved whenever its fidelity
-    decreased and grown by 1.1 otherwise (a cheap stand-in for a line search;
-    the paper does not specify the update rule).  Stops early once every
-    pulse reached ``threshold``.
+    ``optimizer="gd"``: ``u <- clamp(u + step * dF/du)``; with ``adaptive`` the
+    step of a pulse is halved whenever its fidelity decreased and grown by 1.1
+    otherwise.  ``optimizer="adam"``: Adam moments per coefficient, ``step`` is
+    then the learning rate in rad/s, decayed as step / (1 + it / lr_decay).
+    Stops early once every pulse reached ``threshold``.
     """
     u = u0.clone().contiguous()
     B, M, K = u.shape
@@ -64,6 +66,9 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
     q = torch.empty(u.shape, dtype=torch.int32, device=u.device)
     F = torch.empty(B, dtype=torch.float64, device=u.device)
     g = torch.empty(u.shape, dtype=torch.float64, device=u.device)
+    if optimizer == "adam":
+        m_ = torch.zeros_like(u)
+        v_ = torch.zeros_like(u)
     for it in range(iters):
         redo.redo_quantize(table.handle, u, q)
         redo.redo_fidelity_grad(table.handle, q, target, prec, checkpoint_every, F, g, ws)
@@ -74,6 +79,10 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
             reached[newly] = it
             if bool((reached >= 0).all()):
                 break
+        if optimizer == "adam":
+            redo.redo_grape_adam_step(table.handle, u, g, m_, v_, it + 1, step / (1.0 + it / lr_decay))
+            res.iterations = it + 1
+            continue
         if adaptive and prev_F is not None:
             worse = Fh < prev_F
             scale_h = torch.where(worse, scale_h * 0.5, torch.clamp(scale_h * 1.1, max=8.0))

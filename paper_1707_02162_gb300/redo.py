@@ -28,7 +28,7 @@ EXPORTS = [
     "redo_propagate", "redo_propagate_workspace", "redo_last_error", "redo_profile_enable",
     "redo_profile_read", "redo_propagate_noalloc", "redo_fidelity_grad", "redo_fidelity_grad_workspace",
     "redo_grape_step", "redo_simulate", "redo_simulate_workspace", "redo_mlp_sizes", "redo_mlp_forward",
-    "redo_mlp_backward", "redo_mlp_adam",
+    "redo_mlp_backward", "redo_mlp_adam", "redo_grape_adam_step",
 ]
 PROFILE_PHASES = 8
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_mlp_backward.argtypes = [i32, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp]
     L.redo_mlp_adam.argtypes = [i64, vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                 ctypes.c_float, vp]
+    L.redo_grape_adam_step.argtypes = [vp, vp, vp, vp, vp, i64, i64, i32, dbl, dbl, dbl, dbl, vp]
     L.redo_profile_enable.argtypes = [i32]
     L.redo_profile_read.argtypes = [vp, vp, i32]
     L.redo_last_error.restype = ctypes.c_char_p
@@ -246,6 +247,15 @@ def redo_mlp_backward(sizes, params, x, acts, y_target, grads, loss, work, strea
 def redo_mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     _check(load_library().redo_mlp_adam(params.numel(), _ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(step),
                                         float(lr), float(beta1), float(beta2), float(eps), _stream(stream)))
+
+
+def redo_grape_adam_step(handle: int, u, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-12,
+                         stream=None):
+    """In place Adam ascent on the coefficients u (clamped to each term's grid)."""
+    B, M = u.shape[0], u.shape[1]
+    _check(load_library().redo_grape_adam_step(ctypes.c_void_p(handle), _ptr(u), _ptr(grad), _ptr(m), _ptr(v), B, M,
+                                               int(step), float(lr), float(beta1), float(beta2), float(eps),
+                                               _stream(stream)))
 
 
 def redo_profile_enable(enable: bool):

@@ -75,6 +75,10 @@ class WarmStartReport:
     random_iters: list
     mlp_iters: list
     final_loss: float
+    random_F0: float = float("nan")     # median fidelity of the initial pulses
+    mlp_F0: float = float("nan")
+    random_Fend: float = float("nan")   # median fidelity after the iteration budget
+    mlp_Fend: float = float("nan")
 
     def summary(self) -> dict:
         def med(v):
@@ -83,12 +87,83 @@ class WarmStartReport:
         return {"threshold": self.threshold, "train": self.train_instances, "test": self.test_instances,
                 "median_iters_random_init": med(self.random_iters), "median_iters_mlp_init": med(self.mlp_iters),
                 "reached_random": int(sum(x >= 0 for x in self.random_iters)),
-                "reached_mlp": int(sum(x >= 0 for x in self.mlp_iters)), "final_train_loss": self.final_loss}
+                "reached_mlp": int(sum(x >= 0 for x in self.mlp_iters)), "final_train_loss": self.final_loss,
+                "median_F_initial_random": self.random_F0, "median_F_initial_mlp": self.mlp_F0,
+                "median_F_final_random": self.random_Fend, "median_F_final_mlp": self.mlp_Fend}
 
 
 def converge(table: redo.Table, targets: np.ndarray, u0: np.ndarray, iters: int, step: float, threshold: float,
-             prec="fp64"):
+             prec="fp64", optimizer="gd"):
     """Batched GRAPE on per-instance targets; returns (u, first iteration reaching threshold per instance)."""
     res = grape(table, torch.as_tensor(targets, device=table.device), torch.as_tensor(u0, device=table.device),
-                iters=iters, step=step, prec=prec, threshold=threshold)
+                iters=iters, step=step, prec=prec, threshold=threshold, optimizer=optimizer)
     return res.u, res.reached.tolist(), res
+
+
+def local_pauli_family(n_qubits: int, n_strings: int, rng: np.random.Generator) -> list[str]:
+    """Weight-one Pauli strings (one X, Y or Z on one qubit): targets built from them are
+    products of single-qubit rotations, reachable with per-qubit x/y controls."""
+    out = []
+    while len(out) < n_strings:
+        qb = int(rng.integers(n_qubits))
+        s = ["I"] * n_qubits
+        s[qb] = "XYZ"[int(rng.integers(3))]
+        s = "".join(s)
+        if s not in out:
+            out.append(s)
+    return out
+
+
+def study(table: redo.Table, n_qubits: int, M: int, K: int, Omega: float, features_const: np.ndarray,
+          n_train: int = 512, n_test: int = 64, threshold: float = 0.99, iters: int = 400, step: float = 0.0,
+          theta_max: float = np.pi / 2, train_steps: int = 1500, hidden=(512, 512, 512), seed: int = 4,
+          prec: str = "fp32") -> WarmStartReport:
+    """Learned warm start on one system: targets exp(-i sum_k theta_k P_k) over a fixed set of
+    Pauli strings; MLP input = (system constants, theta); output = M*K normalised amplitudes."""
+    from scipy.linalg import expm as _expm   # target construction only (problem input)
+    from .inputs import pauli_generator
+    rng = np.random.default_rng(seed)
+    strings = local_pauli_family(n_qubits, 8, rng)
+    lr = step if step > 0 else 0.01 * Omega          # Adam learning rate in rad/s
+
+    def targets(count):
+        th = rng.uniform(0.0, theta_max, size=(count, len(strings)))
+        T = np.stack([_expm(-1j * pauli_generator(strings, t)) for t in th])
+        return th, T
+
+    def feats(th):
+        const = np.broadcast_to(features_const, (th.shape[0], features_const.size))
+        return torch.tensor(np.concatenate([const, th / theta_max * 2 - 1], axis=1), dtype=torch.float32)
+
+    th_tr, T_tr = targets(n_train)
+    # every training instance starts from the same pulse, so that the converged pulses
+    # follow one smooth branch of solutions in theta (what the network can learn)
+    u0 = np.broadcast_to(rng.uniform(-0.3 * Omega, 0.3 * Omega, size=(1, M, K)), (n_train, M, K)).copy()
+    u_tr, reached, _ = converge(table, T_tr, u0, iters, lr, threshold, prec, "adam")
+    ok = np.array(reached) >= 0
+    if not ok.any():
+        raise RuntimeError("no training instance reached the threshold; raise iters or lr")
+    x = feats(th_tr[ok])
+    y = torch.tensor(u_tr.cpu().numpy()[ok].reshape(int(ok.sum()), -1) / Omega, dtype=torch.float32)
+    net = MLP([x.shape[1], *hidden, M * K], seed=seed)
+    loss = float("nan")
+    for _ in range(train_steps):
+        loss = net.train_step(x, y, 1e-3)
+    th_te, T_te = targets(n_test)
+    u_mlp = net.forward(feats(th_te)).cpu().numpy().reshape(n_test, M, K).astype(np.float64) * Omega
+    u_rnd = rng.uniform(-0.3 * Omega, 0.3 * Omega, size=(n_test, M, K))
+    # threshold=None keeps every run to the full budget so the final fidelities compare
+    _, _, r_mlp = converge(table, T_te, u_mlp, iters, lr, None, prec, "adam")
+    _, _, r_rnd = converge(table, T_te, u_rnd, iters, lr, None, prec, "adam")
+
+    def first_reach(res):
+        F = torch.stack(res.F_history)                      # [iters][B]
+        hit = F >= threshold
+        out = []
+        for b in range(F.shape[1]):
+            idx = torch.nonzero(hit[:, b])
+            out.append(int(idx[0]) if idx.numel() else -1)
+        return out, float(F[0].median()), float(F[-1].median())
+    it_mlp, f0m, fem = first_reach(r_mlp)
+    it_rnd, f0r, fer = first_reach(r_rnd)
+    return WarmStartReport(int(ok.sum()), n_test, threshold, it_rnd, it_mlp, loss, f0r, f0m, fer, fem)
