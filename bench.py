@@ -373,7 +373,8 @@ def run_workload(args):
         # 8 qubits (N=256), K=16, M=1000, dt=2 us, Haar target; forward checkpoints every 32 steps
         w = inputs.config(2, M=args.M if args.M != M_FULL else None)
         t0 = time.time()
-        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True)
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True,
+                       levels=args.levels)
         build_s = time.time() - t0
         u = torch.tensor(w.u, device="cuda")
         target = torch.as_tensor(w.target, device="cuda")
@@ -394,7 +395,7 @@ def run_workload(args):
             it()
             ms = _events_time(it, reps)
             res[prec] = {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "timed_iterations": reps}
-        flop = 3 * w.M * w.K * w.digits * 8.0 * w.N ** 3
+        flop = 3 * w.M * w.K * (1 if args.levels else w.digits) * 8.0 * w.N ** 3
         out.update({"metric": "GRAPE iters/s", "unit": "iterations/s", "value": res["fp16x3"]["iters_per_s"],
                     "precision": "fp16x3 (tcgen05 lockstep chains, FP32 accumulate)", "fp32_simt": res.get("fp32"),
                     "fp64_plain_redo": res.get("fp64"),
@@ -405,7 +406,8 @@ def run_workload(args):
                     "achieved_tflops_fp32": (flop / (res["fp32"]["ms_per_iter"] / 1e3) / 1e12
                                              if "fp32" in res else None),
                     "table_build_s": build_s,
-                    "config": {"N": w.N, "K": w.K, "M": w.M, "dt": w.dt, "checkpoint_every": 32, "B": 1}})
+                    "config": {"N": w.N, "K": w.K, "M": w.M, "dt": w.dt, "checkpoint_every": 32, "B": 1,
+                               "table": "level table" if args.levels else "digit table"}})
     elif args.workload == "sim":
         # 10-qubit ZZ chain (N=1024), global X drive with OU noise, 64 realisations; M_sample steps timed
         Ms = args.M if args.M != M_FULL else 40

@@ -105,8 +105,9 @@ typedef struct redo_table redo_table;
  *           E[k][q] = T[k][d-1][c_{d-1}] ... T[k][0][c_0] is evaluated once and
  *           stored, and the table then holds K x levels operators (reported by
  *           redo_table_info as base = levels, digits = 1), so a time step costs
- *           K products instead of K*digits.  N <= 64; K * levels * N^2 * 16
- *           bytes must stay below 64 GiB.
+ *           K products instead of K*digits.  K * levels * N^2 * 16 bytes (the
+ *           FP64 copy) must stay below 200 GiB; the FP32 copy and the split-FP16
+ *           planes, when requested, add half and (N > 64: two sets of) half of that.
  *  stream   stream for the build; synchronised before returning.
  *  out      receives the handle; free with redo_table_free.
  * Errors: REDO_ERR_INVALID, REDO_ERR_NOT_HERMITIAN (relative tolerance 1e-12

@@ -448,6 +448,71 @@ cudaError_t large_table_build(redo_table* t, const double2* H0, const double2* H
   return e;
 }
 
+// Level operators (process 3) for large N: E[k][q] = T[k][d-1][c_{d-1}] ... T[k][0][c_0],
+// built with batched GEMMs over chunks of levels (two chunk-sized ping-pong buffers).
+cudaError_t large_table_expand(const redo_table* t, double2* E, cudaStream_t s) {
+  const int N = t->N, K = t->K, d = t->digits, base = t->base;
+  const int64_t n2 = (int64_t)N * N, L = t->levels;
+  const int64_t chunk = L < 1024 ? L : 1024;
+  double2* buf = nullptr;
+  int32_t *ia = nullptr, *ib = nullptr, *ic = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&buf, sizeof(double2) * n2 * chunk)) || (e = cudaMalloc(&ia, sizeof(int32_t) * chunk)) ||
+      (e = cudaMalloc(&ib, sizeof(int32_t) * chunk)) || (e = cudaMalloc(&ic, sizeof(int32_t) * chunk))) {
+    cudaFree(buf);
+    cudaFree(ia);
+    cudaFree(ib);
+    cudaFree(ic);
+    return e;
+  }
+  std::vector<int32_t> A_(chunk), B_(chunk), C_(chunk);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    for (int64_t q0 = 0; q0 < L && e == cudaSuccess; q0 += chunk) {
+      const int64_t cnt = (q0 + chunk <= L) ? chunk : L - q0;
+      double2* dst = E + ((int64_t)k * L + q0) * n2;
+      // start: digit-0 operators (the product accumulates into dst / buf alternately)
+      double2* cur = (d % 2 == 1) ? dst : buf;
+      double2* nxt = (d % 2 == 1) ? buf : dst;
+      for (int64_t i = 0; i < cnt; ++i) {
+        A_[i] = (int32_t)((int64_t)(k * d + 0) * base + (q0 + i) % base);
+        C_[i] = (int32_t)i;
+      }
+      if ((e = cudaMemcpyAsync(ia, A_.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, s)) ||
+          (e = cudaMemcpyAsync(ic, C_.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, s)))
+        break;
+      for (int64_t i = 0; i < cnt; ++i) {
+        const double2* src = t->T64 + (int64_t)A_[i] * n2;
+        if ((e = cudaMemcpyAsync(cur + i * n2, src, sizeof(double2) * n2, cudaMemcpyDeviceToDevice, s))) break;
+      }
+      for (int j = 1; j < d && e == cudaSuccess; ++j) {
+        int64_t bj = 1;
+        for (int x = 0; x < j; ++x) bj *= base;
+        for (int64_t i = 0; i < cnt; ++i) {
+          A_[i] = (int32_t)((int64_t)(k * d + j) * base + ((q0 + i) / bj) % base);
+          B_[i] = (int32_t)i;
+          C_[i] = (int32_t)i;
+        }
+        if ((e = cudaMemcpyAsync(ia, A_.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(ib, B_.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(ic, C_.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, s)))
+          break;
+        // A from the table, B and C chunk-relative (IndexOps with separate base pointers)
+        IndexOps<double> op{t->T64, cur, nxt, ia, ib, ic, n2};
+        if ((e = cgemm<double, false>(op, cnt, N, 1.0, 0.0, s))) break;
+        if ((e = cudaStreamSynchronize(s))) break;    // host index vectors are reused
+        std::swap(cur, nxt);
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(buf);
+  cudaFree(ia);
+  cudaFree(ib);
+  cudaFree(ic);
+  return e;
+}
+
 // ============================================================================
 // Chains, combine, re-unitarisation
 // ============================================================================

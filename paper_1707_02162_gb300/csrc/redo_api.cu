@@ -120,11 +120,9 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
       return set_error(REDO_ERR_INVALID, "term %d: need finite lo < hi", k);
   if ((flags & REDO_TABLE_FP16X3) && N != 64 && N < 128)
     return set_error(REDO_ERR_UNSUPPORTED, "REDO_TABLE_FP16X3 needs N = 64 or N >= 128");
-  if ((flags & REDO_TABLE_LEVELS) && N > kSmallN)
-    return set_error(REDO_ERR_UNSUPPORTED, "REDO_TABLE_LEVELS needs N <= 64");
   if ((flags & REDO_TABLE_LEVELS) &&
-      (double)K * lv * (double)N * N * 16.0 > 64.0 * 1024 * 1024 * 1024)
-    return set_error(REDO_ERR_INVALID, "level table above 64 GiB (K * levels * N^2 * 16 bytes)");
+      (double)K * lv * (double)N * N * 16.0 > 200.0 * 1024 * 1024 * 1024)
+    return set_error(REDO_ERR_INVALID, "level table above 200 GiB (K * levels * N^2 * 16 bytes)");
   cudaStream_t s = (cudaStream_t)stream;
 
   // Hermitian check on the host (one synchronous copy, build time only)
@@ -242,7 +240,8 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
     const int64_t ne = (int64_t)K * t->levels;
     if ((e = cudaMalloc(&E, sizeof(double2) * n2 * ne)) != cudaSuccess)
       return fail(set_error(REDO_ERR_OOM, "level table allocation: %s", cudaGetErrorString(e)));
-    if ((e = launch_table_expand(t, E, s)) != cudaSuccess || (e = cudaStreamSynchronize(s))) {
+    e = N > kSmallN ? large_table_expand(t, E, s) : launch_table_expand(t, E, s);
+    if (e != cudaSuccess || (e = cudaStreamSynchronize(s))) {
       cudaFree(E);
       return fail(cuda_error(e, "level table"));
     }

@@ -156,6 +156,7 @@ namespace redo {
 cudaError_t large_table_build(redo_table* t, const double2* H0, const double2* Hk,
                               const std::vector<double>& hnorm1, double h0norm1, cudaStream_t s);
 ChainPlan plan_chain_large(const redo_table* t, int64_t B, int64_t M);
+cudaError_t large_table_expand(const redo_table* t, double2* E, cudaStream_t s);
 size_t large_prop_workspace(const redo_table* t, const ChainPlan& p, int prec, bool reunit);
 cudaError_t large_propagate(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
                             bool reunit, void* ws, void** result, int* result_prec,

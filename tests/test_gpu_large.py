@@ -142,3 +142,28 @@ def test_large_tc_gradient_n7(ck):
         Fo, go = O.grape_gradient(To, Do, w.Hk, w.dt, dig[b], w.target)
         assert np.abs(g.cpu().numpy()[b] - go).max() <= 1e-3 * np.abs(go).max()
         assert abs(F.cpu().numpy()[b] - Fo) < 1e-6
+
+
+def test_large_level_table_matches_digit_products():
+    from paper_1707_02162_gb300 import redo
+    w = _reduced(2, 7, 2, 2, 12, base=16, digits=2)       # N=128, 256 levels
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True, levels=True)
+    assert t.info["digits"] == 1 and t.info["entries"] == w.K * w.levels
+    E, _ = t.operators()
+    To, Do = _ref.oracle_table(w)
+    Tf = _ref.folded(To, Do)
+    Eg = E.cpu().numpy()
+    for qv in [0, 1, 17, 255, 130]:
+        c = O.level_digits(np.array([qv]), w.base, w.digits)[0]
+        for k in range(w.K):
+            assert np.abs(Eg[k, 0, qv] - Tf[k, 1, c[1]] @ Tf[k, 0, c[0]]).max() < 1e-13
+    q = t.quantize(w.u)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    Uo = _ref.oracle_propagators(w, To, Do, dig, range(w.B))
+    U64, _, _ = t.propagate(q, "fp64")
+    assert np.abs(U64.cpu().numpy() - Uo).max() < 1e-12
+    U16, _, _ = t.propagate(q, "fp16x3", reunit_every=6)
+    assert np.abs(U16.cpu().numpy() - Uo).max() < 2e-4
+    F, g = t.fidelity_grad(q, w.target, "fp16x3")
+    Fo, go = O.grape_gradient(To, Do, w.Hk, w.dt, dig[0], w.target)
+    assert np.abs(g.cpu().numpy()[0] - go).max() <= 1e-3 * np.abs(go).max()
