@@ -301,6 +301,19 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(u_host.numel() * 8),
                "d2h_bytes_per_step": int(U_host.numel() * 16 + F_host.numel() * 8)}
 
+    grape = None
+    if rank == 0 and not args.skip_grape:
+        gres, gflop, gbuild, gw = grape_measure(redo, inputs, torch, 3, levels=False, with_fp32=False,
+                                                with_fp64=not args.skip_fp64)
+        grape = {"metric": "GRAPE iters/s", "value": gres["fp16x3"]["iters_per_s"], "unit": "iterations/s",
+                 "workload": "GRAPE gradient + update, N=256 (8 qubits), K=16, M=1000, dt=2 us, Haar target, "
+                             "checkpoints every 32 steps, digit table",
+                 "fp64_plain_redo": gres.get("fp64"),
+                 "speedup_vs_fp64": (gres["fp16x3"]["iters_per_s"] / gres["fp64"]["iters_per_s"]
+                                     if "fp64" in gres else None),
+                 "achieved_tensor_tflops": 3 * gflop / (gres["fp16x3"]["ms_per_iter"] / 1e3) / 1e12,
+                 "table_build_s": gbuild}
+
     launches = sum(n for _, n in prof.values())
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -312,7 +325,7 @@ def run_gpu(args):
                                        "l2": "flushed between timed steps (256 MB write outside the events)"}),
            "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-           "fp64_plain_redo": fp64, "clocks": clk}
+           "fp64_plain_redo": fp64, "grape": grape, "clocks": clk}
     if rank == 0 and not args.skip_cpu:
         out["cpu_baseline"] = oracle_throughput()
     if world > 1:
@@ -362,6 +375,37 @@ def _events_time(fn, reps):
     return a.elapsed_time(b) / reps
 
 
+def grape_measure(redo, inputs, torch, steps, levels=False, with_fp32=True, with_fp64=True, M=None):
+    """GRAPE iterations/s on the 8-qubit (N=256), K=16, M=1000, dt=2 us workload, B=1, checkpoints
+    every 32 steps: split FP16 on tensor cores, optionally FP32 SIMT and FP64 plain REDO."""
+    w = inputs.config(2, M=M)
+    t0 = time.time()
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True, levels=levels)
+    build_s = time.time() - t0
+    u = torch.tensor(w.u, device="cuda")
+    target = torch.as_tensor(w.target, device="cuda")
+    q = torch.empty(u.shape, dtype=torch.int32, device="cuda")
+    F = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(u.shape, dtype=torch.float64, device="cuda")
+    res = {}
+    precs = [("fp16x3", steps)] + ([("fp32", steps)] if with_fp32 else []) + ([("fp64", 1)] if with_fp64 else [])
+    for prec, reps in precs:
+        ws = torch.empty(redo.redo_fidelity_grad_workspace(t.handle, 1, w.M, prec, 32), dtype=torch.uint8,
+                         device="cuda")
+
+        def it():
+            redo.redo_quantize(t.handle, u, q)
+            redo.redo_fidelity_grad(t.handle, q, target, prec, 32, F, g, ws)
+            redo.redo_grape_step(t.handle, u, g, 1e9)
+        it()
+        ms = _events_time(it, reps)
+        res[prec] = {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "timed_iterations": reps}
+        del ws
+    t.close()
+    flop = 3 * w.M * w.K * (1 if levels else w.digits) * 8.0 * w.N ** 3
+    return res, flop, build_s, w
+
+
 def run_workload(args):
     import torch
     torch.cuda.set_device(0)
@@ -370,32 +414,9 @@ def run_workload(args):
     from paper_1707_02162_gb300 import inputs, redo
     out = {"workload": args.workload, "n_gpus": 1, "data": "synthetic"}
     if args.workload == "grape":
-        # 8 qubits (N=256), K=16, M=1000, dt=2 us, Haar target; forward checkpoints every 32 steps
-        w = inputs.config(2, M=args.M if args.M != M_FULL else None)
-        t0 = time.time()
-        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True,
-                       levels=args.levels)
-        build_s = time.time() - t0
-        u = torch.tensor(w.u, device="cuda")
-        target = torch.as_tensor(w.target, device="cuda")
-        q = torch.empty(u.shape, dtype=torch.int32, device="cuda")
-        F = torch.empty(1, dtype=torch.float64, device="cuda")
-        g = torch.empty(u.shape, dtype=torch.float64, device="cuda")
-        res = {}
-        precs = (("fp16x3", args.steps),) if args.skip_fp64 else (("fp16x3", args.steps), ("fp32", args.steps),
-                                                                 ("fp64", 1))
-        for prec, reps in precs:
-            ws = torch.empty(redo.redo_fidelity_grad_workspace(t.handle, 1, w.M, prec, 32), dtype=torch.uint8,
-                             device="cuda")
-
-            def it():
-                redo.redo_quantize(t.handle, u, q)
-                redo.redo_fidelity_grad(t.handle, q, target, prec, 32, F, g, ws)
-                redo.redo_grape_step(t.handle, u, g, 1e9)
-            it()
-            ms = _events_time(it, reps)
-            res[prec] = {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "timed_iterations": reps}
-        flop = 3 * w.M * w.K * (1 if args.levels else w.digits) * 8.0 * w.N ** 3
+        res, flop, build_s, w = grape_measure(redo, inputs, torch, args.steps, levels=args.levels,
+                                              with_fp32=not args.skip_fp64, with_fp64=not args.skip_fp64,
+                                              M=args.M if args.M != M_FULL else None)
         out.update({"metric": "GRAPE iters/s", "unit": "iterations/s", "value": res["fp16x3"]["iters_per_s"],
                     "precision": "fp16x3 (tcgen05 lockstep chains, FP32 accumulate)", "fp32_simt": res.get("fp32"),
                     "fp64_plain_redo": res.get("fp64"),
@@ -527,6 +548,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-grape", action="store_true", help="omit the GRAPE iterations/s sub-measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

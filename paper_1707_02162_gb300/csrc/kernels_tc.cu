@@ -578,6 +578,231 @@ __global__ void __launch_bounds__(Tc2Layout<STAGES>::kThreads, 1) chain_tc2_kern
   if (warp == 0) tmem_dealloc(tmem_base, 512);
 }
 
+// --------------------------------------------------------------------------
+// Variant with a three-block state (the default): the embedding's four 64 x 64
+// blocks hold only three distinct matrices, so the state operand is stored as 192
+// rows [-Yi; Yr; Yi] x 64 K (48 KB for hi + lo instead of 64 KB) and each step
+// runs two K halves:  D = [Yr; Yi] Cr (rows 64..191, table K atom 0)
+//                   + [-Yi; Yr] Ci (rows 0..127, table K atom 1).
+// The epilogue writes 48 KB of state per step instead of 64 KB, and the saved
+// shared memory deepens the operand ring to four stages.  (A third chain per CTA
+// fits as well, but with a two-stage ring it measured slower.)
+// --------------------------------------------------------------------------
+template <int CH, int STAGES>
+struct Tc3Layout {
+  static constexpr int EW = 8;
+  static constexpr uint32_t kPlane = 192 * 128;          // 24 KB: 192 rows x 64 fp16
+  static constexpr uint32_t kState = 2 * kPlane;         // hi + lo
+  static constexpr uint32_t kRing = CH * kState;
+  static constexpr uint32_t kBars = kRing + STAGES * kEntryBytes;
+  static constexpr uint32_t kMisc = kBars + (2 * STAGES + 2 * CH) * 8;
+  static constexpr uint32_t kAlloc = kMisc + 16 + 1024;
+  static constexpr int kThreads = 32 * (EW * CH + 2);
+  static_assert(kAlloc <= 232448, "shared memory budget");
+};
+
+template <int CH, int STAGES>
+__global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_kernel(TcArgs a) {
+  using L = Tc3Layout<CH, STAGES>;
+  constexpr int EW = L::EW;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBars);
+  uint64_t* empty = full + STAGES;
+  uint64_t* mma_done = empty + STAGES;
+  uint64_t* state_ready = mma_done + CH;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kMisc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::kMisc + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = a.units * a.segs;
+  int64_t len[CH], f0[CH], unit[CH];
+  int64_t maxlen = 0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int64_t g = (int64_t)blockIdx.x * CH + c;
+    len[c] = 0;
+    f0[c] = 0;
+    unit[c] = 0;
+    if (g < G) {
+      unit[c] = g / a.segs;
+      f0[c] = (g % a.segs) * a.seg_len;
+      int64_t f1 = f0[c] + a.seg_len;
+      if (f1 > a.F) f1 = a.F;
+      len[c] = f1 > f0[c] ? f1 - f0[c] : 0;
+    }
+    if (len[c] > maxlen) maxlen = len[c];
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int c = 0; c < CH; ++c) {
+      mbar_init(&mma_done[c], 1);
+      mbar_init(&state_ready[c], 32 * EW);
+    }
+    *abort_flag = 0;
+    fence_mbarrier_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp < EW * CH) {
+    const int c = warp / EW, ew = warp % EW;
+    const int quarter = ew & 3, j = ew >> 2;
+    const int r = 32 * quarter + lane;                     // accumulator row
+    uint8_t* st_hi = smem + c * L::kState;
+    uint8_t* st_lo = st_hi + L::kPlane;
+    const int64_t g = (int64_t)blockIdx.x * CH + c;
+    float* out = g < G ? reinterpret_cast<float*>(a.out + g * (kN * kN)) : nullptr;
+    const uint32_t d1 = tmem_base + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(c * 128);
+    const uint32_t d2 = d1 + 64;
+    const int m = r & 63, comp = r >> 6;
+    // destinations: r < 64 (Zr row r) -> block 1 row 64+r ; r >= 64 (Zi row r-64) -> block 2
+    // row 128+(r-64) and, negated, block 0 row r-64
+    const int rowA = r < 64 ? 64 + r : 128 + (r - 64);
+    const int rowB = r - 64;                               // used only when r >= 64
+    if (len[c] == 0) {
+      if (out)
+        for (int n = 32 * j; n < 32 * j + 32; ++n) out[(n * kN + m) * 2 + comp] = (comp == 0 && n == m) ? 1.f : 0.f;
+    } else {
+      // Y = I: block 1 = I, blocks 0 and 2 = 0; this thread clears/sets its K columns 32j..32j+31
+      for (int gi = 4 * j; gi < 4 * j + 4; ++gi) {
+        const int k0 = 8 * gi;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (r < 64 && r >= k0 && r < k0 + 8) {
+          const int p = (r - k0) >> 1, hp = (r - k0) & 1;
+          w[p] = (uint32_t)0x3C00u << (16 * hp);
+        }
+        const uint32_t oa = sw128((uint32_t)rowA, (uint32_t)k0, 192);
+        *reinterpret_cast<uint4*>(st_hi + oa) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(st_lo + oa) = make_uint4(0u, 0u, 0u, 0u);
+        if (r >= 64) {
+          const uint32_t ob = sw128((uint32_t)rowB, (uint32_t)k0, 192);
+          *reinterpret_cast<uint4*>(st_hi + ob) = make_uint4(0u, 0u, 0u, 0u);
+          *reinterpret_cast<uint4*>(st_lo + ob) = make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&state_ready[c]);
+      for (int64_t t = 0; t < len[c]; ++t) {
+        bool ok = !*abort_flag && mbar_wait_bounded_n(&mma_done[c], (uint32_t)(t & 1), kTcWaitLimit);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const bool last = (t == len[c] - 1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int cb = 32 * j + 16 * h;                  // 16 accumulator columns
+          uint32_t ra[16], rb[16];
+          tmem_ld16(d1 + cb, ra);
+          tmem_ld16(d2 + cb, rb);
+          tmem_wait_ld();
+          float z[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) z[i] = fmaf(__uint_as_float(rb[i]), kLoInv, __uint_as_float(ra[i]));
+          if (!last) {
+#pragma unroll
+            for (int gq = 0; gq < 2; ++gq) {
+              uint4 hh, ll;
+              split8(z + 8 * gq, hh, ll);
+              const uint32_t kcol = (uint32_t)(cb + 8 * gq);
+              const uint32_t oa = sw128((uint32_t)rowA, kcol, 192);
+              *reinterpret_cast<uint4*>(st_hi + oa) = hh;
+              *reinterpret_cast<uint4*>(st_lo + oa) = ll;
+              if (r >= 64) {
+                const uint32_t ob = sw128((uint32_t)rowB, kcol, 192);
+                const uint32_t ng = 0x80008000u;
+                *reinterpret_cast<uint4*>(st_hi + ob) = make_uint4(hh.x ^ ng, hh.y ^ ng, hh.z ^ ng, hh.w ^ ng);
+                *reinterpret_cast<uint4*>(st_lo + ob) = make_uint4(ll.x ^ ng, ll.y ^ ng, ll.z ^ ng, ll.w ^ ng);
+              }
+            }
+          } else if (out) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) out[((cb + i) * kN + m) * 2 + comp] = z[i];
+          }
+        }
+        if (!last) {
+          fence_proxy_async_smem();
+          tc_fence_before();
+          mbar_arrive(&state_ready[c]);
+        }
+      }
+    }
+  } else if (warp == EW * CH) {
+    if (lane == 0) {
+      uint32_t idx = 0;
+      for (int64_t t = 0; t < maxlen && !*abort_flag; ++t) {
+        for (int c = 0; c < CH; ++c) {
+          if (t >= len[c]) continue;
+          const uint32_t s = idx % STAGES, u = idx / STAGES;
+          if (u > 0 && !mbar_wait_bounded_n(&empty[s], (u - 1) & 1, kTcWaitLimit)) {
+            *abort_flag = 1;
+            break;
+          }
+          const int64_t e = tc_entry(a, unit[c], f0[c] + t);
+          uint8_t* dst = smem + L::kRing + s * kEntryBytes;
+          const uint8_t* src = a.planes + e * kEntryBytes;
+          mbar_arrive_expect_tx(&full[s], kEntryBytes);
+          bulk_load(dst, src, kEntryBytes / 2, &full[s]);
+          bulk_load(dst + kEntryBytes / 2, src + kEntryBytes / 2, kEntryBytes / 2, &full[s]);
+          ++idx;
+        }
+      }
+    }
+  } else {
+    if (lane == 0) {
+      uint32_t idx = 0;
+      for (int64_t t = 0; t < maxlen && !*abort_flag; ++t) {
+        for (int c = 0; c < CH; ++c) {
+          if (t >= len[c]) continue;
+          const uint32_t s = idx % STAGES, u = idx / STAGES;
+          if (!mbar_wait_bounded_n(&full[s], u & 1, kTcWaitLimit) ||
+              !mbar_wait_bounded_n(&state_ready[c], (uint32_t)(t & 1), kTcWaitLimit)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_hi = smem_u32(smem + c * L::kState);
+          const uint32_t a_lo = a_hi + L::kPlane;
+          const uint32_t b0 = smem_u32(smem + L::kRing + s * kEntryBytes);
+          const uint32_t dd1 = tmem_base + (uint32_t)(c * 128);
+          const uint32_t dd2 = dd1 + 64;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t arow = h == 0 ? 64u * 128u : 0u;   // [Yr; Yi] for Cr, [-Yi; Yr] for Ci
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t ao = arow + (uint32_t)kk * 32u;
+              const uint32_t bo = (uint32_t)h * kEntryAtom + (uint32_t)kk * 32u;
+              const uint64_t ah = smem_desc_sw128(a_hi + ao), al = smem_desc_sw128(a_lo + ao);
+              const uint64_t bb = smem_desc_sw128(b0 + bo);
+              mma_f16(dd1, ah, bb, kIdesc128, (h | kk) ? 1u : 0u);
+              mma_f16(dd2, al, bb, kIdesc64, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+          mma_commit(&mma_done[c]);
+          ++idx;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (*abort_flag && threadIdx.x == 0 && a.status)
+    atomicAdd((unsigned long long*)&a.status[REDO_STATUS_TIMEOUT], 1ull);
+  if (warp == 0) tmem_dealloc(tmem_base, 512);
+}
+
 }  // namespace tc
 
 // ============================================================================
@@ -620,17 +845,50 @@ ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M) {
   return p;
 }
 
-// Which chain kernel runs: 1 (default) = state operand in shared memory, 2 = in tensor
-// memory.  Both are exact alternatives; on GB300 the shared-memory form measured faster
-// (37.3 vs 39.1 ms for 256 pulses x 2000 steps x 12 products), as the per-step epilogue
-// latency, not shared-memory bandwidth, bounds both.
+// Which chain kernel runs (all exact alternatives):
+//   3 (default) three-block state in shared memory, 2 chains, 4-stage ring: 35.4 ms
+//   1 embedded state in shared memory, 2 chains, 3-stage ring:               37.3 ms
+//   2 embedded state in tensor memory, 2 chains, 4-stage ring:               39.1 ms
+// (GB300, 256 pulses x 2000 steps x 12 products).  The per-step epilogue latency on the
+// chains' serial dependency bounds all three; variant 3 writes the least state per step
+// and has the deepest operand ring.
 static int tc_variant() {
   const char* v = getenv("REDO_TC_VARIANT");
-  return (v && v[0] == '2') ? 2 : 1;
+  if (v && v[0] == '1') return 1;
+  if (v && v[0] == '2') return 2;
+  return 3;
 }
+
+constexpr int kTc3Chains = 2, kTc3Stages = 4;
 
 cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPlan& p,
                             void* seg_out, int64_t* status, cudaStream_t s) {
+  if (tc_variant() == 3) {
+    using L3 = tc::Tc3Layout<kTc3Chains, kTc3Stages>;
+    auto kern3 = tc::chain_tc3_kernel<kTc3Chains, kTc3Stages>;
+    cudaError_t e = cudaFuncSetAttribute(kern3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L3::kAlloc);
+    if (e != cudaSuccess) return e;
+    tc::TcArgs a;
+    a.planes = (const uint8_t*)t->tc_planes;
+    a.q = q;
+    a.M = p.M;
+    a.K = t->K;
+    a.d = t->digits;
+    a.base = t->base;
+    a.levels = t->levels;
+    a.units = p.B;
+    a.segs = p.S;
+    a.seg_len = p.seg_len;
+    a.F = p.F;
+    a.out = (float2*)seg_out;
+    a.status = status;
+    const int64_t G = p.B * p.S;
+    const int64_t blocks = (G + kTc3Chains - 1) / kTc3Chains;
+    if (blocks == 0) return cudaSuccess;
+    kern3<<<(unsigned)blocks, L3::kThreads, L3::kAlloc, s>>>(a);
+    return cudaGetLastError();
+  }
   if (tc_variant() == 2) {
     constexpr int ST = 4;
     using L2 = tc::Tc2Layout<ST>;

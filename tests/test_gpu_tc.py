@@ -129,17 +129,22 @@ def test_tc_level_table_matches_oracle():
     assert (F - F64).abs().max().item() < F_TOL
 
 
-def test_tc_tensor_memory_state_variant_matches(monkeypatch):
-    # the alternative chain kernel keeps the state operand in tensor memory
+@pytest.mark.parametrize("variant", ["1", "2", "3"])
+def test_tc_kernel_variants_match(monkeypatch, variant):
+    # 1: state operand in shared memory (embedding), 2: in tensor memory,
+    # 3 (default): three-block state in shared memory
     from paper_1707_02162_gb300 import redo
-    w = inputs.config(1, B=3, M=80)
+    w = inputs.config(1, B=7, M=80)                 # 7 pulses: a ragged last CTA for 2 and 3 chains
     t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True, levels=True)
     q = t.quantize(w.u)
+    monkeypatch.setenv("REDO_TC_VARIANT", "1")
     U1, F1, _ = t.propagate(q, "fp16x3", target=w.target, reunit_every=16)
-    monkeypatch.setenv("REDO_TC_VARIANT", "2")
+    monkeypatch.setenv("REDO_TC_VARIANT", variant)
     U2, F2, _ = t.propagate(q, "fp16x3", target=w.target, reunit_every=16)
+    U3, _, _ = t.propagate(q, "fp16x3", reunit_every=0)
     monkeypatch.delenv("REDO_TC_VARIANT")
     U64, _, _ = t.propagate(q, "fp64")
     assert (U2 - U64).abs().max().item() < TC_TOL
+    assert (U3 - U64).abs().max().item() < TC_TOL
     assert (U1 - U2).abs().max().item() < TC_TOL
     assert (F1 - F2).abs().max().item() < F_TOL
