@@ -698,13 +698,18 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
         }
         tc_fence_after();
         const bool last = (t == len[c] - 1);
+        // issue all four accumulator loads before waiting once
+        uint32_t ra0[16], rb0[16], ra1[16], rb1[16];
+        tmem_ld16(d1 + 32 * j, ra0);
+        tmem_ld16(d2 + 32 * j, rb0);
+        tmem_ld16(d1 + 32 * j + 16, ra1);
+        tmem_ld16(d2 + 32 * j + 16, rb1);
+        tmem_wait_ld();
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int cb = 32 * j + 16 * h;                  // 16 accumulator columns
-          uint32_t ra[16], rb[16];
-          tmem_ld16(d1 + cb, ra);
-          tmem_ld16(d2 + cb, rb);
-          tmem_wait_ld();
+          const uint32_t* ra = h == 0 ? ra0 : ra1;
+          const uint32_t* rb = h == 0 ? rb0 : rb1;
           float z[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) z[i] = fmaf(__uint_as_float(rb[i]), kLoInv, __uint_as_float(ra[i]));
