@@ -35,6 +35,12 @@ MAIN_PREC = os.environ.get("REDO_BENCH_PREC", "fp16x3")
 REUNIT = 64          # re-unitarisation period (steps) of the reduced-precision forms
 
 
+def tc_variant_env() -> str:
+    """Tensor-core chain variant the library will run (see REDO_TC_VARIANT in kernels_tc.cu)."""
+    v = os.environ.get("REDO_TC_VARIANT", "3")
+    return v if v in ("1", "2", "3") else "3"
+
+
 def _workload_config(extra=None):
     cfg = {"workload": "batched REDO propagation: N=64 (6 qubits), K=12 x/y controls, B=256 pulses, "
                        "M=2000 steps of 1 us, 4096 levels (b=64, d=2), fidelity vs Haar target",
@@ -233,11 +239,20 @@ def run_gpu(args):
     flops_per_launch = B * M * prods_per_step * 8.0 * N ** 3       # algorithmic: complex products per step
     avg_s = (dom_ms / max(dom_n, 1)) / 1e3
     achieved_tf = flops_per_launch / avg_s / 1e12
-    if MAIN_PREC == "fp16x3":
-        roof = {"bound": "tensor", "peak": peaks.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
-                "peak_source": "measured bf16 dense (sustained); fp16 has the same nominal rate",
-                # three fp16 products per complex product
-                "achieved": achieved_tf * 3}
+    tensor_roof = {"peak": peaks.get("bf16_tflops_sustained", 1709.6), "unit": "TFLOP/s",
+                   "peak_source": "measured bf16 dense (sustained) of measured; fp16 has the same nominal rate",
+                   "achieved": achieved_tf * 3}          # three fp16 products per complex product
+    tensor_roof["frac"] = tensor_roof["achieved"] / tensor_roof["peak"]
+    if MAIN_PREC == "fp16x3" and args.levels:
+        # the level table (1.6 GB of operand planes) streams one 32 KB operand per product from HBM
+        op_bytes = B * M * prods_per_step * 32768.0
+        roof = {"bound": "hbm", "peak": peaks.get("hbm_gbs", 6794.5), "unit": "GB/s",
+                "peak_source": "measured HBM copy bandwidth (of measured)",
+                "achieved": op_bytes / avg_s / 1e9,
+                "algorithmic_bytes_per_launch": op_bytes,
+                "tensor": tensor_roof}
+    elif MAIN_PREC == "fp16x3":
+        roof = dict(tensor_roof, bound="tensor")
     elif MAIN_PREC == "fp32":
         clk_max = (clk.get("sm_max_mhz") or 2070.0) * 1e6
         peak = 152 * 128 * 2 * clk_max / 1e12
@@ -248,9 +263,18 @@ def run_gpu(args):
                 "achieved": achieved_tf}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom_name
-    roof["traffic"] = None
+    # DRAM bytes (read + write) of one full-size launch of chain_tc3_kernel<2,4> with the level
+    # table, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/
+    # chain_tc_fp16x3_n64.md); only valid for that kernel and configuration.
+    full_size = (B, M) == (B_FULL, M_FULL)
+    roof["traffic"] = (190010190080 + 342801152) if (MAIN_PREC == "fp16x3" and args.levels and full_size
+                                                     and tc_variant_env() == "3") else None
     roof["algorithmic_per_launch"] = (f"{flops_per_launch:.4g} flop (B*M*{prods_per_step} complex {N}x{N} "
                                       f"products, 8N^3 each)")
+    if roof["bound"] == "hbm":
+        roof["algorithmic_per_launch"] = (f"{roof['algorithmic_bytes_per_launch']:.4g} B (B*M*{prods_per_step} "
+                                          f"split-FP16 operands of 32 KB streamed from HBM); "
+                                          + roof["algorithmic_per_launch"])
 
     # ---- FP64 plain REDO on the same GPU (subset of pulses, same steps)
     fp64 = None
