@@ -1,26 +1,37 @@
-// Tensor-core (tcgen05, split-FP16) lockstep chains for 128 <= N <= 1024.
+// Tensor-core (tcgen05, split-FP16) sweeps for 128 <= N <= 1024.
 //
-// Every chain keeps its state as the real embedding Emb(Y) = [[Yr, -Yi], [Yi, Yr]]
-// (2N x 2N) in HBM, in split FP16 (hi, lo = (v - hi) * 2^11), laid out as
-// pre-swizzled tiles: tile (rt, kt) holds rows 128 rt.. and K columns 64 kt..
-// as a 128-byte-swizzled K-major 128 x 64 block for hi followed by the same
-// block for lo (32 KB), so a single bulk copy lands a tile in shared memory
-// ready for the MMA descriptors.  Table operators are stored the same way as
-// the operand B^T of Z = Y C: tile (nt, kt) holds 128 hi rows then 128 lo rows
-// of B^T, row n = [Re C[:, n], Im C[:, n]].  Two operand sets exist: "row"
-// planes with C = A^T (forward steps Y <- Y A^T, i.e. X <- A X for Y = X^T)
-// and "column" planes with C = A (reverse gradient sweep, V <- V A, R <- R A).
+// State layout.  A chain state Y (N x N complex) is stored as the real N x 2N matrix
+// S = [Re Y | Im Y] in split FP16 (hi = fp16(v), lo = fp16((v - hi) 2^11)), cut into tiles
+// of 128 rows x 64 columns: tile (rt, kt) is the hi block (128 rows of 128 B, K-major,
+// 128-byte swizzled) followed by the lo block, 32 KB, tiles row-major.  A step Y <- Y C
+// gives, with the operand B^T whose row n is [Re C[:, n], Im C[:, n]],
+//     Re Z = [Re Y | Im Y] [Re C; -Im C],    Im Z = [Im Y | Re Y] [Re C; Im C]:
+// both halves read the same tiles of S (the Im half with its K tiles rotated by N) against
+// one operand plane, and the Re half negates the products of its second K half through the
+// instruction descriptor's negate-B bit.
 //
-// One launch per chain step; CTA (chain, rt, nt) computes the 128 x 128 block
-// [D1 | D2] of Z with a K loop over 2N/64 tiles (3-stage bulk-copy ring):
-//     D[:, 0:256]  (+)= A_hi [B_hi; B_lo]^T      (one N = 256 MMA)
-//     D[:, 128:256] += A_lo B_hi^T               (one N = 128 MMA)
-// and its epilogue writes Z = D1 + 2^-11 D2, split again, into the next
-// state's direct and mirrored positions of the embedding.
+// Operand planes.  Every table entry C is stored as tiles (nb, kt) holding NB rows of B^T
+// hi followed by the same NB rows lo, 64 K columns wide (NB = 256 for N >= 256, else 128),
+// swizzled like the states.  Two sets exist: "row" planes with C = A^T (forward steps
+// X <- A X on Y = X^T) and "column" planes with C = A (reverse sweep V <- V A, R <- R A).
+//
+// Sweep kernel.  A right product acts on every row of Y separately, so each 128-row block
+// of each chain is its own sequence of steps.  A unit of work is (step, chain, row block,
+// half, column block); units are handed out in step order from a global ticket counter to
+// persistent CTAs, and a unit waits only until the previous step of its own row block is
+// complete (a counter per chain and row block that every finished unit increments).  In a
+// CTA, one warp claims tickets, waits for the counters and streams the A (state) and B
+// (operand) tiles through a ring of bulk copies; one thread issues the MMAs into tensor
+// memory; four epilogue warps turn the FP32 accumulators into the next state's split
+// FP16 tiles.  In the reverse sweep of the gradient the epilogue warps also evaluate
+// Tr(H_k V^dag R) for a slice of rows of the current states while the MMAs run.
+// Every wait is bounded; a timed-out CTA raises a sweep-wide abort flag and leaves.
 #include "redo_internal.cuh"
 #include "device_sync.cuh"
 #include "tcgen05.cuh"
 
+#include <cstdlib>
+#include <cstring>
 #include <type_traits>
 
 namespace redo {
@@ -28,47 +39,68 @@ namespace tcl {
 
 using namespace tc;
 
-constexpr uint32_t kTile = 32768;     // hi (16 KB) + lo (16 KB)
+constexpr uint32_t kTile = 32768;     // state tile: hi (16 KB) + lo (16 KB)
 constexpr uint32_t kHalf = 16384;
-constexpr uint32_t kLimit = 1u << 24;
+constexpr uint32_t kLimit = 1u << 24; // mbarrier polls before a wait gives up
+constexpr uint32_t kSpin = 1u << 22;  // counter polls before a dependency wait gives up
 constexpr float kScale = 2048.0f, kInv = 1.0f / 2048.0f;
-constexpr int kStages = 3;
+constexpr uint32_t kNegB = 1u << 14;  // instruction descriptor: negate B
+constexpr int kQ = 4;                 // depth of the in-CTA unit queue
 
-__host__ __device__ inline size_t state_bytes(int N) { return (size_t)16 * N * N; }
+__host__ __device__ inline size_t state_bytes(int N) { return (size_t)8 * N * N; }
 __host__ __device__ inline size_t entry_bytes(int N) { return (size_t)8 * N * N; }
+__host__ __device__ inline int trace_warps(int N) { return N >= 1024 ? 2 : 4; }
 
-// byte offset of the hi element (row, kcol) of an embedded state; lo at +kHalf
-__device__ __forceinline__ uint32_t emb_off(int N, int row, int kcol) {
+template <int NB>
+struct Geo {
+  static constexpr uint32_t kB = (uint32_t)NB * 256u;      // NB rows hi + NB rows lo, 128 B each
+  static constexpr uint32_t kStage = kTile + kB;
+  static constexpr int kStages = NB == 256 ? 2 : 3;
+  static constexpr int kAcc = 2 * NB;                       // TMEM columns of D1 | D2
+  static constexpr int kBufs = 512 / kAcc;
+  static constexpr uint32_t kRing = kStages * kStage;
+};
+
+inline size_t sweep_smem(int NB, int N) {
+  const size_t ring = NB == 256 ? Geo<256>::kRing : Geo<128>::kRing;
+  return ring + (size_t)trace_warps(N) * 16 * N + 2048;
+}
+
+// byte offset of the hi element (row, kcol) of a state; lo at +kHalf
+__host__ __device__ __forceinline__ uint32_t s_off(int N, int row, int kcol) {
   const int KT = 2 * N / 64;
   return (uint32_t)(((row >> 7) * KT + (kcol >> 6))) * kTile + sw128(row & 127, kcol & 63, 128);
 }
 
-__device__ __forceinline__ float emb_val(const uint8_t* st, int N, int row, int kcol) {
-  const uint32_t o = emb_off(N, row, kcol);
+__device__ __forceinline__ float s_val(const uint8_t* st, int N, int row, int kcol) {
+  const uint32_t o = s_off(N, row, kcol);
   const float h = __half2float(*reinterpret_cast<const __half*>(st + o));
   const float l = __half2float(*reinterpret_cast<const __half*>(st + o + kHalf));
   return fmaf(l, kInv, h);
 }
 
-// complex element (i, j) of the matrix Y whose embedding is st
-__device__ __forceinline__ float2 emb_get(const uint8_t* st, int N, int i, int j) {
-  return make_float2(emb_val(st, N, i, j), emb_val(st, N, N + i, j));
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& h, uint32_t& l) {
+  const __half2 hh = __floats2half2_rn(x0, x1);
+  const float2 hf = __half22float2(hh);
+  const __half2 ll = __floats2half2_rn((x0 - hf.x) * kScale, (x1 - hf.y) * kScale);
+  h = *reinterpret_cast<const uint32_t*>(&hh);
+  l = *reinterpret_cast<const uint32_t*>(&ll);
 }
 
-// ---------------------------------------------------------------------------- table planes
-// grid: entries * (N/128) * KT tiles; each tile 256 rows x 8 granules
-__global__ void __launch_bounds__(256) build_large_planes_kernel(const double2* __restrict__ T, int N,
-                                                                 int transpose, uint8_t* __restrict__ out) {
-  const int KT = 2 * N / 64, NT = N / 128;
+// ---------------------------------------------------------------------------- operand planes
+// grid: entries * (N / NB) * KT tiles; a tile is 2 NB rows (hi, lo) x 8 granules of 8 fp16.
+__global__ void __launch_bounds__(256) build_planes_kernel(const double2* __restrict__ T, int N, int NB,
+                                                           int transpose, uint8_t* __restrict__ out) {
+  const int KT = 2 * N / 64, TNB = N / NB;
   const int64_t tile = blockIdx.x;
-  const int64_t e = tile / ((int64_t)NT * KT);
-  const int rem = (int)(tile % ((int64_t)NT * KT));
-  const int nt = rem / KT, kt = rem % KT;
+  const int64_t e = tile / ((int64_t)TNB * KT);
+  const int rem = (int)(tile % ((int64_t)TNB * KT));
+  const int nb = rem / KT, kt = rem % KT;
   const double2* A = T + e * (int64_t)N * N;
-  uint8_t* dst = out + tile * kTile;
-  for (int gi = threadIdx.x; gi < 256 * 8; gi += blockDim.x) {
+  uint8_t* dst = out + tile * (int64_t)NB * 256;
+  for (int gi = threadIdx.x; gi < 2 * NB * 8; gi += blockDim.x) {
     const int r = gi >> 3, g = gi & 7;
-    const int plane = r >> 7, n = nt * 128 + (r & 127);
+    const int plane = r / NB, n = nb * NB + r % NB;
     uint32_t w[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
@@ -84,24 +116,16 @@ __global__ void __launch_bounds__(256) build_large_planes_kernel(const double2* 
       }
       w[p] = pack_half2(hv[0], hv[1]);
     }
-    *reinterpret_cast<uint4*>(dst + sw128(r, 8 * g, 256)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(dst + sw128(r, 8 * g, 2 * NB)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
 // ---------------------------------------------------------------------------- state conversions
-__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& h, uint32_t& l) {
-  const __half2 hh = __floats2half2_rn(x0, x1);
-  const float2 hf = __half22float2(hh);
-  const __half2 ll = __floats2half2_rn((x0 - hf.x) * kScale, (x1 - hf.y) * kScale);
-  h = *reinterpret_cast<const uint32_t*>(&hh);
-  l = *reinterpret_cast<const uint32_t*>(&ll);
-}
-
-// Emb(Y) for Y given per chain: mode 0 Y = X^T, mode 1 Y = X^dag, mode 2 Y = X; src [G][N][N].
-// One thread per (chain, row i of Y, granule of 8 columns j).
+// S from complex X per chain: mode 0 Y = X^T, mode 1 Y = X^dag, mode 2 Y = X; src [G][N][N].
+// One thread per (chain, row i, granule of 8 columns j).
 template <typename R>
-__global__ void emb_from_complex_kernel(const cplx<R>* __restrict__ src, int N, int64_t G, int mode,
-                                        uint8_t* __restrict__ dst) {
+__global__ void s_from_complex_kernel(const cplx<R>* __restrict__ src, int N, int64_t G, int mode,
+                                      uint8_t* __restrict__ dst) {
   const int64_t per = (int64_t)N * (N / 8);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < G * per;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -113,7 +137,7 @@ __global__ void emb_from_complex_kernel(const cplx<R>* __restrict__ src, int N, 
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int j = j0 + q;
-      cplx<R> v = mode == 2 ? X[(int64_t)i * N + j] : X[(int64_t)j * N + i];
+      const cplx<R> v = mode == 2 ? X[(int64_t)i * N + j] : X[(int64_t)j * N + i];
       re[q] = (float)v.x;
       im[q] = mode == 1 ? -(float)v.y : (float)v.y;
     }
@@ -124,44 +148,34 @@ __global__ void emb_from_complex_kernel(const cplx<R>* __restrict__ src, int N, 
       split_pair(im[2 * p], im[2 * p + 1], hi_[p], li_[p]);
     }
     uint8_t* st = dst + c * state_bytes(N);
-    const uint32_t neg = 0x80008000u;
-    // (i, j): Re ; (i, N+j): -Im ; (N+i, j): Im ; (N+i, N+j): Re
-    uint32_t o = emb_off(N, i, j0);
+    uint32_t o = s_off(N, i, j0);
     *reinterpret_cast<uint4*>(st + o) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
     *reinterpret_cast<uint4*>(st + o + kHalf) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-    o = emb_off(N, N + i, N + j0);
-    *reinterpret_cast<uint4*>(st + o) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-    *reinterpret_cast<uint4*>(st + o + kHalf) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-    o = emb_off(N, N + i, j0);
+    o = s_off(N, i, N + j0);
     *reinterpret_cast<uint4*>(st + o) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
     *reinterpret_cast<uint4*>(st + o + kHalf) = make_uint4(li_[0], li_[1], li_[2], li_[3]);
-    o = emb_off(N, i, N + j0);
-    *reinterpret_cast<uint4*>(st + o) =
-        make_uint4(hi_[0] ^ neg, hi_[1] ^ neg, hi_[2] ^ neg, hi_[3] ^ neg);
-    *reinterpret_cast<uint4*>(st + o + kHalf) =
-        make_uint4(li_[0] ^ neg, li_[1] ^ neg, li_[2] ^ neg, li_[3] ^ neg);
   }
 }
 
-// X from Emb(Y): mode 0 X = Y^T, mode 2 X = Y.  dst [G][N][N] complex<R>.
+// X from S: mode 0 X = Y^T, mode 2 X = Y.  dst [G][N][N] complex<R>.
 template <typename R>
-__global__ void emb_to_complex_kernel(const uint8_t* __restrict__ src, int N, int64_t G, int mode,
-                                      cplx<R>* __restrict__ dst) {
+__global__ void s_to_complex_kernel(const uint8_t* __restrict__ src, int N, int64_t G, int mode,
+                                    cplx<R>* __restrict__ dst) {
   const int64_t n2 = (int64_t)N * N;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < G * n2;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = idx / n2;
     const int e = (int)(idx % n2);
     const int i = e / N, j = e % N;
-    const float2 v = mode == 0 ? emb_get(src + c * state_bytes(N), N, j, i)
-                               : emb_get(src + c * state_bytes(N), N, i, j);
-    dst[idx] = cmake<R>((R)v.x, (R)v.y);
+    const uint8_t* st = src + c * state_bytes(N);
+    const int row = mode == 0 ? j : i, col = mode == 0 ? i : j;
+    dst[idx] = cmake<R>((R)s_val(st, N, row, col), (R)s_val(st, N, row, N + col));
   }
 }
 
-__global__ void emb_identity_kernel(uint8_t* __restrict__ dst, int N, int64_t G) {
-  // Emb(I) = I_{2N}: one granule of 8 per thread
-  const int64_t per = (int64_t)2 * N * (2 * N / 8);
+// S of the identity: one granule of 8 per thread
+__global__ void s_identity_kernel(uint8_t* __restrict__ dst, int N, int64_t G) {
+  const int64_t per = (int64_t)N * (2 * N / 8);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < G * per;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = idx / per;
@@ -173,284 +187,462 @@ __global__ void emb_identity_kernel(uint8_t* __restrict__ dst, int N, int64_t G)
       w[p] = (uint32_t)0x3C00u << (16 * hp);
     }
     uint8_t* st = dst + c * state_bytes(N);
-    const uint32_t o = emb_off(N, row, k0);
+    const uint32_t o = s_off(N, row, k0);
     *reinterpret_cast<uint4*>(st + o) = make_uint4(w[0], w[1], w[2], w[3]);
     *reinterpret_cast<uint4*>(st + o + kHalf) = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
-// ---------------------------------------------------------------------------- the step kernel
-struct StepArgs {
-  const uint8_t* cur;
-  uint8_t* next;
+// ---------------------------------------------------------------------------- the sweep kernel
+struct SweepArgs {
+  uint8_t* buf0;          // states at even steps, chains x state_bytes
+  uint8_t* buf1;          // states at odd steps
   const uint8_t* planes;
   const int32_t* q;
   int64_t M;
   int K, d, base;
   int64_t levels;
-  int64_t S, seg_len, F, t;
-  int64_t gmod;       // chain c uses the factor of chain c % gmod
-  int reverse;
+  int64_t S, seg_len, F;
+  int64_t chains;         // forward: G; reverse: 2G (V chains, then R chains)
+  int64_t gmod;           // chain c multiplies by the factor of chain c % gmod
+  int64_t steps;
+  int reverse;            // 0: factors in order from the segment start; 1: from its end
+  int trace;              // reverse sweep of the gradient: traces and V/R coupling
   int N;
+  uint32_t* cnt;          // [chains][N / 128] finished units per row block
+  uint32_t* ticket;
+  int* abort;
+  const int32_t* hk_ptr;
+  const int32_t* hk_col;
+  const int32_t* hk_row;
+  const double2* hk_val;
+  double2* acc;           // [gmod][seg_len] trace accumulators
   int64_t* status;
 };
 
-__device__ __forceinline__ int64_t step_entry(const StepArgs& a, int64_t g) {
+struct Unit {
+  int64_t t, c;
+  int rt, h, nb;
+};
+
+__device__ __forceinline__ Unit decode(const SweepArgs& a, int64_t tk, int RT, int TNB) {
+  const int per_chain = RT * 2 * TNB;
+  const int64_t per_step = a.chains * per_chain;
+  Unit u;
+  u.t = tk / per_step;
+  const int64_t r = tk - u.t * per_step;
+  u.c = r / per_chain;
+  const int r2 = (int)(r - u.c * per_chain);
+  u.rt = r2 / (2 * TNB);
+  const int r3 = r2 % (2 * TNB);
+  u.h = r3 / TNB;
+  u.nb = r3 % TNB;
+  return u;
+}
+
+// table entry multiplied at step t of chain g (or -1 past its segment); k and whether
+// the factor is its term's last digit (where the gradient needs a trace)
+__device__ __forceinline__ int64_t factor_entry(const SweepArgs& a, int64_t g, int64_t t, int& k, bool& last) {
   const int64_t u = g / a.S, s = g % a.S;
   const int64_t f0 = s * a.seg_len;
   int64_t f1 = f0 + a.seg_len;
   if (f1 > a.F) f1 = a.F;
-  const int64_t f = a.reverse ? f1 - 1 - a.t : f0 + a.t;
+  const int64_t f = a.reverse ? f1 - 1 - t : f0 + t;
+  k = 0;
+  last = false;
   if (f < f0 || f >= f1) return -1;
   const int64_t kd = (int64_t)a.K * a.d;
   const int64_t n = f / kd;
   const int r = (int)(f - n * kd);
-  const int k = r / a.d, j = r - k * a.d;
+  k = r / a.d;
+  const int j = r - k * a.d;
+  last = j == a.d - 1;
   int32_t qv = a.q[(u * a.M + n) * a.K + k];
   if (qv < 0 || qv >= a.levels) qv = 0;
   for (int i = 0; i < j; ++i) qv /= a.base;
   return (int64_t)(k * a.d + j) * a.base + qv % a.base;
 }
 
-__global__ void __launch_bounds__(192, 1) tc_large_step_kernel(StepArgs a) {
-  const int N = a.N;
-  const int KT = 2 * N / 64, TM = 2 * N / 128, TN = N / 128;
-  const int64_t c = blockIdx.x / (TM * TN);
-  const int rem = (int)(blockIdx.x % (TM * TN));
-  const int rt = rem / TN, nt = rem % TN;
-  const int64_t e = step_entry(a, c % a.gmod);
-  const uint8_t* Yc = a.cur + c * state_bytes(N);
-  uint8_t* Yn = a.next + c * state_bytes(N);
-  if (e < 0) {
-    // chain finished its segment: carry this tile's destinations over unchanged
-    for (int idx = threadIdx.x; idx < 128 * 16; idx += blockDim.x) {
-      const int r = idx >> 4, gq = idx & 15;
-      const int R = rt * 128 + r, kcol = nt * 128 + 8 * gq;
-      const int Rm = R < N ? R + N : R - N;
-      const uint32_t od = emb_off(N, R, kcol), om = emb_off(N, Rm, N + kcol);
-      *reinterpret_cast<uint4*>(Yn + od) = *reinterpret_cast<const uint4*>(Yc + od);
-      *reinterpret_cast<uint4*>(Yn + od + kHalf) = *reinterpret_cast<const uint4*>(Yc + od + kHalf);
-      *reinterpret_cast<uint4*>(Yn + om) = *reinterpret_cast<const uint4*>(Yc + om);
-      *reinterpret_cast<uint4*>(Yn + om + kHalf) = *reinterpret_cast<const uint4*>(Yc + om + kHalf);
-    }
-    return;
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// false on time-out or when the sweep was aborted
+__device__ bool wait_count(const uint32_t* cnt, uint32_t target, const int* abort) {
+  for (uint32_t i = 0; i < kSpin; ++i) {
+    if (ld_acquire(cnt) >= target) return true;
+    if ((i & 63) == 63 && ld_relaxed(abort)) return false;
+    __nanosleep(64);
   }
+  return false;
+}
+
+// mbarrier wait that also gives up once the CTA or the sweep was aborted
+__device__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* local_abort, const int* abort) {
+  for (uint32_t i = 0; i < kLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 1023) == 1023 && (*local_abort || ld_relaxed(abort))) return false;
+  }
+  return false;
+}
+
+// one row of S (complex row x of Y) into shared memory as FP32 real and imaginary parts
+__device__ __forceinline__ void row_to_smem(const uint8_t* st, int N, int x, float* re, float* im, int lane) {
+  for (int g = lane; g < 2 * N / 8; g += 32) {
+    const int kcol = 8 * g;
+    const uint32_t o = s_off(N, x, kcol);
+    const uint4 hv = __ldcg(reinterpret_cast<const uint4*>(st + o));
+    const uint4 lv = __ldcg(reinterpret_cast<const uint4*>(st + o + kHalf));
+    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+    float* d = kcol < N ? re + kcol : im + (kcol - N);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hw[p]));
+      const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&lw[p]));
+      d[2 * p] = fmaf(b.x, kInv, a.x);
+      d[2 * p + 1] = fmaf(b.y, kInv, a.y);
+    }
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(192, 1) sweep_kernel(SweepArgs a) {
+  using Gm = Geo<NB>;
+  constexpr int kStages = Gm::kStages, kBufs = Gm::kBufs;
+  const int N = a.N;
+  const int KT = 2 * N / 64, RT = N / 128, TNB = N / NB;
+  const int64_t total = a.steps * a.chains * (int64_t)(RT * 2 * TNB);
+  const size_t sb = state_bytes(N);
+  const int TW = trace_warps(N);
+
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * 2 * kTile);
+  uint8_t* ring = smem;
+  float* trace_rows = reinterpret_cast<float*>(smem + Gm::kRing);
+  uint8_t* ctrl = smem + Gm::kRing + (size_t)TW * 16 * N;  // 1024-byte aligned
+  int4* uq = reinterpret_cast<int4*>(ctrl);                  // {ticket, entry, trace k, -}
+  uint64_t* full = reinterpret_cast<uint64_t*>(ctrl + kQ * sizeof(int4));
   uint64_t* empty = full + kStages;
   uint64_t* mma_done = empty + kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  uint64_t* tmem_empty = mma_done + kBufs;
+  uint64_t* uq_full = tmem_empty + kBufs;
+  uint64_t* uq_empty = uq_full + kQ;
+  uint64_t* drain = uq_empty + kQ;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_local = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(mma_done, 1);
-    *abort_flag = 0;
+    for (int b = 0; b < kBufs; ++b) {
+      mbar_init(&mma_done[b], 1);
+      mbar_init(&tmem_empty[b], 4);
+    }
+    for (int i = 0; i < kQ; ++i) {
+      mbar_init(&uq_full[i], 1);
+      mbar_init(&uq_empty[i], 5);
+    }
+    mbar_init(drain, 1);
+    *abort_local = 0;
     fence_mbarrier_init();
   }
-  if (warp == 0) tmem_alloc(tmem_slot, 256);
+  if (warp == 0) tmem_alloc(tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  auto fail = [&]() {
+    *abort_local = 1;
+    atomicExch(a.abort, 1);
+  };
+
   if (warp == 4) {
+    // ------------------------------------------------------------------ producer
     if (lane == 0) {
-      const uint8_t* Bbase = a.planes + (size_t)e * entry_bytes(N);
-      for (int kt = 0; kt < KT; ++kt) {
-        const uint32_t s = kt % kStages, u = kt / kStages;
-        if (u > 0 && !mbar_wait_bounded_n(&empty[s], (u - 1) & 1, kLimit)) {
-          *abort_flag = 1;
+      uint32_t kit = 0, ui = 0;
+      for (;;) {
+        int32_t tk = -1, e = -1, trk = -1;
+        Unit u{};
+        if (!*abort_local && !ld_relaxed(a.abort)) {
+          const uint32_t got = atomicAdd(a.ticket, 1u);
+          if ((int64_t)got < total) tk = (int32_t)got;
+        }
+        if (tk >= 0) {
+          u = decode(a, tk, RT, TNB);
+          int k;
+          bool last;
+          e = (int32_t)factor_entry(a, u.c % a.gmod, u.t, k, last);
+          if (a.trace && e >= 0 && last) trk = k;
+          // this row block's previous step (and, in the reverse sweep, its partner's)
+          const uint32_t target = (uint32_t)(u.t * 2 * TNB);
+          bool ok = wait_count(&a.cnt[u.c * RT + u.rt], target, a.abort);
+          if (ok && a.trace) {
+            const int64_t partner = u.c < a.gmod ? u.c + a.gmod : u.c - a.gmod;
+            ok = wait_count(&a.cnt[partner * RT + u.rt], target, a.abort);
+          }
+          if (!ok) {
+            fail();
+            tk = -1;
+          }
+        }
+        const uint32_t slot = ui % kQ;
+        if (ui >= kQ && !wait_bar(&uq_empty[slot], ((ui / kQ) - 1) & 1, abort_local, a.abort)) {
+          fail();
           break;
         }
-        uint8_t* dA = smem + s * 2 * kTile;
-        uint8_t* dB = dA + kTile;
-        const uint8_t* sA = Yc + (size_t)(rt * KT + kt) * kTile;
-        const uint8_t* sB = Bbase + (size_t)(nt * KT + kt) * kTile;
-        mbar_arrive_expect_tx(&full[s], 2 * kTile);
-        bulk_load(dA, sA, kHalf, &full[s]);
-        bulk_load(dA + kHalf, sA + kHalf, kHalf, &full[s]);
-        bulk_load(dB, sB, kHalf, &full[s]);
-        bulk_load(dB + kHalf, sB + kHalf, kHalf, &full[s]);
+        uq[slot] = make_int4(tk, e, trk, 0);
+        mbar_arrive(&uq_full[slot]);
+        ++ui;
+        if (tk < 0) break;
+        if (e < 0) continue;
+        fence_proxy_async_global();
+        const uint8_t* Sc = ((u.t & 1) ? a.buf1 : a.buf0) + u.c * sb;
+        const uint8_t* Bb = a.planes + (size_t)e * entry_bytes(N) + (size_t)u.nb * KT * Gm::kB;
+        bool ok = true;
+        for (int kt = 0; kt < KT && ok; ++kt, ++kit) {
+          const uint32_t s = kit % kStages;
+          if (kit >= (uint32_t)kStages &&
+              !wait_bar(&empty[s], ((kit / kStages) - 1) & 1, abort_local, a.abort)) {
+            fail();
+            ok = false;
+            break;
+          }
+          const int kta = u.h ? (kt + KT / 2) % KT : kt;
+          uint8_t* dst = ring + s * Gm::kStage;
+          const uint8_t* sa = Sc + ((size_t)u.rt * KT + kta) * kTile;
+          const uint8_t* sbp = Bb + (size_t)kt * Gm::kB;
+          mbar_arrive_expect_tx(&full[s], Gm::kStage);
+          bulk_load(dst, sa, kHalf, &full[s]);
+          bulk_load(dst + kHalf, sa + kHalf, kHalf, &full[s]);
+#pragma unroll
+          for (uint32_t o = 0; o < Gm::kB; o += kHalf) bulk_load(dst + kTile + o, sbp + o, kHalf, &full[s]);
+        }
+        if (!ok) break;
+      }
+      if (*abort_local) {
+        // let the copies already issued land before the CTA leaves
+        const uint32_t n = kit < (uint32_t)kStages ? kit : (uint32_t)kStages;
+        for (uint32_t i = 0; i < n; ++i) {
+          const uint32_t it = kit - 1 - i;
+          mbar_wait_bounded_n(&full[it % kStages], (it / kStages) & 1, kLimit);
+        }
       }
     }
   } else if (warp == 5) {
+    // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      for (int kt = 0; kt < KT; ++kt) {
-        const uint32_t s = kt % kStages, u = kt / kStages;
-        if (*abort_flag || !mbar_wait_bounded_n(&full[s], u & 1, kLimit)) {
-          *abort_flag = 1;
+      uint32_t kit = 0, ui = 0, use = 0;
+      for (;;) {
+        const uint32_t slot = ui % kQ;
+        if (!wait_bar(&uq_full[slot], (ui / kQ) & 1, abort_local, a.abort)) {
+          fail();
+          break;
+        }
+        const int4 m = uq[slot];
+        mbar_arrive(&uq_empty[slot]);
+        ++ui;
+        if (m.x < 0) break;
+        if (m.y < 0) continue;
+        const Unit u = decode(a, m.x, RT, TNB);
+        const uint32_t b = use % kBufs;
+        if (use >= (uint32_t)kBufs &&
+            !wait_bar(&tmem_empty[b], ((use / kBufs) - 1) & 1, abort_local, a.abort)) {
+          fail();
           break;
         }
         tc_fence_after();
-        const uint32_t a_hi = smem_u32(smem + s * 2 * kTile);
-        const uint32_t a_lo = a_hi + kHalf;
-        const uint32_t b0 = a_hi + kTile;       // 256 rows: hi then lo
+        const uint32_t d = tmem + b * Gm::kAcc;
+        bool ok = true;
+        for (int kt = 0; kt < KT; ++kt, ++kit) {
+          const uint32_t s = kit % kStages;
+          if (!wait_bar(&full[s], (kit / kStages) & 1, abort_local, a.abort)) {
+            fail();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t neg = (u.h == 0 && kt >= KT / 2) ? kNegB : 0u;
+          const uint32_t a_hi = smem_u32(ring + s * Gm::kStage);
+          const uint32_t a_lo = a_hi + kHalf;
+          const uint32_t b_hi = a_hi + kTile;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint32_t o = (uint32_t)kk * 32u;
-          mma_f16(tmem, smem_desc_sw128(a_hi + o), smem_desc_sw128(b0 + o), kIdesc256,
-                  (kt | kk) ? 1u : 0u);
-          mma_f16(tmem + 128, smem_desc_sw128(a_lo + o), smem_desc_sw128(b0 + o), kIdesc128, 1u);
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t o = (uint32_t)kk * 32u;
+            const uint32_t first = (kt | kk) ? 1u : 0u;
+            if (NB == 256) {
+              const uint32_t b_lo = b_hi + NB * 128;
+              mma_f16(d, smem_desc_sw128(a_hi + o), smem_desc_sw128(b_hi + o), kIdesc256 | neg, first);
+              mma_f16(d + 256, smem_desc_sw128(a_hi + o), smem_desc_sw128(b_lo + o), kIdesc256 | neg, first);
+              mma_f16(d + 256, smem_desc_sw128(a_lo + o), smem_desc_sw128(b_hi + o), kIdesc256 | neg, 1u);
+            } else {
+              // B rows 0..255 = hi then lo: D[0:128] = A_hi B_hi, D[128:256] = A_hi B_lo
+              mma_f16(d, smem_desc_sw128(a_hi + o), smem_desc_sw128(b_hi + o), kIdesc256 | neg, first);
+              mma_f16(d + 128, smem_desc_sw128(a_lo + o), smem_desc_sw128(b_hi + o), kIdesc128 | neg, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
         }
-        mma_commit(&empty[s]);
+        if (!ok) break;
+        mma_commit(&mma_done[b]);
+        ++use;
       }
-      mma_commit(mma_done);
+      // nothing may be in flight in tensor memory when it is released
+      mma_commit(drain);
+      mbar_wait_bounded_n(drain, 0, kLimit);
     }
   } else {
-    // epilogue: warps 0-3, thread = row of the output tile
-    const int r = threadIdx.x;
-    const int R = rt * 128 + r;
-    const int Rm = R < N ? R + N : R - N;
-    const uint32_t neg = R < N ? 0u : 0x80008000u;
-    bool ok = mbar_wait_bounded_n(mma_done, 0, kLimit) && !*abort_flag;
-    ok = __all_sync(0xffffffffu, ok);
-    if (!ok) {
-      *abort_flag = 1;
-    } else {
-      tc_fence_after();
-      const uint32_t d1 = tmem + ((uint32_t)(32 * warp) << 16);
-#pragma unroll 1
-      for (int j = 0; j < 4; ++j) {
-        uint32_t ra[32], rb[32];
-        tmem_ld32(d1 + 32 * j, ra);
-        tmem_ld32(d1 + 128 + 32 * j, rb);
-        tmem_wait_ld();
-        float z[32];
+    // ------------------------------------------------------------------ epilogue (warps 0-3)
+    uint32_t ui = 0, use = 0;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    for (;;) {
+      const uint32_t slot = ui % kQ;
+      if (threadIdx.x == 0 && !wait_bar(&uq_full[slot], (ui / kQ) & 1, abort_local, a.abort)) fail();
+      named_barrier(1, 128);
+      if (*abort_local) break;
+      const int4 m = uq[slot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&uq_empty[slot]);
+      ++ui;
+      if (m.x < 0) break;
+      const Unit u = decode(a, m.x, RT, TNB);
+      const uint8_t* cur = ((u.t & 1) ? a.buf1 : a.buf0);
+      uint8_t* nxt = ((u.t & 1) ? a.buf0 : a.buf1);
+      if (m.z >= 0 && warp < TW) {
+        // rows of this unit's slice of Tr(H_k V^dag R) at step t (V chain g, R chain gmod + g)
+        const int64_t g = u.c % a.gmod;
+        const int li = (u.c >= a.gmod ? 2 * TNB : 0) + u.h * TNB + u.nb;
+        const int rs = 128 / (4 * TNB);
+        const uint8_t* Vs = cur + g * sb;
+        const uint8_t* Rs = cur + (a.gmod + g) * sb;
+        float* vre = trace_rows + (size_t)warp * 4 * N;
+        float* vim = vre + N;
+        float* rre = vim + N;
+        float* rim = rre + N;
+        const int k = m.z;
+        const int p0 = a.hk_ptr[k * (N + 1)], p1 = a.hk_ptr[k * (N + 1) + N];
+        double sr = 0.0, si = 0.0;
+        for (int r = warp; r < rs; r += TW) {
+          const int x = u.rt * 128 + li * rs + r;
+          row_to_smem(Vs, N, x, vre, vim, lane);
+          row_to_smem(Rs, N, x, rre, rim, lane);
+          __syncwarp();
+          float tr = 0.0f, ti = 0.0f;
+          for (int e = p0 + lane; e < p1; e += 32) {
+            const int i = a.hk_row[e], cc = a.hk_col[e];
+            const double2 hv = a.hk_val[e];
+            const float hx = (float)hv.x, hy = (float)hv.y;
+            // conj(V[x][cc]) R[x][i]
+            const float va = vre[cc], vb = vim[cc], ra = rre[i], rb = rim[i];
+            const float pr = fmaf(va, ra, vb * rb), pi = fmaf(va, rb, -vb * ra);
+            tr = fmaf(hx, pr, fmaf(-hy, pi, tr));
+            ti = fmaf(hx, pi, fmaf(hy, pr, ti));
+          }
 #pragma unroll
-        for (int i = 0; i < 32; ++i) z[i] = fmaf(__uint_as_float(rb[i]), kInv, __uint_as_float(ra[i]));
-#pragma unroll
-        for (int gq = 0; gq < 4; ++gq) {
-          uint32_t h[4], l[4];
-#pragma unroll
-          for (int p = 0; p < 4; ++p) split_pair(z[8 * gq + 2 * p], z[8 * gq + 2 * p + 1], h[p], l[p]);
-          const int kcol = nt * 128 + 32 * j + 8 * gq;
-          const uint32_t od = emb_off(N, R, kcol), om = emb_off(N, Rm, N + kcol);
-          *reinterpret_cast<uint4*>(Yn + od) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(Yn + od + kHalf) = make_uint4(l[0], l[1], l[2], l[3]);
-          *reinterpret_cast<uint4*>(Yn + om) = make_uint4(h[0] ^ neg, h[1] ^ neg, h[2] ^ neg, h[3] ^ neg);
-          *reinterpret_cast<uint4*>(Yn + om + kHalf) =
-              make_uint4(l[0] ^ neg, l[1] ^ neg, l[2] ^ neg, l[3] ^ neg);
+          for (int off = 16; off > 0; off >>= 1) {
+            tr += __shfl_xor_sync(0xffffffffu, tr, off);
+            ti += __shfl_xor_sync(0xffffffffu, ti, off);
+          }
+          sr += (double)tr;
+          si += (double)ti;
+          __syncwarp();
         }
+        if (lane == 0) {
+          double2* slot_acc = a.acc + g * a.seg_len + u.t;
+          atomicAdd(&slot_acc->x, sr);
+          atomicAdd(&slot_acc->y, si);
+        }
+      }
+      const size_t region = ((size_t)u.rt * KT + (size_t)(u.h * N + u.nb * NB) / 64) * kTile;
+      if (m.y < 0) {
+        // past the end of its segment: carry the region over unchanged
+        const uint4* src = reinterpret_cast<const uint4*>(cur + u.c * sb + region);
+        uint4* dst = reinterpret_cast<uint4*>(nxt + u.c * sb + region);
+        for (int i = threadIdx.x; i < (int)((NB / 64) * kTile / 16); i += 128) dst[i] = __ldcg(src + i);
+      } else {
+        const uint32_t b = use % kBufs;
+        if (!wait_bar(&mma_done[b], (use / kBufs) & 1, abort_local, a.abort)) {
+          fail();
+        } else {
+          tc_fence_after();
+          const uint32_t d1 = tmem + lane_base + b * Gm::kAcc, d2 = d1 + NB;
+          const int R = u.rt * 128 + 32 * warp + lane;
+          uint8_t* out = nxt + u.c * sb;
+          const int kc0 = u.h * N + u.nb * NB;
+#pragma unroll 1
+          for (int ch = 0; ch < NB / 32; ch += 2) {
+            uint32_t ra0[32], rb0[32], ra1[32], rb1[32];
+            tmem_ld32(d1 + 32 * ch, ra0);
+            tmem_ld32(d2 + 32 * ch, rb0);
+            tmem_ld32(d1 + 32 * ch + 32, ra1);
+            tmem_ld32(d2 + 32 * ch + 32, rb1);
+            tmem_wait_ld();
+            if (ch + 2 >= NB / 32) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&tmem_empty[b]);
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              const uint32_t* ra = half ? ra1 : ra0;
+              const uint32_t* rb = half ? rb1 : rb0;
+#pragma unroll
+              for (int gq = 0; gq < 4; ++gq) {
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                  const int i0 = 8 * gq + 2 * p;
+                  split_pair(fmaf(__uint_as_float(rb[i0]), kInv, __uint_as_float(ra[i0])),
+                             fmaf(__uint_as_float(rb[i0 + 1]), kInv, __uint_as_float(ra[i0 + 1])), h[p], l[p]);
+                }
+                const uint32_t o = s_off(N, R, kc0 + 32 * (ch + half) + 8 * gq);
+                *reinterpret_cast<uint4*>(out + o) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4*>(out + o + kHalf) = make_uint4(l[0], l[1], l[2], l[3]);
+              }
+            }
+          }
+          ++use;
+        }
+      }
+      // publish: this unit's part of step t+1 is written
+      fence_proxy_async_global();
+      named_barrier(1, 128);
+      if (threadIdx.x == 0 && !*abort_local) {
+        __threadfence();
+        atomicAdd(&a.cnt[u.c * RT + u.rt], 1u);
       }
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (*abort_flag && threadIdx.x == 0 && a.status)
+  if (*abort_local && threadIdx.x == 0 && a.status)
     atomicAdd((unsigned long long*)&a.status[REDO_STATUS_TIMEOUT], 1ull);
-  if (warp == 0) tmem_dealloc(tmem, 256);
+  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-constexpr uint32_t kStepSmem = kStages * 2 * kTile + 1024 + 128;
-
-// ---------------------------------------------------------------------------- gradient traces
-// Tr(H_k V^dag R) = sum_x sum_{(i,c) in nz(H_k)} H[i][c] conj(V[x][c]) R[x][i]  (V = P^dag):
-// a sum over rows x of V and R, read straight from their embeddings (row x of Emb
-// holds Re(row x) in K columns 0..N-1; row N+x holds Im(row x)).  Grid (chain, row block):
-// each warp stages one row of V and of R in shared memory, its lanes walk the
-// nonzeros, and block partials are added into acc[g]; trace_finish_kernel turns
-// acc into dF/du and clears it.
-__device__ __forceinline__ void emb_row_to_smem(const uint8_t* st, int N, int x, float* re, float* im,
-                                                int lane) {
-  for (int g = lane; g < N / 8; g += 32) {
-    const uint32_t orr = emb_off(N, x, 8 * g), oi = emb_off(N, N + x, 8 * g);
-    const uint4 hr = *reinterpret_cast<const uint4*>(st + orr);
-    const uint4 lr = *reinterpret_cast<const uint4*>(st + orr + kHalf);
-    const uint4 hi = *reinterpret_cast<const uint4*>(st + oi);
-    const uint4 li = *reinterpret_cast<const uint4*>(st + oi + kHalf);
-    const uint32_t hrw[4] = {hr.x, hr.y, hr.z, hr.w}, lrw[4] = {lr.x, lr.y, lr.z, lr.w};
-    const uint32_t hiw[4] = {hi.x, hi.y, hi.z, hi.w}, liw[4] = {li.x, li.y, li.z, li.w};
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hrw[p]));
-      const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&lrw[p]));
-      const float2 c = __half22float2(*reinterpret_cast<const __half2*>(&hiw[p]));
-      const float2 d = __half22float2(*reinterpret_cast<const __half2*>(&liw[p]));
-      re[8 * g + 2 * p] = fmaf(b.x, kInv, a.x);
-      re[8 * g + 2 * p + 1] = fmaf(b.y, kInv, a.y);
-      im[8 * g + 2 * p] = fmaf(d.x, kInv, c.x);
-      im[8 * g + 2 * p + 1] = fmaf(d.y, kInv, c.y);
-    }
-  }
-}
-
-constexpr int kTraceRows = 8;   // rows per block (one per warp)
-
-__global__ void __launch_bounds__(256) trace_emb_kernel(const uint8_t* __restrict__ V,
-                                                        const uint8_t* __restrict__ Rs, int N, int64_t S,
-                                                        int64_t seg_len, int64_t F, int64_t t, int K, int d,
-                                                        const int32_t* __restrict__ hk_ptr,
-                                                        const int32_t* __restrict__ hk_col,
-                                                        const int32_t* __restrict__ hk_row,
-                                                        const double2* __restrict__ hk_val,
-                                                        double2* __restrict__ acc) {
-  const int64_t g = blockIdx.x;
-  const int64_t s = g % S;
-  const int64_t f0 = s * seg_len;
-  int64_t f1 = f0 + seg_len;
-  if (f1 > F) f1 = F;
-  const int64_t f = f1 - 1 - t;
-  if (f < f0 || f >= f1) return;
-  const int64_t kd = (int64_t)K * d;
-  const int64_t n = f / kd;
-  const int rr = (int)(f - n * kd);
-  const int k = rr / d, j = rr - k * d;
-  if (j != d - 1) return;
-  extern __shared__ float rows[];            // per warp: Vre, Vim, Rre, Rim (N floats each)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* vre = rows + (size_t)warp * 4 * N;
-  float* vim = vre + N;
-  float* rre = vim + N;
-  float* rim = rre + N;
-  const int x = blockIdx.y * kTraceRows + warp;
-  const uint8_t* Vg = V + g * state_bytes(N);
-  const uint8_t* Rg = Rs + g * state_bytes(N);
-  emb_row_to_smem(Vg, N, x, vre, vim, lane);
-  emb_row_to_smem(Rg, N, x, rre, rim, lane);
-  __syncwarp();
-  const int p0 = hk_ptr[k * (N + 1)], p1 = hk_ptr[k * (N + 1) + N];
-  double re = 0.0, im = 0.0;
-  for (int e = p0 + lane; e < p1; e += 32) {
-    const int i = hk_row[e], c = hk_col[e];
-    // conj(V[x][c]) R[x][i]
-    const float a = vre[c], b = vim[c], cr = rre[i], ci = rim[i];
-    const float pr = a * cr + b * ci, pi = a * ci - b * cr;
-    const double2 h = hk_val[e];
-    re += h.x * pr - h.y * pi;
-    im += h.x * pi + h.y * pr;
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    re += __shfl_down_sync(0xffffffffu, re, off);
-    im += __shfl_down_sync(0xffffffffu, im, off);
-  }
-  __shared__ double sre[8], sim[8];
-  if (lane == 0) {
-    sre[warp] = re;
-    sim[warp] = im;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tr = 0.0, ti = 0.0;
-    for (int w = 0; w < 8; ++w) {
-      tr += sre[w];
-      ti += sim[w];
-    }
-    atomicAdd(&acc[g].x, tr);
-    atomicAdd(&acc[g].y, ti);
-  }
-}
-
-__global__ void trace_finish_kernel(double2* __restrict__ acc, int64_t G, int64_t S, int64_t seg_len,
-                                    int64_t F, int64_t t, int K, int d, const double2* __restrict__ tau,
-                                    double scale, int64_t M, double* __restrict__ grad) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= G) return;
+// dF/du from the trace accumulators: one thread per (chain, sweep step)
+__global__ void trace_finish_kernel(const double2* __restrict__ acc, int64_t G, int64_t S, int64_t seg_len,
+                                    int64_t F, int K, int d, const double2* __restrict__ tau, double scale,
+                                    int64_t M, double* __restrict__ grad) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= G * seg_len) return;
+  const int64_t g = idx / seg_len, t = idx % seg_len;
   const int64_t u = g / S, s = g % S;
   const int64_t f0 = s * seg_len;
   int64_t f1 = f0 + seg_len;
@@ -462,10 +654,9 @@ __global__ void trace_finish_kernel(double2* __restrict__ acc, int64_t G, int64_
   const int rr = (int)(f - n * kd);
   const int k = rr / d, j = rr - k * d;
   if (j != d - 1) return;
-  const double2 T = acc[g];
+  const double2 T = acc[idx];
   const double2 tu = tau[u];
   grad[(u * M + n) * K + k] = scale * (tu.x * T.y - tu.y * T.x);
-  acc[g] = make_double2(0.0, 0.0);
 }
 
 static unsigned blocks_for(int64_t n) {
@@ -474,12 +665,23 @@ static unsigned blocks_for(int64_t n) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-static cudaError_t step(const redo_table* t, const int32_t* q, const ChainPlan& p, int64_t tt, int reverse,
-                        int64_t chains, int64_t gmod, const uint8_t* planes, const uint8_t* cur,
-                        uint8_t* next, int64_t* status, cudaStream_t s) {
-  StepArgs a;
-  a.cur = cur;
-  a.next = next;
+static size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t sync_bytes(int N, int64_t chains) { return up(((size_t)chains * (N / 128) + 2) * sizeof(uint32_t)); }
+
+// Runs `p.seg_len` steps of `chains` chains from b0; the result is in b0 (even count) or b1.
+static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan& p, int64_t chains,
+                         int reverse, bool trace, const uint8_t* planes, uint8_t* b0, uint8_t* b1,
+                         uint32_t* sync, double2* acc, int64_t* status, cudaStream_t s) {
+  const int N = t->N, NB = t->tc_nb, RT = N / 128, TNB = N / NB;
+  const int64_t total = p.seg_len * chains * (int64_t)(RT * 2 * TNB);
+  if (total == 0) return cudaSuccess;
+  if (total >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(sync, 0, ((size_t)chains * RT + 2) * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  SweepArgs a;
+  a.buf0 = b0;
+  a.buf1 = b1;
   a.planes = planes;
   a.q = q;
   a.M = p.M;
@@ -490,13 +692,32 @@ static cudaError_t step(const redo_table* t, const int32_t* q, const ChainPlan& 
   a.S = p.S;
   a.seg_len = p.seg_len;
   a.F = p.F;
-  a.t = tt;
-  a.gmod = gmod;
+  a.chains = chains;
+  a.gmod = trace ? chains / 2 : chains;
+  a.steps = p.seg_len;
   a.reverse = reverse;
-  a.N = t->N;
+  a.trace = trace ? 1 : 0;
+  a.N = N;
+  a.cnt = sync;
+  a.ticket = sync + (size_t)chains * RT;
+  a.abort = reinterpret_cast<int*>(sync + (size_t)chains * RT + 1);
+  a.hk_ptr = t->hk_ptr;
+  a.hk_col = t->hk_col;
+  a.hk_row = t->hk_row;
+  a.hk_val = t->hk_val;
+  a.acc = acc;
   a.status = status;
-  const int64_t blocks = chains * (2 * t->N / 128) * (t->N / 128);
-  tc_large_step_kernel<<<(unsigned)blocks, 192, kStepSmem, s>>>(a);
+  const size_t smem = sweep_smem(NB, N);
+  int64_t grid = total < t->num_sms ? total : t->num_sms;
+  if (NB == 256) {
+    if ((e = cudaFuncSetAttribute(sweep_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    sweep_kernel<256><<<(unsigned)grid, 192, smem, s>>>(a);
+  } else {
+    if ((e = cudaFuncSetAttribute(sweep_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    sweep_kernel<128><<<(unsigned)grid, 192, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -504,67 +725,63 @@ static cudaError_t step(const redo_table* t, const int32_t* q, const ChainPlan& 
 
 using namespace tcl;
 
+int tc_large_nb(int N) {
+  if (N < 256) return 128;
+  const char* v = std::getenv("REDO_TCL_NB");
+  return (v && std::strcmp(v, "128") == 0) ? 128 : 256;
+}
+
 size_t tc_large_planes_bytes(const redo_table* t) { return 2 * (size_t)t->entries * entry_bytes(t->N); }
 
 cudaError_t launch_build_tc_large_planes(const redo_table* t, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(tc_large_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kStepSmem);
-  if (e != cudaSuccess) return e;
-  const int64_t tiles = t->entries * (t->N / 128) * (2 * t->N / 64);
+  const int NB = t->tc_nb;
+  const int64_t tiles = t->entries * (t->N / NB) * (2 * t->N / 64);
   uint8_t* rows = (uint8_t*)t->tc_planes;
   uint8_t* cols = rows + (size_t)t->entries * entry_bytes(t->N);
-  build_large_planes_kernel<<<(unsigned)tiles, 256, 0, s>>>(t->T64, t->N, 0, rows);
-  build_large_planes_kernel<<<(unsigned)tiles, 256, 0, s>>>(t->T64, t->N, 1, cols);
+  build_planes_kernel<<<(unsigned)tiles, 256, 0, s>>>(t->T64, t->N, NB, 0, rows);
+  build_planes_kernel<<<(unsigned)tiles, 256, 0, s>>>(t->T64, t->N, NB, 1, cols);
   return cudaGetLastError();
 }
 
 size_t tc_large_prop_workspace(const redo_table* t, const ChainPlan& p, bool reunit) {
-  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  return large_prop_workspace(t, p, REDO_FP32, reunit) + 2 * up((size_t)p.B * p.S * state_bytes(t->N));
+  const size_t G = (size_t)p.B * p.S;
+  return large_prop_workspace(t, p, REDO_FP32, reunit) + 2 * up(G * state_bytes(t->N)) + sync_bytes(t->N, G);
 }
 
-// Segment products by tensor-core chains, then the FP32 re-unitarisation, combine and
+// Segment products by tensor-core sweeps, then the FP32 re-unitarisation, combine and
 // FP64 polar step of the SIMT large-N path.
 cudaError_t tc_large_propagate(const redo_table* t, const int32_t* q, const ChainPlan& p, bool reunit,
                                void* ws, void** result, int* result_prec, int64_t* status,
                                cudaStream_t s) {
-  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int N = t->N;
   const int64_t G = p.B * p.S;
   char* base = (char*)ws;
-  cudaError_t e = cudaFuncSetAttribute(tc_large_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kStepSmem);
-  if (e != cudaSuccess) return e;
   const size_t simt = large_prop_workspace(t, p, REDO_FP32, reunit);
   uint8_t* st0 = (uint8_t*)(base + simt);
   uint8_t* st1 = st0 + up((size_t)G * state_bytes(N));
-  emb_identity_kernel<<<blocks_for(G * 2 * N * (2 * N / 8)), 256, 0, s>>>(st0, N, G);
-  uint8_t* cur = st0;
-  uint8_t* nxt = st1;
-  const uint8_t* rows = (const uint8_t*)t->tc_planes;
-  for (int64_t tt = 0; tt < p.seg_len; ++tt) {
-    if ((e = step(t, q, p, tt, 0, G, G, rows, cur, nxt, status, s))) return e;
-    std::swap(cur, nxt);
-  }
+  uint32_t* sync = (uint32_t*)(st1 + up((size_t)G * state_bytes(N)));
+  s_identity_kernel<<<blocks_for(G * N * (2 * N / 8)), 256, 0, s>>>(st0, N, G);
+  cudaError_t e = sweep(t, q, p, G, 0, false, (const uint8_t*)t->tc_planes, st0, st1, sync, nullptr, status, s);
+  if (e != cudaSuccess) return e;
+  const uint8_t* res = (p.seg_len & 1) ? st1 : st0;
   // segment products X = Y^T into the SIMT path's segment buffer (its first region)
   float2* seg = (float2*)base;
-  emb_to_complex_kernel<float><<<blocks_for(G * (int64_t)N * N), 256, 0, s>>>(cur, N, G, 0, seg);
+  s_to_complex_kernel<float><<<blocks_for(G * (int64_t)N * N), 256, 0, s>>>(res, N, G, 0, seg);
   return large_finish_fp32(t, p, reunit, ws, result, result_prec, s);
 }
 
 size_t tc_large_grad_workspace(const redo_table* t, const ChainPlan& p) {
-  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t G = (size_t)p.B * p.S;
-  // + 2G embedded states x 2 (ping-pong) + 2G row-major FP32 transposes for the traces
-  return large_grad_workspace(t, p, REDO_FP32) + 4 * up(G * state_bytes(t->N)) + up(G * sizeof(double2));
+  // + 2 x 2G states (V and R, ping-pong) + trace accumulators + sweep counters
+  return large_grad_workspace(t, p, REDO_FP32) + 4 * up(G * state_bytes(t->N)) +
+         up(G * (size_t)p.seg_len * sizeof(double2)) + sync_bytes(t->N, 2 * G);
 }
 
-// Gradient: tensor-core forward segments, SIMT FP32 checkpoint/costate scans,
-// tensor-core reverse sweep of (V = P^dag, R) with embedded-state traces.
+// Gradient: tensor-core forward sweep, SIMT FP32 checkpoint/costate scans, tensor-core
+// reverse sweep of (V = P^dag, R) with the traces evaluated inside the sweep.
 cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, const double2* UT,
                           int tb, double* F_out, double* grad, void* ws, int64_t* status,
                           cudaStream_t s) {
-  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int N = t->N;
   const int64_t G = p.B * p.S;
   const int64_t n2 = (int64_t)N * N;
@@ -573,53 +790,28 @@ cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan
   const size_t sb = up((size_t)G * state_bytes(N));
   uint8_t* s0 = (uint8_t*)(base + simt);       // 2G states (V then R)
   uint8_t* s1 = s0 + 2 * sb;                   // ping
+  double2* acc = (double2*)(s1 + 2 * sb);
+  uint32_t* sync = (uint32_t*)((char*)acc + up(G * (size_t)p.seg_len * sizeof(double2)));
   const uint8_t* rows = (const uint8_t*)t->tc_planes;
   const uint8_t* cols = rows + (size_t)t->entries * entry_bytes(N);
-  cudaError_t e = cudaFuncSetAttribute(tc_large_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kStepSmem);
+  // forward segment products
+  s_identity_kernel<<<blocks_for(G * N * (2 * N / 8)), 256, 0, s>>>(s0, N, G);
+  cudaError_t e = sweep(t, q, p, G, 0, false, rows, s0, s1, sync, nullptr, status, s);
   if (e != cudaSuccess) return e;
-  // forward segment chains on s0 / s1 (first G states)
-  emb_identity_kernel<<<blocks_for(G * 2 * N * (2 * N / 8)), 256, 0, s>>>(s0, N, G);
-  uint8_t* cur = s0;
-  uint8_t* nxt = s1;
-  for (int64_t tt = 0; tt < p.seg_len; ++tt) {
-    if ((e = step(t, q, p, tt, 0, G, G, rows, cur, nxt, status, s))) return e;
-    std::swap(cur, nxt);
-  }
   float2* seg = (float2*)base;                 // the SIMT layout's segment region
-  emb_to_complex_kernel<float><<<blocks_for(G * n2), 256, 0, s>>>(cur, N, G, 0, seg);
+  s_to_complex_kernel<float><<<blocks_for(G * n2), 256, 0, s>>>((p.seg_len & 1) ? s1 : s0, N, G, 0, seg);
   float2 *Pck = nullptr, *Rck = nullptr;
   double2* tau = nullptr;
   if ((e = large_grad_scans_fp32(t, p, UT, tb, F_out, ws, &Pck, &Rck, &tau, s))) return e;
   if (p.M == 0) return cudaGetLastError();
   // reverse sweep: chains [0, G) hold V = P^dag, [G, 2G) hold R; both right-multiplied by A_f
-  emb_from_complex_kernel<float><<<blocks_for(G * N * (N / 8)), 256, 0, s>>>(Pck, N, G, 1, s0);
-  emb_from_complex_kernel<float><<<blocks_for(G * N * (N / 8)), 256, 0, s>>>(Rck, N, G, 2, s0 + sb);
-  cur = s0;
-  nxt = s1;
-  double2* acc = (double2*)(s1 + 2 * sb);      // per-chain trace accumulators
-  if ((e = cudaMemsetAsync(acc, 0, sizeof(double2) * G, s))) return e;
-  const size_t trace_smem = (size_t)kTraceRows * 4 * N * sizeof(float);
-  if ((e = cudaFuncSetAttribute(trace_emb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)trace_smem)))
-    return e;
+  s_from_complex_kernel<float><<<blocks_for(G * N * (N / 8)), 256, 0, s>>>(Pck, N, G, 1, s0);
+  s_from_complex_kernel<float><<<blocks_for(G * N * (N / 8)), 256, 0, s>>>(Rck, N, G, 2, s0 + G * state_bytes(N));
+  if ((e = cudaMemsetAsync(acc, 0, sizeof(double2) * G * p.seg_len, s))) return e;
+  if ((e = sweep(t, q, p, 2 * G, 1, true, cols, s0, s1, sync, acc, status, s))) return e;
   const double scale = 2.0 * t->dt / ((double)N * (double)N);
-  const int64_t kd = (int64_t)t->K * t->digits;
-  const bool aligned = (p.seg_len % kd) == 0;
-  for (int64_t tt = 0; tt < p.seg_len; ++tt) {
-    // traces are needed where the visited factor is a term's last digit; with
-    // segments aligned to whole steps that is every d-th sweep step for all chains
-    if (!aligned || ((p.seg_len - 1 - tt) % t->digits) == (t->digits - 1)) {
-      dim3 grid((unsigned)G, (unsigned)(N / kTraceRows));
-      trace_emb_kernel<<<grid, 256, trace_smem, s>>>(cur, cur + sb, N, p.S, p.seg_len, p.F, tt, t->K,
-                                                     t->digits, t->hk_ptr, t->hk_col, t->hk_row, t->hk_val,
-                                                     acc);
-      trace_finish_kernel<<<(unsigned)((G + 127) / 128), 128, 0, s>>>(acc, G, p.S, p.seg_len, p.F, tt, t->K,
-                                                                      t->digits, tau, scale, p.M, grad);
-    }
-    if ((e = step(t, q, p, tt, 1, 2 * G, G, cols, cur, nxt, status, s))) return e;
-    std::swap(cur, nxt);
-  }
+  trace_finish_kernel<<<(unsigned)((G * p.seg_len + 255) / 256), 256, 0, s>>>(
+      acc, G, p.S, p.seg_len, p.F, t->K, t->digits, tau, scale, p.M, grad);
   return cudaGetLastError();
 }
 

@@ -260,6 +260,7 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
   if (t->T32 && (e = launch_to_fp32(t->T64, t->T32, (int64_t)n2 * t->entries, s)) != cudaSuccess)
     return fail(cuda_error(e, "FP32 copy"));
   if (flags & REDO_TABLE_FP16X3) {
+    t->tc_nb = N > kSmallN ? tc_large_nb(N) : 0;
     t->tc_bytes = N > kSmallN ? tc_large_planes_bytes(t) : tc_planes_bytes(t);
     if ((e = cudaMalloc(&t->tc_planes, t->tc_bytes)) != cudaSuccess)
       return fail(set_error(REDO_ERR_OOM, "FP16x3 planes allocation: %s", cudaGetErrorString(e)));

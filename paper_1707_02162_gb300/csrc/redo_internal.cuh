@@ -56,6 +56,7 @@ struct redo_table {
   int64_t hk_nnz;
   void* tc_planes;            // tensor-core planes or nullptr
   size_t tc_bytes;
+  int tc_nb;                  // operand block height of the large-N planes (128 or 256)
   cudaStream_t build_stream;
   int num_sms;
 };
@@ -172,6 +173,7 @@ cudaError_t large_grad_scans_fp32(const redo_table* t, const ChainPlan& p, const
                                   double* F_out, void* ws, float2** Pck, float2** Rck, double2** tau,
                                   cudaStream_t s);
 // Tensor-core large-N path (kernels_tc_large.cu), split FP16, 128 <= N <= 1024.
+int tc_large_nb(int N);
 size_t tc_large_planes_bytes(const redo_table* t);
 cudaError_t launch_build_tc_large_planes(const redo_table* t, cudaStream_t s);
 size_t tc_large_prop_workspace(const redo_table* t, const ChainPlan& p, bool reunit);
