@@ -339,13 +339,15 @@ redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
  * Kernel timing for measurement.  While enabled, the library brackets each of
  * its kernel launches with CUDA events on the launching stream.  Phases:
  *   0 quantize, 1 table, 2 chain segments, 3 chain combine, 4 finalize,
- *   5 tensor-core chain, 6 re-unitarisation, 7 gradient.
+ *   5 tensor-core chain, 6 re-unitarisation, 7 gradient (all of it), and inside
+ *   the tensor-core gradient for N >= 128: 8 forward sweep, 9 checkpoint and
+ *   costate scans, 10 reverse sweep with traces.
  * redo_profile_read synchronises on the recorded events, adds each phase's
  * elapsed milliseconds and launch count into ms_out[p] / launches_out[p]
  * (arrays of n <= REDO_PROFILE_PHASES entries, either may be NULL) and clears
  * the record.  Not thread-safe; meant for benchmarks, not production.
  */
-#define REDO_PROFILE_PHASES 8
+#define REDO_PROFILE_PHASES 11
 redo_status redo_profile_enable(int32_t enable);
 redo_status redo_profile_read(double* ms_out, int64_t* launches_out, int32_t n);
 

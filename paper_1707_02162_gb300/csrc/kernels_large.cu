@@ -645,6 +645,14 @@ cudaError_t large_finish_fp32(const redo_table* t, const ChainPlan& p, bool reun
   return large_finish_t<float>(t, p, reunit, (char*)ws, result, result_prec, s);
 }
 
+// out[b] = in[2b + 1] in[2b] for b < count (FP32): joins pairs of consecutive sub-segment
+// products (the later one on the left) into segment products.
+cudaError_t large_pair_products_fp32(const float2* in, float2* out, int64_t count, int N, cudaStream_t s) {
+  const int64_t n2 = (int64_t)N * N;
+  DenseOps<float> op{in + n2, in, out, 2 * n2, 2 * n2, n2};
+  return cgemm<float, false>(op, count, N, 1.0f, 0.0f, s);
+}
+
 cudaError_t large_propagate(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
                             bool reunit, void* ws, void** result, int* result_prec,
                             int64_t* status, cudaStream_t s) {

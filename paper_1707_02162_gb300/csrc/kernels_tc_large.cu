@@ -11,7 +11,7 @@
 // instruction descriptor's negate-B bit.
 //
 // Operand planes.  Every table entry C is stored as tiles (nb, kt) holding NB rows of B^T
-// hi followed by the same NB rows lo, 64 K columns wide (NB = 256 for N >= 256, else 128),
+// hi followed by the same NB rows lo, 64 K columns wide (NB = 128, or 256 on request),
 // swizzled like the states.  Two sets exist: "row" planes with C = A^T (forward steps
 // X <- A X on Y = X^T) and "column" planes with C = A (reverse sweep V <- V A, R <- R A).
 //
@@ -23,8 +23,10 @@
 // CTA, one warp claims tickets, waits for the counters and streams the A (state) and B
 // (operand) tiles through a ring of bulk copies; one thread issues the MMAs into tensor
 // memory; four epilogue warps turn the FP32 accumulators into the next state's split
-// FP16 tiles.  In the reverse sweep of the gradient the epilogue warps also evaluate
-// Tr(H_k V^dag R) for a slice of rows of the current states while the MMAs run.
+// FP16 tiles.  In the reverse sweep of the gradient four more warps evaluate
+// Tr(H_k V^dag R) for a slice of rows of the current states while the MMAs run; they
+// count their finished slices per row block of a V/R pair, and a unit writes over the
+// states of step t-1 only once all of that step's slices of its rows are added.
 // Every wait is bounded; a timed-out CTA raises a sweep-wide abort flag and leaves.
 #include "redo_internal.cuh"
 #include "device_sync.cuh"
@@ -209,13 +211,16 @@ struct SweepArgs {
   int reverse;            // 0: factors in order from the segment start; 1: from its end
   int trace;              // reverse sweep of the gradient: traces and V/R coupling
   int N;
-  uint32_t* cnt;          // [chains][N / 128] finished units per row block
+  uint32_t* cnt;          // [chains][N / 128] units per row block whose outputs are written
+  uint32_t* tcnt;         // [gmod][N / 128] units per row block of a V/R pair whose trace part is added
   uint32_t* ticket;
   int* abort;
   const int32_t* hk_ptr;
   const int32_t* hk_col;
   const int32_t* hk_row;
   const double2* hk_val;
+  const int32_t* xmask;   // compact operators (one nonzero per row, at r ^ m_k) or nullptr
+  const float2* xval;
   double2* acc;           // [gmod][seg_len] trace accumulators
   int64_t* status;
 };
@@ -231,8 +236,10 @@ __device__ __forceinline__ Unit decode(const SweepArgs& a, int64_t tk, int RT, i
   Unit u;
   u.t = tk / per_step;
   const int64_t r = tk - u.t * per_step;
-  u.c = r / per_chain;
-  const int r2 = (int)(r - u.c * per_chain);
+  const int64_t ci = r / per_chain;
+  // the reverse sweep hands out the units of V chain g and R chain gmod + g together
+  u.c = a.trace ? ((ci & 1) ? a.gmod + (ci >> 1) : (ci >> 1)) : ci;
+  const int r2 = (int)(r - ci * per_chain);
   u.rt = r2 / (2 * TNB);
   const int r3 = r2 % (2 * TNB);
   u.h = r3 / TNB;
@@ -298,27 +305,169 @@ __device__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* local_abo
   return false;
 }
 
-// one row of S (complex row x of Y) into shared memory as FP32 real and imaginary parts
-__device__ __forceinline__ void row_to_smem(const uint8_t* st, int N, int x, float* re, float* im, int lane) {
-  for (int g = lane; g < 2 * N / 8; g += 32) {
-    const int kcol = 8 * g;
-    const uint32_t o = s_off(N, x, kcol);
-    const uint4 hv = __ldcg(reinterpret_cast<const uint4*>(st + o));
-    const uint4 lv = __ldcg(reinterpret_cast<const uint4*>(st + o + kHalf));
-    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
-    float* d = kcol < N ? re + kcol : im + (kcol - N);
+__device__ __forceinline__ void unpack8(const uint4& hv, const uint4& lv, float* d) {
+  const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hw[p]));
-      const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&lw[p]));
-      d[2 * p] = fmaf(b.x, kInv, a.x);
-      d[2 * p + 1] = fmaf(b.y, kInv, a.y);
+  for (int p = 0; p < 4; ++p) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hw[p]));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&lw[p]));
+    d[2 * p] = fmaf(b.x, kInv, a.x);
+    d[2 * p + 1] = fmaf(b.y, kInv, a.y);
+  }
+}
+
+// Part of Tr(H_k V^dag R) = sum_x sum_{(i,c) in nz(H_k)} H[i][c] conj(V[x][c]) R[x][i] over the
+// rows x0, x0 + stride, ... (nrows of them) of the states Vs and Rs, added into (sr, si).
+// Rows of V and R pass through shared memory as FP32 (vre, vim, rre, rim: N floats each);
+// a lane holds GPL = N / 128 granules of a row.  For GPL <= 2 the next row's loads are
+// issued before the current row's sum; larger rows are loaded in pieces of two granules.
+template <int GPL>
+__device__ __forceinline__ void trace_slice(const uint8_t* Vs, const uint8_t* Rs, int N, int x0, int nrows,
+                                            int stride, int p0, int p1, const int32_t* __restrict__ hk_row,
+                                            const int32_t* __restrict__ hk_col,
+                                            const double2* __restrict__ hk_val, float* vre, float* vim,
+                                            float* rre, float* rim, int lane, double& sr, double& si) {
+  constexpr int CH = GPL < 2 ? GPL : 2;           // granules per lane held in registers
+  constexpr bool kPrefetch = GPL <= 2;
+  uint4 vh[CH], vl[CH], rh[CH], rl[CH];
+  auto issue = [&](int x, int c0) {
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      const uint32_t o = s_off(N, x, 8 * (lane + 32 * (c0 + i)));
+      vh[i] = __ldcg(reinterpret_cast<const uint4*>(Vs + o));
+      vl[i] = __ldcg(reinterpret_cast<const uint4*>(Vs + o + kHalf));
+      rh[i] = __ldcg(reinterpret_cast<const uint4*>(Rs + o));
+      rl[i] = __ldcg(reinterpret_cast<const uint4*>(Rs + o + kHalf));
+    }
+  };
+  auto unpack = [&](int c0) {
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      const int kcol = 8 * (lane + 32 * (c0 + i));
+      const bool re = kcol < N;
+      unpack8(vh[i], vl[i], (re ? vre : vim) + (re ? kcol : kcol - N));
+      unpack8(rh[i], rl[i], (re ? rre : rim) + (re ? kcol : kcol - N));
+    }
+  };
+  if (kPrefetch && nrows > 0) issue(x0, 0);
+  for (int r = 0; r < nrows; ++r) {
+    if (kPrefetch) {
+      unpack(0);
+      if (r + 1 < nrows) issue(x0 + (r + 1) * stride, 0);
+    } else {
+#pragma unroll
+      for (int c0 = 0; c0 < GPL; c0 += CH) {
+        issue(x0 + r * stride, c0);
+        unpack(c0);
+      }
+    }
+    __syncwarp();
+    float tr = 0.0f, ti = 0.0f;
+    for (int e = p0 + lane; e < p1; e += 32) {
+      const int i = hk_row[e], cc = hk_col[e];
+      const double2 hv = hk_val[e];
+      const float hx = (float)hv.x, hy = (float)hv.y;
+      // conj(V[x][cc]) R[x][i]
+      const float va = vre[cc], vb = vim[cc], ra = rre[i], rb = rim[i];
+      const float pr = fmaf(va, ra, vb * rb), pi = fmaf(va, rb, -vb * ra);
+      tr = fmaf(hx, pr, fmaf(-hy, pi, tr));
+      ti = fmaf(hx, pi, fmaf(hy, pr, ti));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      tr += __shfl_xor_sync(0xffffffffu, tr, off);
+      ti += __shfl_xor_sync(0xffffffffu, ti, off);
+    }
+    sr += (double)tr;
+    si += (double)ti;
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ void xor_perm8(float (&v)[8], int m7) {
+  if (m7 & 1) {
+#pragma unroll
+    for (int w = 0; w < 8; w += 2) { const float x = v[w]; v[w] = v[w + 1]; v[w + 1] = x; }
+  }
+  if (m7 & 2) {
+#pragma unroll
+    for (int w = 0; w < 8; ++w)
+      if (!(w & 2)) { const float x = v[w]; v[w] = v[w + 2]; v[w + 2] = x; }
+  }
+  if (m7 & 4) {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) { const float x = v[w]; v[w] = v[w + 4]; v[w + 4] = x; }
+  }
+}
+
+// The same part of the trace when H_k has one nonzero per row, h_i = H_k[i][i ^ m]:
+// sum_x sum_i h_i conj(V[x][i ^ m]) R[x][i].  A lane takes the complex granules
+// q = lane + 32 j (columns 8q .. 8q+7) of a row: R's own granule and V's granule q ^ (m >> 3),
+// permuted inside by m & 7, straight from global memory into registers, kRB rows at a
+// time.  FP32 partial sums (tr, ti) stay per lane.
+__device__ __forceinline__ void trace_xor(const uint8_t* Vs, const uint8_t* Rs, int N, int x0, int nrows,
+                                          int stride, int m, const float2* __restrict__ hv, int lane,
+                                          float& tr, float& ti) {
+  constexpr int kRB = 2;
+  const int NG = N / 8, mq = m >> 3, m7 = m & 7;
+  for (int q = lane; q < NG; q += 32) {
+    const int qv = q ^ mq;
+    float2 h[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) h[w] = __ldg(hv + 8 * q + w);
+    const uint32_t orr = s_off(N, 0, 8 * q) , ori = s_off(N, 0, N + 8 * q);
+    const uint32_t ovr = s_off(N, 0, 8 * qv), ovi = s_off(N, 0, N + 8 * qv);
+    for (int r0 = 0; r0 < nrows; r0 += kRB) {
+      uint4 ld[kRB][8];
+#pragma unroll
+      for (int b = 0; b < kRB; ++b) {
+        if (r0 + b < nrows) {
+          // s_off(x, kcol) = ro(x) + (s_off(0, kcol) ^ sw(x)): the row moves by 128 B inside
+          // a tile and by a tile row per 128 rows, and swizzles the 16-byte granule index
+          const int x = x0 + (r0 + b) * stride;
+          const uint32_t ro = (uint32_t)((x >> 7) * (2 * N / 64)) * kTile + (uint32_t)(x & 127) * 128u;
+          const uint32_t sw = (uint32_t)((x & 7) << 4);        // swizzle of row x
+          const uint8_t* pr = Rs + ro + (orr ^ sw);
+          const uint8_t* pi = Rs + ro + (ori ^ sw);
+          const uint8_t* vr = Vs + ro + (ovr ^ sw);
+          const uint8_t* vi = Vs + ro + (ovi ^ sw);
+          ld[b][0] = __ldcg(reinterpret_cast<const uint4*>(pr));
+          ld[b][1] = __ldcg(reinterpret_cast<const uint4*>(pr + kHalf));
+          ld[b][2] = __ldcg(reinterpret_cast<const uint4*>(pi));
+          ld[b][3] = __ldcg(reinterpret_cast<const uint4*>(pi + kHalf));
+          ld[b][4] = __ldcg(reinterpret_cast<const uint4*>(vr));
+          ld[b][5] = __ldcg(reinterpret_cast<const uint4*>(vr + kHalf));
+          ld[b][6] = __ldcg(reinterpret_cast<const uint4*>(vi));
+          ld[b][7] = __ldcg(reinterpret_cast<const uint4*>(vi + kHalf));
+        } else {
+#pragma unroll
+          for (int z = 0; z < 8; ++z) ld[b][z] = make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kRB; ++b) {
+        float rr[8], ri[8], vr[8], vi[8];
+        unpack8(ld[b][0], ld[b][1], rr);
+        unpack8(ld[b][2], ld[b][3], ri);
+        unpack8(ld[b][4], ld[b][5], vr);
+        unpack8(ld[b][6], ld[b][7], vi);
+        xor_perm8(vr, m7);
+        xor_perm8(vi, m7);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          // conj(V[x][i ^ m]) R[x][i]
+          const float pr = fmaf(vr[w], rr[w], vi[w] * ri[w]);
+          const float pi = fmaf(vr[w], ri[w], -vi[w] * rr[w]);
+          tr = fmaf(h[w].x, pr, fmaf(-h[w].y, pi, tr));
+          ti = fmaf(h[w].x, pi, fmaf(h[w].y, pr, ti));
+        }
+      }
     }
   }
 }
 
 template <int NB>
-__global__ void __launch_bounds__(192, 1) sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
   using Gm = Geo<NB>;
   constexpr int kStages = Gm::kStages, kBufs = Gm::kBufs;
   const int N = a.N;
@@ -355,7 +504,7 @@ __global__ void __launch_bounds__(192, 1) sweep_kernel(SweepArgs a) {
     }
     for (int i = 0; i < kQ; ++i) {
       mbar_init(&uq_full[i], 1);
-      mbar_init(&uq_empty[i], 5);
+      mbar_init(&uq_empty[i], 9);     // MMA thread + 4 epilogue warps + 4 trace warps
     }
     mbar_init(drain, 1);
     *abort_local = 0;
@@ -389,13 +538,8 @@ __global__ void __launch_bounds__(192, 1) sweep_kernel(SweepArgs a) {
           bool last;
           e = (int32_t)factor_entry(a, u.c % a.gmod, u.t, k, last);
           if (a.trace && e >= 0 && last) trk = k;
-          // this row block's previous step (and, in the reverse sweep, its partner's)
-          const uint32_t target = (uint32_t)(u.t * 2 * TNB);
-          bool ok = wait_count(&a.cnt[u.c * RT + u.rt], target, a.abort);
-          if (ok && a.trace) {
-            const int64_t partner = u.c < a.gmod ? u.c + a.gmod : u.c - a.gmod;
-            ok = wait_count(&a.cnt[partner * RT + u.rt], target, a.abort);
-          }
+          // the previous step of this row block is written
+          const bool ok = wait_count(&a.cnt[u.c * RT + u.rt], (uint32_t)(u.t * 2 * TNB), a.abort);
           if (!ok) {
             fail();
             tk = -1;
@@ -506,7 +650,7 @@ __global__ void __launch_bounds__(192, 1) sweep_kernel(SweepArgs a) {
       mma_commit(drain);
       mbar_wait_bounded_n(drain, 0, kLimit);
     }
-  } else {
+  } else if (warp < 4) {
     // ------------------------------------------------------------------ epilogue (warps 0-3)
     uint32_t ui = 0, use = 0;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
@@ -523,50 +667,11 @@ __global__ void __launch_bounds__(192, 1) sweep_kernel(SweepArgs a) {
       const Unit u = decode(a, m.x, RT, TNB);
       const uint8_t* cur = ((u.t & 1) ? a.buf1 : a.buf0);
       uint8_t* nxt = ((u.t & 1) ? a.buf0 : a.buf1);
-      if (m.z >= 0 && warp < TW) {
-        // rows of this unit's slice of Tr(H_k V^dag R) at step t (V chain g, R chain gmod + g)
-        const int64_t g = u.c % a.gmod;
-        const int li = (u.c >= a.gmod ? 2 * TNB : 0) + u.h * TNB + u.nb;
-        const int rs = 128 / (4 * TNB);
-        const uint8_t* Vs = cur + g * sb;
-        const uint8_t* Rs = cur + (a.gmod + g) * sb;
-        float* vre = trace_rows + (size_t)warp * 4 * N;
-        float* vim = vre + N;
-        float* rre = vim + N;
-        float* rim = rre + N;
-        const int k = m.z;
-        const int p0 = a.hk_ptr[k * (N + 1)], p1 = a.hk_ptr[k * (N + 1) + N];
-        double sr = 0.0, si = 0.0;
-        for (int r = warp; r < rs; r += TW) {
-          const int x = u.rt * 128 + li * rs + r;
-          row_to_smem(Vs, N, x, vre, vim, lane);
-          row_to_smem(Rs, N, x, rre, rim, lane);
-          __syncwarp();
-          float tr = 0.0f, ti = 0.0f;
-          for (int e = p0 + lane; e < p1; e += 32) {
-            const int i = a.hk_row[e], cc = a.hk_col[e];
-            const double2 hv = a.hk_val[e];
-            const float hx = (float)hv.x, hy = (float)hv.y;
-            // conj(V[x][cc]) R[x][i]
-            const float va = vre[cc], vb = vim[cc], ra = rre[i], rb = rim[i];
-            const float pr = fmaf(va, ra, vb * rb), pi = fmaf(va, rb, -vb * ra);
-            tr = fmaf(hx, pr, fmaf(-hy, pi, tr));
-            ti = fmaf(hx, pi, fmaf(hy, pr, ti));
-          }
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            tr += __shfl_xor_sync(0xffffffffu, tr, off);
-            ti += __shfl_xor_sync(0xffffffffu, ti, off);
-          }
-          sr += (double)tr;
-          si += (double)ti;
-          __syncwarp();
-        }
-        if (lane == 0) {
-          double2* slot_acc = a.acc + g * a.seg_len + u.t;
-          atomicAdd(&slot_acc->x, sr);
-          atomicAdd(&slot_acc->y, si);
-        }
+      if (a.trace && u.t > 0) {
+        // the outputs overwrite the states of step t-1, which that step's traces read
+        const uint32_t target = (uint32_t)(u.t * 4 * TNB);
+        if (threadIdx.x == 0 && !wait_count(&a.tcnt[(u.c % a.gmod) * RT + u.rt], target, a.abort)) fail();
+        named_barrier(1, 128);
       }
       const size_t region = ((size_t)u.rt * KT + (size_t)(u.h * N + u.nb * NB) / 64) * kTile;
       if (m.y < 0) {
@@ -627,6 +732,98 @@ __global__ void __launch_bounds__(192, 1) sweep_kernel(SweepArgs a) {
         atomicAdd(&a.cnt[u.c * RT + u.rt], 1u);
       }
     }
+  } else {
+    // ------------------------------------------------------------------ trace warps (6-9)
+    const int tw = warp - 6;
+    uint32_t ui = 0;
+    for (;;) {
+      const uint32_t slot = ui % kQ;
+      if (threadIdx.x == 192 && !wait_bar(&uq_full[slot], (ui / kQ) & 1, abort_local, a.abort)) fail();
+      named_barrier(2, 128);
+      if (*abort_local) break;
+      const int4 m = uq[slot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&uq_empty[slot]);
+      ++ui;
+      if (m.x < 0) break;
+      if (!a.trace) continue;
+      const Unit u = decode(a, m.x, RT, TNB);
+      if (m.z >= 0) {
+        // the partner chain's rows of step t are written too (this chain's are: the
+        // producer waited for them before handing the unit out)
+        const int64_t partner = u.c < a.gmod ? u.c + a.gmod : u.c - a.gmod;
+        if (threadIdx.x == 192 && !wait_count(&a.cnt[partner * RT + u.rt], (uint32_t)(u.t * 2 * TNB), a.abort))
+          fail();
+        named_barrier(2, 128);
+        if (*abort_local) break;
+      }
+      if (m.z >= 0 && tw < TW) {
+        // this unit's rows of Tr(H_k V^dag R) at step t (V chain g, R chain gmod + g)
+        const uint8_t* cur = ((u.t & 1) ? a.buf1 : a.buf0);
+        const int64_t g = u.c % a.gmod;
+        const int li = (u.c >= a.gmod ? 2 * TNB : 0) + u.h * TNB + u.nb;
+        const int rs = 128 / (4 * TNB);
+        const uint8_t* Vs = cur + g * sb;
+        const uint8_t* Rs = cur + (a.gmod + g) * sb;
+        float* vre = trace_rows + (size_t)tw * 4 * N;
+        float* vim = vre + N;
+        float* rre = vim + N;
+        float* rim = rre + N;
+        const int k = m.z;
+        const int p0 = a.hk_ptr[k * (N + 1)], p1 = a.hk_ptr[k * (N + 1) + N];
+        const int x0 = u.rt * 128 + li * rs + tw;
+        const int nrows = (rs - tw + TW - 1) / TW;
+        double sr = 0.0, si = 0.0;
+        if (a.xval) {
+          float tr = 0.0f, ti = 0.0f;
+          const float2* hv = a.xval + (size_t)k * N;
+          const int mk = a.xmask[k];
+          trace_xor(Vs, Rs, N, x0, nrows, TW, mk, hv, lane, tr, ti);
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            tr += __shfl_xor_sync(0xffffffffu, tr, off);
+            ti += __shfl_xor_sync(0xffffffffu, ti, off);
+          }
+          sr = (double)tr;
+          si = (double)ti;
+        } else switch (N) {
+          case 128:
+            trace_slice<1>(Vs, Rs, N, x0, nrows, TW, p0, p1, a.hk_row, a.hk_col, a.hk_val, vre, vim, rre, rim,
+                           lane, sr, si);
+            break;
+          case 256:
+            trace_slice<2>(Vs, Rs, N, x0, nrows, TW, p0, p1, a.hk_row, a.hk_col, a.hk_val, vre, vim, rre, rim,
+                           lane, sr, si);
+            break;
+          case 512:
+            trace_slice<4>(Vs, Rs, N, x0, nrows, TW, p0, p1, a.hk_row, a.hk_col, a.hk_val, vre, vim, rre, rim,
+                           lane, sr, si);
+            break;
+          default:
+            trace_slice<8>(Vs, Rs, N, x0, nrows, TW, p0, p1, a.hk_row, a.hk_col, a.hk_val, vre, vim, rre, rim,
+                           lane, sr, si);
+            break;
+        }
+        if (lane == 0) {
+          double2* slot_acc = a.acc + g * a.seg_len + u.t;
+          atomicAdd(&slot_acc->x, sr);
+          atomicAdd(&slot_acc->y, si);
+        }
+      }
+      // publish: this unit's reads of the step-t states are over.  A slice of step t is
+      // counted only after every slice of step t-1 of these rows, so tcnt >= t * 4 TNB
+      // means exactly that the slices of steps < t are done (as cnt does for outputs).
+      named_barrier(2, 128);
+      if (threadIdx.x == 192 && !*abort_local) {
+        uint32_t* tc = &a.tcnt[(u.c % a.gmod) * RT + u.rt];
+        if (u.t == 0 || wait_count(tc, (uint32_t)(u.t * 4 * TNB), a.abort)) {
+          __threadfence();
+          atomicAdd(tc, 1u);
+        } else {
+          fail();
+        }
+      }
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -667,7 +864,9 @@ static unsigned blocks_for(int64_t n) {
 
 static size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static size_t sync_bytes(int N, int64_t chains) { return up(((size_t)chains * (N / 128) + 2) * sizeof(uint32_t)); }
+// counters of a sweep: cnt [chains][N/128], tcnt [chains][N/128] (used up to gmod), ticket, abort
+static size_t sync_words(int N, int64_t chains) { return 2 * (size_t)chains * (N / 128) + 2; }
+static size_t sync_bytes(int N, int64_t chains) { return up(sync_words(N, chains) * sizeof(uint32_t)); }
 
 // Runs `p.seg_len` steps of `chains` chains from b0; the result is in b0 (even count) or b1.
 static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan& p, int64_t chains,
@@ -677,7 +876,7 @@ static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan&
   const int64_t total = p.seg_len * chains * (int64_t)(RT * 2 * TNB);
   if (total == 0) return cudaSuccess;
   if (total >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(sync, 0, ((size_t)chains * RT + 2) * sizeof(uint32_t), s);
+  cudaError_t e = cudaMemsetAsync(sync, 0, sync_words(N, chains) * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   SweepArgs a;
   a.buf0 = b0;
@@ -699,12 +898,15 @@ static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan&
   a.trace = trace ? 1 : 0;
   a.N = N;
   a.cnt = sync;
-  a.ticket = sync + (size_t)chains * RT;
-  a.abort = reinterpret_cast<int*>(sync + (size_t)chains * RT + 1);
+  a.tcnt = sync + (size_t)chains * RT;
+  a.ticket = sync + 2 * (size_t)chains * RT;
+  a.abort = reinterpret_cast<int*>(sync + 2 * (size_t)chains * RT + 1);
   a.hk_ptr = t->hk_ptr;
   a.hk_col = t->hk_col;
   a.hk_row = t->hk_row;
   a.hk_val = t->hk_val;
+  a.xmask = t->hk_xmask;
+  a.xval = t->hk_xval;
   a.acc = acc;
   a.status = status;
   const size_t smem = sweep_smem(NB, N);
@@ -712,11 +914,11 @@ static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan&
   if (NB == 256) {
     if ((e = cudaFuncSetAttribute(sweep_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
       return e;
-    sweep_kernel<256><<<(unsigned)grid, 192, smem, s>>>(a);
+    sweep_kernel<256><<<(unsigned)grid, 320, smem, s>>>(a);
   } else {
     if ((e = cudaFuncSetAttribute(sweep_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
       return e;
-    sweep_kernel<128><<<(unsigned)grid, 192, smem, s>>>(a);
+    sweep_kernel<128><<<(unsigned)grid, 320, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -725,10 +927,13 @@ static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan&
 
 using namespace tcl;
 
+// Operand block height: 128 (two accumulator buffers in tensor memory, so a unit's
+// epilogue overlaps the next unit's MMAs) unless REDO_TCL_NB=256 asks for the wider block
+// (one buffer, a third less operand traffic per flop); read when a table is built.
 int tc_large_nb(int N) {
   if (N < 256) return 128;
   const char* v = std::getenv("REDO_TCL_NB");
-  return (v && std::strcmp(v, "128") == 0) ? 128 : 256;
+  return (v && std::strcmp(v, "256") == 0) ? 256 : 128;
 }
 
 size_t tc_large_planes_bytes(const redo_table* t) { return 2 * (size_t)t->entries * entry_bytes(t->N); }
@@ -794,16 +999,41 @@ cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan
   uint32_t* sync = (uint32_t*)((char*)acc + up(G * (size_t)p.seg_len * sizeof(double2)));
   const uint8_t* rows = (const uint8_t*)t->tc_planes;
   const uint8_t* cols = rows + (size_t)t->entries * entry_bytes(N);
-  // forward segment products
-  s_identity_kernel<<<blocks_for(G * N * (2 * N / 8)), 256, 0, s>>>(s0, N, G);
-  cudaError_t e = sweep(t, q, p, G, 0, false, rows, s0, s1, sync, nullptr, status, s);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   float2* seg = (float2*)base;                 // the SIMT layout's segment region
-  s_to_complex_kernel<float><<<blocks_for(G * n2), 256, 0, s>>>((p.seg_len & 1) ? s1 : s0, N, G, 0, seg);
+  {
+    ProfScope ps(8, s);                        // forward segment products
+    // With few segments the forward sweep alone cannot keep every SM busy: run it on two
+    // half segments per checkpoint segment (the state buffers hold 2G chains) and join
+    // each pair with one FP32 product.
+    const int64_t units = G * (N / 128) * 2 * (N / t->tc_nb);
+    const bool split = units < 3 * (int64_t)t->num_sms && p.seg_len % 2 == 0 && p.seg_len >= 2;
+    ChainPlan pf = p;
+    if (split) {
+      pf.seg_len = p.seg_len / 2;
+      pf.S = 2 * p.S;
+    }
+    const int64_t Gf = pf.B * pf.S;
+    s_identity_kernel<<<blocks_for(Gf * N * (2 * N / 8)), 256, 0, s>>>(s0, N, Gf);
+    if ((e = sweep(t, q, pf, Gf, 0, false, rows, s0, s1, sync, nullptr, status, s))) return e;
+    const uint8_t* fin = (pf.seg_len & 1) ? s1 : s0;
+    if (split) {
+      // the checkpoint and costate regions (2G matrices, unused until the scans) hold the halves
+      float2* halves = (float2*)(base + up((size_t)G * n2 * sizeof(float2)));
+      s_to_complex_kernel<float><<<blocks_for(Gf * n2), 256, 0, s>>>(fin, N, Gf, 0, halves);
+      if ((e = large_pair_products_fp32(halves, seg, G, N, s))) return e;
+    } else {
+      s_to_complex_kernel<float><<<blocks_for(G * n2), 256, 0, s>>>(fin, N, G, 0, seg);
+    }
+  }
   float2 *Pck = nullptr, *Rck = nullptr;
   double2* tau = nullptr;
-  if ((e = large_grad_scans_fp32(t, p, UT, tb, F_out, ws, &Pck, &Rck, &tau, s))) return e;
+  {
+    ProfScope ps(9, s);
+    if ((e = large_grad_scans_fp32(t, p, UT, tb, F_out, ws, &Pck, &Rck, &tau, s))) return e;
+  }
   if (p.M == 0) return cudaGetLastError();
+  ProfScope ps(10, s);
   // reverse sweep: chains [0, G) hold V = P^dag, [G, 2G) hold R; both right-multiplied by A_f
   s_from_complex_kernel<float><<<blocks_for(G * N * (N / 8)), 256, 0, s>>>(Pck, N, G, 1, s0);
   s_from_complex_kernel<float><<<blocks_for(G * N * (N / 8)), 256, 0, s>>>(Rck, N, G, 2, s0 + G * state_bytes(N));

@@ -34,24 +34,18 @@ struct ProfRecord {
 static bool g_prof_on = false;
 static std::vector<ProfRecord> g_prof;
 
-struct ProfScope {
-  ProfRecord r{-1, nullptr, nullptr};
-  cudaStream_t s;
-  ProfScope(int phase, cudaStream_t st) : s(st) {
-    if (!g_prof_on) return;
-    r.phase = phase;
-    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
-      r.phase = -1;
-      return;
-    }
-    cudaEventRecord(r.a, s);
-  }
-  ~ProfScope() {
-    if (r.phase < 0) return;
-    cudaEventRecord(r.b, s);
-    g_prof.push_back(r);
-  }
-};
+ProfScope::ProfScope(int ph, cudaStream_t st) : phase(-1), a(nullptr), b(nullptr), s(st) {
+  if (!g_prof_on) return;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+  phase = ph;
+  cudaEventRecord(a, s);
+}
+
+ProfScope::~ProfScope() {
+  if (phase < 0) return;
+  cudaEventRecord(b, s);
+  g_prof.push_back(ProfRecord{phase, a, b});
+}
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
@@ -205,6 +199,32 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
           (e = cudaMemcpy(t->hk_row, rowi.data(), sizeof(int32_t) * rowi.size(), cudaMemcpyHostToDevice)) ||
           (e = cudaMemcpy(t->hk_val, val.data(), sizeof(double2) * val.size(), cudaMemcpyHostToDevice)))))
       return fail(cuda_error(e, "operator CSR upload"));
+    // Operators with exactly one nonzero per row, at column r ^ m_k (every Pauli string:
+    // X/Y flip bits, Z only sets phases) also get the compact form m_k, h_k[r] in FP32
+    // that the tensor-core gradient's trace reads without gathering.
+    bool xr = N > kSmallN;
+    std::vector<int32_t> xm(K, 0);
+    std::vector<float2> xv((size_t)K * N);
+    for (int k = 0; k < K && xr; ++k)
+      for (int r = 0; r < N && xr; ++r) {
+        const size_t a = (size_t)k * (N + 1) + r;
+        if (ptr[a + 1] - ptr[a] != 1) {
+          xr = false;
+          break;
+        }
+        const int m = col[ptr[a]] ^ r;
+        if (r == 0) xm[k] = m;
+        if (m != xm[k]) xr = false;
+        xv[(size_t)k * N + r] = make_float2((float)val[ptr[a]].x, (float)val[ptr[a]].y);
+      }
+    if (xr) {
+      if ((e = cudaMalloc(&t->hk_xmask, sizeof(int32_t) * K)) != cudaSuccess ||
+          (e = cudaMalloc(&t->hk_xval, sizeof(float2) * K * N)) != cudaSuccess)
+        return fail(set_error(REDO_ERR_OOM, "operator allocation: %s", cudaGetErrorString(e)));
+      if ((e = cudaMemcpy(t->hk_xmask, xm.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice)) ||
+          (e = cudaMemcpy(t->hk_xval, xv.data(), sizeof(float2) * K * N, cudaMemcpyHostToDevice)))
+        return fail(cuda_error(e, "operator upload"));
+    }
   }
   if ((flags & (REDO_TABLE_FP32 | REDO_TABLE_FP16X3)) &&
       (e = cudaMalloc(&t->T32, sizeof(float2) * n2 * t->entries)) != cudaSuccess)
@@ -285,6 +305,8 @@ redo_status redo_table_free(redo_table* t) {
   cudaFree(t->hk_col);
   cudaFree(t->hk_row);
   cudaFree(t->hk_val);
+  cudaFree(t->hk_xmask);
+  cudaFree(t->hk_xval);
   std::free(t);
   return REDO_OK;
 }

@@ -54,6 +54,8 @@ struct redo_table {
   int32_t* hk_row;            // row index of every nonzero [nnz] (COO view of the same CSR)
   double2* hk_val;            // values [nnz]
   int64_t hk_nnz;
+  int32_t* hk_xmask;          // [K] m_k when every H_k has its one nonzero of row r at r ^ m_k, else nullptr
+  float2* hk_xval;            // [K][N] that nonzero, H_k[r][r ^ m_k], in FP32
   void* tc_planes;            // tensor-core planes or nullptr
   size_t tc_bytes;
   int tc_nb;                  // operand block height of the large-N planes (128 or 256)
@@ -62,6 +64,20 @@ struct redo_table {
 };
 
 namespace redo {
+
+// ----------------------------------------------------------------------------
+// Event timing of a phase of launches on a stream while profiling is enabled
+// (redo_profile_enable); a no-op otherwise.
+// ----------------------------------------------------------------------------
+struct ProfScope {
+  int phase;
+  cudaEvent_t a, b;
+  cudaStream_t s;
+  ProfScope(int phase, cudaStream_t st);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+};
 
 // ----------------------------------------------------------------------------
 // Error plumbing
@@ -169,6 +185,7 @@ cudaError_t large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p
 size_t large_sim_workspace(const redo_table* t, int64_t B);
 cudaError_t large_finish_fp32(const redo_table* t, const ChainPlan& p, bool reunit, void* ws,
                               void** result, int* result_prec, cudaStream_t s);
+cudaError_t large_pair_products_fp32(const float2* in, float2* out, int64_t count, int N, cudaStream_t s);
 cudaError_t large_grad_scans_fp32(const redo_table* t, const ChainPlan& p, const double2* UT, int tb,
                                   double* F_out, void* ws, float2** Pck, float2** Rck, double2** tau,
                                   cudaStream_t s);

@@ -30,9 +30,9 @@ EXPORTS = [
     "redo_grape_step", "redo_simulate", "redo_simulate_workspace", "redo_mlp_sizes", "redo_mlp_forward",
     "redo_mlp_backward", "redo_mlp_adam", "redo_grape_adam_step",
 ]
-PROFILE_PHASES = 8
+PROFILE_PHASES = 11
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
-               "gradient"]
+               "gradient", "grad_forward_sweep", "grad_scans", "grad_reverse_sweep"]
 
 
 class RedoError(RuntimeError):

@@ -167,3 +167,40 @@ def test_large_level_table_matches_digit_products():
     F, g = t.fidelity_grad(q, w.target, "fp16x3")
     Fo, go = O.grape_gradient(To, Do, w.Hk, w.dt, dig[0], w.target)
     assert np.abs(g.cpu().numpy()[0] - go).max() <= 1e-3 * np.abs(go).max()
+
+
+@pytest.mark.parametrize("nb", ["256", "128"])
+@pytest.mark.parametrize("ck", [0, 2])
+def test_large_tc_gradient_n8(monkeypatch, nb, ck):
+    """N = 256: both operand-block widths of the tensor-core sweeps, one segment per pulse
+    and several (checkpoints every 2 steps), against the oracle's gradient."""
+    monkeypatch.setenv("REDO_TCL_NB", nb)
+    w = _reduced(2, 8, 2, 2, 5, base=16, digits=2)     # N=256, K=2, 256 levels
+    t = _tc_table(w)
+    q = t.quantize(w.u)
+    F, g = t.fidelity_grad(q, w.target, "fp16x3", checkpoint_every=ck)
+    To, Do = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    for b in range(w.B):
+        Fo, go = O.grape_gradient(To, Do, w.Hk, w.dt, dig[b], w.target)
+        assert np.abs(g.cpu().numpy()[b] - go).max() <= 1e-3 * np.abs(go).max()
+        assert abs(F.cpu().numpy()[b] - Fo) < 1e-6
+    U, _, _ = t.propagate(q, "fp16x3", reunit_every=2)
+    Uo = _ref.oracle_propagators(w, To, Do, dig, range(w.B))
+    assert np.abs(U.cpu().numpy() - Uo).max() < 2e-4
+
+
+def test_large_tc_gradient_general_h():
+    """Controls with several nonzeros per row (global X and Y on 7 qubits, N=128) take the
+    sparse-row trace path of the tensor-core reverse sweep."""
+    w = inputs.config(0, n_qubits=7, B=2, M=6, base=16, digits=2)
+    t = _tc_table(w)
+    q = t.quantize(w.u)
+    for ck in (0, 3):
+        F, g = t.fidelity_grad(q, w.target, "fp16x3", checkpoint_every=ck)
+        To, Do = _ref.oracle_table(w)
+        _, dig, _, _ = _ref.oracle_levels(w)
+        for b in range(w.B):
+            Fo, go = O.grape_gradient(To, Do, w.Hk, w.dt, dig[b], w.target)
+            assert np.abs(g.cpu().numpy()[b] - go).max() <= 1e-3 * np.abs(go).max()
+            assert abs(F.cpu().numpy()[b] - Fo) < 1e-6
