@@ -327,15 +327,20 @@ def run_gpu(args):
 
     grape = None
     if rank == 0 and not args.skip_grape:
-        gres, gflop, gbuild, gw = grape_measure(redo, inputs, torch, 3, levels=False, with_fp32=False,
+        gres, gflop, gbuild, gw = grape_measure(redo, inputs, torch, 3, levels=True, with_fp32=False,
                                                 with_fp64=not args.skip_fp64)
         grape = {"metric": "GRAPE iters/s", "value": gres["fp16x3"]["iters_per_s"], "unit": "iterations/s",
                  "workload": "GRAPE gradient + update, N=256 (8 qubits), K=16, M=1000, dt=2 us, Haar target, "
-                             "checkpoints every 32 steps, digit table",
+                             "checkpoints every 32 steps, level table (one operator per control level)",
                  "fp64_plain_redo": gres.get("fp64"),
                  "speedup_vs_fp64": (gres["fp16x3"]["iters_per_s"] / gres["fp64"]["iters_per_s"]
                                      if "fp64" in gres else None),
                  "achieved_tensor_tflops": 3 * gflop / (gres["fp16x3"]["ms_per_iter"] / 1e3) / 1e12,
+                 "tensor_frac_of_sustained": (3 * gflop / (gres["fp16x3"]["ms_per_iter"] / 1e3) / 1e12
+                                              / peaks.get("bf16_tflops_sustained", 1709.6)),
+                 "algorithmic": "3 complex N x N products per factor (forward, V and R sweeps), 8N^3 flop each, "
+                                "x3 fp16 products",
+                 "phase_ms": gres["fp16x3"].get("phase_ms"),
                  "table_build_s": gbuild}
 
     launches = sum(n for _, n in prof.values())

@@ -11,7 +11,7 @@
 // instruction descriptor's negate-B bit.
 //
 // Operand planes.  Every table entry C is stored as tiles (nb, kt) holding NB rows of B^T
-// hi followed by the same NB rows lo, 64 K columns wide (NB = 128, or 256 on request),
+// hi followed by the same NB rows lo, 64 K columns wide (NB = 128 for N <= 256, else 256),
 // swizzled like the states.  Two sets exist: "row" planes with C = A^T (forward steps
 // X <- A X on Y = X^T) and "column" planes with C = A (reverse sweep V <- V A, R <- R A).
 //
@@ -927,13 +927,17 @@ static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan&
 
 using namespace tcl;
 
-// Operand block height: 128 (two accumulator buffers in tensor memory, so a unit's
-// epilogue overlaps the next unit's MMAs) unless REDO_TCL_NB=256 asks for the wider block
-// (one buffer, a third less operand traffic per flop); read when a table is built.
+// Operand block height, fixed when a table is built.  128 keeps two accumulator buffers
+// in tensor memory (a unit's epilogue overlaps the next unit's MMAs) and gives twice the
+// units per step, which pays while units are short (N = 256: K loop of 8 tiles); 256 has
+// one buffer but a third less operand traffic per flop, which pays from N = 512 on.
+// REDO_TCL_NB=128 or 256 overrides the choice.
 int tc_large_nb(int N) {
   if (N < 256) return 128;
   const char* v = std::getenv("REDO_TCL_NB");
-  return (v && std::strcmp(v, "256") == 0) ? 256 : 128;
+  if (v && std::strcmp(v, "128") == 0) return 128;
+  if (v && std::strcmp(v, "256") == 0) return 256;
+  return N >= 512 ? 256 : 128;
 }
 
 size_t tc_large_planes_bytes(const redo_table* t) { return 2 * (size_t)t->entries * entry_bytes(t->N); }
