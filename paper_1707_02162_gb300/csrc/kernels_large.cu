@@ -802,8 +802,63 @@ size_t large_grad_workspace(const redo_table* t, const ChainPlan& p, int prec) {
   return 5 * up(G * n2 * el) + 2 * up(p.B * n2 * el) + up(p.B * sizeof(double2));
 }
 
+// One round of the log-depth (Hillis-Steele) scans over the S segment products of every
+// pulse, prefix and suffix in one launch.  Items [0, B S) are prefix entries,
+//     P_s <- P_s P_{s-off}            (s >= off; else copied),
+// items [B S, 2 B S) suffix entries,
+//     Q_s <- Q_{s+off} Q_s            (s + off < S; else copied),
+// so after rounds off = 1, 2, 4, ... < S, P_s = X_s ... X_0 and Q_s = X_{S-1} ... X_s.
+template <typename R>
+struct ScanRoundOps {
+  const cplx<R>* ps;
+  cplx<R>* pd;
+  const cplx<R>* qs;
+  cplx<R>* qd;
+  int64_t BS, S, off, n2;
+  __device__ void get(int64_t b, const cplx<R>*& a, const cplx<R>*& bb, cplx<R>*& c) const {
+    const bool suffix = b >= BS;
+    const int64_t i = suffix ? b - BS : b;
+    const int64_t s = i % S;
+    if (!suffix) {
+      a = s >= off ? ps + i * n2 : nullptr;
+      bb = s >= off ? ps + (i - off) * n2 : ps + i * n2;
+      c = pd + i * n2;
+    } else {
+      a = s + off < S ? qs + (i + off) * n2 : nullptr;
+      bb = qs + i * n2;
+      c = qd + i * n2;
+    }
+  }
+};
+
+// Costates R_s = U_T^dag Q_{s+1} (U_T^dag alone for the last segment) and a contiguous copy
+// of every pulse's full product P_{S-1} (items [B S, B S + B)).
+template <typename R>
+struct CostateOps {
+  const cplx<R>* Q;
+  const cplx<R>* Uadj;     // [B] U_T^dag
+  const cplx<R>* P;
+  cplx<R>* Rck;
+  cplx<R>* last;           // [B]
+  int64_t BS, S, n2;
+  __device__ void get(int64_t b, const cplx<R>*& a, const cplx<R>*& bb, cplx<R>*& c) const {
+    if (b < BS) {
+      const int64_t s = b % S, u = b / S;
+      a = s + 1 < S ? Uadj + u * n2 : nullptr;
+      bb = s + 1 < S ? Q + (b + 1) * n2 : Uadj + u * n2;
+      c = Rck + b * n2;
+    } else {
+      const int64_t u = b - BS;
+      a = nullptr;
+      bb = P + (u * S + S - 1) * n2;
+      c = last + u * n2;
+    }
+  }
+};
+
 // Prefix checkpoints, tau/F and suffix costates from the segment products in the first
-// workspace region.
+// workspace region, by log-depth scans (ceil(log2 S) batched rounds instead of 2S
+// dependent products).
 template <typename R>
 static cudaError_t large_scans_t(const redo_table* t, const ChainPlan& p, const double2* UT, int tb,
                                  double* F_out, char* ws, cplx<R>** Pck_out, cplx<R>** Rck_out,
@@ -815,28 +870,37 @@ static cudaError_t large_scans_t(const redo_table* t, const ChainPlan& p, const 
   cplx<R>* seg = (cplx<R>*)ws;
   cplx<R>* Pck = (cplx<R>*)(ws + mat);
   cplx<R>* Rck = (cplx<R>*)(ws + 2 * mat);
+  cplx<R>* ping = (cplx<R>*)(ws + 3 * mat);
+  cplx<R>* pong = (cplx<R>*)(ws + 4 * mat);
   cplx<R>* run = (cplx<R>*)(ws + 5 * mat);
   cplx<R>* run2 = (cplx<R>*)(ws + 5 * mat + up(p.B * n2 * sizeof(cplx<R>)));
   double2* tau = (double2*)(ws + 5 * mat + 2 * up(p.B * n2 * sizeof(cplx<R>)));
   cudaError_t e;
-  if ((e = set_identity<R>(run, p.B, N, s))) return e;
-  for (int64_t ss = 0; ss < p.S; ++ss) {
-    ListStepOps<R> op{seg, p.S, ss, false, run, run2, n2};
-    if ((e = cgemm<R, false>(op, p.B, N, R(1), R(0), s))) return e;
-    std::swap(run, run2);
-    DenseOps<R> cp{nullptr, run, Pck + ss * n2, 0, n2, p.S * n2};   // copy through the identity path
-    if ((e = cgemm<R, false>(cp, p.B, N, R(1), R(0), s))) return e;
+  // prefix in Pck / ping, suffix in pong / Rck; the first round reads the segment products
+  const cplx<R>* ps = seg;
+  const cplx<R>* qs = seg;
+  cplx<R>* pbuf[2] = {Pck, ping};
+  cplx<R>* qbuf[2] = {pong, Rck};
+  int r = 0;
+  for (int64_t off = 1; off < p.S || r == 0; off *= 2, ++r) {
+    ScanRoundOps<R> op{ps, pbuf[r & 1], qs, qbuf[r & 1], G, p.S, off, n2};
+    if ((e = cgemm<R, false>(op, 2 * G, N, R(1), R(0), s))) return e;
+    ps = pbuf[r & 1];
+    qs = qbuf[r & 1];
   }
-  tau_kernel<R><<<(unsigned)p.B, 256, 0, s>>>(run, UT, tb, N, tau, F_out);
+  // checkpoints end in Pck and the suffix products in pong (copy over when they did not)
+  if (ps != Pck) {
+    DenseOps<R> cp{nullptr, ps, Pck, 0, n2, n2};
+    if ((e = cgemm<R, false>(cp, G, N, R(1), R(0), s))) return e;
+  }
+  if (qs != pong) {
+    DenseOps<R> cp{nullptr, qs, pong, 0, n2, n2};
+    if ((e = cgemm<R, false>(cp, G, N, R(1), R(0), s))) return e;
+  }
   adjoint_target_kernel<R><<<blocks_for(p.B * n2), 256, 0, s>>>(UT, tb, N, p.B, run);
-  for (int64_t ss = p.S - 1; ss >= 0; --ss) {
-    DenseOps<R> cp{nullptr, run, Rck + ss * n2, 0, n2, p.S * n2};
-    if ((e = cgemm<R, false>(cp, p.B, N, R(1), R(0), s))) return e;
-    if (ss == 0) break;
-    ListStepOps<R> op{seg, p.S, ss, true, run, run2, n2};
-    if ((e = cgemm<R, false>(op, p.B, N, R(1), R(0), s))) return e;
-    std::swap(run, run2);
-  }
+  CostateOps<R> co{pong, run, Pck, Rck, run2, G, p.S, n2};
+  if ((e = cgemm<R, false>(co, G + p.B, N, R(1), R(0), s))) return e;
+  tau_kernel<R><<<(unsigned)p.B, 256, 0, s>>>(run2, UT, tb, N, tau, F_out);
   *Pck_out = Pck;
   *Rck_out = Rck;
   *tau_out = tau;
