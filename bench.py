@@ -392,6 +392,11 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- other workloads
 # One JSON line each; the driver's default run is the batched-propagation line above.
 
+def _peaks() -> dict:
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(pk)) if os.path.exists(pk) else {}
+
+
 def _events_time(fn, reps):
     import torch
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -493,6 +498,8 @@ def run_workload(args):
         out.update({"metric": "REDO prop steps/s (noisy-drive ensemble)", "unit": "realisation-steps/s",
                     "value": res["fp16x3_with_U"]["realisation_steps_per_s"], "results": res,
                     "achieved_tensor_tflops_fp16x3": flop_step * res["fp16x3_with_U"]["realisation_steps_per_s"] / 1e12,
+                    "tensor_frac_of_sustained": (flop_step * res["fp16x3_with_U"]["realisation_steps_per_s"] / 1e12
+                                                 / _peaks().get("bf16_tflops_sustained", 1709.6)),
                     "sample": f"{Ms} of the 2000 steps, all 64 realisations", "table_build_s": build_s,
                     "config": {"N": w.N, "K": w.K, "B": w.B, "M_timed": Ms}})
     elif args.workload == "plain":

@@ -748,15 +748,20 @@ __global__ void __launch_bounds__(256) trace_kernel(const cplx<R>* __restrict__ 
 }
 
 // tau_u = Tr(U_T^dag X_u) (FP64), F_u
+// tau_u = Tr(U_T^dag X_u) = sum_ij conj(U_T[i][j]) X_u[i][j], in FP64: grid (pulse, part),
+// each block sums 1/kTauParts of the entries and adds into tau[u] (zeroed beforehand).
+constexpr int kTauParts = 32;
+
 template <typename R>
 __global__ void __launch_bounds__(256) tau_kernel(const cplx<R>* __restrict__ X, const double2* __restrict__ UT,
-                                                  int tb, int N, double2* __restrict__ tau,
-                                                  double* __restrict__ F) {
-  const int64_t u = blockIdx.x;
+                                                  int tb, int N, double2* __restrict__ tau) {
+  const int64_t u = blockIdx.x / kTauParts;
+  const int part = blockIdx.x % kTauParts;
   const int64_t n2 = (int64_t)N * N;
+  const int64_t i0 = n2 * part / kTauParts, i1 = n2 * (part + 1) / kTauParts;
   const double2* Ut = UT + (tb ? u * n2 : 0);
   double re = 0.0, im = 0.0;
-  for (int64_t i = threadIdx.x; i < n2; i += 256) {
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += 256) {
     const double2 g = Ut[i];
     const double xr = (double)X[u * n2 + i].x, xi = (double)X[u * n2 + i].y;
     re += g.x * xr + g.y * xi;
@@ -774,9 +779,14 @@ __global__ void __launch_bounds__(256) tau_kernel(const cplx<R>* __restrict__ X,
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    tau[u] = make_double2(sre[0], sim[0]);
-    if (F) F[u] = (sre[0] * sre[0] + sim[0] * sim[0]) / ((double)N * (double)N);
+    atomicAdd(&tau[u].x, sre[0]);
+    atomicAdd(&tau[u].y, sim[0]);
   }
+}
+
+__global__ void fidelity_from_tau_kernel(const double2* __restrict__ tau, int64_t B, int N, double* __restrict__ F) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u < B) F[u] = (tau[u].x * tau[u].x + tau[u].y * tau[u].y) / ((double)N * (double)N);
 }
 
 // X_u = U_T^dag (converted)
@@ -900,7 +910,9 @@ static cudaError_t large_scans_t(const redo_table* t, const ChainPlan& p, const 
   adjoint_target_kernel<R><<<blocks_for(p.B * n2), 256, 0, s>>>(UT, tb, N, p.B, run);
   CostateOps<R> co{pong, run, Pck, Rck, run2, G, p.S, n2};
   if ((e = cgemm<R, false>(co, G + p.B, N, R(1), R(0), s))) return e;
-  tau_kernel<R><<<(unsigned)p.B, 256, 0, s>>>(run2, UT, tb, N, tau, F_out);
+  if ((e = cudaMemsetAsync(tau, 0, sizeof(double2) * p.B, s))) return e;
+  tau_kernel<R><<<(unsigned)(p.B * kTauParts), 256, 0, s>>>(run2, UT, tb, N, tau);
+  if (F_out) fidelity_from_tau_kernel<<<(unsigned)((p.B + 127) / 128), 128, 0, s>>>(tau, p.B, N, F_out);
   *Pck_out = Pck;
   *Rck_out = Rck;
   *tau_out = tau;

@@ -532,17 +532,36 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
           const uint32_t got = atomicAdd(a.ticket, 1u);
           if ((int64_t)got < total) tk = (int32_t)got;
         }
+        uint32_t pre = 0;                 // ring stages armed with their operand tile only
+        const uint8_t* Bb = nullptr;
         if (tk >= 0) {
           u = decode(a, tk, RT, TNB);
           int k;
           bool last;
           e = (int32_t)factor_entry(a, u.c % a.gmod, u.t, k, last);
           if (a.trace && e >= 0 && last) trk = k;
+          if (e >= 0) {
+            // the operand tiles do not depend on the previous step: start the first ones now
+            Bb = a.planes + (size_t)e * entry_bytes(N) + (size_t)u.nb * KT * Gm::kB;
+            for (; pre < (uint32_t)kStages && pre < (uint32_t)KT; ++pre) {
+              const uint32_t it = kit + pre, s = it % kStages;
+              if (it >= (uint32_t)kStages && !wait_bar(&empty[s], ((it / kStages) - 1) & 1, abort_local, a.abort)) {
+                fail();
+                break;
+              }
+              uint8_t* dst = ring + s * Gm::kStage;
+              mbar_arrive_expect_tx(&full[s], Gm::kStage);
+#pragma unroll
+              for (uint32_t o = 0; o < Gm::kB; o += kHalf)
+                bulk_load(dst + kTile + o, Bb + (size_t)pre * Gm::kB + o, kHalf, &full[s]);
+            }
+          }
           // the previous step of this row block is written
-          const bool ok = wait_count(&a.cnt[u.c * RT + u.rt], (uint32_t)(u.t * 2 * TNB), a.abort);
+          const bool ok = !*abort_local && wait_count(&a.cnt[u.c * RT + u.rt], (uint32_t)(u.t * 2 * TNB), a.abort);
           if (!ok) {
             fail();
             tk = -1;
+            kit += pre;                   // stages with copies in flight, drained below
           }
         }
         const uint32_t slot = ui % kQ;
@@ -557,25 +576,26 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
         if (e < 0) continue;
         fence_proxy_async_global();
         const uint8_t* Sc = ((u.t & 1) ? a.buf1 : a.buf0) + u.c * sb;
-        const uint8_t* Bb = a.planes + (size_t)e * entry_bytes(N) + (size_t)u.nb * KT * Gm::kB;
         bool ok = true;
         for (int kt = 0; kt < KT && ok; ++kt, ++kit) {
           const uint32_t s = kit % kStages;
-          if (kit >= (uint32_t)kStages &&
-              !wait_bar(&empty[s], ((kit / kStages) - 1) & 1, abort_local, a.abort)) {
-            fail();
-            ok = false;
-            break;
+          uint8_t* dst = ring + s * Gm::kStage;
+          if ((uint32_t)kt >= pre) {
+            if (kit >= (uint32_t)kStages &&
+                !wait_bar(&empty[s], ((kit / kStages) - 1) & 1, abort_local, a.abort)) {
+              fail();
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&full[s], Gm::kStage);
+#pragma unroll
+            for (uint32_t o = 0; o < Gm::kB; o += kHalf)
+              bulk_load(dst + kTile + o, Bb + (size_t)kt * Gm::kB + o, kHalf, &full[s]);
           }
           const int kta = u.h ? (kt + KT / 2) % KT : kt;
-          uint8_t* dst = ring + s * Gm::kStage;
           const uint8_t* sa = Sc + ((size_t)u.rt * KT + kta) * kTile;
-          const uint8_t* sbp = Bb + (size_t)kt * Gm::kB;
-          mbar_arrive_expect_tx(&full[s], Gm::kStage);
           bulk_load(dst, sa, kHalf, &full[s]);
           bulk_load(dst + kHalf, sa + kHalf, kHalf, &full[s]);
-#pragma unroll
-          for (uint32_t o = 0; o < Gm::kB; o += kHalf) bulk_load(dst + kTile + o, sbp + o, kHalf, &full[s]);
         }
         if (!ok) break;
       }
