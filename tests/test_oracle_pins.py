@@ -221,6 +221,87 @@ def test_splitting_error_is_first_order():
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
 
 
+def test_strang_local_error_is_third_order():
+    # symmetric placement of the drift around one control (or commuting controls): the
+    # one-step error drops by 8 when dt halves.  Non-commuting controls keep their own
+    # first-order ordering error; the symmetric step removes the drift's part only.
+    n = 1
+    H0 = 2 * np.pi * 3e3 * SZ / 2
+    Hk = np.stack([SX / 2])
+    u = np.array([5e4])
+    errs = [np.abs(O.strang_split_step(H0, Hk, dt, u) - O.exact_step(H0, Hk, dt, u)).max()
+            for dt in [4e-6, 2e-6, 1e-6]]
+    assert 7.0 < errs[0] / errs[1] < 9.0 and 7.0 < errs[1] / errs[2] < 9.0
+
+
+def test_strang_global_error_is_second_order():
+    # fixed total time, constant controls: exact = exp(-i t_f (H0 + u.H)); the symmetric
+    # chain's error quarters when the number of steps doubles (the Lie chain's halves)
+    H0 = 2 * np.pi * 3e3 * SZ / 2
+    Hk = np.stack([SX / 2])
+    u, tf = np.array([4e4]), 40e-6
+    exact = O.expm_pade13(-1j * tf * (H0 + np.tensordot(u, Hk, axes=1)))
+    es, el = [], []
+    for M in (10, 20, 40):
+        dt = tf / M
+        S = np.linalg.matrix_power(O.strang_split_step(H0, Hk, dt, u), M)
+        L = np.linalg.matrix_power(O.split_step(H0, Hk, dt, u), M)
+        es.append(np.abs(S - exact).max())
+        el.append(np.abs(L - exact).max())
+    assert 3.6 < es[0] / es[1] < 4.4 and 3.6 < es[1] / es[2] < 4.4
+    assert 1.7 < el[0] / el[1] < 2.3
+
+
+def test_strang_step_is_time_reversible():
+    # S(dt) S(-dt) = I for one control (a drift placed on one side only fails this)
+    rng = np.random.default_rng(11)
+    n = 2
+    H0 = inputs.drift_zz(n, rng.uniform(-5e3, 5e3, n), np.array([[0, 150.0], [0, 0]]))
+    Hk = inputs.controls_global_xy(n)[:1]
+    u, dt = np.array([3.1e4]), 3e-6
+    P = O.strang_split_step(H0, Hk, dt, u) @ O.strang_split_step(H0, Hk, -dt, u)
+    assert np.abs(P - np.eye(4)).max() < 1e-13
+    L = O.split_step(H0, Hk, dt, u) @ O.split_step(H0, Hk, -dt, u)
+    assert np.abs(L - np.eye(4)).max() > 1e-4
+
+
+def test_strang_table_chain_matches_split_steps_at_level_values():
+    # the table/digit path of the symmetric chain equals the continuous symmetric steps
+    # evaluated at the quantised coefficients
+    rng = np.random.default_rng(12)
+    n = 2
+    H0 = inputs.drift_zz(n, rng.uniform(-5e3, 5e3, n), np.array([[0, 120.0], [0, 0]]))
+    Hk = inputs.controls_global_xy(n)
+    lo, hi, L, b, d, dt = np.array([-6e4, -6e4]), np.array([6e4, 6e4]), 4096, 64, 2, 1e-6
+    T, D = O.build_table(H0, Hk, dt, lo, hi, L, b, d)
+    Dh = O.half_drift(H0, dt)
+    assert np.abs(Dh @ Dh - D).max() < 1e-14
+    u = rng.uniform(-6e4, 6e4, size=(1, 12, 2))
+    q, _, _ = O.quantize(u, lo, hi, L)
+    dig = O.level_digits(q, b, d)
+    U = O.propagate_strang(T, Dh, dig[0])
+    ref = np.eye(4, dtype=complex)
+    for row in O.level_values(q[0], lo, hi, L):
+        ref = O.strang_split_step(H0, Hk, dt, row) @ ref
+    assert np.abs(U - ref).max() < 1e-12
+    ex, X = O.simulate_expectation_strang(T, Dh, dig[0], np.eye(4)[0].astype(complex), np.array([1., 1., -1., -1.]))
+    assert np.abs(X - U).max() < 1e-15 and ex[0] == 1.0
+
+
+def test_strang_commuting_case_has_no_splitting_error():
+    n = 2
+    rng = np.random.default_rng(13)
+    H0 = inputs.drift_zz(n, rng.uniform(-5e3, 5e3, n), np.array([[0, 150.0], [0, 0]]))
+    Hk = np.stack([inputs.embed({0: SZ / 2}, n), inputs.embed({1: SZ / 2}, n)])
+    lo, hi, L, b, d, dt = np.array([-6e4, -6e4]), np.array([6e4, 6e4]), 4096, 64, 2, 1e-6
+    T, D = O.build_table(H0, Hk, dt, lo, hi, L, b, d)
+    u = rng.uniform(-6e4, 6e4, size=(1, 20, 2))
+    q, _, _ = O.quantize(u, lo, hi, L)
+    U = O.propagate_strang(T, O.half_drift(H0, dt, method="eig"), O.level_digits(q, b, d)[0])
+    Htot = 20 * H0 + np.tensordot(O.level_values(q[0], lo, hi, L).sum(axis=0), Hk, axes=1)
+    assert np.abs(U - O.expm_hermitian(Htot, dt)).max() < 1e-12
+
+
 def test_chain_time_order():
     # Step 1 is applied first: U = U_2 U_1.  pi/2 about x then pi/2 about y.
     n = 1
