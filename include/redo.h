@@ -108,6 +108,14 @@ typedef struct redo_table redo_table;
  *           K products instead of K*digits.  K * levels * N^2 * 16 bytes (the
  *           FP64 copy) must stay below 200 GiB; the FP32 copy and the split-FP16
  *           planes, when requested, add half and (N > 64: two sets of) half of that.
+ *           REDO_TABLE_STRANG makes every call on the table use the symmetric step
+ *           S_n = D_h E_{K-1} ... E_0 D_h with D_h = exp(-i dt/2 H0) (the drift split
+ *           evenly around the control factors instead of applied once per step; the
+ *           second-order variant of the Section III step).  The table also stores D_h;
+ *           propagators are D_h (U_M ... U_1) D_h^dag of the folded chain, fidelities and
+ *           gradients use the target D_h^dag U_T D_h, and redo_simulate (which then needs
+ *           a diagonal H0) starts the folded chain from D_h^dag psi0.  The workspace of
+ *           each call grows by B FP64 matrices (two sets when H0 is not diagonal).
  *  stream   stream for the build; synchronised before returning.
  *  out      receives the handle; free with redo_table_free.
  * Errors: REDO_ERR_INVALID, REDO_ERR_NOT_HERMITIAN (relative tolerance 1e-12
@@ -116,6 +124,7 @@ typedef struct redo_table redo_table;
 #define REDO_TABLE_FP32 0x1u
 #define REDO_TABLE_FP16X3 0x2u
 #define REDO_TABLE_LEVELS 0x4u
+#define REDO_TABLE_STRANG 0x8u
 redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, const void* Hk,
                              const double* lo, const double* hi, int32_t base, int32_t digits,
                              uint32_t flags, void* stream, redo_table** out);

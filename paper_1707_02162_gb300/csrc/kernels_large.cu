@@ -389,6 +389,12 @@ cudaError_t large_table_build(redo_table* t, const double2* H0, const double2* H
       cleanup();
       return e;
     }
+    // half drift exp(-i dt/2 H0) of the symmetric split
+    std::vector<double> ch{0.5 * t->dt};
+    if (t->Dh64 && (e = batched_expm(N, H0, k0, ch, hn, t->Dh64, work, d_idx, d_coef, s))) {
+      cleanup();
+      return e;
+    }
   }
   // digit powers: slot (k, j, 1) = generator G_kj (S_k for j = 0), slot c = 0 identity
   double2* T = t->T64;

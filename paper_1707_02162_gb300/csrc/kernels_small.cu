@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(SmemMM<double, N, (N >= 64 ? 4 : (N >= 32 ? 2 
 table_expm_kernel(const double2* __restrict__ H0, const double2* __restrict__ Hk, int K,
                   int digits, int base, double dt, const double* __restrict__ lo,
                   const double* __restrict__ delta, int64_t entries, double2* __restrict__ T,
-                  double2* __restrict__ D) {
+                  double2* __restrict__ D, double2* __restrict__ Dh) {
   constexpr int TM = (N >= 64 ? 4 : (N >= 32 ? 2 : 1));
   using MM = SmemMM<double, N, TM, TM>;
   constexpr int N2 = N * N;
@@ -165,10 +165,11 @@ table_expm_kernel(const double2* __restrict__ H0, const double2* __restrict__ Hk
   const double2* H;
   double theta;
   double2* out;
-  if (e == entries) {
+  if (e >= entries) {
+    // the drift step, and (block entries + 1) the half drift step of the symmetric split
     H = H0;
-    theta = 1.0;
-    out = D;
+    theta = e == entries ? 1.0 : 0.5;
+    out = e == entries ? D : Dh;
   } else {
     const int c = (int)(e % base);
     const int j = (int)((e / base) % digits);
@@ -334,8 +335,8 @@ static cudaError_t table_expm_n(const redo_table* t, const double2* H0, const do
   cudaError_t e = cudaFuncSetAttribute(table_expm_kernel<N>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  table_expm_kernel<N><<<(unsigned)(t->entries + 1), MM::THREADS, smem, s>>>(
-      H0, Hk, t->K, t->digits, t->base, t->dt, t->d_lo, t->d_delta, t->entries, t->T64, t->D64);
+  table_expm_kernel<N><<<(unsigned)(t->entries + (t->Dh64 ? 2 : 1)), MM::THREADS, smem, s>>>(
+      H0, Hk, t->K, t->digits, t->base, t->dt, t->d_lo, t->d_delta, t->entries, t->T64, t->D64, t->Dh64);
   return cudaGetLastError();
 }
 

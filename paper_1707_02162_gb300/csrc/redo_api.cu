@@ -167,6 +167,21 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
       (e = cudaMalloc(&t->T64, sizeof(double2) * n2 * t->entries)) != cudaSuccess ||
       (e = cudaMalloc(&t->D64, sizeof(double2) * n2)) != cudaSuccess)
     return fail(set_error(REDO_ERR_OOM, "table allocation: %s", cudaGetErrorString(e)));
+  if (flags & REDO_TABLE_STRANG) {
+    t->strang = 1;
+    if ((e = cudaMalloc(&t->Dh64, sizeof(double2) * n2)) != cudaSuccess)
+      return fail(set_error(REDO_ERR_OOM, "half drift allocation: %s", cudaGetErrorString(e)));
+  }
+  {
+    bool diag = true;
+    for (int r = 0; r < N && diag; ++r)
+      for (int c = 0; c < N; ++c)
+        if (r != c && (h[2 * (r * N + c)] != 0.0 || h[2 * (r * N + c) + 1] != 0.0)) {
+          diag = false;
+          break;
+        }
+    t->h0_diagonal = diag ? 1 : 0;
+  }
   {
     // sparse (CSR) copy of the control operators for the gradient traces Tr(H_k W)
     std::vector<int32_t> ptr((size_t)K * (N + 1)), col, rowi;
@@ -299,6 +314,7 @@ redo_status redo_table_free(redo_table* t) {
   cudaFree(t->d_delta);
   cudaFree(t->T64);
   cudaFree(t->D64);
+  cudaFree(t->Dh64);
   cudaFree(t->T32);
   cudaFree(t->tc_planes);
   cudaFree(t->hk_ptr);
@@ -369,7 +385,22 @@ struct PropLayout {
   ChainPlan p;
   int eff_prec;       // precision of segment and pulse products
   size_t seg_off, prod_off, prod64_off, total;
+  size_t strang_off, strang_tmp_off;   // symmetric split: conjugated products (+ dense-drift scratch)
 };
+
+// FP64 matrices appended to a workspace for the symmetric split's conjugation
+static size_t strang_bytes(const redo_table* t, int64_t count) {
+  if (!t->strang) return 0;
+  const size_t m = ((size_t)count * t->N * t->N * sizeof(double2) + 255) & ~(size_t)255;
+  return t->h0_diagonal ? m : 2 * m;
+}
+
+static void add_strang(const redo_table* t, int64_t count, size_t& total, size_t& off, size_t& tmp_off) {
+  const size_t m = ((size_t)count * t->N * t->N * sizeof(double2) + 255) & ~(size_t)255;
+  off = total;
+  tmp_off = total + m;
+  total += strang_bytes(t, count);
+}
 
 static PropLayout prop_layout(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
                               int32_t reunit_every) {
@@ -380,6 +411,7 @@ static PropLayout prop_layout(const redo_table* t, int64_t B, int64_t M, redo_pr
     L.seg_off = L.prod_off = L.prod64_off = 0;
     L.total = prec == REDO_FP16X3 ? tc_large_prop_workspace(t, L.p, reunit_every > 0)
                                   : large_prop_workspace(t, L.p, prec, reunit_every > 0);
+    add_strang(t, B, L.total, L.strang_off, L.strang_tmp_off);
     return L;
   }
   // the tensor-core path forms segment products in split FP16 and combines them in FP32
@@ -395,6 +427,7 @@ static PropLayout prop_layout(const redo_table* t, int64_t B, int64_t M, redo_pr
   L.prod_off = up((size_t)L.p.B * L.p.S * n2 * el);
   L.prod64_off = L.prod_off + up((size_t)L.p.B * n2 * el);
   L.total = L.prod64_off + (reunit_every > 0 ? up((size_t)L.p.B * n2 * sizeof(double2)) : 0);
+  add_strang(t, B, L.total, L.strang_off, L.strang_tmp_off);
   return L;
 }
 
@@ -446,6 +479,15 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
                                 dev_status, s);
       if (e != cudaSuccess) return cuda_error(e, "large-N chains");
     }
+    if (t->strang) {
+      // symmetric split: S_M ... S_1 = D_h (U_M ... U_1) D_h^dag
+      double2* sb = (double2*)((char*)workspace + L.strang_off);
+      if ((e = launch_half_drift_conj(t, res_prec, res, B, 0, sb,
+                                      (double2*)((char*)workspace + L.strang_tmp_off), s)) != cudaSuccess)
+        return cuda_error(e, "half-drift conjugation");
+      res = sb;
+      res_prec = REDO_FP64;
+    }
     ProfScope ps(4, s);
     if ((e = launch_finalize(t, B, res_prec, res, U_out, (const double2*)U_target, F_out,
                              (double2*)tau_out, s)) != cudaSuccess)
@@ -480,6 +522,14 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
     fin = prod64;
     fin_prec = REDO_FP64;
   }
+  if (t->strang) {
+    double2* sb = (double2*)((char*)workspace + L.strang_off);
+    if ((e = launch_half_drift_conj(t, fin_prec, fin, B, 0, sb,
+                                    (double2*)((char*)workspace + L.strang_tmp_off), s)) != cudaSuccess)
+      return cuda_error(e, "half-drift conjugation");
+    fin = sb;
+    fin_prec = REDO_FP64;
+  }
   {
     ProfScope ps(4, s);
     if ((e = launch_finalize(t, B, fin_prec, fin, U_out, (const double2*)U_target, F_out,
@@ -495,6 +545,7 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
 struct GradLayout {
   ChainPlan p;
   size_t seg_off, pck_off, rck_off, tau_off, total;
+  size_t strang_off, strang_tmp_off;   // symmetric split: transformed targets (+ scratch)
 };
 
 static GradLayout grad_layout(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
@@ -505,6 +556,7 @@ static GradLayout grad_layout(const redo_table* t, int64_t B, int64_t M, redo_pr
                                : plan_chain_large(t, B, M);
     L.seg_off = L.pck_off = L.rck_off = L.tau_off = 0;
     L.total = prec == REDO_FP16X3 ? tc_large_grad_workspace(t, L.p) : large_grad_workspace(t, L.p, prec);
+    add_strang(t, B, L.total, L.strang_off, L.strang_tmp_off);
     return L;
   }
   L.p = checkpoint_every > 0 ? plan_chain_aligned(t, B, M, checkpoint_every)
@@ -517,6 +569,7 @@ static GradLayout grad_layout(const redo_table* t, int64_t B, int64_t M, redo_pr
   L.rck_off = 2 * mats;
   L.tau_off = 3 * mats;
   L.total = L.tau_off + up((size_t)B * sizeof(double2));
+  add_strang(t, B, L.total, L.strang_off, L.strang_tmp_off);
   return L;
 }
 
@@ -560,6 +613,14 @@ redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B,
   double2* tau = (double2*)(w + L.tau_off);
   cudaError_t e;
   ProfScope ps(7, s);
+  if (t->strang) {
+    // symmetric split: F(U_T, D_h U D_h^dag) = F(D_h^dag U_T D_h, U) for the folded chain U
+    double2* sb = (double2*)(w + L.strang_off);
+    if ((e = launch_half_drift_conj(t, REDO_FP64, U_target, target_batched ? B : 1, 1, sb,
+                                    (double2*)(w + L.strang_tmp_off), s)) != cudaSuccess)
+      return cuda_error(e, "half-drift conjugation of the target");
+    U_target = sb;
+  }
   if (t->N > kSmallN) {
     e = prec == REDO_FP16X3
             ? tc_large_grad(t, q, L.p, (const double2*)U_target, target_batched, F_out, grad,
@@ -587,7 +648,8 @@ redo_status redo_simulate_workspace(const redo_table* t, int64_t B, int64_t M,
   if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
   redo_status st = check_prec(t, prec);
   if (st != REDO_OK) return st;
-  const size_t state = t->N > kSmallN ? large_sim_workspace(t, B) : 0;
+  size_t state = t->N > kSmallN ? large_sim_workspace(t, B) : 0;
+  if (t->strang) state += ((size_t)B * t->N * sizeof(double2) + 255) & ~(size_t)255;   // D_h^dag psi0
   size_t prop = 0;
   if (want_U) {
     st = redo_propagate_workspace(t, B, M, prec, reunit_every, &prop);
@@ -611,12 +673,27 @@ redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int6
   if (B == 0) return REDO_OK;
   if (!psi0 || !obs_diag || !expect) return set_error(REDO_ERR_INVALID, "null psi0, obs_diag or expect");
   if (M > 0 && !q) return set_error(REDO_ERR_INVALID, "q is NULL");
+  if (t->strang && !t->h0_diagonal)
+    return set_error(REDO_ERR_UNSUPPORTED,
+                     "state simulation with the symmetric split needs a diagonal drift H0");
   cudaStream_t s = (cudaStream_t)stream;
   {
     ProfScope ps(2, s);
     cudaError_t e;
+    const size_t need_state = t->N > kSmallN ? large_sim_workspace(t, B) : 0;
+    if (t->strang) {
+      // symmetric split with a diagonal drift and observable: the symmetric states give the
+      // same expectations as the folded chain started from D_h^dag psi0
+      const size_t need = need_state + (((size_t)B * t->N * sizeof(double2) + 255) & ~(size_t)255);
+      if (!workspace || workspace_bytes < need)
+        return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", need);
+      double2* pw = (double2*)((char*)workspace + need_state);
+      if ((e = launch_half_drift_vec(t, (const double2*)psi0, psi0_batched ? B : 1, pw, s)) != cudaSuccess)
+        return cuda_error(e, "half-drift of the initial state");
+      psi0 = pw;
+    }
     if (t->N > kSmallN) {
-      const size_t need = large_sim_workspace(t, B);
+      const size_t need = need_state;
       if (!workspace || workspace_bytes < need)
         return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", need);
       e = large_sim(t, q, B, M, prec == REDO_FP64 ? REDO_FP64 : REDO_FP32, (const double2*)psi0,

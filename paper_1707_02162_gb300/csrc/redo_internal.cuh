@@ -48,6 +48,9 @@ struct redo_table {
   double* d_delta;            // [K]
   double2* T64;               // [entries][N][N], term 0 digit 0 folded with D
   double2* D64;               // [N][N]
+  double2* Dh64;              // [N][N] half drift exp(-i dt/2 H0) of a symmetric-split table, else nullptr
+  int strang;                 // calls use the symmetric step D_h E_{K-1} ... E_0 D_h
+  int h0_diagonal;            // H0 (so D_h) is diagonal
   float2* T32;                // [entries][N][N] or nullptr
   int32_t* hk_ptr;            // CSR of the control operators: row pointers [K][N+1]
   int32_t* hk_col;            // column indices [nnz]
@@ -204,6 +207,15 @@ cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan
 cudaError_t large_sim(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
                       const double2* psi0, int pb, const double* obs, double* expect, void* ws,
                       cudaStream_t s);
+
+// out_b = A X_b A^dag (adjoint = 0) or A^dag X_b A (adjoint = 1), A = the table's half
+// drift, FP64 out (may be X itself); X_b of precision `prec` (REDO_FP64 or REDO_FP32).
+// tmp: count FP64 matrices of scratch when H0 is not diagonal (unused, may be NULL, otherwise).
+cudaError_t launch_half_drift_conj(const redo_table* t, int prec, const void* X, int64_t count, int adjoint,
+                                   double2* out, double2* tmp, cudaStream_t s);
+// psi'_b = D_h^dag psi_b for a diagonal half drift (count vectors of N)
+cudaError_t launch_half_drift_vec(const redo_table* t, const double2* psi, int64_t count, double2* out,
+                                  cudaStream_t s);
 
 cudaError_t launch_finalize(const redo_table* t, int64_t B, int prec, const void* prod,
                             void* U_out, const double2* U_target, double* F_out, double2* tau_out,

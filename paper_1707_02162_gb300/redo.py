@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libredo.so")
 REDO_OK = 0
 REDO_FP64, REDO_FP32, REDO_FP16X3 = 0, 1, 4
 PRECISIONS = {"fp64": REDO_FP64, "fp32": REDO_FP32, "fp16x3": REDO_FP16X3}
-REDO_TABLE_FP32, REDO_TABLE_FP16X3, REDO_TABLE_LEVELS = 0x1, 0x2, 0x4
+REDO_TABLE_FP32, REDO_TABLE_FP16X3, REDO_TABLE_LEVELS, REDO_TABLE_STRANG = 0x1, 0x2, 0x4, 0x8
 STATUS_WORDS = 4
 STATUS_NONFINITE, STATUS_SATURATED, STATUS_TIMEOUT, STATUS_BADINDEX = range(4)
 
@@ -274,12 +274,13 @@ def redo_profile_read() -> dict:
 class Table:
     """Owning wrapper of a redo_table built from torch tensors on the current device."""
 
-    def __init__(self, H0, Hk, dt, lo, hi, base=64, digits=2, fp32=True, fp16x3=False, levels=False,
+    def __init__(self, H0, Hk, dt, lo, hi, base=64, digits=2, fp32=True, fp16x3=False, levels=False, strang=False,
                  device="cuda"):
         H0 = torch.as_tensor(H0, dtype=torch.complex128, device=device).contiguous()
         Hk = torch.as_tensor(Hk, dtype=torch.complex128, device=device).contiguous()
         flags = ((REDO_TABLE_FP32 if fp32 else 0) | (REDO_TABLE_FP16X3 if fp16x3 else 0)
-                 | (REDO_TABLE_LEVELS if levels else 0))
+                 | (REDO_TABLE_LEVELS if levels else 0) | (REDO_TABLE_STRANG if strang else 0))
+        self.strang = bool(strang)
         self.handle = redo_build_table(H0, Hk, dt, lo, hi, base, digits, flags)
         self.info = redo_table_info(self.handle)
         self.N, self.K = self.info["N"], self.info["K"]
@@ -355,7 +356,8 @@ def _table_simulate(self, q, psi0, obs_diag, prec="fp64", reunit_every=0, want_U
     obs = torch.as_tensor(obs_diag, dtype=torch.float64, device=self.device).contiguous()
     ex = torch.empty((B, M + 1), dtype=torch.float64, device=self.device)
     U = torch.empty((B, self.N, self.N), dtype=torch.complex128, device=self.device) if want_U else None
-    ws = self.workspace(B, M, prec, reunit_every) if want_U else None
+    nbytes = redo_simulate_workspace(self.handle, B, M, prec, reunit_every, want_U)
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device) if nbytes else None
     redo_simulate(self.handle, q, prec, reunit_every, psi0, obs, ex, U, ws, status)
     return ex, U
 
