@@ -36,7 +36,8 @@ Functions and the passage each one follows:
   symmetric (Strang) placement of the drift around the control factors of a
   step, the second-order variant of the Section III step.
 * :func:`simulate_expectation` -- ``<M> = Tr[M rho(t)]`` of Section IV for a
-  pure initial state.
+  pure initial state; :func:`expect_mixed` -- the same for a dense (mixed or
+  deviation) initial density matrix, the order parameter of the freezing study.
 * :func:`mlp_*` -- an FP64 multilayer perceptron with exact (erf) GELU and Adam,
   the learned warm start of the control problem (no counterpart in the paper).
 
@@ -440,6 +441,23 @@ def simulate_expectation(T, D, digits_bm, psi0, obs_diag):
         X = step_propagator(T, D, digits_bm[n]) @ X
         psi = X @ psi0
         out[n + 1] = float(np.sum(obs_diag * (psi.real ** 2 + psi.imag ** 2)))
+    return out, X
+
+
+def expect_mixed(T, D, digits_bm, rho0, obs):
+    """``Tr[rho(t_n) O]`` with ``rho(t_n) = U_n ... U_1 rho0 (U_n ... U_1)^dag``, n = 0..M, for a
+    Hermitian (mixed or deviation) initial density matrix and a Hermitian observable, both
+    dense (Section IV, the order parameter of the noisy exotic-freezing study).
+
+    Returns ``(expect[M+1], U_final)``.
+    """
+    N = D.shape[0]
+    X = np.eye(N, dtype=np.complex128)
+    out = np.empty(digits_bm.shape[0] + 1, dtype=np.float64)
+    out[0] = float(np.trace(rho0 @ obs).real)
+    for n in range(digits_bm.shape[0]):
+        X = step_propagator(T, D, digits_bm[n]) @ X
+        out[n + 1] = float(np.trace(X @ rho0 @ X.conj().T @ obs).real)
     return out, X
 
 

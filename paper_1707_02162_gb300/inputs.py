@@ -257,3 +257,59 @@ def pauli_generator(strings: list[str], theta: np.ndarray) -> np.ndarray:
     (the target is an input of the control problem, not part of REDO).
     """
     return sum(t * pauli_string(s) for s, t in zip(strings, theta))
+
+
+# ---------------------------------------------------------------------------
+# Noisy exotic freezing (Section IV): driven Ising chain, order parameter Q(omega, lambda)
+# ---------------------------------------------------------------------------
+
+FREEZE_H0_AMP = 5 * np.pi        # h0 (rad/s)
+FREEZE_T = 20 * np.pi            # averaging window [0, T] (s)
+
+
+def _hadamard_all(n: int) -> np.ndarray:
+    h = np.array([[1, 1], [1, -1]], dtype=np.complex128) / np.sqrt(2.0)
+    out = np.array([[1.0 + 0j]])
+    for _ in range(n):
+        out = np.kron(out, h)
+    return out
+
+
+def freezing_system(n: int = 3, h0: float = FREEZE_H0_AMP, basis: str = "z"):
+    """Ising chain ``H(t) = -J sum_i 2 I_iz I_{i+1,z} - h(t) sum_i I_ix`` with ``J = h0/20``.
+
+    Returns ``(H0, Hk, rho0, obs)``: the drift (the Z-Z chain), one control term
+    ``Hk[0] = -sum_i I_ix`` whose coefficient is the drive ``h(t)``, and
+    ``rho0 = obs = sum_i I_ix`` (initial deviation density matrix and measured
+    x-magnetisation).  ``basis="x"`` conjugates all four by the Hadamard on every
+    qubit, where ``rho0`` and ``obs`` become diagonal (returned as their diagonals).
+    """
+    J = h0 / 20.0
+    H0 = -J * sum(2 * embed({i: _Z / 2, i + 1: _Z / 2}, n) for i in range(n - 1))
+    Mx = sum(embed({i: _X / 2}, n) for i in range(n))
+    Hk = np.stack([-Mx])
+    if basis == "z":
+        return H0, Hk, Mx.copy(), Mx.copy()
+    Hd = _hadamard_all(n)
+    rot = lambda A: Hd @ A @ Hd
+    m = np.real(np.diag(rot(Mx))).copy()
+    return rot(H0), np.stack([rot(Hk[0])]), m, m.copy()
+
+
+def freezing_drive(omegas: np.ndarray, lams: np.ndarray, M: int, h0: float = FREEZE_H0_AMP,
+                   T: float = FREEZE_T, seed: int = 5) -> np.ndarray:
+    """Drive coefficients ``h0 {(1 - lambda) cos(omega t_n) + lambda eta_n}`` on M steps of
+    ``dt = T/M``, sampled at step midpoints ``t_n = (n + 1/2) dt``, with ``eta_n`` uniform on
+    [-1, 1], independent per step and per (omega, lambda) pulse.  Pulses are ordered
+    omega-major: pulse ``i * len(lams) + j`` has ``omegas[i]``, ``lams[j]``.  Shape (B, M, 1)."""
+    rng = np.random.default_rng(seed)
+    omegas = np.asarray(omegas, dtype=np.float64)
+    lams = np.asarray(lams, dtype=np.float64)
+    dt = T / M
+    t = (np.arange(M) + 0.5) * dt
+    om = np.repeat(omegas, lams.size)[:, None]
+    la = np.tile(lams, omegas.size)[:, None]
+    eta = rng.uniform(-1.0, 1.0, size=(om.shape[0], M))
+    u = h0 * ((1.0 - la) * np.cos(om * t[None, :]) + la * eta)
+    return u[:, :, None]
+

@@ -450,6 +450,68 @@ def test_expectation_rabi_closed_form():
     assert ex[0] == 1.0
 
 
+def _freezing_table(h0, levels_base=100, digits=2, M=400, T=None):
+    H0, Hk, rho0, obs = inputs.freezing_system(3, h0)
+    T_ = inputs.FREEZE_T if T is None else T
+    dt = T_ / M
+    lo, hi = np.array([-h0]), np.array([h0])
+    Tt, D = O.build_table(H0, Hk, dt, lo, hi, levels_base ** digits, levels_base, digits)
+    return H0, Hk, rho0, obs, Tt, D, dt, lo, hi
+
+
+def test_expect_mixed_zero_drive_closed_form():
+    # no drive: the x-magnetisation of the 3-spin Z-Z chain precesses as
+    # (2 cos Jt + cos^2 Jt) / 3 (end spins at J, the middle one at 0 or 2J)
+    h0 = inputs.FREEZE_H0_AMP
+    H0, Hk, rho0, obs, T, D, dt, lo, hi = _freezing_table(h0, levels_base=101, digits=1, M=300, T=6.0)
+    q = np.full((1, 300, 1), 50)                        # level 50 of 101 on [-h0, h0] is u = 0
+    assert abs(O.level_values(q[0, 0, 0], lo[0], hi[0], 101)) < 1e-12
+    ex, _ = O.expect_mixed(T, D, O.level_digits(q, 101, 1)[0], rho0, obs)
+    J = h0 / 20.0
+    t = dt * np.arange(301)
+    Q = ex / ex[0]
+    assert ex[0] == 6.0
+    assert np.abs(Q - (2 * np.cos(J * t) + np.cos(J * t) ** 2) / 3).max() < 1e-10
+
+
+def test_expect_mixed_within_quantisation_bound():
+    # REDO chain against the unquantised split steps of the same drive: |dQ| <= 3 eps_U with
+    # eps_U = sum_n dt |u_n - u^_n| ||H_1||, ||H_1|| = 3/2 (trace norm of rho0 = 6, ||O|| = 3/2)
+    h0 = inputs.FREEZE_H0_AMP
+    M, Tw = 200, 2 * np.pi
+    H0, Hk, rho0, obs, T, D, dt, lo, hi = _freezing_table(h0, M=M, T=Tw)
+    u = inputs.freezing_drive([9.0], [0.3], M, h0=h0, T=Tw)
+    q, _, _ = O.quantize(u, lo, hi, 10000)
+    ex, _ = O.expect_mixed(T, D, O.level_digits(q, 100, 2)[0], rho0, obs)
+    X = np.eye(8, dtype=complex)
+    ref = [float(np.trace(rho0 @ obs).real)]
+    for n in range(M):
+        X = O.split_step(H0, Hk, dt, u[0, n]) @ X
+        ref.append(float(np.trace(X @ rho0 @ X.conj().T @ obs).real))
+    uh = O.level_values(q[0, :, 0], lo[0], hi[0], 10000)
+    eps = np.cumsum(dt * np.abs(u[0, :, 0] - uh) * 1.5)
+    dQ = np.abs(ex - np.array(ref))[1:] / 6.0
+    assert np.all(dQ <= 3 * eps + 1e-12)
+    assert dQ.max() > 0                                  # the grid is coarse enough to show
+
+
+def test_freezing_at_first_bessel_root():
+    # Section IV: at lambda = 0 the order parameter reaches ~1 where J0(2 h0 / omega) = 0;
+    # the first root is omega_1 = 2 h0 / 2.404825557695773
+    h0 = inputs.FREEZE_H0_AMP
+    M = 10000
+    H0, Hk, rho0, obs, T, D, dt, lo, hi = _freezing_table(h0, M=M)
+    w1 = 2 * h0 / 2.404825557695773
+    Qbar = {}
+    for om in (w1 - 3.0, w1, w1 + 3.0):
+        u = inputs.freezing_drive([om], [0.0], M, h0=h0)
+        q, _, _ = O.quantize(u, lo, hi, 10000)
+        ex, _ = O.expect_mixed(T, D, O.level_digits(q, 100, 2)[0], rho0, obs)
+        Qbar[om] = ex[1:].mean() / ex[0]
+    assert Qbar[w1] > 0.99
+    assert Qbar[w1] > Qbar[w1 - 3.0] + 0.1 and Qbar[w1] > Qbar[w1 + 3.0] + 0.1
+
+
 # ---------------------------------------------------------------- MLP
 
 def test_gelu_values():
