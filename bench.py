@@ -502,6 +502,80 @@ def run_workload(args):
                                                  / _peaks().get("bf16_tflops_sustained", 1709.6)),
                     "sample": f"{Ms} of the 2000 steps, all 64 realisations", "table_build_s": build_s,
                     "config": {"N": w.N, "K": w.K, "B": w.B, "M_timed": Ms}})
+    elif args.workload == "freeze":
+        # Section IV noisy exotic freezing: 3-spin Ising chain, Q(omega, lambda) over 500 omegas in
+        # [1, 25] rad/s x 1000 lambdas in [0, 1], 10^4 steps on [0, 20 pi], coefficient grid b=100, d=2.
+        # The drive h0{(1-lambda) cos(omega t_n) + lambda eta_n} is synthesised on the device
+        # (eta_n uniform on [-1, 1] from a seeded Philox generator), pulses omega-major.
+        n_om = args.B if args.B != B_FULL else 500
+        n_la = 1000
+        M = args.M if args.M != M_FULL else 10000
+        h0, Tw = inputs.FREEZE_H0_AMP, inputs.FREEZE_T
+        H0, Hk, rho, obs = inputs.freezing_system(3, h0, basis="x")
+        t = redo.Table(H0, Hk, Tw / M, np.array([-h0]), np.array([h0]), 100, 2, fp32=True)
+        rho_d = torch.as_tensor(rho, device="cuda")
+        obs_d = torch.as_tensor(obs, device="cuda")
+        oms = torch.linspace(1.0, 25.0, n_om, dtype=torch.float64, device="cuda")
+        las = torch.linspace(0.0, 1.0, n_la, dtype=torch.float64, device="cuda")
+        tn = (torch.arange(M, dtype=torch.float64, device="cuda") + 0.5) * (Tw / M)
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        chunk_om = max(1, min(n_om, 20))
+        Qmap = torch.empty((n_om, n_la), dtype=torch.float64, device="cuda")
+        kern_ms = 0.0
+        ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.time()
+        for i0 in range(0, n_om, chunk_om):
+            om = oms[i0:i0 + chunk_om]
+            Bc = om.numel() * n_la
+            eta = torch.rand((Bc, M), dtype=torch.float64, device="cuda", generator=gen) * 2.0 - 1.0
+            la = las.repeat(om.numel())[:, None]
+            u = (h0 * ((1.0 - la) * torch.cos(om.repeat_interleave(n_la)[:, None] * tn[None, :]) + la * eta))[:, :, None]
+            del eta
+            q = torch.empty(u.shape, dtype=torch.int32, device="cuda")
+            mean = torch.empty(Bc, dtype=torch.float64, device="cuda")
+            ev_a.record()
+            redo.redo_quantize(t.handle, u.contiguous(), q)
+            redo.redo_expect_diag(t.handle, q, "fp32", rho_d, obs_d, None, mean)
+            ev_b.record()
+            torch.cuda.synchronize()
+            kern_ms += ev_a.elapsed_time(ev_b)
+            Qmap[i0:i0 + om.numel()] = (mean / float(np.sum(rho * obs))).reshape(om.numel(), n_la)
+            del u, q
+        wall = time.time() - t0
+        # same-GPU FP64 on the first omega's 1000 pulses (context for the FP32 map)
+        om = oms[:1]
+        eta = torch.rand((n_la, M), dtype=torch.float64, device="cuda", generator=gen) * 2.0 - 1.0
+        u = (h0 * ((1.0 - las[:, None]) * torch.cos(om[0] * tn[None, :]) + las[:, None] * eta))[:, :, None].contiguous()
+        q = torch.empty(u.shape, dtype=torch.int32, device="cuda")
+        redo.redo_quantize(t.handle, u, q)
+        mean64 = torch.empty(n_la, dtype=torch.float64, device="cuda")
+        ev_a.record()
+        redo.redo_expect_diag(t.handle, q, "fp64", rho_d, obs_d, None, mean64)
+        ev_b.record()
+        torch.cuda.synchronize()
+        fp64_rate = n_la * M / (ev_a.elapsed_time(ev_b) / 1e3)
+        mean32 = torch.empty(n_la, dtype=torch.float64, device="cuda")
+        redo.redo_expect_diag(t.handle, q, "fp32", rho_d, obs_d, None, mean32)
+        fp32_vs_fp64 = float((mean32 - mean64).abs().max() / float(np.sum(rho * obs)))
+        Q0 = Qmap[:, 0].cpu().numpy()
+        omh = oms.cpu().numpy()
+        from scipy.special import jn_zeros
+        roots = [2 * h0 / z for z in jn_zeros(0, 3)]
+        peaks = {}
+        for r in roots:
+            sel = np.abs(omh - r) < 1.5
+            if sel.any():
+                peaks[f"{r:.3f}"] = {"omega_at_max_Q": float(omh[sel][np.argmax(Q0[sel])]), "max_Q": float(Q0[sel].max())}
+        steps = n_om * n_la * M
+        out.update({"metric": "noisy exotic freezing Q(omega, lambda) map: pulse-steps/s", "unit": "pulse-steps/s",
+                    "value": steps / (kern_ms / 1e3), "kernel_ms": kern_ms, "wall_s_with_drive_synthesis": wall,
+                    "precision": "fp32 chains, fp64 reductions", "pulses": n_om * n_la, "steps": M,
+                    "fp64_same_gpu": {"pulse_steps_per_s": fp64_rate, "sample": f"{n_la} pulses x {M} steps",
+                                      "max_abs_dQ_fp32_vs_fp64": fp32_vs_fp64},
+                    "lambda0_peaks_vs_bessel_roots": peaks,
+                    "Q_mean_lambda1": float(Qmap[:, -1].mean()), "Q_mean_lambda0": float(Q0.mean()),
+                    "config": {"N": 8, "K": 1, "h0": h0, "J": h0 / 20, "omegas": [1.0, 25.0, n_om],
+                               "lambdas": [0.0, 1.0, n_la], "T": Tw, "base": 100, "digits": 2}})
     elif args.workload == "plain":
         # 3 qubits (N=8), M=1000: latency of one pulse and throughput of 4096 replicas
         res = {}
@@ -581,7 +655,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="prop",
-                    choices=["prop", "grape", "sim", "plain", "warmstart", "warmstart_study"],
+                    choices=["prop", "grape", "sim", "plain", "warmstart", "warmstart_study", "freeze"],
                     help="prop (default): the batched propagation line; others: auxiliary measurements")
     ap.add_argument("--B", type=int, default=B_FULL, help="pulses (smaller only for profiling captures)")
     ap.add_argument("--M", type=int, default=M_FULL, help="steps per pulse (smaller only for profiling captures)")

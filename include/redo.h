@@ -281,6 +281,26 @@ redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int6
                           int32_t psi0_batched, const double* obs_diag, double* expect,
                           void* U_final, void* workspace, size_t workspace_bytes,
                           int64_t* dev_status, void* stream);
+
+/*
+ * redo_expect_diag -- e_n = Tr[rho(t_n) O], rho(t_n) = U_n ... U_1 rho (U_n ... U_1)^dag,
+ * n = 0..M, for a diagonal initial density matrix rho (mixed or a traceless deviation
+ * matrix) and a diagonal observable O: e_n = sum_{r,c} rho_c O_r |(U_n ... U_1)[r][c]|^2.
+ * Section IV's order parameter Q of the noisy exotic-freezing study is of this form in the
+ * basis where rho(0) = O = sum_i I_ix are diagonal (the Hamiltonian terms passed to
+ * redo_build_table are then given in that basis).  N <= 64.
+ *  q            device int32 [B][M][K] levels from redo_quantize.
+ *  prec         REDO_FP64 or REDO_FP32 (the latter needs REDO_TABLE_FP32); the reduction is FP64.
+ *  rho_diag     device double [N];  obs_diag device double [N].
+ *  expect       device double [B][M+1] or NULL;  expect_mean device double [B] or NULL:
+ *               the mean of e_1 .. e_M (e_0 when M = 0).  At least one of the two.
+ * With a symmetric-split table the drift must be diagonal (then e_n equals that of the
+ * folded chain).  Errors: REDO_ERR_INVALID, REDO_ERR_UNSUPPORTED (N > 64, other
+ * precisions), REDO_ERR_CUDA.  No synchronisation.
+ */
+redo_status redo_expect_diag(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                             redo_precision prec, const double* rho_diag, const double* obs_diag,
+                             double* expect, double* expect_mean, int64_t* dev_status, void* stream);
 redo_status redo_simulate_workspace(const redo_table* t, int64_t B, int64_t M,
                                     redo_precision prec, int32_t reunit_every, int32_t want_U,
                                     size_t* bytes);

@@ -130,4 +130,146 @@ cudaError_t launch_sim_state(const redo_table* t, const int32_t* q, int64_t B, i
 #undef SIM_CASE
 }
 
+// ============================================================================
+// Mixed diagonal states: e_n = Tr[U_n rho U_n^dag O] = sum_{r,c} rho_c o_r |U_n[r][c]|^2 for
+// diagonal rho and O (Section IV's order parameter when both are diagonal in the working
+// basis).  One CTA per pulse keeps U_n in shared memory (ping-pong), stages each gathered
+// operator in shared memory with the next one already loaded into registers, and reduces
+// e_n after every step; it writes the series and/or its mean over n = 1..M.
+// ============================================================================
+template <int N> struct MixShape {
+  static constexpr int THREADS = N * N < 64 ? 64 : (N * N > 256 ? 256 : N * N);
+  static constexpr int EPT = (N * N + THREADS - 1) / THREADS;   // entries per thread
+};
+
+template <typename R, int N>
+__global__ void __launch_bounds__(MixShape<N>::THREADS)
+expect_diag_kernel(const cplx<R>* __restrict__ T, const int32_t* __restrict__ q, int64_t M, int K, int d,
+                   int base, int64_t levels, const double* __restrict__ rho, const double* __restrict__ obs,
+                   double* __restrict__ expect, double* __restrict__ mean, int64_t* status) {
+  using MS = MixShape<N>;
+  constexpr int TH = MS::THREADS, EPT = MS::EPT, N2 = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* U0 = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* U1 = U0 + N2;
+  cplx<R>* A = U1 + N2;
+  __shared__ double red[TH / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t b = blockIdx.x;
+  for (int e = tid; e < N2; e += TH) U0[e] = cmake<R>((e / N == e % N) ? R(1) : R(0), R(0));
+
+  auto reduce = [&](const cplx<R>* U) -> double {
+    double v = 0.0;
+    for (int e = tid; e < N2; e += TH) {
+      const double re = (double)U[e].x, im = (double)U[e].y;
+      v += rho[e % N] * obs[e / N] * (re * re + im * im);
+    }
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double out = 0.0;
+#pragma unroll
+    for (int w = 0; w < TH / 32; ++w) out += red[w];
+    return out;
+  };
+  auto factor = [&](int64_t f) -> const cplx<R>* {
+    const int64_t kd = (int64_t)K * d;
+    const int64_t n = f / kd;
+    const int rr = (int)(f - n * kd);
+    const int k = rr / d, j = rr - k * d;
+    int32_t qv = q[(b * M + n) * K + k];
+    if (qv < 0 || qv >= levels) {
+      if (status && tid == 0) atomicAdd((unsigned long long*)&status[REDO_STATUS_BADINDEX], 1ull);
+      qv = 0;
+    }
+    for (int i = 0; i < j; ++i) qv /= base;
+    return T + ((int64_t)(k * d + j) * base + qv % base) * N2;
+  };
+
+  __syncthreads();
+  const double e0 = reduce(U0);
+  if (tid == 0 && expect) expect[b * (M + 1)] = e0;
+  double acc = 0.0;
+  const int64_t kd = (int64_t)K * d, F = M * kd;
+  cplx<R> nxt[EPT];
+  if (F > 0) {
+    const cplx<R>* a = factor(0);
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = tid + i * TH;
+      if (e < N2) nxt[i] = a[e];
+    }
+  }
+  cplx<R>* cur = U0;
+  cplx<R>* out = U1;
+  for (int64_t f = 0; f < F; ++f) {
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = tid + i * TH;
+      if (e < N2) A[e] = nxt[i];
+    }
+    __syncthreads();
+    if (f + 1 < F) {
+      const cplx<R>* a = factor(f + 1);
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        const int e = tid + i * TH;
+        if (e < N2) nxt[i] = a[e];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = tid + i * TH;
+      if (e < N2) {
+        const int r = e / N, c = e % N;
+        cplx<R> s = cmake<R>(R(0), R(0));
+#pragma unroll 8
+        for (int k = 0; k < N; ++k) cfma<R>(s, A[r * N + k], cur[k * N + c]);
+        out[e] = s;
+      }
+    }
+    __syncthreads();
+    cplx<R>* tmp = cur;
+    cur = out;
+    out = tmp;
+    if ((f + 1) % kd == 0) {
+      const double ev = reduce(cur);
+      acc += ev;
+      if (tid == 0 && expect) expect[b * (M + 1) + (f + 1) / kd] = ev;
+    }
+  }
+  if (tid == 0 && mean) mean[b] = M > 0 ? acc / (double)M : e0;
+}
+
+template <typename R, int N>
+static cudaError_t expect_diag_n(const redo_table* t, const int32_t* q, int64_t B, int64_t M, const double* rho,
+                                 const double* obs, double* expect, double* mean, int64_t* status,
+                                 cudaStream_t s) {
+  const cplx<R>* T = std::is_same<R, double>::value ? (const cplx<R>*)t->T64 : (const cplx<R>*)t->T32;
+  const size_t smem = 3 * sizeof(cplx<R>) * N * N;
+  cudaError_t e = cudaFuncSetAttribute(expect_diag_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  expect_diag_kernel<R, N><<<(unsigned)B, MixShape<N>::THREADS, smem, s>>>(
+      T, q, M, t->K, t->digits, t->base, t->levels, rho, obs, expect, mean, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expect_diag(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
+                               const double* rho, const double* obs, double* expect, double* mean,
+                               int64_t* status, cudaStream_t s) {
+  if (B == 0) return cudaSuccess;
+  const bool dbl = prec == REDO_FP64;
+#define MIX_CASE(n)                                                                                  \
+  case n:                                                                                            \
+    return dbl ? expect_diag_n<double, n>(t, q, B, M, rho, obs, expect, mean, status, s)             \
+               : expect_diag_n<float, n>(t, q, B, M, rho, obs, expect, mean, status, s);
+  switch (t->N) {
+    MIX_CASE(2) MIX_CASE(4) MIX_CASE(8) MIX_CASE(16) MIX_CASE(32) MIX_CASE(64)
+    default: return cudaErrorInvalidValue;
+  }
+#undef MIX_CASE
+}
+
 }  // namespace redo

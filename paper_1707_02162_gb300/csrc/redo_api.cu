@@ -710,6 +710,29 @@ redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int6
   return REDO_OK;
 }
 
+redo_status redo_expect_diag(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                             redo_precision prec, const double* rho_diag, const double* obs_diag,
+                             double* expect, double* expect_mean, int64_t* dev_status, void* stream) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  if (prec != REDO_FP64 && prec != REDO_FP32)
+    return set_error(REDO_ERR_UNSUPPORTED, "redo_expect_diag supports REDO_FP64 and REDO_FP32");
+  redo_status st = check_prec(t, prec);
+  if (st != REDO_OK) return st;
+  if (t->N > kSmallN) return set_error(REDO_ERR_UNSUPPORTED, "redo_expect_diag needs N <= 64");
+  if (t->strang && !t->h0_diagonal)
+    return set_error(REDO_ERR_UNSUPPORTED, "symmetric split with a non-diagonal drift");
+  if (B == 0) return REDO_OK;
+  if (!rho_diag || !obs_diag) return set_error(REDO_ERR_INVALID, "null rho_diag or obs_diag");
+  if (!expect && !expect_mean) return set_error(REDO_ERR_INVALID, "nothing to compute");
+  if (M > 0 && !q) return set_error(REDO_ERR_INVALID, "q is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(2, s);
+  cudaError_t e = launch_expect_diag(t, q, B, M, prec, rho_diag, obs_diag, expect, expect_mean, dev_status, s);
+  if (e != cudaSuccess) return cuda_error(e, "mixed-state expectations");
+  return REDO_OK;
+}
+
 static redo_status check_mlp(int32_t layers, const int32_t* sizes) {
   if (layers < 1 || layers > 32 || !sizes) return set_error(REDO_ERR_INVALID, "1 <= layers <= 32");
   for (int l = 0; l <= layers; ++l)

@@ -28,7 +28,7 @@ EXPORTS = [
     "redo_propagate", "redo_propagate_workspace", "redo_last_error", "redo_profile_enable",
     "redo_profile_read", "redo_propagate_noalloc", "redo_fidelity_grad", "redo_fidelity_grad_workspace",
     "redo_grape_step", "redo_simulate", "redo_simulate_workspace", "redo_mlp_sizes", "redo_mlp_forward",
-    "redo_mlp_backward", "redo_mlp_adam", "redo_grape_adam_step",
+    "redo_mlp_backward", "redo_mlp_adam", "redo_grape_adam_step", "redo_expect_diag",
 ]
 PROFILE_PHASES = 11
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_grape_step.argtypes = [vp, vp, vp, i64, i64, dbl, vp, vp]
     L.redo_simulate.argtypes = [vp, vp, i64, i64, i32, i32, vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_simulate_workspace.argtypes = [vp, i64, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_expect_diag.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
     L.redo_mlp_sizes.argtypes = [i32, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.redo_mlp_forward.argtypes = [i32, vp, vp, vp, i64, vp, vp, vp]
     L.redo_mlp_backward.argtypes = [i32, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp]
@@ -218,6 +219,15 @@ def redo_simulate(handle: int, q: torch.Tensor, prec, reunit_every: int, psi0: t
                                         _ptr(workspace), nbytes, _ptr(status), _stream(stream)))
 
 
+def redo_expect_diag(handle: int, q: torch.Tensor, prec, rho_diag: torch.Tensor, obs_diag: torch.Tensor,
+                     expect: torch.Tensor | None, expect_mean: torch.Tensor | None,
+                     status: torch.Tensor | None = None, stream=None):
+    B, M = q.shape[0], q.shape[1]
+    _check(load_library().redo_expect_diag(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), _ptr(rho_diag),
+                                           _ptr(obs_diag), _ptr(expect), _ptr(expect_mean), _ptr(status),
+                                           _stream(stream)))
+
+
 def _sizes_arg(sizes):
     arr = (ctypes.c_int32 * len(sizes))(*[int(x) for x in sizes])
     return arr, len(sizes) - 1
@@ -363,6 +373,20 @@ def _table_simulate(self, q, psi0, obs_diag, prec="fp64", reunit_every=0, want_U
 
 
 Table.simulate = _table_simulate
+
+
+def _table_expect_diag(self, q, rho_diag, obs_diag, prec="fp64", series=True, status=None):
+    """(expect [B][M+1] or None, mean over steps 1..M [B]) of Tr[rho(t_n) O], diagonal rho and O."""
+    B, M = q.shape[0], q.shape[1]
+    rho = torch.as_tensor(rho_diag, dtype=torch.float64, device=self.device).contiguous()
+    obs = torch.as_tensor(obs_diag, dtype=torch.float64, device=self.device).contiguous()
+    ex = torch.empty((B, M + 1), dtype=torch.float64, device=self.device) if series else None
+    mean = torch.empty(B, dtype=torch.float64, device=self.device)
+    redo_expect_diag(self.handle, q, prec, rho, obs, ex, mean, status)
+    return ex, mean
+
+
+Table.expect_diag = _table_expect_diag
 
 
 def new_status(device="cuda") -> torch.Tensor:

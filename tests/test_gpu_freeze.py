@@ -1,0 +1,83 @@
+"""Mixed diagonal-state expectations (Tr[rho(t) O]) and the noisy exotic-freezing order
+parameter of Section IV on the GPU, against the oracle's dense-matrix definition."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import redo_oracle as O
+from paper_1707_02162_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+H0_AMP = inputs.FREEZE_H0_AMP
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_02162_gb300 import build
+    build.build()
+
+
+def _gpu_table(M, T):
+    from paper_1707_02162_gb300 import redo
+    H0, Hk, rho, obs = inputs.freezing_system(3, H0_AMP, basis="x")
+    t = redo.Table(H0, Hk, T / M, np.array([-H0_AMP]), np.array([H0_AMP]), 100, 2, fp32=True)
+    return t, rho, obs
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_freezing_series_matches_oracle(prec, tol):
+    M, T = 300, 2 * np.pi
+    u = inputs.freezing_drive([7.0, 13.06], [0.0, 0.4], M, T=T)
+    t, rho, obs = _gpu_table(M, T)
+    q = t.quantize(u)
+    ex, mean = t.expect_diag(q, rho, obs, prec)
+    H0z, Hkz, rho0, obsz = inputs.freezing_system(3, H0_AMP, basis="z")
+    lo, hi = np.array([-H0_AMP]), np.array([H0_AMP])
+    To, Do = O.build_table(H0z, Hkz, T / M, lo, hi, 10000, 100, 2)
+    qo, _, _ = O.quantize(u, lo, hi, 10000)
+    dig = O.level_digits(qo, 100, 2)
+    exg = ex.cpu().numpy()
+    for b in range(u.shape[0]):
+        eo, _ = O.expect_mixed(To, Do, dig[b], rho0, obsz)
+        assert np.abs(exg[b] - eo).max() < tol * abs(eo[0])
+        assert abs(mean.cpu().numpy()[b] - exg[b, 1:].mean()) < 1e-12 * abs(eo[0])
+
+
+def test_freezing_at_first_bessel_root_gpu():
+    M = 10000
+    w1 = 2 * H0_AMP / 2.404825557695773
+    u = inputs.freezing_drive([w1 - 3.0, w1, w1 + 3.0], [0.0], M)
+    t, rho, obs = _gpu_table(M, inputs.FREEZE_T)
+    q = t.quantize(u)
+    _, mean = t.expect_diag(q, rho, obs, "fp32", series=False)
+    Q = mean.cpu().numpy() / float(np.sum(rho * obs))
+    assert Q[1] > 0.99 and Q[1] > Q[0] + 0.1 and Q[1] > Q[2] + 0.1
+
+
+@pytest.mark.parametrize("n", [1, 4])
+def test_expect_diag_random_diagonals(n):
+    # generic diagonal rho and O on the x/y-controlled ZZ system, N = 2 and 16
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(0, n_qubits=n, B=3, M=25, base=16, digits=2)
+    rng = np.random.default_rng(9)
+    rho, obs = rng.uniform(-1, 1, w.N), rng.uniform(-1, 1, w.N)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits)
+    ex, mean = t.expect_diag(t.quantize(w.u), rho, obs, "fp64")
+    To, Do = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
+    qo, _, _ = O.quantize(w.u, w.lo, w.hi, w.levels)
+    dig = O.level_digits(qo, w.base, w.digits)
+    for b in range(w.B):
+        Tf = To.copy()
+        eo, _ = O.expect_mixed(Tf, Do, dig[b], np.diag(rho).astype(complex), np.diag(obs).astype(complex))
+        assert np.abs(ex.cpu().numpy()[b] - eo).max() < 1e-12
+
+
+def test_expect_diag_rejects_unsupported():
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(0, n_qubits=7, B=1, M=4, base=16, digits=2)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits)
+    with pytest.raises(redo.RedoError):
+        t.expect_diag(t.quantize(w.u), np.ones(128), np.ones(128), "fp64")
