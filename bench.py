@@ -560,10 +560,10 @@ def run_workload(args):
         Q0 = Qmap[:, 0].cpu().numpy()
         omh = oms.cpu().numpy()
         from scipy.special import jn_zeros
-        roots = [2 * h0 / z for z in jn_zeros(0, 3)]
+        roots = [2 * h0 / z for z in jn_zeros(0, 4)]
         peaks = {}
         for r in roots:
-            sel = np.abs(omh - r) < 1.5
+            sel = np.abs(omh - r) < 0.4
             if sel.any():
                 peaks[f"{r:.3f}"] = {"omega_at_max_Q": float(omh[sel][np.argmax(Q0[sel])]), "max_Q": float(Q0[sel].max())}
         steps = n_om * n_la * M
