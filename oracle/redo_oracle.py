@@ -30,6 +30,8 @@ Functions and the passage each one follows:
 * :func:`grape_gradient` -- the GRAPE gradient ``dF/du_kn`` of the REDO split
   model (Section III, flowchart Fig. fc; the paper gives no formula, the
   derivative is taken from the definitions, see its docstring).
+* :func:`state_transfer_gradient` -- the state-to-state fidelity ``|<psi_T|U|psi0>|^2``
+  and its GRAPE gradient, from the same definitions.
 * :func:`polar_unitary` -- polar factor ``P (P^dag P)^(-1/2)``.
 * :func:`half_drift` / :func:`strang_step_propagator` / :func:`propagate_strang`
   / :func:`strang_split_step` / :func:`simulate_expectation_strang` -- the
@@ -408,6 +410,47 @@ def grape_gradient(T, D, Hk, dt, digits_bm, U_target):
             W = Bk[k] @ Y @ Ak[k]
             dtau = -1j * dt * np.trace(Hk[k] @ W)
             g[n, k] = 2.0 / (N * N) * (np.conj(tau) * dtau).real
+    return F, g
+
+
+def state_transfer_gradient(T, D, Hk, dt, digits_bm, psi0, psiT):
+    """``(F_S, g)``: the state-transfer fidelity ``F_S = |<psi_T| U |psi0>|^2`` (Section III's
+    state-to-state fidelity) and ``g[n][k] = dF_S/du_kn`` of the split model at the quantised
+    point, from the same factorisation as :func:`grape_gradient`:
+    ``a = <psi_T| U |psi0>``, ``da/du_kn = -i dt <psi_T| L_n A_k H_k B_k X_{n-1} |psi0>``,
+    ``dF_S/du_kn = 2 Re(conj(a) da/du_kn)``.  Formed explicitly (no recursion).
+    """
+    M, K, _ = digits_bm.shape
+    N = D.shape[0]
+    I = np.eye(N, dtype=np.complex128)
+    steps = [step_propagator(T, D, digits_bm[n]) for n in range(M)]
+    X = [I]
+    for n in range(M):
+        X.append(steps[n] @ X[-1])
+    Lsuf = [None] * (M + 1)
+    Lsuf[M] = I
+    for n in range(M - 1, -1, -1):
+        Lsuf[n] = Lsuf[n + 1] @ steps[n]
+    psi0 = np.asarray(psi0, dtype=np.complex128)
+    bra = np.conj(np.asarray(psiT, dtype=np.complex128))
+    a = complex(bra @ (X[M] @ psi0))
+    F = abs(a) ** 2
+    g = np.zeros((M, K), dtype=np.float64)
+    for n in range(M):
+        E = step_factors(T, D, digits_bm[n])
+        Bk = []
+        acc = D
+        for k in range(K):
+            acc = E[k] @ acc
+            Bk.append(acc)
+        Ak = [None] * K
+        acc = I
+        for k in range(K - 1, -1, -1):
+            Ak[k] = acc
+            acc = acc @ E[k]
+        for k in range(K):
+            da = -1j * dt * complex(bra @ (Lsuf[n + 1] @ Ak[k] @ Hk[k] @ Bk[k] @ X[n] @ psi0))
+            g[n, k] = 2.0 * (np.conj(a) * da).real
     return F, g
 
 

@@ -408,6 +408,65 @@ def test_gradient_single_qubit_closed_form():
     assert np.abs(g[:, 0] + dt / 2 * math.sin(phi)).max() < 1e-16
 
 
+def _split_state_fidelity(H0, Hk, dt, u, psi0, psiT):
+    U = np.eye(H0.shape[0], dtype=complex)
+    for n in range(u.shape[0]):
+        U = O.split_step(H0, Hk, dt, u[n]) @ U
+    return abs(np.conj(psiT) @ U @ psi0) ** 2
+
+
+def test_state_transfer_gradient_matches_central_differences():
+    w = inputs.config(0, M=8)
+    T, D = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
+    q, _, _ = O.quantize(w.u, w.lo, w.hi, w.levels)
+    dig = O.level_digits(q, w.base, w.digits)
+    rng = np.random.default_rng(21)
+    psi0 = np.eye(w.N)[0].astype(complex)
+    psiT = rng.normal(size=w.N) + 1j * rng.normal(size=w.N)
+    psiT /= np.linalg.norm(psiT)
+    F, g = O.state_transfer_gradient(T, D, w.Hk, w.dt, dig[0], psi0, psiT)
+    uh = O.level_values(q[0], w.lo, w.hi, w.levels)
+    assert abs(F - _split_state_fidelity(w.H0, w.Hk, w.dt, uh, psi0, psiT)) < 1e-13
+    h = 1e-6 * w.extra["Omega"]
+    for n in range(w.M):
+        for k in range(w.K):
+            up, um = uh.copy(), uh.copy()
+            up[n, k] += h
+            um[n, k] -= h
+            fd = (_split_state_fidelity(w.H0, w.Hk, w.dt, up, psi0, psiT)
+                  - _split_state_fidelity(w.H0, w.Hk, w.dt, um, psi0, psiT)) / (2 * h)
+            assert abs(fd - g[n, k]) < 1e-9 * max(1.0, abs(g).max()) + 2e-12 / h
+
+
+def test_state_transfer_single_qubit_closed_form():
+    # H0 = 0, control X/2, |0> -> |1>: F_S = sin^2(phi/2), phi = dt sum u; dF_S/du_n = (dt/2) sin(phi)
+    H0 = np.zeros((2, 2), dtype=complex)
+    Hk = np.stack([SX / 2])
+    dt, L = 1e-4, 4096
+    lo, hi = np.array([-1e4]), np.array([1e4])
+    T, D = O.build_table(H0, Hk, dt, lo, hi, L, 64, 2)
+    rng = np.random.default_rng(22)
+    q, _, _ = O.quantize(rng.uniform(-1e4, 1e4, size=(6, 1)), lo, hi, L)
+    dig = O.level_digits(q, 64, 2)
+    F, g = O.state_transfer_gradient(T, D, Hk, dt, dig, np.array([1, 0], complex), np.array([0, 1], complex))
+    phi = dt * O.level_values(q, lo, hi, L).sum()
+    assert abs(F - math.sin(phi / 2) ** 2) < 1e-14
+    assert np.abs(g[:, 0] - dt / 2 * math.sin(phi)).max() < 1e-16
+
+
+def test_state_transfer_is_the_unitary_fidelity_of_one_column():
+    # for N = 2 and psi_T = U psi0 the state fidelity is 1 and its gradient vanishes
+    w = inputs.config(0, n_qubits=1, M=6)
+    w.Hk = w.Hk[:2]
+    T, D = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
+    q, _, _ = O.quantize(w.u, w.lo, w.hi, w.levels)
+    dig = O.level_digits(q, w.base, w.digits)
+    U = O.propagate(T, D, dig[0])
+    psi0 = np.array([0.6, 0.8j])
+    F, g = O.state_transfer_gradient(T, D, w.Hk, w.dt, dig[0], psi0, U @ psi0)
+    assert abs(F - 1.0) < 1e-14 and np.abs(g).max() < 1e-12
+
+
 def test_gradient_vanishes_at_reached_target():
     w = inputs.config(0, M=6)
     T, D = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
