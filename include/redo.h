@@ -283,6 +283,27 @@ redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int6
                           int64_t* dev_status, void* stream);
 
 /*
+ * redo_state_grad -- state-to-state GRAPE (Section III's state fidelity, the gradient
+ * derived like redo_fidelity_grad's): a_b = <psi_T| U_M ... U_1 |psi0>, F_b = |a_b|^2 and
+ * grad[b][n][k] = dF_b/du_kn = 2 dt Im(conj(a_b) <chi| H_k |phi>), phi the state after the last
+ * digit factor of term k in step n and chi the target pulled back through the later factors.
+ * Costs O(N^2) per factor (matrix-vector products, forward and then reverse, undoing each
+ * unitary factor on both vectors), so it is the cheap form of GRAPE for large N.
+ *  q            device int32 [B][M][K] levels.
+ *  prec         REDO_FP64 or REDO_FP32 (operators of that precision; traces and a in FP64).
+ *  psi0, psi_target  device complex128 [N], or [B][N] when batched != 0.
+ *  F_out        device double [B] or NULL;  grad device double [B][M][K] or NULL (one of the two).
+ *  workspace    >= redo_state_grad_workspace bytes (zero unless the table is a symmetric-split
+ *               one, which also needs a diagonal H0).
+ * Errors: REDO_ERR_INVALID, REDO_ERR_UNSUPPORTED, REDO_ERR_CUDA.  No synchronisation.
+ */
+redo_status redo_state_grad_workspace(const redo_table* t, int64_t B, size_t* bytes);
+redo_status redo_state_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M, redo_precision prec,
+                            const void* psi0, const void* psi_target, int32_t batched, double* F_out,
+                            double* grad, void* workspace, size_t workspace_bytes, int64_t* dev_status,
+                            void* stream);
+
+/*
  * redo_expect_diag -- e_n = Tr[rho(t_n) O], rho(t_n) = U_n ... U_1 rho (U_n ... U_1)^dag,
  * n = 0..M, for a diagonal initial density matrix rho (mixed or a traceless deviation
  * matrix) and a diagonal observable O: e_n = sum_{r,c} rho_c O_r |(U_n ... U_1)[r][c]|^2.

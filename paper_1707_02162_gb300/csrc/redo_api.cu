@@ -710,6 +710,54 @@ redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int6
   return REDO_OK;
 }
 
+redo_status redo_state_grad_workspace(const redo_table* t, int64_t B, size_t* bytes) {
+  if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
+  if (B < 0) return set_error(REDO_ERR_INVALID, "negative B");
+  *bytes = t->strang ? 2 * (((size_t)B * t->N * sizeof(double2) + 255) & ~(size_t)255) : 0;
+  return REDO_OK;
+}
+
+redo_status redo_state_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M, redo_precision prec,
+                            const void* psi0, const void* psi_target, int32_t batched, double* F_out,
+                            double* grad, void* workspace, size_t workspace_bytes, int64_t* dev_status,
+                            void* stream) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  if (prec != REDO_FP64 && prec != REDO_FP32)
+    return set_error(REDO_ERR_UNSUPPORTED, "redo_state_grad supports REDO_FP64 and REDO_FP32");
+  redo_status st = check_prec(t, prec);
+  if (st != REDO_OK) return st;
+  if (t->strang && !t->h0_diagonal)
+    return set_error(REDO_ERR_UNSUPPORTED, "symmetric split with a non-diagonal drift");
+  if (B == 0) return REDO_OK;
+  if (!psi0 || !psi_target) return set_error(REDO_ERR_INVALID, "null psi0 or psi_target");
+  if (!F_out && !grad) return set_error(REDO_ERR_INVALID, "nothing to compute");
+  if (M > 0 && !q) return set_error(REDO_ERR_INVALID, "q is NULL");
+  size_t need = 0;
+  redo_state_grad_workspace(t, B, &need);
+  if (need && (!workspace || workspace_bytes < need))
+    return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", need);
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(7, s);
+  cudaError_t e;
+  const double2* p0 = (const double2*)psi0;
+  const double2* pT = (const double2*)psi_target;
+  if (t->strang) {
+    // <psi_T| D_h U D_h^dag |psi0> = <D_h^dag psi_T| U |D_h^dag psi0>
+    const int64_t nv = batched ? B : 1;
+    double2* w0 = (double2*)workspace;
+    double2* wT = (double2*)((char*)workspace + need / 2);
+    if ((e = launch_half_drift_vec(t, p0, nv, w0, s)) != cudaSuccess ||
+        (e = launch_half_drift_vec(t, pT, nv, wT, s)) != cudaSuccess)
+      return cuda_error(e, "half-drift of the states");
+    p0 = w0;
+    pT = wT;
+  }
+  if ((e = launch_state_grad(t, q, B, M, prec, p0, pT, batched, F_out, grad, dev_status, s)) != cudaSuccess)
+    return cuda_error(e, "state-transfer gradient");
+  return REDO_OK;
+}
+
 redo_status redo_expect_diag(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
                              redo_precision prec, const double* rho_diag, const double* obs_diag,
                              double* expect, double* expect_mean, int64_t* dev_status, void* stream) {

@@ -155,6 +155,9 @@ cudaError_t launch_grad_sweep(const redo_table* t, const int32_t* q, const Chain
                               int64_t* status, cudaStream_t s);
 
 // State simulation (kernels_sim.cu).
+cudaError_t launch_state_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
+                              const double2* psi0, const double2* psiT, int batched, double* F_out, double* grad,
+                              int64_t* status, cudaStream_t s);
 cudaError_t launch_expect_diag(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
                                const double* rho, const double* obs, double* expect, double* mean,
                                int64_t* status, cudaStream_t s);

@@ -29,6 +29,7 @@ EXPORTS = [
     "redo_profile_read", "redo_propagate_noalloc", "redo_fidelity_grad", "redo_fidelity_grad_workspace",
     "redo_grape_step", "redo_simulate", "redo_simulate_workspace", "redo_mlp_sizes", "redo_mlp_forward",
     "redo_mlp_backward", "redo_mlp_adam", "redo_grape_adam_step", "redo_expect_diag",
+    "redo_state_grad", "redo_state_grad_workspace",
 ]
 PROFILE_PHASES = 11
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -67,6 +68,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_simulate.argtypes = [vp, vp, i64, i64, i32, i32, vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_simulate_workspace.argtypes = [vp, i64, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_expect_diag.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
+    L.redo_state_grad_workspace.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_state_grad.argtypes = [vp, vp, i64, i64, i32, vp, vp, i32, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_mlp_sizes.argtypes = [i32, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.redo_mlp_forward.argtypes = [i32, vp, vp, vp, i64, vp, vp, vp]
     L.redo_mlp_backward.argtypes = [i32, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp]
@@ -228,6 +231,23 @@ def redo_expect_diag(handle: int, q: torch.Tensor, prec, rho_diag: torch.Tensor,
                                            _stream(stream)))
 
 
+def redo_state_grad_workspace(handle: int, B: int) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().redo_state_grad_workspace(ctypes.c_void_p(handle), B, ctypes.byref(n)))
+    return n.value
+
+
+def redo_state_grad(handle: int, q: torch.Tensor, prec, psi0: torch.Tensor, psi_target: torch.Tensor,
+                    F: torch.Tensor | None, grad: torch.Tensor | None, workspace: torch.Tensor | None,
+                    status: torch.Tensor | None = None, stream=None):
+    B, M = q.shape[0], q.shape[1]
+    batched = 1 if psi0.dim() == 2 else 0
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load_library().redo_state_grad(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), _ptr(psi0),
+                                          _ptr(psi_target), batched, _ptr(F), _ptr(grad), _ptr(workspace), nbytes,
+                                          _ptr(status), _stream(stream)))
+
+
 def _sizes_arg(sizes):
     arr = (ctypes.c_int32 * len(sizes))(*[int(x) for x in sizes])
     return arr, len(sizes) - 1
@@ -387,6 +407,25 @@ def _table_expect_diag(self, q, rho_diag, obs_diag, prec="fp64", series=True, st
 
 
 Table.expect_diag = _table_expect_diag
+
+
+def _table_state_grad(self, q, psi0, psi_target, prec="fp64", want_grad=True, status=None):
+    """(F [B], grad [B][M][K] or None) of the state fidelity |<psi_T|U|psi0>|^2 at levels q;
+    psi0 and psi_target of shape [N] (shared) or [B][N]."""
+    B, M = q.shape[0], q.shape[1]
+    p0 = torch.as_tensor(psi0, dtype=torch.complex128, device=self.device).contiguous()
+    pT = torch.as_tensor(psi_target, dtype=torch.complex128, device=self.device).contiguous()
+    if p0.dim() != pT.dim():
+        raise ValueError("psi0 and psi_target must both be shared or both batched")
+    F = torch.empty(B, dtype=torch.float64, device=self.device)
+    g = torch.empty((B, M, self.K), dtype=torch.float64, device=self.device) if want_grad else None
+    nbytes = redo_state_grad_workspace(self.handle, B)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device) if nbytes else None
+    redo_state_grad(self.handle, q, prec, p0, pT, F, g, ws, status)
+    return F, g
+
+
+Table.state_grad = _table_state_grad
 
 
 def new_status(device="cuda") -> torch.Tensor:

@@ -1,0 +1,94 @@
+"""State-to-state GRAPE on the GPU (redo_state_grad) against the oracle's explicit gradient,
+for the small and large-N operator layouts, batched states and symmetric-split tables."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import redo_oracle as O
+from paper_1707_02162_gb300 import inputs
+from tests import _ref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_02162_gb300 import build
+    build.build()
+
+
+def _reduced(idx, n, K, B, M, base=16, digits=2):
+    w = inputs.config(idx, n_qubits=n, B=B, M=M, base=base, digits=digits)
+    w.Hk = w.Hk[:K].copy()
+    w.lo, w.hi = w.lo[:K].copy(), w.hi[:K].copy()
+    w.u = w.u[:, :, :K].copy()
+    return w
+
+
+def _states(N, B, seed):
+    rng = np.random.default_rng(seed)
+    p0 = rng.normal(size=(B, N)) + 1j * rng.normal(size=(B, N))
+    pT = rng.normal(size=(B, N)) + 1j * rng.normal(size=(B, N))
+    return p0 / np.linalg.norm(p0, axis=1, keepdims=True), pT / np.linalg.norm(pT, axis=1, keepdims=True)
+
+
+def _check(w, prec, rel, batched=True, seed=3, **tkw):
+    from paper_1707_02162_gb300 import redo
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, **tkw)
+    q = t.quantize(w.u)
+    p0, pT = _states(w.N, w.B, seed)
+    if not batched:
+        p0, pT = p0[0], pT[0]
+    F, g = t.state_grad(q, p0, pT, prec)
+    To, Do = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    for b in range(w.B):
+        a0, aT = (p0[b], pT[b]) if batched else (p0, pT)
+        Fo, go = O.state_transfer_gradient(To, Do, w.Hk, w.dt, dig[b], a0, aT)
+        assert abs(F.cpu().numpy()[b] - Fo) < (1e-13 if prec == "fp64" else 1e-6)
+        assert np.abs(g.cpu().numpy()[b] - go).max() <= rel * np.abs(go).max()
+
+
+@pytest.mark.parametrize("prec,rel", [("fp64", 1e-11), ("fp32", 1e-4)])
+def test_state_grad_n8(prec, rel):
+    _check(inputs.config(0, B=3, M=12, base=16, digits=2), prec, rel)
+
+
+def test_state_grad_n8_shared_states():
+    _check(inputs.config(0, B=2, M=9, base=16, digits=2), "fp64", 1e-11, batched=False)
+
+
+def test_state_grad_n64():
+    _check(_reduced(1, 6, 2, 2, 8), "fp64", 1e-11)
+
+
+@pytest.mark.parametrize("prec,rel", [("fp64", 1e-10), ("fp32", 1e-3)])
+def test_state_grad_n256_level_table(prec, rel):
+    _check(_reduced(2, 8, 2, 1, 5), prec, rel, levels=True)
+
+
+def test_state_grad_symmetric_split_central_differences():
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(0, B=1, M=10, base=64, digits=2)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, strang=True)
+    q = t.quantize(w.u)
+    p0, pT = _states(w.N, 1, 7)
+    F, g = t.state_grad(q, p0[0], pT[0], "fp64")
+    qh, _, _, _ = _ref.oracle_levels(w)
+    uhat = O.level_values(qh[0], w.lo, w.hi, w.levels)
+
+    def fs(u):
+        U = np.eye(w.N, dtype=complex)
+        for row in u:
+            U = O.strang_split_step(w.H0, w.Hk, w.dt, row) @ U
+        return abs(np.conj(pT[0]) @ U @ p0[0]) ** 2
+
+    assert abs(F.cpu().numpy()[0] - fs(uhat)) < 1e-12
+    gg = g.cpu().numpy()[0]
+    for n, k in [(0, 0), (3, 1), (9, 0), (9, 1)]:
+        up, dn = uhat.copy(), uhat.copy()
+        up[n, k] += 1.0
+        dn[n, k] -= 1.0
+        assert abs(gg[n, k] - (fs(up) - fs(dn)) / 2.0) <= 1e-6 * np.abs(gg).max()
