@@ -576,6 +576,33 @@ def run_workload(args):
                     "Q_mean_lambda1": float(Qmap[:, -1].mean()), "Q_mean_lambda0": float(Q0.mean()),
                     "config": {"N": 8, "K": 1, "h0": h0, "J": h0 / 20, "omegas": [1.0, 25.0, n_om],
                                "lambdas": [0.0, 1.0, n_la], "T": Tw, "base": 100, "digits": 2}})
+    elif args.workload == "state":
+        # state-to-state GRAPE on the 8-qubit GRAPE system (N=256, K=16, M=1000, dt=2 us): fidelity +
+        # gradient per pulse by matrix-vector sweeps; one pulse and a batch of 152 (one CTA each)
+        w = inputs.config(2, M=args.M if args.M != M_FULL else None)
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, levels=not args.digit_table)
+        res = {}
+        for B in (1, 152):
+            rng = np.random.default_rng(2)
+            u = torch.tensor(rng.uniform(w.lo[0], w.hi[0], size=(B, w.M, w.K)), device="cuda")
+            q = t.quantize(u)
+            p0 = np.zeros((B, w.N), dtype=np.complex128)
+            p0[:, 0] = 1.0
+            pT = rng.normal(size=(B, w.N)) + 1j * rng.normal(size=(B, w.N))
+            pT /= np.linalg.norm(pT, axis=1, keepdims=True)
+            p0d, pTd = torch.as_tensor(p0, device="cuda"), torch.as_tensor(pT, device="cuda")
+            F = torch.empty(B, dtype=torch.float64, device="cuda")
+            g = torch.empty((B, w.M, w.K), dtype=torch.float64, device="cuda")
+            for prec in ("fp32", "fp64"):
+                def it():
+                    redo.redo_state_grad(t.handle, q, prec, p0d, pTd, F, g, None)
+                it()
+                ms = _events_time(it, 2)
+                res[f"B{B}_{prec}"] = {"ms_per_iteration": ms, "instance_iters_per_s": B * 1e3 / ms}
+        out.update({"metric": "state-transfer GRAPE instance-iterations/s", "unit": "instance-iterations/s",
+                    "value": res["B152_fp32"]["instance_iters_per_s"], "results": res,
+                    "config": {"N": w.N, "K": w.K, "M": w.M, "dt": w.dt,
+                               "table": "digit table" if args.digit_table else "level table"}})
     elif args.workload == "plain":
         # 3 qubits (N=8), M=1000: latency of one pulse and throughput of 4096 replicas
         res = {}
@@ -655,7 +682,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="prop",
-                    choices=["prop", "grape", "sim", "plain", "warmstart", "warmstart_study", "freeze"],
+                    choices=["prop", "grape", "sim", "plain", "warmstart", "warmstart_study", "freeze", "state"],
                     help="prop (default): the batched propagation line; others: auxiliary measurements")
     ap.add_argument("--B", type=int, default=B_FULL, help="pulses (smaller only for profiling captures)")
     ap.add_argument("--M", type=int, default=M_FULL, help="steps per pulse (smaller only for profiling captures)")
