@@ -81,3 +81,12 @@ def test_expect_diag_rejects_unsupported():
     t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits)
     with pytest.raises(redo.RedoError):
         t.expect_diag(t.quantize(w.u), np.ones(128), np.ones(128), "fp64")
+
+
+def test_expect_diag_zero_steps_mean_is_initial_value():
+    t, rho, obs = _gpu_table(10, 1.0)
+    q = torch.zeros((3, 0, 1), dtype=torch.int32, device="cuda")
+    ex, mean = t.expect_diag(q, rho, obs, "fp64")
+    assert ex.shape == (3, 1)
+    assert np.abs(ex.cpu().numpy()[:, 0] - np.sum(rho * obs)).max() < 1e-12
+    assert np.abs(mean.cpu().numpy() - np.sum(rho * obs)).max() < 1e-12

@@ -204,3 +204,46 @@ def test_large_tc_gradient_general_h():
             Fo, go = O.grape_gradient(To, Do, w.Hk, w.dt, dig[b], w.target)
             assert np.abs(g.cpu().numpy()[b] - go).max() <= 1e-3 * np.abs(go).max()
             assert abs(F.cpu().numpy()[b] - Fo) < 1e-6
+
+
+def test_n1024_sampled_against_oracle():
+    """Largest size (10 qubits, N=1024): two short pulses of the noisy-drive system, FP64 and the
+    tensor-core path, against the oracle evaluated on just the table entries the pulses use."""
+    w = inputs.config(3, n_qubits=10, B=2, M=2, base=16, digits=2)
+    t = _tc_table(w)
+    q = t.quantize(w.u)
+    U64, _, _ = t.propagate(q, "fp64")
+    U16, _, _ = t.propagate(q, "fp16x3")
+    qo, dig, _, _ = _ref.oracle_levels(w)
+    th = O.table_thetas(w.lo[0], w.hi[0], w.levels, w.base, w.digits)
+    D = O.expm_pade13(-1j * w.dt * w.H0)
+    cache = {}
+
+    def entry(j, c):
+        if (j, c) not in cache:
+            cache[(j, c)] = O.expm_pade13(-1j * w.dt * th[j, c] * w.Hk[0])
+        return cache[(j, c)]
+
+    for b in range(w.B):
+        U = np.eye(w.N, dtype=complex)
+        for n in range(w.u.shape[1]):
+            E = entry(0, dig[b, n, 0, 0])
+            for j in range(1, w.digits):
+                E = entry(j, dig[b, n, 0, j]) @ E
+            U = E @ D @ U
+        assert np.abs(U64.cpu().numpy()[b] - U).max() < 1e-12
+        assert np.abs(U16.cpu().numpy()[b] - U).max() < 2e-4
+
+
+def test_large_zero_steps():
+    """M = 0 on the large-N paths: identity propagators, F = |Tr U_T|^2 / N^2, empty gradient."""
+    w = _reduced(2, 7, 2, 2, 3)
+    t = _tc_table(w)
+    q = t.quantize(w.u)[:, :0].contiguous()
+    for prec in ("fp64", "fp16x3"):
+        U, F, _ = t.propagate(q, prec, target=w.target)
+        assert (U - torch.eye(w.N, dtype=U.dtype, device=U.device)).abs().max().item() < 1e-12
+        Fo = abs(np.trace(w.target)) ** 2 / w.N ** 2
+        assert abs(F.cpu().numpy() - Fo).max() < 1e-12
+        F2, g = t.fidelity_grad(q, w.target, prec)
+        assert g.numel() == 0 and abs(F2.cpu().numpy() - Fo).max() < 1e-12

@@ -92,3 +92,14 @@ def test_state_grad_symmetric_split_central_differences():
         up[n, k] += 1.0
         dn[n, k] -= 1.0
         assert abs(gg[n, k] - (fs(up) - fs(dn)) / 2.0) <= 1e-6 * np.abs(gg).max()
+
+
+def test_state_grad_zero_steps():
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(0, B=2, M=4, base=16, digits=2)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits)
+    q = t.quantize(w.u)[:, :0].contiguous()
+    p0, pT = _states(w.N, w.B, 11)
+    F, g = t.state_grad(q, p0, pT, "fp64")
+    assert g.numel() == 0
+    assert np.abs(F.cpu().numpy() - np.abs(np.sum(np.conj(pT) * p0, axis=1)) ** 2).max() < 1e-14
