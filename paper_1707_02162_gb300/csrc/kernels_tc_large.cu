@@ -551,9 +551,7 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
               }
               uint8_t* dst = ring + s * Gm::kStage;
               mbar_arrive_expect_tx(&full[s], Gm::kStage);
-#pragma unroll
-              for (uint32_t o = 0; o < Gm::kB; o += kHalf)
-                bulk_load(dst + kTile + o, Bb + (size_t)pre * Gm::kB + o, kHalf, &full[s]);
+              bulk_load(dst + kTile, Bb + (size_t)pre * Gm::kB, Gm::kB, &full[s]);
             }
           }
           // the previous step of this row block is written
@@ -588,14 +586,11 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
               break;
             }
             mbar_arrive_expect_tx(&full[s], Gm::kStage);
-#pragma unroll
-            for (uint32_t o = 0; o < Gm::kB; o += kHalf)
-              bulk_load(dst + kTile + o, Bb + (size_t)kt * Gm::kB + o, kHalf, &full[s]);
+            bulk_load(dst + kTile, Bb + (size_t)kt * Gm::kB, Gm::kB, &full[s]);
           }
           const int kta = u.h ? (kt + KT / 2) % KT : kt;
           const uint8_t* sa = Sc + ((size_t)u.rt * KT + kta) * kTile;
-          bulk_load(dst, sa, kHalf, &full[s]);
-          bulk_load(dst + kHalf, sa + kHalf, kHalf, &full[s]);
+          bulk_load(dst, sa, kTile, &full[s]);
         }
         if (!ok) break;
       }
