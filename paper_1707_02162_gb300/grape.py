@@ -4,6 +4,7 @@
   pulse against a target, differentiable with respect to the control
   coefficients through libredo's gradient entry point (the derivative of the
   split model at the quantised point; the quantizer is passed straight through).
+* :class:`RedoStateFidelity` -- the same for the state fidelity ``|<psi_T|U|psi0>|^2``.
 * :func:`grape` -- the ascent loop: quantise, fidelity + gradient, update in
   place; the table is built once outside the loop as the method prescribes.
   Every step of an iteration runs in libredo kernels; the only host read per
@@ -16,6 +17,23 @@ from dataclasses import dataclass, field
 import torch
 
 from . import redo
+
+
+class RedoStateFidelity(torch.autograd.Function):
+    """F_S = |<psi_T| U(u) |psi0>|^2 for u of shape [B][M][K], differentiable through libredo's
+    state-transfer gradient (matrix-vector sweeps; the quantizer is passed straight through)."""
+
+    @staticmethod
+    def forward(ctx, u, table: redo.Table, psi0, psi_target, prec="fp64"):
+        q = table.quantize(u.detach())
+        F, g = table.state_grad(q, psi0, psi_target, prec)
+        ctx.save_for_backward(g)
+        return F
+
+    @staticmethod
+    def backward(ctx, grad_F):
+        (g,) = ctx.saved_tensors
+        return grad_F[:, None, None] * g, None, None, None, None
 
 
 class RedoFidelity(torch.autograd.Function):
@@ -44,14 +62,16 @@ class GrapeResult:
 
 def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, prec="fp64",
           checkpoint_every=0, threshold: float | None = None, adaptive: bool = True,
-          optimizer: str = "gd", lr_decay: float = 150.0) -> GrapeResult:
+          optimizer: str = "gd", lr_decay: float = 150.0, psi0=None) -> GrapeResult:
     """Gradient ascent on the fidelity (the paper does not specify the update rule).
 
     ``optimizer="gd"``: ``u <- clamp(u + step * dF/du)``; with ``adaptive`` the
     step of a pulse is halved whenever its fidelity decreased and grown by 1.1
     otherwise.  ``optimizer="adam"``: Adam moments per coefficient, ``step`` is
     then the learning rate in rad/s, decayed as step / (1 + it / lr_decay).
-    Stops early once every pulse reached ``threshold``.
+    Stops early once every pulse reached ``threshold``.  With ``psi0`` given, ``target`` is a
+    state ([N] or [B][N]) and the objective is the state fidelity |<target| U |psi0>|^2
+    (redo_state_grad: matrix-vector sweeps instead of propagators).
     """
     u = u0.clone().contiguous()
     B, M, K = u.shape
@@ -60,7 +80,12 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
     prev_F = None
     reached = torch.full((B,), -1, dtype=torch.int64)
     res = GrapeResult(u=u)
-    nbytes = redo.redo_fidelity_grad_workspace(table.handle, B, M, prec, checkpoint_every)
+    state = psi0 is not None
+    if state:
+        nbytes = redo.redo_state_grad_workspace(table.handle, B)
+        psi0 = torch.as_tensor(psi0, dtype=torch.complex128, device=u.device).contiguous()
+    else:
+        nbytes = redo.redo_fidelity_grad_workspace(table.handle, B, M, prec, checkpoint_every)
     ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=u.device)
     target = torch.as_tensor(target, dtype=torch.complex128, device=u.device).contiguous()
     q = torch.empty(u.shape, dtype=torch.int32, device=u.device)
@@ -71,7 +96,10 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
         v_ = torch.zeros_like(u)
     for it in range(iters):
         redo.redo_quantize(table.handle, u, q)
-        redo.redo_fidelity_grad(table.handle, q, target, prec, checkpoint_every, F, g, ws)
+        if state:
+            redo.redo_state_grad(table.handle, q, prec, psi0, target, F, g, ws)
+        else:
+            redo.redo_fidelity_grad(table.handle, q, target, prec, checkpoint_every, F, g, ws)
         Fh = F.cpu()
         res.F_history.append(Fh.clone())
         if threshold is not None:

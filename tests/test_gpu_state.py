@@ -103,3 +103,25 @@ def test_state_grad_zero_steps():
     F, g = t.state_grad(q, p0, pT, "fp64")
     assert g.numel() == 0
     assert np.abs(F.cpu().numpy() - np.abs(np.sum(np.conj(pT) * p0, axis=1)) ** 2).max() < 1e-14
+
+
+def test_state_autograd_and_grape_loop_reach_the_state():
+    from paper_1707_02162_gb300 import redo
+    from paper_1707_02162_gb300.grape import RedoStateFidelity, grape
+    w = inputs.config(0, B=4, M=100, base=64, digits=2)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits)
+    p0 = np.zeros(w.N, dtype=complex)
+    p0[0] = 1.0
+    # reachable targets: the states another random pulse of the same system produces
+    u2 = np.random.default_rng(14).uniform(w.lo[0], w.hi[0], size=w.u.shape)
+    U2, _, _ = t.propagate(t.quantize(u2), "fp64")
+    pT = U2.cpu().numpy()[:, :, 0].copy()
+    u = torch.tensor(w.u, dtype=torch.float64, device="cuda", requires_grad=True)
+    F = RedoStateFidelity.apply(u, t, np.tile(p0, (w.B, 1)), pT, "fp64")
+    F.sum().backward()
+    _, g = t.state_grad(t.quantize(w.u), np.tile(p0, (w.B, 1)), pT, "fp64")
+    assert torch.equal(u.grad, g)
+    res = grape(t, pT, torch.tensor(w.u, device="cuda"), iters=300, step=0.02 * w.extra["Omega"],
+                optimizer="adam", psi0=np.tile(p0, (w.B, 1)), threshold=0.99)
+    assert (res.reached >= 0).all()
+    assert res.u.max().item() <= w.hi[0] and res.u.min().item() >= w.lo[0]
