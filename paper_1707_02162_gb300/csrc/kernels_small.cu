@@ -388,6 +388,57 @@ cudaError_t launch_table_fold_drift(const redo_table* t, cudaStream_t s) {
   }
 }
 
+// Level operators in closed form for controls with H_k^2 = a_k^2 I and one nonzero per row,
+// h_k[i] at column i ^ m_k (every Pauli string):
+//     exp(-i dt theta H_k) = cos(a_k dt theta) I - i sin(a_k dt theta) / a_k H_k,
+// theta = lo_k + q delta_k (the level value, no contraction), with the diagonal drift of term 0
+// folded on the right (column j scaled by D[j][j]).  One thread per entry of E [K][levels][N][N];
+// only the two nonzeros of a row evaluate the sine and cosine.
+__global__ void levels_closed_form_kernel(int N, int K, int64_t levels, double dt, const double* __restrict__ lo,
+                                          const double* __restrict__ delta, const int32_t* __restrict__ xm,
+                                          const double2* __restrict__ xh, const double* __restrict__ xa,
+                                          const double2* __restrict__ D, double2* __restrict__ E) {
+  const int64_t n2 = (int64_t)N * N;
+  const int64_t total = (int64_t)K * levels * n2;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = idx / n2;
+    const int r = (int)(idx - e * n2);
+    const int i = r / N, j = r - i * N;
+    const int k = (int)(e / levels);
+    const int64_t q = e - (int64_t)k * levels;
+    const int c = i ^ xm[k];
+    double2 v = make_double2(0.0, 0.0);
+    if (j == i || j == c) {
+      const double th = __dadd_rn(lo[k], __dmul_rn((double)q, delta[k]));
+      const double ak = xa[k];
+      double sn, cs;
+      sincos(dt * th * ak, &sn, &cs);
+      if (j == c) {
+        const double2 h = xh[(int64_t)k * N + i];
+        v.x = sn / ak * h.y;            // -i (sin / a) h
+        v.y = -sn / ak * h.x;
+      }
+      if (j == i) v.x += cs;
+      if (k == 0) {
+        const double2 dj = D[(int64_t)j * N + j];
+        v = make_double2(v.x * dj.x - v.y * dj.y, v.x * dj.y + v.y * dj.x);
+      }
+    }
+    E[idx] = v;
+  }
+}
+
+cudaError_t launch_levels_closed_form(const redo_table* t, const int32_t* xm, const double2* xh, const double* xa,
+                                      double2* E, cudaStream_t s) {
+  const int64_t total = (int64_t)t->K * t->levels * t->N * t->N;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  levels_closed_form_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(
+      t->N, t->K, t->levels, t->dt, t->d_lo, t->d_delta, xm, xh, xa, t->D64, E);
+  return cudaGetLastError();
+}
+
 __global__ void to_fp32_kernel(const double2* __restrict__ src, float2* __restrict__ dst,
                                int64_t count) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;

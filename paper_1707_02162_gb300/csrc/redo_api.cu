@@ -182,6 +182,12 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
         }
     t->h0_diagonal = diag ? 1 : 0;
   }
+  // one-nonzero-per-row operators (row r at column r ^ m_k, value h_k[r]) with H_k^2 = a_k^2 I:
+  // their level operators have a closed form (Pauli strings)
+  std::vector<int32_t> mono_m(K, 0);
+  std::vector<double2> mono_h((size_t)K * N);
+  std::vector<double> mono_a(K, 0.0);
+  bool mono_involutory = false;
   {
     // sparse (CSR) copy of the control operators for the gradient traces Tr(H_k W)
     std::vector<int32_t> ptr((size_t)K * (N + 1)), col, rowi;
@@ -217,21 +223,39 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
     // Operators with exactly one nonzero per row, at column r ^ m_k (every Pauli string:
     // X/Y flip bits, Z only sets phases) also get the compact form m_k, h_k[r] in FP32
     // that the tensor-core gradient's trace reads without gathering.
-    bool xr = N > kSmallN;
-    std::vector<int32_t> xm(K, 0);
+    bool mono = true;
+    std::vector<int32_t>& xm = mono_m;
     std::vector<float2> xv((size_t)K * N);
-    for (int k = 0; k < K && xr; ++k)
-      for (int r = 0; r < N && xr; ++r) {
+    for (int k = 0; k < K && mono; ++k)
+      for (int r = 0; r < N && mono; ++r) {
         const size_t a = (size_t)k * (N + 1) + r;
         if (ptr[a + 1] - ptr[a] != 1) {
-          xr = false;
+          mono = false;
           break;
         }
         const int m = col[ptr[a]] ^ r;
         if (r == 0) xm[k] = m;
-        if (m != xm[k]) xr = false;
+        if (m != xm[k]) mono = false;
+        mono_h[(size_t)k * N + r] = val[ptr[a]];
         xv[(size_t)k * N + r] = make_float2((float)val[ptr[a]].x, (float)val[ptr[a]].y);
       }
+    if (mono) {
+      // H_k^2 is diagonal with entries h_r h_{r ^ m}; involutory up to scale when they all equal a^2 > 0
+      mono_involutory = true;
+      for (int k = 0; k < K && mono_involutory; ++k) {
+        const double2* h = mono_h.data() + (size_t)k * N;
+        const double2 p0 = h[0], p1 = h[xm[k]];
+        const double a2 = p0.x * p1.x - p0.y * p1.y;
+        if (!(a2 > 0.0)) mono_involutory = false;
+        for (int r = 0; r < N && mono_involutory; ++r) {
+          const double2 x = h[r], y = h[r ^ xm[k]];
+          const double re = x.x * y.x - x.y * y.y, im = x.x * y.y + x.y * y.x;
+          if (std::fabs(re - a2) > 1e-14 * a2 || std::fabs(im) > 1e-14 * a2) mono_involutory = false;
+        }
+        mono_a[k] = std::sqrt(a2);
+      }
+    }
+    const bool xr = mono && N > kSmallN;
     if (xr) {
       if ((e = cudaMalloc(&t->hk_xmask, sizeof(int32_t) * K)) != cudaSuccess ||
           (e = cudaMalloc(&t->hk_xval, sizeof(float2) * K * N)) != cudaSuccess)
@@ -275,8 +299,27 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
     const int64_t ne = (int64_t)K * t->levels;
     if ((e = cudaMalloc(&E, sizeof(double2) * n2 * ne)) != cudaSuccess)
       return fail(set_error(REDO_ERR_OOM, "level table allocation: %s", cudaGetErrorString(e)));
-    e = N > kSmallN ? large_table_expand(t, E, s) : launch_table_expand(t, E, s);
-    if (e != cudaSuccess || (e = cudaStreamSynchronize(s))) {
+    if (mono_involutory && t->h0_diagonal) {
+      // every level's operator in closed form (equal to the digit product up to rounding)
+      int32_t* d_m = nullptr;
+      double2* d_h = nullptr;
+      double* d_a = nullptr;
+      e = cudaMalloc(&d_m, sizeof(int32_t) * K);
+      if (e == cudaSuccess) e = cudaMalloc(&d_h, sizeof(double2) * K * N);
+      if (e == cudaSuccess) e = cudaMalloc(&d_a, sizeof(double) * K);
+      if (e == cudaSuccess) e = cudaMemcpy(d_m, mono_m.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(d_h, mono_h.data(), sizeof(double2) * K * N, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(d_a, mono_a.data(), sizeof(double) * K, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = launch_levels_closed_form(t, d_m, d_h, d_a, E, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      cudaFree(d_m);
+      cudaFree(d_h);
+      cudaFree(d_a);
+    } else {
+      e = N > kSmallN ? large_table_expand(t, E, s) : launch_table_expand(t, E, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
       cudaFree(E);
       return fail(cuda_error(e, "level table"));
     }

@@ -158,6 +158,8 @@ cudaError_t launch_grad_sweep(const redo_table* t, const int32_t* q, const Chain
 cudaError_t launch_state_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
                               const double2* psi0, const double2* psiT, int batched, double* F_out, double* grad,
                               int64_t* status, cudaStream_t s);
+cudaError_t launch_levels_closed_form(const redo_table* t, const int32_t* xm, const double2* xh, const double* xa,
+                                      double2* E, cudaStream_t s);
 cudaError_t launch_expect_diag(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
                                const double* rho, const double* obs, double* expect, double* mean,
                                int64_t* status, cudaStream_t s);

@@ -169,6 +169,29 @@ def test_large_level_table_matches_digit_products():
     assert np.abs(g.cpu().numpy()[0] - go).max() <= 1e-3 * np.abs(go).max()
 
 
+def test_large_level_table_product_form_global_controls():
+    """Controls with several nonzeros per row (global sums of X and Y) keep the batched
+    digit-product form of the level table at N = 128."""
+    from paper_1707_02162_gb300 import redo
+    w = _reduced(2, 7, 2, 1, 6, base=16, digits=2)
+    P = inputs.PAULI
+    w.Hk = np.stack([sum(inputs.embed({i: P[c] / 2}, 7) for i in range(7)) for c in ("X", "Y")])
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, levels=True)
+    E, _ = t.operators()
+    To, Do = _ref.oracle_table(w)
+    Tf = _ref.folded(To, Do)
+    Eg = E.cpu().numpy()
+    for qv in [0, 17, 255]:
+        c = O.level_digits(np.array([qv]), w.base, w.digits)[0]
+        for k in range(w.K):
+            assert np.abs(Eg[k, 0, qv] - Tf[k, 1, c[1]] @ Tf[k, 0, c[0]]).max() < 1e-13
+    q = t.quantize(w.u)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    Uo = _ref.oracle_propagators(w, To, Do, dig, range(w.B))
+    U64, _, _ = t.propagate(q, "fp64")
+    assert np.abs(U64.cpu().numpy() - Uo).max() < 1e-12
+
+
 @pytest.mark.parametrize("nb", ["256", "128"])
 @pytest.mark.parametrize("ck", [0, 2])
 def test_large_tc_gradient_n8(monkeypatch, nb, ck):

@@ -228,6 +228,35 @@ def test_propagate_full_size_batched_sampled_fp64_fp32():
             assert abs(Fg[b] - O.fidelity(w.target, Uo[i])) < F_TOL
 
 
+@pytest.mark.parametrize("controls", ["pauli", "global"])
+def test_level_table_closed_form_and_product_forms(controls):
+    """Single-qubit Pauli controls (one nonzero per row, H_k^2 = I/4, one of them diagonal) take
+    the closed-form level operators; global sums of X take the digit-product form.  Both must
+    equal the oracle's digit products."""
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(0, B=2, M=30)
+    P = inputs.PAULI
+    if controls == "pauli":
+        w.Hk = np.stack([inputs.embed({0: P["X"] / 2}, 3), -inputs.embed({2: P["Z"] / 2}, 3)])
+    else:
+        w.Hk = np.stack([sum(inputs.embed({i: P["X"] / 2}, 3) for i in range(3)),
+                         inputs.embed({1: P["Y"] / 2}, 3) + inputs.embed({2: P["X"] / 2}, 3)])
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, levels=True)
+    E, _ = t.operators()
+    To, Do = _ref.oracle_table(w)
+    Tf = _ref.folded(To, Do)
+    Eg = E.cpu().numpy()
+    for qv in [0, 1, 63, 64, 2047, 2048, w.levels - 1]:
+        c = O.level_digits(np.array([qv]), w.base, w.digits)[0]
+        for k in range(w.K):
+            assert np.abs(Eg[k, 0, qv] - Tf[k, 1, c[1]] @ Tf[k, 0, c[0]]).max() < 1e-13
+    q = t.quantize(w.u)
+    U, _, _ = t.propagate(q, "fp64")
+    _, dig, _, _ = _ref.oracle_levels(w)
+    Uo = _ref.oracle_propagators(w, To, Do, dig, range(w.B))
+    assert np.abs(U.cpu().numpy() - Uo).max() < FP64_TOL
+
+
 def test_level_table_operators_are_digit_products():
     from paper_1707_02162_gb300 import redo
     w = inputs.config(0, B=2, M=50)
