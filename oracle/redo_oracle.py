@@ -37,6 +37,10 @@ Functions and the passage each one follows:
   / :func:`strang_split_step` / :func:`simulate_expectation_strang` -- the
   symmetric (Strang) placement of the drift around the control factors of a
   step, the second-order variant of the Section III step.
+* :func:`phase_rotation` / :func:`phase_step_propagator` / :func:`propagate_phase` /
+  :func:`phase_split_step` -- amplitude/phase controls (Section III, Eq. vn and the
+  Dirac-frame step after Eq. vnd): one x-table per species, the phase applied as the
+  diagonal rotation Z_n on both sides of the step's control factors.
 * :func:`simulate_expectation` -- ``<M> = Tr[M rho(t)]`` of Section IV for a
   pure initial state; :func:`expect_mixed` -- the same for a dense (mixed or
   deviation) initial density matrix, the order parameter of the freezing study.
@@ -339,6 +343,49 @@ def simulate_expectation_strang(T, Dh, digits_bm, psi0, obs_diag):
         psi = X @ psi0
         out[n + 1] = float(np.sum(obs_diag * (psi.real ** 2 + psi.imag ** 2)))
     return out, X
+
+
+# ---------------------------------------------------------------------------
+# Amplitude/phase controls (Section III, Eq. vn and the Dirac-frame step that follows Eq. vnd)
+# ---------------------------------------------------------------------------
+# A linearly polarised drive on species k, amplitude A_kn and phase phi_kn, is the x-polarised
+# drive turned about z:  sum_k A_kn (S_xk cos phi_kn + S_yk sin phi_kn) = Z_n (sum_k A_kn S_xk) Z_n^dag
+# with Z_n = exp(-i sum_k phi_kn S_kz).  One x-table per species then serves every phase:
+#     U_n = Z_n E_{K-1} ... E_0 Z_n^dag D,
+# E_k the table product for the quantised amplitude of species k, drift first in time as in the
+# Section III step.  Phases are not quantised: Z_n is diagonal for diagonal S_kz and is evaluated
+# per basis state, exp(-i sum_k phi_kn sz[k][a]).
+
+def phase_rotation(phi_row, sz):
+    """Diagonal of ``Z_n = exp(-i sum_k phi_kn S_kz)``; ``sz[k]`` is the diagonal of ``S_kz``."""
+    return np.exp(-1j * (np.asarray(phi_row, dtype=np.float64) @ np.asarray(sz, dtype=np.float64)))
+
+
+def phase_step_propagator(T, D, digit_row, phi_row, sz):
+    """One amplitude/phase step ``U_n = Z_n E_{K-1} ... E_0 Z_n^dag D`` (T not folded with the drift)."""
+    Z = np.diag(phase_rotation(phi_row, sz))
+    E = np.eye(D.shape[0], dtype=np.complex128)
+    for Ek in step_factors(T, D, digit_row):
+        E = Ek @ E
+    return Z @ E @ Z.conj().T @ D
+
+
+def propagate_phase(T, D, digits_bm, phi_bm, sz):
+    """Chained amplitude/phase propagator ``U_M ... U_1`` for one pulse; ``phi_bm`` is (M, K)."""
+    U = np.eye(D.shape[0], dtype=np.complex128)
+    for n in range(digits_bm.shape[0]):
+        U = phase_step_propagator(T, D, digits_bm[n], phi_bm[n], sz) @ U
+    return U
+
+
+def phase_split_step(H0, Sx, sz, dt, amp_row, phi_row):
+    """Unquantised amplitude/phase step ``Z_n exp(-i dt A_{K-1} S_x,K-1) ... exp(-i dt A_0 S_x0) Z_n^dag
+    exp(-i dt H0)``."""
+    Z = np.diag(phase_rotation(phi_row, sz))
+    E = np.eye(H0.shape[0], dtype=np.complex128)
+    for k in range(Sx.shape[0]):
+        E = expm_pade13(-1j * dt * amp_row[k] * Sx[k]) @ E
+    return Z @ E @ Z.conj().T @ expm_pade13(-1j * dt * np.asarray(H0, dtype=np.complex128))
 
 
 # ---------------------------------------------------------------------------

@@ -612,3 +612,89 @@ def test_adam_first_step_is_signed_lr():
     g = np.array([0.3, -4.0, 1e-3])
     p2, m, v = O.adam_step(p, g, np.zeros(3), np.zeros(3), 1, 0.01)
     assert np.allclose(p2, p - 0.01 * np.sign(g), atol=1e-7)
+
+
+# ---------------------------------------------------------------- amplitude/phase controls
+
+def _two_species():
+    """Two spin-1/2 species on two qubits: S_x, S_y and the diagonal of S_z for each."""
+    Sx = np.stack([np.kron(SX, I2) / 2, np.kron(I2, SX) / 2])
+    Sy = np.stack([np.kron(SY, I2) / 2, np.kron(I2, SY) / 2])
+    sz = np.stack([np.diag(np.kron(SZ, I2)).real / 2, np.diag(np.kron(I2, SZ)).real / 2])
+    return Sx, Sy, sz
+
+
+def test_phase_rotation_turns_the_x_drive_into_the_xy_drive():
+    # Eq. vn: Z (sum A S_x) Z^dag = sum A (S_x cos phi + S_y sin phi); checked through the
+    # exponentials against scipy (a Z / Z^dag swap or a sign of phi fails)
+    from scipy.linalg import expm
+    Sx, Sy, sz = _two_species()
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        A = rng.uniform(0, 2 * np.pi * 1e4, 2)
+        phi = rng.uniform(0, 2 * np.pi, 2)
+        dt = 7e-6
+        Z = np.diag(O.phase_rotation(phi, sz))
+        E = expm(-1j * dt * A[1] * Sx[1]) @ expm(-1j * dt * A[0] * Sx[0])
+        H = sum(A[k] * (np.cos(phi[k]) * Sx[k] + np.sin(phi[k]) * Sy[k]) for k in range(2))
+        assert np.abs(Z @ E @ Z.conj().T - expm(-1j * dt * H)).max() < 1e-13
+
+
+def test_phase_step_at_levels_matches_the_xy_exponential():
+    # table form at the quantised amplitudes = exp(-i dt sum A_hat (S_x cos phi + S_y sin phi)) D,
+    # drift first in time
+    from scipy.linalg import expm
+    Sx, Sy, sz = _two_species()
+    rng = np.random.default_rng(12)
+    H0 = np.diag(rng.uniform(-3e4, 3e4, 4)).astype(complex)
+    dt, base, digits = 2e-6, 16, 2
+    levels = base ** digits
+    lo, hi = np.zeros(2), np.full(2, 2 * np.pi * 1e4)
+    T, D = O.build_table(H0, Sx, dt, lo, hi, levels, base, digits)
+    amp = rng.uniform(0, hi[0], (6, 2))
+    phi = rng.uniform(0, 2 * np.pi, (6, 2))
+    q, _, _ = O.quantize(amp[None], lo, hi, levels)
+    dig = O.level_digits(q, base, digits)[0]
+    ahat = O.level_values(q[0], lo, hi, levels)
+    for n in range(6):
+        H = sum(ahat[n, k] * (np.cos(phi[n, k]) * Sx[k] + np.sin(phi[n, k]) * Sy[k]) for k in range(2))
+        ref = expm(-1j * dt * H) @ expm(-1j * dt * H0)
+        assert np.abs(O.phase_step_propagator(T, D, dig[n], phi[n], sz) - ref).max() < 1e-12
+    # the continuous form at the level values is the same operator
+    assert np.abs(O.phase_split_step(H0, Sx, sz, dt, ahat[2], phi[2])
+                  - O.phase_step_propagator(T, D, dig[2], phi[2], sz)).max() < 1e-12
+
+
+def test_phase_zero_is_the_x_only_chain():
+    Sx, _, sz = _two_species()
+    rng = np.random.default_rng(13)
+    H0 = np.diag(rng.uniform(-3e4, 3e4, 4)).astype(complex)
+    lo, hi = np.zeros(2), np.full(2, 2 * np.pi * 1e4)
+    T, D = O.build_table(H0, Sx, 1e-6, lo, hi, 256, 16, 2)
+    q, _, _ = O.quantize(rng.uniform(0, hi[0], (1, 9, 2)), lo, hi, 256)
+    dig = O.level_digits(q, 16, 2)[0]
+    U0 = O.propagate_phase(T, D, dig, np.zeros((9, 2)), sz)
+    assert np.abs(U0 - O.propagate(T, D, dig)).max() < 1e-15
+    # a phase common to the whole pulse conjugates the x-only chain by Z only if the drift
+    # commutes with S_z (it does: diagonal); a phase of pi flips the sign of the drive
+    U1 = O.propagate_phase(T, D, dig, np.full((9, 2), np.pi), sz)
+    Zpi = np.diag(O.phase_rotation([np.pi, np.pi], sz))
+    assert np.abs(U1 - Zpi @ U0 @ Zpi.conj().T).max() < 1e-13
+
+
+def test_phase_single_spin_closed_form():
+    # one spin, no drift, constant amplitude on the grid and phase phi for M steps:
+    # U = cos(A T / 2) I - i sin(A T / 2) (cos phi X + sin phi Y)
+    base, digits = 16, 2
+    levels = base ** digits
+    lo, hi = np.zeros(1), np.array([2 * np.pi * 1e4])
+    dt, M = 3e-6, 40
+    T, D = O.build_table(np.zeros((2, 2), complex), (SX / 2)[None], dt, lo, hi, levels, base, digits)
+    qv = 173
+    A = lo[0] + qv * (hi[0] - lo[0]) / (levels - 1)
+    dig = O.level_digits(np.full((M, 1), qv), base, digits)
+    for phi in (0.0, 0.4, 2.5, -1.1):
+        U = O.propagate_phase(T, D, dig, np.full((M, 1), phi), (np.diag(SZ).real / 2)[None])
+        th = A * M * dt / 2
+        ref = np.cos(th) * I2 - 1j * np.sin(th) * (np.cos(phi) * SX + np.sin(phi) * SY)
+        assert np.abs(U - ref).max() < 1e-12
