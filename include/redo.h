@@ -381,6 +381,40 @@ redo_status redo_grape_adam_step(const redo_table* t, double* u, const double* g
                                  double* v, int64_t B, int64_t M, int32_t step, double lr, double beta1,
                                  double beta2, double eps, void* stream);
 
+/*
+ * Amplitude/phase controls (Section III, Eq. vn and the Dirac-frame step after Eq. vnd).
+ *
+ * A linearly polarised drive of amplitude A_kn and phase phi_kn on species k equals the
+ * x-polarised drive turned about z, so a table built on the species' x-operators
+ * (H_k = S_xk in redo_build_table, lo/hi spanning the amplitude range) serves every phase:
+ *     U_n = Z_n E_{K-1,n} ... E_{0,n} Z_n^dag D,   Z_n = exp(-i sum_k phi_kn S_kz),
+ * E_k the table operator of the quantised amplitude q[b][n][k].  The phases are not
+ * quantised: Z_n is diagonal and is evaluated per basis state in FP64.
+ *
+ * redo_table_set_phase_axes -- attach the diagonals of S_kz to the table.
+ *  sz   host double [K][N]: sz[k][a] = <a|S_kz|a>.  Copied; the caller keeps ownership.
+ * Synchronous (like redo_build_table).  REDO_ERR_UNSUPPORTED when some S_kz does not commute
+ * with H0 (an off-diagonal H0[a][b] != 0 with sz[k][a] != sz[k][b]): Z_n must commute with the
+ * drift for the regrouping the library uses.  A second call replaces the axes.
+ */
+redo_status redo_table_set_phase_axes(redo_table* t, const double* sz);
+
+/*
+ * redo_propagate_phase -- U_b = U_M ... U_1 for amplitude/phase controls, and optionally
+ * F_b = |Tr(U_target^dag U_b)|^2 / N^2; arguments as redo_propagate plus
+ *  phi   device double [B][M][K], phases in radians (any real value).
+ * REDO_FP64 and REDO_FP32 for every N; REDO_FP16X3 for N <= 64 (tensor-core chains, the
+ * phase diagonals entering as split-FP16 factors).  Not on a REDO_TABLE_STRANG table.
+ * REDO_ERR_INVALID when the table has no phase axes.  Workspace from
+ * redo_propagate_phase_workspace.
+ */
+redo_status redo_propagate_phase(const redo_table* t, const int32_t* q, const double* phi, int64_t B, int64_t M,
+                                 redo_precision prec, int32_t reunit_every, void* U_out, const void* U_target,
+                                 double* F_out, void* tau_out, void* workspace, size_t workspace_bytes,
+                                 int64_t* dev_status, void* stream);
+redo_status redo_propagate_phase_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                           int32_t reunit_every, size_t* bytes);
+
 /* Scratch bytes redo_propagate needs for (B, M, prec, reunit_every) on this table. */
 redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
                                      redo_precision prec, int32_t reunit_every, size_t* bytes);

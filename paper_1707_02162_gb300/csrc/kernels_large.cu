@@ -546,7 +546,13 @@ static cudaError_t large_chain_t(const redo_table* t, const int32_t* q, const Ch
   if (e) return e;
   cplx<R>* cur = seg;
   cplx<R>* nxt = ping;
+  const int64_t kd = (int64_t)t->K * t->digits;
   for (int64_t tt = 0; tt < p.seg_len; ++tt) {
+    // amplitude/phase calls: the segments hold whole steps, each opened by its diagonal P_n
+    if (p.pd && tt % kd == 0 &&
+        (e = launch_phase_rows(N, std::is_same<R, double>::value ? REDO_FP64 : REDO_FP32, cur, G, p.S,
+                               p.seg_len / kd, tt / kd, p.M, p.pd, s)))
+      return e;
     op.t = tt;
     op.X = cur;
     op.Y = nxt;

@@ -1,0 +1,118 @@
+// Amplitude/phase controls (Section III, Eq. vn and the Dirac-frame step after Eq. vnd).
+//
+// A drive of amplitude A_kn and phase phi_kn on species k is the x-polarised drive turned
+// about z, so with one x-table per species the step is
+//     U_n = Z_n E_n Z_n^dag D,   Z_n = exp(-i sum_k phi_kn S_kz),   E_n = E_{K-1,n} ... E_{0,n}.
+// When D commutes with every S_kz the chain regroups as
+//     U_M ... U_1 = Z_{M-1} (E'_M P_M) ... (E'_1 P_1),   P_n = Z_n^dag Z_{n-1},  E'_n = E_n D,
+// (0-based steps in the code, Z_{-1} = I): the folded table serves unchanged and each step
+// gains one diagonal factor.  These kernels evaluate the diagonals in FP64 and apply them
+// where the chain kernels do not (the large-N chains and the final Z_{M-1}).
+#include "redo_internal.cuh"
+
+namespace redo {
+
+namespace {
+
+// one thread per (b, n, a): pd[b][n][a] = exp(i sum_k (phi[b][n][k] - phi[b][n-1][k]) sz[k][a]);
+// the threads of step M (n == M) write zf[b][a] = exp(-i sum_k phi[b][M-1][k] sz[k][a]).
+__global__ void phase_diag_kernel(const double* __restrict__ phi, const double* __restrict__ sz, int64_t B,
+                                  int64_t M, int K, int N, double2* __restrict__ pd, double2* __restrict__ zf) {
+  const int64_t total = B * (M + 1) * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx % N);
+    const int64_t bn = idx / N;
+    const int64_t n = bn % (M + 1), b = bn / (M + 1);
+    const double* cur = phi + (b * M + n) * K;
+    double th = 0.0;
+    if (n < M) {
+      for (int k = 0; k < K; ++k) {
+        const double prev = n > 0 ? cur[k - K] : 0.0;
+        th += (cur[k] - prev) * sz[(int64_t)k * N + a];
+      }
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      pd[(b * M + n) * N + a] = make_double2(cs, sn);
+    } else {
+      for (int k = 0; k < K && M > 0; ++k) th += cur[k - K] * sz[(int64_t)k * N + a];
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      zf[b * N + a] = make_double2(cs, -sn);
+    }
+  }
+}
+
+// X_g <- diag(pd[u][n]) X_g, n = s * sps + i, for the chains g = u * S + s with n < M
+template <typename R>
+__global__ void phase_rows_kernel(cplx<R>* __restrict__ X, int N, int64_t S, int64_t sps, int64_t i,
+                                  int64_t M, const double2* __restrict__ pd) {
+  const int64_t g = blockIdx.x;
+  const int64_t u = g / S, sg = g - u * S;
+  const int64_t n = sg * sps + i;
+  if (n >= M) return;
+  const int64_t n2 = (int64_t)N * N;
+  cplx<R>* Xg = X + g * n2;
+  const double2* p = pd + (u * M + n) * N;
+  for (int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.y * blockDim.x) {
+    const double2 pv = p[e / N];
+    const cplx<R> x = Xg[e];
+    const double xr = (double)x.x, xi = (double)x.y;
+    Xg[e] = cmake<R>((R)(pv.x * xr - pv.y * xi), (R)(pv.x * xi + pv.y * xr));
+  }
+}
+
+template <typename R>
+__global__ void phase_final_kernel(const cplx<R>* __restrict__ X, int N, const double2* __restrict__ zf,
+                                   double2* __restrict__ out) {
+  const int64_t b = blockIdx.x;
+  const int64_t n2 = (int64_t)N * N;
+  for (int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.y * blockDim.x) {
+    const double2 z = zf[b * N + e / N];
+    const cplx<R> x = X[b * n2 + e];
+    const double xr = (double)x.x, xi = (double)x.y;
+    out[b * n2 + e] = make_double2(z.x * xr - z.y * xi, z.x * xi + z.y * xr);
+  }
+}
+
+unsigned grid_y(int64_t n2) {
+  int64_t b = (n2 + 255) / 256;
+  if (b > 64) b = 64;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_phase_diag(const redo_table* t, const double* phi, int64_t B, int64_t M, double2* pd,
+                              double2* zf, cudaStream_t s) {
+  const int64_t total = B * (M + 1) * t->N;
+  if (total == 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > (int64_t)t->num_sms * 32) blocks = (int64_t)t->num_sms * 32;
+  phase_diag_kernel<<<(unsigned)blocks, 256, 0, s>>>(phi, t->sz64, B, M, t->K, t->N, pd, zf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_rows(int N, int prec, void* X, int64_t G, int64_t S, int64_t sps, int64_t i,
+                              int64_t M, const double2* pd, cudaStream_t s) {
+  if (G == 0) return cudaSuccess;
+  const dim3 grid((unsigned)G, grid_y((int64_t)N * N));
+  if (prec == REDO_FP64)
+    phase_rows_kernel<double><<<grid, 256, 0, s>>>((double2*)X, N, S, sps, i, M, pd);
+  else
+    phase_rows_kernel<float><<<grid, 256, 0, s>>>((float2*)X, N, S, sps, i, M, pd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_final(int N, int64_t B, int prec, const void* X, const double2* zf, double2* out,
+                               cudaStream_t s) {
+  if (B == 0) return cudaSuccess;
+  const dim3 grid((unsigned)B, grid_y((int64_t)N * N));
+  if (prec == REDO_FP64)
+    phase_final_kernel<double><<<grid, 256, 0, s>>>((const double2*)X, N, zf, out);
+  else
+    phase_final_kernel<float><<<grid, 256, 0, s>>>((const float2*)X, N, zf, out);
+  return cudaGetLastError();
+}
+
+}  // namespace redo

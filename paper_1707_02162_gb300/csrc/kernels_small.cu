@@ -463,6 +463,8 @@ cudaError_t launch_to_fp32(const double2* src, float2* dst, int64_t count, cudaS
 // Factor f of pulse b is table operator (k, j, c) with
 //   n = f / (K d), k = (f mod K d) / d, j = f mod d, c = floor(q[b][n][k] / base^j) mod base.
 // Factor 0 (drift-folded digit 0 of term 0, step 0) is applied first.
+// With amplitude/phase controls (pd non-null) every step opens with a diagonal factor:
+// factor r = 0 of step n is P_n = diag(pd[b][n]) and r = 1.. are the table factors.
 template <typename R>
 struct GatherSrc {
   const cplx<R>* T;
@@ -471,10 +473,23 @@ struct GatherSrc {
   int K, d, base;
   int64_t levels;
   int64_t* status;
+  int64_t fps;                // factors per step
+  const double2* pd;          // [B][M][N] or nullptr
+  int N;
+  // diagonal of factor f when it is a phase factor, else nullptr
+  __device__ __forceinline__ const double2* phase(int64_t b, int64_t f) const {
+    if (!pd) return nullptr;
+    const int64_t n = f / fps;
+    return f - n * fps == 0 ? pd + (b * M + n) * N : nullptr;
+  }
+  // table operator of factor f (nullptr for a phase factor)
   __device__ __forceinline__ const cplx<R>* addr(int64_t b, int64_t f, int N2) const {
-    const int64_t kd = (int64_t)K * d;
-    const int64_t n = f / kd;
-    const int r = (int)(f - n * kd);
+    const int64_t n = f / fps;
+    int r = (int)(f - n * fps);
+    if (pd) {
+      if (r == 0) return nullptr;
+      --r;
+    }
     const int k = r / d, j = r - k * d;
     int32_t qv = q[(b * M + n) * K + k];
     if (qv < 0 || qv >= levels) {
@@ -492,6 +507,7 @@ template <typename R>
 struct DenseSrc {
   const cplx<R>* P;
   int64_t per_unit;
+  __device__ __forceinline__ const double2* phase(int64_t, int64_t) const { return nullptr; }
   __device__ __forceinline__ const cplx<R>* addr(int64_t b, int64_t f, int N2) const {
     return P + (b * per_unit + f) * N2;
   }
@@ -546,11 +562,18 @@ chain_kernel(Src src, int64_t units, int64_t segs_per_unit, int64_t seg_len, int
   for (int i = lt; i < N2; i += MM::THREADS)
     X[i] = cmake<R>((i / N == i % N) ? R(1) : R(0), R(0));
   __syncthreads();
-  if (lt == 0) {
-    for (int s = 0; s < STAGES && s < my_len; ++s) {
-      mbar_arrive_expect_tx(&bar[s], BYTES);
-      bulk_load(A + s * N2, src.addr(my_unit, my_f0 + s, N2), BYTES, &bar[s]);
+  // a phase factor has no operand to copy: its stage completes on the arrival alone
+  auto issue = [&](int st, int64_t f) {
+    const cplx<R>* op = src.addr(my_unit, f, N2);
+    if (op) {
+      mbar_arrive_expect_tx(&bar[st], BYTES);
+      bulk_load(A + st * N2, op, BYTES, &bar[st]);
+    } else {
+      mbar_arrive(&bar[st]);
     }
+  };
+  if (lt == 0) {
+    for (int s = 0; s < STAGES && s < my_len; ++s) issue(s, my_f0 + s);
   }
   cplx<R> Y[TL::TM][TL::TN];
   for (int64_t t = 0; t < maxlen; ++t) {
@@ -561,7 +584,11 @@ chain_kernel(Src src, int64_t units, int64_t segs_per_unit, int64_t seg_len, int
       if (!mbar_wait_bounded(&bar[stage], parity)) {
         abort_flag = 1;
       } else {
-        MM::run(A + stage * N2, X, lt, Y);
+        const double2* ph = src.phase(my_unit, my_f0 + t);
+        if (ph)
+          MM::scale_rows(ph, X, lt, Y);
+        else
+          MM::run(A + stage * N2, X, lt, Y);
       }
     }
     __syncthreads();
@@ -570,8 +597,7 @@ chain_kernel(Src src, int64_t units, int64_t segs_per_unit, int64_t seg_len, int
       MM::store(X, lt, Y);
       if (lt == 0 && t + STAGES < my_len) {
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar[stage], BYTES);
-        bulk_load(A + stage * N2, src.addr(my_unit, my_f0 + t + STAGES, N2), BYTES, &bar[stage]);
+        issue(stage, my_f0 + t + STAGES);
       }
     }
     __syncthreads();
@@ -633,11 +659,12 @@ static int chain_slots(int N, int num_sms) {
   return num_sms * per_sm * ch;
 }
 
-ChainPlan plan_chain(const redo_table* t, int64_t B, int64_t M, int prec) {
+ChainPlan plan_chain(const redo_table* t, int64_t B, int64_t M, int prec, bool phase) {
   ChainPlan p;
   p.B = B;
   p.M = M;
-  p.F = M * (int64_t)t->K * t->digits;
+  p.fps = (int64_t)t->K * t->digits + (phase ? 1 : 0);
+  p.F = M * p.fps;
   const int slots = prec == REDO_FP64 ? chain_slots<double>(t->N, t->num_sms)
                                       : chain_slots<float>(t->N, t->num_sms);
   // about two segments per resident chain, each at least 16 factors long
@@ -672,6 +699,9 @@ static cudaError_t chain_segments_t(const redo_table* t, const int32_t* q, const
   src.base = t->base;
   src.levels = t->levels;
   src.status = status;
+  src.fps = p.fps > 0 ? p.fps : (int64_t)t->K * t->digits;
+  src.pd = p.pd;
+  src.N = t->N;
   cplx<R>* out = (cplx<R>*)seg_out;
   switch (t->N) {
     case 2: return launch_chain_n<R, 2>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
@@ -803,12 +833,14 @@ cudaError_t launch_polar(const redo_table* t, int prec_in, int prec_out, const v
   return cudaErrorInvalidValue;
 }
 
-ChainPlan plan_chain_aligned(const redo_table* t, int64_t B, int64_t M, int64_t steps_per_segment) {
+ChainPlan plan_chain_aligned(const redo_table* t, int64_t B, int64_t M, int64_t steps_per_segment,
+                             bool phase) {
   ChainPlan p;
   p.B = B;
   p.M = M;
-  p.F = M * (int64_t)t->K * t->digits;
-  p.seg_len = steps_per_segment * (int64_t)t->K * t->digits;
+  p.fps = (int64_t)t->K * t->digits + (phase ? 1 : 0);
+  p.F = M * p.fps;
+  p.seg_len = steps_per_segment * p.fps;
   p.S = p.F > 0 ? (p.F + p.seg_len - 1) / p.seg_len : 1;
   return p;
 }

@@ -94,7 +94,16 @@ struct TcArgs {
   int64_t units, segs, seg_len, F;
   float2* out;
   int64_t* status;
+  int64_t fps;                // factors per step
+  const double2* pd;          // amplitude/phase calls: [units][M][64] step-opening diagonals, else nullptr
 };
+
+// Diagonal of factor f when it is a step-opening phase factor (amplitude/phase calls), else nullptr.
+__device__ __forceinline__ const double2* tc_phase(const TcArgs& a, int64_t unit, int64_t f) {
+  if (!a.pd) return nullptr;
+  const int64_t n = f / a.fps;
+  return f - n * a.fps == 0 ? a.pd + (unit * a.M + n) * kN : nullptr;
+}
 
 template <int CH, int EW, int STAGES>
 struct TcLayout {
@@ -114,9 +123,9 @@ struct TcLayout {
 };
 
 __device__ __forceinline__ int64_t tc_entry(const TcArgs& a, int64_t unit, int64_t f) {
-  const int64_t kd = (int64_t)a.K * a.d;
-  const int64_t n = f / kd;
-  const int r = (int)(f - n * kd);
+  const int64_t n = f / a.fps;
+  int r = (int)(f - n * a.fps);
+  if (a.pd) --r;                                         // factor 0 of a step is its phase
   const int k = r / a.d, j = r - k * a.d;
   int32_t qv = a.q[(unit * a.M + n) * a.K + k];
   if (qv < 0 || qv >= a.levels) {
@@ -742,24 +751,54 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
       }
     }
   } else if (warp == EW * CH) {
-    if (lane == 0) {
-      uint32_t idx = 0;
-      for (int64_t t = 0; t < maxlen && !*abort_flag; ++t) {
-        for (int c = 0; c < CH; ++c) {
-          if (t >= len[c]) continue;
-          const uint32_t s = idx % STAGES, u = idx / STAGES;
-          if (u > 0 && !mbar_wait_bounded_n(&empty[s], (u - 1) & 1, kTcWaitLimit)) {
-            *abort_flag = 1;
-            break;
+    // Operand producer.  A table factor is two bulk copies issued by lane 0; a phase factor
+    // (amplitude/phase calls) is written into its stage by the whole warp: zeros, then the
+    // split-FP16 diagonal at (n, n) and (n, 64 + n) of the hi rows and the lo rows.
+    uint32_t idx = 0;
+    bool stop = false;
+    for (int64_t t = 0; t < maxlen && !stop; ++t) {
+      for (int c = 0; c < CH; ++c) {
+        if (t >= len[c]) continue;
+        const uint32_t s = idx % STAGES, u = idx / STAGES;
+        int ok = 1;
+        if (lane == 0) ok = !*abort_flag && (u == 0 || mbar_wait_bounded_n(&empty[s], (u - 1) & 1, kTcWaitLimit));
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) *abort_flag = 1;
+          stop = true;
+          break;
+        }
+        uint8_t* dst = smem + L::kRing + s * kEntryBytes;
+        const double2* ph = tc_phase(a, unit[c], f0[c] + t);
+        if (ph) {
+          for (uint32_t o = (uint32_t)lane * 16u; o < kEntryBytes; o += 32u * 16u)
+            *reinterpret_cast<uint4*>(dst + o) = make_uint4(0u, 0u, 0u, 0u);
+          __syncwarp();
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int n = lane + 32 * h;
+            const double2 z = ph[n];
+#pragma unroll
+            for (int comp = 0; comp < 2; ++comp) {
+              const double v = comp == 0 ? z.x : z.y;
+              const __half hv = __double2half(v);
+              const __half lv = __double2half((v - (double)__half2float(hv)) * 2048.0);
+              const uint32_t k = (uint32_t)(64 * comp + n);
+              *reinterpret_cast<__half*>(dst + sw128((uint32_t)n, k, 128)) = hv;
+              *reinterpret_cast<__half*>(dst + sw128((uint32_t)(64 + n), k, 128)) = lv;
+            }
           }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full[s]);
+        } else if (lane == 0) {
           const int64_t e = tc_entry(a, unit[c], f0[c] + t);
-          uint8_t* dst = smem + L::kRing + s * kEntryBytes;
           const uint8_t* src = a.planes + e * kEntryBytes;
           mbar_arrive_expect_tx(&full[s], kEntryBytes);
           bulk_load(dst, src, kEntryBytes / 2, &full[s]);
           bulk_load(dst + kEntryBytes / 2, src + kEntryBytes / 2, kEntryBytes / 2, &full[s]);
-          ++idx;
         }
+        ++idx;
       }
     }
   } else {
@@ -825,11 +864,12 @@ constexpr int kTcChains = 2;
 constexpr int kTcEpiWarps = 8;
 constexpr int kTcStages = 3;
 
-ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M) {
+ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M, bool phase) {
   ChainPlan p;
   p.B = B;
   p.M = M;
-  p.F = M * (int64_t)t->K * t->digits;
+  p.fps = (int64_t)t->K * t->digits + (phase ? 1 : 0);
+  p.F = M * p.fps;
   const int64_t slots = (int64_t)t->num_sms * kTcChains;
   // pick the segment count minimising (waves x segment length) + combine cost
   int64_t bestS = 1;
@@ -868,13 +908,14 @@ constexpr int kTc3Chains = 2, kTc3Stages = 4;
 
 cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPlan& p,
                             void* seg_out, int64_t* status, cudaStream_t s) {
-  if (tc_variant() == 3) {
+  // amplitude/phase calls run on the three-block kernel only
+  if (p.pd || tc_variant() == 3) {
     using L3 = tc::Tc3Layout<kTc3Chains, kTc3Stages>;
     auto kern3 = tc::chain_tc3_kernel<kTc3Chains, kTc3Stages>;
     cudaError_t e = cudaFuncSetAttribute(kern3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)L3::kAlloc);
     if (e != cudaSuccess) return e;
-    tc::TcArgs a;
+    tc::TcArgs a{};
     a.planes = (const uint8_t*)t->tc_planes;
     a.q = q;
     a.M = p.M;
@@ -888,6 +929,8 @@ cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPl
     a.F = p.F;
     a.out = (float2*)seg_out;
     a.status = status;
+    a.fps = p.fps > 0 ? p.fps : (int64_t)t->K * t->digits;
+    a.pd = p.pd;
     const int64_t G = p.B * p.S;
     const int64_t blocks = (G + kTc3Chains - 1) / kTc3Chains;
     if (blocks == 0) return cudaSuccess;
@@ -901,7 +944,7 @@ cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPl
     cudaError_t e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)L2::kAlloc);
     if (e != cudaSuccess) return e;
-    tc::TcArgs a;
+    tc::TcArgs a{};
     a.planes = (const uint8_t*)t->tc_planes;
     a.q = q;
     a.M = p.M;
@@ -915,6 +958,8 @@ cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPl
     a.F = p.F;
     a.out = (float2*)seg_out;
     a.status = status;
+    a.fps = p.fps > 0 ? p.fps : (int64_t)t->K * t->digits;
+    a.pd = p.pd;
     const int64_t G = p.B * p.S;
     const int64_t blocks = (G + L2::CH - 1) / L2::CH;
     if (blocks == 0) return cudaSuccess;
@@ -926,7 +971,7 @@ cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPl
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L::kAlloc);
   if (e != cudaSuccess) return e;
-  tc::TcArgs a;
+  tc::TcArgs a{};
   a.planes = (const uint8_t*)t->tc_planes;
   a.q = q;
   a.M = p.M;
@@ -940,6 +985,7 @@ cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPl
   a.F = p.F;
   a.out = (float2*)seg_out;
   a.status = status;
+  a.fps = p.fps > 0 ? p.fps : (int64_t)t->K * t->digits;
   const int64_t G = p.B * p.S;
   const int64_t blocks = (G + kTcChains - 1) / kTcChains;
   if (blocks == 0) return cudaSuccess;

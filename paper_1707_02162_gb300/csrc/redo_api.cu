@@ -173,14 +173,21 @@ redo_status redo_build_table(int32_t N, int32_t K, double dt, const void* H0, co
       return fail(set_error(REDO_ERR_OOM, "half drift allocation: %s", cudaGetErrorString(e)));
   }
   {
-    bool diag = true;
-    for (int r = 0; r < N && diag; ++r)
+    // off-diagonal nonzeros of H0 (the commutation check of the amplitude/phase calls)
+    std::vector<int32_t> pairs;
+    for (int r = 0; r < N; ++r)
       for (int c = 0; c < N; ++c)
         if (r != c && (h[2 * (r * N + c)] != 0.0 || h[2 * (r * N + c) + 1] != 0.0)) {
-          diag = false;
-          break;
+          pairs.push_back(r);
+          pairs.push_back(c);
         }
-    t->h0_diagonal = diag ? 1 : 0;
+    t->h0_diagonal = pairs.empty() ? 1 : 0;
+    t->h0_npairs = (int64_t)pairs.size() / 2;
+    if (!pairs.empty()) {
+      t->h0_pairs = (int32_t*)std::malloc(sizeof(int32_t) * pairs.size());
+      if (!t->h0_pairs) return fail(set_error(REDO_ERR_OOM, "host allocation"));
+      std::memcpy(t->h0_pairs, pairs.data(), sizeof(int32_t) * pairs.size());
+    }
   }
   // one-nonzero-per-row operators (row r at column r ^ m_k, value h_k[r]) with H_k^2 = a_k^2 I:
   // their level operators have a closed form (Pauli strings)
@@ -366,7 +373,33 @@ redo_status redo_table_free(redo_table* t) {
   cudaFree(t->hk_val);
   cudaFree(t->hk_xmask);
   cudaFree(t->hk_xval);
+  cudaFree(t->sz64);
+  std::free(t->h0_pairs);
   std::free(t);
+  return REDO_OK;
+}
+
+redo_status redo_table_set_phase_axes(redo_table* t, const double* sz) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (!sz) return set_error(REDO_ERR_INVALID, "sz is NULL");
+  const int N = t->N, K = t->K;
+  for (int64_t i = 0; i < (int64_t)K * N; ++i)
+    if (!std::isfinite(sz[i])) return set_error(REDO_ERR_INVALID, "sz[%lld] is not finite", (long long)i);
+  // Z_n commutes with the drift (Section III): H0[a][b] != 0 needs sz[k][a] == sz[k][b]
+  for (int64_t e = 0; e < t->h0_npairs; ++e) {
+    const int a = t->h0_pairs[2 * e], b = t->h0_pairs[2 * e + 1];
+    for (int k = 0; k < K; ++k)
+      if (sz[(int64_t)k * N + a] != sz[(int64_t)k * N + b])
+        return set_error(REDO_ERR_UNSUPPORTED, "S_z of term %d does not commute with H0 (entry %d, %d)", k, a, b);
+  }
+  if (!t->sz64) {
+    cudaError_t e = cudaMalloc(&t->sz64, sizeof(double) * K * N);
+    if (e != cudaSuccess) {
+      t->sz64 = nullptr;
+      return set_error(REDO_ERR_OOM, "phase axes: %s", cudaGetErrorString(e));
+    }
+  }
+  REDO_CUDA_TRY(cudaMemcpy(t->sz64, sz, sizeof(double) * K * N, cudaMemcpyHostToDevice));
   return REDO_OK;
 }
 
@@ -429,6 +462,7 @@ struct PropLayout {
   int eff_prec;       // precision of segment and pulse products
   size_t seg_off, prod_off, prod64_off, total;
   size_t strang_off, strang_tmp_off;   // symmetric split: conjugated products (+ dense-drift scratch)
+  size_t pd_off, zf_off, phout_off;     // amplitude/phase calls
 };
 
 // FP64 matrices appended to a workspace for the symmetric split's conjugation
@@ -445,24 +479,45 @@ static void add_strang(const redo_table* t, int64_t count, size_t& total, size_t
   total += strang_bytes(t, count);
 }
 
+// amplitude/phase calls: step diagonals, final rotation and the rotated FP64 product
+static void add_phase(const redo_table* t, int64_t B, int64_t M, size_t& total, size_t& pd_off, size_t& zf_off,
+                      size_t& out_off) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  pd_off = total;
+  zf_off = pd_off + up((size_t)B * M * t->N * sizeof(double2));
+  out_off = zf_off + up((size_t)B * t->N * sizeof(double2));
+  total = out_off + up((size_t)B * t->N * t->N * sizeof(double2));
+}
+
 static PropLayout prop_layout(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
-                              int32_t reunit_every) {
+                              int32_t reunit_every, bool phase = false) {
   PropLayout L;
+  L.pd_off = L.zf_off = L.phout_off = 0;
   if (t->N > kSmallN) {
     L.eff_prec = prec == REDO_FP16X3 ? REDO_FP32 : prec;
-    L.p = reunit_every > 0 ? plan_chain_aligned(t, B, M, reunit_every) : plan_chain_large(t, B, M);
+    if (reunit_every > 0) {
+      L.p = plan_chain_aligned(t, B, M, reunit_every);
+    } else {
+      L.p = plan_chain_large(t, B, M);
+      if (phase) {
+        // whole steps per segment, so that the step diagonals fall between launches
+        const int64_t kd = (int64_t)t->K * t->digits;
+        L.p = plan_chain_aligned(t, B, M, L.p.seg_len > 0 ? (L.p.seg_len + kd - 1) / kd : 1);
+      }
+    }
     L.seg_off = L.prod_off = L.prod64_off = 0;
     L.total = prec == REDO_FP16X3 ? tc_large_prop_workspace(t, L.p, reunit_every > 0)
                                   : large_prop_workspace(t, L.p, prec, reunit_every > 0);
     add_strang(t, B, L.total, L.strang_off, L.strang_tmp_off);
+    if (phase) add_phase(t, B, M, L.total, L.pd_off, L.zf_off, L.phout_off);
     return L;
   }
   // the tensor-core path forms segment products in split FP16 and combines them in FP32
   L.eff_prec = prec == REDO_FP16X3 ? REDO_FP32 : prec;
   if (reunit_every > 0)
-    L.p = plan_chain_aligned(t, B, M, reunit_every);
+    L.p = plan_chain_aligned(t, B, M, reunit_every, phase);
   else
-    L.p = prec == REDO_FP16X3 ? plan_chain_tc(t, B, M) : plan_chain(t, B, M, L.eff_prec);
+    L.p = prec == REDO_FP16X3 ? plan_chain_tc(t, B, M, phase) : plan_chain(t, B, M, L.eff_prec, phase);
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t el = L.eff_prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
   const size_t n2 = (size_t)t->N * t->N;
@@ -471,6 +526,7 @@ static PropLayout prop_layout(const redo_table* t, int64_t B, int64_t M, redo_pr
   L.prod64_off = L.prod_off + up((size_t)L.p.B * n2 * el);
   L.total = L.prod64_off + (reunit_every > 0 ? up((size_t)L.p.B * n2 * sizeof(double2)) : 0);
   add_strang(t, B, L.total, L.strang_off, L.strang_tmp_off);
+  if (phase) add_phase(t, B, M, L.total, L.pd_off, L.zf_off, L.phout_off);
   return L;
 }
 
@@ -485,32 +541,50 @@ redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
   return REDO_OK;
 }
 
-redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
-                           redo_precision prec, int32_t reunit_every, void* U_out,
-                           const void* U_target, double* F_out, void* tau_out, void* workspace,
-                           size_t workspace_bytes, int64_t* dev_status, void* stream) {
+// Shared body of redo_propagate and redo_propagate_phase (phi non-null: amplitude/phase controls).
+static redo_status propagate_core(const redo_table* t, const int32_t* q, const double* phi, int64_t B, int64_t M,
+                                  redo_precision prec, int32_t reunit_every, void* U_out, const void* U_target,
+                                  double* F_out, void* tau_out, void* workspace, size_t workspace_bytes,
+                                  int64_t* dev_status, void* stream) {
   if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
   if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
   if (reunit_every < 0) return set_error(REDO_ERR_INVALID, "reunit_every must be >= 0");
   redo_status st = check_prec(t, prec);
   if (st != REDO_OK) return st;
+  const bool phase = phi != nullptr;
   if (B == 0) return REDO_OK;
   if (M > 0 && !q) return set_error(REDO_ERR_INVALID, "q is NULL");
   if (U_target && !F_out && !tau_out)
     return set_error(REDO_ERR_INVALID, "U_target given without F_out or tau_out");
   if (!U_out && !U_target) return set_error(REDO_ERR_INVALID, "nothing to compute");
   if (reunit_every > M) reunit_every = M > 0 ? (int32_t)M : 0;
-  const PropLayout L = prop_layout(t, B, M, prec, reunit_every);
+  PropLayout L = prop_layout(t, B, M, prec, reunit_every, phase);
   if (!workspace || workspace_bytes < L.total)
     return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", L.total);
   if (((uintptr_t)workspace & 255) != 0) return set_error(REDO_ERR_INVALID, "workspace not 256-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  double2* zf = nullptr;
+  if (phase) {
+    double2* pd = (double2*)((char*)workspace + L.pd_off);
+    zf = (double2*)((char*)workspace + L.zf_off);
+    if ((e = launch_phase_diag(t, phi, B, M, pd, zf, s)) != cudaSuccess) return cuda_error(e, "phase diagonals");
+    L.p.pd = pd;
+  }
+  // the last rotation Z_{M-1} of an amplitude/phase call, applied before the fidelity
+  auto rotate = [&](const void*& fin, int& fin_prec) -> cudaError_t {
+    if (!phase) return cudaSuccess;
+    double2* o = (double2*)((char*)workspace + L.phout_off);
+    cudaError_t er = launch_phase_final(t->N, B, fin_prec, fin, zf, o, s);
+    fin = o;
+    fin_prec = REDO_FP64;
+    return er;
+  };
   const ChainPlan& p = L.p;
   const int eff = L.eff_prec;
   char* seg = (char*)workspace + L.seg_off;
   char* prod = (char*)workspace + L.prod_off;
   char* prod64 = (char*)workspace + L.prod64_off;
-  cudaError_t e;
   if (t->N > kSmallN) {
     void* res = nullptr;
     int res_prec = eff;
@@ -531,6 +605,9 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
       res = sb;
       res_prec = REDO_FP64;
     }
+    const void* rc = res;
+    if ((e = rotate(rc, res_prec)) != cudaSuccess) return cuda_error(e, "phase rotation");
+    res = const_cast<void*>(rc);
     ProfScope ps(4, s);
     if ((e = launch_finalize(t, B, res_prec, res, U_out, (const double2*)U_target, F_out,
                              (double2*)tau_out, s)) != cudaSuccess)
@@ -573,6 +650,7 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
     fin = sb;
     fin_prec = REDO_FP64;
   }
+  if ((e = rotate(fin, fin_prec)) != cudaSuccess) return cuda_error(e, "phase rotation");
   {
     ProfScope ps(4, s);
     if ((e = launch_finalize(t, B, fin_prec, fin, U_out, (const double2*)U_target, F_out,
@@ -580,6 +658,47 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
       return cuda_error(e, "finalize");
   }
   return REDO_OK;
+}
+
+redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
+                           redo_precision prec, int32_t reunit_every, void* U_out,
+                           const void* U_target, double* F_out, void* tau_out, void* workspace,
+                           size_t workspace_bytes, int64_t* dev_status, void* stream) {
+  return propagate_core(t, q, nullptr, B, M, prec, reunit_every, U_out, U_target, F_out, tau_out, workspace,
+                        workspace_bytes, dev_status, stream);
+}
+
+static redo_status check_phase(const redo_table* t, redo_precision prec) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (!t->sz64) return set_error(REDO_ERR_INVALID, "no phase axes: call redo_table_set_phase_axes first");
+  if (t->strang) return set_error(REDO_ERR_UNSUPPORTED, "amplitude/phase calls on a symmetric-split table");
+  if (prec == REDO_FP16X3 && t->N > kSmallN)
+    return set_error(REDO_ERR_UNSUPPORTED, "amplitude/phase calls in REDO_FP16X3 need N <= 64");
+  return REDO_OK;
+}
+
+redo_status redo_propagate_phase_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                           int32_t reunit_every, size_t* bytes) {
+  if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
+  if (B < 0 || M < 0 || reunit_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  redo_status st = check_prec(t, prec);
+  if (st != REDO_OK) return st;
+  if ((st = check_phase(t, prec)) != REDO_OK) return st;
+  if (reunit_every > M) reunit_every = M > 0 ? (int32_t)M : 0;
+  *bytes = prop_layout(t, B, M, prec, reunit_every, true).total;
+  return REDO_OK;
+}
+
+redo_status redo_propagate_phase(const redo_table* t, const int32_t* q, const double* phi, int64_t B, int64_t M,
+                                 redo_precision prec, int32_t reunit_every, void* U_out, const void* U_target,
+                                 double* F_out, void* tau_out, void* workspace, size_t workspace_bytes,
+                                 int64_t* dev_status, void* stream) {
+  redo_status st = check_phase(t, prec);
+  if (st != REDO_OK) return st;
+  if (B > 0 && M > 0 && !phi) return set_error(REDO_ERR_INVALID, "phi is NULL");
+  static const double kNoPhase = 0.0;
+  return propagate_core(t, q, phi ? phi : &kNoPhase, B, M, prec, reunit_every, U_out, U_target, F_out, tau_out,
+                        workspace, workspace_bytes, dev_status, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -62,6 +62,9 @@ struct redo_table {
   void* tc_planes;            // tensor-core planes or nullptr
   size_t tc_bytes;
   int tc_nb;                  // operand block height of the large-N planes (128 or 256)
+  double* sz64;               // [K][N] diagonals of the species' S_kz (amplitude/phase calls), or nullptr
+  int32_t* h0_pairs;          // host: (row, column) of every off-diagonal nonzero of H0
+  int64_t h0_npairs;
   cudaStream_t build_stream;
   int num_sms;
 };
@@ -111,13 +114,18 @@ cudaError_t launch_to_fp32(const double2* src, float2* dst, int64_t count, cudaS
 cudaError_t launch_table_expand(const redo_table* t, double2* E, cudaStream_t s);
 
 // Segmented chain products for N <= 64 (SIMT, FP64 or FP32).
+// Amplitude/phase calls (pd non-null): every step opens with the diagonal factor
+// P_n = Z_n^dag Z_{n-1} (pd[b][n][0..N)), so a step has fps = K*digits + 1 factors on the
+// N <= 64 paths; the large-N path keeps fps = K*digits and applies P_n between launches.
 struct ChainPlan {
   int64_t B, M;
-  int64_t F;          // factors per pulse = M*K*digits
+  int64_t F;          // factors per pulse = M*fps
   int64_t seg_len;    // factors per segment
   int64_t S;          // segments per pulse
+  int64_t fps = 0;    // factors per step
+  const double2* pd = nullptr;
 };
-ChainPlan plan_chain(const redo_table* t, int64_t B, int64_t M, int prec);
+ChainPlan plan_chain(const redo_table* t, int64_t B, int64_t M, int prec, bool phase = false);
 size_t chain_workspace_bytes(const redo_table* t, const ChainPlan& p, int prec);
 cudaError_t launch_chain_segments(const redo_table* t, const int32_t* q, const ChainPlan& p,
                                   int prec, void* seg_out, int64_t* status, cudaStream_t s);
@@ -125,7 +133,8 @@ cudaError_t launch_chain_combine(const redo_table* t, const ChainPlan& p, int pr
                                  const void* seg_in, void* prod_out, int64_t* status,
                                  cudaStream_t s);
 // Segments of exactly `steps_per_segment` time steps (re-unitarisation period).
-ChainPlan plan_chain_aligned(const redo_table* t, int64_t B, int64_t M, int64_t steps_per_segment);
+ChainPlan plan_chain_aligned(const redo_table* t, int64_t B, int64_t M, int64_t steps_per_segment,
+                             bool phase = false);
 // One or more Newton-Schulz polar steps on `count` N x N matrices (in may equal out
 // when the precisions match); prec_in/prec_out are REDO_FP64 or REDO_FP32.
 cudaError_t launch_polar(const redo_table* t, int prec_in, int prec_out, const void* in, void* out,
@@ -134,7 +143,7 @@ cudaError_t launch_polar(const redo_table* t, int prec_in, int prec_out, const v
 // Tensor-core chains (kernels_tc.cu), N = 64, split-FP16.
 size_t tc_planes_bytes(const redo_table* t);
 cudaError_t launch_build_tc_planes(const redo_table* t, cudaStream_t s);
-ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M);
+ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M, bool phase = false);
 cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPlan& p,
                             void* seg_out, int64_t* status, cudaStream_t s);
 
@@ -224,6 +233,19 @@ cudaError_t launch_half_drift_conj(const redo_table* t, int prec, const void* X,
 // psi'_b = D_h^dag psi_b for a diagonal half drift (count vectors of N)
 cudaError_t launch_half_drift_vec(const redo_table* t, const double2* psi, int64_t count, double2* out,
                                   cudaStream_t s);
+
+// Amplitude/phase controls (kernels_phase.cu).  pd[b][n][a] = exp(i sum_k (phi[b][n][k] -
+// phi[b][n-1][k]) sz[k][a]) (phi[b][-1] = 0), the diagonal of Z_n^dag Z_{n-1};
+// zf[b][a] = exp(-i sum_k phi[b][M-1][k] sz[k][a]), the diagonal of Z_{M-1} (1 when M = 0).
+cudaError_t launch_phase_diag(const redo_table* t, const double* phi, int64_t B, int64_t M, double2* pd,
+                              double2* zf, cudaStream_t s);
+// X_g <- P_n X_g in place for the chains g = (u, s) of a step-aligned plan, n = s*sps + i
+// (chains with n >= M untouched); X of precision prec.
+cudaError_t launch_phase_rows(int N, int prec, void* X, int64_t G, int64_t S, int64_t sps, int64_t i,
+                              int64_t M, const double2* pd, cudaStream_t s);
+// out_b = diag(zf_b) X_b in FP64 (X of precision prec; out may not alias X unless FP64).
+cudaError_t launch_phase_final(int N, int64_t B, int prec, const void* X, const double2* zf, double2* out,
+                               cudaStream_t s);
 
 cudaError_t launch_finalize(const redo_table* t, int64_t B, int prec, const void* prod,
                             void* U_out, const double2* U_target, double* F_out, double2* tau_out,

@@ -58,6 +58,22 @@ struct SmemMM {
         for (int c = 0; c < TN; ++c) cfma<R>(Y[a][c], av[a], xv[c]);
     }
   }
+  // Y = diag(p) X (a row scaling, p in FP64)
+  __device__ __forceinline__ static void scale_rows(const double2* __restrict__ p,
+                                                    const cplx<R>* __restrict__ X, int lt,
+                                                    cplx<R> (&Y)[TM][TN]) {
+    const int ty = lt / TX, tx = lt % TX;
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+      const double2 pv = p[ty + TY * a];
+      const cplx<R> pa = cmake<R>((R)pv.x, (R)pv.y);
+#pragma unroll
+      for (int c = 0; c < TN; ++c) {
+        Y[a][c] = cmake<R>(R(0), R(0));
+        cfma<R>(Y[a][c], pa, X[(ty + TY * a) * N + tx + TX * c]);
+      }
+    }
+  }
   __device__ __forceinline__ static void store(cplx<R>* __restrict__ X, int lt,
                                                const cplx<R> (&Y)[TM][TN]) {
     const int ty = lt / TX, tx = lt % TX;

@@ -250,6 +250,32 @@ def config(idx: int, *, B: int | None = None, M: int | None = None, n_qubits: in
     raise ValueError(f"unknown workload index {idx}")
 
 
+def species_z_diagonals(n: int) -> np.ndarray:
+    """Diagonals of ``S_z = Z_i/2`` for every qubit i as its own species: shape (n, 2**n)."""
+    idx = np.arange(2 ** n)
+    return np.stack([(1.0 - 2.0 * ((idx >> (n - 1 - i)) & 1)) / 2.0 for i in range(n)])
+
+
+def phase_config(n_qubits: int = 6, *, B: int = 256, M: int = 2000, seed: int = 1, base: int = 64,
+                 digits: int = 2, dt: float = 1e-6) -> Workload:
+    """Amplitude/phase drive (Section III, Eq. vn): every qubit its own species with x-operator
+    ``X_i/2`` (``Hk``) and z-operator diagonal ``extra["sz"][i]``; amplitudes uniform on
+    [0, Omega] (``u``, levels on [0, Omega]), phases uniform on [0, 2 pi) (``extra["phi"]``,
+    shape (B, M, n)), Omega = 2 pi 10 kHz, NMR drift and Haar target as in the x/y workloads.
+    The same pulse in x/y form has coefficients ``A cos phi`` and ``A sin phi``."""
+    rng = np.random.default_rng(seed)
+    n = n_qubits
+    Om = 2 * np.pi * 1e4
+    nu, J = _offsets_couplings(rng, n)
+    H0 = drift_zz(n, nu, J)
+    Hk = np.stack([embed({i: _X / 2}, n) for i in range(n)])
+    target = haar_unitary(rng, 2 ** n)
+    u = rng.uniform(0.0, Om, size=(B, M, n))
+    phi = rng.uniform(0.0, 2 * np.pi, size=(B, M, n))
+    return Workload(f"amp_phase_n{n}", n, H0, Hk, dt, np.zeros(n), np.full(n, Om), base ** digits, base, digits,
+                    u, target=target, extra={"Omega": Om, "phi": phi, "sz": species_z_diagonals(n)})
+
+
 def pauli_generator(strings: list[str], theta: np.ndarray) -> np.ndarray:
     """Hermitian generator ``G = sum_k theta_k P_k`` of a target ``exp(-i G)``.
 

@@ -29,7 +29,8 @@ EXPORTS = [
     "redo_profile_read", "redo_propagate_noalloc", "redo_fidelity_grad", "redo_fidelity_grad_workspace",
     "redo_grape_step", "redo_simulate", "redo_simulate_workspace", "redo_mlp_sizes", "redo_mlp_forward",
     "redo_mlp_backward", "redo_mlp_adam", "redo_grape_adam_step", "redo_expect_diag",
-    "redo_state_grad", "redo_state_grad_workspace",
+    "redo_state_grad", "redo_state_grad_workspace", "redo_table_set_phase_axes", "redo_propagate_phase",
+    "redo_propagate_phase_workspace",
 ]
 PROFILE_PHASES = 11
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -61,6 +62,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_quantize.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.redo_propagate.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_propagate_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_table_set_phase_axes.argtypes = [vp, vp]
+    L.redo_propagate_phase.argtypes = [vp, vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
+    L.redo_propagate_phase_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_noalloc.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
     L.redo_fidelity_grad.argtypes = [vp, vp, i64, i64, vp, i32, i32, i32, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_fidelity_grad_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
@@ -165,6 +169,32 @@ def redo_propagate(handle: int, q: torch.Tensor, prec, U_out: torch.Tensor | Non
                                          _ptr(U_out), _ptr(U_target), _ptr(F_out), _ptr(tau_out),
                                          _ptr(workspace), workspace.numel() * workspace.element_size(),
                                          _ptr(status), _stream(stream)))
+
+
+def redo_table_set_phase_axes(handle: int, sz: np.ndarray):
+    """Attach the diagonals of the species' S_kz ([K][N], host) for amplitude/phase calls."""
+    sz = np.ascontiguousarray(sz, dtype=np.float64)
+    _check(load_library().redo_table_set_phase_axes(ctypes.c_void_p(handle), sz.ctypes.data))
+
+
+def redo_propagate_phase_workspace(handle: int, B: int, M: int, prec, reunit_every: int = 0) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().redo_propagate_phase_workspace(ctypes.c_void_p(handle), B, M, _prec(prec), reunit_every,
+                                                         ctypes.byref(n)))
+    return n.value
+
+
+def redo_propagate_phase(handle: int, q: torch.Tensor, phi: torch.Tensor, prec, U_out: torch.Tensor | None,
+                         U_target: torch.Tensor | None, F_out: torch.Tensor | None, tau_out: torch.Tensor | None,
+                         workspace: torch.Tensor, status: torch.Tensor | None = None, reunit_every: int = 0,
+                         stream=None):
+    """Amplitude/phase controls: q the quantised amplitudes, phi [B][M][K] the phases (radians)."""
+    B, M = q.shape[0], q.shape[1]
+    _check(load_library().redo_propagate_phase(ctypes.c_void_p(handle), _ptr(q), _ptr(phi), B, M, _prec(prec),
+                                               reunit_every, _ptr(U_out), _ptr(U_target), _ptr(F_out),
+                                               _ptr(tau_out), _ptr(workspace),
+                                               workspace.numel() * workspace.element_size(), _ptr(status),
+                                               _stream(stream)))
 
 
 def redo_propagate_noalloc(handle: int, q: torch.Tensor, prec, U_out: torch.Tensor | None,
@@ -362,6 +392,32 @@ class Table:
         ws = self.workspace(B, q.shape[1], prec, reunit_every)
         redo_propagate(self.handle, q, prec, U, target, F, tau, ws, status, reunit_every=reunit_every)
         return U, F, tau
+
+
+def _table_set_phase_axes(self, sz):
+    """Diagonals [K][N] of the species' S_kz, for :meth:`propagate_phase`."""
+    redo_table_set_phase_axes(self.handle, sz)
+
+
+def _table_propagate_phase(self, q, phi, prec="fp64", target=None, want_U=True, status=None, reunit_every=0):
+    """(U [B][N][N] or None, F or None, tau or None) for amplitude/phase controls: amplitudes
+    quantised to q on this table's x-operators, phases phi [B][M][K] in radians."""
+    B, M = q.shape[0], q.shape[1]
+    phi = torch.as_tensor(phi, dtype=torch.float64, device=self.device).contiguous()
+    U = torch.empty((B, self.N, self.N), dtype=torch.complex128, device=self.device) if want_U else None
+    F = tau = None
+    if target is not None:
+        target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
+        F = torch.empty(B, dtype=torch.float64, device=self.device)
+        tau = torch.empty(B, dtype=torch.complex128, device=self.device)
+    nbytes = redo_propagate_phase_workspace(self.handle, B, M, prec, reunit_every)
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+    redo_propagate_phase(self.handle, q, phi, prec, U, target, F, tau, ws, status, reunit_every=reunit_every)
+    return U, F, tau
+
+
+Table.set_phase_axes = _table_set_phase_axes
+Table.propagate_phase = _table_propagate_phase
 
 
 def _table_fidelity_grad(self, q, target, prec="fp64", checkpoint_every=0, status=None):
