@@ -603,6 +603,92 @@ def run_workload(args):
                     "value": res["B152_fp32"]["instance_iters_per_s"], "results": res,
                     "config": {"N": w.N, "K": w.K, "M": w.M, "dt": w.dt,
                                "table": "digit table" if args.digit_table else "level table"}})
+    elif args.workload == "phase":
+        # Section III amplitude/phase drive: 6 qubits (N=64), each its own species (x-table of X_i/2,
+        # levels on [0, Omega]), phases on [0, 2 pi), B=256 pulses x M=2000 steps, level table,
+        # split FP16 with re-unitarisation every 64 steps.  Against the same pulses in x/y form
+        # (coefficients A cos phi, A sin phi on 12 per-qubit x/y controls).
+        B = args.B if args.B != B_FULL else 256
+        M = args.M if args.M != M_FULL else 2000
+        w = inputs.phase_config(6, B=B, M=M, seed=1)
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True,
+                       levels=args.levels)
+        t.set_phase_axes(w.extra["sz"])
+        u = torch.tensor(w.u, device="cuda")
+        phi = torch.tensor(w.extra["phi"], device="cuda")
+        target = torch.as_tensor(w.target, device="cuda")
+        q = torch.empty(u.shape, dtype=torch.int32, device="cuda")
+        U = torch.empty((B, w.N, w.N), dtype=torch.complex128, device="cuda")
+        F = torch.empty(B, dtype=torch.float64, device="cuda")
+        tau = torch.empty(B, dtype=torch.complex128, device="cuda")
+        ws = torch.empty(redo.redo_propagate_phase_workspace(t.handle, B, M, "fp16x3", REUNIT), dtype=torch.uint8,
+                         device="cuda")
+
+        def it():
+            redo.redo_quantize(t.handle, u, q)
+            redo.redo_propagate_phase(t.handle, q, phi, "fp16x3", U, target, F, tau, ws, reunit_every=REUNIT)
+        it()
+        ms = _events_time(it, args.steps)
+        redo.redo_profile_read()
+        redo.redo_profile_enable(True)
+        it()
+        torch.cuda.synchronize()
+        redo.redo_profile_enable(False)
+        prof = redo.redo_profile_read()
+        tc_ms = prof.get("chain_tc", (0.0, 0))[0]
+        # FP64 on 16 pulses: accuracy of the split-FP16 result
+        Bs = 16
+        U64 = torch.empty((Bs, w.N, w.N), dtype=torch.complex128, device="cuda")
+        F64 = torch.empty(Bs, dtype=torch.float64, device="cuda")
+        t64 = torch.empty(Bs, dtype=torch.complex128, device="cuda")
+        ws64 = torch.empty(redo.redo_propagate_phase_workspace(t.handle, Bs, M, "fp64", 0), dtype=torch.uint8,
+                           device="cuda")
+        q16, p16 = q[:Bs].contiguous(), phi[:Bs].contiguous()
+        ms64 = _events_time(lambda: redo.redo_propagate_phase(t.handle, q16, p16, "fp64", U64, target, F64, t64,
+                                                               ws64), 1)
+        dF = float((F64 - F[:Bs]).abs().max())
+        dU = float((U64 - U[:Bs]).abs().max())
+        t.close()
+        del ws, ws64
+        # the same pulses in x/y form: 12 controls, one more factor per species and step
+        Hxy = inputs.controls_local_xy(6)
+        txy = redo.Table(w.H0, Hxy, w.dt, np.full(12, -w.extra["Omega"]), np.full(12, w.extra["Omega"]), w.base,
+                         w.digits, fp32=True, fp16x3=True, levels=args.levels)
+        uxy = torch.stack([u * torch.cos(phi), u * torch.sin(phi)], dim=3).reshape(B, M, 12).contiguous()
+        qxy = torch.empty(uxy.shape, dtype=torch.int32, device="cuda")
+        wsxy = txy.workspace(B, M, "fp16x3", REUNIT)
+        Fxy = torch.empty(B, dtype=torch.float64, device="cuda")
+
+        def itxy():
+            redo.redo_quantize(txy.handle, uxy, qxy)
+            redo.redo_propagate(txy.handle, qxy, "fp16x3", U, target, Fxy, tau, wsxy, reunit_every=REUNIT)
+        itxy()
+        msxy = _events_time(itxy, args.steps)
+        txy.close()
+        K = w.K
+        op_bytes = B * M * K * 32768.0
+        flop = B * M * K * 8.0 * w.N ** 3 * 3
+        pk = _peaks()
+        out.update({"metric": "REDO prop steps/s (amplitude/phase controls)", "unit": "pulse-steps/s",
+                    "value": B * M / (ms / 1e3), "ms_per_call": ms,
+                    "xy_form_same_pulses": {"pulse_steps_per_s": B * M / (msxy / 1e3), "ms_per_call": msxy,
+                                            "controls": 12},
+                    "speedup_vs_xy_form": msxy / ms,
+                    "fp64_same_gpu": {"pulse_steps_per_s": Bs * M / (ms64 / 1e3), "pulses": Bs,
+                                      "max_abs_dF_fp16x3_vs_fp64": dF, "max_abs_dU": dU},
+                    "roofline": {"kernel": "chain_tc", "kernel_ms": tc_ms,
+                                 "hbm_achieved_gbs": op_bytes / (tc_ms / 1e3) / 1e9 if tc_ms else None,
+                                 "hbm_frac": (op_bytes / (tc_ms / 1e3) / 1e9 / pk.get("hbm_gbs", 6794.5)
+                                              if tc_ms else None),
+                                 "tensor_tflops": flop / (tc_ms / 1e3) / 1e12 if tc_ms else None,
+                                 "tensor_frac_of_sustained": (flop / (tc_ms / 1e3) / 1e12
+                                                              / pk.get("bf16_tflops_sustained", 1709.6)
+                                                              if tc_ms else None),
+                                 "algorithmic": f"{op_bytes:.4g} B of table operands (B*M*{K} x 32 KB), "
+                                                f"{flop:.4g} fp16 flop (B*M*{K} complex products x 3)"},
+                    "precision": "fp16x3 (tcgen05 chains; step phases applied in the chain epilogue, FP32)",
+                    "config": {"N": w.N, "species": K, "B": B, "M": M, "dt": w.dt, "reunit_every": REUNIT,
+                               "table": "level table" if args.levels else "digit table"}})
     elif args.workload == "plain":
         # 3 qubits (N=8), M=1000: latency of one pulse and throughput of 4096 replicas
         res = {}
@@ -682,7 +768,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="prop",
-                    choices=["prop", "grape", "sim", "plain", "warmstart", "warmstart_study", "freeze", "state"],
+                    choices=["prop", "grape", "sim", "plain", "warmstart", "warmstart_study", "freeze", "state",
+                             "phase"],
                     help="prop (default): the batched propagation line; others: auxiliary measurements")
     ap.add_argument("--B", type=int, default=B_FULL, help="pulses (smaller only for profiling captures)")
     ap.add_argument("--M", type=int, default=M_FULL, help="steps per pulse (smaller only for profiling captures)")

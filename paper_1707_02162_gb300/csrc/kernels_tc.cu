@@ -94,16 +94,11 @@ struct TcArgs {
   int64_t units, segs, seg_len, F;
   float2* out;
   int64_t* status;
-  int64_t fps;                // factors per step
-  const double2* pd;          // amplitude/phase calls: [units][M][64] step-opening diagonals, else nullptr
+  int64_t fps;                // factors per step (K * digits)
+  // amplitude/phase calls: [units][M][64] diagonals P_n = Z_n^dag Z_{n-1} that open every step,
+  // applied by the epilogue of the step before (or as the initial state of a segment), else nullptr
+  const double2* pd;
 };
-
-// Diagonal of factor f when it is a step-opening phase factor (amplitude/phase calls), else nullptr.
-__device__ __forceinline__ const double2* tc_phase(const TcArgs& a, int64_t unit, int64_t f) {
-  if (!a.pd) return nullptr;
-  const int64_t n = f / a.fps;
-  return f - n * a.fps == 0 ? a.pd + (unit * a.M + n) * kN : nullptr;
-}
 
 template <int CH, int EW, int STAGES>
 struct TcLayout {
@@ -124,8 +119,7 @@ struct TcLayout {
 
 __device__ __forceinline__ int64_t tc_entry(const TcArgs& a, int64_t unit, int64_t f) {
   const int64_t n = f / a.fps;
-  int r = (int)(f - n * a.fps);
-  if (a.pd) --r;                                         // factor 0 of a step is its phase
+  const int r = (int)(f - n * a.fps);
   const int k = r / a.d, j = r - k * a.d;
   int32_t qv = a.q[(unit * a.M + n) * a.K + k];
   if (qv < 0 || qv >= a.levels) {
@@ -605,7 +599,8 @@ struct Tc3Layout {
   static constexpr uint32_t kRing = CH * kState;
   static constexpr uint32_t kBars = kRing + STAGES * kEntryBytes;
   static constexpr uint32_t kMisc = kBars + (2 * STAGES + 2 * CH) * 8;
-  static constexpr uint32_t kAlloc = kMisc + 16 + 1024;
+  static constexpr uint32_t kPhase = kMisc + 16;         // per chain: the next step diagonal, 64 float2
+  static constexpr uint32_t kAlloc = kPhase + CH * 64 * 8 + 1024;
   static constexpr int kThreads = 32 * (EW * CH + 2);
   static_assert(kAlloc <= 232448, "shared memory budget");
 };
@@ -675,38 +670,105 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
     // row 128+(r-64) and, negated, block 0 row r-64
     const int rowA = r < 64 ? 64 + r : 128 + (r - 64);
     const int rowB = r - 64;                               // used only when r >= 64
+    // amplitude/phase calls: the row holding the other component of the same state entries
+    const int rowP = r < 64 ? 128 + r : r;                 // Zi row m (block 2) / Zr row m (block 1)
+    float2* ph = reinterpret_cast<float2*>(smem + L::kPhase) + c * 64;
+    const int et = ew * 32 + lane;                         // thread index within the chain's epilogue
+    const int64_t kd = a.fps;
+    // split-store 16 accumulator columns cb.. of this thread's row (and its negated copy)
+    auto store16 = [&](const float* z, int cb) {
+#pragma unroll
+      for (int gq = 0; gq < 2; ++gq) {
+        uint4 hh, ll;
+        split8(z + 8 * gq, hh, ll);
+        const uint32_t kcol = (uint32_t)(cb + 8 * gq);
+        const uint32_t oa = sw128((uint32_t)rowA, kcol, 192);
+        *reinterpret_cast<uint4*>(st_hi + oa) = hh;
+        *reinterpret_cast<uint4*>(st_lo + oa) = ll;
+        if (r >= 64) {
+          const uint32_t ob = sw128((uint32_t)rowB, kcol, 192);
+          const uint32_t ng = 0x80008000u;
+          *reinterpret_cast<uint4*>(st_hi + ob) = make_uint4(hh.x ^ ng, hh.y ^ ng, hh.z ^ ng, hh.w ^ ng);
+          *reinterpret_cast<uint4*>(st_lo + ob) = make_uint4(ll.x ^ ng, ll.y ^ ng, ll.z ^ ng, ll.w ^ ng);
+        }
+      }
+    };
+    // the 16 stored (split) values of row `row`, columns cb..
+    auto load16 = [&](int row, int cb, float* v) {
+#pragma unroll
+      for (int gq = 0; gq < 2; ++gq) {
+        const uint32_t o = sw128((uint32_t)row, (uint32_t)(cb + 8 * gq), 192);
+        const uint4 hh = *reinterpret_cast<const uint4*>(st_hi + o);
+        const uint4 ll = *reinterpret_cast<const uint4*>(st_lo + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t hw = q == 0 ? hh.x : q == 1 ? hh.y : q == 2 ? hh.z : hh.w;
+          const uint32_t lw = q == 0 ? ll.x : q == 1 ? ll.y : q == 2 ? ll.z : ll.w;
+          const float h0 = __half2float(__ushort_as_half((unsigned short)(hw & 0xffffu)));
+          const float h1 = __half2float(__ushort_as_half((unsigned short)(hw >> 16)));
+          const float l0 = __half2float(__ushort_as_half((unsigned short)(lw & 0xffffu)));
+          const float l1 = __half2float(__ushort_as_half((unsigned short)(lw >> 16)));
+          v[8 * gq + 2 * q] = fmaf(l0, kLoInv, h0);
+          v[8 * gq + 2 * q + 1] = fmaf(l1, kLoInv, h1);
+        }
+      }
+    };
     if (len[c] == 0) {
       if (out)
         for (int n = 32 * j; n < 32 * j + 32; ++n) out[(n * kN + m) * 2 + comp] = (comp == 0 && n == m) ? 1.f : 0.f;
     } else {
-      // Y = I: block 1 = I, blocks 0 and 2 = 0; this thread clears/sets its K columns 32j..32j+31
+      // Initial state Y = I, or the step diagonal P_n when the segment opens step n of an
+      // amplitude/phase call (Y = X^T is diagonal either way): this thread sets its K columns
+      // 32j..32j+31 of its rows, the diagonal entry (m, m) to its component of the value.
+      double dv = comp == 0 ? 1.0 : 0.0;
+      if (a.pd && f0[c] % kd == 0) {
+        const double2 pv = a.pd[(unit[c] * a.M + f0[c] / kd) * kN + m];
+        dv = comp == 0 ? pv.x : pv.y;
+      }
+      const __half dh = __double2half(dv);
+      const __half dl = __double2half((dv - (double)__half2float(dh)) * 2048.0);
       for (int gi = 4 * j; gi < 4 * j + 4; ++gi) {
         const int k0 = 8 * gi;
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
-        if (r < 64 && r >= k0 && r < k0 + 8) {
-          const int p = (r - k0) >> 1, hp = (r - k0) & 1;
-          w[p] = (uint32_t)0x3C00u << (16 * hp);
+        uint32_t wh[4] = {0u, 0u, 0u, 0u}, wl[4] = {0u, 0u, 0u, 0u};
+        if (m >= k0 && m < k0 + 8) {
+          const int p = (m - k0) >> 1, hp = (m - k0) & 1;
+          wh[p] = (uint32_t)__half_as_ushort(dh) << (16 * hp);
+          wl[p] = (uint32_t)__half_as_ushort(dl) << (16 * hp);
         }
         const uint32_t oa = sw128((uint32_t)rowA, (uint32_t)k0, 192);
-        *reinterpret_cast<uint4*>(st_hi + oa) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4*>(st_lo + oa) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(st_hi + oa) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        *reinterpret_cast<uint4*>(st_lo + oa) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
         if (r >= 64) {
           const uint32_t ob = sw128((uint32_t)rowB, (uint32_t)k0, 192);
-          *reinterpret_cast<uint4*>(st_hi + ob) = make_uint4(0u, 0u, 0u, 0u);
-          *reinterpret_cast<uint4*>(st_lo + ob) = make_uint4(0u, 0u, 0u, 0u);
+          const uint32_t ng = 0x80008000u;
+          *reinterpret_cast<uint4*>(st_hi + ob) = make_uint4(wh[0] ^ ng, wh[1] ^ ng, wh[2] ^ ng, wh[3] ^ ng);
+          *reinterpret_cast<uint4*>(st_lo + ob) = make_uint4(wl[0] ^ ng, wl[1] ^ ng, wl[2] ^ ng, wl[3] ^ ng);
         }
       }
       fence_proxy_async_smem();
       mbar_arrive(&state_ready[c]);
       for (int64_t t = 0; t < len[c]; ++t) {
+        const int64_t f = f0[c] + t;
+        const bool last = (t == len[c] - 1);
+        // amplitude/phase calls: the first product of a step (in this segment) stages the
+        // diagonal that opens the next step, when that step starts inside the segment
+        const bool stage_ph = a.pd && (t == 0 || f % kd == 0) && (f / kd + 1) * kd < f0[c] + len[c];
+        const bool apply_ph = a.pd && !last && (f + 1) % kd == 0;
+        double2 pv = make_double2(0.0, 0.0);
+        if (stage_ph && et < 64) pv = a.pd[(unit[c] * a.M + f / kd + 1) * kN + et];
         bool ok = !*abort_flag && mbar_wait_bounded_n(&mma_done[c], (uint32_t)(t & 1), kTcWaitLimit);
-        ok = __all_sync(0xffffffffu, ok);
+        if (a.pd) {
+          // the chain's epilogue warps meet at barriers below: they agree on every step
+          if (stage_ph && et < 64) ph[et] = make_float2((float)pv.x, (float)pv.y);
+          ok = named_barrier_and(1 + c, 32 * EW, ok);
+        } else {
+          ok = __all_sync(0xffffffffu, ok);
+        }
         if (!ok) {
           *abort_flag = 1;
           break;
         }
         tc_fence_after();
-        const bool last = (t == len[c] - 1);
         // issue all four accumulator loads before waiting once
         uint32_t ra0[16], rb0[16], ra1[16], rb1[16];
         tmem_ld16(d1 + 32 * j, ra0);
@@ -723,24 +785,31 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
 #pragma unroll
           for (int i = 0; i < 16; ++i) z[i] = fmaf(__uint_as_float(rb[i]), kLoInv, __uint_as_float(ra[i]));
           if (!last) {
-#pragma unroll
-            for (int gq = 0; gq < 2; ++gq) {
-              uint4 hh, ll;
-              split8(z + 8 * gq, hh, ll);
-              const uint32_t kcol = (uint32_t)(cb + 8 * gq);
-              const uint32_t oa = sw128((uint32_t)rowA, kcol, 192);
-              *reinterpret_cast<uint4*>(st_hi + oa) = hh;
-              *reinterpret_cast<uint4*>(st_lo + oa) = ll;
-              if (r >= 64) {
-                const uint32_t ob = sw128((uint32_t)rowB, kcol, 192);
-                const uint32_t ng = 0x80008000u;
-                *reinterpret_cast<uint4*>(st_hi + ob) = make_uint4(hh.x ^ ng, hh.y ^ ng, hh.z ^ ng, hh.w ^ ng);
-                *reinterpret_cast<uint4*>(st_lo + ob) = make_uint4(ll.x ^ ng, ll.y ^ ng, ll.z ^ ng, ll.w ^ ng);
-              }
-            }
+            store16(z, cb);
           } else if (out) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) out[((cb + i) * kN + m) * 2 + comp] = z[i];
+          }
+        }
+        if (apply_ph) {
+          // Y <- Y P (column n scaled by p_n): each entry needs both components, which live in
+          // TMEM lanes m and m + 64 (different warps), so the partners exchange them through the
+          // state just written; every thread then rewrites its own rows.
+          named_barrier(3 + c, 32 * EW);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int cb = 32 * j + 16 * h;
+            float zo[16], zp[16];
+            load16(rowA, cb, zo);
+            load16(rowP, cb, zp);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float2 pc = ph[cb + i];
+              const float zr = comp == 0 ? zo[i] : zp[i], zi = comp == 0 ? zp[i] : zo[i];
+              zo[i] = comp == 0 ? fmaf(zr, pc.x, -zi * pc.y) : fmaf(zr, pc.y, zi * pc.x);
+            }
+            named_barrier(3 + c, 32 * EW);               // both rows read before either is rewritten
+            store16(zo, cb);
           }
         }
         if (!last) {
@@ -751,54 +820,24 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
       }
     }
   } else if (warp == EW * CH) {
-    // Operand producer.  A table factor is two bulk copies issued by lane 0; a phase factor
-    // (amplitude/phase calls) is written into its stage by the whole warp: zeros, then the
-    // split-FP16 diagonal at (n, n) and (n, 64 + n) of the hi rows and the lo rows.
-    uint32_t idx = 0;
-    bool stop = false;
-    for (int64_t t = 0; t < maxlen && !stop; ++t) {
-      for (int c = 0; c < CH; ++c) {
-        if (t >= len[c]) continue;
-        const uint32_t s = idx % STAGES, u = idx / STAGES;
-        int ok = 1;
-        if (lane == 0) ok = !*abort_flag && (u == 0 || mbar_wait_bounded_n(&empty[s], (u - 1) & 1, kTcWaitLimit));
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) {
-          if (lane == 0) *abort_flag = 1;
-          stop = true;
-          break;
-        }
-        uint8_t* dst = smem + L::kRing + s * kEntryBytes;
-        const double2* ph = tc_phase(a, unit[c], f0[c] + t);
-        if (ph) {
-          for (uint32_t o = (uint32_t)lane * 16u; o < kEntryBytes; o += 32u * 16u)
-            *reinterpret_cast<uint4*>(dst + o) = make_uint4(0u, 0u, 0u, 0u);
-          __syncwarp();
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int n = lane + 32 * h;
-            const double2 z = ph[n];
-#pragma unroll
-            for (int comp = 0; comp < 2; ++comp) {
-              const double v = comp == 0 ? z.x : z.y;
-              const __half hv = __double2half(v);
-              const __half lv = __double2half((v - (double)__half2float(hv)) * 2048.0);
-              const uint32_t k = (uint32_t)(64 * comp + n);
-              *reinterpret_cast<__half*>(dst + sw128((uint32_t)n, k, 128)) = hv;
-              *reinterpret_cast<__half*>(dst + sw128((uint32_t)(64 + n), k, 128)) = lv;
-            }
+    if (lane == 0) {
+      uint32_t idx = 0;
+      for (int64_t t = 0; t < maxlen && !*abort_flag; ++t) {
+        for (int c = 0; c < CH; ++c) {
+          if (t >= len[c]) continue;
+          const uint32_t s = idx % STAGES, u = idx / STAGES;
+          if (u > 0 && !mbar_wait_bounded_n(&empty[s], (u - 1) & 1, kTcWaitLimit)) {
+            *abort_flag = 1;
+            break;
           }
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&full[s]);
-        } else if (lane == 0) {
           const int64_t e = tc_entry(a, unit[c], f0[c] + t);
+          uint8_t* dst = smem + L::kRing + s * kEntryBytes;
           const uint8_t* src = a.planes + e * kEntryBytes;
           mbar_arrive_expect_tx(&full[s], kEntryBytes);
           bulk_load(dst, src, kEntryBytes / 2, &full[s]);
           bulk_load(dst + kEntryBytes / 2, src + kEntryBytes / 2, kEntryBytes / 2, &full[s]);
+          ++idx;
         }
-        ++idx;
       }
     }
   } else {
@@ -864,11 +903,11 @@ constexpr int kTcChains = 2;
 constexpr int kTcEpiWarps = 8;
 constexpr int kTcStages = 3;
 
-ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M, bool phase) {
+ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M) {
   ChainPlan p;
   p.B = B;
   p.M = M;
-  p.fps = (int64_t)t->K * t->digits + (phase ? 1 : 0);
+  p.fps = (int64_t)t->K * t->digits;
   p.F = M * p.fps;
   const int64_t slots = (int64_t)t->num_sms * kTcChains;
   // pick the segment count minimising (waves x segment length) + combine cost
@@ -908,7 +947,7 @@ constexpr int kTc3Chains = 2, kTc3Stages = 4;
 
 cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPlan& p,
                             void* seg_out, int64_t* status, cudaStream_t s) {
-  // amplitude/phase calls run on the three-block kernel only
+  // amplitude/phase calls run on the three-block kernel only (its epilogue applies the step diagonals)
   if (p.pd || tc_variant() == 3) {
     using L3 = tc::Tc3Layout<kTc3Chains, kTc3Stages>;
     auto kern3 = tc::chain_tc3_kernel<kTc3Chains, kTc3Stages>;

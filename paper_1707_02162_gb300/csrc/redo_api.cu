@@ -514,10 +514,13 @@ static PropLayout prop_layout(const redo_table* t, int64_t B, int64_t M, redo_pr
   }
   // the tensor-core path forms segment products in split FP16 and combines them in FP32
   L.eff_prec = prec == REDO_FP16X3 ? REDO_FP32 : prec;
+  // amplitude/phase calls: the SIMT chains carry each step's diagonal as an extra factor, the
+  // tensor-core chains apply it in the epilogue of the step's last product
+  const bool phase_factors = phase && prec != REDO_FP16X3;
   if (reunit_every > 0)
-    L.p = plan_chain_aligned(t, B, M, reunit_every, phase);
+    L.p = plan_chain_aligned(t, B, M, reunit_every, phase_factors);
   else
-    L.p = prec == REDO_FP16X3 ? plan_chain_tc(t, B, M, phase) : plan_chain(t, B, M, L.eff_prec, phase);
+    L.p = prec == REDO_FP16X3 ? plan_chain_tc(t, B, M) : plan_chain(t, B, M, L.eff_prec, phase_factors);
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t el = L.eff_prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
   const size_t n2 = (size_t)t->N * t->N;

@@ -115,8 +115,9 @@ cudaError_t launch_table_expand(const redo_table* t, double2* E, cudaStream_t s)
 
 // Segmented chain products for N <= 64 (SIMT, FP64 or FP32).
 // Amplitude/phase calls (pd non-null): every step opens with the diagonal factor
-// P_n = Z_n^dag Z_{n-1} (pd[b][n][0..N)), so a step has fps = K*digits + 1 factors on the
-// N <= 64 paths; the large-N path keeps fps = K*digits and applies P_n between launches.
+// P_n = Z_n^dag Z_{n-1} (pd[b][n][0..N)).  The N <= 64 SIMT chains carry it as a factor
+// (fps = K*digits + 1); the tensor-core chains apply it in an epilogue and the large-N chains
+// between launches (fps = K*digits).
 struct ChainPlan {
   int64_t B, M;
   int64_t F;          // factors per pulse = M*fps
@@ -143,7 +144,7 @@ cudaError_t launch_polar(const redo_table* t, int prec_in, int prec_out, const v
 // Tensor-core chains (kernels_tc.cu), N = 64, split-FP16.
 size_t tc_planes_bytes(const redo_table* t);
 cudaError_t launch_build_tc_planes(const redo_table* t, cudaStream_t s);
-ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M, bool phase = false);
+ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M);
 cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPlan& p,
                             void* seg_out, int64_t* status, cudaStream_t s);
 
