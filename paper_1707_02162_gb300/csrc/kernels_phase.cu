@@ -16,8 +16,11 @@ namespace {
 
 // one thread per (b, n, a): pd[b][n][a] = exp(i sum_k (phi[b][n][k] - phi[b][n-1][k]) sz[k][a]);
 // the threads of step M (n == M) write zf[b][a] = exp(-i sum_k phi[b][M-1][k] sz[k][a]).
+// With pd32 non-null the step diagonals are written in FP32 instead (for the split-FP16 chains):
+// the angle is summed and reduced to [-pi, pi] in FP64, its sine and cosine taken in FP32.
 __global__ void phase_diag_kernel(const double* __restrict__ phi, const double* __restrict__ sz, int64_t B,
-                                  int64_t M, int K, int N, double2* __restrict__ pd, double2* __restrict__ zf) {
+                                  int64_t M, int K, int N, double2* __restrict__ pd, float2* __restrict__ pd32,
+                                  double2* __restrict__ zf) {
   const int64_t total = B * (M + 1) * N;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -31,9 +34,16 @@ __global__ void phase_diag_kernel(const double* __restrict__ phi, const double* 
         const double prev = n > 0 ? cur[k - K] : 0.0;
         th += (cur[k] - prev) * sz[(int64_t)k * N + a];
       }
-      double sn, cs;
-      sincos(th, &sn, &cs);
-      pd[(b * M + n) * N + a] = make_double2(cs, sn);
+      if (pd32) {
+        const double red = th - 6.283185307179586 * rint(th * 0.15915494309189535);
+        float sf, cf;
+        sincosf((float)red, &sf, &cf);
+        pd32[(b * M + n) * N + a] = make_float2(cf, sf);
+      } else {
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        pd[(b * M + n) * N + a] = make_double2(cs, sn);
+      }
     } else {
       for (int k = 0; k < K && M > 0; ++k) th += cur[k - K] * sz[(int64_t)k * N + a];
       double sn, cs;
@@ -84,12 +94,12 @@ unsigned grid_y(int64_t n2) {
 }  // namespace
 
 cudaError_t launch_phase_diag(const redo_table* t, const double* phi, int64_t B, int64_t M, double2* pd,
-                              double2* zf, cudaStream_t s) {
+                              float2* pd32, double2* zf, cudaStream_t s) {
   const int64_t total = B * (M + 1) * t->N;
   if (total == 0) return cudaSuccess;
   int64_t blocks = (total + 255) / 256;
   if (blocks > (int64_t)t->num_sms * 32) blocks = (int64_t)t->num_sms * 32;
-  phase_diag_kernel<<<(unsigned)blocks, 256, 0, s>>>(phi, t->sz64, B, M, t->K, t->N, pd, zf);
+  phase_diag_kernel<<<(unsigned)blocks, 256, 0, s>>>(phi, t->sz64, B, M, t->K, t->N, pd, pd32, zf);
   return cudaGetLastError();
 }
 

@@ -95,9 +95,9 @@ struct TcArgs {
   float2* out;
   int64_t* status;
   int64_t fps;                // factors per step (K * digits)
-  // amplitude/phase calls: [units][M][64] diagonals P_n = Z_n^dag Z_{n-1} that open every step,
-  // applied by the epilogue of the step before (or as the initial state of a segment), else nullptr
-  const double2* pd;
+  // amplitude/phase calls: [units][M][64] diagonals P_n = Z_n^dag Z_{n-1} (FP32) that open every
+  // step, applied by the epilogue of the step before (or as the initial state of a segment), else nullptr
+  const float2* pd;
 };
 
 template <int CH, int EW, int STAGES>
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
       // 32j..32j+31 of its rows, the diagonal entry (m, m) to its component of the value.
       double dv = comp == 0 ? 1.0 : 0.0;
       if (a.pd && f0[c] % kd == 0) {
-        const double2 pv = a.pd[(unit[c] * a.M + f0[c] / kd) * kN + m];
+        const float2 pv = a.pd[(unit[c] * a.M + f0[c] / kd) * kN + m];
         dv = comp == 0 ? pv.x : pv.y;
       }
       const __half dh = __double2half(dv);
@@ -754,12 +754,12 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
         // diagonal that opens the next step, when that step starts inside the segment
         const bool stage_ph = a.pd && (t == 0 || f % kd == 0) && (f / kd + 1) * kd < f0[c] + len[c];
         const bool apply_ph = a.pd && !last && (f + 1) % kd == 0;
-        double2 pv = make_double2(0.0, 0.0);
+        float2 pv = make_float2(0.f, 0.f);
         if (stage_ph && et < 64) pv = a.pd[(unit[c] * a.M + f / kd + 1) * kN + et];
         bool ok = !*abort_flag && mbar_wait_bounded_n(&mma_done[c], (uint32_t)(t & 1), kTcWaitLimit);
         if (a.pd) {
           // the chain's epilogue warps meet at barriers below: they agree on every step
-          if (stage_ph && et < 64) ph[et] = make_float2((float)pv.x, (float)pv.y);
+          if (stage_ph && et < 64) ph[et] = pv;
           ok = named_barrier_and(1 + c, 32 * EW, ok);
         } else {
           ok = __all_sync(0xffffffffu, ok);
@@ -948,7 +948,7 @@ constexpr int kTc3Chains = 2, kTc3Stages = 4;
 cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPlan& p,
                             void* seg_out, int64_t* status, cudaStream_t s) {
   // amplitude/phase calls run on the three-block kernel only (its epilogue applies the step diagonals)
-  if (p.pd || tc_variant() == 3) {
+  if (p.pd32 || tc_variant() == 3) {
     using L3 = tc::Tc3Layout<kTc3Chains, kTc3Stages>;
     auto kern3 = tc::chain_tc3_kernel<kTc3Chains, kTc3Stages>;
     cudaError_t e = cudaFuncSetAttribute(kern3, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -969,7 +969,7 @@ cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPl
     a.out = (float2*)seg_out;
     a.status = status;
     a.fps = p.fps > 0 ? p.fps : (int64_t)t->K * t->digits;
-    a.pd = p.pd;
+    a.pd = p.pd32;
     const int64_t G = p.B * p.S;
     const int64_t blocks = (G + kTc3Chains - 1) / kTc3Chains;
     if (blocks == 0) return cudaSuccess;
@@ -998,7 +998,7 @@ cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPl
     a.out = (float2*)seg_out;
     a.status = status;
     a.fps = p.fps > 0 ? p.fps : (int64_t)t->K * t->digits;
-    a.pd = p.pd;
+    a.pd = p.pd32;
     const int64_t G = p.B * p.S;
     const int64_t blocks = (G + L2::CH - 1) / L2::CH;
     if (blocks == 0) return cudaSuccess;

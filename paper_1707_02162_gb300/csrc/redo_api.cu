@@ -571,8 +571,13 @@ static redo_status propagate_core(const redo_table* t, const int32_t* q, const d
   if (phase) {
     double2* pd = (double2*)((char*)workspace + L.pd_off);
     zf = (double2*)((char*)workspace + L.zf_off);
-    if ((e = launch_phase_diag(t, phi, B, M, pd, zf, s)) != cudaSuccess) return cuda_error(e, "phase diagonals");
-    L.p.pd = pd;
+    const bool tc = prec == REDO_FP16X3 && t->N <= kSmallN;     // the split-FP16 chains take FP32 diagonals
+    if ((e = launch_phase_diag(t, phi, B, M, tc ? nullptr : pd, tc ? (float2*)pd : nullptr, zf, s)) != cudaSuccess)
+      return cuda_error(e, "phase diagonals");
+    if (tc)
+      L.p.pd32 = (const float2*)pd;
+    else
+      L.p.pd = pd;
   }
   // the last rotation Z_{M-1} of an amplitude/phase call, applied before the fidelity
   auto rotate = [&](const void*& fin, int& fin_prec) -> cudaError_t {

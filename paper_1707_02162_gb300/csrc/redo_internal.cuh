@@ -125,6 +125,7 @@ struct ChainPlan {
   int64_t S;          // segments per pulse
   int64_t fps = 0;    // factors per step
   const double2* pd = nullptr;
+  const float2* pd32 = nullptr;   // the same diagonals in FP32 (tensor-core chains)
 };
 ChainPlan plan_chain(const redo_table* t, int64_t B, int64_t M, int prec, bool phase = false);
 size_t chain_workspace_bytes(const redo_table* t, const ChainPlan& p, int prec);
@@ -238,8 +239,9 @@ cudaError_t launch_half_drift_vec(const redo_table* t, const double2* psi, int64
 // Amplitude/phase controls (kernels_phase.cu).  pd[b][n][a] = exp(i sum_k (phi[b][n][k] -
 // phi[b][n-1][k]) sz[k][a]) (phi[b][-1] = 0), the diagonal of Z_n^dag Z_{n-1};
 // zf[b][a] = exp(-i sum_k phi[b][M-1][k] sz[k][a]), the diagonal of Z_{M-1} (1 when M = 0).
+// With pd32 non-null the diagonals go there in FP32 (pd unused).
 cudaError_t launch_phase_diag(const redo_table* t, const double* phi, int64_t B, int64_t M, double2* pd,
-                              double2* zf, cudaStream_t s);
+                              float2* pd32, double2* zf, cudaStream_t s);
 // X_g <- P_n X_g in place for the chains g = (u, s) of a step-aligned plan, n = s*sps + i
 // (chains with n >= M untouched); X of precision prec.
 cudaError_t launch_phase_rows(int N, int prec, void* X, int64_t G, int64_t S, int64_t sps, int64_t i,
