@@ -415,6 +415,20 @@ redo_status redo_propagate_phase(const redo_table* t, const int32_t* q, const do
 redo_status redo_propagate_phase_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
                                            int32_t reunit_every, size_t* bytes);
 
+/*
+ * redo_batched_product -- C_b = op(A_b) op(B_b), b < count, for the time-split layer (one pulse
+ * cut into time segments, one per rank: U = S_{G-1} ... S_0, and segment r's gradient taken
+ * against the target L_r^dag U_T P_r^dag with P_r = S_{r-1} ... S_0, L_r = S_{G-1} ... S_{r+1};
+ * Section III's unitary fidelity is unchanged by that regrouping).
+ *  N          dimension, 1..1024.
+ *  A, B       device complex128 [count][N][N] when *_batched != 0, else one [N][N] used for all b.
+ *  adjA/adjB  nonzero: use the conjugate transpose.
+ *  C          device complex128 [count][N][N], written; must not overlap A or B (REDO_ERR_INVALID).
+ * FP64 throughout; asynchronous on `stream`.
+ */
+redo_status redo_batched_product(int32_t N, int64_t count, const void* A, int32_t adjA, int32_t A_batched,
+                                 const void* B, int32_t adjB, int32_t B_batched, void* C, void* stream);
+
 /* Scratch bytes redo_propagate needs for (B, M, prec, reunit_every) on this table. */
 redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
                                      redo_precision prec, int32_t reunit_every, size_t* bytes);

@@ -605,7 +605,8 @@ struct Tc3Layout {
   static_assert(kAlloc <= 232448, "shared memory budget");
 };
 
-template <int CH, int STAGES>
+// PH: amplitude/phase call (a.pd non-null), the step diagonals applied by the epilogue.
+template <int CH, int STAGES, bool PH>
 __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_kernel(TcArgs a) {
   using L = Tc3Layout<CH, STAGES>;
   constexpr int EW = L::EW;
@@ -721,7 +722,7 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
       // amplitude/phase call (Y = X^T is diagonal either way): this thread sets its K columns
       // 32j..32j+31 of its rows, the diagonal entry (m, m) to its component of the value.
       double dv = comp == 0 ? 1.0 : 0.0;
-      if (a.pd && f0[c] % kd == 0) {
+      if (PH && f0[c] % kd == 0) {
         const float2 pv = a.pd[(unit[c] * a.M + f0[c] / kd) * kN + m];
         dv = comp == 0 ? pv.x : pv.y;
       }
@@ -752,12 +753,12 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
         const bool last = (t == len[c] - 1);
         // amplitude/phase calls: the first product of a step (in this segment) stages the
         // diagonal that opens the next step, when that step starts inside the segment
-        const bool stage_ph = a.pd && (t == 0 || f % kd == 0) && (f / kd + 1) * kd < f0[c] + len[c];
-        const bool apply_ph = a.pd && !last && (f + 1) % kd == 0;
+        const bool stage_ph = PH && (t == 0 || f % kd == 0) && (f / kd + 1) * kd < f0[c] + len[c];
+        const bool apply_ph = PH && !last && (f + 1) % kd == 0;
         float2 pv = make_float2(0.f, 0.f);
         if (stage_ph && et < 64) pv = a.pd[(unit[c] * a.M + f / kd + 1) * kN + et];
         bool ok = !*abort_flag && mbar_wait_bounded_n(&mma_done[c], (uint32_t)(t & 1), kTcWaitLimit);
-        if (a.pd) {
+        if (PH) {
           // the chain's epilogue warps meet at barriers below: they agree on every step
           if (stage_ph && et < 64) ph[et] = pv;
           ok = named_barrier_and(1 + c, 32 * EW, ok);
@@ -950,7 +951,8 @@ cudaError_t launch_chain_tc(const redo_table* t, const int32_t* q, const ChainPl
   // amplitude/phase calls run on the three-block kernel only (its epilogue applies the step diagonals)
   if (p.pd32 || tc_variant() == 3) {
     using L3 = tc::Tc3Layout<kTc3Chains, kTc3Stages>;
-    auto kern3 = tc::chain_tc3_kernel<kTc3Chains, kTc3Stages>;
+    auto kern3 = p.pd32 ? tc::chain_tc3_kernel<kTc3Chains, kTc3Stages, true>
+                        : tc::chain_tc3_kernel<kTc3Chains, kTc3Stages, false>;
     cudaError_t e = cudaFuncSetAttribute(kern3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)L3::kAlloc);
     if (e != cudaSuccess) return e;

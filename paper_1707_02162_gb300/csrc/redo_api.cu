@@ -709,6 +709,24 @@ redo_status redo_propagate_phase(const redo_table* t, const int32_t* q, const do
                         workspace, workspace_bytes, dev_status, stream);
 }
 
+redo_status redo_batched_product(int32_t N, int64_t count, const void* A, int32_t adjA, int32_t A_batched,
+                                 const void* B, int32_t adjB, int32_t B_batched, void* C, void* stream) {
+  if (N <= 0 || N > kMaxN) return set_error(REDO_ERR_INVALID, "N=%d out of range", N);
+  if (count < 0) return set_error(REDO_ERR_INVALID, "negative count");
+  if (count == 0) return REDO_OK;
+  if (!A || !B || !C) return set_error(REDO_ERR_INVALID, "null matrix pointer");
+  const int64_t n2 = (int64_t)N * N;
+  const char *a0 = (const char*)A, *b0 = (const char*)B, *c0 = (const char*)C;
+  const int64_t ab = (A_batched ? count : 1) * n2 * 16, bb = (B_batched ? count : 1) * n2 * 16, cb = count * n2 * 16;
+  if ((c0 < a0 + ab && a0 < c0 + cb) || (c0 < b0 + bb && b0 < c0 + cb))
+    return set_error(REDO_ERR_INVALID, "C overlaps A or B");
+  cudaError_t e = launch_batched_product(N, count, (const double2*)A, adjA ? 1 : 0, A_batched ? n2 : 0,
+                                         (const double2*)B, adjB ? 1 : 0, B_batched ? n2 : 0, (double2*)C,
+                                         (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "batched product");
+  return REDO_OK;
+}
+
 // ---------------------------------------------------------------------------
 // GRAPE gradient
 // ---------------------------------------------------------------------------

@@ -250,6 +250,11 @@ cudaError_t launch_phase_rows(int N, int prec, void* X, int64_t G, int64_t S, in
 cudaError_t launch_phase_final(int N, int64_t B, int prec, const void* X, const double2* zf, double2* out,
                                cudaStream_t s);
 
+// C_b = op(A_b) op(B_b) for b < count, FP64 complex N x N, op = conjugate transpose when adj != 0;
+// sA / sB are the element strides between consecutive A_b / B_b (0 broadcasts one matrix).
+cudaError_t launch_batched_product(int N, int64_t count, const double2* A, int adjA, int64_t sA, const double2* B,
+                                   int adjB, int64_t sB, double2* C, cudaStream_t s);
+
 cudaError_t launch_finalize(const redo_table* t, int64_t B, int prec, const void* prod,
                             void* U_out, const double2* U_target, double* F_out, double2* tau_out,
                             cudaStream_t s);

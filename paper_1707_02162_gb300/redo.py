@@ -30,7 +30,7 @@ EXPORTS = [
     "redo_grape_step", "redo_simulate", "redo_simulate_workspace", "redo_mlp_sizes", "redo_mlp_forward",
     "redo_mlp_backward", "redo_mlp_adam", "redo_grape_adam_step", "redo_expect_diag",
     "redo_state_grad", "redo_state_grad_workspace", "redo_table_set_phase_axes", "redo_propagate_phase",
-    "redo_propagate_phase_workspace",
+    "redo_propagate_phase_workspace", "redo_batched_product",
 ]
 PROFILE_PHASES = 11
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -63,6 +63,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_propagate.argtypes = [vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_propagate_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_table_set_phase_axes.argtypes = [vp, vp]
+    L.redo_batched_product.argtypes = [i32, i64, vp, i32, i32, vp, i32, i32, vp, vp]
     L.redo_propagate_phase.argtypes = [vp, vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_propagate_phase_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_noalloc.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
@@ -169,6 +170,19 @@ def redo_propagate(handle: int, q: torch.Tensor, prec, U_out: torch.Tensor | Non
                                          _ptr(U_out), _ptr(U_target), _ptr(F_out), _ptr(tau_out),
                                          _ptr(workspace), workspace.numel() * workspace.element_size(),
                                          _ptr(status), _stream(stream)))
+
+
+def redo_batched_product(A: torch.Tensor, B: torch.Tensor, adjA: bool = False, adjB: bool = False,
+                         out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """C_b = op(A_b) op(B_b) (complex128 on the device; a 2-D operand is used for every b)."""
+    N = A.shape[-1]
+    count = max(A.shape[0] if A.dim() == 3 else 1, B.shape[0] if B.dim() == 3 else 1)
+    if out is None:
+        out = torch.empty((count, N, N), dtype=torch.complex128, device=A.device)
+    A, B = A.contiguous(), B.contiguous()
+    _check(load_library().redo_batched_product(N, count, _ptr(A), int(adjA), int(A.dim() == 3), _ptr(B), int(adjB),
+                                               int(B.dim() == 3), _ptr(out), _stream(stream)))
+    return out
 
 
 def redo_table_set_phase_axes(handle: int, sz: np.ndarray):
