@@ -38,9 +38,10 @@ Functions and the passage each one follows:
   symmetric (Strang) placement of the drift around the control factors of a
   step, the second-order variant of the Section III step.
 * :func:`phase_rotation` / :func:`phase_step_propagator` / :func:`propagate_phase` /
-  :func:`phase_split_step` -- amplitude/phase controls (Section III, Eq. vn and the
-  Dirac-frame step after Eq. vnd): one x-table per species, the phase applied as the
-  diagonal rotation Z_n on both sides of the step's control factors.
+  :func:`phase_split_step` / :func:`phase_gradient` -- amplitude/phase controls (Section
+  III, Eq. vn and the Dirac-frame step after Eq. vnd): one x-table per species, the phase
+  applied as the diagonal rotation Z_n on both sides of the step's control factors; the GRAPE
+  gradient in amplitudes and phases from the definitions.
 * :func:`simulate_expectation` -- ``<M> = Tr[M rho(t)]`` of Section IV for a
   pure initial state; :func:`expect_mixed` -- the same for a dense (mixed or
   deviation) initial density matrix, the order parameter of the freezing study.
@@ -386,6 +387,60 @@ def phase_split_step(H0, Sx, sz, dt, amp_row, phi_row):
     for k in range(Sx.shape[0]):
         E = expm_pade13(-1j * dt * amp_row[k] * Sx[k]) @ E
     return Z @ E @ Z.conj().T @ expm_pade13(-1j * dt * np.asarray(H0, dtype=np.complex128))
+
+
+def phase_gradient(T, D, Sx, sz, dt, digits_bm, phi_bm, U_target):
+    """``(F, gA, gphi)``: the unitary fidelity of the amplitude/phase chain and its derivatives
+    ``gA[n][k] = dF/dA_kn`` (at the quantised amplitudes) and ``gphi[n][k] = dF/dphi_kn``.
+
+    The paper optimises the control profiles {Omega_kn, phi_kn} by GRAPE (Section III) without
+    printing the gradient; this one follows from the definitions.  With ``U = U_M ... U_1``,
+    ``X_{n-1} = U_{n-1} ... U_1``, ``L_n = U_M ... U_{n+1}`` and ``tau = Tr(U_T^dag U)``,
+    ``dF/dx = (2/N^2) Re(conj(tau) Tr(U_T^dag L_n (dU_n/dx) X_{n-1}))`` for a parameter x of step n,
+    where, for ``U_n = Z_n E_{K-1} ... E_0 Z_n^dag D``,
+    ``dU_n/dA_kn = Z_n E_{K-1} ... E_{k+1} (-i dt S_xk) E_k ... E_0 Z_n^dag D`` (S_xk commutes with
+    its own exponential) and ``dU_n/dphi_kn = -i [S_kz, Z_n E_n Z_n^dag] D``.
+    """
+    N = D.shape[0]
+    M = digits_bm.shape[0]
+    K = Sx.shape[0]
+    steps = [phase_step_propagator(T, D, digits_bm[n], phi_bm[n], sz) for n in range(M)]
+    X = [np.eye(N, dtype=np.complex128)]
+    for n in range(M):
+        X.append(steps[n] @ X[-1])
+    U = X[M]
+    L = []                                               # L[n]: the steps after step n (0-based)
+    for n in range(M):
+        Ln = np.eye(N, dtype=np.complex128)
+        for m in range(n + 1, M):
+            Ln = steps[m] @ Ln
+        L.append(Ln)
+    tau = trace_overlap(U_target, U)
+    F = (tau.real * tau.real + tau.imag * tau.imag) / float(N * N)
+    gA = np.zeros((M, K))
+    gphi = np.zeros((M, K))
+    Sz = [np.diag(np.asarray(sz[k], dtype=np.float64)).astype(np.complex128) for k in range(K)]
+    for n in range(M):
+        Z = np.diag(phase_rotation(phi_bm[n], sz))
+        E = step_factors(T, D, digits_bm[n])
+        Et = np.eye(N, dtype=np.complex128)
+        for Ek in E:
+            Et = Ek @ Et
+        for k in range(K):
+            before = np.eye(N, dtype=np.complex128)
+            for m in range(k + 1):
+                before = E[m] @ before                   # E_k ... E_0
+            after = np.eye(N, dtype=np.complex128)
+            for m in range(k + 1, K):
+                after = E[m] @ after                     # E_{K-1} ... E_{k+1}
+            dU = Z @ after @ (-1j * dt * Sx[k]) @ before @ Z.conj().T @ D
+            dtau = np.trace(U_target.conj().T @ L[n] @ dU @ X[n])
+            gA[n, k] = 2.0 / (N * N) * (np.conj(tau) * dtau).real
+            W = Z @ Et @ Z.conj().T
+            dU = -1j * (Sz[k] @ W - W @ Sz[k]) @ D
+            dtau = np.trace(U_target.conj().T @ L[n] @ dU @ X[n])
+            gphi[n, k] = 2.0 / (N * N) * (np.conj(tau) * dtau).real
+    return F, gA, gphi
 
 
 # ---------------------------------------------------------------------------

@@ -698,3 +698,78 @@ def test_phase_single_spin_closed_form():
         th = A * M * dt / 2
         ref = np.cos(th) * I2 - 1j * np.sin(th) * (np.cos(phi) * SX + np.sin(phi) * SY)
         assert np.abs(U - ref).max() < 1e-12
+
+
+def _phase_system(seed=21, M=5):
+    Sx, Sy, sz = _two_species()
+    rng = np.random.default_rng(seed)
+    H0 = np.diag(rng.uniform(-3e4, 3e4, 4)).astype(complex)
+    dt, base, digits = 2e-6, 16, 2
+    lo, hi = np.zeros(2), np.full(2, 2 * np.pi * 2e4)
+    T, D = O.build_table(H0, Sx, dt, lo, hi, base ** digits, base, digits)
+    q, _, _ = O.quantize(rng.uniform(0, hi[0], (1, M, 2)), lo, hi, base ** digits)
+    dig = O.level_digits(q, base, digits)[0]
+    ahat = O.level_values(q[0], lo, hi, base ** digits)
+    phi = rng.uniform(0, 2 * np.pi, (M, 2))
+    from scipy.stats import unitary_group
+    UT = unitary_group.rvs(4, random_state=seed)
+    return H0, Sx, Sy, sz, dt, T, D, dig, ahat, phi, UT
+
+
+def test_phase_gradient_matches_central_differences():
+    # derivatives of F of the continuous amplitude/phase chain (Pade exponentials, unquantised
+    # amplitudes at the level values) by central differences in A_kn and phi_kn
+    H0, Sx, Sy, sz, dt, T, D, dig, ahat, phi, UT = _phase_system()
+    F, gA, gphi = O.phase_gradient(T, D, Sx, sz, dt, dig, phi, UT)
+
+    def fid(a, p):
+        U = np.eye(4, dtype=complex)
+        for n in range(a.shape[0]):
+            U = O.phase_split_step(H0, Sx, sz, dt, a[n], p[n]) @ U
+        return O.fidelity(UT, U)
+    assert abs(F - fid(ahat, phi)) < 1e-12
+    for n in range(phi.shape[0]):
+        for k in range(2):
+            h = 10.0                                     # rad/s: dt h = 2e-5 rad
+            ap, am = ahat.copy(), ahat.copy()
+            ap[n, k] += h
+            am[n, k] -= h
+            assert abs((fid(ap, phi) - fid(am, phi)) / (2 * h) - gA[n, k]) <= 1e-7 * np.abs(gA).max()
+            e = 1e-5
+            pp, pm = phi.copy(), phi.copy()
+            pp[n, k] += e
+            pm[n, k] -= e
+            assert abs((fid(ahat, pp) - fid(ahat, pm)) / (2 * e) - gphi[n, k]) <= 1e-7 * np.abs(gphi).max()
+
+
+def test_phase_gradient_zero_phase_amplitudes_are_the_x_gradient():
+    H0, Sx, Sy, sz, dt, T, D, dig, ahat, phi, UT = _phase_system(22)
+    F, gA, _ = O.phase_gradient(T, D, Sx, sz, dt, dig, np.zeros_like(phi), UT)
+    Fo, go = O.grape_gradient(T, D, Sx, dt, dig, UT)
+    assert abs(F - Fo) < 1e-14 and np.abs(gA - go).max() <= 1e-12 * np.abs(go).max()
+
+
+def test_phase_gradient_single_spin_common_axis_closed_form():
+    # one spin, no drift, every step with the same amplitude A (on the grid) and phase phi: the
+    # steps commute, U = exp(-i theta (cos phi X + sin phi Y)/2), theta = A M dt; against the
+    # target exp(-i theta_T X / 2), tau = 2 cos(theta_T/2) cos(theta/2) + 2 sin(theta_T/2) sin(theta/2) cos phi,
+    # and the step derivatives add up to the derivatives in the common A and phi
+    base, digits = 16, 2
+    levels = base ** digits
+    lo, hi = np.zeros(1), np.array([2 * np.pi * 1e4])
+    dt, M = 3e-6, 12
+    T, D = O.build_table(np.zeros((2, 2), complex), (SX / 2)[None], dt, lo, hi, levels, base, digits)
+    qv = 201
+    A = lo[0] + qv * (hi[0] - lo[0]) / (levels - 1)
+    dig = O.level_digits(np.full((M, 1), qv), base, digits)
+    thT, phi = 0.7, 0.9
+    UT = np.cos(thT / 2) * I2 - 1j * np.sin(thT / 2) * SX
+    F, gA, gphi = O.phase_gradient(T, D, (SX / 2)[None], (np.diag(SZ).real / 2)[None], dt, dig,
+                                   np.full((M, 1), phi), UT)
+    th = A * M * dt
+    tau = 2 * np.cos(thT / 2) * np.cos(th / 2) + 2 * np.sin(thT / 2) * np.sin(th / 2) * np.cos(phi)
+    assert abs(F - tau * tau / 4) < 1e-13
+    dtau_dth = -np.cos(thT / 2) * np.sin(th / 2) + np.sin(thT / 2) * np.cos(th / 2) * np.cos(phi)
+    dtau_dphi = -2 * np.sin(thT / 2) * np.sin(th / 2) * np.sin(phi)
+    assert abs(gA.sum() - 2 * tau * dtau_dth * M * dt / 4) < 1e-12 * abs(gA.sum()) + 1e-15
+    assert abs(gphi.sum() - 2 * tau * dtau_dphi / 4) < 1e-12
