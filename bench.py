@@ -15,6 +15,7 @@ oracle instead, on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import multiprocessing as mp
 import os
@@ -648,8 +649,26 @@ def run_workload(args):
                                                                ws64), 1)
         dF = float((F64 - F[:Bs]).abs().max())
         dU = float((U64 - U[:Bs]).abs().max())
+        # GRAPE gradient in amplitudes and phases (FP32 SIMT chains), all pulses
+        gA = torch.empty((B, M, w.K), dtype=torch.float64, device="cuda")
+        gP = torch.empty_like(gA)
+        Fg = torch.empty(B, dtype=torch.float64, device="cuda")
+        nbg = ctypes.c_size_t()
+        Lr = redo.load_library()
+        redo._check(Lr.redo_fidelity_grad_phase_workspace(ctypes.c_void_p(t.handle), B, M, redo._prec("fp32"), 64,
+                                                          ctypes.byref(nbg)))
+        wsg = torch.empty(nbg.value, dtype=torch.uint8, device="cuda")
+
+        def itg():
+            redo.redo_quantize(t.handle, u, q)
+            redo._check(Lr.redo_fidelity_grad_phase(ctypes.c_void_p(t.handle), redo._ptr(q), redo._ptr(phi), B, M,
+                                                    redo._ptr(target), 0, redo._prec("fp32"), 64, redo._ptr(Fg),
+                                                    redo._ptr(gA), redo._ptr(gP), redo._ptr(wsg), wsg.numel(), None,
+                                                    None))
+        itg()
+        msg = _events_time(itg, 1)
         t.close()
-        del ws, ws64
+        del ws, ws64, wsg
         # the same pulses in x/y form: 12 controls, one more factor per species and step
         Hxy = inputs.controls_local_xy(6)
         txy = redo.Table(w.H0, Hxy, w.dt, np.full(12, -w.extra["Omega"]), np.full(12, w.extra["Omega"]), w.base,
@@ -676,6 +695,9 @@ def run_workload(args):
                     "speedup_vs_xy_form": msxy / ms,
                     "fp64_same_gpu": {"pulse_steps_per_s": Bs * M / (ms64 / 1e3), "pulses": Bs,
                                       "max_abs_dF_fp16x3_vs_fp64": dF, "max_abs_dU": dU},
+                    "grape_gradient_fp32": {"instance_iters_per_s": B * 1e3 / msg, "ms_per_call": msg,
+                                            "what": "F, dF/dA and dF/dphi of all pulses, FP32 SIMT chains, "
+                                                    "checkpoints every 64 steps"},
                     "roofline": {"kernel": "chain_tc", "kernel_ms": tc_ms,
                                  "hbm_achieved_gbs": op_bytes / (tc_ms / 1e3) / 1e9 if tc_ms else None,
                                  "hbm_frac": (op_bytes / (tc_ms / 1e3) / 1e9 / pk.get("hbm_gbs", 6794.5)

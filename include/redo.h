@@ -416,6 +416,26 @@ redo_status redo_propagate_phase_workspace(const redo_table* t, int64_t B, int64
                                            int32_t reunit_every, size_t* bytes);
 
 /*
+ * redo_fidelity_grad_phase -- GRAPE gradient of F = |Tr(U_target^dag U)|^2 / N^2 for amplitude/phase
+ * controls (Section III: the control profiles {Omega_kn, phi_kn} are what GRAPE optimises):
+ *  grad_amp    device double [B][M][K]: dF/dA_kn at the quantised amplitudes (1/(rad/s)),
+ *  grad_phase  device double [B][M][K]: dF/dphi_kn (1/rad),
+ * the other arguments as redo_fidelity_grad plus phi (device double [B][M][K]).  With
+ * P_n = Z_n^dag Z_{n-1} the chain is Z_{M-1} (E'_M P_M) ... (E'_1 P_1); dF/dA follows from the table
+ * factors as in redo_fidelity_grad, and dF/dphi_kn = (2/N^2) Im(conj(tau) (Tz_{n+1,k} - Tz_{n,k}))
+ * with Tz_{n,k} = Tr(S_kz W_n) at the step boundaries (W_n the product of the chain after the
+ * boundary, the transformed target and the chain before it).
+ * N <= 64, REDO_FP64 or REDO_FP32; REDO_ERR_UNSUPPORTED otherwise.  Workspace from
+ * redo_fidelity_grad_phase_workspace.
+ */
+redo_status redo_fidelity_grad_phase(const redo_table* t, const int32_t* q, const double* phi, int64_t B, int64_t M,
+                                     const void* U_target, int32_t target_batched, redo_precision prec,
+                                     int32_t checkpoint_every, double* F_out, double* grad_amp, double* grad_phase,
+                                     void* workspace, size_t workspace_bytes, int64_t* dev_status, void* stream);
+redo_status redo_fidelity_grad_phase_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                               int32_t checkpoint_every, size_t* bytes);
+
+/*
  * redo_batched_product -- C_b = op(A_b) op(B_b), b < count, for the time-split layer (one pulse
  * cut into time segments, one per rank: U = S_{G-1} ... S_0, and segment r's gradient taken
  * against the target L_r^dag U_T P_r^dag with P_r = S_{r-1} ... S_0, L_r = S_{G-1} ... S_{r+1};

@@ -122,14 +122,26 @@ struct GradArgs {
   double scale;              // 2 dt / N^2
   double* grad;              // [B][M][K]
   int64_t* status;
+  // amplitude/phase calls: every step opens with the diagonal P_n = pd[b][n] (factor 0 of
+  // fps = K*d + 1); at each such factor the sweep records Tz[b][n][k] = Tr(S_kz P R), and the
+  // last segment records Tz[b][M][k] at the end of the chain.  pd == nullptr otherwise.
+  int64_t fps;
+  const double2* pd;
+  const double* sz;          // [K][N]
+  double2* Tz;               // [B][M+1][K]
 };
 
+// Table operator of factor f (nullptr for a step-opening phase factor).
 template <typename R, int N>
 __device__ __forceinline__ const cplx<R>* grad_factor(const GradArgs<R>& a, int64_t b, int64_t f,
                                                       int* k_out, int* j_out, int64_t* n_out) {
-  const int64_t kd = (int64_t)a.K * a.d;
-  const int64_t n = f / kd;
-  const int r = (int)(f - n * kd);
+  const int64_t n = f / a.fps;
+  int r = (int)(f - n * a.fps);
+  *n_out = n;
+  if (a.pd) {
+    if (r == 0) return nullptr;
+    --r;
+  }
   const int k = r / a.d, j = r - k * a.d;
   int32_t qv = a.q[(b * a.M + n) * a.K + k];
   if (qv < 0 || qv >= a.levels) {
@@ -176,23 +188,56 @@ grad_sweep_kernel(GradArgs<R> a) {
   }
   __syncthreads();
   // factors are visited in reverse: t-th visit is factor f1-1-t
-  if (lt == 0) {
-    for (int st = 0; st < STAGES && st < len; ++st) {
-      int k, j;
-      int64_t n;
-      const cplx<R>* src = grad_factor<R, N>(a, b, f1 - 1 - st, &k, &j, &n);
+  // a phase factor has no operand to copy: its stage completes on the arrival alone
+  auto issue = [&](int st, int64_t f) {
+    int k, j;
+    int64_t n;
+    const cplx<R>* src = grad_factor<R, N>(a, b, f, &k, &j, &n);
+    if (src) {
       mbar_arrive_expect_tx(&bar[st], BYTES);
       bulk_load(Abuf + st * N2, src, BYTES, &bar[st]);
+    } else {
+      mbar_arrive(&bar[st]);
     }
+  };
+  if (lt == 0) {
+    for (int st = 0; st < STAGES && st < len; ++st) issue(st, f1 - 1 - st);
   }
+  __shared__ double2 dg[64];
+  // Tz[b][nz][k] = sum_a sz[k][a] (P R)[a][a] for every species k
+  auto phase_traces = [&](int64_t nz) {
+    if (lt < N) {
+      double re = 0.0, im = 0.0;
+      for (int x = 0; x < N; ++x) {
+        const cplx<R> pv = P[lt * N + x], rv = Rm[x * N + lt];
+        re += (double)pv.x * rv.x - (double)pv.y * rv.y;
+        im += (double)pv.x * rv.y + (double)pv.y * rv.x;
+      }
+      dg[lt] = make_double2(re, im);
+    }
+    __syncthreads();
+    for (int kk = lt; kk < a.K; kk += MM::THREADS) {
+      double re = 0.0, im = 0.0;
+      for (int x = 0; x < N; ++x) {
+        const double w = a.sz[(int64_t)kk * N + x];
+        re += w * dg[x].x;
+        im += w * dg[x].y;
+      }
+      a.Tz[(b * (a.M + 1) + nz) * a.K + kk] = make_double2(re, im);
+    }
+    __syncthreads();
+  };
+  if (a.pd && len > 0 && f1 == a.F) phase_traces(a.M);   // end of the chain
   cplx<R> Y1[TM][TM], Y2[TM][TM];
   for (int64_t t = 0; t < len; ++t) {
     const int64_t f = f1 - 1 - t;
-    const int64_t kd = (int64_t)a.K * a.d;
-    const int64_t n = f / kd;
-    const int r = (int)(f - n * kd);
+    const int64_t n = f / a.fps;
+    int r = (int)(f - n * a.fps);
+    const bool phase = a.pd && r == 0;
+    if (a.pd) --r;
     const int k = r / a.d, j = r - k * a.d;
-    if (j == a.d - 1) {
+    if (phase) phase_traces(n);
+    if (!phase && j == a.d - 1) {
       // Tr(H_k P R) = sum over nonzeros (row i, col c) of H_k[i][c] (P R)[c][i]
       const int p0 = a.hk_ptr[k * (N + 1)];
       const int p1 = a.hk_ptr[k * (N + 1) + N];
@@ -233,18 +278,30 @@ grad_sweep_kernel(GradArgs<R> a) {
     __syncthreads();
     if (abort_flag) break;
     const cplx<R>* A = Abuf + stage * N2;
-    MM::run_adj(A, P, lt, Y1);     // P <- A^dag P
-    MM::run(Rm, A, lt, Y2);        // R <- R A
+    if (phase) {
+      // P <- diag(p)^dag P (rows), R <- R diag(p) (columns)
+      const double2* pv = a.pd + (b * a.M + n) * N;
+      const int ty = lt / MM::TX, tx = lt % MM::TX;
+#pragma unroll
+      for (int u = 0; u < TM; ++u)
+#pragma unroll
+        for (int v = 0; v < TM; ++v) {
+          const int row = ty + MM::TY * u, col = tx + MM::TX * v;
+          const double2 pr = pv[row], pc = pv[col];
+          const cplx<R> x = P[row * N + col], y = Rm[row * N + col];
+          Y1[u][v] = cmake<R>((R)(pr.x * (double)x.x + pr.y * (double)x.y), (R)(pr.x * (double)x.y - pr.y * (double)x.x));
+          Y2[u][v] = cmake<R>((R)(pc.x * (double)y.x - pc.y * (double)y.y), (R)(pc.x * (double)y.y + pc.y * (double)y.x));
+        }
+    } else {
+      MM::run_adj(A, P, lt, Y1);     // P <- A^dag P
+      MM::run(Rm, A, lt, Y2);        // R <- R A
+    }
     __syncthreads();
     MM::store(P, lt, Y1);
     MM::store(Rm, lt, Y2);
     if (lt == 0 && t + STAGES < len) {
       fence_proxy_async_smem();
-      int k2, j2;
-      int64_t n2;
-      const cplx<R>* src = grad_factor<R, N>(a, b, f1 - 1 - (t + STAGES), &k2, &j2, &n2);
-      mbar_arrive_expect_tx(&bar[stage], BYTES);
-      bulk_load(Abuf + stage * N2, src, BYTES, &bar[stage]);
+      issue(stage, f1 - 1 - (t + STAGES));
     }
     __syncthreads();
   }
@@ -307,8 +364,12 @@ cudaError_t launch_grad_scan(const redo_table* t, int64_t B, int64_t S, int prec
 template <typename R>
 static cudaError_t grad_sweep_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
                                 const void* Pck, const void* Rck, const double2* tau,
-                                double* grad, int64_t* status, cudaStream_t s) {
+                                double* grad, int64_t* status, double2* Tz, cudaStream_t s) {
   GradArgs<R> a;
+  a.fps = p.fps > 0 ? p.fps : (int64_t)t->K * t->digits;
+  a.pd = p.pd;
+  a.sz = t->sz64;
+  a.Tz = Tz;
   a.T = std::is_same<R, double>::value ? (const cplx<R>*)t->T64 : (const cplx<R>*)t->T32;
   a.q = q;
   a.M = p.M;
@@ -342,9 +403,9 @@ static cudaError_t grad_sweep_t(const redo_table* t, const int32_t* q, const Cha
 
 cudaError_t launch_grad_sweep(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
                               const void* Pck, const void* Rck, const double2* tau, double* grad,
-                              int64_t* status, cudaStream_t s) {
-  if (prec == REDO_FP64) return grad_sweep_t<double>(t, q, p, Pck, Rck, tau, grad, status, s);
-  return grad_sweep_t<float>(t, q, p, Pck, Rck, tau, grad, status, s);
+                              int64_t* status, cudaStream_t s, double2* Tz) {
+  if (prec == REDO_FP64) return grad_sweep_t<double>(t, q, p, Pck, Rck, tau, grad, status, Tz, s);
+  return grad_sweep_t<float>(t, q, p, Pck, Rck, tau, grad, status, Tz, s);
 }
 
 }  // namespace redo

@@ -85,6 +85,34 @@ __global__ void phase_final_kernel(const cplx<R>* __restrict__ X, int N, const d
   }
 }
 
+__global__ void phase_target_kernel(const double2* __restrict__ UT, int batched, int N,
+                                    const double2* __restrict__ zf, double2* __restrict__ out) {
+  const int64_t b = blockIdx.x;
+  const int64_t n2 = (int64_t)N * N;
+  const double2* U = UT + (batched ? b * n2 : 0);
+  for (int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.y * blockDim.x) {
+    const double2 z = zf[b * N + e / N];
+    const double2 u = U[e];
+    out[b * n2 + e] = make_double2(z.x * u.x + z.y * u.y, z.x * u.y - z.y * u.x);   // conj(z) u
+  }
+}
+
+__global__ void phase_grad_finish_kernel(int N, int64_t B, int64_t M, int K, const double2* __restrict__ Tz,
+                                         const double2* __restrict__ tau, double* __restrict__ gphi) {
+  const int64_t total = B * M * K;
+  const double scale = 2.0 / ((double)N * (double)N);
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % K);
+    const int64_t bn = idx / K;
+    const int64_t n = bn % M, b = bn / M;
+    const double2 t1 = Tz[(b * (M + 1) + n + 1) * K + k], t0 = Tz[(b * (M + 1) + n) * K + k];
+    const double dr = t1.x - t0.x, di = t1.y - t0.y;
+    const double2 ta = tau[b];
+    gphi[idx] = scale * (ta.x * di - ta.y * dr);
+  }
+}
+
 unsigned grid_y(int64_t n2) {
   int64_t b = (n2 + 255) / 256;
   if (b > 64) b = 64;
@@ -111,6 +139,23 @@ cudaError_t launch_phase_rows(int N, int prec, void* X, int64_t G, int64_t S, in
     phase_rows_kernel<double><<<grid, 256, 0, s>>>((double2*)X, N, S, sps, i, M, pd);
   else
     phase_rows_kernel<float><<<grid, 256, 0, s>>>((float2*)X, N, S, sps, i, M, pd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_target(int N, int64_t B, const double2* UT, int batched, const double2* zf, double2* out,
+                                cudaStream_t s) {
+  if (B == 0) return cudaSuccess;
+  phase_target_kernel<<<dim3((unsigned)B, grid_y((int64_t)N * N)), 256, 0, s>>>(UT, batched, N, zf, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_grad_finish(int N, int64_t B, int64_t M, int K, const double2* Tz, const double2* tau,
+                                     double* gphi, cudaStream_t s) {
+  const int64_t total = B * M * K;
+  if (total == 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  phase_grad_finish_kernel<<<(unsigned)blocks, 256, 0, s>>>(N, B, M, K, Tz, tau, gphi);
   return cudaGetLastError();
 }
 

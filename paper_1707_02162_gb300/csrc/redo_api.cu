@@ -830,6 +830,100 @@ redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B,
   return REDO_OK;
 }
 
+// Amplitude/phase GRAPE gradient (N <= 64, SIMT): the chain with the step diagonals as
+// factors, against the target Z_{M-1}^dag U_T of the regrouped chain.
+struct PhaseGradLayout {
+  GradLayout g;
+  size_t pd_off, zf_off, ut_off, tz_off, total;
+};
+
+static PhaseGradLayout phase_grad_layout(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                         int32_t checkpoint_every) {
+  PhaseGradLayout L;
+  L.g.p = checkpoint_every > 0 ? plan_chain_aligned(t, B, M, checkpoint_every, true)
+                               : plan_chain(t, B, M, prec, true);
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t el = prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t mats = up((size_t)L.g.p.B * L.g.p.S * t->N * t->N * el);
+  L.g.seg_off = 0;
+  L.g.pck_off = mats;
+  L.g.rck_off = 2 * mats;
+  L.g.tau_off = 3 * mats;
+  L.pd_off = L.g.tau_off + up((size_t)B * sizeof(double2));
+  L.zf_off = L.pd_off + up((size_t)B * M * t->N * sizeof(double2));
+  L.ut_off = L.zf_off + up((size_t)B * t->N * sizeof(double2));
+  L.tz_off = L.ut_off + up((size_t)B * t->N * t->N * sizeof(double2));
+  L.total = L.tz_off + up((size_t)B * (M + 1) * t->K * sizeof(double2));
+  return L;
+}
+
+static redo_status check_phase_grad(const redo_table* t, redo_precision prec) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (!t->sz64) return set_error(REDO_ERR_INVALID, "no phase axes: call redo_table_set_phase_axes first");
+  if (t->strang) return set_error(REDO_ERR_UNSUPPORTED, "amplitude/phase calls on a symmetric-split table");
+  if (t->N > kSmallN) return set_error(REDO_ERR_UNSUPPORTED, "the amplitude/phase gradient needs N <= 64");
+  if (prec != REDO_FP64 && prec != REDO_FP32)
+    return set_error(REDO_ERR_UNSUPPORTED, "the amplitude/phase gradient supports REDO_FP64 and REDO_FP32");
+  return check_prec(t, prec);
+}
+
+redo_status redo_fidelity_grad_phase_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                               int32_t checkpoint_every, size_t* bytes) {
+  if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
+  if (B < 0 || M < 0 || checkpoint_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  redo_status st = check_phase_grad(t, prec);
+  if (st != REDO_OK) return st;
+  if (checkpoint_every > M) checkpoint_every = M > 0 ? (int32_t)M : 0;
+  *bytes = phase_grad_layout(t, B, M, prec, checkpoint_every).total;
+  return REDO_OK;
+}
+
+redo_status redo_fidelity_grad_phase(const redo_table* t, const int32_t* q, const double* phi, int64_t B, int64_t M,
+                                     const void* U_target, int32_t target_batched, redo_precision prec,
+                                     int32_t checkpoint_every, double* F_out, double* grad_amp, double* grad_phase,
+                                     void* workspace, size_t workspace_bytes, int64_t* dev_status, void* stream) {
+  redo_status st = check_phase_grad(t, prec);
+  if (st != REDO_OK) return st;
+  if (B < 0 || M < 0 || checkpoint_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  if (B == 0) return REDO_OK;
+  if (!U_target) return set_error(REDO_ERR_INVALID, "U_target is NULL");
+  if (M > 0 && (!q || !phi || !grad_amp || !grad_phase))
+    return set_error(REDO_ERR_INVALID, "q, phi, grad_amp or grad_phase is NULL");
+  if (checkpoint_every > M) checkpoint_every = M > 0 ? (int32_t)M : 0;
+  PhaseGradLayout L = phase_grad_layout(t, B, M, prec, checkpoint_every);
+  if (!workspace || workspace_bytes < L.total)
+    return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", L.total);
+  if (((uintptr_t)workspace & 255) != 0) return set_error(REDO_ERR_INVALID, "workspace not 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  double2* tau = (double2*)(w + L.g.tau_off);
+  double2* pd = (double2*)(w + L.pd_off);
+  double2* zf = (double2*)(w + L.zf_off);
+  double2* ut = (double2*)(w + L.ut_off);
+  double2* tz = (double2*)(w + L.tz_off);
+  static const double kNoPhase = 0.0;
+  cudaError_t e;
+  ProfScope ps(7, s);
+  if ((e = launch_phase_diag(t, M > 0 ? phi : &kNoPhase, B, M, pd, nullptr, zf, s)) != cudaSuccess)
+    return cuda_error(e, "phase diagonals");
+  if ((e = launch_phase_target(t->N, B, (const double2*)U_target, target_batched, zf, ut, s)) != cudaSuccess)
+    return cuda_error(e, "phase target");
+  L.g.p.pd = pd;
+  if ((e = launch_chain_segments(t, q, L.g.p, prec, w + L.g.seg_off, dev_status, s)) != cudaSuccess)
+    return cuda_error(e, "gradient segments");
+  if ((e = launch_grad_scan(t, B, L.g.p.S, prec, w + L.g.seg_off, ut, 1, w + L.g.pck_off, w + L.g.rck_off, tau,
+                            F_out, s)) != cudaSuccess)
+    return cuda_error(e, "gradient checkpoints");
+  if (M > 0) {
+    if ((e = launch_grad_sweep(t, q, L.g.p, prec, w + L.g.pck_off, w + L.g.rck_off, tau, grad_amp, dev_status, s,
+                               tz)) != cudaSuccess)
+      return cuda_error(e, "gradient sweep");
+    if ((e = launch_phase_grad_finish(t->N, B, M, t->K, tz, tau, grad_phase, s)) != cudaSuccess)
+      return cuda_error(e, "phase gradient");
+  }
+  return REDO_OK;
+}
+
 redo_status redo_simulate_workspace(const redo_table* t, int64_t B, int64_t M,
                                     redo_precision prec, int32_t reunit_every, int32_t want_U,
                                     size_t* bytes) {

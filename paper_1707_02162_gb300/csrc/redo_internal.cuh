@@ -161,9 +161,11 @@ cudaError_t launch_grape_adam(double* u, const double* g, double* m, double* v, 
 cudaError_t launch_grad_scan(const redo_table* t, int64_t B, int64_t S, int prec, const void* seg,
                              const double2* U_target, int target_batched, void* Pck, void* Rck,
                              double2* tau, double* F_out, cudaStream_t s);
+// With p.pd set (amplitude/phase calls) the sweep also records Tz[b][n][k] = Tr(S_kz P R) at
+// every step boundary n = 0..M ([B][M+1][K]).
 cudaError_t launch_grad_sweep(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
                               const void* Pck, const void* Rck, const double2* tau, double* grad,
-                              int64_t* status, cudaStream_t s);
+                              int64_t* status, cudaStream_t s, double2* Tz = nullptr);
 
 // State simulation (kernels_sim.cu).
 cudaError_t launch_state_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
@@ -246,6 +248,12 @@ cudaError_t launch_phase_diag(const redo_table* t, const double* phi, int64_t B,
 // (chains with n >= M untouched); X of precision prec.
 cudaError_t launch_phase_rows(int N, int prec, void* X, int64_t G, int64_t S, int64_t sps, int64_t i,
                               int64_t M, const double2* pd, cudaStream_t s);
+// out_b = diag(conj(zf_b)) U_T (U_T[b] when batched), FP64: the target of the regrouped chain.
+cudaError_t launch_phase_target(int N, int64_t B, const double2* UT, int batched, const double2* zf, double2* out,
+                                cudaStream_t s);
+// gphi[b][n][k] = (2/N^2) Im(conj(tau_b) (Tz[b][n+1][k] - Tz[b][n][k])), n < M.
+cudaError_t launch_phase_grad_finish(int N, int64_t B, int64_t M, int K, const double2* Tz, const double2* tau,
+                                     double* gphi, cudaStream_t s);
 // out_b = diag(zf_b) X_b in FP64 (X of precision prec; out may not alias X unless FP64).
 cudaError_t launch_phase_final(int N, int64_t B, int prec, const void* X, const double2* zf, double2* out,
                                cudaStream_t s);

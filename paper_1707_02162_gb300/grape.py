@@ -5,6 +5,8 @@
   coefficients through libredo's gradient entry point (the derivative of the
   split model at the quantised point; the quantizer is passed straight through).
 * :class:`RedoStateFidelity` -- the same for the state fidelity ``|<psi_T|U|psi0>|^2``.
+* :class:`RedoPhaseFidelity` -- the unitary fidelity of amplitude/phase controls (Section III's
+  {Omega_kn, phi_kn}), differentiable in both amplitudes and phases.
 * :func:`grape` -- the ascent loop: quantise, fidelity + gradient, update in
   place; the table is built once outside the loop as the method prescribes.
   Every step of an iteration runs in libredo kernels; the only host read per
@@ -34,6 +36,25 @@ class RedoStateFidelity(torch.autograd.Function):
     def backward(ctx, grad_F):
         (g,) = ctx.saved_tensors
         return grad_F[:, None, None] * g, None, None, None, None
+
+
+class RedoPhaseFidelity(torch.autograd.Function):
+    """F = |Tr(U_T^dag U(A, phi))|^2 / N^2 for amplitudes A and phases phi of shape [B][M][K]
+    (one x-table per species, the table's phase axes set); gradients in both through libredo's
+    amplitude/phase gradient (the amplitude quantizer is passed straight through)."""
+
+    @staticmethod
+    def forward(ctx, amp, phi, table: redo.Table, target, prec="fp64", checkpoint_every=0):
+        q = table.quantize(amp.detach())
+        F, gA, gP = table.fidelity_grad_phase(q, phi.detach(), target, prec, checkpoint_every)
+        ctx.save_for_backward(gA, gP)
+        return F
+
+    @staticmethod
+    def backward(ctx, grad_F):
+        gA, gP = ctx.saved_tensors
+        w = grad_F[:, None, None]
+        return w * gA, w * gP, None, None, None, None
 
 
 class RedoFidelity(torch.autograd.Function):

@@ -30,7 +30,8 @@ EXPORTS = [
     "redo_grape_step", "redo_simulate", "redo_simulate_workspace", "redo_mlp_sizes", "redo_mlp_forward",
     "redo_mlp_backward", "redo_mlp_adam", "redo_grape_adam_step", "redo_expect_diag",
     "redo_state_grad", "redo_state_grad_workspace", "redo_table_set_phase_axes", "redo_propagate_phase",
-    "redo_propagate_phase_workspace", "redo_batched_product",
+    "redo_propagate_phase_workspace", "redo_batched_product", "redo_fidelity_grad_phase",
+    "redo_fidelity_grad_phase_workspace",
 ]
 PROFILE_PHASES = 11
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -64,6 +65,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_propagate_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_table_set_phase_axes.argtypes = [vp, vp]
     L.redo_batched_product.argtypes = [i32, i64, vp, i32, i32, vp, i32, i32, vp, vp]
+    L.redo_fidelity_grad_phase.argtypes = [vp, vp, vp, i64, i64, vp, i32, i32, i32, vp, vp, vp, vp, ctypes.c_size_t,
+                                           vp, vp]
+    L.redo_fidelity_grad_phase_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_phase.argtypes = [vp, vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_propagate_phase_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_noalloc.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
@@ -430,6 +434,26 @@ def _table_propagate_phase(self, q, phi, prec="fp64", target=None, want_U=True, 
     return U, F, tau
 
 
+def _table_fidelity_grad_phase(self, q, phi, target, prec="fp64", checkpoint_every=0, status=None):
+    """(F [B], dF/dA [B][M][K], dF/dphi [B][M][K]) for amplitude/phase controls."""
+    B, M = q.shape[0], q.shape[1]
+    phi = torch.as_tensor(phi, dtype=torch.float64, device=self.device).contiguous()
+    target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
+    F = torch.empty(B, dtype=torch.float64, device=self.device)
+    gA = torch.empty((B, M, self.K), dtype=torch.float64, device=self.device)
+    gP = torch.empty((B, M, self.K), dtype=torch.float64, device=self.device)
+    n = ctypes.c_size_t()
+    L = load_library()
+    _check(L.redo_fidelity_grad_phase_workspace(ctypes.c_void_p(self.handle), B, M, _prec(prec), checkpoint_every,
+                                                ctypes.byref(n)))
+    ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+    _check(L.redo_fidelity_grad_phase(ctypes.c_void_p(self.handle), _ptr(q), _ptr(phi), B, M, _ptr(target),
+                                      int(target.dim() == 3), _prec(prec), checkpoint_every, _ptr(F), _ptr(gA),
+                                      _ptr(gP), _ptr(ws), ws.numel(), _ptr(status), _stream(None)))
+    return F, gA, gP
+
+
+Table.fidelity_grad_phase = _table_fidelity_grad_phase
 Table.set_phase_axes = _table_set_phase_axes
 Table.propagate_phase = _table_propagate_phase
 

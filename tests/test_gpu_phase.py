@@ -119,3 +119,66 @@ def test_phase_errors():
     ts.set_phase_axes(w.extra["sz"])
     with pytest.raises(redo.RedoError):
         ts.propagate_phase(q, w.extra["phi"], "fp64")
+
+
+@pytest.mark.parametrize("n,B,M,prec,ck,rel", [(3, 2, 12, "fp64", 0, 1e-10), (3, 2, 12, "fp64", 4, 1e-10),
+                                               (3, 2, 12, "fp32", 0, 2e-3), (6, 1, 6, "fp64", 2, 1e-10)])
+def test_phase_gradient_matches_oracle(n, B, M, prec, ck, rel):
+    w = inputs.phase_config(n, B=B, M=M, base=16, digits=2)
+    t = _table(w, fp32=True)
+    q = t.quantize(w.u)
+    F, gA, gP = t.fidelity_grad_phase(q, w.extra["phi"], w.target, prec, checkpoint_every=ck)
+    T, D = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    for b in range(B):
+        Fo, gAo, gPo = O.phase_gradient(T, D, w.Hk, w.extra["sz"], w.dt, dig[b], w.extra["phi"][b], w.target)
+        assert abs(F.cpu().numpy()[b] - Fo) < (1e-12 if prec == "fp64" else 1e-6)
+        assert np.abs(gA.cpu().numpy()[b] - gAo).max() <= rel * np.abs(gAo).max()
+        assert np.abs(gP.cpu().numpy()[b] - gPo).max() <= rel * np.abs(gPo).max()
+
+
+def test_phase_gradient_zero_phase_is_the_x_gradient():
+    w = inputs.phase_config(4, B=2, M=15, base=16, digits=2)
+    t = _table(w, fp32=True)
+    q = t.quantize(w.u)
+    F, gA, _ = t.fidelity_grad_phase(q, np.zeros_like(w.extra["phi"]), w.target, "fp64")
+    F1, g1 = t.fidelity_grad(q, w.target, "fp64")
+    assert (F - F1).abs().max().item() < 1e-13
+    assert (gA - g1).abs().max().item() <= 1e-12 * g1.abs().max().item()
+
+
+def test_phase_gradient_refuses_large_n():
+    from paper_1707_02162_gb300 import redo
+    w = inputs.phase_config(7, B=1, M=2, base=16, digits=2)
+    t = _table(w, fp32=True)
+    q = t.quantize(w.u)
+    with pytest.raises(redo.RedoError):
+        t.fidelity_grad_phase(q, w.extra["phi"], w.target, "fp64")
+
+
+def test_phase_grape_reaches_a_reachable_target():
+    # targets made by other amplitude/phase pulses of the same system; Adam on (A, phi) through
+    # the autograd function
+    from paper_1707_02162_gb300 import grape
+    w = inputs.phase_config(3, B=2, M=30, base=64, digits=2)
+    t = _table(w, fp32=True)
+    rng = np.random.default_rng(9)
+    a_t = torch.tensor(rng.uniform(0, w.hi[0], w.u.shape), device="cuda")
+    p_t = torch.tensor(rng.uniform(0, 2 * np.pi, w.u.shape), device="cuda")
+    targets, _, _ = t.propagate_phase(t.quantize(a_t), p_t, "fp64")
+    amp = torch.tensor(w.u, device="cuda", requires_grad=True)
+    phi = torch.tensor(w.extra["phi"], device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([{"params": [amp], "lr": 0.02 * w.hi[0]}, {"params": [phi], "lr": 0.05}])
+    F0 = None
+    for it in range(300):
+        F = grape.RedoPhaseFidelity.apply(amp, phi, t, targets, "fp64")
+        if F0 is None:
+            F0 = F.detach().clone()
+        opt.zero_grad()
+        (-F.sum()).backward()
+        opt.step()
+        with torch.no_grad():
+            amp.clamp_(float(w.lo[0]), float(w.hi[0]))
+        if F.min().item() > 0.99:
+            break
+    assert F.min().item() > 0.99 > F0.max().item()
