@@ -659,6 +659,28 @@ cudaError_t large_finish_fp32(const redo_table* t, const ChainPlan& p, bool reun
 
 // out[b] = in[2b + 1] in[2b] for b < count (FP32): joins pairs of consecutive sub-segment
 // products (the later one on the left) into segment products.
+// out[h] = Pck[h-1] Rck[h] for the chains h = u S + s with s > 0, Rck[h] for s = 0 (FP32): the
+// costate of a segment carried back by the checkpoint before it, so that a trace against the
+// segment's own partial products (which start from the identity) is a trace against P_f.
+struct CostateShiftOps {
+  const float2* P;
+  const float2* Rc;
+  float2* C;
+  int64_t S, n2;
+  __device__ void get(int64_t h, const float2*& a, const float2*& bb, float2*& c) const {
+    a = (h % S == 0) ? nullptr : P + (h - 1) * n2;
+    bb = Rc + h * n2;
+    c = C + h * n2;
+  }
+};
+
+cudaError_t large_costate_shift_fp32(const float2* Pck, const float2* Rck, float2* out, int64_t G, int64_t S, int N,
+                                     cudaStream_t s) {
+  const int64_t n2 = (int64_t)N * N;
+  CostateShiftOps op{Pck, Rck, out, S, n2};
+  return cgemm<float, false>(op, G, N, 1.0f, 0.0f, s);
+}
+
 cudaError_t large_pair_products_fp32(const float2* in, float2* out, int64_t count, int N, cudaStream_t s) {
   const int64_t n2 = (int64_t)N * N;
   DenseOps<float> op{in + n2, in, out, 2 * n2, 2 * n2, n2};

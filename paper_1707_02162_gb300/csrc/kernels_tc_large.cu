@@ -162,14 +162,14 @@ __global__ void s_from_complex_kernel(const cplx<R>* __restrict__ src, int N, in
 // X from S: mode 0 X = Y^T, mode 2 X = Y.  dst [G][N][N] complex<R>.
 template <typename R>
 __global__ void s_to_complex_kernel(const uint8_t* __restrict__ src, int N, int64_t G, int mode,
-                                    cplx<R>* __restrict__ dst) {
+                                    cplx<R>* __restrict__ dst, size_t stride) {
   const int64_t n2 = (int64_t)N * N;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < G * n2;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = idx / n2;
     const int e = (int)(idx % n2);
     const int i = e / N, j = e % N;
-    const uint8_t* st = src + c * state_bytes(N);
+    const uint8_t* st = src + c * stride;
     const int row = mode == 0 ? j : i, col = mode == 0 ? i : j;
     dst[idx] = cmake<R>((R)s_val(st, N, row, col), (R)s_val(st, N, row, N + col));
   }
@@ -223,7 +223,23 @@ struct SweepArgs {
   const float2* xval;
   double2* acc;           // [gmod][seg_len] trace accumulators
   int64_t* status;
+  // Kept forward states (the gradient with every forward state kept): a forward sweep with
+  // `store` writes the state after step t of chain c to store[c][t] (inputs: buf0 at t = 0,
+  // store[c][t-1] after), and a reverse sweep with `vstore` has R chains only and reads the
+  // trace's V = P^dag as the conjugate of the kept forward state of the same factor.
+  uint8_t* store;
+  const uint8_t* vstore;
 };
+
+__device__ __forceinline__ const uint8_t* state_in(const SweepArgs& a, int64_t c, int64_t t, size_t sb) {
+  if (a.store) return t == 0 ? a.buf0 + c * sb : a.store + ((size_t)c * a.steps + (size_t)(t - 1)) * sb;
+  return ((t & 1) ? a.buf1 : a.buf0) + c * sb;
+}
+
+__device__ __forceinline__ uint8_t* state_out(const SweepArgs& a, int64_t c, int64_t t, size_t sb) {
+  if (a.store) return a.store + ((size_t)c * a.steps + (size_t)t) * sb;
+  return ((t & 1) ? a.buf0 : a.buf1) + c * sb;
+}
 
 struct Unit {
   int64_t t, c;
@@ -238,7 +254,7 @@ __device__ __forceinline__ Unit decode(const SweepArgs& a, int64_t tk, int RT, i
   const int64_t r = tk - u.t * per_step;
   const int64_t ci = r / per_chain;
   // the reverse sweep hands out the units of V chain g and R chain gmod + g together
-  u.c = a.trace ? ((ci & 1) ? a.gmod + (ci >> 1) : (ci >> 1)) : ci;
+  u.c = (a.trace && !a.vstore) ? ((ci & 1) ? a.gmod + (ci >> 1) : (ci >> 1)) : ci;
   const int r2 = (int)(r - ci * per_chain);
   u.rt = r2 / (2 * TNB);
   const int r3 = r2 % (2 * TNB);
@@ -326,7 +342,8 @@ __device__ __forceinline__ void trace_slice(const uint8_t* Vs, const uint8_t* Rs
                                             int stride, int p0, int p1, const int32_t* __restrict__ hk_row,
                                             const int32_t* __restrict__ hk_col,
                                             const double2* __restrict__ hk_val, float* vre, float* vim,
-                                            float* rre, float* rim, int lane, double& sr, double& si) {
+                                            float* rre, float* rim, int lane, bool conjV, double& sr,
+                                            double& si) {
   constexpr int CH = GPL < 2 ? GPL : 2;           // granules per lane held in registers
   constexpr bool kPrefetch = GPL <= 2;
   uint4 vh[CH], vl[CH], rh[CH], rl[CH];
@@ -368,7 +385,7 @@ __device__ __forceinline__ void trace_slice(const uint8_t* Vs, const uint8_t* Rs
       const double2 hv = hk_val[e];
       const float hx = (float)hv.x, hy = (float)hv.y;
       // conj(V[x][cc]) R[x][i]
-      const float va = vre[cc], vb = vim[cc], ra = rre[i], rb = rim[i];
+      const float va = vre[cc], vb = conjV ? -vim[cc] : vim[cc], ra = rre[i], rb = rim[i];
       const float pr = fmaf(va, ra, vb * rb), pi = fmaf(va, rb, -vb * ra);
       tr = fmaf(hx, pr, fmaf(-hy, pi, tr));
       ti = fmaf(hx, pi, fmaf(hy, pr, ti));
@@ -407,7 +424,7 @@ __device__ __forceinline__ void xor_perm8(float (&v)[8], int m7) {
 // time.  FP32 partial sums (tr, ti) stay per lane.
 __device__ __forceinline__ void trace_xor(const uint8_t* Vs, const uint8_t* Rs, int N, int x0, int nrows,
                                           int stride, int m, const float2* __restrict__ hv, int lane,
-                                          float& tr, float& ti) {
+                                          bool conjV, float& tr, float& ti) {
   constexpr int kRB = 2;
   const int NG = N / 8, mq = m >> 3, m7 = m & 7;
   for (int q = lane; q < NG; q += 32) {
@@ -451,6 +468,10 @@ __device__ __forceinline__ void trace_xor(const uint8_t* Vs, const uint8_t* Rs, 
         unpack8(ld[b][2], ld[b][3], ri);
         unpack8(ld[b][4], ld[b][5], vr);
         unpack8(ld[b][6], ld[b][7], vi);
+        if (conjV) {
+#pragma unroll
+          for (int w = 0; w < 8; ++w) vi[w] = -vi[w];
+        }
         xor_perm8(vr, m7);
         xor_perm8(vi, m7);
 #pragma unroll
@@ -573,7 +594,7 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
         if (tk < 0) break;
         if (e < 0) continue;
         fence_proxy_async_global();
-        const uint8_t* Sc = ((u.t & 1) ? a.buf1 : a.buf0) + u.c * sb;
+        const uint8_t* Sc = state_in(a, u.c, u.t, sb);
         bool ok = true;
         for (int kt = 0; kt < KT && ok; ++kt, ++kit) {
           const uint32_t s = kit % kStages;
@@ -680,19 +701,19 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
       ++ui;
       if (m.x < 0) break;
       const Unit u = decode(a, m.x, RT, TNB);
-      const uint8_t* cur = ((u.t & 1) ? a.buf1 : a.buf0);
-      uint8_t* nxt = ((u.t & 1) ? a.buf0 : a.buf1);
+      const uint8_t* cur = state_in(a, u.c, u.t, sb);
+      uint8_t* nxt = state_out(a, u.c, u.t, sb);
       if (a.trace && u.t > 0) {
         // the outputs overwrite the states of step t-1, which that step's traces read
-        const uint32_t target = (uint32_t)(u.t * 4 * TNB);
+        const uint32_t target = (uint32_t)(u.t * (a.vstore ? 2 : 4) * TNB);
         if (threadIdx.x == 0 && !wait_count(&a.tcnt[(u.c % a.gmod) * RT + u.rt], target, a.abort)) fail();
         named_barrier(1, 128);
       }
       const size_t region = ((size_t)u.rt * KT + (size_t)(u.h * N + u.nb * NB) / 64) * kTile;
       if (m.y < 0) {
         // past the end of its segment: carry the region over unchanged
-        const uint4* src = reinterpret_cast<const uint4*>(cur + u.c * sb + region);
-        uint4* dst = reinterpret_cast<uint4*>(nxt + u.c * sb + region);
+        const uint4* src = reinterpret_cast<const uint4*>(cur + region);
+        uint4* dst = reinterpret_cast<uint4*>(nxt + region);
         for (int i = threadIdx.x; i < (int)((NB / 64) * kTile / 16); i += 128) dst[i] = __ldcg(src + i);
       } else {
         const uint32_t b = use % kBufs;
@@ -702,7 +723,7 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
           tc_fence_after();
           const uint32_t d1 = tmem + lane_base + b * Gm::kAcc, d2 = d1 + NB;
           const int R = u.rt * 128 + 32 * warp + lane;
-          uint8_t* out = nxt + u.c * sb;
+          uint8_t* out = nxt;
           const int kc0 = u.h * N + u.nb * NB;
 #pragma unroll 1
           for (int ch = 0; ch < NB / 32; ch += 2) {
@@ -763,7 +784,7 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
       if (m.x < 0) break;
       if (!a.trace) continue;
       const Unit u = decode(a, m.x, RT, TNB);
-      if (m.z >= 0) {
+      if (m.z >= 0 && !a.vstore) {
         // the partner chain's rows of step t are written too (this chain's are: the
         // producer waited for them before handing the unit out)
         const int64_t partner = u.c < a.gmod ? u.c + a.gmod : u.c - a.gmod;
@@ -773,13 +794,21 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
         if (*abort_local) break;
       }
       if (m.z >= 0 && tw < TW) {
-        // this unit's rows of Tr(H_k V^dag R) at step t (V chain g, R chain gmod + g)
+        // this unit's rows of Tr(H_k V^dag R) at step t (V chain g, R chain gmod + g; or the
+        // kept forward state of the same factor as conj(V) and R chain g)
         const uint8_t* cur = ((u.t & 1) ? a.buf1 : a.buf0);
         const int64_t g = u.c % a.gmod;
-        const int li = (u.c >= a.gmod ? 2 * TNB : 0) + u.h * TNB + u.nb;
-        const int rs = 128 / (4 * TNB);
+        const int li = (a.vstore || u.c < a.gmod ? 0 : 2 * TNB) + u.h * TNB + u.nb;
+        const int rs = 128 / ((a.vstore ? 2 : 4) * TNB);
         const uint8_t* Vs = cur + g * sb;
         const uint8_t* Rs = cur + (a.gmod + g) * sb;
+        if (a.vstore) {
+          const int64_t f0 = (g % a.S) * a.seg_len;
+          const int64_t f1 = f0 + a.seg_len < a.F ? f0 + a.seg_len : a.F;
+          Vs = a.vstore + ((size_t)g * a.steps + (size_t)(f1 - f0 - 1 - u.t)) * sb;
+          Rs = cur + g * sb;
+        }
+        const bool conjV = a.vstore != nullptr;
         float* vre = trace_rows + (size_t)tw * 4 * N;
         float* vim = vre + N;
         float* rre = vim + N;
@@ -793,7 +822,7 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
           float tr = 0.0f, ti = 0.0f;
           const float2* hv = a.xval + (size_t)k * N;
           const int mk = a.xmask[k];
-          trace_xor(Vs, Rs, N, x0, nrows, TW, mk, hv, lane, tr, ti);
+          trace_xor(Vs, Rs, N, x0, nrows, TW, mk, hv, lane, conjV, tr, ti);
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) {
             tr += __shfl_xor_sync(0xffffffffu, tr, off);
@@ -804,19 +833,19 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
         } else switch (N) {
           case 128:
             trace_slice<1>(Vs, Rs, N, x0, nrows, TW, p0, p1, a.hk_row, a.hk_col, a.hk_val, vre, vim, rre, rim,
-                           lane, sr, si);
+                           lane, conjV, sr, si);
             break;
           case 256:
             trace_slice<2>(Vs, Rs, N, x0, nrows, TW, p0, p1, a.hk_row, a.hk_col, a.hk_val, vre, vim, rre, rim,
-                           lane, sr, si);
+                           lane, conjV, sr, si);
             break;
           case 512:
             trace_slice<4>(Vs, Rs, N, x0, nrows, TW, p0, p1, a.hk_row, a.hk_col, a.hk_val, vre, vim, rre, rim,
-                           lane, sr, si);
+                           lane, conjV, sr, si);
             break;
           default:
             trace_slice<8>(Vs, Rs, N, x0, nrows, TW, p0, p1, a.hk_row, a.hk_col, a.hk_val, vre, vim, rre, rim,
-                           lane, sr, si);
+                           lane, conjV, sr, si);
             break;
         }
         if (lane == 0) {
@@ -831,7 +860,7 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
       named_barrier(2, 128);
       if (threadIdx.x == 192 && !*abort_local) {
         uint32_t* tc = &a.tcnt[(u.c % a.gmod) * RT + u.rt];
-        if (u.t == 0 || wait_count(tc, (uint32_t)(u.t * 4 * TNB), a.abort)) {
+        if (u.t == 0 || wait_count(tc, (uint32_t)(u.t * (a.vstore ? 2 : 4) * TNB), a.abort)) {
           __threadfence();
           atomicAdd(tc, 1u);
         } else {
@@ -886,7 +915,8 @@ static size_t sync_bytes(int N, int64_t chains) { return up(sync_words(N, chains
 // Runs `p.seg_len` steps of `chains` chains from b0; the result is in b0 (even count) or b1.
 static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan& p, int64_t chains,
                          int reverse, bool trace, const uint8_t* planes, uint8_t* b0, uint8_t* b1,
-                         uint32_t* sync, double2* acc, int64_t* status, cudaStream_t s) {
+                         uint32_t* sync, double2* acc, int64_t* status, cudaStream_t s,
+                         uint8_t* store = nullptr, const uint8_t* vstore = nullptr) {
   const int N = t->N, NB = t->tc_nb, RT = N / 128, TNB = N / NB;
   const int64_t total = p.seg_len * chains * (int64_t)(RT * 2 * TNB);
   if (total == 0) return cudaSuccess;
@@ -907,7 +937,7 @@ static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan&
   a.seg_len = p.seg_len;
   a.F = p.F;
   a.chains = chains;
-  a.gmod = trace ? chains / 2 : chains;
+  a.gmod = (trace && !vstore) ? chains / 2 : chains;
   a.steps = p.seg_len;
   a.reverse = reverse;
   a.trace = trace ? 1 : 0;
@@ -924,6 +954,8 @@ static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan&
   a.xval = t->hk_xval;
   a.acc = acc;
   a.status = status;
+  a.store = store;
+  a.vstore = vstore;
   const size_t smem = sweep_smem(NB, N);
   int64_t grid = total < t->num_sms ? total : t->num_sms;
   if (NB == 256) {
@@ -990,15 +1022,100 @@ cudaError_t tc_large_propagate(const redo_table* t, const int32_t* q, const Chai
   const uint8_t* res = (p.seg_len & 1) ? st1 : st0;
   // segment products X = Y^T into the SIMT path's segment buffer (its first region)
   float2* seg = (float2*)base;
-  s_to_complex_kernel<float><<<blocks_for(G * (int64_t)N * N), 256, 0, s>>>(res, N, G, 0, seg);
+  s_to_complex_kernel<float><<<blocks_for(G * (int64_t)N * N), 256, 0, s>>>(res, N, G, 0, seg, state_bytes(N));
   return large_finish_fp32(t, p, reunit, ws, result, result_prec, s);
 }
 
+// The forward sweep runs on two half segments per checkpoint segment when the segments alone
+// would leave SMs idle.
+static ChainPlan forward_plan(const redo_table* t, const ChainPlan& p) {
+  const int N = t->N;
+  const int64_t units = p.B * p.S * (N / 128) * 2 * (N / t->tc_nb);
+  ChainPlan pf = p;
+  if (units < 3 * (int64_t)t->num_sms && p.seg_len % 2 == 0 && p.seg_len >= 2) {
+    pf.seg_len = p.seg_len / 2;
+    pf.S = 2 * p.S;
+  }
+  return pf;
+}
+
+// Every forward state kept (chains x steps states; one per factor of every pulse) when they
+// fit in kKeepBytes: the reverse sweep then needs no V chains (half its products).
+// REDO_TCL_KEEP=0 selects the V/R form.
+constexpr size_t kKeepBytes = (size_t)24 << 30;
+
+static bool keep_states(const redo_table* t, const ChainPlan& pf) {
+  const char* v = std::getenv("REDO_TCL_KEEP");
+  if (v && v[0] == '0') return false;
+  return (size_t)pf.B * pf.S * pf.seg_len * state_bytes(t->N) <= kKeepBytes;
+}
+
 size_t tc_large_grad_workspace(const redo_table* t, const ChainPlan& p) {
+  const ChainPlan pf = forward_plan(t, p);
+  if (keep_states(t, pf)) {
+    const size_t Gf = (size_t)pf.B * pf.S, n2 = (size_t)t->N * t->N;
+    // SIMT layout over the half segments + 2 Gf states (ping-pong) + kept states + shifted
+    // costates (FP32) + trace accumulators + sweep counters
+    return large_grad_workspace(t, pf, REDO_FP32) + 2 * up(Gf * state_bytes(t->N)) +
+           up(Gf * (size_t)pf.seg_len * state_bytes(t->N)) + up(Gf * n2 * sizeof(float2)) +
+           up(Gf * (size_t)pf.seg_len * sizeof(double2)) + sync_bytes(t->N, Gf);
+  }
   const size_t G = (size_t)p.B * p.S;
   // + 2 x 2G states (V and R, ping-pong) + trace accumulators + sweep counters
   return large_grad_workspace(t, p, REDO_FP32) + 4 * up(G * state_bytes(t->N)) +
          up(G * (size_t)p.seg_len * sizeof(double2)) + sync_bytes(t->N, 2 * G);
+}
+
+// Gradient with every forward state kept: forward sweep of the (half) segment chains writing
+// each step's state to its own slot, FP32 checkpoint/costate scans over those chains, costates
+// carried back by the checkpoint before each chain (the kept states start from the identity),
+// and a reverse sweep of R chains only whose traces read conj(V) = P^T from the kept states.
+static cudaError_t tc_large_grad_keep(const redo_table* t, const int32_t* q, const ChainPlan& pf, const double2* UT,
+                                      int tb, double* F_out, double* grad, void* ws, int64_t* status,
+                                      cudaStream_t s) {
+  const int N = t->N;
+  const int64_t Gf = pf.B * pf.S;
+  const int64_t n2 = (int64_t)N * N;
+  const size_t sb = state_bytes(N);
+  char* base = (char*)ws;
+  const size_t simt = large_grad_workspace(t, pf, REDO_FP32);
+  uint8_t* s0 = (uint8_t*)(base + simt);
+  uint8_t* s1 = s0 + up((size_t)Gf * sb);
+  uint8_t* keep = s1 + up((size_t)Gf * sb);
+  float2* shifted = (float2*)(keep + up((size_t)Gf * pf.seg_len * sb));
+  double2* acc = (double2*)((char*)shifted + up((size_t)Gf * n2 * sizeof(float2)));
+  uint32_t* sync = (uint32_t*)((char*)acc + up((size_t)Gf * pf.seg_len * sizeof(double2)));
+  const uint8_t* rows = (const uint8_t*)t->tc_planes;
+  const uint8_t* cols = rows + (size_t)t->entries * entry_bytes(N);
+  float2* seg = (float2*)base;                 // the SIMT layout's segment region
+  cudaError_t e;
+  {
+    ProfScope ps(8, s);
+    s_identity_kernel<<<blocks_for(Gf * N * (2 * N / 8)), 256, 0, s>>>(s0, N, Gf);
+    if ((e = sweep(t, q, pf, Gf, 0, false, rows, s0, s1, sync, nullptr, status, s, keep, nullptr))) return e;
+    // segment products: each chain's last kept state (the identity when there are no steps)
+    if (pf.seg_len > 0)
+      s_to_complex_kernel<float><<<blocks_for(Gf * n2), 256, 0, s>>>(keep + (size_t)(pf.seg_len - 1) * sb, N, Gf,
+                                                                     0, seg, (size_t)pf.seg_len * sb);
+    else
+      s_to_complex_kernel<float><<<blocks_for(Gf * n2), 256, 0, s>>>(s0, N, Gf, 0, seg, sb);
+  }
+  float2 *Pck = nullptr, *Rck = nullptr;
+  double2* tau = nullptr;
+  {
+    ProfScope ps(9, s);
+    if ((e = large_grad_scans_fp32(t, pf, UT, tb, F_out, ws, &Pck, &Rck, &tau, s))) return e;
+  }
+  if (pf.M == 0) return cudaGetLastError();
+  ProfScope ps(10, s);
+  if ((e = large_costate_shift_fp32(Pck, Rck, shifted, Gf, pf.S, N, s))) return e;
+  s_from_complex_kernel<float><<<blocks_for(Gf * N * (N / 8)), 256, 0, s>>>(shifted, N, Gf, 2, s0);
+  if ((e = cudaMemsetAsync(acc, 0, sizeof(double2) * Gf * pf.seg_len, s))) return e;
+  if ((e = sweep(t, q, pf, Gf, 1, true, cols, s0, s1, sync, acc, status, s, nullptr, keep))) return e;
+  const double scale = 2.0 * t->dt / ((double)N * (double)N);
+  trace_finish_kernel<<<(unsigned)((Gf * pf.seg_len + 255) / 256), 256, 0, s>>>(
+      acc, Gf, pf.S, pf.seg_len, pf.F, t->K, t->digits, tau, scale, pf.M, grad);
+  return cudaGetLastError();
 }
 
 // Gradient: tensor-core forward sweep, SIMT FP32 checkpoint/costate scans, tensor-core
@@ -1006,6 +1123,10 @@ size_t tc_large_grad_workspace(const redo_table* t, const ChainPlan& p) {
 cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, const double2* UT,
                           int tb, double* F_out, double* grad, void* ws, int64_t* status,
                           cudaStream_t s) {
+  {
+    const ChainPlan pf = forward_plan(t, p);
+    if (keep_states(t, pf)) return tc_large_grad_keep(t, q, pf, UT, tb, F_out, grad, ws, status, s);
+  }
   const int N = t->N;
   const int64_t G = p.B * p.S;
   const int64_t n2 = (int64_t)N * N;
@@ -1025,13 +1146,8 @@ cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan
     // With few segments the forward sweep alone cannot keep every SM busy: run it on two
     // half segments per checkpoint segment (the state buffers hold 2G chains) and join
     // each pair with one FP32 product.
-    const int64_t units = G * (N / 128) * 2 * (N / t->tc_nb);
-    const bool split = units < 3 * (int64_t)t->num_sms && p.seg_len % 2 == 0 && p.seg_len >= 2;
-    ChainPlan pf = p;
-    if (split) {
-      pf.seg_len = p.seg_len / 2;
-      pf.S = 2 * p.S;
-    }
+    const ChainPlan pf = forward_plan(t, p);
+    const bool split = pf.S != p.S;
     const int64_t Gf = pf.B * pf.S;
     s_identity_kernel<<<blocks_for(Gf * N * (2 * N / 8)), 256, 0, s>>>(s0, N, Gf);
     if ((e = sweep(t, q, pf, Gf, 0, false, rows, s0, s1, sync, nullptr, status, s))) return e;
@@ -1039,10 +1155,10 @@ cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan
     if (split) {
       // the checkpoint and costate regions (2G matrices, unused until the scans) hold the halves
       float2* halves = (float2*)(base + up((size_t)G * n2 * sizeof(float2)));
-      s_to_complex_kernel<float><<<blocks_for(Gf * n2), 256, 0, s>>>(fin, N, Gf, 0, halves);
+      s_to_complex_kernel<float><<<blocks_for(Gf * n2), 256, 0, s>>>(fin, N, Gf, 0, halves, state_bytes(N));
       if ((e = large_pair_products_fp32(halves, seg, G, N, s))) return e;
     } else {
-      s_to_complex_kernel<float><<<blocks_for(G * n2), 256, 0, s>>>(fin, N, G, 0, seg);
+      s_to_complex_kernel<float><<<blocks_for(G * n2), 256, 0, s>>>(fin, N, G, 0, seg, state_bytes(N));
     }
   }
   float2 *Pck = nullptr, *Rck = nullptr;

@@ -210,6 +210,9 @@ size_t large_sim_workspace(const redo_table* t, int64_t B);
 cudaError_t large_finish_fp32(const redo_table* t, const ChainPlan& p, bool reunit, void* ws,
                               void** result, int* result_prec, cudaStream_t s);
 cudaError_t large_pair_products_fp32(const float2* in, float2* out, int64_t count, int N, cudaStream_t s);
+// out[h] = Pck[h-1] Rck[h] (h mod S > 0), Rck[h] (h mod S = 0), h < G, FP32.
+cudaError_t large_costate_shift_fp32(const float2* Pck, const float2* Rck, float2* out, int64_t G, int64_t S, int N,
+                                     cudaStream_t s);
 cudaError_t large_grad_scans_fp32(const redo_table* t, const ChainPlan& p, const double2* UT, int tb,
                                   double* F_out, void* ws, float2** Pck, float2** Rck, double2** tau,
                                   cudaStream_t s);
