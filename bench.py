@@ -339,7 +339,7 @@ def run_gpu(args):
                  "achieved_tensor_tflops": 3 * gflop / (gres["fp16x3"]["ms_per_iter"] / 1e3) / 1e12,
                  "tensor_frac_of_sustained": (3 * gflop / (gres["fp16x3"]["ms_per_iter"] / 1e3) / 1e12
                                               / peaks.get("bf16_tflops_sustained", 1709.6)),
-                 "algorithmic": "3 complex N x N products per factor (forward, V and R sweeps), 8N^3 flop each, "
+                 "algorithmic": "2 complex N x N products per factor (forward sweep keeping every state, costate sweep), 8N^3 flop each, "
                                 "x3 fp16 products",
                  "phase_ms": gres["fp16x3"].get("phase_ms"),
                  "table_build_s": gbuild}
@@ -444,7 +444,8 @@ def grape_measure(redo, inputs, torch, steps, levels=False, with_fp32=True, with
             res[prec]["phase_ms"] = {k: round(v[0], 3) for k, v in redo.redo_profile_read().items()}
         del ws
     t.close()
-    flop = 3 * w.M * w.K * (1 if levels else w.digits) * 8.0 * w.N ** 3
+    # two complex products per factor: the forward sweep (every state kept) and the costate sweep
+    flop = 2 * w.M * w.K * (1 if levels else w.digits) * 8.0 * w.N ** 3
     return res, flop, build_s, w
 
 

@@ -681,6 +681,33 @@ cudaError_t large_costate_shift_fp32(const float2* Pck, const float2* Rck, float
   return cgemm<float, false>(op, G, N, 1.0f, 0.0f, s);
 }
 
+// Costates of half segments from their segment's shifted costate C_s (h = 2s + i):
+//     out[2s+1] = H[2s] C_s,   out[2s] = C_s H[2s+1]   (FP32),
+// H the half-segment products: the later half sees the earlier half as part of its prefix,
+// the earlier half sees the later one as part of its suffix.
+struct HalfCostateOps {
+  const float2* H;
+  const float2* Cs;
+  float2* C;
+  int64_t n2;
+  __device__ void get(int64_t h, const float2*& a, const float2*& bb, float2*& c) const {
+    if (h & 1) {
+      a = H + (h - 1) * n2;
+      bb = Cs + (h >> 1) * n2;
+    } else {
+      a = Cs + (h >> 1) * n2;
+      bb = H + (h + 1) * n2;
+    }
+    c = C + h * n2;
+  }
+};
+
+cudaError_t large_half_costates_fp32(const float2* H, const float2* Cs, float2* out, int64_t Gf, int N,
+                                     cudaStream_t s) {
+  HalfCostateOps op{H, Cs, out, (int64_t)N * N};
+  return cgemm<float, false>(op, Gf, N, 1.0f, 0.0f, s);
+}
+
 cudaError_t large_pair_products_fp32(const float2* in, float2* out, int64_t count, int N, cudaStream_t s) {
   const int64_t n2 = (int64_t)N * N;
   DenseOps<float> op{in + n2, in, out, 2 * n2, 2 * n2, n2};

@@ -1053,12 +1053,13 @@ static bool keep_states(const redo_table* t, const ChainPlan& pf) {
 size_t tc_large_grad_workspace(const redo_table* t, const ChainPlan& p) {
   const ChainPlan pf = forward_plan(t, p);
   if (keep_states(t, pf)) {
-    const size_t Gf = (size_t)pf.B * pf.S, n2 = (size_t)t->N * t->N;
-    // SIMT layout over the half segments + 2 Gf states (ping-pong) + kept states + shifted
-    // costates (FP32) + trace accumulators + sweep counters
-    return large_grad_workspace(t, pf, REDO_FP32) + 2 * up(Gf * state_bytes(t->N)) +
-           up(Gf * (size_t)pf.seg_len * state_bytes(t->N)) + up(Gf * n2 * sizeof(float2)) +
-           up(Gf * (size_t)pf.seg_len * sizeof(double2)) + sync_bytes(t->N, Gf);
+    const size_t G = (size_t)p.B * p.S, Gf = (size_t)pf.B * pf.S, n2 = (size_t)t->N * t->N;
+    // SIMT layout over the segments + 2 Gf states (ping-pong) + kept states + half-segment
+    // products and costates (FP32, Gf each) + segment costates (G) + trace accumulators +
+    // sweep counters
+    return large_grad_workspace(t, p, REDO_FP32) + 2 * up(Gf * state_bytes(t->N)) +
+           up(Gf * (size_t)pf.seg_len * state_bytes(t->N)) + 2 * up(Gf * n2 * sizeof(float2)) +
+           up(G * n2 * sizeof(float2)) + up(Gf * (size_t)pf.seg_len * sizeof(double2)) + sync_bytes(t->N, Gf);
   }
   const size_t G = (size_t)p.B * p.S;
   // + 2 x 2G states (V and R, ping-pong) + trace accumulators + sweep counters
@@ -1067,23 +1068,27 @@ size_t tc_large_grad_workspace(const redo_table* t, const ChainPlan& p) {
 }
 
 // Gradient with every forward state kept: forward sweep of the (half) segment chains writing
-// each step's state to its own slot, FP32 checkpoint/costate scans over those chains, costates
-// carried back by the checkpoint before each chain (the kept states start from the identity),
-// and a reverse sweep of R chains only whose traces read conj(V) = P^T from the kept states.
-static cudaError_t tc_large_grad_keep(const redo_table* t, const int32_t* q, const ChainPlan& pf, const double2* UT,
-                                      int tb, double* F_out, double* grad, void* ws, int64_t* status,
-                                      cudaStream_t s) {
+// each step's state to its own slot; the segment products (halves joined in pairs) go through
+// the FP32 checkpoint/costate scans; every chain's costate is carried back by the product
+// before it (the kept states start from the identity at the chain's start); a reverse sweep
+// of R chains only then reads conj(V) = P^T for its traces from the kept states.
+static cudaError_t tc_large_grad_keep(const redo_table* t, const int32_t* q, const ChainPlan& p,
+                                      const ChainPlan& pf, const double2* UT, int tb, double* F_out, double* grad,
+                                      void* ws, int64_t* status, cudaStream_t s) {
   const int N = t->N;
-  const int64_t Gf = pf.B * pf.S;
+  const int64_t G = p.B * p.S, Gf = pf.B * pf.S;
+  const bool split = Gf != G;
   const int64_t n2 = (int64_t)N * N;
   const size_t sb = state_bytes(N);
   char* base = (char*)ws;
-  const size_t simt = large_grad_workspace(t, pf, REDO_FP32);
+  const size_t simt = large_grad_workspace(t, p, REDO_FP32);
   uint8_t* s0 = (uint8_t*)(base + simt);
   uint8_t* s1 = s0 + up((size_t)Gf * sb);
   uint8_t* keep = s1 + up((size_t)Gf * sb);
-  float2* shifted = (float2*)(keep + up((size_t)Gf * pf.seg_len * sb));
-  double2* acc = (double2*)((char*)shifted + up((size_t)Gf * n2 * sizeof(float2)));
+  float2* halves = (float2*)(keep + up((size_t)Gf * pf.seg_len * sb));
+  float2* chain_costates = (float2*)((char*)halves + up((size_t)Gf * n2 * sizeof(float2)));
+  float2* seg_costates = (float2*)((char*)chain_costates + up((size_t)Gf * n2 * sizeof(float2)));
+  double2* acc = (double2*)((char*)seg_costates + up((size_t)G * n2 * sizeof(float2)));
   uint32_t* sync = (uint32_t*)((char*)acc + up((size_t)Gf * pf.seg_len * sizeof(double2)));
   const uint8_t* rows = (const uint8_t*)t->tc_planes;
   const uint8_t* cols = rows + (size_t)t->entries * entry_bytes(N);
@@ -1093,23 +1098,30 @@ static cudaError_t tc_large_grad_keep(const redo_table* t, const int32_t* q, con
     ProfScope ps(8, s);
     s_identity_kernel<<<blocks_for(Gf * N * (2 * N / 8)), 256, 0, s>>>(s0, N, Gf);
     if ((e = sweep(t, q, pf, Gf, 0, false, rows, s0, s1, sync, nullptr, status, s, keep, nullptr))) return e;
-    // segment products: each chain's last kept state (the identity when there are no steps)
+    // chain products: each chain's last kept state (the identity when there are no steps)
+    float2* prods = split ? halves : seg;
     if (pf.seg_len > 0)
       s_to_complex_kernel<float><<<blocks_for(Gf * n2), 256, 0, s>>>(keep + (size_t)(pf.seg_len - 1) * sb, N, Gf,
-                                                                     0, seg, (size_t)pf.seg_len * sb);
+                                                                     0, prods, (size_t)pf.seg_len * sb);
     else
-      s_to_complex_kernel<float><<<blocks_for(Gf * n2), 256, 0, s>>>(s0, N, Gf, 0, seg, sb);
+      s_to_complex_kernel<float><<<blocks_for(Gf * n2), 256, 0, s>>>(s0, N, Gf, 0, prods, sb);
+    if (split && (e = large_pair_products_fp32(halves, seg, G, N, s))) return e;
   }
   float2 *Pck = nullptr, *Rck = nullptr;
   double2* tau = nullptr;
   {
     ProfScope ps(9, s);
-    if ((e = large_grad_scans_fp32(t, pf, UT, tb, F_out, ws, &Pck, &Rck, &tau, s))) return e;
+    if ((e = large_grad_scans_fp32(t, p, UT, tb, F_out, ws, &Pck, &Rck, &tau, s))) return e;
   }
-  if (pf.M == 0) return cudaGetLastError();
+  if (p.M == 0) return cudaGetLastError();
   ProfScope ps(10, s);
-  if ((e = large_costate_shift_fp32(Pck, Rck, shifted, Gf, pf.S, N, s))) return e;
-  s_from_complex_kernel<float><<<blocks_for(Gf * N * (N / 8)), 256, 0, s>>>(shifted, N, Gf, 2, s0);
+  if (split) {
+    if ((e = large_costate_shift_fp32(Pck, Rck, seg_costates, G, p.S, N, s))) return e;
+    if ((e = large_half_costates_fp32(halves, seg_costates, chain_costates, Gf, N, s))) return e;
+  } else if ((e = large_costate_shift_fp32(Pck, Rck, chain_costates, G, p.S, N, s))) {
+    return e;
+  }
+  s_from_complex_kernel<float><<<blocks_for(Gf * N * (N / 8)), 256, 0, s>>>(chain_costates, N, Gf, 2, s0);
   if ((e = cudaMemsetAsync(acc, 0, sizeof(double2) * Gf * pf.seg_len, s))) return e;
   if ((e = sweep(t, q, pf, Gf, 1, true, cols, s0, s1, sync, acc, status, s, nullptr, keep))) return e;
   const double scale = 2.0 * t->dt / ((double)N * (double)N);
@@ -1118,14 +1130,12 @@ static cudaError_t tc_large_grad_keep(const redo_table* t, const int32_t* q, con
   return cudaGetLastError();
 }
 
-// Gradient: tensor-core forward sweep, SIMT FP32 checkpoint/costate scans, tensor-core
-// reverse sweep of (V = P^dag, R) with the traces evaluated inside the sweep.
 cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, const double2* UT,
                           int tb, double* F_out, double* grad, void* ws, int64_t* status,
                           cudaStream_t s) {
   {
     const ChainPlan pf = forward_plan(t, p);
-    if (keep_states(t, pf)) return tc_large_grad_keep(t, q, pf, UT, tb, F_out, grad, ws, status, s);
+    if (keep_states(t, pf)) return tc_large_grad_keep(t, q, p, pf, UT, tb, F_out, grad, ws, status, s);
   }
   const int N = t->N;
   const int64_t G = p.B * p.S;

@@ -213,6 +213,9 @@ cudaError_t large_pair_products_fp32(const float2* in, float2* out, int64_t coun
 // out[h] = Pck[h-1] Rck[h] (h mod S > 0), Rck[h] (h mod S = 0), h < G, FP32.
 cudaError_t large_costate_shift_fp32(const float2* Pck, const float2* Rck, float2* out, int64_t G, int64_t S, int N,
                                      cudaStream_t s);
+// out[2s+1] = H[2s] Cs[s], out[2s] = Cs[s] H[2s+1], for 2s+1 < Gf (FP32).
+cudaError_t large_half_costates_fp32(const float2* H, const float2* Cs, float2* out, int64_t Gf, int N,
+                                     cudaStream_t s);
 cudaError_t large_grad_scans_fp32(const redo_table* t, const ChainPlan& p, const double2* UT, int tb,
                                   double* F_out, void* ws, float2** Pck, float2** Rck, double2** tau,
                                   cudaStream_t s);
