@@ -242,11 +242,106 @@ expect_diag_kernel(const cplx<R>* __restrict__ T, const int32_t* __restrict__ q,
   if (tid == 0 && mean) mean[b] = M > 0 ? acc / (double)M : e0;
 }
 
+// Small N (<= 16) with a table that fits in shared memory: the whole table is staged once per
+// CTA and every thread carries one column of one pulse's U_n in registers, so a CTA of 256
+// threads serves 256/N pulses with no barrier inside the chain:
+//     column c:  u <- T_f u  (N^2 complex FMAs per factor, T_f read from shared memory),
+//     e_n = sum_c rho_c sum_r o_r |U_n[r][c]|^2 (the columns' parts added by shuffles within the
+// pulse's N lanes; the mean needs only each lane's running sum).
+constexpr int kColThreads = 256;
+
+template <typename R, int N>
+__global__ void __launch_bounds__(kColThreads, 2)
+expect_cols_kernel(const cplx<R>* __restrict__ T, int64_t entries, const int32_t* __restrict__ q, int64_t B,
+                   int64_t M, int K, int d, int base, int64_t levels, const double* __restrict__ rho,
+                   const double* __restrict__ obs, double* __restrict__ expect, double* __restrict__ mean,
+                   int64_t* status) {
+  constexpr int N2 = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* Ts = reinterpret_cast<cplx<R>*>(smem_raw);
+  for (int64_t i = threadIdx.x; i < entries * N2; i += kColThreads) Ts[i] = T[i];
+  __syncthreads();
+  const int c = threadIdx.x % N;
+  const int64_t b_raw = (int64_t)blockIdx.x * (kColThreads / N) + threadIdx.x / N;
+  const bool active = b_raw < B;
+  const int64_t b = active ? b_raw : B - 1;        // idle lanes follow the last pulse, write nothing
+  R o[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) o[r] = (R)obs[r];
+  const double rc = rho[c];
+  cplx<R> u[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) u[r] = cmake<R>(r == c ? R(1) : R(0), R(0));
+  auto part = [&]() -> double {
+    R v = R(0);
+#pragma unroll
+    for (int r = 0; r < N; ++r) v = fma(o[r], fma(u[r].x, u[r].x, u[r].y * u[r].y), v);
+    return rc * (double)v;
+  };
+  auto group_sum = [&](double v) -> double {
+#pragma unroll
+    for (int off = N / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, N);
+    return v;
+  };
+  const double e0 = group_sum(part());
+  if (expect && active && c == 0) expect[b * (M + 1)] = e0;
+  double acc = 0.0;
+  const int32_t* qb = q + b * M * K;
+  int32_t qn = M > 0 ? qb[0] : 0;
+  for (int64_t n = 0; n < M; ++n) {
+    const int32_t* qrow = qb + n * K;
+    for (int k = 0; k < K; ++k) {
+      int32_t qv = qn;
+      // next coefficient's level, loaded while this one is applied
+      qn = (k + 1 < K) ? qrow[k + 1] : (n + 1 < M ? qrow[K] : 0);
+      if (qv < 0 || qv >= levels) {
+        if (status && active) atomicAdd((unsigned long long*)&status[REDO_STATUS_BADINDEX], 1ull);
+        qv = 0;
+      }
+      for (int j = 0; j < d; ++j) {
+        const cplx<R>* A = Ts + ((int64_t)(k * d + j) * base + qv % base) * N2;
+        qv /= base;
+        cplx<R> v[N];
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+          cplx<R> sacc = cmake<R>(R(0), R(0));
+#pragma unroll
+          for (int kk = 0; kk < N; ++kk) cfma<R>(sacc, A[r * N + kk], u[kk]);
+          v[r] = sacc;
+        }
+#pragma unroll
+        for (int r = 0; r < N; ++r) u[r] = v[r];
+      }
+    }
+    const double pv = part();
+    acc += pv;
+    if (expect) {
+      const double ev = group_sum(pv);
+      if (active && c == 0) expect[b * (M + 1) + n + 1] = ev;
+    }
+  }
+  const double tot = group_sum(acc);
+  if (mean && active && c == 0) mean[b] = M > 0 ? tot / (double)M : e0;
+}
+
 template <typename R, int N>
 static cudaError_t expect_diag_n(const redo_table* t, const int32_t* q, int64_t B, int64_t M, const double* rho,
                                  const double* obs, double* expect, double* mean, int64_t* status,
                                  cudaStream_t s) {
   const cplx<R>* T = std::is_same<R, double>::value ? (const cplx<R>*)t->T64 : (const cplx<R>*)t->T32;
+  if constexpr (N * sizeof(R) <= 64) {            // one column in registers: N <= 16 (FP32), 8 (FP64)
+    const size_t table_smem = (size_t)t->entries * N * N * sizeof(cplx<R>);
+    // worth it once every SM gets a full CTA (256 / N pulses); fewer pulses keep one CTA each
+    if (table_smem <= 200 * 1024 && B * N >= (int64_t)t->num_sms * kColThreads) {
+      cudaError_t e = cudaFuncSetAttribute(expect_cols_kernel<R, N>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table_smem);
+      if (e != cudaSuccess) return e;
+      const int64_t per = kColThreads / N;
+      expect_cols_kernel<R, N><<<(unsigned)((B + per - 1) / per), kColThreads, table_smem, s>>>(
+          T, t->entries, q, B, M, t->K, t->digits, t->base, t->levels, rho, obs, expect, mean, status);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = 3 * sizeof(cplx<R>) * N * N;
   cudaError_t e = cudaFuncSetAttribute(expect_diag_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);

@@ -57,22 +57,28 @@ def test_freezing_at_first_bessel_root_gpu():
     assert Q[1] > 0.99 and Q[1] > Q[0] + 0.1 and Q[1] > Q[2] + 0.1
 
 
-@pytest.mark.parametrize("n", [1, 4])
-def test_expect_diag_random_diagonals(n):
-    # generic diagonal rho and O on the x/y-controlled ZZ system, N = 2 and 16
+@pytest.mark.parametrize("n,B,prec,tol", [(1, 3, "fp64", 1e-12), (4, 3, "fp64", 1e-12), (4, 3, "fp32", 2e-5),
+                                         (1, 19461, "fp32", 2e-5), (3, 4870, "fp64", 1e-12),
+                                         (3, 4870, "fp32", 2e-5), (4, 2450, "fp32", 2e-5)])
+def test_expect_diag_random_diagonals(n, B, prec, tol):
+    # generic diagonal rho and O on the x/y-controlled ZZ system, N = 2 .. 16; the large batches
+    # take the column-per-thread kernel (N <= 16 in FP32, <= 8 in FP64; at least one CTA of
+    # 256 / N pulses per SM) with idle lanes in its last CTA, the small ones the CTA-per-pulse
+    # kernel
     from paper_1707_02162_gb300 import redo
-    w = inputs.config(0, n_qubits=n, B=3, M=25, base=16, digits=2)
+    w = inputs.config(0, n_qubits=n, B=B, M=25, base=16, digits=2)
     rng = np.random.default_rng(9)
     rho, obs = rng.uniform(-1, 1, w.N), rng.uniform(-1, 1, w.N)
-    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits)
-    ex, mean = t.expect_diag(t.quantize(w.u), rho, obs, "fp64")
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+    ex, mean = t.expect_diag(t.quantize(w.u), rho, obs, prec)
     To, Do = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
     qo, _, _ = O.quantize(w.u, w.lo, w.hi, w.levels)
     dig = O.level_digits(qo, w.base, w.digits)
-    for b in range(w.B):
+    for b in sorted({0, 1, w.B // 2, w.B - 2, w.B - 1}):
         Tf = To.copy()
         eo, _ = O.expect_mixed(Tf, Do, dig[b], np.diag(rho).astype(complex), np.diag(obs).astype(complex))
-        assert np.abs(ex.cpu().numpy()[b] - eo).max() < 1e-12
+        assert np.abs(ex.cpu().numpy()[b] - eo).max() < tol
+        assert abs(mean.cpu().numpy()[b] - eo[1:].mean()) < tol
 
 
 def test_expect_diag_rejects_unsupported():
