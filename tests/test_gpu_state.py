@@ -64,6 +64,18 @@ def test_state_grad_n64():
     _check(_reduced(1, 6, 2, 2, 8), "fp64", 1e-11)
 
 
+@pytest.mark.parametrize("n,prec,rel,batched", [(6, "fp32", 1e-3, False), (7, "fp32", 1e-3, True),
+                                                (7, "fp64", 1e-11, True), (9, "fp32", 1e-3, True)])
+def test_state_grad_streamed_sizes(n, prec, rel, batched):
+    # N = 64, 128 (four row groups per chunk in the reverse pass), 512 (one column per thread)
+    _check(_reduced(3, n, 1, 2, 3, base=4, digits=2), prec, rel, batched=batched)
+
+
+def test_state_grad_n1024_two_columns_per_thread():
+    # N = 1024: two columns per thread in the reverse pass, eight rows per 64 KB chunk, two stages
+    _check(_reduced(3, 10, 1, 1, 2, base=2, digits=2), "fp32", 1e-3)
+
+
 @pytest.mark.parametrize("prec,rel", [("fp64", 1e-10), ("fp32", 1e-3)])
 def test_state_grad_n256_level_table(prec, rel):
     _check(_reduced(2, 8, 2, 1, 5), prec, rel, levels=True)
