@@ -159,7 +159,8 @@ state_grad_stream_kernel(const cplx<R>* __restrict__ T, const int32_t* __restric
                          const double2* __restrict__ psiT, int batched, const int32_t* __restrict__ hk_ptr,
                          const int32_t* __restrict__ hk_col, const int32_t* __restrict__ hk_row,
                          const double2* __restrict__ hk_val, double dt, double* __restrict__ F_out,
-                         double* __restrict__ grad, int64_t* status, int stages, int rows) {
+                         double* __restrict__ grad, int64_t* status, int stages, int rows,
+                         const double* __restrict__ obs, double* __restrict__ expect) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint8_t* ring = smem_raw;
   cplx<R>* v = reinterpret_cast<cplx<R>*>(ring + (size_t)stages * kSgChunk);
@@ -179,7 +180,7 @@ state_grad_stream_kernel(const cplx<R>* __restrict__ T, const int32_t* __restric
   const int passes = grad ? 2 : 1;
   const int64_t total = (int64_t)passes * F * cpf;
   const double2* p0 = psi0 + (batched ? b * N : 0);
-  const double2* pT = psiT + (batched ? b * N : 0);
+  const double2* pT = psiT ? psiT + (batched ? b * N : 0) : nullptr;
   if (tid == 0) {
     for (int i = 0; i < stages; ++i) {
       mbar_init(&full[i], 1);
@@ -250,6 +251,17 @@ state_grad_stream_kernel(const cplx<R>* __restrict__ T, const int32_t* __restric
     for (int i = 0; i < kSgWarps; ++i) o += red[i];
     return o;
   };
+  // simulation (expect non-null): <O>(t_n) = sum_a o_a |psi_n[a]|^2 after every step
+  auto observe = [&](int64_t n) {
+    double x = 0.0;
+    for (int i = tid; i < N; i += kSgCompute) {
+      const double vr = (double)v[i].x, vi = (double)v[i].y;
+      x += obs[i] * (vr * vr + vi * vi);
+    }
+    x = block_sum(x);
+    if (tid == 0) expect[b * (M + 1) + n] = x;
+  };
+  if (expect) observe(0);
   // forward: v <- A_f v
   for (int64_t f = 0; f < F; ++f) {
     for (int ch = 0; ch < cpf; ++ch) {
@@ -272,6 +284,7 @@ state_grad_stream_kernel(const cplx<R>* __restrict__ T, const int32_t* __restric
     cplx<R>* x = v;
     v = tv;
     tv = x;
+    if (expect && (f + 1) % kd == 0) observe((f + 1) / kd);
   }
   if (!ok) {
     if (tid == 0) {
@@ -280,6 +293,7 @@ state_grad_stream_kernel(const cplx<R>* __restrict__ T, const int32_t* __restric
     }
     return;
   }
+  if (!pT) return;                                  // simulation: no target state
   // a = <psi_T | v>
   double ar = 0.0, ai = 0.0;
   for (int i = tid; i < N; i += kSgCompute) {
@@ -380,7 +394,8 @@ state_grad_stream_kernel(const cplx<R>* __restrict__ T, const int32_t* __restric
 template <typename R>
 static cudaError_t launch_state_stream(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
                                        const double2* psi0, const double2* psiT, int batched, double* F_out,
-                                       double* grad, int64_t* status, cudaStream_t s) {
+                                       double* grad, int64_t* status, cudaStream_t s, const double* obs = nullptr,
+                                       double* expect = nullptr) {
   const int N = t->N;
   const size_t el = sizeof(cplx<R>);
   int rows = (int)(kSgChunk / (N * el));
@@ -396,8 +411,19 @@ static cudaError_t launch_state_stream(const redo_table* t, const int32_t* q, in
   state_grad_stream_kernel<R><<<(unsigned)B, kSgThreads, smem, s>>>(
       std::is_same<R, double>::value ? (const cplx<R>*)t->T64 : (const cplx<R>*)t->T32, q, N, M, t->K, t->digits,
       t->base, t->levels, psi0, psiT, batched, t->hk_ptr, t->hk_col, t->hk_row, t->hk_val, t->dt, F_out, grad,
-      status, stages, rows);
+      status, stages, rows, obs, expect);
   return cudaGetLastError();
+}
+
+cudaError_t launch_sim_stream(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
+                              const double2* psi0, int psi0_batched, const double* obs, double* expect,
+                              int64_t* status, cudaStream_t s) {
+  if (B == 0) return cudaSuccess;
+  return prec == REDO_FP64
+             ? launch_state_stream<double>(t, q, B, M, psi0, nullptr, psi0_batched, nullptr, nullptr, status, s, obs,
+                                           expect)
+             : launch_state_stream<float>(t, q, B, M, psi0, nullptr, psi0_batched, nullptr, nullptr, status, s, obs,
+                                          expect);
 }
 
 cudaError_t launch_state_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,

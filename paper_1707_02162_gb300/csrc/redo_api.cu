@@ -930,7 +930,8 @@ redo_status redo_simulate_workspace(const redo_table* t, int64_t B, int64_t M,
   if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
   redo_status st = check_prec(t, prec);
   if (st != REDO_OK) return st;
-  size_t state = t->N > kSmallN ? large_sim_workspace(t, B) : 0;
+  // the lockstep state simulation (N > 64 with fewer pulses than SMs) needs two state vectors
+  size_t state = t->N > kSmallN && B < t->num_sms ? large_sim_workspace(t, B) : 0;
   if (t->strang) state += ((size_t)B * t->N * sizeof(double2) + 255) & ~(size_t)255;   // D_h^dag psi0
   size_t prop = 0;
   if (want_U) {
@@ -962,7 +963,8 @@ redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int6
   {
     ProfScope ps(2, s);
     cudaError_t e;
-    const size_t need_state = t->N > kSmallN ? large_sim_workspace(t, B) : 0;
+    const bool lockstep = t->N > kSmallN && B < t->num_sms;
+    const size_t need_state = lockstep ? large_sim_workspace(t, B) : 0;
     if (t->strang) {
       // symmetric split with a diagonal drift and observable: the symmetric states give the
       // same expectations as the folded chain started from D_h^dag psi0
@@ -974,12 +976,16 @@ redo_status redo_simulate(const redo_table* t, const int32_t* q, int64_t B, int6
         return cuda_error(e, "half-drift of the initial state");
       psi0 = pw;
     }
-    if (t->N > kSmallN) {
-      const size_t need = need_state;
-      if (!workspace || workspace_bytes < need)
-        return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", need);
+    if (lockstep) {
+      // fewer pulses than SMs: every SM works on every step (one launch per factor)
+      if (!workspace || workspace_bytes < need_state)
+        return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", need_state);
       e = large_sim(t, q, B, M, prec == REDO_FP64 ? REDO_FP64 : REDO_FP32, (const double2*)psi0,
                     psi0_batched, obs_diag, expect, workspace, s);
+    } else if (t->N > kSmallN) {
+      // a pulse per CTA, its operators streamed through shared memory
+      e = launch_sim_stream(t, q, B, M, prec == REDO_FP64 ? REDO_FP64 : REDO_FP32, (const double2*)psi0,
+                            psi0_batched, obs_diag, expect, dev_status, s);
     } else {
       e = launch_sim_state(t, q, B, M, prec == REDO_FP64 ? REDO_FP64 : REDO_FP32,
                            (const double2*)psi0, psi0_batched, obs_diag, expect, dev_status, s);

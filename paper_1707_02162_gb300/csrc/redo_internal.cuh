@@ -171,6 +171,11 @@ cudaError_t launch_grad_sweep(const redo_table* t, const int32_t* q, const Chain
 cudaError_t launch_state_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
                               const double2* psi0, const double2* psiT, int batched, double* F_out, double* grad,
                               int64_t* status, cudaStream_t s);
+// <O>(t_n) of psi_n = U_n ... U_1 psi0 for N >= 64, one CTA per pulse streaming the operators
+// (the forward sweep of the state-transfer kernel); expect [B][M+1].
+cudaError_t launch_sim_stream(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
+                              const double2* psi0, int psi0_batched, const double* obs, double* expect,
+                              int64_t* status, cudaStream_t s);
 cudaError_t launch_levels_closed_form(const redo_table* t, const int32_t* xm, const double2* xh, const double* xa,
                                       double2* E, cudaStream_t s);
 cudaError_t launch_expect_diag(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
@@ -207,6 +212,9 @@ cudaError_t large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p
                        const double2* UT, int tb, double* F_out, double* grad, void* ws,
                        int64_t* status, cudaStream_t s);
 size_t large_sim_workspace(const redo_table* t, int64_t B);
+cudaError_t large_sim(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
+                      const double2* psi0, int pb, const double* obs, double* expect, void* ws,
+                      cudaStream_t s);
 cudaError_t large_finish_fp32(const redo_table* t, const ChainPlan& p, bool reunit, void* ws,
                               void** result, int* result_prec, cudaStream_t s);
 cudaError_t large_pair_products_fp32(const float2* in, float2* out, int64_t count, int N, cudaStream_t s);
@@ -231,9 +239,6 @@ size_t tc_large_grad_workspace(const redo_table* t, const ChainPlan& p);
 cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, const double2* UT,
                           int tb, double* F_out, double* grad, void* ws, int64_t* status,
                           cudaStream_t s);
-cudaError_t large_sim(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
-                      const double2* psi0, int pb, const double* obs, double* expect, void* ws,
-                      cudaStream_t s);
 
 // out_b = A X_b A^dag (adjoint = 0) or A^dag X_b A (adjoint = 1), A = the table's half
 // drift, FP64 out (may be X itself); X_b of precision `prec` (REDO_FP64 or REDO_FP32).

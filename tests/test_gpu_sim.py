@@ -26,8 +26,10 @@ def _table(w, fp16x3=False):
 
 
 @pytest.mark.parametrize("n,prec,tol", [(4, "fp64", 1e-12), (4, "fp32", 2e-5), (6, "fp64", 1e-12),
-                                        (3, "fp64", 1e-12)])
+                                        (3, "fp64", 1e-12), (7, "fp64", 5e-12), (7, "fp32", 2e-5)])
 def test_noisy_drive_expectation_matches_oracle(n, prec, tol):
+    # N = 128 (streamed states): its FP64 table comes from the large-N Taylor build, ~1e-14 per
+    # operator from the oracle's Pade table, and the 240 factors of a pulse add that up linearly
     w = inputs.config(3, B=3, M=120, n_qubits=n)      # OU-noise drive, Z on qubit 0, psi0 = |0...0>
     t = _table(w)
     st = torch.zeros(4, dtype=torch.int64, device="cuda")
@@ -87,3 +89,18 @@ def test_final_propagator_with_tensor_cores_n6():
     eo, Uo = O.simulate_expectation(T, D, dig[0], w.psi0, w.obs_diag)
     assert np.abs(U.cpu().numpy()[0] - Uo).max() < 2e-4
     assert np.abs(ex.cpu().numpy()[0] - eo).max() < 2e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_streamed_simulation_many_pulses(prec, tol):
+    # at least one pulse per SM takes the streamed path (a pulse per CTA, operators through
+    # shared memory); fewer take the lockstep path tested above
+    w = inputs.config(3, B=160, M=12, n_qubits=7)
+    t = _table(w)
+    q = t.quantize(w.u)
+    ex, _ = t.simulate(q, w.psi0, w.obs_diag, prec, want_U=False)
+    T, D = _ref.oracle_table(w)
+    _, dig, _, _ = _ref.oracle_levels(w)
+    for b in (0, 77, 159):
+        eo, _ = O.simulate_expectation(T, D, dig[b], w.psi0, w.obs_diag)
+        assert np.abs(ex.cpu().numpy()[b] - eo).max() < tol
