@@ -425,7 +425,8 @@ redo_status redo_propagate_phase_workspace(const redo_table* t, int64_t B, int64
  * factors as in redo_fidelity_grad, and dF/dphi_kn = (2/N^2) Im(conj(tau) (Tz_{n+1,k} - Tz_{n,k}))
  * with Tz_{n,k} = Tr(S_kz W_n) at the step boundaries (W_n the product of the chain after the
  * boundary, the transformed target and the chain before it).
- * N <= 64, REDO_FP64 or REDO_FP32; REDO_ERR_UNSUPPORTED otherwise.  Workspace from
+ * REDO_FP64 or REDO_FP32 at every N (for N > 64 on segments of whole steps: checkpoint_every is
+ * then the segment length in steps); REDO_ERR_UNSUPPORTED otherwise.  Workspace from
  * redo_fidelity_grad_phase_workspace.
  */
 redo_status redo_fidelity_grad_phase(const redo_table* t, const int32_t* q, const double* phi, int64_t B, int64_t M,

@@ -989,7 +989,7 @@ cudaError_t large_grad_scans_fp32(const redo_table* t, const ChainPlan& p, const
 template <typename R>
 static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
                                 const double2* UT, int tb, double* F_out, double* grad, char* ws,
-                                int64_t* status, cudaStream_t s) {
+                                int64_t* status, cudaStream_t s, double2* Tz, double* grad_phase) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int N = t->N;
   const int64_t n2 = (int64_t)N * N, G = p.B * p.S;
@@ -1028,6 +1028,11 @@ static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const Cha
   cplx<R>* Rr = Rck;
   cplx<R>* Rn = pB;
   const double scale = 2.0 * t->dt / ((double)N * (double)N);
+  const int prec = std::is_same<R, double>::value ? REDO_FP64 : REDO_FP32;
+  const int64_t kd = (int64_t)t->K * t->digits;
+  if (p.pd && (e = launch_phase_boundary(N, prec, P, Rr, G, p.S, p.seg_len, p.F, -1, kd, p.M, p.pd, t->sz64,
+                                         t->K, Tz, s)))
+    return e;
   for (int64_t tt = 0; tt < p.seg_len; ++tt) {
     trace_kernel<R><<<(unsigned)G, 256, 0, s>>>(P, Rr, N, p.S, p.seg_len, p.F, tt, t->K, t->digits,
                                                 t->hk_ptr, t->hk_col, t->hk_row, t->hk_val, tau, scale, p.M,
@@ -1042,16 +1047,22 @@ static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const Cha
     if ((e = cgemm<R, false>(right, G, N, R(1), R(0), s))) return e;
     std::swap(P, Pn);
     std::swap(Rr, Rn);
+    // the factor just undone opened its step: record the boundary trace, undo the diagonal
+    if (p.pd && (tt + 1) % kd == 0 &&
+        (e = launch_phase_boundary(N, prec, P, Rr, G, p.S, p.seg_len, p.F, tt, kd, p.M, p.pd, t->sz64, t->K, Tz,
+                                   s)))
+      return e;
   }
+  if (p.pd && (e = launch_phase_grad_finish(N, p.B, p.M, t->K, Tz, tau, grad_phase, s))) return e;
   return cudaGetLastError();
 }
 
 cudaError_t large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
                        const double2* UT, int tb, double* F_out, double* grad, void* ws,
-                       int64_t* status, cudaStream_t s) {
+                       int64_t* status, cudaStream_t s, double2* Tz, double* grad_phase) {
   if (prec == REDO_FP64)
-    return large_grad_t<double>(t, q, p, UT, tb, F_out, grad, (char*)ws, status, s);
-  return large_grad_t<float>(t, q, p, UT, tb, F_out, grad, (char*)ws, status, s);
+    return large_grad_t<double>(t, q, p, UT, tb, F_out, grad, (char*)ws, status, s, Tz, grad_phase);
+  return large_grad_t<float>(t, q, p, UT, tb, F_out, grad, (char*)ws, status, s, Tz, grad_phase);
 }
 
 // ============================================================================

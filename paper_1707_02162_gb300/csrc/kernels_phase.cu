@@ -113,6 +113,85 @@ __global__ void phase_grad_finish_kernel(int N, int64_t B, int64_t M, int K, con
   }
 }
 
+// Reverse sweeps of the large-N gradient (segments of whole steps, every chain at the same
+// offset tt from its end): the chain's factor f = f1 - 1 - tt.  With tt = -1 the chain end itself
+// (f = f1), a step boundary only for the last segment.
+__device__ __forceinline__ int64_t boundary_factor(int64_t g, int64_t S, int64_t seg_len, int64_t F, int64_t tt,
+                                                   int64_t* f0_out) {
+  const int64_t sg = g % S;
+  const int64_t f0 = sg * seg_len;
+  const int64_t f1 = f0 + seg_len < F ? f0 + seg_len : F;
+  *f0_out = f0;
+  return f1 - 1 - tt;
+}
+
+// Tz[u][n][k] = sum_a sz[k][a] (P R)[a][a] at the boundary n = f / kd of every chain g = u S + s
+// whose factor f opens step n (or, with tt = -1, at the end of the last segment: n = M).
+template <typename R>
+__global__ void __launch_bounds__(256) phase_boundary_tz_kernel(const cplx<R>* __restrict__ P,
+                                                                const cplx<R>* __restrict__ Rm, int N, int64_t S,
+                                                                int64_t seg_len, int64_t F, int64_t tt, int64_t kd,
+                                                                int64_t M, const double* __restrict__ sz, int K,
+                                                                double2* __restrict__ Tz) {
+  __shared__ double2 dg[1024];
+  const int64_t g = blockIdx.x;
+  int64_t f0;
+  const int64_t f = boundary_factor(g, S, seg_len, F, tt, &f0);
+  if (tt < 0 ? f != F : (f < f0 || f % kd != 0)) return;
+  const int64_t n = f / kd;
+  const int64_t u = g / S;
+  const int64_t n2 = (int64_t)N * N;
+  const cplx<R>* Pg = P + g * n2;
+  const cplx<R>* Rg = Rm + g * n2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int a = warp; a < N; a += 8) {
+    double re = 0.0, im = 0.0;
+    for (int x = lane; x < N; x += 32) {
+      const cplx<R> pv = Pg[(int64_t)a * N + x], rv = Rg[(int64_t)x * N + a];
+      re += (double)pv.x * rv.x - (double)pv.y * rv.y;
+      im += (double)pv.x * rv.y + (double)pv.y * rv.x;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, off);
+      im += __shfl_xor_sync(0xffffffffu, im, off);
+    }
+    if (lane == 0) dg[a] = make_double2(re, im);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int a = 0; a < N; ++a) {
+      const double w = sz[(int64_t)k * N + a];
+      re += w * dg[a].x;
+      im += w * dg[a].y;
+    }
+    Tz[(u * (M + 1) + n) * K + k] = make_double2(re, im);
+  }
+}
+
+// Undo the step-opening diagonal P_n of every chain at a boundary: P <- diag(p_n)^dag P,
+// R <- R diag(p_n).
+template <typename R>
+__global__ void phase_undo_kernel(cplx<R>* __restrict__ P, cplx<R>* __restrict__ Rm, int N, int64_t S,
+                                  int64_t seg_len, int64_t F, int64_t tt, int64_t kd, int64_t M,
+                                  const double2* __restrict__ pd) {
+  const int64_t g = blockIdx.x;
+  int64_t f0;
+  const int64_t f = boundary_factor(g, S, seg_len, F, tt, &f0);
+  if (f < f0 || f % kd != 0) return;
+  const int64_t n = f / kd, u = g / S;
+  const int64_t n2 = (int64_t)N * N;
+  const double2* p = pd + (u * M + n) * N;
+  cplx<R>* Pg = P + g * n2;
+  cplx<R>* Rg = Rm + g * n2;
+  for (int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.y * blockDim.x) {
+    const double2 pr = p[e / N], pc = p[e % N];
+    const cplx<R> x = Pg[e], y = Rg[e];
+    Pg[e] = cmake<R>((R)(pr.x * (double)x.x + pr.y * (double)x.y), (R)(pr.x * (double)x.y - pr.y * (double)x.x));
+    Rg[e] = cmake<R>((R)(pc.x * (double)y.x - pc.y * (double)y.y), (R)(pc.x * (double)y.y + pc.y * (double)y.x));
+  }
+}
+
 unsigned grid_y(int64_t n2) {
   int64_t b = (n2 + 255) / 256;
   if (b > 64) b = 64;
@@ -156,6 +235,26 @@ cudaError_t launch_phase_grad_finish(int N, int64_t B, int64_t M, int K, const d
   int64_t blocks = (total + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   phase_grad_finish_kernel<<<(unsigned)blocks, 256, 0, s>>>(N, B, M, K, Tz, tau, gphi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_boundary(int N, int prec, void* P, void* Rm, int64_t G, int64_t S, int64_t seg_len,
+                                  int64_t F, int64_t tt, int64_t kd, int64_t M, const double2* pd, const double* sz,
+                                  int K, double2* Tz, cudaStream_t s) {
+  if (G == 0) return cudaSuccess;
+  if (prec == REDO_FP64) {
+    phase_boundary_tz_kernel<double><<<(unsigned)G, 256, 0, s>>>((const double2*)P, (const double2*)Rm, N, S,
+                                                                  seg_len, F, tt, kd, M, sz, K, Tz);
+    if (tt >= 0)
+      phase_undo_kernel<double><<<dim3((unsigned)G, grid_y((int64_t)N * N)), 256, 0, s>>>(
+          (double2*)P, (double2*)Rm, N, S, seg_len, F, tt, kd, M, pd);
+  } else {
+    phase_boundary_tz_kernel<float><<<(unsigned)G, 256, 0, s>>>((const float2*)P, (const float2*)Rm, N, S,
+                                                                 seg_len, F, tt, kd, M, sz, K, Tz);
+    if (tt >= 0)
+      phase_undo_kernel<float><<<dim3((unsigned)G, grid_y((int64_t)N * N)), 256, 0, s>>>(
+          (float2*)P, (float2*)Rm, N, S, seg_len, F, tt, kd, M, pd);
+  }
   return cudaGetLastError();
 }
 

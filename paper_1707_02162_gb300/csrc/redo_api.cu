@@ -840,16 +840,29 @@ struct PhaseGradLayout {
 static PhaseGradLayout phase_grad_layout(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
                                          int32_t checkpoint_every) {
   PhaseGradLayout L;
-  L.g.p = checkpoint_every > 0 ? plan_chain_aligned(t, B, M, checkpoint_every, true)
-                               : plan_chain(t, B, M, prec, true);
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t el = prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
-  const size_t mats = up((size_t)L.g.p.B * L.g.p.S * t->N * t->N * el);
-  L.g.seg_off = 0;
-  L.g.pck_off = mats;
-  L.g.rck_off = 2 * mats;
-  L.g.tau_off = 3 * mats;
-  L.pd_off = L.g.tau_off + up((size_t)B * sizeof(double2));
+  if (t->N > kSmallN) {
+    // lockstep SIMT sweeps on segments of whole steps (the diagonals fall between launches)
+    const int64_t kd = (int64_t)t->K * t->digits;
+    int64_t sps = checkpoint_every;
+    if (sps <= 0) {
+      const ChainPlan p0 = plan_chain_large(t, B, M);
+      sps = p0.seg_len > 0 ? (p0.seg_len + kd - 1) / kd : 1;
+    }
+    L.g.p = plan_chain_aligned(t, B, M, sps);
+    L.g.seg_off = L.g.pck_off = L.g.rck_off = L.g.tau_off = 0;
+    L.pd_off = up(large_grad_workspace(t, L.g.p, prec));
+  } else {
+    L.g.p = checkpoint_every > 0 ? plan_chain_aligned(t, B, M, checkpoint_every, true)
+                                 : plan_chain(t, B, M, prec, true);
+    const size_t el = prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t mats = up((size_t)L.g.p.B * L.g.p.S * t->N * t->N * el);
+    L.g.seg_off = 0;
+    L.g.pck_off = mats;
+    L.g.rck_off = 2 * mats;
+    L.g.tau_off = 3 * mats;
+    L.pd_off = L.g.tau_off + up((size_t)B * sizeof(double2));
+  }
   L.zf_off = L.pd_off + up((size_t)B * M * t->N * sizeof(double2));
   L.ut_off = L.zf_off + up((size_t)B * t->N * sizeof(double2));
   L.tz_off = L.ut_off + up((size_t)B * t->N * t->N * sizeof(double2));
@@ -861,7 +874,6 @@ static redo_status check_phase_grad(const redo_table* t, redo_precision prec) {
   if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
   if (!t->sz64) return set_error(REDO_ERR_INVALID, "no phase axes: call redo_table_set_phase_axes first");
   if (t->strang) return set_error(REDO_ERR_UNSUPPORTED, "amplitude/phase calls on a symmetric-split table");
-  if (t->N > kSmallN) return set_error(REDO_ERR_UNSUPPORTED, "the amplitude/phase gradient needs N <= 64");
   if (prec != REDO_FP64 && prec != REDO_FP32)
     return set_error(REDO_ERR_UNSUPPORTED, "the amplitude/phase gradient supports REDO_FP64 and REDO_FP32");
   return check_prec(t, prec);
@@ -909,6 +921,12 @@ redo_status redo_fidelity_grad_phase(const redo_table* t, const int32_t* q, cons
   if ((e = launch_phase_target(t->N, B, (const double2*)U_target, target_batched, zf, ut, s)) != cudaSuccess)
     return cuda_error(e, "phase target");
   L.g.p.pd = pd;
+  if (t->N > kSmallN) {
+    if ((e = large_grad(t, q, L.g.p, prec, ut, 1, F_out, grad_amp, workspace, dev_status, s, tz, grad_phase)) !=
+        cudaSuccess)
+      return cuda_error(e, "large-N phase gradient");
+    return REDO_OK;
+  }
   if ((e = launch_chain_segments(t, q, L.g.p, prec, w + L.g.seg_off, dev_status, s)) != cudaSuccess)
     return cuda_error(e, "gradient segments");
   if ((e = launch_grad_scan(t, B, L.g.p.S, prec, w + L.g.seg_off, ut, 1, w + L.g.pck_off, w + L.g.rck_off, tau,

@@ -208,9 +208,11 @@ cudaError_t large_propagate(const redo_table* t, const int32_t* q, const ChainPl
                             bool reunit, void* ws, void** result, int* result_prec,
                             int64_t* status, cudaStream_t s);
 size_t large_grad_workspace(const redo_table* t, const ChainPlan& p, int prec);
+// With p.pd set (amplitude/phase calls, segments of whole steps) the reverse sweep also records
+// Tz [B][M+1][K] at the step boundaries and undoes the step diagonals.
 cudaError_t large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
                        const double2* UT, int tb, double* F_out, double* grad, void* ws,
-                       int64_t* status, cudaStream_t s);
+                       int64_t* status, cudaStream_t s, double2* Tz = nullptr, double* grad_phase = nullptr);
 size_t large_sim_workspace(const redo_table* t, int64_t B);
 cudaError_t large_sim(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
                       const double2* psi0, int pb, const double* obs, double* expect, void* ws,
@@ -265,6 +267,12 @@ cudaError_t launch_phase_target(int N, int64_t B, const double2* UT, int batched
 // gphi[b][n][k] = (2/N^2) Im(conj(tau_b) (Tz[b][n+1][k] - Tz[b][n][k])), n < M.
 cudaError_t launch_phase_grad_finish(int N, int64_t B, int64_t M, int K, const double2* Tz, const double2* tau,
                                      double* gphi, cudaStream_t s);
+// Reverse sweep of the large-N phase gradient at offset tt from every chain's end (segments of
+// whole steps): where the chain's factor opens step n, record Tz[u][n][k] = Tr(S_kz P R) and undo
+// P_n (P <- P_n^dag P, R <- R P_n); tt = -1 records Tz[u][M] at the end of the last segment.
+cudaError_t launch_phase_boundary(int N, int prec, void* P, void* Rm, int64_t G, int64_t S, int64_t seg_len,
+                                  int64_t F, int64_t tt, int64_t kd, int64_t M, const double2* pd, const double* sz,
+                                  int K, double2* Tz, cudaStream_t s);
 // out_b = diag(zf_b) X_b in FP64 (X of precision prec; out may not alias X unless FP64).
 cudaError_t launch_phase_final(int N, int64_t B, int prec, const void* X, const double2* zf, double2* out,
                                cudaStream_t s);

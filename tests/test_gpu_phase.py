@@ -122,7 +122,9 @@ def test_phase_errors():
 
 
 @pytest.mark.parametrize("n,B,M,prec,ck,rel", [(3, 2, 12, "fp64", 0, 1e-10), (3, 2, 12, "fp64", 4, 1e-10),
-                                               (3, 2, 12, "fp32", 0, 2e-3), (6, 1, 6, "fp64", 2, 1e-10)])
+                                               (3, 2, 12, "fp32", 0, 2e-3), (6, 1, 6, "fp64", 2, 1e-10),
+                                               (7, 2, 5, "fp64", 0, 1e-10), (7, 1, 5, "fp64", 2, 1e-10),
+                                               (7, 1, 5, "fp32", 0, 2e-3)])
 def test_phase_gradient_matches_oracle(n, B, M, prec, ck, rel):
     w = inputs.phase_config(n, B=B, M=M, base=16, digits=2)
     t = _table(w, fp32=True)
@@ -147,13 +149,13 @@ def test_phase_gradient_zero_phase_is_the_x_gradient():
     assert (gA - g1).abs().max().item() <= 1e-12 * g1.abs().max().item()
 
 
-def test_phase_gradient_refuses_large_n():
+def test_phase_gradient_refuses_split_fp16():
     from paper_1707_02162_gb300 import redo
     w = inputs.phase_config(7, B=1, M=2, base=16, digits=2)
-    t = _table(w, fp32=True)
+    t = _table(w, fp32=True, fp16x3=True)
     q = t.quantize(w.u)
     with pytest.raises(redo.RedoError):
-        t.fidelity_grad_phase(q, w.extra["phi"], w.target, "fp64")
+        t.fidelity_grad_phase(q, w.extra["phi"], w.target, "fp16x3")
 
 
 def test_phase_grape_reaches_a_reachable_target():
