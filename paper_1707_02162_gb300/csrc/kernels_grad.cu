@@ -155,7 +155,8 @@ __device__ __forceinline__ const cplx<R>* grad_factor(const GradArgs<R>& a, int6
   return a.T + ((int64_t)(k * a.d + j) * a.base + qv % a.base) * (N * N);
 }
 
-template <typename R, int N>
+// PH: amplitude/phase call (a.pd non-null: step-opening diagonal factors and boundary traces).
+template <typename R, int N, bool PH>
 __global__ void __launch_bounds__(SmemMM<R, N, SqTile<N>::TM, SqTile<N>::TM>::THREADS)
 grad_sweep_kernel(GradArgs<R> a) {
   constexpr int TM = SqTile<N>::TM;
@@ -227,14 +228,14 @@ grad_sweep_kernel(GradArgs<R> a) {
     }
     __syncthreads();
   };
-  if (a.pd && len > 0 && f1 == a.F) phase_traces(a.M);   // end of the chain
+  if (PH && len > 0 && f1 == a.F) phase_traces(a.M);     // end of the chain
   cplx<R> Y1[TM][TM], Y2[TM][TM];
   for (int64_t t = 0; t < len; ++t) {
     const int64_t f = f1 - 1 - t;
     const int64_t n = f / a.fps;
     int r = (int)(f - n * a.fps);
-    const bool phase = a.pd && r == 0;
-    if (a.pd) --r;
+    const bool phase = PH && r == 0;
+    if (PH) --r;
     const int k = r / a.d, j = r - k * a.d;
     if (phase) phase_traces(n);
     if (!phase && j == a.d - 1) {
@@ -278,7 +279,7 @@ grad_sweep_kernel(GradArgs<R> a) {
     __syncthreads();
     if (abort_flag) break;
     const cplx<R>* A = Abuf + stage * N2;
-    if (phase) {
+    if (PH && phase) {
       // P <- diag(p)^dag P (rows), R <- R diag(p) (columns)
       const double2* pv = a.pd + (b * a.M + n) * N;
       const int ty = lt / MM::TX, tx = lt % MM::TX;
@@ -287,10 +288,10 @@ grad_sweep_kernel(GradArgs<R> a) {
 #pragma unroll
         for (int v = 0; v < TM; ++v) {
           const int row = ty + MM::TY * u, col = tx + MM::TX * v;
-          const double2 pr = pv[row], pc = pv[col];
+          const R prx = (R)pv[row].x, pry = (R)pv[row].y, pcx = (R)pv[col].x, pcy = (R)pv[col].y;
           const cplx<R> x = P[row * N + col], y = Rm[row * N + col];
-          Y1[u][v] = cmake<R>((R)(pr.x * (double)x.x + pr.y * (double)x.y), (R)(pr.x * (double)x.y - pr.y * (double)x.x));
-          Y2[u][v] = cmake<R>((R)(pc.x * (double)y.x - pc.y * (double)y.y), (R)(pc.x * (double)y.y + pc.y * (double)y.x));
+          Y1[u][v] = cmake<R>(prx * x.x + pry * x.y, prx * x.y - pry * x.x);
+          Y2[u][v] = cmake<R>(pcx * y.x - pcy * y.y, pcx * y.y + pcy * y.x);
         }
     } else {
       MM::run_adj(A, P, lt, Y1);     // P <- A^dag P
@@ -328,7 +329,7 @@ static cudaError_t grad_sweep_n(const GradArgs<R>& a, int64_t B, cudaStream_t s)
   using MM = SmemMM<R, N, SqTile<N>::TM, SqTile<N>::TM>;
   constexpr int STAGES = (sizeof(R) == 8 && N == 64) ? 1 : 2;
   const size_t smem = (2 + STAGES) * sizeof(cplx<R>) * N * N + 2 * sizeof(uint64_t);
-  auto kern = grad_sweep_kernel<R, N>;
+  auto kern = a.pd ? grad_sweep_kernel<R, N, true> : grad_sweep_kernel<R, N, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t blocks = B * a.S;

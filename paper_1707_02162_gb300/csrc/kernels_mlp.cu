@@ -1,11 +1,23 @@
 // Multilayer perceptron for the learned warm start of GRAPE: forward,
-// backward (mean-squared error) and Adam, FP32 master weights, FP32 SIMT.
+// backward (mean-squared error) and Adam, FP32 master weights.
 //
 // Network: h_0 = x; z_l = h_l W_l^T + b_l; h_{l+1} = GELU(z_l) for hidden
 // layers (exact erf form) and tanh(z_l) for the output layer, whose entries are
 // normalised pulse amplitudes in [-1, 1].  Parameters are one flat array with
 // W_l (out x in, row-major) followed by b_l (out) for every layer.
+//
+// The GEMMs run on the tensor cores (tcgen05, kind::f16 with BF16 operands): every FP32
+// operand value is split as hi = bf16(v), lo = bf16(v - hi) and a product takes
+// hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory (about 16 significant bits
+// per operand, the FP32 exponent range).  A CTA computes one 128 x 128 tile of C: its threads
+// stage 64-wide K slices of A and B (any strides, converted and split on the way) into
+// 128-byte-swizzled K-major tiles, one thread issues the MMAs of a slice while the next slice
+// is staged, and eight warps read the accumulator back for the bias and activation.
+#include <cuda_bf16.h>
+
 #include "redo_internal.cuh"
+#include "device_sync.cuh"
+#include "tcgen05.cuh"
 
 namespace redo {
 
@@ -33,56 +45,146 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
   return Phi + x * phi;
 }
 
-constexpr int kGT = 64, kGK = 16;
+constexpr int kMT = 128, kNT = 128, kKT = 64;                 // C tile, K slice (bf16)
+constexpr uint32_t kMPlane = kMT * kKT * 2;                      // 16 KB: 128 rows x 64 bf16
+constexpr uint32_t kMStage = 4 * kMPlane;                        // A hi, A lo, B hi, B lo
+constexpr uint32_t kMSmem = 2 * kMStage + 1024 + 64;
+constexpr uint32_t kMLimit = 1u << 24;
+// kind::f16 instruction descriptor: D f32, A and B bf16, K-major, N = 128, M = 128
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kNT >> 3) << 17) |
+                                ((uint32_t)(kMT >> 4) << 24);
 
-__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
-  __shared__ float As[kGK][kGT + 1];
-  __shared__ float Bs[kGK][kGT + 1];
-  const int tid = threadIdx.x;
-  const int tx = tid % 16, ty = tid / 16;
-  const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < g.K; k0 += kGK) {
-    for (int e = tid; e < kGT * kGK; e += 256) {
-      const int ii = e / kGK, kk = e % kGK;
-      const int i = i0 + ii, k = k0 + kk;
-      As[kk][ii] = (i < g.M && k < g.K) ? g.A[i * g.sa0 + k * g.sa1] : 0.f;
-      const int jj = e % kGT, kb = e / kGT;
-      const int j = j0 + jj, k2 = k0 + kb;
-      Bs[kb][jj] = (j < g.N && k2 < g.K) ? g.B[k2 * g.sb0 + j * g.sb1] : 0.f;
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Stage a 128-row x 64-K tile of a strided operand (element (r, k) at X[r * s_r + k * s_k],
+// zero outside rows x K) into hi / lo planes; groups of 8 consecutive k per thread, threads
+// laid along whichever index is contiguous in memory.
+__device__ __forceinline__ void stage_tile(const float* __restrict__ X, int64_t s_r, int64_t s_k, int rows, int K,
+                                           int r0, int k0, uint8_t* hi, uint8_t* lo, int tid) {
+  const bool kfast = s_k == 1;
+  for (int idx = tid; idx < kMT * (kKT / 8); idx += 256) {
+    const int r = kfast ? idx / (kKT / 8) : idx % kMT;
+    const int g = kfast ? idx % (kKT / 8) : idx / kMT;
+    const int rr = r0 + r;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      float v[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int k = k0 + 8 * g + 2 * p + q;
+        v[q] = (rr < rows && k < K) ? X[(int64_t)rr * s_r + (int64_t)k * s_k] : 0.f;
+      }
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]), h1 = __float2bfloat16_rn(v[1]);
+      h[p] = pack_bf16(h0, h1);
+      l[p] = pack_bf16(__float2bfloat16_rn(v[0] - __bfloat162float(h0)),
+                       __float2bfloat16_rn(v[1] - __bfloat162float(h1)));
     }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kGK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
-    }
-    __syncthreads();
+    const uint32_t o = tc::sw128((uint32_t)r, (uint32_t)(8 * g), kMT);
+    *reinterpret_cast<uint4*>(hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
   }
+}
+
+__global__ void __launch_bounds__(256, 1) gemm_tc_kernel(GemmArgs g, int64_t* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* done = reinterpret_cast<uint64_t*>(smem + 2 * kMStage);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = blockIdx.y * kMT, j0 = blockIdx.x * kNT;
+  if (tid == 0) {
+    mbar_init(&done[0], 1);
+    mbar_init(&done[1], 1);
+    *abort_flag = 0;
+    fence_mbarrier_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, kNT);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int nk = (g.K + kKT - 1) / kKT;
+  bool ok = true;
+  int issued = 0;                                   // slices whose MMAs were committed
+  for (int kt = 0; kt < nk; ++kt) {
+    const int st = kt & 1;
+    uint8_t* base = smem + st * kMStage;
+    // the MMAs that read this stage two slices ago are done
+    if (kt >= 2 && !mbar_wait_bounded_n(&done[st], (uint32_t)(((kt - 2) >> 1) & 1), kMLimit)) ok = false;
+    ok = __syncthreads_and(ok && !*abort_flag);
+    if (!ok) break;
+    stage_tile(g.A, g.sa0, g.sa1, g.M, g.K, i0, kt * kKT, base, base + kMPlane, tid);
+    stage_tile(g.B, g.sb1, g.sb0, g.N, g.K, j0, kt * kKT, base + 2 * kMPlane, base + 3 * kMPlane, tid);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::tc_fence_after();
+      const uint32_t a_hi = smem_u32(base), a_lo = a_hi + kMPlane;
+      const uint32_t b_hi = a_hi + 2 * kMPlane, b_lo = a_hi + 3 * kMPlane;
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+      for (int kk = 0; kk < kKT / 16; ++kk) {
+        const uint32_t o = (uint32_t)kk * 32u;
+        tc::mma_f16(tmem, tc::smem_desc_sw128(a_hi + o), tc::smem_desc_sw128(b_hi + o), kIdescBf16,
+                    (kt | kk) ? 1u : 0u);
+        tc::mma_f16(tmem, tc::smem_desc_sw128(a_hi + o), tc::smem_desc_sw128(b_lo + o), kIdescBf16, 1u);
+        tc::mma_f16(tmem, tc::smem_desc_sw128(a_lo + o), tc::smem_desc_sw128(b_hi + o), kIdescBf16, 1u);
+      }
+      tc::mma_commit(&done[st]);
+    }
+    ++issued;
+  }
+  // the last committed slice's MMAs (and with them every earlier one) are done
+  if (issued > 0) {
+    const int last = issued - 1;
+    if (!mbar_wait_bounded_n(&done[last & 1], (uint32_t)((last >> 1) & 1), kMLimit)) ok = false;
+  }
+  ok = __syncthreads_and(ok);
+  tc::tc_fence_after();
+  if (!ok) {
+    if (tid == 0 && status) atomicAdd((unsigned long long*)&status[REDO_STATUS_TIMEOUT], 1ull);
+  } else {
+    // warp w: accumulator rows 32 (w mod 4) + lane, columns 64 (w / 4) .. + 63
+    const int q = warp & 3, hcol = warp >> 2;
+    const int i = i0 + 32 * q + lane;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
-      if (i < g.M && j < g.N) {
-        float v = acc[r][c] + (g.bias ? g.bias[j] : 0.f);
-        g.C[(int64_t)i * g.ldc + j] = v;
-        if (g.Cact) g.Cact[(int64_t)i * g.ldc + j] = g.act == 1 ? gelu_f(v) : (g.act == 2 ? tanhf(v) : v);
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      uint32_t r[32];
+      const int jb = 64 * hcol + c0;
+      if (nk > 0) {
+        tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)jb, r);
+        tc::tmem_wait_ld();
+      } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) r[c] = 0u;
+      }
+      if (i < g.M) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int j = j0 + jb + c;
+          if (j < g.N) {
+            const float v = __uint_as_float(r[c]) + (g.bias ? g.bias[j] : 0.f);
+            g.C[(int64_t)i * g.ldc + j] = v;
+            if (g.Cact) g.Cact[(int64_t)i * g.ldc + j] = g.act == 1 ? gelu_f(v) : (g.act == 2 ? tanhf(v) : v);
+          }
+        }
       }
     }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kNT);
 }
 
 static cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
   if (g.M == 0 || g.N == 0) return cudaSuccess;
-  dim3 grid((g.N + kGT - 1) / kGT, (g.M + kGT - 1) / kGT);
-  gemm_kernel<<<grid, 256, 0, s>>>(g);
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMSmem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.N + kNT - 1) / kNT, (g.M + kMT - 1) / kMT);
+  gemm_tc_kernel<<<grid, 256, kMSmem, s>>>(g, nullptr);
   return cudaGetLastError();
 }
 
