@@ -264,11 +264,11 @@ def run_gpu(args):
                 "achieved": achieved_tf}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom_name
-    # DRAM bytes (read + write) of one full-size launch of chain_tc3_kernel<2,4> with the level
-    # table, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/
+    # DRAM bytes (read + write) of one full-size launch of chain_tc3_kernel<2,4,false> with the
+    # level table, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/
     # chain_tc_fp16x3_n64.md); only valid for that kernel and configuration.
     full_size = (B, M) == (B_FULL, M_FULL)
-    roof["traffic"] = (190010190080 + 342801152) if (MAIN_PREC == "fp16x3" and args.levels and full_size
+    roof["traffic"] = (190015116032 + 376372480) if (MAIN_PREC == "fp16x3" and args.levels and full_size
                                                      and tc_variant_env() == "3") else None
     roof["algorithmic_per_launch"] = (f"{flops_per_launch:.4g} flop (B*M*{prods_per_step} complex {N}x{N} "
                                       f"products, 8N^3 each)")
