@@ -521,7 +521,7 @@ def run_workload(args):
         las = torch.linspace(0.0, 1.0, n_la, dtype=torch.float64, device="cuda")
         tn = (torch.arange(M, dtype=torch.float64, device="cuda") + 0.5) * (Tw / M)
         gen = torch.Generator(device="cuda").manual_seed(5)
-        chunk_om = max(1, min(n_om, 20))
+        chunk_om = max(1, min(n_om, 100))      # 100 000 pulses per launch: ten waves of CTAs
         Qmap = torch.empty((n_om, n_la), dtype=torch.float64, device="cuda")
         kern_ms = 0.0
         ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

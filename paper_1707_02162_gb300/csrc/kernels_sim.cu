@@ -305,8 +305,20 @@ expect_cols_kernel(const cplx<R>* __restrict__ T, int64_t entries, const int32_t
 #pragma unroll
         for (int r = 0; r < N; ++r) {
           cplx<R> sacc = cmake<R>(R(0), R(0));
+          if constexpr (std::is_same<R, float>::value && N % 2 == 0) {
+            // two operator entries per 16-byte load: the N lanes of a pulse read the same
+            // address, so each quarter-warp phase of the load serves one pulse
+            const float4* A4 = reinterpret_cast<const float4*>(A + r * N);
 #pragma unroll
-          for (int kk = 0; kk < N; ++kk) cfma<R>(sacc, A[r * N + kk], u[kk]);
+            for (int kk = 0; kk < N; kk += 2) {
+              const float4 a2 = A4[kk / 2];
+              cfma<R>(sacc, cmake<R>(a2.x, a2.y), u[kk]);
+              cfma<R>(sacc, cmake<R>(a2.z, a2.w), u[kk + 1]);
+            }
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < N; ++kk) cfma<R>(sacc, A[r * N + kk], u[kk]);
+          }
           v[r] = sacc;
         }
 #pragma unroll
