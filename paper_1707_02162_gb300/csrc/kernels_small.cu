@@ -613,6 +613,68 @@ chain_kernel(Src src, int64_t units, int64_t segs_per_unit, int64_t seg_len, int
   }
 }
 
+// ----------------------------------------------------------------------------
+// Small N (N * sizeof(R) <= 64: N <= 16 in FP32, <= 8 in FP64) with a table that fits in
+// shared memory: the table is staged once per CTA and a thread carries one column of one
+// segment product in registers, u <- T_f u factor after factor (T_f read from shared memory,
+// two entries per 16-byte load in FP32), with no barrier inside the chain.
+// ----------------------------------------------------------------------------
+constexpr int kColsThreads = 256;
+constexpr size_t kColsTableBytes = 200 * 1024;
+
+template <typename R>
+static bool cols_eligible(const redo_table* t, const ChainPlan& p) {
+  const size_t table = (size_t)t->entries * t->N * t->N * sizeof(cplx<R>);
+  return !p.pd && t->N * sizeof(R) <= 64 && table <= kColsTableBytes;
+}
+
+template <typename R, int N>
+__global__ void __launch_bounds__(kColsThreads, 1)
+chain_cols_kernel(const cplx<R>* __restrict__ T, int64_t entries, GatherSrc<R> src, int64_t units,
+                  int64_t segs, int64_t seg_len, int64_t total_len, cplx<R>* __restrict__ out) {
+  constexpr int N2 = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* Ts = reinterpret_cast<cplx<R>*>(smem_raw);
+  for (int64_t i = threadIdx.x; i < entries * N2; i += kColsThreads) Ts[i] = T[i];
+  __syncthreads();
+  const int c = threadIdx.x % N;
+  const int64_t g = (int64_t)blockIdx.x * (kColsThreads / N) + threadIdx.x / N;
+  if (g >= units * segs) return;
+  const int64_t unit = g / segs, sgi = g - unit * segs;
+  if (c != 0) src.status = nullptr;               // a bad level index is counted once per factor
+  const int64_t f0 = sgi * seg_len;
+  const int64_t f1 = f0 + seg_len < total_len ? f0 + seg_len : total_len;
+  cplx<R> u[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) u[r] = cmake<R>(r == c ? R(1) : R(0), R(0));
+  for (int64_t f = f0; f < f1; ++f) {
+    const cplx<R>* A = Ts + (src.addr(unit, f, N2) - src.T);
+    cplx<R> v[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      cplx<R> sacc = cmake<R>(R(0), R(0));
+      if constexpr (std::is_same<R, float>::value && N % 2 == 0) {
+        const float4* A4 = reinterpret_cast<const float4*>(A + r * N);
+#pragma unroll
+        for (int kk = 0; kk < N; kk += 2) {
+          const float4 a2 = A4[kk / 2];
+          cfma<R>(sacc, cmake<R>(a2.x, a2.y), u[kk]);
+          cfma<R>(sacc, cmake<R>(a2.z, a2.w), u[kk + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < N; ++kk) cfma<R>(sacc, A[r * N + kk], u[kk]);
+      }
+      v[r] = sacc;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r) u[r] = v[r];
+  }
+  cplx<R>* o = out + g * N2;
+#pragma unroll
+  for (int r = 0; r < N; ++r) o[r * N + c] = u[r];
+}
+
 template <typename R, int N>
 struct ChainCfg {
   static constexpr int STAGES = (N >= 64) ? 2 : ((N >= 32) ? 3 : 4);
@@ -665,8 +727,11 @@ ChainPlan plan_chain(const redo_table* t, int64_t B, int64_t M, int prec, bool p
   p.M = M;
   p.fps = (int64_t)t->K * t->digits + (phase ? 1 : 0);
   p.F = M * p.fps;
-  const int slots = prec == REDO_FP64 ? chain_slots<double>(t->N, t->num_sms)
-                                      : chain_slots<float>(t->N, t->num_sms);
+  int slots = prec == REDO_FP64 ? chain_slots<double>(t->N, t->num_sms)
+                                : chain_slots<float>(t->N, t->num_sms);
+  const bool cols = !phase && (prec == REDO_FP64 ? cols_eligible<double>(t, p) : cols_eligible<float>(t, p));
+  // column chains: four CTAs of 256 / N segment products per SM, one per SM at a time
+  if (cols) slots = 2 * t->num_sms * (kColsThreads / t->N);
   // about two segments per resident chain, each at least 16 factors long
   int64_t S = (2 * (int64_t)slots + B - 1) / (B > 0 ? B : 1);
   const int64_t max_s = (p.F + 15) / 16;
@@ -703,6 +768,27 @@ static cudaError_t chain_segments_t(const redo_table* t, const int32_t* q, const
   src.pd = p.pd;
   src.N = t->N;
   cplx<R>* out = (cplx<R>*)seg_out;
+  if (cols_eligible<R>(t, p)) {
+    const size_t smem = (size_t)t->entries * t->N * t->N * sizeof(cplx<R>);
+    const int64_t G = p.B * p.S;
+    if (G == 0) return cudaSuccess;
+#define COLS_CASE(n)                                                                                        \
+  case n:                                                                                                   \
+    if constexpr (n * sizeof(R) <= 64) {                                                                    \
+      cudaError_t e = cudaFuncSetAttribute(chain_cols_kernel<R, n>,                                         \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+      if (e != cudaSuccess) return e;                                                                       \
+      chain_cols_kernel<R, n><<<(unsigned)((G + kColsThreads / n - 1) / (kColsThreads / n)), kColsThreads,  \
+                                smem, s>>>(src.T, t->entries, src, p.B, p.S, p.seg_len, p.F, out);          \
+      return cudaGetLastError();                                                                            \
+    }                                                                                                       \
+    break;
+    switch (t->N) {
+      COLS_CASE(2) COLS_CASE(4) COLS_CASE(8) COLS_CASE(16)
+      default: break;
+    }
+#undef COLS_CASE
+  }
   switch (t->N) {
     case 2: return launch_chain_n<R, 2>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
     case 4: return launch_chain_n<R, 4>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
