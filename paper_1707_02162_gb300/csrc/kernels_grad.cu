@@ -129,6 +129,9 @@ struct GradArgs {
   const double2* pd;
   const double* sz;          // [K][N]
   double2* Tz;               // [B][M+1][K]
+  // kept forward states (the partial products of every segment, [chains][seg_len][N][N]) or
+  // nullptr: with them the sweep reads P_f instead of undoing it (one product per factor)
+  const cplx<R>* keep;
 };
 
 // Table operator of factor f (nullptr for a step-opening phase factor).
@@ -156,7 +159,10 @@ __device__ __forceinline__ const cplx<R>* grad_factor(const GradArgs<R>& a, int6
 }
 
 // PH: amplitude/phase call (a.pd non-null: step-opening diagonal factors and boundary traces).
-template <typename R, int N, bool PH>
+// KEEP: every forward state kept (a.keep): P_f is copied in with the factor, R starts from the
+// costate carried back by the checkpoint before the segment (the kept states start from the
+// identity at the segment's start), and only R <- R A_f is multiplied.
+template <typename R, int N, bool PH, bool KEEP>
 __global__ void __launch_bounds__(SmemMM<R, N, SqTile<N>::TM, SqTile<N>::TM>::THREADS)
 grad_sweep_kernel(GradArgs<R> a) {
   constexpr int TM = SqTile<N>::TM;
@@ -165,10 +171,12 @@ grad_sweep_kernel(GradArgs<R> a) {
   constexpr int STAGES = (sizeof(R) == 8 && N == 64) ? 1 : 2;   // shared memory budget
   constexpr uint32_t BYTES = (uint32_t)(N2 * sizeof(cplx<R>));
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  // layout: P, R, STAGES operators (KEEP: R, STAGES operators, STAGES kept states)
   cplx<R>* P = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* Rm = P + N2;
-  cplx<R>* Abuf = Rm + N2;                                   // STAGES operators
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Abuf + STAGES * N2);
+  cplx<R>* Rm = KEEP ? P : P + N2;
+  cplx<R>* Abuf = Rm + N2;
+  cplx<R>* Pbuf = Abuf + STAGES * N2;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(KEEP ? Pbuf + STAGES * N2 : Abuf + STAGES * N2);
   __shared__ double red_re[MM::THREADS], red_im[MM::THREADS];
   __shared__ int abort_flag;
   const int lt = threadIdx.x;
@@ -183,18 +191,38 @@ grad_sweep_kernel(GradArgs<R> a) {
   if (lt == 0) abort_flag = 0;
   if (lt < STAGES) mbar_init(&bar[lt], 1);
   fence_mbarrier_init();
-  for (int i = lt; i < N2; i += MM::THREADS) {
-    P[i] = a.Pck[g * N2 + i];
-    Rm[i] = a.Rck[g * N2 + i];
+  cplx<R> Y1[TM][TM], Y2[TM][TM];
+  if constexpr (KEEP) {
+    // R' = P_{s-1} R_s (R_0 for the first segment of a pulse)
+    for (int i = lt; i < N2; i += MM::THREADS) {
+      Rm[i] = a.Rck[g * N2 + i];
+      if (s > 0) Pbuf[i] = a.Pck[(g - 1) * N2 + i];
+    }
+    __syncthreads();
+    if (s > 0) {
+      MM::run(Pbuf, Rm, lt, Y2);
+      __syncthreads();
+      MM::store(Rm, lt, Y2);
+      __syncthreads();
+    }
+  } else {
+    for (int i = lt; i < N2; i += MM::THREADS) {
+      P[i] = a.Pck[g * N2 + i];
+      Rm[i] = a.Rck[g * N2 + i];
+    }
+    __syncthreads();
   }
-  __syncthreads();
   // factors are visited in reverse: t-th visit is factor f1-1-t
   // a phase factor has no operand to copy: its stage completes on the arrival alone
   auto issue = [&](int st, int64_t f) {
     int k, j;
     int64_t n;
     const cplx<R>* src = grad_factor<R, N>(a, b, f, &k, &j, &n);
-    if (src) {
+    if (KEEP) {
+      mbar_arrive_expect_tx(&bar[st], 2 * BYTES);
+      bulk_load(Abuf + st * N2, src, BYTES, &bar[st]);
+      bulk_load(Pbuf + st * N2, a.keep + (g * a.seg_len + (f - f0)) * N2, BYTES, &bar[st]);
+    } else if (src) {
       mbar_arrive_expect_tx(&bar[st], BYTES);
       bulk_load(Abuf + st * N2, src, BYTES, &bar[st]);
     } else {
@@ -229,7 +257,6 @@ grad_sweep_kernel(GradArgs<R> a) {
     __syncthreads();
   };
   if (PH && len > 0 && f1 == a.F) phase_traces(a.M);     // end of the chain
-  cplx<R> Y1[TM][TM], Y2[TM][TM];
   for (int64_t t = 0; t < len; ++t) {
     const int64_t f = f1 - 1 - t;
     const int64_t n = f / a.fps;
@@ -237,6 +264,15 @@ grad_sweep_kernel(GradArgs<R> a) {
     const bool phase = PH && r == 0;
     if (PH) --r;
     const int k = r / a.d, j = r - k * a.d;
+    const int stage = (int)(t % STAGES);
+    const uint32_t parity = (uint32_t)((t / STAGES) & 1);
+    if constexpr (KEEP) {
+      // the trace needs this factor's kept state: wait for the stage first
+      if (!mbar_wait_bounded(&bar[stage], parity)) abort_flag = 1;
+      __syncthreads();
+      if (abort_flag) break;
+    }
+    const cplx<R>* Pt = KEEP ? Pbuf + stage * N2 : P;
     if (phase) phase_traces(n);
     if (!phase && j == a.d - 1) {
       // Tr(H_k P R) = sum over nonzeros (row i, col c) of H_k[i][c] (P R)[c][i]
@@ -247,7 +283,7 @@ grad_sweep_kernel(GradArgs<R> a) {
         const int i = a.hk_row[e], c = a.hk_col[e];
         R dr = 0, di = 0;
         for (int x = 0; x < N; ++x) {
-          const cplx<R> pv = P[c * N + x], rv = Rm[x * N + i];
+          const cplx<R> pv = Pt[c * N + x], rv = Rm[x * N + i];
           dr = fma(pv.x, rv.x, dr);
           dr = fma(-pv.y, rv.y, dr);
           di = fma(pv.x, rv.y, di);
@@ -273,11 +309,11 @@ grad_sweep_kernel(GradArgs<R> a) {
         a.grad[(b * a.M + n) * a.K + k] = a.scale * (tau.x * ti - tau.y * tr);
       }
     }
-    const int stage = (int)(t % STAGES);
-    const uint32_t parity = (uint32_t)((t / STAGES) & 1);
-    if (!mbar_wait_bounded(&bar[stage], parity)) abort_flag = 1;
-    __syncthreads();
-    if (abort_flag) break;
+    if constexpr (!KEEP) {
+      if (!mbar_wait_bounded(&bar[stage], parity)) abort_flag = 1;
+      __syncthreads();
+      if (abort_flag) break;
+    }
     const cplx<R>* A = Abuf + stage * N2;
     if (PH && phase) {
       // P <- diag(p)^dag P (rows), R <- R diag(p) (columns)
@@ -293,12 +329,14 @@ grad_sweep_kernel(GradArgs<R> a) {
           Y1[u][v] = cmake<R>(prx * x.x + pry * x.y, prx * x.y - pry * x.x);
           Y2[u][v] = cmake<R>(pcx * y.x - pcy * y.y, pcx * y.y + pcy * y.x);
         }
+    } else if constexpr (KEEP) {
+      MM::run(Rm, A, lt, Y2);        // R <- R A
     } else {
       MM::run_adj(A, P, lt, Y1);     // P <- A^dag P
       MM::run(Rm, A, lt, Y2);        // R <- R A
     }
     __syncthreads();
-    MM::store(P, lt, Y1);
+    if constexpr (!KEEP) MM::store(P, lt, Y1);
     MM::store(Rm, lt, Y2);
     if (lt == 0 && t + STAGES < len) {
       fence_proxy_async_smem();
@@ -328,8 +366,9 @@ template <typename R, int N>
 static cudaError_t grad_sweep_n(const GradArgs<R>& a, int64_t B, cudaStream_t s) {
   using MM = SmemMM<R, N, SqTile<N>::TM, SqTile<N>::TM>;
   constexpr int STAGES = (sizeof(R) == 8 && N == 64) ? 1 : 2;
-  const size_t smem = (2 + STAGES) * sizeof(cplx<R>) * N * N + 2 * sizeof(uint64_t);
-  auto kern = a.pd ? grad_sweep_kernel<R, N, true> : grad_sweep_kernel<R, N, false>;
+  const size_t smem = (a.keep ? 1 + 2 * STAGES : 2 + STAGES) * sizeof(cplx<R>) * N * N + 2 * sizeof(uint64_t);
+  auto kern = a.pd ? grad_sweep_kernel<R, N, true, false>
+                   : (a.keep ? grad_sweep_kernel<R, N, false, true> : grad_sweep_kernel<R, N, false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t blocks = B * a.S;
@@ -365,8 +404,9 @@ cudaError_t launch_grad_scan(const redo_table* t, int64_t B, int64_t S, int prec
 template <typename R>
 static cudaError_t grad_sweep_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
                                 const void* Pck, const void* Rck, const double2* tau,
-                                double* grad, int64_t* status, double2* Tz, cudaStream_t s) {
+                                double* grad, int64_t* status, double2* Tz, const void* keep, cudaStream_t s) {
   GradArgs<R> a;
+  a.keep = (const cplx<R>*)keep;
   a.fps = p.fps > 0 ? p.fps : (int64_t)t->K * t->digits;
   a.pd = p.pd;
   a.sz = t->sz64;
@@ -404,9 +444,9 @@ static cudaError_t grad_sweep_t(const redo_table* t, const int32_t* q, const Cha
 
 cudaError_t launch_grad_sweep(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
                               const void* Pck, const void* Rck, const double2* tau, double* grad,
-                              int64_t* status, cudaStream_t s, double2* Tz) {
-  if (prec == REDO_FP64) return grad_sweep_t<double>(t, q, p, Pck, Rck, tau, grad, status, Tz, s);
-  return grad_sweep_t<float>(t, q, p, Pck, Rck, tau, grad, status, Tz, s);
+                              int64_t* status, cudaStream_t s, double2* Tz, const void* keep) {
+  if (prec == REDO_FP64) return grad_sweep_t<double>(t, q, p, Pck, Rck, tau, grad, status, Tz, keep, s);
+  return grad_sweep_t<float>(t, q, p, Pck, Rck, tau, grad, status, Tz, keep, s);
 }
 
 }  // namespace redo

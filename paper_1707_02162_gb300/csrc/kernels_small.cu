@@ -516,7 +516,7 @@ struct DenseSrc {
 template <typename R, int N, int STAGES, class Src>
 __global__ void __launch_bounds__(SmemMM<R, N, Tiling<N>::TM, Tiling<N>::TN>::THREADS * Tiling<N>::CH)
 chain_kernel(Src src, int64_t units, int64_t segs_per_unit, int64_t seg_len, int64_t total_len,
-             cplx<R>* __restrict__ out, int64_t* status) {
+             cplx<R>* __restrict__ out, int64_t* status, cplx<R>* __restrict__ keep) {
   using TL = Tiling<N>;
   using MM = SmemMM<R, N, TL::TM, TL::TN>;
   constexpr int CH = TL::CH;
@@ -595,6 +595,7 @@ chain_kernel(Src src, int64_t units, int64_t segs_per_unit, int64_t seg_len, int
     if (abort_flag) break;
     if (active) {
       MM::store(X, lt, Y);
+      if (keep) MM::store(keep + (my_g * seg_len + t) * N2, lt, Y);   // every partial product kept
       if (lt == 0 && t + STAGES < my_len) {
         fence_proxy_async_smem();
         issue(stage, my_f0 + t + STAGES);
@@ -631,7 +632,8 @@ static bool cols_eligible(const redo_table* t, const ChainPlan& p) {
 template <typename R, int N>
 __global__ void __launch_bounds__(kColsThreads, 1)
 chain_cols_kernel(const cplx<R>* __restrict__ T, int64_t entries, GatherSrc<R> src, int64_t units,
-                  int64_t segs, int64_t seg_len, int64_t total_len, cplx<R>* __restrict__ out) {
+                  int64_t segs, int64_t seg_len, int64_t total_len, cplx<R>* __restrict__ out,
+                  cplx<R>* __restrict__ keep) {
   constexpr int N2 = N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<R>* Ts = reinterpret_cast<cplx<R>*>(smem_raw);
@@ -669,6 +671,11 @@ chain_cols_kernel(const cplx<R>* __restrict__ T, int64_t entries, GatherSrc<R> s
     }
 #pragma unroll
     for (int r = 0; r < N; ++r) u[r] = v[r];
+    if (keep) {
+      cplx<R>* kp = keep + (g * seg_len + (f - f0)) * N2;
+#pragma unroll
+      for (int r = 0; r < N; ++r) kp[r * N + c] = u[r];
+    }
   }
   cplx<R>* o = out + g * N2;
 #pragma unroll
@@ -687,7 +694,7 @@ struct ChainCfg {
 template <typename R, int N, class Src>
 static cudaError_t launch_chain_n(Src src, int64_t units, int64_t segs, int64_t seg_len,
                                   int64_t total_len, cplx<R>* out, int64_t* status,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, cplx<R>* keep = nullptr) {
   using C = ChainCfg<R, N>;
   auto kern = chain_kernel<R, N, C::STAGES, Src>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -697,7 +704,7 @@ static cudaError_t launch_chain_n(Src src, int64_t units, int64_t segs, int64_t 
   const int64_t blocks = (G + Tiling<N>::CH - 1) / Tiling<N>::CH;
   if (blocks == 0) return cudaSuccess;
   kern<<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(src, units, segs, seg_len, total_len, out,
-                                                      status);
+                                                      status, keep);
   return cudaGetLastError();
 }
 
@@ -754,7 +761,8 @@ size_t chain_workspace_bytes(const redo_table* t, const ChainPlan& p, int prec) 
 
 template <typename R>
 static cudaError_t chain_segments_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
-                                    void* seg_out, int64_t* status, cudaStream_t s) {
+                                    void* seg_out, int64_t* status, cudaStream_t s, void* keep) {
+  cplx<R>* kp = (cplx<R>*)keep;
   GatherSrc<R> src;
   src.T = std::is_same<R, double>::value ? (const cplx<R>*)t->T64 : (const cplx<R>*)t->T32;
   src.q = q;
@@ -779,7 +787,7 @@ static cudaError_t chain_segments_t(const redo_table* t, const int32_t* q, const
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
       if (e != cudaSuccess) return e;                                                                       \
       chain_cols_kernel<R, n><<<(unsigned)((G + kColsThreads / n - 1) / (kColsThreads / n)), kColsThreads,  \
-                                smem, s>>>(src.T, t->entries, src, p.B, p.S, p.seg_len, p.F, out);          \
+                                smem, s>>>(src.T, t->entries, src, p.B, p.S, p.seg_len, p.F, out, kp);      \
       return cudaGetLastError();                                                                            \
     }                                                                                                       \
     break;
@@ -790,20 +798,20 @@ static cudaError_t chain_segments_t(const redo_table* t, const int32_t* q, const
 #undef COLS_CASE
   }
   switch (t->N) {
-    case 2: return launch_chain_n<R, 2>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
-    case 4: return launch_chain_n<R, 4>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
-    case 8: return launch_chain_n<R, 8>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
-    case 16: return launch_chain_n<R, 16>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
-    case 32: return launch_chain_n<R, 32>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
-    case 64: return launch_chain_n<R, 64>(src, p.B, p.S, p.seg_len, p.F, out, status, s);
+    case 2: return launch_chain_n<R, 2>(src, p.B, p.S, p.seg_len, p.F, out, status, s, kp);
+    case 4: return launch_chain_n<R, 4>(src, p.B, p.S, p.seg_len, p.F, out, status, s, kp);
+    case 8: return launch_chain_n<R, 8>(src, p.B, p.S, p.seg_len, p.F, out, status, s, kp);
+    case 16: return launch_chain_n<R, 16>(src, p.B, p.S, p.seg_len, p.F, out, status, s, kp);
+    case 32: return launch_chain_n<R, 32>(src, p.B, p.S, p.seg_len, p.F, out, status, s, kp);
+    case 64: return launch_chain_n<R, 64>(src, p.B, p.S, p.seg_len, p.F, out, status, s, kp);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_chain_segments(const redo_table* t, const int32_t* q, const ChainPlan& p,
-                                  int prec, void* seg_out, int64_t* status, cudaStream_t s) {
-  if (prec == REDO_FP64) return chain_segments_t<double>(t, q, p, seg_out, status, s);
-  return chain_segments_t<float>(t, q, p, seg_out, status, s);
+                                  int prec, void* seg_out, int64_t* status, cudaStream_t s, void* keep) {
+  if (prec == REDO_FP64) return chain_segments_t<double>(t, q, p, seg_out, status, s, keep);
+  return chain_segments_t<float>(t, q, p, seg_out, status, s, keep);
 }
 
 template <typename R>

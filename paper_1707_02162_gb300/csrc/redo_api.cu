@@ -733,6 +733,8 @@ redo_status redo_batched_product(int32_t N, int64_t count, const void* A, int32_
 struct GradLayout {
   ChainPlan p;
   size_t seg_off, pck_off, rck_off, tau_off, total;
+  size_t keep_off = 0;                 // N <= 64: every forward state kept (0: not kept)
+  bool keep = false;
   size_t strang_off, strang_tmp_off;   // symmetric split: transformed targets (+ scratch)
 };
 
@@ -757,6 +759,14 @@ static GradLayout grad_layout(const redo_table* t, int64_t B, int64_t M, redo_pr
   L.rck_off = 2 * mats;
   L.tau_off = 3 * mats;
   L.total = L.tau_off + up((size_t)B * sizeof(double2));
+  // every forward state kept when they fit in 24 GiB: the sweep then multiplies only the
+  // costates (one product per factor instead of two)
+  const size_t keep_bytes = (size_t)L.p.B * L.p.S * L.p.seg_len * t->N * t->N * el;
+  if (M > 0 && keep_bytes <= ((size_t)24 << 30)) {
+    L.keep = true;
+    L.keep_off = L.total;
+    L.total += up(keep_bytes);
+  }
   add_strang(t, B, L.total, L.strang_off, L.strang_tmp_off);
   return L;
 }
@@ -818,14 +828,15 @@ redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B,
     if (e != cudaSuccess) return cuda_error(e, "large-N gradient");
     return REDO_OK;
   }
-  if ((e = launch_chain_segments(t, q, L.p, prec, w + L.seg_off, dev_status, s)) != cudaSuccess)
+  void* keep = L.keep ? w + L.keep_off : nullptr;
+  if ((e = launch_chain_segments(t, q, L.p, prec, w + L.seg_off, dev_status, s, keep)) != cudaSuccess)
     return cuda_error(e, "gradient segments");
   if ((e = launch_grad_scan(t, B, L.p.S, prec, w + L.seg_off, (const double2*)U_target,
                             target_batched, w + L.pck_off, w + L.rck_off, tau, F_out, s)) !=
       cudaSuccess)
     return cuda_error(e, "gradient checkpoints");
   if (M > 0 && (e = launch_grad_sweep(t, q, L.p, prec, w + L.pck_off, w + L.rck_off, tau, grad,
-                                      dev_status, s)) != cudaSuccess)
+                                      dev_status, s, nullptr, keep)) != cudaSuccess)
     return cuda_error(e, "gradient sweep");
   return REDO_OK;
 }

@@ -129,8 +129,10 @@ struct ChainPlan {
 };
 ChainPlan plan_chain(const redo_table* t, int64_t B, int64_t M, int prec, bool phase = false);
 size_t chain_workspace_bytes(const redo_table* t, const ChainPlan& p, int prec);
+// keep non-null: every segment's partial product after each factor is also written to
+// keep[chain][t] (N x N, the chain precision).
 cudaError_t launch_chain_segments(const redo_table* t, const int32_t* q, const ChainPlan& p,
-                                  int prec, void* seg_out, int64_t* status, cudaStream_t s);
+                                  int prec, void* seg_out, int64_t* status, cudaStream_t s, void* keep = nullptr);
 cudaError_t launch_chain_combine(const redo_table* t, const ChainPlan& p, int prec,
                                  const void* seg_in, void* prod_out, int64_t* status,
                                  cudaStream_t s);
@@ -165,7 +167,7 @@ cudaError_t launch_grad_scan(const redo_table* t, int64_t B, int64_t S, int prec
 // every step boundary n = 0..M ([B][M+1][K]).
 cudaError_t launch_grad_sweep(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
                               const void* Pck, const void* Rck, const double2* tau, double* grad,
-                              int64_t* status, cudaStream_t s, double2* Tz = nullptr);
+                              int64_t* status, cudaStream_t s, double2* Tz = nullptr, const void* keep = nullptr);
 
 // State simulation (kernels_sim.cu).
 cudaError_t launch_state_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
