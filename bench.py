@@ -738,15 +738,22 @@ def run_workload(args):
     elif args.workload == "warmstart_study":
         # 5 qubits, K=10, M=500, dt=2 us; targets from weight-one Pauli strings (reachable)
         from paper_1707_02162_gb300 import warmstart
+        # every instance its own offsets and couplings (table without drift, per-pulse diagonal
+        # drift); --shared-drift: the one-system study
         w = inputs.config(4, B=1)
-        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+        per_instance = not args.shared_drift
+        H0 = np.zeros_like(w.H0) if per_instance else w.H0
+        t = redo.Table(H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
         t0 = time.time()
         const = np.concatenate([w.extra["nu"][0] / 5e3, w.extra["J"][0][np.triu_indices(w.n_qubits, 1)] / 200.0])
-        rep = warmstart.study(t, w.n_qubits, w.M, w.K, w.extra["Omega"], const, n_train=args.B if args.B != B_FULL else 512)
+        rep = warmstart.study(t, w.n_qubits, w.M, w.K, w.extra["Omega"], const,
+                              n_train=args.B if args.B != B_FULL else 512, per_instance_drift=per_instance)
         out.update({"metric": "GRAPE iterations to F>=0.99 (MLP warm start vs random init, Adam ascent)",
                     "unit": "iterations", "value": rep.summary()["median_iters_mlp_init"],
                     "summary": rep.summary(), "wall_s": time.time() - t0,
                     "config": {"N": w.N, "K": w.K, "M": w.M, "dt": w.dt,
+                               "systems": ("per instance: nu ~ U[-5,5] kHz, J ~ U[-200,200] Hz" if per_instance
+                                           else "one system"),
                                "targets": "exp(-i sum theta_k P_k), 8 weight-one Pauli strings, theta ~ U[0, pi/2]"}})
     elif args.workload == "warmstart":
         # 5 qubits (N=32), K=10, M=500: batched GRAPE iterations and MLP training throughput
@@ -771,6 +778,20 @@ def run_workload(args):
             it()
             ms = _events_time(it, args.steps if prec == "fp32" else 1)
             res[prec] = {"instance_iters_per_s": B * 1e3 / ms, "ms_per_batched_iter": ms}
+        # every instance with its own offsets and couplings: a table without drift and the
+        # per-pulse diagonal drift of each instance
+        t_nd = redo.Table(np.zeros_like(w.H0), w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+        h = torch.as_tensor(inputs.drift_diagonals(w), device="cuda")
+        ws = torch.empty(redo.redo_fidelity_grad_drift_workspace(t_nd.handle, B, w.M, "fp32", 0), dtype=torch.uint8,
+                         device="cuda")
+
+        def it_drift():
+            redo.redo_quantize(t_nd.handle, u, q)
+            redo.redo_fidelity_grad_drift(t_nd.handle, q, h, targets, "fp32", 0, F, g, ws)
+            redo.redo_grape_step(t_nd.handle, u, g, 1e9)
+        it_drift()
+        ms = _events_time(it_drift, args.steps)
+        res["fp32_per_instance_drift"] = {"instance_iters_per_s": B * 1e3 / ms, "ms_per_batched_iter": ms}
         from paper_1707_02162_gb300.warmstart import MLP
         net = MLP([23, 512, 512, 512, w.M * w.K])
         x = torch.randn(1024, 23)
@@ -800,6 +821,8 @@ def main():
     ap.add_argument("--digit-table", action="store_true",
                     help="multiply digit operators every step instead of using the level table "
                          "(process 3: every level's operator evaluated once, the default)")
+    ap.add_argument("--shared-drift", action="store_true",
+                    help="warmstart_study: one system for every instance instead of per-instance offsets/couplings")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")

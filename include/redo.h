@@ -437,6 +437,42 @@ redo_status redo_fidelity_grad_phase_workspace(const redo_table* t, int64_t B, i
                                                int32_t checkpoint_every, size_t* bytes);
 
 /*
+ * redo_propagate_drift -- U_b = U_M ... U_1 with a diagonal drift of each pulse's own:
+ *   U_n = E_{K-1,n} ... E_{0,n} D diag(exp(-i dt h_b)),
+ * the Lie split (Section III, the step after Eq. vnd, drift first in time) of the drift
+ * H0 + diag(h_b), exact when the table's H0 is diagonal (build the table with H0 = 0 and pass
+ * each pulse's whole diagonal drift in h; the NMR offsets and couplings of Section III are
+ * diagonal).  One table then serves pulses on systems that differ in their offsets and couplings.
+ *  h      device double [B][N]: the diagonal drift energies of pulse b (rad/s); the factors
+ *         exp(-i dt h) are taken in FP64 (FP32 copies for REDO_FP16X3).
+ * The other arguments, outputs and errors as redo_propagate.  REDO_ERR_UNSUPPORTED on a
+ * symmetric-split table and for REDO_FP16X3 with N > 64.  Workspace from
+ * redo_propagate_drift_workspace.
+ */
+redo_status redo_propagate_drift(const redo_table* t, const int32_t* q, const double* h, int64_t B, int64_t M,
+                                 redo_precision prec, int32_t reunit_every, void* U_out, const void* U_target,
+                                 double* F_out, void* tau_out, void* workspace, size_t workspace_bytes,
+                                 int64_t* dev_status, void* stream);
+redo_status redo_propagate_drift_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                           int32_t reunit_every, size_t* bytes);
+
+/*
+ * redo_fidelity_grad_drift -- F and dF/du of redo_fidelity_grad for the chain of
+ * redo_propagate_drift (h: device double [B][N], pulse b's diagonal drift in rad/s).
+ * The drift factors are constants of the pulse, so the gradient keeps Section III's form
+ * g_kn = (2 dt / N^2) Im(conj(tau) Tr(H_k W_{n,k})) with each step's diagonal inside its W.
+ * REDO_FP64 or REDO_FP32 at every N (for N > 64 on segments of whole steps: checkpoint_every is
+ * then the segment length in steps); REDO_ERR_UNSUPPORTED otherwise and on a symmetric-split
+ * table.  Workspace from redo_fidelity_grad_drift_workspace.
+ */
+redo_status redo_fidelity_grad_drift(const redo_table* t, const int32_t* q, const double* h, int64_t B, int64_t M,
+                                     const void* U_target, int32_t target_batched, redo_precision prec,
+                                     int32_t checkpoint_every, double* F_out, double* grad, void* workspace,
+                                     size_t workspace_bytes, int64_t* dev_status, void* stream);
+redo_status redo_fidelity_grad_drift_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                               int32_t checkpoint_every, size_t* bytes);
+
+/*
  * redo_batched_product -- C_b = op(A_b) op(B_b), b < count, for the time-split layer (one pulse
  * cut into time segments, one per rank: U = S_{G-1} ... S_0, and segment r's gradient taken
  * against the target L_r^dag U_T P_r^dag with P_r = S_{r-1} ... S_0, L_r = S_{G-1} ... S_{r+1};

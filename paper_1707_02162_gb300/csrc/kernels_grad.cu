@@ -161,7 +161,9 @@ __device__ __forceinline__ const cplx<R>* grad_factor(const GradArgs<R>& a, int6
 // PH: amplitude/phase call (a.pd non-null: step-opening diagonal factors and boundary traces).
 // KEEP: every forward state kept (a.keep): P_f is copied in with the factor, R starts from the
 // costate carried back by the checkpoint before the segment (the kept states start from the
-// identity at the segment's start), and only R <- R A_f is multiplied.
+// identity at the segment's start), and only R <- R A_f is multiplied.  PH and KEEP together
+// serve the per-pulse drift diagonals, which record no boundary traces (a.Tz == nullptr): at a
+// diagonal factor only R <- R diag(p) remains.
 template <typename R, int N, bool PH, bool KEEP>
 __global__ void __launch_bounds__(SmemMM<R, N, SqTile<N>::TM, SqTile<N>::TM>::THREADS)
 grad_sweep_kernel(GradArgs<R> a) {
@@ -219,8 +221,8 @@ grad_sweep_kernel(GradArgs<R> a) {
     int64_t n;
     const cplx<R>* src = grad_factor<R, N>(a, b, f, &k, &j, &n);
     if (KEEP) {
-      mbar_arrive_expect_tx(&bar[st], 2 * BYTES);
-      bulk_load(Abuf + st * N2, src, BYTES, &bar[st]);
+      mbar_arrive_expect_tx(&bar[st], src ? 2 * BYTES : BYTES);
+      if (src) bulk_load(Abuf + st * N2, src, BYTES, &bar[st]);
       bulk_load(Pbuf + st * N2, a.keep + (g * a.seg_len + (f - f0)) * N2, BYTES, &bar[st]);
     } else if (src) {
       mbar_arrive_expect_tx(&bar[st], BYTES);
@@ -235,6 +237,7 @@ grad_sweep_kernel(GradArgs<R> a) {
   __shared__ double2 dg[64];
   // Tz[b][nz][k] = sum_a sz[k][a] (P R)[a][a] for every species k
   auto phase_traces = [&](int64_t nz) {
+    if (KEEP || !a.Tz) return;   // step diagonals without phase axes (per-pulse drift): no traces
     if (lt < N) {
       double re = 0.0, im = 0.0;
       for (int x = 0; x < N; ++x) {
@@ -324,9 +327,13 @@ grad_sweep_kernel(GradArgs<R> a) {
 #pragma unroll
         for (int v = 0; v < TM; ++v) {
           const int row = ty + MM::TY * u, col = tx + MM::TX * v;
-          const R prx = (R)pv[row].x, pry = (R)pv[row].y, pcx = (R)pv[col].x, pcy = (R)pv[col].y;
-          const cplx<R> x = P[row * N + col], y = Rm[row * N + col];
-          Y1[u][v] = cmake<R>(prx * x.x + pry * x.y, prx * x.y - pry * x.x);
+          const R pcx = (R)pv[col].x, pcy = (R)pv[col].y;
+          const cplx<R> y = Rm[row * N + col];
+          if constexpr (!KEEP) {
+            const R prx = (R)pv[row].x, pry = (R)pv[row].y;
+            const cplx<R> x = P[row * N + col];
+            Y1[u][v] = cmake<R>(prx * x.x + pry * x.y, prx * x.y - pry * x.x);
+          }
           Y2[u][v] = cmake<R>(pcx * y.x - pcy * y.y, pcx * y.y + pcy * y.x);
         }
     } else if constexpr (KEEP) {
@@ -367,7 +374,7 @@ static cudaError_t grad_sweep_n(const GradArgs<R>& a, int64_t B, cudaStream_t s)
   using MM = SmemMM<R, N, SqTile<N>::TM, SqTile<N>::TM>;
   constexpr int STAGES = (sizeof(R) == 8 && N == 64) ? 1 : 2;
   const size_t smem = (a.keep ? 1 + 2 * STAGES : 2 + STAGES) * sizeof(cplx<R>) * N * N + 2 * sizeof(uint64_t);
-  auto kern = a.pd ? grad_sweep_kernel<R, N, true, false>
+  auto kern = a.pd ? (a.keep ? grad_sweep_kernel<R, N, true, true> : grad_sweep_kernel<R, N, true, false>)
                    : (a.keep ? grad_sweep_kernel<R, N, false, true> : grad_sweep_kernel<R, N, false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -405,6 +412,7 @@ template <typename R>
 static cudaError_t grad_sweep_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
                                 const void* Pck, const void* Rck, const double2* tau,
                                 double* grad, int64_t* status, double2* Tz, const void* keep, cudaStream_t s) {
+  if (keep && p.pd && Tz) return cudaErrorInvalidValue;   // kept states carry no boundary traces
   GradArgs<R> a;
   a.keep = (const cplx<R>*)keep;
   a.fps = p.fps > 0 ? p.fps : (int64_t)t->K * t->digits;

@@ -1053,7 +1053,7 @@ static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const Cha
                                    s)))
       return e;
   }
-  if (p.pd && (e = launch_phase_grad_finish(N, p.B, p.M, t->K, Tz, tau, grad_phase, s))) return e;
+  if (p.pd && Tz && (e = launch_phase_grad_finish(N, p.B, p.M, t->K, Tz, tau, grad_phase, s))) return e;
   return cudaGetLastError();
 }
 

@@ -53,6 +53,31 @@ __global__ void phase_diag_kernel(const double* __restrict__ phi, const double* 
   }
 }
 
+// Per-pulse diagonal drift: pd[b][n][a] = exp(-i dt h[b][a]) for every step n, so that each
+// step reads U_n = E_n D diag(exp(-i dt h_b)) (the Lie split of the drift H0 + diag(h_b), exact
+// when H0 is diagonal).  Each (b, a) takes its sine and cosine once, in FP64, and writes them
+// for a run of kDriftSteps steps; pd32 non-null writes them in FP32 instead.
+constexpr int64_t kDriftSteps = 64;
+
+__global__ void drift_diag_kernel(const double* __restrict__ h, double dt, int64_t B, int64_t M, int N,
+                                  double2* __restrict__ pd, float2* __restrict__ pd32) {
+  const int64_t runs = (M + kDriftSteps - 1) / kDriftSteps;
+  for (int64_t w = blockIdx.x; w < B * runs; w += gridDim.x) {
+    const int64_t b = w / runs, n0 = (w % runs) * kDriftSteps;
+    const int64_t n1 = n0 + kDriftSteps < M ? n0 + kDriftSteps : M;
+    for (int a = threadIdx.x; a < N; a += blockDim.x) {
+      double sn, cs;
+      sincos(dt * h[b * N + a], &sn, &cs);
+      for (int64_t n = n0; n < n1; ++n) {
+        if (pd32)
+          pd32[(b * M + n) * N + a] = make_float2((float)cs, (float)-sn);
+        else
+          pd[(b * M + n) * N + a] = make_double2(cs, -sn);
+      }
+    }
+  }
+}
+
 // X_g <- diag(pd[u][n]) X_g, n = s * sps + i, for the chains g = u * S + s with n < M
 template <typename R>
 __global__ void phase_rows_kernel(cplx<R>* __restrict__ X, int N, int64_t S, int64_t sps, int64_t i,
@@ -210,6 +235,15 @@ cudaError_t launch_phase_diag(const redo_table* t, const double* phi, int64_t B,
   return cudaGetLastError();
 }
 
+cudaError_t launch_drift_diag(const redo_table* t, const double* h, int64_t B, int64_t M, double2* pd,
+                              float2* pd32, cudaStream_t s) {
+  const int64_t work = B * ((M + kDriftSteps - 1) / kDriftSteps);
+  if (work == 0) return cudaSuccess;
+  const int64_t blocks = work < (int64_t)t->num_sms * 16 ? work : (int64_t)t->num_sms * 16;
+  drift_diag_kernel<<<(unsigned)blocks, 128, 0, s>>>(h, t->dt, B, M, t->N, pd, pd32);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_phase_rows(int N, int prec, void* X, int64_t G, int64_t S, int64_t sps, int64_t i,
                               int64_t M, const double2* pd, cudaStream_t s) {
   if (G == 0) return cudaSuccess;
@@ -243,14 +277,16 @@ cudaError_t launch_phase_boundary(int N, int prec, void* P, void* Rm, int64_t G,
                                   int K, double2* Tz, cudaStream_t s) {
   if (G == 0) return cudaSuccess;
   if (prec == REDO_FP64) {
-    phase_boundary_tz_kernel<double><<<(unsigned)G, 256, 0, s>>>((const double2*)P, (const double2*)Rm, N, S,
-                                                                  seg_len, F, tt, kd, M, sz, K, Tz);
+    if (Tz)
+      phase_boundary_tz_kernel<double><<<(unsigned)G, 256, 0, s>>>((const double2*)P, (const double2*)Rm, N, S,
+                                                                    seg_len, F, tt, kd, M, sz, K, Tz);
     if (tt >= 0)
       phase_undo_kernel<double><<<dim3((unsigned)G, grid_y((int64_t)N * N)), 256, 0, s>>>(
           (double2*)P, (double2*)Rm, N, S, seg_len, F, tt, kd, M, pd);
   } else {
-    phase_boundary_tz_kernel<float><<<(unsigned)G, 256, 0, s>>>((const float2*)P, (const float2*)Rm, N, S,
-                                                                 seg_len, F, tt, kd, M, sz, K, Tz);
+    if (Tz)
+      phase_boundary_tz_kernel<float><<<(unsigned)G, 256, 0, s>>>((const float2*)P, (const float2*)Rm, N, S,
+                                                                   seg_len, F, tt, kd, M, sz, K, Tz);
     if (tt >= 0)
       phase_undo_kernel<float><<<dim3((unsigned)G, grid_y((int64_t)N * N)), 256, 0, s>>>(
           (float2*)P, (float2*)Rm, N, S, seg_len, F, tt, kd, M, pd);

@@ -544,9 +544,11 @@ redo_status redo_propagate_workspace(const redo_table* t, int64_t B, int64_t M,
   return REDO_OK;
 }
 
-// Shared body of redo_propagate and redo_propagate_phase (phi non-null: amplitude/phase controls).
-static redo_status propagate_core(const redo_table* t, const int32_t* q, const double* phi, int64_t B, int64_t M,
-                                  redo_precision prec, int32_t reunit_every, void* U_out, const void* U_target,
+// Shared body of redo_propagate, redo_propagate_phase (phi non-null: amplitude/phase controls) and
+// redo_propagate_drift (h non-null: a diagonal drift per pulse).
+static redo_status propagate_core(const redo_table* t, const int32_t* q, const double* phi, const double* h,
+                                  int64_t B, int64_t M, redo_precision prec, int32_t reunit_every, void* U_out,
+                                  const void* U_target,
                                   double* F_out, void* tau_out, void* workspace, size_t workspace_bytes,
                                   int64_t* dev_status, void* stream) {
   if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
@@ -555,25 +557,27 @@ static redo_status propagate_core(const redo_table* t, const int32_t* q, const d
   redo_status st = check_prec(t, prec);
   if (st != REDO_OK) return st;
   const bool phase = phi != nullptr;
+  const bool diag = phase || h != nullptr;   // step-opening diagonal factors
   if (B == 0) return REDO_OK;
   if (M > 0 && !q) return set_error(REDO_ERR_INVALID, "q is NULL");
   if (U_target && !F_out && !tau_out)
     return set_error(REDO_ERR_INVALID, "U_target given without F_out or tau_out");
   if (!U_out && !U_target) return set_error(REDO_ERR_INVALID, "nothing to compute");
   if (reunit_every > M) reunit_every = M > 0 ? (int32_t)M : 0;
-  PropLayout L = prop_layout(t, B, M, prec, reunit_every, phase);
+  PropLayout L = prop_layout(t, B, M, prec, reunit_every, diag);
   if (!workspace || workspace_bytes < L.total)
     return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", L.total);
   if (((uintptr_t)workspace & 255) != 0) return set_error(REDO_ERR_INVALID, "workspace not 256-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   double2* zf = nullptr;
-  if (phase) {
+  if (diag) {
     double2* pd = (double2*)((char*)workspace + L.pd_off);
     zf = (double2*)((char*)workspace + L.zf_off);
     const bool tc = prec == REDO_FP16X3 && t->N <= kSmallN;     // the split-FP16 chains take FP32 diagonals
-    if ((e = launch_phase_diag(t, phi, B, M, tc ? nullptr : pd, tc ? (float2*)pd : nullptr, zf, s)) != cudaSuccess)
-      return cuda_error(e, "phase diagonals");
+    e = phase ? launch_phase_diag(t, phi, B, M, tc ? nullptr : pd, tc ? (float2*)pd : nullptr, zf, s)
+              : launch_drift_diag(t, h, B, M, tc ? nullptr : pd, tc ? (float2*)pd : nullptr, s);
+    if (e != cudaSuccess) return cuda_error(e, phase ? "phase diagonals" : "drift diagonals");
     if (tc)
       L.p.pd32 = (const float2*)pd;
     else
@@ -672,8 +676,8 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
                            redo_precision prec, int32_t reunit_every, void* U_out,
                            const void* U_target, double* F_out, void* tau_out, void* workspace,
                            size_t workspace_bytes, int64_t* dev_status, void* stream) {
-  return propagate_core(t, q, nullptr, B, M, prec, reunit_every, U_out, U_target, F_out, tau_out, workspace,
-                        workspace_bytes, dev_status, stream);
+  return propagate_core(t, q, nullptr, nullptr, B, M, prec, reunit_every, U_out, U_target, F_out, tau_out,
+                        workspace, workspace_bytes, dev_status, stream);
 }
 
 static redo_status check_phase(const redo_table* t, redo_precision prec) {
@@ -705,8 +709,39 @@ redo_status redo_propagate_phase(const redo_table* t, const int32_t* q, const do
   if (st != REDO_OK) return st;
   if (B > 0 && M > 0 && !phi) return set_error(REDO_ERR_INVALID, "phi is NULL");
   static const double kNoPhase = 0.0;
-  return propagate_core(t, q, phi ? phi : &kNoPhase, B, M, prec, reunit_every, U_out, U_target, F_out, tau_out,
-                        workspace, workspace_bytes, dev_status, stream);
+  return propagate_core(t, q, phi ? phi : &kNoPhase, nullptr, B, M, prec, reunit_every, U_out, U_target, F_out,
+                        tau_out, workspace, workspace_bytes, dev_status, stream);
+}
+
+static redo_status check_drift(const redo_table* t, redo_precision prec) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (t->strang) return set_error(REDO_ERR_UNSUPPORTED, "per-pulse drift on a symmetric-split table");
+  if (prec == REDO_FP16X3 && t->N > kSmallN)
+    return set_error(REDO_ERR_UNSUPPORTED, "per-pulse drift in REDO_FP16X3 needs N <= 64");
+  return check_prec(t, prec);
+}
+
+redo_status redo_propagate_drift_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                           int32_t reunit_every, size_t* bytes) {
+  if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
+  if (B < 0 || M < 0 || reunit_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  redo_status st = check_drift(t, prec);
+  if (st != REDO_OK) return st;
+  if (reunit_every > M) reunit_every = M > 0 ? (int32_t)M : 0;
+  *bytes = prop_layout(t, B, M, prec, reunit_every, true).total;
+  return REDO_OK;
+}
+
+redo_status redo_propagate_drift(const redo_table* t, const int32_t* q, const double* h, int64_t B, int64_t M,
+                                 redo_precision prec, int32_t reunit_every, void* U_out, const void* U_target,
+                                 double* F_out, void* tau_out, void* workspace, size_t workspace_bytes,
+                                 int64_t* dev_status, void* stream) {
+  redo_status st = check_drift(t, prec);
+  if (st != REDO_OK) return st;
+  if (B > 0 && M > 0 && !h) return set_error(REDO_ERR_INVALID, "h is NULL");
+  static const double kNoDrift = 0.0;
+  return propagate_core(t, q, nullptr, h ? h : &kNoDrift, B, M, prec, reunit_every, U_out, U_target, F_out,
+                        tau_out, workspace, workspace_bytes, dev_status, stream);
 }
 
 redo_status redo_batched_product(int32_t N, int64_t count, const void* A, int32_t adjA, int32_t A_batched,
@@ -849,7 +884,7 @@ struct PhaseGradLayout {
 };
 
 static PhaseGradLayout phase_grad_layout(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
-                                         int32_t checkpoint_every) {
+                                         int32_t checkpoint_every, bool phase = true) {
   PhaseGradLayout L;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   if (t->N > kSmallN) {
@@ -874,10 +909,23 @@ static PhaseGradLayout phase_grad_layout(const redo_table* t, int64_t B, int64_t
     L.g.tau_off = 3 * mats;
     L.pd_off = L.g.tau_off + up((size_t)B * sizeof(double2));
   }
+  // the per-pulse drift form has no final rotation, transformed target or boundary traces
+  const size_t ph = phase ? 1 : 0;
   L.zf_off = L.pd_off + up((size_t)B * M * t->N * sizeof(double2));
-  L.ut_off = L.zf_off + up((size_t)B * t->N * sizeof(double2));
-  L.tz_off = L.ut_off + up((size_t)B * t->N * t->N * sizeof(double2));
-  L.total = L.tz_off + up((size_t)B * (M + 1) * t->K * sizeof(double2));
+  L.ut_off = L.zf_off + ph * up((size_t)B * t->N * sizeof(double2));
+  L.tz_off = L.ut_off + ph * up((size_t)B * t->N * t->N * sizeof(double2));
+  L.total = L.tz_off + ph * up((size_t)B * (M + 1) * t->K * sizeof(double2));
+  if (!phase && t->N <= kSmallN) {
+    // per-pulse drift at N <= 64: every forward state kept when they fit in 24 GiB (the sweep
+    // then multiplies only the costates), as in the plain gradient
+    const size_t el = prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t keep_bytes = (size_t)L.g.p.B * L.g.p.S * L.g.p.seg_len * t->N * t->N * el;
+    if (M > 0 && keep_bytes <= ((size_t)24 << 30)) {
+      L.g.keep = true;
+      L.g.keep_off = L.total;
+      L.total += up(keep_bytes);
+    }
+  }
   return L;
 }
 
@@ -950,6 +998,70 @@ redo_status redo_fidelity_grad_phase(const redo_table* t, const int32_t* q, cons
     if ((e = launch_phase_grad_finish(t->N, B, M, t->K, tz, tau, grad_phase, s)) != cudaSuccess)
       return cuda_error(e, "phase gradient");
   }
+  return REDO_OK;
+}
+
+// GRAPE gradient with a diagonal drift per pulse: the chain with the step diagonals
+// diag(exp(-i dt h_b)) as factors, against the caller's target (SIMT sweeps, FP64 or FP32).
+static redo_status check_drift_grad(const redo_table* t, redo_precision prec) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (t->strang) return set_error(REDO_ERR_UNSUPPORTED, "per-pulse drift on a symmetric-split table");
+  if (prec != REDO_FP64 && prec != REDO_FP32)
+    return set_error(REDO_ERR_UNSUPPORTED, "the per-pulse drift gradient supports REDO_FP64 and REDO_FP32");
+  return check_prec(t, prec);
+}
+
+redo_status redo_fidelity_grad_drift_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                               int32_t checkpoint_every, size_t* bytes) {
+  if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
+  if (B < 0 || M < 0 || checkpoint_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  redo_status st = check_drift_grad(t, prec);
+  if (st != REDO_OK) return st;
+  if (checkpoint_every > M) checkpoint_every = M > 0 ? (int32_t)M : 0;
+  *bytes = phase_grad_layout(t, B, M, prec, checkpoint_every, false).total;
+  return REDO_OK;
+}
+
+redo_status redo_fidelity_grad_drift(const redo_table* t, const int32_t* q, const double* h, int64_t B, int64_t M,
+                                     const void* U_target, int32_t target_batched, redo_precision prec,
+                                     int32_t checkpoint_every, double* F_out, double* grad, void* workspace,
+                                     size_t workspace_bytes, int64_t* dev_status, void* stream) {
+  redo_status st = check_drift_grad(t, prec);
+  if (st != REDO_OK) return st;
+  if (B < 0 || M < 0 || checkpoint_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  if (B == 0) return REDO_OK;
+  if (!U_target) return set_error(REDO_ERR_INVALID, "U_target is NULL");
+  if (M > 0 && (!q || !h || !grad)) return set_error(REDO_ERR_INVALID, "q, h or grad is NULL");
+  if (checkpoint_every > M) checkpoint_every = M > 0 ? (int32_t)M : 0;
+  PhaseGradLayout L = phase_grad_layout(t, B, M, prec, checkpoint_every, false);
+  if (!workspace || workspace_bytes < L.total)
+    return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", L.total);
+  if (((uintptr_t)workspace & 255) != 0) return set_error(REDO_ERR_INVALID, "workspace not 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  double2* tau = (double2*)(w + L.g.tau_off);
+  double2* pd = (double2*)(w + L.pd_off);
+  const double2* ut = (const double2*)U_target;
+  cudaError_t e;
+  ProfScope ps(7, s);
+  if (M > 0 && (e = launch_drift_diag(t, h, B, M, pd, nullptr, s)) != cudaSuccess)
+    return cuda_error(e, "drift diagonals");
+  L.g.p.pd = pd;
+  if (t->N > kSmallN) {
+    if ((e = large_grad(t, q, L.g.p, prec, ut, target_batched, F_out, grad, workspace, dev_status, s)) !=
+        cudaSuccess)
+      return cuda_error(e, "large-N drift gradient");
+    return REDO_OK;
+  }
+  void* keep = L.g.keep ? w + L.g.keep_off : nullptr;
+  if ((e = launch_chain_segments(t, q, L.g.p, prec, w + L.g.seg_off, dev_status, s, keep)) != cudaSuccess)
+    return cuda_error(e, "gradient segments");
+  if ((e = launch_grad_scan(t, B, L.g.p.S, prec, w + L.g.seg_off, ut, target_batched, w + L.g.pck_off,
+                            w + L.g.rck_off, tau, F_out, s)) != cudaSuccess)
+    return cuda_error(e, "gradient checkpoints");
+  if (M > 0 && (e = launch_grad_sweep(t, q, L.g.p, prec, w + L.g.pck_off, w + L.g.rck_off, tau, grad, dev_status,
+                                      s, nullptr, keep)) != cudaSuccess)
+    return cuda_error(e, "gradient sweep");
   return REDO_OK;
 }
 

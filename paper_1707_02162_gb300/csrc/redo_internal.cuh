@@ -259,6 +259,11 @@ cudaError_t launch_half_drift_vec(const redo_table* t, const double2* psi, int64
 // With pd32 non-null the diagonals go there in FP32 (pd unused).
 cudaError_t launch_phase_diag(const redo_table* t, const double* phi, int64_t B, int64_t M, double2* pd,
                               float2* pd32, double2* zf, cudaStream_t s);
+// Per-pulse diagonal drift: pd[b][n][a] = exp(-i dt h[b][a]) for every step n (pd32 non-null:
+// FP32 there instead), the step-opening diagonals of a chain whose steps read
+// U_n = E_n D diag(exp(-i dt h_b)).
+cudaError_t launch_drift_diag(const redo_table* t, const double* h, int64_t B, int64_t M, double2* pd,
+                              float2* pd32, cudaStream_t s);
 // X_g <- P_n X_g in place for the chains g = (u, s) of a step-aligned plan, n = s*sps + i
 // (chains with n >= M untouched); X of precision prec.
 cudaError_t launch_phase_rows(int N, int prec, void* X, int64_t G, int64_t S, int64_t sps, int64_t i,
@@ -272,6 +277,7 @@ cudaError_t launch_phase_grad_finish(int N, int64_t B, int64_t M, int K, const d
 // Reverse sweep of the large-N phase gradient at offset tt from every chain's end (segments of
 // whole steps): where the chain's factor opens step n, record Tz[u][n][k] = Tr(S_kz P R) and undo
 // P_n (P <- P_n^dag P, R <- R P_n); tt = -1 records Tz[u][M] at the end of the last segment.
+// Tz == nullptr (per-pulse drift diagonals) records nothing and only undoes P_n.
 cudaError_t launch_phase_boundary(int N, int prec, void* P, void* Rm, int64_t G, int64_t S, int64_t seg_len,
                                   int64_t F, int64_t tt, int64_t kd, int64_t M, const double2* pd, const double* sz,
                                   int K, double2* Tz, cudaStream_t s);

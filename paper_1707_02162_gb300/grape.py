@@ -83,7 +83,7 @@ class GrapeResult:
 
 def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, prec="fp64",
           checkpoint_every=0, threshold: float | None = None, adaptive: bool = True,
-          optimizer: str = "gd", lr_decay: float = 150.0, psi0=None) -> GrapeResult:
+          optimizer: str = "gd", lr_decay: float = 150.0, psi0=None, drift=None) -> GrapeResult:
     """Gradient ascent on the fidelity (the paper does not specify the update rule).
 
     ``optimizer="gd"``: ``u <- clamp(u + step * dF/du)``; with ``adaptive`` the
@@ -92,7 +92,9 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
     then the learning rate in rad/s, decayed as step / (1 + it / lr_decay).
     Stops early once every pulse reached ``threshold``.  With ``psi0`` given, ``target`` is a
     state ([N] or [B][N]) and the objective is the state fidelity |<target| U |psi0>|^2
-    (redo_state_grad: matrix-vector sweeps instead of propagators).
+    (redo_state_grad: matrix-vector sweeps instead of propagators).  With ``drift`` ([B][N], rad/s)
+    every pulse carries its own diagonal drift (redo_fidelity_grad_drift; the table's own drift,
+    usually zero then, is applied as well).
     """
     u = u0.clone().contiguous()
     B, M, K = u.shape
@@ -102,9 +104,14 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
     reached = torch.full((B,), -1, dtype=torch.int64)
     res = GrapeResult(u=u)
     state = psi0 is not None
+    if state and drift is not None:
+        raise ValueError("per-pulse drift is supported for the unitary fidelity only")
     if state:
         nbytes = redo.redo_state_grad_workspace(table.handle, B)
         psi0 = torch.as_tensor(psi0, dtype=torch.complex128, device=u.device).contiguous()
+    elif drift is not None:
+        drift = torch.as_tensor(drift, dtype=torch.float64, device=u.device).contiguous()
+        nbytes = redo.redo_fidelity_grad_drift_workspace(table.handle, B, M, prec, checkpoint_every)
     else:
         nbytes = redo.redo_fidelity_grad_workspace(table.handle, B, M, prec, checkpoint_every)
     ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=u.device)
@@ -119,6 +126,8 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
         redo.redo_quantize(table.handle, u, q)
         if state:
             redo.redo_state_grad(table.handle, q, prec, psi0, target, F, g, ws)
+        elif drift is not None:
+            redo.redo_fidelity_grad_drift(table.handle, q, drift, target, prec, checkpoint_every, F, g, ws)
         else:
             redo.redo_fidelity_grad(table.handle, q, target, prec, checkpoint_every, F, g, ws)
         Fh = F.cpu()

@@ -276,6 +276,14 @@ def phase_config(n_qubits: int = 6, *, B: int = 256, M: int = 2000, seed: int = 
                     u, target=target, extra={"Omega": Om, "phi": phi, "sz": species_z_diagonals(n)})
 
 
+def drift_diagonals(w: Workload) -> np.ndarray:
+    """Each instance's own diagonal drift ``h[b] = diag(H0_b)`` (rad/s), shape (B, N), from the
+    per-instance offsets ``extra["nu"]`` and couplings ``extra["J"]`` of the warm-start
+    workload (index 4): the input of the per-pulse drift calls, whose table is built with H0 = 0."""
+    nu, J = w.extra["nu"], w.extra["J"]
+    return np.stack([np.real(np.diag(drift_zz(w.n_qubits, nu[b], J[b]))) for b in range(nu.shape[0])])
+
+
 def pauli_generator(strings: list[str], theta: np.ndarray) -> np.ndarray:
     """Hermitian generator ``G = sum_k theta_k P_k`` of a target ``exp(-i G)``.
 

@@ -31,7 +31,8 @@ EXPORTS = [
     "redo_mlp_backward", "redo_mlp_adam", "redo_grape_adam_step", "redo_expect_diag",
     "redo_state_grad", "redo_state_grad_workspace", "redo_table_set_phase_axes", "redo_propagate_phase",
     "redo_propagate_phase_workspace", "redo_batched_product", "redo_fidelity_grad_phase",
-    "redo_fidelity_grad_phase_workspace",
+    "redo_fidelity_grad_phase_workspace", "redo_propagate_drift", "redo_propagate_drift_workspace",
+    "redo_fidelity_grad_drift", "redo_fidelity_grad_drift_workspace",
 ]
 PROFILE_PHASES = 11
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -70,6 +71,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_fidelity_grad_phase_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_phase.argtypes = [vp, vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_propagate_phase_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_propagate_drift.argtypes = [vp, vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
+    L.redo_propagate_drift_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_fidelity_grad_drift.argtypes = [vp, vp, vp, i64, i64, vp, i32, i32, i32, vp, vp, vp, ctypes.c_size_t, vp,
+                                           vp]
+    L.redo_fidelity_grad_drift_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_noalloc.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
     L.redo_fidelity_grad.argtypes = [vp, vp, i64, i64, vp, i32, i32, i32, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_fidelity_grad_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
@@ -244,6 +250,25 @@ def redo_fidelity_grad(handle: int, q: torch.Tensor, U_target: torch.Tensor, pre
                                              _stream(stream)))
 
 
+def redo_fidelity_grad_drift_workspace(handle: int, B: int, M: int, prec, checkpoint_every: int = 0) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().redo_fidelity_grad_drift_workspace(ctypes.c_void_p(handle), B, M, _prec(prec),
+                                                             checkpoint_every, ctypes.byref(n)))
+    return n.value
+
+
+def redo_fidelity_grad_drift(handle: int, q: torch.Tensor, h: torch.Tensor, U_target: torch.Tensor, prec,
+                             checkpoint_every: int, F_out: torch.Tensor | None, grad: torch.Tensor,
+                             workspace: torch.Tensor, status: torch.Tensor | None = None, stream=None):
+    """redo_fidelity_grad with pulse b's diagonal drift h[b] (device float64 [B][N], rad/s)."""
+    B, M = q.shape[0], q.shape[1]
+    batched = 1 if U_target.dim() == 3 else 0
+    _check(load_library().redo_fidelity_grad_drift(ctypes.c_void_p(handle), _ptr(q), _ptr(h), B, M, _ptr(U_target),
+                                                   batched, _prec(prec), checkpoint_every, _ptr(F_out), _ptr(grad),
+                                                   _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                                   _ptr(status), _stream(stream)))
+
+
 def redo_grape_step(handle: int, u: torch.Tensor, grad: torch.Tensor, step: float,
                     step_scale: torch.Tensor | None = None, stream=None):
     """In place: u <- clamp(u + step * s_b * grad, lo_k, hi_k) (gradient ascent on the fidelity)."""
@@ -349,6 +374,14 @@ def redo_profile_read() -> dict:
     return {PHASE_NAMES[i]: (ms[i], n[i]) for i in range(PROFILE_PHASES) if n[i]}
 
 
+def _single_target(table, target) -> torch.Tensor:
+    """The one [N][N] target of a propagation call (the gradient calls take one per pulse)."""
+    target = torch.as_tensor(target, dtype=torch.complex128, device=table.device).contiguous()
+    if tuple(target.shape) != (table.N, table.N):
+        raise ValueError(f"propagation target must be [{table.N}][{table.N}], got {tuple(target.shape)}")
+    return target
+
+
 class Table:
     """Owning wrapper of a redo_table built from torch tensors on the current device."""
 
@@ -404,7 +437,7 @@ class Table:
         U = torch.empty((B, self.N, self.N), dtype=torch.complex128, device=self.device) if want_U else None
         F = tau = None
         if target is not None:
-            target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
+            target = _single_target(self, target)
             F = torch.empty(B, dtype=torch.float64, device=self.device)
             tau = torch.empty(B, dtype=torch.complex128, device=self.device)
         ws = self.workspace(B, q.shape[1], prec, reunit_every)
@@ -425,7 +458,7 @@ def _table_propagate_phase(self, q, phi, prec="fp64", target=None, want_U=True, 
     U = torch.empty((B, self.N, self.N), dtype=torch.complex128, device=self.device) if want_U else None
     F = tau = None
     if target is not None:
-        target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
+        target = _single_target(self, target)
         F = torch.empty(B, dtype=torch.float64, device=self.device)
         tau = torch.empty(B, dtype=torch.complex128, device=self.device)
     nbytes = redo_propagate_phase_workspace(self.handle, B, M, prec, reunit_every)
@@ -456,6 +489,45 @@ def _table_fidelity_grad_phase(self, q, phi, target, prec="fp64", checkpoint_eve
 Table.fidelity_grad_phase = _table_fidelity_grad_phase
 Table.set_phase_axes = _table_set_phase_axes
 Table.propagate_phase = _table_propagate_phase
+
+
+def _table_propagate_drift(self, q, h, prec="fp64", target=None, want_U=True, status=None, reunit_every=0):
+    """(U [B][N][N] or None, F or None, tau or None) with a diagonal drift per pulse: h [B][N] the
+    drift energies (rad/s) applied each step as diag(exp(-i dt h_b)) before the table factors."""
+    B, M = q.shape[0], q.shape[1]
+    h = torch.as_tensor(h, dtype=torch.float64, device=self.device).contiguous()
+    U = torch.empty((B, self.N, self.N), dtype=torch.complex128, device=self.device) if want_U else None
+    F = tau = None
+    if target is not None:
+        target = _single_target(self, target)
+        F = torch.empty(B, dtype=torch.float64, device=self.device)
+        tau = torch.empty(B, dtype=torch.complex128, device=self.device)
+    n = ctypes.c_size_t()
+    L = load_library()
+    _check(L.redo_propagate_drift_workspace(ctypes.c_void_p(self.handle), B, M, _prec(prec), reunit_every,
+                                            ctypes.byref(n)))
+    ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+    _check(L.redo_propagate_drift(ctypes.c_void_p(self.handle), _ptr(q), _ptr(h), B, M, _prec(prec), reunit_every,
+                                  _ptr(U), _ptr(target), _ptr(F), _ptr(tau), _ptr(ws), ws.numel(), _ptr(status),
+                                  _stream(None)))
+    return U, F, tau
+
+
+def _table_fidelity_grad_drift(self, q, h, target, prec="fp64", checkpoint_every=0, status=None):
+    """(F [B], dF/du [B][M][K]) with a diagonal drift per pulse (h [B][N], rad/s)."""
+    B, M = q.shape[0], q.shape[1]
+    h = torch.as_tensor(h, dtype=torch.float64, device=self.device).contiguous()
+    target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
+    F = torch.empty(B, dtype=torch.float64, device=self.device)
+    g = torch.empty((B, M, self.K), dtype=torch.float64, device=self.device)
+    nbytes = redo_fidelity_grad_drift_workspace(self.handle, B, M, prec, checkpoint_every)
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+    redo_fidelity_grad_drift(self.handle, q, h, target, prec, checkpoint_every, F, g, ws, status)
+    return F, g
+
+
+Table.propagate_drift = _table_propagate_drift
+Table.fidelity_grad_drift = _table_fidelity_grad_drift
 
 
 def _table_fidelity_grad(self, q, target, prec="fp64", checkpoint_every=0, status=None):

@@ -93,10 +93,11 @@ class WarmStartReport:
 
 
 def converge(table: redo.Table, targets: np.ndarray, u0: np.ndarray, iters: int, step: float, threshold: float,
-             prec="fp64", optimizer="gd"):
-    """Batched GRAPE on per-instance targets; returns (u, first iteration reaching threshold per instance)."""
+             prec="fp64", optimizer="gd", drift=None):
+    """Batched GRAPE on per-instance targets (and, with ``drift`` [B][N], per-instance diagonal
+    drifts); returns (u, first iteration reaching threshold per instance, the GRAPE result)."""
     res = grape(table, torch.as_tensor(targets, device=table.device), torch.as_tensor(u0, device=table.device),
-                iters=iters, step=step, prec=prec, threshold=threshold, optimizer=optimizer)
+                iters=iters, step=step, prec=prec, threshold=threshold, optimizer=optimizer, drift=drift)
     return res.u, res.reached.tolist(), res
 
 
@@ -114,47 +115,68 @@ def local_pauli_family(n_qubits: int, n_strings: int, rng: np.random.Generator) 
     return out
 
 
-def study(table: redo.Table, n_qubits: int, M: int, K: int, Omega: float, features_const: np.ndarray,
+def study(table: redo.Table, n_qubits: int, M: int, K: int, Omega: float, features_const: np.ndarray | None = None,
           n_train: int = 512, n_test: int = 64, threshold: float = 0.99, iters: int = 400, step: float = 0.0,
           theta_max: float = np.pi / 2, train_steps: int = 1500, hidden=(512, 512, 512), seed: int = 4,
-          prec: str = "fp32") -> WarmStartReport:
-    """Learned warm start on one system: targets exp(-i sum_k theta_k P_k) over a fixed set of
-    Pauli strings; MLP input = (system constants, theta); output = M*K normalised amplitudes."""
+          prec: str = "fp32", per_instance_drift: bool = False) -> WarmStartReport:
+    """Learned warm start: targets exp(-i sum_k theta_k P_k) over a fixed set of Pauli strings;
+    MLP input = (system constants, theta); output = M*K normalised amplitudes.
+
+    ``per_instance_drift=False``: one system, the table's own drift, whose constants
+    ``features_const`` head every input.  ``per_instance_drift=True``: the table must be built
+    with H0 = 0; every instance draws its own offsets nu ~ U[-5, 5] kHz and couplings
+    J ~ U[-200, 200] Hz (i < j), GRAPE runs with that diagonal drift per instance, and the input
+    is (nu / 5 kHz, J / 200 Hz, theta): for 5 qubits 5 + 10 + 8 = 23 numbers."""
     from scipy.linalg import expm as _expm   # target construction only (problem input)
-    from .inputs import pauli_generator
+    from .inputs import drift_zz, pauli_generator
     rng = np.random.default_rng(seed)
     strings = local_pauli_family(n_qubits, 8, rng)
     lr = step if step > 0 else 0.01 * Omega          # Adam learning rate in rad/s
+    iu = np.triu_indices(n_qubits, 1)
 
     def targets(count):
         th = rng.uniform(0.0, theta_max, size=(count, len(strings)))
         T = np.stack([_expm(-1j * pauli_generator(strings, t)) for t in th])
         return th, T
 
-    def feats(th):
-        const = np.broadcast_to(features_const, (th.shape[0], features_const.size))
-        return torch.tensor(np.concatenate([const, th / theta_max * 2 - 1], axis=1), dtype=torch.float32)
+    def systems(count):
+        """(system features [count][F], diagonal drifts [count][N] or None)."""
+        if not per_instance_drift:
+            return np.broadcast_to(features_const, (count, features_const.size)), None
+        nu = rng.uniform(-5e3, 5e3, size=(count, n_qubits))
+        J = rng.uniform(-200.0, 200.0, size=(count, iu[0].size))
+        h = np.empty((count, 2 ** n_qubits))
+        for b in range(count):
+            Jm = np.zeros((n_qubits, n_qubits))
+            Jm[iu] = J[b]
+            h[b] = np.real(np.diag(drift_zz(n_qubits, nu[b], Jm)))
+        return np.concatenate([nu / 5e3, J / 200.0], axis=1), h
+
+    def feats(sysf, th):
+        return torch.tensor(np.concatenate([sysf, th / theta_max * 2 - 1], axis=1), dtype=torch.float32)
 
     th_tr, T_tr = targets(n_train)
+    sys_tr, h_tr = systems(n_train)
     # every training instance starts from the same pulse, so that the converged pulses
     # follow one smooth branch of solutions in theta (what the network can learn)
     u0 = np.broadcast_to(rng.uniform(-0.3 * Omega, 0.3 * Omega, size=(1, M, K)), (n_train, M, K)).copy()
-    u_tr, reached, _ = converge(table, T_tr, u0, iters, lr, threshold, prec, "adam")
+    u_tr, reached, _ = converge(table, T_tr, u0, iters, lr, threshold, prec, "adam", drift=h_tr)
     ok = np.array(reached) >= 0
     if not ok.any():
         raise RuntimeError("no training instance reached the threshold; raise iters or lr")
-    x = feats(th_tr[ok])
+    x = feats(sys_tr[ok], th_tr[ok])
     y = torch.tensor(u_tr.cpu().numpy()[ok].reshape(int(ok.sum()), -1) / Omega, dtype=torch.float32)
     net = MLP([x.shape[1], *hidden, M * K], seed=seed)
     loss = float("nan")
     for _ in range(train_steps):
         loss = net.train_step(x, y, 1e-3)
     th_te, T_te = targets(n_test)
-    u_mlp = net.forward(feats(th_te)).cpu().numpy().reshape(n_test, M, K).astype(np.float64) * Omega
+    sys_te, h_te = systems(n_test)
+    u_mlp = net.forward(feats(sys_te, th_te)).cpu().numpy().reshape(n_test, M, K).astype(np.float64) * Omega
     u_rnd = rng.uniform(-0.3 * Omega, 0.3 * Omega, size=(n_test, M, K))
     # threshold=None keeps every run to the full budget so the final fidelities compare
-    _, _, r_mlp = converge(table, T_te, u_mlp, iters, lr, None, prec, "adam")
-    _, _, r_rnd = converge(table, T_te, u_rnd, iters, lr, None, prec, "adam")
+    _, _, r_mlp = converge(table, T_te, u_mlp, iters, lr, None, prec, "adam", drift=h_te)
+    _, _, r_rnd = converge(table, T_te, u_rnd, iters, lr, None, prec, "adam", drift=h_te)
 
     def first_reach(res):
         F = torch.stack(res.F_history)                      # [iters][B]
