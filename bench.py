@@ -747,8 +747,9 @@ def run_workload(args):
         t0 = time.time()
         const = np.concatenate([w.extra["nu"][0] / 5e3, w.extra["J"][0][np.triu_indices(w.n_qubits, 1)] / 200.0])
         rep = warmstart.study(t, w.n_qubits, w.M, w.K, w.extra["Omega"], const,
-                              n_train=args.B if args.B != B_FULL else 512, per_instance_drift=per_instance)
-        out.update({"metric": "GRAPE iterations to F>=0.99 (MLP warm start vs random init, Adam ascent)",
+                              n_train=args.B if args.B != B_FULL else 512, per_instance_drift=per_instance,
+                              threshold=args.ws_threshold, iters=args.ws_iters)
+        out.update({"metric": f"GRAPE iterations to F>={args.ws_threshold} (MLP warm start vs random init, Adam ascent)",
                     "unit": "iterations", "value": rep.summary()["median_iters_mlp_init"],
                     "summary": rep.summary(), "wall_s": time.time() - t0,
                     "config": {"N": w.N, "K": w.K, "M": w.M, "dt": w.dt,
@@ -823,6 +824,8 @@ def main():
                          "(process 3: every level's operator evaluated once, the default)")
     ap.add_argument("--shared-drift", action="store_true",
                     help="warmstart_study: one system for every instance instead of per-instance offsets/couplings")
+    ap.add_argument("--ws-threshold", type=float, default=0.99, help="warmstart_study: fidelity threshold")
+    ap.add_argument("--ws-iters", type=int, default=400, help="warmstart_study: GRAPE iteration budget")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
