@@ -161,10 +161,11 @@ __device__ __forceinline__ const cplx<R>* grad_factor(const GradArgs<R>& a, int6
 // PH: amplitude/phase call (a.pd non-null: step-opening diagonal factors and boundary traces).
 // KEEP: every forward state kept (a.keep): P_f is copied in with the factor, R starts from the
 // costate carried back by the checkpoint before the segment (the kept states start from the
-// identity at the segment's start), and only R <- R A_f is multiplied.  PH and KEEP together
-// serve the per-pulse drift diagonals, which record no boundary traces (a.Tz == nullptr): at a
-// diagonal factor only R <- R diag(p) remains.
-template <typename R, int N, bool PH, bool KEEP>
+// identity at the segment's start), and only R <- R A_f is multiplied.  With PH and KEEP
+// together a diagonal factor leaves only R <- R diag(p), and the boundary traces read the kept
+// state (with R' = P_{s-1} R_s, Tr(S P_kept R') = Tr(S P R_s) for the whole prefix P).
+// TZ: record the boundary traces Tz (amplitude/phase calls; not for per-pulse drift diagonals).
+template <typename R, int N, bool PH, bool KEEP, bool TZ>
 __global__ void __launch_bounds__(SmemMM<R, N, SqTile<N>::TM, SqTile<N>::TM>::THREADS)
 grad_sweep_kernel(GradArgs<R> a) {
   constexpr int TM = SqTile<N>::TM;
@@ -235,13 +236,13 @@ grad_sweep_kernel(GradArgs<R> a) {
     for (int st = 0; st < STAGES && st < len; ++st) issue(st, f1 - 1 - st);
   }
   __shared__ double2 dg[64];
-  // Tz[b][nz][k] = sum_a sz[k][a] (P R)[a][a] for every species k
-  auto phase_traces = [&](int64_t nz) {
-    if (KEEP || !a.Tz) return;   // step diagonals without phase axes (per-pulse drift): no traces
+  // Tz[b][nz][k] = sum_a sz[k][a] (Pq R)[a][a] for every species k
+  auto phase_traces = [&](int64_t nz, const cplx<R>* Pq) {
+    if constexpr (!TZ) return;   // step diagonals without phase axes (per-pulse drift): no traces
     if (lt < N) {
       double re = 0.0, im = 0.0;
       for (int x = 0; x < N; ++x) {
-        const cplx<R> pv = P[lt * N + x], rv = Rm[x * N + lt];
+        const cplx<R> pv = Pq[lt * N + x], rv = Rm[x * N + lt];
         re += (double)pv.x * rv.x - (double)pv.y * rv.y;
         im += (double)pv.x * rv.y + (double)pv.y * rv.x;
       }
@@ -259,7 +260,7 @@ grad_sweep_kernel(GradArgs<R> a) {
     }
     __syncthreads();
   };
-  if (PH && len > 0 && f1 == a.F) phase_traces(a.M);     // end of the chain
+  if (PH && !KEEP && len > 0 && f1 == a.F) phase_traces(a.M, P);     // end of the chain
   for (int64_t t = 0; t < len; ++t) {
     const int64_t f = f1 - 1 - t;
     const int64_t n = f / a.fps;
@@ -276,7 +277,9 @@ grad_sweep_kernel(GradArgs<R> a) {
       if (abort_flag) break;
     }
     const cplx<R>* Pt = KEEP ? Pbuf + stage * N2 : P;
-    if (phase) phase_traces(n);
+    // kept states: the first visit's state is the whole segment's product, the chain's end
+    if (PH && KEEP && t == 0 && f1 == a.F) phase_traces(a.M, Pt);
+    if (phase) phase_traces(n, Pt);
     if (!phase && j == a.d - 1) {
       // Tr(H_k P R) = sum over nonzeros (row i, col c) of H_k[i][c] (P R)[c][i]
       const int p0 = a.hk_ptr[k * (N + 1)];
@@ -374,8 +377,12 @@ static cudaError_t grad_sweep_n(const GradArgs<R>& a, int64_t B, cudaStream_t s)
   using MM = SmemMM<R, N, SqTile<N>::TM, SqTile<N>::TM>;
   constexpr int STAGES = (sizeof(R) == 8 && N == 64) ? 1 : 2;
   const size_t smem = (a.keep ? 1 + 2 * STAGES : 2 + STAGES) * sizeof(cplx<R>) * N * N + 2 * sizeof(uint64_t);
-  auto kern = a.pd ? (a.keep ? grad_sweep_kernel<R, N, true, true> : grad_sweep_kernel<R, N, true, false>)
-                   : (a.keep ? grad_sweep_kernel<R, N, false, true> : grad_sweep_kernel<R, N, false, false>);
+  auto kern = a.pd ? (a.Tz ? (a.keep ? grad_sweep_kernel<R, N, true, true, true>
+                                     : grad_sweep_kernel<R, N, true, false, true>)
+                           : (a.keep ? grad_sweep_kernel<R, N, true, true, false>
+                                     : grad_sweep_kernel<R, N, true, false, false>))
+                   : (a.keep ? grad_sweep_kernel<R, N, false, true, false>
+                             : grad_sweep_kernel<R, N, false, false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t blocks = B * a.S;
@@ -412,7 +419,6 @@ template <typename R>
 static cudaError_t grad_sweep_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
                                 const void* Pck, const void* Rck, const double2* tau,
                                 double* grad, int64_t* status, double2* Tz, const void* keep, cudaStream_t s) {
-  if (keep && p.pd && Tz) return cudaErrorInvalidValue;   // kept states carry no boundary traces
   GradArgs<R> a;
   a.keep = (const cplx<R>*)keep;
   a.fps = p.fps > 0 ? p.fps : (int64_t)t->K * t->digits;

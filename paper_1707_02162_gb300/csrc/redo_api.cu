@@ -915,9 +915,9 @@ static PhaseGradLayout phase_grad_layout(const redo_table* t, int64_t B, int64_t
   L.ut_off = L.zf_off + ph * up((size_t)B * t->N * sizeof(double2));
   L.tz_off = L.ut_off + ph * up((size_t)B * t->N * t->N * sizeof(double2));
   L.total = L.tz_off + ph * up((size_t)B * (M + 1) * t->K * sizeof(double2));
-  if (!phase && t->N <= kSmallN) {
-    // per-pulse drift at N <= 64: every forward state kept when they fit in 24 GiB (the sweep
-    // then multiplies only the costates), as in the plain gradient
+  if (t->N <= kSmallN) {
+    // N <= 64: every forward state kept when they fit in 24 GiB (the sweep then multiplies only
+    // the costates), as in the plain gradient
     const size_t el = prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t keep_bytes = (size_t)L.g.p.B * L.g.p.S * L.g.p.seg_len * t->N * t->N * el;
     if (M > 0 && keep_bytes <= ((size_t)24 << 30)) {
@@ -986,14 +986,15 @@ redo_status redo_fidelity_grad_phase(const redo_table* t, const int32_t* q, cons
       return cuda_error(e, "large-N phase gradient");
     return REDO_OK;
   }
-  if ((e = launch_chain_segments(t, q, L.g.p, prec, w + L.g.seg_off, dev_status, s)) != cudaSuccess)
+  void* keep = L.g.keep ? w + L.g.keep_off : nullptr;
+  if ((e = launch_chain_segments(t, q, L.g.p, prec, w + L.g.seg_off, dev_status, s, keep)) != cudaSuccess)
     return cuda_error(e, "gradient segments");
   if ((e = launch_grad_scan(t, B, L.g.p.S, prec, w + L.g.seg_off, ut, 1, w + L.g.pck_off, w + L.g.rck_off, tau,
                             F_out, s)) != cudaSuccess)
     return cuda_error(e, "gradient checkpoints");
   if (M > 0) {
     if ((e = launch_grad_sweep(t, q, L.g.p, prec, w + L.g.pck_off, w + L.g.rck_off, tau, grad_amp, dev_status, s,
-                               tz)) != cudaSuccess)
+                               tz, keep)) != cudaSuccess)
       return cuda_error(e, "gradient sweep");
     if ((e = launch_phase_grad_finish(t->N, B, M, t->K, tz, tau, grad_phase, s)) != cudaSuccess)
       return cuda_error(e, "phase gradient");
