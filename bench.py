@@ -21,6 +21,7 @@ import multiprocessing as mp
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -62,7 +63,10 @@ class ClockSampler:
     def __init__(self, gpu_index=0):
         self.proc = None
         self.gpu_index = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples go to REDO_CLOCKS_DIR (default: the system temporary directory); the JSON
+        # line carries their summary
+        out_dir = os.environ.get("REDO_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
