@@ -866,14 +866,7 @@ polar_ns_kernel(const cplx<Rin>* __restrict__ in, cplx<Rc>* __restrict__ out, in
   cplx<Rc> Y[TM][TM];
   const int ty = lt / MM::TX, tx = lt % MM::TX;
   for (int it = 0; it < iters; ++it) {
-    for (int i = lt; i < N2; i += MM::THREADS) {
-      const int r = i / N, c = i % N;
-      const cplx<Rc> v = P[c * N + r];
-      Q[i] = cmake<Rc>(v.x, -v.y);                       // Q = P^dag
-    }
-    __syncthreads();
-    MM::run(Q, P, lt, Y);                                // G = P^dag P
-    __syncthreads();
+    MM::run_adj(P, P, lt, Y);                            // G = P^dag P (P read in column order)
 #pragma unroll
     for (int a = 0; a < TM; ++a)
 #pragma unroll
