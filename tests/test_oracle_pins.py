@@ -194,6 +194,31 @@ def test_commuting_case_has_no_splitting_error():
     assert np.abs(U - O.expm_hermitian(Htot, dt)).max() < 1e-12
 
 
+def test_per_instance_diagonal_drift_enters_through_the_drift_factor_only():
+    # Each warm-start instance has its own diagonal drift h_b (offsets and couplings).  The
+    # operator table does not depend on H0, the drift factor is the closed form
+    # diag(exp(-i dt h_b)), and the chain with that factor is the split model at the level
+    # values: so one table built with H0 = 0 serves every instance.
+    w = inputs.config(4, n_qubits=3, B=2, M=12, seed=11, base=16, digits=2)
+    h = inputs.drift_diagonals(w)
+    T0, D0 = O.build_table(np.zeros_like(w.H0), w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
+    assert np.abs(D0 - np.eye(8)).max() < 1e-15
+    q, _, _ = O.quantize(w.u, w.lo, w.hi, w.levels)
+    dig = O.level_digits(q, w.base, w.digits)
+    for b in range(2):
+        H0b = np.diag(h[b]).astype(complex)
+        assert np.abs(H0b - inputs.drift_zz(3, w.extra["nu"][b], w.extra["J"][b])).max() == 0.0
+        Tb, Db = O.build_table(H0b, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits)
+        assert np.array_equal(Tb, T0)
+        assert np.abs(Db - np.diag(np.exp(-1j * w.dt * h[b]))).max() < 1e-14
+        uh = O.level_values(q[b], w.lo, w.hi, w.levels)
+        ref = np.eye(8, dtype=complex)
+        for n in range(w.M):
+            ref = O.split_step(H0b, w.Hk, w.dt, uh[n]) @ ref
+        assert np.abs(O.propagate(T0, Db, dig[b]) - ref).max() < 1e-12
+    assert np.abs(h[0] - h[1]).max() > 1e3         # the instances really differ
+
+
 def test_dirac_frame_step_equals_split_step():
     # Section III: U_n = V(dt) exp(-i Omega dt S~), S~ = V^dag(dt) S V(dt)
     rng = np.random.default_rng(3)
