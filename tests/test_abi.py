@@ -63,6 +63,31 @@ def test_host_validation_without_device(lib):
     assert lib.redo_propagate(None, None, 1, 1, 0, 0, None, None, None, None, None, 0, None, None) == 1
     assert lib.redo_quantize(None, None, 1, 1, None, None, None) == 1
     assert lib.redo_table_free(None) == 0
+    # per-pulse drift, amplitude/phase and time-split entry points: no table, bad sizes
+    n = ctypes.c_size_t()
+    assert lib.redo_propagate_drift(None, None, None, 1, 1, 0, 0, None, None, None, None, None, 0, None, None) == 1
+    assert lib.redo_propagate_drift_workspace(None, 1, 1, 0, 0, ctypes.byref(n)) == 1
+    assert lib.redo_fidelity_grad_drift(None, None, None, 1, 1, None, 0, 0, 0, None, None, None, 0, None, None) == 1
+    assert lib.redo_fidelity_grad_drift_workspace(None, 1, 1, 0, 0, ctypes.byref(n)) == 1
+    assert lib.redo_propagate_phase(None, None, None, 1, 1, 0, 0, None, None, None, None, None, 0, None, None) == 1
+    assert lib.redo_fidelity_grad_phase(None, None, None, 1, 1, None, 0, 0, 0, None, None, None, None, 0, None,
+                                        None) == 1
+    assert lib.redo_batched_product(0, 1, dummy, 0, 0, dummy, 0, 0, dummy, None) == 1
+    assert lib.redo_batched_product(8, -1, dummy, 0, 0, dummy, 0, 0, dummy, None) == 1
+    assert lib.redo_batched_product(8, 0, dummy, 0, 0, dummy, 0, 0, dummy, None) == 0     # nothing to do
+
+
+class _FakeTable:
+    N = 4
+    device = "cpu"
+
+
+def test_propagation_wrappers_take_one_target():
+    import numpy as np
+    t = redo._single_target(_FakeTable(), np.eye(4))
+    assert tuple(t.shape) == (4, 4)
+    with pytest.raises(ValueError):
+        redo._single_target(_FakeTable(), np.stack([np.eye(4)] * 2))
 
 
 def test_build_flags_are_sm103a():
