@@ -205,7 +205,7 @@ def test_bad_level_index_is_counted_not_faulted():
 
 
 def test_propagate_full_size_batched_sampled_fp64_fp32():
-    # BASELINE workload shape (N=64, K=12, B=256, M=2000) in the launch
+    # the benchmark workload shape (N=64, K=12, B=256, M=2000) in the launch
     # configuration the benchmark times; the oracle checks two sampled pulses.
     w = inputs.config(1)
     t = _table(w)
