@@ -32,6 +32,9 @@ Functions and the passage each one follows:
   derivative is taken from the definitions, see its docstring).
 * :func:`state_transfer_gradient` -- the state-to-state fidelity ``|<psi_T|U|psi0>|^2``
   and its GRAPE gradient, from the same definitions.
+* :func:`grape_update` / :func:`grape_step_scale` / :func:`grape_adam_update` --
+  the control update of the GRAPE loop (Section III, Fig. fc; the rule is this
+  module's reading: clipped ascent with per-pulse step factors, or Adam).
 * :func:`polar_unitary` -- polar factor ``P (P^dag P)^(-1/2)``.
 * :func:`half_drift` / :func:`strang_step_propagator` / :func:`propagate_strang`
   / :func:`strang_split_step` / :func:`simulate_expectation_strang` -- the
@@ -62,7 +65,7 @@ __all__ = [
     "quantize", "level_digits", "level_values", "table_thetas", "expm_pade13", "expm_hermitian",
     "build_table", "step_factors", "step_propagator", "propagate", "fidelity", "trace_overlap",
     "grape_gradient", "polar_unitary", "simulate_expectation", "exact_step", "split_step",
-    "plan_digits", "mlp_init", "mlp_forward", "mlp_backward", "adam_step", "gelu", "gelu_grad",
+    "plan_digits", "grape_update", "grape_step_scale", "grape_adam_update", "mlp_init", "mlp_forward", "mlp_backward", "adam_step", "gelu", "gelu_grad",
 ]
 
 
@@ -554,6 +557,66 @@ def state_transfer_gradient(T, D, Hk, dt, digits_bm, psi0, psiT):
             da = -1j * dt * complex(bra @ (Lsuf[n + 1] @ Ak[k] @ Hk[k] @ Bk[k] @ X[n] @ psi0))
             g[n, k] = 2.0 * (np.conj(a) * da).real
     return F, g
+
+
+# ---------------------------------------------------------------------------
+# GRAPE update (Section III, flowchart Fig. fc; the paper leaves the rule open)
+# ---------------------------------------------------------------------------
+# The flowchart evaluates the fidelity and its gradient with REDO propagators,
+# changes the controls, and repeats.  It fixes neither the step rule nor how the
+# controls are kept inside the coefficient range.  The reading taken here: plain
+# ascent along dF/du with a per-pulse step factor (halved when a pulse's
+# fidelity fell, grown by 1.1 up to 8 otherwise), or Adam moments per
+# coefficient; either way the new coefficient is clipped to the ends [lo_k,
+# hi_k] of its level grid, so that it always has a level.
+
+def grape_update(u, g, step, scale, lo, hi):
+    """One ascent step ``u_bnk <- clip(u_bnk + step * s_b * g_bnk, lo_k, hi_k)``.
+
+    ``u``, ``g``: (B, M, K); ``scale``: (B,) per-pulse factors s_b (None: all 1);
+    ``lo``, ``hi``: (K,).  Returns the new array (the input is not modified).
+    """
+    u = np.asarray(u, dtype=np.float64)
+    B, M, K = u.shape
+    out = np.empty_like(u)
+    for b in range(B):
+        s_b = 1.0 if scale is None else float(scale[b])
+        for k in range(K):
+            x = u[b, :, k] + step * s_b * g[b, :, k]
+            out[b, :, k] = np.minimum(np.maximum(x, lo[k]), hi[k])
+    return out
+
+
+def grape_step_scale(scale, F, F_prev):
+    """Per-pulse step factors for the next ascent step: ``s_b / 2`` where the
+    fidelity fell (``F_b < F_prev_b``), else ``min(1.1 s_b, 8)``; unchanged before
+    the first comparison (``F_prev`` None)."""
+    scale = np.asarray(scale, dtype=np.float64)
+    if F_prev is None:
+        return scale.copy()
+    out = np.empty_like(scale)
+    for b in range(scale.shape[0]):
+        out[b] = scale[b] * 0.5 if F[b] < F_prev[b] else min(scale[b] * 1.1, 8.0)
+    return out
+
+
+def grape_adam_update(u, g, m, v, t, lr, lo, hi, beta1=0.9, beta2=0.999, eps=1e-12):
+    """One Adam ascent step (Kingma & Ba 2015, ascending instead of descending) on
+    every coefficient, step number ``t >= 1``:
+    ``m <- b1 m + (1-b1) g``, ``v <- b2 v + (1-b2) g^2``,
+    ``u <- clip(u + lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps), lo_k, hi_k)``.
+    Returns ``(u, m, v)`` (new arrays)."""
+    u = np.asarray(u, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    x = u + lr * m_hat / (np.sqrt(v_hat) + eps)
+    K = u.shape[-1]
+    out = np.empty_like(u)
+    for k in range(K):
+        out[..., k] = np.minimum(np.maximum(x[..., k], lo[k]), hi[k])
+    return out, m, v
 
 
 # ---------------------------------------------------------------------------

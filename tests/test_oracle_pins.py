@@ -639,6 +639,98 @@ def test_adam_first_step_is_signed_lr():
     assert np.allclose(p2, p - 0.01 * np.sign(g), atol=1e-7)
 
 
+# ---------------------------------------------------------------- GRAPE update (Fig. fc)
+
+def test_grape_update_one_step_closed_form():
+    # dyadic values: every product and sum below is exact in binary floating point
+    u = np.full((2, 3, 2), 0.25)
+    g = np.array([0.125, -0.0625])[None, None, :] * np.ones((2, 3, 2))
+    lo, hi = np.array([-1.0, -1.0]), np.array([1.0, 1.0])
+    out = O.grape_update(u, g, 2.0, np.array([1.0, 0.5]), lo, hi)
+    assert np.array_equal(out[0, :, 0], np.full(3, 0.5)) and np.array_equal(out[0, :, 1], np.full(3, 0.125))
+    assert np.array_equal(out[1, :, 0], np.full(3, 0.375)) and np.array_equal(out[1, :, 1], np.full(3, 0.1875))
+    # no scale means a factor of one for every pulse; the input is left alone
+    assert np.array_equal(O.grape_update(u, g, 2.0, None, lo, hi), O.grape_update(u, g, 2.0, np.ones(2), lo, hi))
+    assert np.array_equal(u, np.full((2, 3, 2), 0.25))
+
+
+def test_grape_update_clips_to_each_terms_grid():
+    rng = np.random.default_rng(4)
+    lo, hi = np.array([-3.0, 0.0, 10.0]), np.array([3.0, 1.0, 20.0])
+    u = rng.uniform(lo, hi, size=(4, 50, 3))
+    g = rng.standard_normal((4, 50, 3))
+    out = O.grape_update(u, g, 1e3, None, lo, hi)           # a huge step lands every entry on an end
+    expect = np.where(g > 0, hi[None, None, :], lo[None, None, :])
+    assert np.array_equal(out, expect)
+    small = O.grape_update(u, g, 1e-3, None, lo, hi)        # a tiny step moves along g, inside the grid
+    inside = (u + 1e-3 * g > lo) & (u + 1e-3 * g < hi)
+    assert np.array_equal(small[inside], (u + 1e-3 * g)[inside])
+
+
+def test_grape_step_scale_schedule():
+    s = np.array([1.0, 1.0, 7.5, 2.0])
+    assert np.array_equal(O.grape_step_scale(s, np.array([0.1, 0.2, 0.3, 0.4]), None), s)
+    out = O.grape_step_scale(s, np.array([0.5, 0.1, 0.9, 0.4]), np.array([0.4, 0.2, 0.8, 0.4]))
+    # rose: x1.1; fell: halved; capped at 8; equal counts as not fallen
+    assert np.allclose(out, [1.1, 0.5, 8.0, 2.2], rtol=0, atol=1e-15)
+
+
+def test_grape_adam_first_and_third_step_bias_correction():
+    lo, hi = np.array([-10.0]), np.array([10.0])
+    b1, b2, eps, lr = 0.9, 0.999, 1e-12, 0.01
+    gs = [np.array([[[0.3]], [[-2.0]]]), np.array([[[0.1]], [[-1.0]]]), np.array([[[-0.2]], [[4.0]]])]
+    u = np.zeros((2, 1, 1))
+    m = np.zeros_like(u)
+    v = np.zeros_like(u)
+    u1, m, v = O.grape_adam_update(u, gs[0], m, v, 1, lr, lo, hi, b1, b2, eps)
+    # step 1: the bias-corrected moments are g and g^2, so the step is lr * g / (|g| + eps)
+    assert np.allclose(u1, lr * gs[0] / (np.abs(gs[0]) + eps), rtol=1e-14, atol=0)
+    u2, m, v = O.grape_adam_update(u1, gs[1], m, v, 2, lr, lo, hi, b1, b2, eps)
+    u3, m, v = O.grape_adam_update(u2, gs[2], m, v, 3, lr, lo, hi, b1, b2, eps)
+    # step 3: bias-corrected moments are the normalised exponentially weighted means
+    #   m_hat = (b1^2 g1 + b1 g2 + g3) / (1 + b1 + b1^2),  v_hat likewise with b2 and g^2
+    g1, g2, g3 = gs
+    mh = (b1 ** 2 * g1 + b1 * g2 + g3) / (1 + b1 + b1 ** 2)
+    vh = (b2 ** 2 * g1 ** 2 + b2 * g2 ** 2 + g3 ** 2) / (1 + b2 + b2 ** 2)
+    assert np.allclose(u3 - u2, lr * mh / (np.sqrt(vh) + eps), rtol=1e-12, atol=0)
+
+
+def test_grape_adam_constant_gradient_steps_by_lr_and_clips():
+    lo, hi = np.array([-0.05]), np.array([0.05])
+    u = np.zeros((1, 3, 1))
+    g = np.array([1e-7, -3.0, 5e4]).reshape(1, 3, 1)
+    m = np.zeros_like(u)
+    v = np.zeros_like(u)
+    for t in range(1, 8):
+        u_prev = u
+        u, m, v = O.grape_adam_update(u, g, m, v, t, 0.01, lo, hi)
+        # a constant gradient has bias-corrected moments g and g^2 at every step
+        expect = np.clip(u_prev + 0.01 * g / (np.abs(g) + 1e-12), -0.05, 0.05)
+        assert np.allclose(u, expect, rtol=1e-9, atol=0)
+    assert u[0, 1, 0] == -0.05 and u[0, 2, 0] == 0.05
+
+
+def test_grape_ascent_reaches_a_one_qubit_target():
+    # the update ascends the oracle's gradient: a Hadamard-like rotation from a random start
+    H0 = 2 * np.pi * 300.0 * SZ / 2
+    Hk = np.stack([SX / 2, SY / 2])
+    dt, L, M = 1e-5, 4096, 10
+    Om = 2 * np.pi * 1e4
+    lo, hi = np.array([-Om, -Om]), np.array([Om, Om])
+    T, D = O.build_table(H0, Hk, dt, lo, hi, L, 64, 2)
+    UT = O.expm_hermitian((SX + SZ) / math.sqrt(2), math.pi / 2)
+    u = np.random.default_rng(3).uniform(-Om, Om, size=(1, M, 2)) * 0.3
+    scale, F_prev, hist = np.ones(1), None, []
+    for _ in range(30):
+        q, _, _ = O.quantize(u, lo, hi, L)
+        F, g = O.grape_gradient(T, D, Hk, dt, O.level_digits(q, 64, 2)[0], UT)
+        hist.append(F)
+        scale = O.grape_step_scale(scale, np.array([F]), F_prev)
+        F_prev = np.array([F])
+        u = O.grape_update(u, g[None], 3e9, scale, lo, hi)
+    assert hist[0] < 0.01 and hist[-1] > 0.9999
+
+
 # ---------------------------------------------------------------- amplitude/phase controls
 
 def _two_species():
