@@ -33,17 +33,33 @@ static redo_status scratch_for_current_device(void** out) {
   return REDO_OK;
 }
 
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Symmetric-split tables: the pulse products are conjugated by the half drift,
+// D_h (U_M ... U_1) D_h^dag, into B FP64 matrices (plus as many for the dense
+// product's intermediate when H0 is not diagonal), as redo_propagate does.
+static size_t strang_scratch(const redo_table* t, int64_t B) {
+  if (!t->strang) return 0;
+  const size_t m = up256((size_t)B * t->N * t->N * sizeof(double2));
+  return t->h0_diagonal ? m : 2 * m;
+}
+
+static size_t scratch_need(const redo_table* t, const ChainPlan& p, int prec, int64_t B) {
+  return up256(chain_workspace_bytes(t, p, prec)) + strang_scratch(t, B);
+}
+
 // Same segmented plan as the allocating path, with the number of segments per
-// pulse lowered until segment products and pulse products fit the array.
+// pulse lowered until segment products, pulse products and (symmetric split)
+// the conjugated products fit the array.
 static bool plan_fits(const redo_table* t, int64_t B, int64_t M, int prec, ChainPlan* out) {
   ChainPlan p = plan_chain(t, B, M, prec);
-  while (chain_workspace_bytes(t, p, prec) > (size_t)REDO_NOALLOC_SCRATCH_BYTES && p.S > 1) {
+  while (scratch_need(t, p, prec, B) > (size_t)REDO_NOALLOC_SCRATCH_BYTES && p.S > 1) {
     int64_t S = p.S - 1;
     p.seg_len = p.F > 0 ? (p.F + S - 1) / S : 0;
     p.S = p.seg_len > 0 ? (p.F + p.seg_len - 1) / p.seg_len : 1;
   }
   *out = p;
-  return chain_workspace_bytes(t, p, prec) <= (size_t)REDO_NOALLOC_SCRATCH_BYTES;
+  return scratch_need(t, p, prec, B) <= (size_t)REDO_NOALLOC_SCRATCH_BYTES;
 }
 
 }  // namespace redo
@@ -72,7 +88,7 @@ extern "C" redo_status redo_propagate_noalloc(const redo_table* t, const int32_t
                      "B=%lld pulses of N=%d need %zu scratch bytes; redo_propagate_noalloc holds "
                      "at most %zu (REDO_NOALLOC_SCRATCH_BYTES): use fewer pulses per call or "
                      "redo_propagate with a workspace",
-                     (long long)B, t->N, chain_workspace_bytes(t, p, prec),
+                     (long long)B, t->N, scratch_need(t, p, prec, B),
                      (size_t)REDO_NOALLOC_SCRATCH_BYTES);
   void* scratch = nullptr;
   redo_status st = scratch_for_current_device(&scratch);
@@ -81,13 +97,25 @@ extern "C" redo_status redo_propagate_noalloc(const redo_table* t, const int32_t
   const size_t el = prec == REDO_FP64 ? sizeof(double2) : sizeof(float2);
   const size_t n2 = (size_t)t->N * t->N;
   char* seg = (char*)scratch;
-  char* prod = seg + (((size_t)p.B * p.S * n2 * el + 255) & ~(size_t)255);
+  char* prod = seg + up256((size_t)p.B * p.S * n2 * el);
   cudaError_t e;
   if ((e = launch_chain_segments(t, q, p, prec, seg, dev_status, s)) != cudaSuccess)
     return cuda_error(e, "chain segments");
   if ((e = launch_chain_combine(t, p, prec, seg, prod, dev_status, s)) != cudaSuccess)
     return cuda_error(e, "chain combine");
-  if ((e = launch_finalize(t, B, prec, prod, U_out, (const double2*)U_target, F_out,
+  const void* fin = prod;
+  int fin_prec = prec;
+  if (t->strang) {
+    // S_M ... S_1 = D_h (U_M ... U_1) D_h^dag, D_h = exp(-i dt/2 H0)
+    char* sb = (char*)scratch + up256(chain_workspace_bytes(t, p, prec));
+    const size_t m = up256((size_t)B * n2 * sizeof(double2));
+    if ((e = launch_half_drift_conj(t, prec, prod, B, 0, (double2*)sb,
+                                    t->h0_diagonal ? nullptr : (double2*)(sb + m), s)) != cudaSuccess)
+      return cuda_error(e, "half-drift conjugation");
+    fin = sb;
+    fin_prec = REDO_FP64;
+  }
+  if ((e = launch_finalize(t, B, fin_prec, fin, U_out, (const double2*)U_target, F_out,
                            (double2*)tau_out, s)) != cudaSuccess)
     return cuda_error(e, "finalize");
   return REDO_OK;

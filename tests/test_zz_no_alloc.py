@@ -59,6 +59,34 @@ def test_noalloc_matches_workspace_path_two_calls(redo, prec):
     t.close()
 
 
+@pytest.mark.parametrize("dense_drift", [False, True])
+def test_noalloc_symmetric_split_matches_workspace_path(redo, dense_drift):
+    # A symmetric-split table conjugates the pulse products by the half drift; with a drift
+    # that is not diagonal that takes a second FP64 buffer inside the scratch array.
+    w = inputs.config(0, B=3, M=40, base=16, digits=2)
+    if dense_drift:
+        w.H0 = w.H0 + 2 * np.pi * 800.0 * inputs.embed({1: inputs.PAULI["X"] / 2}, 3)
+    dev = torch.device("cuda")
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, strang=True)
+    plain = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+    target = torch.as_tensor(w.target, device=dev)
+    q = t.quantize(w.u)
+    for prec in ("fp64", "fp32"):
+        for _ in range(2):
+            Ua, Fa, ta = _outputs(redo, w.B, w.N, dev)
+            Ub, Fb, tb = _outputs(redo, w.B, w.N, dev)
+            redo.redo_propagate(t.handle, q, prec, Ua, target, Fa, ta, t.workspace(w.B, w.M, prec))
+            redo.redo_propagate_noalloc(t.handle, q, prec, Ub, target, Fb, tb)
+            torch.cuda.synchronize()
+            assert (Ua - Ub).abs().max().item() < TOL[prec]
+            assert (Fa - Fb).abs().max().item() < 1e-6
+        # and it is the symmetric chain, not the drift-first one
+        Uc, _, _ = plain.propagate(q, prec)
+        assert (Uc - Ub).abs().max().item() > 1e-4
+    t.close()
+    plain.close()
+
+
 def test_noalloc_rejects_requests_beyond_its_scratch(redo):
     w = inputs.config(1, B=1, M=4)
     t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
