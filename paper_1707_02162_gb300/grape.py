@@ -83,7 +83,8 @@ class GrapeResult:
 
 def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, prec="fp64",
           checkpoint_every=0, threshold: float | None = None, adaptive: bool = True,
-          optimizer: str = "gd", lr_decay: float = 150.0, psi0=None, drift=None) -> GrapeResult:
+          optimizer: str = "gd", lr_decay: float = 150.0, psi0=None, drift=None,
+          on_iter=None, reunit_every: int = 0) -> GrapeResult:
     """Gradient ascent on the fidelity (the paper does not specify the update rule).
 
     ``optimizer="gd"``: ``u <- clamp(u + step * dF/du)``; with ``adaptive`` the
@@ -94,7 +95,10 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
     state ([N] or [B][N]) and the objective is the state fidelity |<target| U |psi0>|^2
     (redo_state_grad: matrix-vector sweeps instead of propagators).  With ``drift`` ([B][N], rad/s)
     every pulse carries its own diagonal drift (redo_fidelity_grad_drift; the table's own drift,
-    usually zero then, is applied as well).
+    usually zero then, is applied as well).  ``on_iter(it, u, F)``, if given, is called after each
+    update with the iteration index, the updated coefficients (device, not copied) and that
+    iteration's fidelities (host).  ``reunit_every`` (unitary fidelity without a per-pulse drift; equal
+    to ``checkpoint_every``) re-unitarises every checkpoint segment of the reduced-precision chains.
     """
     u = u0.clone().contiguous()
     B, M, K = u.shape
@@ -129,7 +133,8 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
         elif drift is not None:
             redo.redo_fidelity_grad_drift(table.handle, q, drift, target, prec, checkpoint_every, F, g, ws)
         else:
-            redo.redo_fidelity_grad(table.handle, q, target, prec, checkpoint_every, F, g, ws)
+            redo.redo_fidelity_grad(table.handle, q, target, prec, checkpoint_every, F, g, ws,
+                                    reunit_every=reunit_every)
         Fh = F.cpu()
         res.F_history.append(Fh.clone())
         if threshold is not None:
@@ -140,6 +145,8 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
         if optimizer == "adam":
             redo.redo_grape_adam_step(table.handle, u, g, m_, v_, it + 1, step / (1.0 + it / lr_decay))
             res.iterations = it + 1
+            if on_iter is not None:
+                on_iter(it, u, Fh)
             continue
         if adaptive and prev_F is not None:
             worse = Fh < prev_F
@@ -148,6 +155,8 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
         prev_F = Fh
         redo.redo_grape_step(table.handle, u, g, step, scale_d if adaptive else None)
         res.iterations = it + 1
+        if on_iter is not None:
+            on_iter(it, u, Fh)
     res.u = u
     res.reached = reached
     return res
