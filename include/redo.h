@@ -197,6 +197,56 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
                            size_t workspace_bytes, int64_t* dev_status, void* stream);
 
 /*
+ * redo_propagate_steps -- the per-step propagators U_n themselves (Section III's step formula,
+ * U_n = E_{K-1,n} ... E_{0,n} D, each E_k assembled from table operators as in Eq. exp2prod),
+ * for callers that need every step rather than the chain: e.g. a GRAPE variant of their own,
+ * or checking a pulse step by step.
+ *  q           device int32 [B][M][K] levels from redo_quantize.
+ *  prec        REDO_FP64 or REDO_FP32 (the latter needs REDO_TABLE_FP32); N <= 64.
+ *  U_steps     device complex128 [B][M][N][N]: U_steps[b][n] = U_{n+1} of pulse b (step n applied
+ *              at time index n, the rightmost factor of the chain for n = 0).  With a
+ *              REDO_TABLE_STRANG table these are the symmetric steps D_h E_{K-1} ... E_0 D_h.
+ *  workspace   >= redo_propagate_steps_workspace() bytes (zero for REDO_FP64 with a diagonal
+ *              or no drift: then NULL is accepted), 256-byte aligned.
+ * Level indices outside [0, levels) count in REDO_STATUS_BADINDEX and are replaced by 0.
+ * Errors: REDO_ERR_INVALID, REDO_ERR_UNSUPPORTED (N > 64, other precisions), REDO_ERR_CUDA.
+ */
+redo_status redo_propagate_steps_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                           size_t* bytes);
+redo_status redo_propagate_steps(const redo_table* t, const int32_t* q, int64_t B, int64_t M, redo_precision prec,
+                                 void* U_steps, void* workspace, size_t workspace_bytes, int64_t* dev_status,
+                                 void* stream);
+
+/*
+ * redo_reunitarize -- Newton-Schulz steps towards the unitary polar factor, the
+ * re-unitarisation the reduced-precision chains apply every reunit_every steps (the paper's
+ * chains are exactly unitary; the step keeps finite-precision products on the unitary group):
+ *     P <- P (3 I - P^dag P) / 2,   `iters` times,
+ * which converges quadratically to P (P^dag P)^(-1/2) when ||P^dag P - I|| < 1 (one step maps
+ * an error e of P^dag P - I to about 3e^2/4).
+ *  N        matrix dimension, a power of two, 2 <= N <= 64.
+ *  prec     arithmetic of the steps, REDO_FP64 or REDO_FP32.
+ *  P_in     device complex128 [count][N][N];  U_out device complex128 [count][N][N] (may equal P_in).
+ * Errors: REDO_ERR_INVALID, REDO_ERR_UNSUPPORTED, REDO_ERR_CUDA.  Asynchronous on `stream`.
+ */
+redo_status redo_reunitarize(int32_t N, int64_t count, redo_precision prec, const void* P_in, void* U_out,
+                             int32_t iters, void* stream);
+
+/*
+ * redo_plan -- the cost model of Section II (host only, no device work).  For a coefficient range
+ * [0, omega_max] coarse grained to a grain eps in base b (Eq. cgrain): l is the largest integer
+ * with b^l <= eps (b^l = eps when eps is a power of b), m the smallest with b^(m+1) > omega_max;
+ * then p = m - l products per coefficient and s = (b - 1)(m - l + 1) stored operators (process 1,
+ * identities not counted).  The worked example of Section II (eps = 1, omega_max = 2.6e5, b = 64)
+ * gives l = 0, m = 2, p = 2, s = 189.  Comparisons use a relative slack of 1e-12 on eps so that a
+ * decimal eps that is a power of b (1e-4 with b = 100) counts as equal.
+ * Any output pointer may be NULL.  Errors: REDO_ERR_INVALID (non-positive or non-finite inputs,
+ * eps > omega_max, base < 2).
+ */
+redo_status redo_plan(double omega_max, double eps, int32_t base, int32_t* l, int32_t* m, int32_t* p,
+                      int64_t* s);
+
+/*
  * redo_propagate_noalloc -- redo_propagate for callers that cannot allocate
  * device memory.  The paper has no counterpart; this is a deployment variant.
  *
@@ -209,14 +259,22 @@ redo_status redo_propagate(const redo_table* t, const int32_t* q, int64_t B, int
  * until the process exits.  It calls no cudaMalloc, cudaFree or other
  * allocating routine.  The caller still passes inputs and outputs, with the
  * same meaning, layout and status words as redo_propagate (REDO_FP64 and
- * REDO_FP32 only).
+ * REDO_FP32 only, no re-unitarisation, N <= 64), symmetric-split tables
+ * included.
  *
  *  - Requests whose segment and pulse products cannot fit the array even with
- *    one segment per pulse (about B*N*N*16 bytes for FP64, half for FP32)
- *    return REDO_ERR_INVALID with a message naming the limit.
+ *    one segment per pulse return REDO_ERR_INVALID with a message naming the
+ *    limit.  With one segment per pulse the array holds a segment product and
+ *    a pulse product per pulse: about 2*B*N*N*16 bytes for FP64 (half that for
+ *    FP32), so at most 256 FP64 pulses of N = 64.  A REDO_TABLE_STRANG table
+ *    adds B*N*N*16 bytes for the conjugated products (twice that when H0 is
+ *    not diagonal).
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    life of the process; make that first call before any stream capture.
+ *    cudaDeviceReset (or anything else that destroys the device's primary
+ *    context) invalidates the kept address, and the library cannot see that
+ *    happen: do not call this entry point again on a device after resetting it.
  *  - All calls on a device share the one array and it keeps the previous
  *    call's contents (nothing in it needs to start at zero).  Calls whose
  *    kernels overlap on the GPU -- on different streams or from different host
@@ -245,6 +303,12 @@ redo_status redo_propagate_noalloc(const redo_table* t, const int32_t* q, int64_
  *  prec          REDO_FP64 or REDO_FP32, or REDO_FP16X3 for N >= 128 (products;
  *                traces and tau in FP64).
  *  checkpoint_every  C > 0: forward checkpoints every C steps; 0: automatic.
+ *  reunit_every  R >= 0.  R = 0: none.  R > 0 (requires R = checkpoint_every): every
+ *                checkpoint segment product, the propagator of R consecutive steps, is
+ *                replaced by its polar factor (one Newton-Schulz step in the chain
+ *                precision, as in redo_propagate) before the checkpoints, costates, tau and
+ *                F are formed.  Reduced-precision chains lose norm at ~3e-8 per product; over
+ *                thousands of products that lowers F near 1 by more than 1e-6 unless removed.
  *  F_out         device double [B] or NULL;  grad  device double [B][M][K].
  *  workspace     >= redo_fidelity_grad_workspace() bytes, 256-byte aligned.
  * Method: segment products (one per C steps), prefix checkpoints and suffix
@@ -254,7 +318,7 @@ redo_status redo_propagate_noalloc(const redo_table* t, const int32_t* q, int64_
  */
 redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
                                const void* U_target, int32_t target_batched, redo_precision prec,
-                               int32_t checkpoint_every, double* F_out, double* grad,
+                               int32_t checkpoint_every, int32_t reunit_every, double* F_out, double* grad,
                                void* workspace, size_t workspace_bytes, int64_t* dev_status,
                                void* stream);
 redo_status redo_fidelity_grad_workspace(const redo_table* t, int64_t B, int64_t M,

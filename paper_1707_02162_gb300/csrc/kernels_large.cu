@@ -986,10 +986,19 @@ cudaError_t large_grad_scans_fp32(const redo_table* t, const ChainPlan& p, const
   return large_scans_t<float>(t, p, UT, tb, F_out, (char*)ws, Pck, Rck, tau, s);
 }
 
+cudaError_t large_reunit_segments_fp32(const redo_table* t, const ChainPlan& p, void* ws, cudaStream_t s) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int64_t n2 = (int64_t)t->N * t->N, G = p.B * p.S;
+  const size_t mat = up((size_t)G * n2 * sizeof(float2));
+  // seg, Pck, Rck, then two ping buffers: contiguous scratch for 2G matrices
+  return large_polar_t<float>(t->N, (float2*)ws, G, (float2*)((char*)ws + 3 * mat), s);
+}
+
 template <typename R>
 static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const ChainPlan& p,
                                 const double2* UT, int tb, double* F_out, double* grad, char* ws,
-                                int64_t* status, cudaStream_t s, double2* Tz, double* grad_phase) {
+                                int64_t* status, cudaStream_t s, double2* Tz, double* grad_phase,
+                                bool reunit) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int N = t->N;
   const int64_t n2 = (int64_t)N * N, G = p.B * p.S;
@@ -999,6 +1008,7 @@ static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const Cha
   cplx<R>* pB = (cplx<R>*)(ws + 4 * mat);
   cudaError_t e = large_chain_t<R>(t, q, p, seg, pA, status, s);
   if (e) return e;
+  if (reunit && p.M > 0 && (e = large_polar_t<R>(N, seg, G, pA, s))) return e;
   cplx<R>* Pck;
   cplx<R>* Rck;
   double2* tau;
@@ -1059,10 +1069,10 @@ static cudaError_t large_grad_t(const redo_table* t, const int32_t* q, const Cha
 
 cudaError_t large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
                        const double2* UT, int tb, double* F_out, double* grad, void* ws,
-                       int64_t* status, cudaStream_t s, double2* Tz, double* grad_phase) {
+                       int64_t* status, cudaStream_t s, double2* Tz, double* grad_phase, bool reunit) {
   if (prec == REDO_FP64)
-    return large_grad_t<double>(t, q, p, UT, tb, F_out, grad, (char*)ws, status, s, Tz, grad_phase);
-  return large_grad_t<float>(t, q, p, UT, tb, F_out, grad, (char*)ws, status, s, Tz, grad_phase);
+    return large_grad_t<double>(t, q, p, UT, tb, F_out, grad, (char*)ws, status, s, Tz, grad_phase, reunit);
+  return large_grad_t<float>(t, q, p, UT, tb, F_out, grad, (char*)ws, status, s, Tz, grad_phase, reunit);
 }
 
 // ============================================================================

@@ -846,10 +846,10 @@ cudaError_t launch_chain_combine(const redo_table* t, const ChainPlan& p, int pr
 // P (P^dag P)^(-1/2) when ||P^dag P - I|| < 1; the product chains hand it
 // matrices within ~1e-3 of unitary, so one step leaves ~1e-6 of that.
 // ============================================================================
-template <typename Rin, typename Rc, int N>
+template <typename Rin, typename Rc, int N, typename Rout = Rc>
 __global__ void __launch_bounds__(SmemMM<Rc, N, (N >= 64 ? 4 : (N >= 32 ? 2 : 1)),
                                          (N >= 64 ? 4 : (N >= 32 ? 2 : 1))>::THREADS)
-polar_ns_kernel(const cplx<Rin>* __restrict__ in, cplx<Rc>* __restrict__ out, int iters) {
+polar_ns_kernel(const cplx<Rin>* __restrict__ in, cplx<Rout>* __restrict__ out, int iters) {
   constexpr int TM = (N >= 64 ? 4 : (N >= 32 ? 2 : 1));
   using MM = SmemMM<Rc, N, TM, TM>;
   constexpr int N2 = N * N;
@@ -881,32 +881,35 @@ polar_ns_kernel(const cplx<Rin>* __restrict__ in, cplx<Rc>* __restrict__ out, in
     MM::store(P, lt, Y);
     __syncthreads();
   }
-  for (int i = lt; i < N2; i += MM::THREADS) out[b * N2 + i] = P[i];
+  for (int i = lt; i < N2; i += MM::THREADS) {
+    const cplx<Rc> v = P[i];
+    out[b * N2 + i] = cmake<Rout>((Rout)v.x, (Rout)v.y);
+  }
 }
 
-template <typename Rin, typename Rc, int N>
+template <typename Rin, typename Rc, int N, typename Rout = Rc>
 static cudaError_t polar_n(const void* in, void* out, int64_t count, int iters, cudaStream_t s) {
   constexpr int TM = (N >= 64 ? 4 : (N >= 32 ? 2 : 1));
   using MM = SmemMM<Rc, N, TM, TM>;
   const size_t smem = 2 * sizeof(cplx<Rc>) * N * N;
-  auto kern = polar_ns_kernel<Rin, Rc, N>;
+  auto kern = polar_ns_kernel<Rin, Rc, N, Rout>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (count == 0) return cudaSuccess;
-  kern<<<(unsigned)count, MM::THREADS, smem, s>>>((const cplx<Rin>*)in, (cplx<Rc>*)out, iters);
+  kern<<<(unsigned)count, MM::THREADS, smem, s>>>((const cplx<Rin>*)in, (cplx<Rout>*)out, iters);
   return cudaGetLastError();
 }
 
-template <typename Rin, typename Rc>
+template <typename Rin, typename Rc, typename Rout = Rc>
 static cudaError_t polar_t(int N, const void* in, void* out, int64_t count, int iters,
                            cudaStream_t s) {
   switch (N) {
-    case 2: return polar_n<Rin, Rc, 2>(in, out, count, iters, s);
-    case 4: return polar_n<Rin, Rc, 4>(in, out, count, iters, s);
-    case 8: return polar_n<Rin, Rc, 8>(in, out, count, iters, s);
-    case 16: return polar_n<Rin, Rc, 16>(in, out, count, iters, s);
-    case 32: return polar_n<Rin, Rc, 32>(in, out, count, iters, s);
-    case 64: return polar_n<Rin, Rc, 64>(in, out, count, iters, s);
+    case 2: return polar_n<Rin, Rc, 2, Rout>(in, out, count, iters, s);
+    case 4: return polar_n<Rin, Rc, 4, Rout>(in, out, count, iters, s);
+    case 8: return polar_n<Rin, Rc, 8, Rout>(in, out, count, iters, s);
+    case 16: return polar_n<Rin, Rc, 16, Rout>(in, out, count, iters, s);
+    case 32: return polar_n<Rin, Rc, 32, Rout>(in, out, count, iters, s);
+    case 64: return polar_n<Rin, Rc, 64, Rout>(in, out, count, iters, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -918,6 +921,13 @@ cudaError_t launch_polar(const redo_table* t, int prec_in, int prec_out, const v
   if (!din && dout) return polar_t<float, double>(t->N, in, out, count, iters, s);
   if (!din && !dout) return polar_t<float, float>(t->N, in, out, count, iters, s);
   return cudaErrorInvalidValue;
+}
+
+// complex128 in and out, Newton-Schulz arithmetic in FP64 (prec_arith REDO_FP64) or FP32
+cudaError_t launch_polar_c128(int N, int prec_arith, const double2* in, double2* out, int64_t count, int iters,
+                              cudaStream_t s) {
+  if (prec_arith == REDO_FP64) return polar_t<double, double, double>(N, in, out, count, iters, s);
+  return polar_t<double, float, double>(N, in, out, count, iters, s);
 }
 
 ChainPlan plan_chain_aligned(const redo_table* t, int64_t B, int64_t M, int64_t steps_per_segment,

@@ -1074,7 +1074,7 @@ size_t tc_large_grad_workspace(const redo_table* t, const ChainPlan& p) {
 // of R chains only then reads conj(V) = P^T for its traces from the kept states.
 static cudaError_t tc_large_grad_keep(const redo_table* t, const int32_t* q, const ChainPlan& p,
                                       const ChainPlan& pf, const double2* UT, int tb, double* F_out, double* grad,
-                                      void* ws, int64_t* status, cudaStream_t s) {
+                                      void* ws, int64_t* status, cudaStream_t s, bool reunit) {
   const int N = t->N;
   const int64_t G = p.B * p.S, Gf = pf.B * pf.S;
   const bool split = Gf != G;
@@ -1106,6 +1106,7 @@ static cudaError_t tc_large_grad_keep(const redo_table* t, const int32_t* q, con
     else
       s_to_complex_kernel<float><<<blocks_for(Gf * n2), 256, 0, s>>>(s0, N, Gf, 0, prods, sb);
     if (split && (e = large_pair_products_fp32(halves, seg, G, N, s))) return e;
+    if (reunit && p.M > 0 && (e = large_reunit_segments_fp32(t, p, ws, s))) return e;
   }
   float2 *Pck = nullptr, *Rck = nullptr;
   double2* tau = nullptr;
@@ -1132,10 +1133,10 @@ static cudaError_t tc_large_grad_keep(const redo_table* t, const int32_t* q, con
 
 cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, const double2* UT,
                           int tb, double* F_out, double* grad, void* ws, int64_t* status,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool reunit) {
   {
     const ChainPlan pf = forward_plan(t, p);
-    if (keep_states(t, pf)) return tc_large_grad_keep(t, q, p, pf, UT, tb, F_out, grad, ws, status, s);
+    if (keep_states(t, pf)) return tc_large_grad_keep(t, q, p, pf, UT, tb, F_out, grad, ws, status, s, reunit);
   }
   const int N = t->N;
   const int64_t G = p.B * p.S;
@@ -1170,6 +1171,7 @@ cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan
     } else {
       s_to_complex_kernel<float><<<blocks_for(G * n2), 256, 0, s>>>(fin, N, G, 0, seg, state_bytes(N));
     }
+    if (reunit && p.M > 0 && (e = large_reunit_segments_fp32(t, p, ws, s))) return e;
   }
   float2 *Pck = nullptr, *Rck = nullptr;
   double2* tau = nullptr;

@@ -744,6 +744,112 @@ redo_status redo_propagate_drift(const redo_table* t, const int32_t* q, const do
                         tau_out, workspace, workspace_bytes, dev_status, stream);
 }
 
+// ---------------------------------------------------------------------------
+// Per-step propagators, re-unitarisation, cost model
+// ---------------------------------------------------------------------------
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// FP32 step products (converted to complex128 afterwards) and, for a symmetric-split table with
+// a dense drift, the intermediate of the conjugation.
+static size_t steps_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec, size_t* conj_off) {
+  const size_t count = (size_t)B * M, n2 = (size_t)t->N * t->N;
+  size_t total = prec == REDO_FP32 ? up256(count * n2 * sizeof(float2)) : 0;
+  *conj_off = total;
+  if (t->strang && !t->h0_diagonal) total += up256(count * n2 * sizeof(double2));
+  return total;
+}
+
+static redo_status check_steps(const redo_table* t, redo_precision prec) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (prec != REDO_FP64 && prec != REDO_FP32)
+    return set_error(REDO_ERR_UNSUPPORTED, "per-step propagators in REDO_FP64 or REDO_FP32 only");
+  if (t->N > kSmallN) return set_error(REDO_ERR_UNSUPPORTED, "per-step propagators for N <= 64 only");
+  return check_prec(t, prec);
+}
+
+redo_status redo_propagate_steps_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
+                                           size_t* bytes) {
+  redo_status st = check_steps(t, prec);
+  if (st != REDO_OK) return st;
+  if (!bytes) return set_error(REDO_ERR_INVALID, "bytes is NULL");
+  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
+  size_t off;
+  *bytes = steps_workspace(t, B, M, prec, &off);
+  return REDO_OK;
+}
+
+redo_status redo_propagate_steps(const redo_table* t, const int32_t* q, int64_t B, int64_t M, redo_precision prec,
+                                 void* U_steps, void* workspace, size_t workspace_bytes, int64_t* dev_status,
+                                 void* stream) {
+  redo_status st = check_steps(t, prec);
+  if (st != REDO_OK) return st;
+  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
+  if (B == 0 || M == 0) return REDO_OK;
+  if (!q || !U_steps) return set_error(REDO_ERR_INVALID, "q or U_steps is NULL");
+  size_t conj_off;
+  const size_t need = steps_workspace(t, B, M, prec, &conj_off);
+  if (need > 0 && (!workspace || workspace_bytes < need))
+    return set_error(REDO_ERR_INVALID, "workspace of %zu bytes needed", need);
+  if (need > 0 && ((uintptr_t)workspace & 255) != 0)
+    return set_error(REDO_ERR_INVALID, "workspace not 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  // one segment per time step: segment (b, n) is U_n = E_{K-1} ... E_0 D of pulse b
+  const ChainPlan p = plan_chain_aligned(t, B, M, 1);
+  const int64_t count = B * M;
+  void* seg = prec == REDO_FP64 ? U_steps : workspace;
+  cudaError_t e = launch_chain_segments(t, q, p, prec, seg, dev_status, s);
+  if (e != cudaSuccess) return cuda_error(e, "step products");
+  if (t->strang) {
+    // symmetric step S_n = D_h E_{K-1} ... E_0 D_h = D_h U_n D_h^dag of the folded step
+    double2* tmp = t->h0_diagonal ? nullptr : (double2*)((char*)workspace + conj_off);
+    if ((e = launch_half_drift_conj(t, prec, seg, count, 0, (double2*)U_steps, tmp, s)) != cudaSuccess)
+      return cuda_error(e, "half-drift conjugation");
+  } else if (prec == REDO_FP32) {
+    if ((e = launch_finalize(t, count, REDO_FP32, seg, U_steps, nullptr, nullptr, nullptr, s)) != cudaSuccess)
+      return cuda_error(e, "widen to complex128");
+  }
+  return REDO_OK;
+}
+
+redo_status redo_reunitarize(int32_t N, int64_t count, redo_precision prec, const void* P_in, void* U_out,
+                             int32_t iters, void* stream) {
+  if (N < 2 || N > kSmallN || (N & (N - 1)) != 0)
+    return set_error(REDO_ERR_UNSUPPORTED, "redo_reunitarize takes N a power of two, 2 <= N <= 64 (N=%d)", N);
+  if (prec != REDO_FP64 && prec != REDO_FP32)
+    return set_error(REDO_ERR_UNSUPPORTED, "redo_reunitarize arithmetic is REDO_FP64 or REDO_FP32");
+  if (count < 0 || iters < 0) return set_error(REDO_ERR_INVALID, "negative count or iters");
+  if (count == 0) return REDO_OK;
+  if (!P_in || !U_out) return set_error(REDO_ERR_INVALID, "null matrix pointer");
+  cudaError_t e = launch_polar_c128(N, prec, (const double2*)P_in, (double2*)U_out, count, iters,
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "Newton-Schulz polar steps");
+  return REDO_OK;
+}
+
+redo_status redo_plan(double omega_max, double eps, int32_t base, int32_t* l_out, int32_t* m_out, int32_t* p_out,
+                      int64_t* s_out) {
+  if (!(omega_max > 0.0) || !(eps > 0.0) || !std::isfinite(omega_max) || !std::isfinite(eps))
+    return set_error(REDO_ERR_INVALID, "omega_max and eps must be positive and finite");
+  if (base < 2) return set_error(REDO_ERR_INVALID, "base must be >= 2");
+  if (eps > omega_max) return set_error(REDO_ERR_INVALID, "eps larger than omega_max");
+  const double b = (double)base, rel = 1e-12;
+  // l: the largest integer with b^l <= eps (b^l = eps when eps is a power of b)
+  int l = 0;
+  if (1.0 <= eps * (1.0 + rel)) {
+    while (std::pow(b, l + 1) <= eps * (1.0 + rel)) ++l;
+  } else {
+    while (std::pow(b, l) > eps * (1.0 + rel)) --l;
+  }
+  // m: the smallest integer with b^(m+1) > omega_max
+  int m = l - 1;
+  while (std::pow(b, m + 1) <= omega_max) ++m;
+  if (l_out) *l_out = l;
+  if (m_out) *m_out = m;
+  if (p_out) *p_out = m - l;
+  if (s_out) *s_out = (int64_t)(base - 1) * (int64_t)(m - l + 1);
+  return REDO_OK;
+}
+
 redo_status redo_batched_product(int32_t N, int64_t count, const void* A, int32_t adjA, int32_t A_batched,
                                  const void* B, int32_t adjB, int32_t B_batched, void* C, void* stream) {
   if (N <= 0 || N > kMaxN) return set_error(REDO_ERR_INVALID, "N=%d out of range", N);
@@ -823,11 +929,15 @@ redo_status redo_fidelity_grad_workspace(const redo_table* t, int64_t B, int64_t
 
 redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
                                const void* U_target, int32_t target_batched, redo_precision prec,
-                               int32_t checkpoint_every, double* F_out, double* grad,
+                               int32_t checkpoint_every, int32_t reunit_every, double* F_out, double* grad,
                                void* workspace, size_t workspace_bytes, int64_t* dev_status,
                                void* stream) {
   if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
-  if (B < 0 || M < 0 || checkpoint_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  if (B < 0 || M < 0 || checkpoint_every < 0 || reunit_every < 0)
+    return set_error(REDO_ERR_INVALID, "negative size");
+  if (reunit_every > 0 && reunit_every != checkpoint_every)
+    return set_error(REDO_ERR_INVALID, "reunit_every (%d) must equal checkpoint_every (%d): the segment products "
+                     "of the checkpoints are what is re-unitarised", reunit_every, checkpoint_every);
   if (prec != REDO_FP64 && prec != REDO_FP32 && !(prec == REDO_FP16X3 && t->N > kSmallN))
     return set_error(REDO_ERR_UNSUPPORTED,
                      "the gradient supports REDO_FP64, REDO_FP32 and, for N >= 128, REDO_FP16X3");
@@ -855,17 +965,21 @@ redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B,
     U_target = sb;
   }
   if (t->N > kSmallN) {
+    const bool reunit = reunit_every > 0;
     e = prec == REDO_FP16X3
             ? tc_large_grad(t, q, L.p, (const double2*)U_target, target_batched, F_out, grad,
-                            workspace, dev_status, s)
+                            workspace, dev_status, s, reunit)
             : large_grad(t, q, L.p, prec, (const double2*)U_target, target_batched, F_out, grad,
-                         workspace, dev_status, s);
+                         workspace, dev_status, s, nullptr, nullptr, reunit);
     if (e != cudaSuccess) return cuda_error(e, "large-N gradient");
     return REDO_OK;
   }
   void* keep = L.keep ? w + L.keep_off : nullptr;
   if ((e = launch_chain_segments(t, q, L.p, prec, w + L.seg_off, dev_status, s, keep)) != cudaSuccess)
     return cuda_error(e, "gradient segments");
+  if (reunit_every > 0 && M > 0 &&
+      (e = launch_polar(t, prec, prec, w + L.seg_off, w + L.seg_off, B * L.p.S, 1, s)) != cudaSuccess)
+    return cuda_error(e, "segment re-unitarisation");
   if ((e = launch_grad_scan(t, B, L.p.S, prec, w + L.seg_off, (const double2*)U_target,
                             target_batched, w + L.pck_off, w + L.rck_off, tau, F_out, s)) !=
       cudaSuccess)

@@ -144,6 +144,10 @@ ChainPlan plan_chain_aligned(const redo_table* t, int64_t B, int64_t M, int64_t 
 cudaError_t launch_polar(const redo_table* t, int prec_in, int prec_out, const void* in, void* out,
                          int64_t count, int iters, cudaStream_t s);
 
+// The same Newton-Schulz steps on complex128 matrices (N <= 64), in FP64 or FP32 arithmetic.
+cudaError_t launch_polar_c128(int N, int prec_arith, const double2* in, double2* out, int64_t count, int iters,
+                              cudaStream_t s);
+
 // Tensor-core chains (kernels_tc.cu), N = 64, split-FP16.
 size_t tc_planes_bytes(const redo_table* t);
 cudaError_t launch_build_tc_planes(const redo_table* t, cudaStream_t s);
@@ -212,9 +216,15 @@ cudaError_t large_propagate(const redo_table* t, const int32_t* q, const ChainPl
 size_t large_grad_workspace(const redo_table* t, const ChainPlan& p, int prec);
 // With p.pd set (amplitude/phase calls, segments of whole steps) the reverse sweep also records
 // Tz [B][M+1][K] at the step boundaries and undoes the step diagonals.
+// reunit: every segment product is replaced by its polar factor (one Newton-Schulz step in the
+// chain precision) before the checkpoint and costate scans.
 cudaError_t large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, int prec,
                        const double2* UT, int tb, double* F_out, double* grad, void* ws,
-                       int64_t* status, cudaStream_t s, double2* Tz = nullptr, double* grad_phase = nullptr);
+                       int64_t* status, cudaStream_t s, double2* Tz = nullptr, double* grad_phase = nullptr,
+                       bool reunit = false);
+// The same Newton-Schulz step on the G FP32 segment products at the start of a gradient workspace
+// laid out by large_grad_workspace(t, p, REDO_FP32) (its ping buffers as scratch).
+cudaError_t large_reunit_segments_fp32(const redo_table* t, const ChainPlan& p, void* ws, cudaStream_t s);
 size_t large_sim_workspace(const redo_table* t, int64_t B);
 cudaError_t large_sim(const redo_table* t, const int32_t* q, int64_t B, int64_t M, int prec,
                       const double2* psi0, int pb, const double* obs, double* expect, void* ws,
@@ -242,7 +252,7 @@ cudaError_t tc_large_propagate(const redo_table* t, const int32_t* q, const Chai
 size_t tc_large_grad_workspace(const redo_table* t, const ChainPlan& p);
 cudaError_t tc_large_grad(const redo_table* t, const int32_t* q, const ChainPlan& p, const double2* UT,
                           int tb, double* F_out, double* grad, void* ws, int64_t* status,
-                          cudaStream_t s);
+                          cudaStream_t s, bool reunit = false);
 
 // out_b = A X_b A^dag (adjoint = 0) or A^dag X_b A (adjoint = 1), A = the table's half
 // drift, FP64 out (may be X itself); X_b of precision `prec` (REDO_FP64 or REDO_FP32).

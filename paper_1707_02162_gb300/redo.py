@@ -32,7 +32,8 @@ EXPORTS = [
     "redo_state_grad", "redo_state_grad_workspace", "redo_table_set_phase_axes", "redo_propagate_phase",
     "redo_propagate_phase_workspace", "redo_batched_product", "redo_fidelity_grad_phase",
     "redo_fidelity_grad_phase_workspace", "redo_propagate_drift", "redo_propagate_drift_workspace",
-    "redo_fidelity_grad_drift", "redo_fidelity_grad_drift_workspace",
+    "redo_fidelity_grad_drift", "redo_fidelity_grad_drift_workspace", "redo_propagate_steps",
+    "redo_propagate_steps_workspace", "redo_reunitarize", "redo_plan",
 ]
 PROFILE_PHASES = 11
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -77,7 +78,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                            vp]
     L.redo_fidelity_grad_drift_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_noalloc.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
-    L.redo_fidelity_grad.argtypes = [vp, vp, i64, i64, vp, i32, i32, i32, vp, vp, vp, ctypes.c_size_t, vp, vp]
+    L.redo_fidelity_grad.argtypes = [vp, vp, i64, i64, vp, i32, i32, i32, i32, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_fidelity_grad_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_grape_step.argtypes = [vp, vp, vp, i64, i64, dbl, vp, vp]
     L.redo_simulate.argtypes = [vp, vp, i64, i64, i32, i32, vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
@@ -91,6 +92,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_mlp_adam.argtypes = [i64, vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                 ctypes.c_float, vp]
     L.redo_grape_adam_step.argtypes = [vp, vp, vp, vp, vp, i64, i64, i32, dbl, dbl, dbl, dbl, vp]
+    L.redo_propagate_steps.argtypes = [vp, vp, i64, i64, i32, vp, vp, ctypes.c_size_t, vp, vp]
+    L.redo_propagate_steps_workspace.argtypes = [vp, i64, i64, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_reunitarize.argtypes = [i32, i64, i32, vp, vp, i32, vp]
+    L.redo_plan.argtypes = [dbl, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                            ctypes.POINTER(i64)]
     L.redo_profile_enable.argtypes = [i32]
     L.redo_profile_read.argtypes = [vp, vp, i32]
     L.redo_last_error.restype = ctypes.c_char_p
@@ -232,6 +238,39 @@ def redo_propagate_noalloc(handle: int, q: torch.Tensor, prec, U_out: torch.Tens
                                                  _stream(stream)))
 
 
+def redo_propagate_steps_workspace(handle: int, B: int, M: int, prec) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().redo_propagate_steps_workspace(ctypes.c_void_p(handle), B, M, _prec(prec),
+                                                         ctypes.byref(n)))
+    return n.value
+
+
+def redo_propagate_steps(handle: int, q: torch.Tensor, prec, U_steps: torch.Tensor,
+                         workspace: torch.Tensor | None = None, status: torch.Tensor | None = None, stream=None):
+    """U_steps[b][n] = the step propagator of step n of pulse b (complex128 [B][M][N][N])."""
+    B, M = q.shape[0], q.shape[1]
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(load_library().redo_propagate_steps(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), _ptr(U_steps),
+                                               _ptr(workspace), nbytes, _ptr(status), _stream(stream)))
+
+
+def redo_reunitarize(P_in: torch.Tensor, U_out: torch.Tensor, prec="fp64", iters: int = 1, stream=None):
+    """Newton-Schulz steps P <- P (3I - P^dag P)/2 on complex128 [count][N][N] matrices."""
+    N = P_in.shape[-1]
+    count = P_in.numel() // (N * N)
+    _check(load_library().redo_reunitarize(N, count, _prec(prec), _ptr(P_in), _ptr(U_out), int(iters),
+                                           _stream(stream)))
+
+
+def redo_plan(omega_max: float, eps: float, base: int) -> tuple[int, int, int, int]:
+    """Section II cost model: (l, m, p, s) for a range [0, omega_max], grain eps, base b (host only)."""
+    l, m, p = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    s = ctypes.c_int64()
+    _check(load_library().redo_plan(float(omega_max), float(eps), int(base), ctypes.byref(l), ctypes.byref(m),
+                                    ctypes.byref(p), ctypes.byref(s)))
+    return l.value, m.value, p.value, s.value
+
+
 def redo_fidelity_grad_workspace(handle: int, B: int, M: int, prec, checkpoint_every: int = 0) -> int:
     n = ctypes.c_size_t()
     _check(load_library().redo_fidelity_grad_workspace(ctypes.c_void_p(handle), B, M, _prec(prec), checkpoint_every,
@@ -241,13 +280,14 @@ def redo_fidelity_grad_workspace(handle: int, B: int, M: int, prec, checkpoint_e
 
 def redo_fidelity_grad(handle: int, q: torch.Tensor, U_target: torch.Tensor, prec, checkpoint_every: int,
                        F_out: torch.Tensor | None, grad: torch.Tensor, workspace: torch.Tensor,
-                       status: torch.Tensor | None = None, stream=None):
+                       status: torch.Tensor | None = None, stream=None, reunit_every: int = 0):
+    """F and dF/du; reunit_every > 0 (equal to checkpoint_every) re-unitarises every checkpoint segment."""
     B, M = q.shape[0], q.shape[1]
     batched = 1 if U_target.dim() == 3 else 0
     _check(load_library().redo_fidelity_grad(ctypes.c_void_p(handle), _ptr(q), B, M, _ptr(U_target), batched,
-                                             _prec(prec), checkpoint_every, _ptr(F_out), _ptr(grad), _ptr(workspace),
-                                             workspace.numel() * workspace.element_size(), _ptr(status),
-                                             _stream(stream)))
+                                             _prec(prec), checkpoint_every, int(reunit_every), _ptr(F_out),
+                                             _ptr(grad), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                             _ptr(status), _stream(stream)))
 
 
 def redo_fidelity_grad_drift_workspace(handle: int, B: int, M: int, prec, checkpoint_every: int = 0) -> int:
@@ -530,7 +570,7 @@ Table.propagate_drift = _table_propagate_drift
 Table.fidelity_grad_drift = _table_fidelity_grad_drift
 
 
-def _table_fidelity_grad(self, q, target, prec="fp64", checkpoint_every=0, status=None):
+def _table_fidelity_grad(self, q, target, prec="fp64", checkpoint_every=0, status=None, reunit_every=0):
     """(F [B], grad [B][M][K]) of the fidelity against `target` at levels q."""
     B, M = q.shape[0], q.shape[1]
     target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
@@ -538,7 +578,7 @@ def _table_fidelity_grad(self, q, target, prec="fp64", checkpoint_every=0, statu
     g = torch.empty((B, M, self.K), dtype=torch.float64, device=self.device)
     nbytes = redo_fidelity_grad_workspace(self.handle, B, M, prec, checkpoint_every)
     ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
-    redo_fidelity_grad(self.handle, q, target, prec, checkpoint_every, F, g, ws, status)
+    redo_fidelity_grad(self.handle, q, target, prec, checkpoint_every, F, g, ws, status, reunit_every=reunit_every)
     return F, g
 
 

@@ -92,3 +92,33 @@ def test_propagation_wrappers_take_one_target():
 
 def test_build_flags_are_sm103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
+
+
+def test_plan_through_the_c_abi_matches_the_printed_cost_model(lib):
+    # Section II's worked example and Section IV's freezing grain, as printed
+    import json
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "worked_examples.json")))
+    for key in ("coarse_grain_example", "freezing_grain"):
+        e = g[key]
+        assert redo.redo_plan(e["omega_max"], e["eps"], e["base"]) == (e["l"], e["m"], e["p"], e["s"])
+    # the covered range: b^(m+1) > omega_max >= b^m, and b^l <= eps < b^(l+1)
+    for om, eps, b in [(1e3, 1.0, 2), (65535.0, 1.0, 16), (2 * 3.141592653589793 * 1e4, 30.7, 64), (0.5, 0.01, 10)]:
+        l, m, p, s = redo.redo_plan(om, eps, b)
+        assert b ** (m + 1) > om >= b ** m and b ** l <= eps * (1 + 1e-12) < b ** (l + 1)
+        assert p == m - l and s == (b - 1) * (m - l + 1)
+    with pytest.raises(redo.RedoError):
+        redo.redo_plan(-1.0, 1.0, 64)
+    with pytest.raises(redo.RedoError):
+        redo.redo_plan(10.0, 1.0, 1)
+
+
+def test_new_entry_points_validate_without_device(lib):
+    n = ctypes.c_size_t()
+    dummy = ctypes.c_void_p(16)
+    assert lib.redo_propagate_steps(None, None, 1, 1, 0, None, None, 0, None, None) == 1
+    assert lib.redo_propagate_steps_workspace(None, 1, 1, 0, ctypes.byref(n)) == 1
+    assert lib.redo_reunitarize(3, 1, 0, dummy, dummy, 1, None) == 5          # N not a power of two
+    assert lib.redo_reunitarize(128, 1, 0, dummy, dummy, 1, None) == 5        # beyond the shared-memory kernel
+    assert lib.redo_reunitarize(8, 1, 4, dummy, dummy, 1, None) == 5          # FP64 / FP32 arithmetic only
+    assert lib.redo_reunitarize(8, -1, 0, dummy, dummy, 1, None) == 1
+    assert lib.redo_reunitarize(8, 0, 0, None, None, 1, None) == 0            # nothing to do
