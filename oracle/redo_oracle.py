@@ -200,10 +200,13 @@ def expm_pade13(A):
     return R
 
 
-def expm_hermitian(H, t):
-    """``exp(-i t H)`` for Hermitian H by eigen-decomposition ``H = V diag(w) V^dag``."""
-    H = np.asarray(H, dtype=np.complex128)
-    w, V = np.linalg.eigh(H)
+def expm_hermitian(H, t, eig=None):
+    """``exp(-i t H)`` for Hermitian H by eigen-decomposition ``H = V diag(w) V^dag``.
+
+    ``eig`` may pass ``(w, V) = numpy.linalg.eigh(H)`` computed once for many ``t``."""
+    if eig is None:
+        eig = np.linalg.eigh(np.asarray(H, dtype=np.complex128))
+    w, V = eig
     return (V * np.exp(-1j * t * w)[None, :]) @ V.conj().T
 
 
