@@ -37,12 +37,6 @@ MAIN_PREC = os.environ.get("REDO_BENCH_PREC", "fp16x3")
 REUNIT = 64          # re-unitarisation period (steps) of the reduced-precision forms
 
 
-def tc_variant_env() -> str:
-    """Tensor-core chain variant the library will run (see REDO_TC_VARIANT in kernels_tc.cu)."""
-    v = os.environ.get("REDO_TC_VARIANT", "3")
-    return v if v in ("1", "2", "3") else "3"
-
-
 def _workload_config(extra=None):
     cfg = {"workload": "batched REDO propagation: N=64 (6 qubits), K=12 x/y controls, B=256 pulses, "
                        "M=2000 steps of 1 us, 4096 levels (b=64, d=2), fidelity vs Haar target",
@@ -125,6 +119,35 @@ def _oracle_worker(args):
     return dt, M_sample, F
 
 
+def _oracle_parity_worker(pulse):
+    """The oracle's propagator of one whole pulse of the benchmark workload (all M steps)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import redo_oracle as O
+    from paper_1707_02162_gb300 import inputs
+    w = inputs.config(1, B=B_FULL, M=M_FULL, seed=1)
+    T, D = O.build_table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits, method="eig")
+    q, _, _ = O.quantize(w.u[pulse:pulse + 1], w.lo, w.hi, w.levels)
+    U = O.propagate(T, D, O.level_digits(q, w.base, w.digits)[0])
+    return pulse, U, O.fidelity(w.target, U)
+
+
+def oracle_parity(pulses):
+    """Oracle propagators of the given pulses, one spawn worker each (the CPU leg of the run)."""
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(len(pulses)) as pool:
+            res = pool.map(_oracle_parity_worker, list(pulses))
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {p: (U, F) for p, U, F in res}
+
+
 def oracle_throughput(cores=None, M_sample=600):
     """Oracle pulse-steps/s over `cores` spawn workers, one pulse of M_sample steps each."""
     cores = cores or os.cpu_count() or 1
@@ -156,6 +179,183 @@ def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def chain_roofline(peaks, clk, B, M, N, K, digits, prods_per_step, avg_s, prec, kernel):
+    """Roofline of one chain-kernel launch over B pulses x M steps.
+
+    The algorithmic count is the method's as the survey of the paper states it: K*digits complex
+    N x N products per pulse-step (the digit operators of Eq. exp2prod), 8N^3 flop each.  With the
+    level table the call performs K products per pulse-step (process 3 applied to every level),
+    and the split-FP16 form runs 3 fp16 products per complex product; both are reported beside it.
+    """
+    n3 = 8.0 * N ** 3
+    alg_flop = B * M * K * digits * n3
+    method_flop = B * M * prods_per_step * n3
+    alg_tf = alg_flop / avg_s / 1e12
+    out = {"kernel": kernel, "launch_ms": avg_s * 1e3,
+           "algorithmic_per_launch": (f"{alg_flop:.4g} flop: B*M*{K * digits} complex {N}x{N} products "
+                                      f"(K*d digit operators per pulse-step), 8N^3 each"),
+           "traffic": None}
+    if prec == "fp16x3":
+        sus = peaks.get("bf16_tflops_sustained", 1699.6)
+        burst = peaks.get("bf16_tflops", 1908.8)
+        op_bytes = B * M * prods_per_step * 32768.0            # one 32 KB split-FP16 operand per product
+        out.update({"bound": "tensor", "unit": "TFLOP/s", "achieved": alg_tf, "peak": sus,
+                    "peak_source": "measured dense bf16, sustained (of measured; fp16 has the same nominal rate)",
+                    "frac": alg_tf / sus, "frac_of_burst": alg_tf / burst,
+                    "method_products": {"what": f"{prods_per_step} complex products per pulse-step as performed",
+                                        "achieved": method_flop / avg_s / 1e12,
+                                        "frac": method_flop / avg_s / 1e12 / sus},
+                    "hardware_fp16": {"what": "3 fp16 products per complex product (split operands)",
+                                      "achieved": 3 * method_flop / avg_s / 1e12,
+                                      "frac": 3 * method_flop / avg_s / 1e12 / sus},
+                    "hbm_operand_stream": {"bytes_per_launch": op_bytes, "achieved_gbs": op_bytes / avg_s / 1e9,
+                                           "peak_gbs": peaks.get("hbm_gbs", 6783.5),
+                                           "frac": op_bytes / avg_s / 1e9 / peaks.get("hbm_gbs", 6783.5)}})
+    elif prec == "fp32":
+        clk_max = (clk.get("sm_max_mhz") or 2070.0) * 1e6
+        peak = 152 * 128 * 2 * clk_max / 1e12
+        out.update({"bound": "alu", "unit": "TFLOP/s", "achieved": alg_tf, "peak": peak, "frac": alg_tf / peak,
+                    "peak_source": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock"})
+    else:
+        out.update({"bound": "alu", "unit": "TFLOP/s", "achieved": alg_tf, "peak": 1.25, "frac": alg_tf / 1.25,
+                    "peak_source": "nominal GB300 FP64"})
+    return out
+
+
+def grape_summary(gres, gflop, gbuild, gw, peaks):
+    """GRAPE iterations/s on the N=256 workload with the three flop counts side by side."""
+    ms = gres["fp16x3"]["ms_per_iter"]
+    sus = peaks.get("bf16_tflops_sustained", 1699.6)
+    n3 = 8.0 * gw.N ** 3
+    survey = 2 * gw.M * gw.K * gw.digits * n3            # 2 products per digit factor (forward, costate)
+    counts = {"algorithmic": (survey, "2 complex products per digit factor per step (K*d = "
+                                      f"{gw.K * gw.digits} factors), 8N^3 each"),
+              "method_level_table": (gflop, f"2 complex products per level factor ({gw.K} per step)"),
+              "hardware_fp16": (3 * gflop, "x3 fp16 products per complex product")}
+    flops = {k: {"tflop_per_iteration": v / 1e12, "achieved_tflops": v / (ms / 1e3) / 1e12,
+                 "frac_of_sustained": v / (ms / 1e3) / 1e12 / sus, "what": what}
+             for k, (v, what) in counts.items()}
+    return {"metric": "GRAPE iters/s", "value": gres["fp16x3"]["iters_per_s"], "unit": "iterations/s",
+            "workload": "GRAPE gradient + update, N=256 (8 qubits), K=16, M=1000, dt=2 us, Haar target, "
+                        "checkpoints every 32 steps, level table (one operator per control level)",
+            "fp64_plain_redo": gres.get("fp64"),
+            "speedup_vs_fp64": (gres["fp16x3"]["iters_per_s"] / gres["fp64"]["iters_per_s"]
+                                if "fp64" in gres else None),
+            "roofline": dict(flops["algorithmic"], bound="tensor", peak=sus, unit="TFLOP/s",
+                             peak_source="measured dense bf16, sustained (of measured)"),
+            "flop_counts": flops, "phase_ms": gres["fp16x3"].get("phase_ms"), "table_build_s": gbuild}
+
+
+def precision_table(forms, oracle):
+    """max |U - U_oracle| and |F - F_oracle| of every precision form on the sampled pulses."""
+    table = {}
+    for prec, val in forms.items():
+        if prec == "pulses":
+            continue
+        Ug, Fg, reunit = val
+        dU = max(float(np.abs(Ug[i] - oracle[p][0]).max()) for i, p in enumerate(forms["pulses"]))
+        dF = max(abs(float(Fg[i]) - oracle[p][1]) for i, p in enumerate(forms["pulses"]))
+        table[prec] = {"max_abs_dU": dU, "max_abs_dF": dF, "reunit_every": reunit}
+    table["tf32"] = "not offered: a TF32 chain emulated on this system misses the entry budget by ~30x"
+    table["pulses"] = forms["pulses"]
+    table["what"] = ("error of each product-chain form against the CPU FP64 oracle's chain, whole pulses of "
+                     "the timed workload (all 2000 steps)")
+    return table
+
+
+def plain_measure(redo, inputs, torch, reps=5):
+    """Plain REDO on the 3-qubit system (N=8, K=2 global x/y, M=1000, FP64): one pulse (latency)
+    and 4096 replica pulses (throughput), with the FP32 form beside each."""
+    res = {}
+    for B in (1, 4096):
+        w = inputs.config(0, B=B)
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+        u = torch.tensor(w.u, device="cuda")
+        target = torch.as_tensor(w.target, device="cuda")
+        q = torch.empty(u.shape, dtype=torch.int32, device="cuda")
+        U = torch.empty((B, w.N, w.N), dtype=torch.complex128, device="cuda")
+        F = torch.empty(B, dtype=torch.float64, device="cuda")
+        tau = torch.empty(B, dtype=torch.complex128, device="cuda")
+        for prec in ("fp64", "fp32"):
+            ws = t.workspace(B, w.M, prec)
+
+            def it():
+                redo.redo_quantize(t.handle, u, q)
+                redo.redo_propagate(t.handle, q, prec, U, target, F, tau, ws)
+            it()
+            ms = _events_time(it, reps)
+            # 4 complex 8x8 products per pulse-step: K*d = 4 digit operators, the drift folded in
+            flop = B * w.M * w.K * w.digits * 8.0 * w.N ** 3
+            peak = 1.25 if prec == "fp64" else 152 * 128 * 2 * 2.07e9 / 1e12
+            res[f"B{B}_{prec}"] = {"pulse_steps_per_s": B * w.M / (ms / 1e3), "ms_per_call": ms,
+                                   "roofline": {"bound": "alu", "unit": "TFLOP/s",
+                                                "achieved": flop / (ms / 1e3) / 1e12, "peak": peak,
+                                                "frac": flop / (ms / 1e3) / 1e12 / peak,
+                                                "peak_source": ("nominal GB300 FP64" if prec == "fp64" else
+                                                                "FP32 FMA pipe: 152 x 128 lanes x 2 x 2.07 GHz"),
+                                                "timed": "whole call (quantize, chain, combine, fidelity)"}}
+        t.close()
+    return {"metric": "REDO prop steps/s, plain REDO FP64 (N=8)", "unit": "pulse-steps/s",
+            "workload": "3 qubits (N=8), K=2 global x/y controls, M=1000 steps of 1 us, 4096 levels, "
+                        "FP64, Haar target; B=1 and 4096 replica pulses",
+            "value": res["B1_fp64"]["pulse_steps_per_s"], "replicas_4096_fp64": res["B4096_fp64"]["pulse_steps_per_s"],
+            "results": res}
+
+
+def ensemble_measure(redo, inputs, torch, peaks, M=2000):
+    """Noisy-drive ensemble: 10-qubit ZZ chain (N=1024), global x drive Omega(1 + xi(t)) with OU
+    noise, 64 realisations x M steps: <Z_1>(t) from |0...0> plus every final propagator in split
+    FP16, and <Z_1>(t) in FP64 (state only) for its error.  Primary: the level table (each of the
+    4096 levels' operators evaluated once, process 3: one product per step); beside it the digit
+    table (two products per step)."""
+    w = inputs.config(3, M=M)
+    steps = w.B * M
+    alg = steps * w.K * w.digits * 8.0 * w.N ** 3          # 2 complex 1024x1024 products per realisation-step
+    sus = peaks.get("bf16_tflops_sustained", 1699.6)
+    res = {}
+    for levels in (True, False):
+        t0 = time.time()
+        t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=False, fp16x3=True, levels=levels)
+        torch.cuda.synchronize()
+        build_s = time.time() - t0
+        q = t.quantize(w.u)
+        psi0 = torch.as_tensor(w.psi0, device="cuda")
+        obs = torch.as_tensor(w.obs_diag, device="cuda")
+        ex16 = torch.empty((w.B, M + 1), dtype=torch.float64, device="cuda")
+        ex64 = torch.empty((w.B, M + 1), dtype=torch.float64, device="cuda")
+        Uf = torch.empty((w.B, w.N, w.N), dtype=torch.complex128, device="cuda")
+        ws16 = torch.empty(max(redo.redo_simulate_workspace(t.handle, w.B, M, "fp16x3", 0, True), 256),
+                           dtype=torch.uint8, device="cuda")
+        ws64 = torch.empty(max(redo.redo_simulate_workspace(t.handle, w.B, M, "fp64", 0, False), 256),
+                           dtype=torch.uint8, device="cuda")
+        run16 = lambda: redo.redo_simulate(t.handle, q, "fp16x3", 0, psi0, obs, ex16, Uf, ws16)
+        run64 = lambda: redo.redo_simulate(t.handle, q, "fp64", 0, psi0, obs, ex64, None, ws64)
+        run16()
+        ms16 = _events_time(run16, 1)
+        ms64 = _events_time(run64, 1)
+        res["level_table" if levels else "digit_table"] = {
+            "realisation_steps_per_s": steps / (ms16 / 1e3), "ms_per_call": ms16,
+            "products_per_step": w.K * (1 if levels else w.digits),
+            "fp64_state_only": {"realisation_steps_per_s": steps / (ms64 / 1e3), "ms_per_call": ms64},
+            "max_abs_dZ1_fp16x3_vs_fp64": float((ex16 - ex64).abs().max()),
+            "tensor_frac_algorithmic": alg / (ms16 / 1e3) / 1e12 / sus,
+            "table_build_s": build_s}
+        t.close()
+        del ws16, ws64, Uf
+    lv = res["level_table"]
+    return {"metric": "REDO prop steps/s (noisy-drive ensemble, propagators + <Z_1>(t))", "unit": "realisation-steps/s",
+            "workload": "10-qubit ZZ chain (N=1024), K=1 global x drive Omega(1+xi), OU sigma=0.1 tau=50 us, "
+                        f"64 realisations x {M} steps of 1 us, 4096 levels",
+            "value": lv["realisation_steps_per_s"], "ms_per_call": lv["ms_per_call"],
+            "precision": "fp16x3 products, fp32 state path", "results": res,
+            "roofline": {"bound": "tensor", "unit": "TFLOP/s", "peak": sus,
+                         "peak_source": "measured dense bf16, sustained (of measured)",
+                         "achieved": alg / (lv["ms_per_call"] / 1e3) / 1e12,
+                         "frac": alg / (lv["ms_per_call"] / 1e3) / 1e12 / sus, "timed": "whole call",
+                         "algorithmic_per_call": f"{alg:.4g} flop (2 complex digit-operator products of 8N^3 per "
+                                                 "realisation-step)"}}
 
 
 def run_gpu(args):
@@ -234,52 +434,15 @@ def run_gpu(args):
     # here we only refuse to report if the device flagged a timeout or a bad index.
     assert st[2] == 0 and st[3] == 0, f"device status {st}"
 
-    # ---- roofline of the dominant kernel (chain segments)
+    # ---- roofline of the dominant kernel (the chain kernel)
     seg_ms, seg_n = prof.get("chain_segments", (0.0, 0))
     tc_ms, tc_n = prof.get("chain_tc", (0.0, 0))
     if tc_n:
         dom_ms, dom_n, dom_name = tc_ms, tc_n, "chain_tc"
     else:
         dom_ms, dom_n, dom_name = seg_ms, seg_n, "chain_segments"
-    flops_per_launch = B * M * prods_per_step * 8.0 * N ** 3       # algorithmic: complex products per step
     avg_s = (dom_ms / max(dom_n, 1)) / 1e3
-    achieved_tf = flops_per_launch / avg_s / 1e12
-    tensor_roof = {"peak": peaks.get("bf16_tflops_sustained", 1709.6), "unit": "TFLOP/s",
-                   "peak_source": "measured bf16 dense (sustained) of measured; fp16 has the same nominal rate",
-                   "achieved": achieved_tf * 3}          # three fp16 products per complex product
-    tensor_roof["frac"] = tensor_roof["achieved"] / tensor_roof["peak"]
-    if MAIN_PREC == "fp16x3" and args.levels:
-        # the level table (1.6 GB of operand planes) streams one 32 KB operand per product from HBM
-        op_bytes = B * M * prods_per_step * 32768.0
-        roof = {"bound": "hbm", "peak": peaks.get("hbm_gbs", 6794.5), "unit": "GB/s",
-                "peak_source": "measured HBM copy bandwidth (of measured)",
-                "achieved": op_bytes / avg_s / 1e9,
-                "algorithmic_bytes_per_launch": op_bytes,
-                "tensor": tensor_roof}
-    elif MAIN_PREC == "fp16x3":
-        roof = dict(tensor_roof, bound="tensor")
-    elif MAIN_PREC == "fp32":
-        clk_max = (clk.get("sm_max_mhz") or 2070.0) * 1e6
-        peak = 152 * 128 * 2 * clk_max / 1e12
-        roof = {"bound": "alu", "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock", "achieved": achieved_tf}
-    else:
-        roof = {"bound": "alu", "peak": 1.25, "unit": "TFLOP/s", "peak_source": "nominal GB300 FP64",
-                "achieved": achieved_tf}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = dom_name
-    # DRAM bytes (read + write) of one full-size launch of chain_tc3_kernel<2,4,false> with the
-    # level table, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/
-    # chain_tc_fp16x3_n64.md); only valid for that kernel and configuration.
-    full_size = (B, M) == (B_FULL, M_FULL)
-    roof["traffic"] = (190015116032 + 376372480) if (MAIN_PREC == "fp16x3" and args.levels and full_size
-                                                     and tc_variant_env() == "3") else None
-    roof["algorithmic_per_launch"] = (f"{flops_per_launch:.4g} flop (B*M*{prods_per_step} complex {N}x{N} "
-                                      f"products, 8N^3 each)")
-    if roof["bound"] == "hbm":
-        roof["algorithmic_per_launch"] = (f"{roof['algorithmic_bytes_per_launch']:.4g} B (B*M*{prods_per_step} "
-                                          f"split-FP16 operands of 32 KB streamed from HBM); "
-                                          + roof["algorithmic_per_launch"])
+    roof = chain_roofline(peaks, clk, B, M, N, w.K, w.digits, prods_per_step, avg_s, MAIN_PREC, dom_name)
 
     # ---- FP64 plain REDO on the same GPU (subset of pulses, same steps)
     fp64 = None
@@ -334,19 +497,27 @@ def run_gpu(args):
     if rank == 0 and not args.skip_grape:
         gres, gflop, gbuild, gw = grape_measure(redo, inputs, torch, 3, levels=True, with_fp32=False,
                                                 with_fp64=not args.skip_fp64)
-        grape = {"metric": "GRAPE iters/s", "value": gres["fp16x3"]["iters_per_s"], "unit": "iterations/s",
-                 "workload": "GRAPE gradient + update, N=256 (8 qubits), K=16, M=1000, dt=2 us, Haar target, "
-                             "checkpoints every 32 steps, level table (one operator per control level)",
-                 "fp64_plain_redo": gres.get("fp64"),
-                 "speedup_vs_fp64": (gres["fp16x3"]["iters_per_s"] / gres["fp64"]["iters_per_s"]
-                                     if "fp64" in gres else None),
-                 "achieved_tensor_tflops": 3 * gflop / (gres["fp16x3"]["ms_per_iter"] / 1e3) / 1e12,
-                 "tensor_frac_of_sustained": (3 * gflop / (gres["fp16x3"]["ms_per_iter"] / 1e3) / 1e12
-                                              / peaks.get("bf16_tflops_sustained", 1709.6)),
-                 "algorithmic": "2 complex N x N products per factor (forward sweep keeping every state, costate sweep), 8N^3 flop each, "
-                                "x3 fp16 products",
-                 "phase_ms": gres["fp16x3"].get("phase_ms"),
-                 "table_build_s": gbuild}
+        grape = grape_summary(gres, gflop, gbuild, gw, peaks)
+
+    # ---- each precision form on sampled pulses, for their error against the oracle (CPU leg)
+    forms = None
+    if rank == 0 and not args.skip_cpu and (B, M) == (B_FULL, M_FULL):
+        picks = [0, 131]
+        forms = {"pulses": picks, MAIN_PREC: (U[picks].cpu().numpy(), F[picks].cpu().numpy(), reunit_main)}
+        qp = q[picks].contiguous()
+        for prec, reunit in (("fp64", 0), ("fp32", REUNIT)):
+            if prec == MAIN_PREC:
+                continue
+            Up = torch.empty((len(picks), N, N), dtype=torch.complex128, device=dev)
+            Fp = torch.empty(len(picks), dtype=torch.float64, device=dev)
+            redo.redo_propagate(table.handle, qp, prec, Up, target, Fp, None,
+                                table.workspace(len(picks), M, prec, reunit), status, reunit_every=reunit)
+            forms[prec] = (Up.cpu().numpy(), Fp.cpu().numpy(), reunit)
+
+    plain = ensemble = None
+    if rank == 0 and not args.skip_extra:
+        plain = plain_measure(redo, inputs, torch)
+        ensemble = ensemble_measure(redo, inputs, torch, peaks)
 
     launches = sum(n for _, n in prof.values())
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -359,9 +530,12 @@ def run_gpu(args):
                                        "l2": "flushed between timed steps (256 MB write outside the events)"}),
            "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-           "fp64_plain_redo": fp64, "grape": grape, "clocks": clk}
+           "fp64_plain_redo": fp64, "grape": grape, "plain_n8": plain, "ensemble_n1024": ensemble,
+           "clocks": clk}
     if rank == 0 and not args.skip_cpu:
         out["cpu_baseline"] = oracle_throughput()
+        if forms is not None:
+            out["precision_vs_oracle"] = precision_table(forms, oracle_parity(sorted(forms["pulses"])))
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -834,6 +1008,8 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-grape", action="store_true", help="omit the GRAPE iterations/s sub-measurement")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="omit the N=8 plain-REDO and N=1024 ensemble sub-measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
