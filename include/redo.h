@@ -446,6 +446,32 @@ redo_status redo_grape_adam_step(const redo_table* t, double* u, const double* g
                                  double beta2, double eps, void* stream);
 
 /*
+ * redo_grape_lbfgs_step -- GRAPE ascent by projected L-BFGS with Armijo backtracking (the paper
+ * leaves the update rule open; quasi-Newton ascent needs several times fewer fidelity and gradient
+ * evaluations than plain or Adam ascent near F = 1).  One call per gradient evaluation:
+ *   u        device double [B][M][K], in: the point just evaluated (F, grad from redo_fidelity_grad
+ *            or its variants); out: the next point to evaluate.
+ *   grad, F  device double [B][M][K] and [B] at that point.
+ *   history  number of (s, y) pairs kept per pulse, 1..64.
+ *   first    nonzero on the first call (accepts the point and starts the state).
+ *   step0    size of a gradient step: its largest entry is step0 * max_k (hi_k - lo_k) / 2.
+ *   c1       Armijo constant (1e-4 is usual), 0 < c1 < 1.
+ *   state    device scratch of redo_grape_lbfgs_workspace() bytes, 256-byte aligned, kept between
+ *            calls (nothing in it needs to start at zero).
+ *   u_best, F_best  device [B][M][K] and [B] or NULL: the accepted point and its F (never falls).
+ * Per pulse: a trial point is accepted when F >= F_acc + c1 grad_acc . (u - u_acc); an accepted
+ * step stores the pair s = u - u_acc, y = -(grad - grad_acc) when s.y > 0, and the next direction
+ * is the two-loop recursion with H0 = (s.y / y.y) I of the newest pair (the plain gradient
+ * direction when no pair is kept or the result is not an ascent direction); a rejected one halves
+ * the step, and below 1e-3 of it drops every pair.  The next point is clip(u_acc + alpha d, lo_k,
+ * hi_k).  Errors: REDO_ERR_INVALID, REDO_ERR_CUDA.  Asynchronous on `stream`.
+ */
+redo_status redo_grape_lbfgs_workspace(const redo_table* t, int64_t B, int64_t M, int32_t history, size_t* bytes);
+redo_status redo_grape_lbfgs_step(const redo_table* t, double* u, const double* grad, const double* F, int64_t B,
+                                  int64_t M, int32_t history, int32_t first, double step0, double c1, void* state,
+                                  size_t state_bytes, double* u_best, double* F_best, void* stream);
+
+/*
  * Amplitude/phase controls (Section III, Eq. vn and the Dirac-frame step after Eq. vnd).
  *
  * A linearly polarised drive of amplitude A_kn and phase phi_kn on species k equals the
@@ -527,12 +553,13 @@ redo_status redo_propagate_drift_workspace(const redo_table* t, int64_t B, int64
  * g_kn = (2 dt / N^2) Im(conj(tau) Tr(H_k W_{n,k})) with each step's diagonal inside its W.
  * REDO_FP64 or REDO_FP32 at every N (for N > 64 on segments of whole steps: checkpoint_every is
  * then the segment length in steps); REDO_ERR_UNSUPPORTED otherwise and on a symmetric-split
- * table.  Workspace from redo_fidelity_grad_drift_workspace.
+ * table.  reunit_every as for redo_fidelity_grad (equal to checkpoint_every, or 0).
+ * Workspace from redo_fidelity_grad_drift_workspace.
  */
 redo_status redo_fidelity_grad_drift(const redo_table* t, const int32_t* q, const double* h, int64_t B, int64_t M,
                                      const void* U_target, int32_t target_batched, redo_precision prec,
-                                     int32_t checkpoint_every, double* F_out, double* grad, void* workspace,
-                                     size_t workspace_bytes, int64_t* dev_status, void* stream);
+                                     int32_t checkpoint_every, int32_t reunit_every, double* F_out, double* grad,
+                                     void* workspace, size_t workspace_bytes, int64_t* dev_status, void* stream);
 redo_status redo_fidelity_grad_drift_workspace(const redo_table* t, int64_t B, int64_t M, redo_precision prec,
                                                int32_t checkpoint_every, size_t* bytes);
 

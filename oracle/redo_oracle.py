@@ -32,9 +32,10 @@ Functions and the passage each one follows:
   derivative is taken from the definitions, see its docstring).
 * :func:`state_transfer_gradient` -- the state-to-state fidelity ``|<psi_T|U|psi0>|^2``
   and its GRAPE gradient, from the same definitions.
-* :func:`grape_update` / :func:`grape_step_scale` / :func:`grape_adam_update` --
-  the control update of the GRAPE loop (Section III, Fig. fc; the rule is this
-  module's reading: clipped ascent with per-pulse step factors, or Adam).
+* :func:`grape_update` / :func:`grape_step_scale` / :func:`grape_adam_update` /
+  :func:`lbfgs_direction` / :func:`grape_lbfgs_step` -- the control update of the
+  GRAPE loop (Section III, Fig. fc; the rule is this module's reading: clipped ascent
+  with per-pulse step factors, Adam, or projected L-BFGS with Armijo backtracking).
 * :func:`polar_unitary` -- polar factor ``P (P^dag P)^(-1/2)``.
 * :func:`half_drift` / :func:`strang_step_propagator` / :func:`propagate_strang`
   / :func:`strang_split_step` / :func:`simulate_expectation_strang` -- the
@@ -65,7 +66,8 @@ __all__ = [
     "quantize", "level_digits", "level_values", "table_thetas", "expm_pade13", "expm_hermitian",
     "build_table", "step_factors", "step_propagator", "propagate", "fidelity", "trace_overlap",
     "grape_gradient", "polar_unitary", "simulate_expectation", "exact_step", "split_step",
-    "plan_digits", "grape_update", "grape_step_scale", "grape_adam_update", "mlp_init", "mlp_forward", "mlp_backward", "adam_step", "gelu", "gelu_grad",
+    "plan_digits", "grape_update", "grape_step_scale", "grape_adam_update", "lbfgs_direction",
+    "grape_lbfgs_step", "mlp_init", "mlp_forward", "mlp_backward", "adam_step", "gelu", "gelu_grad",
 ]
 
 
@@ -620,6 +622,99 @@ def grape_adam_update(u, g, m, v, t, lr, lo, hi, beta1=0.9, beta2=0.999, eps=1e-
     for k in range(K):
         out[..., k] = np.minimum(np.maximum(x[..., k], lo[k]), hi[k])
     return out, m, v
+
+
+def lbfgs_direction(g, pairs):
+    """Ascent direction ``d = H g`` of F by the L-BFGS two-loop recursion (Nocedal & Wright,
+    Numerical Optimization, 2nd ed., Algorithm 7.4) for the function f = -F, whose gradient is
+    -g.  ``pairs`` lists ``(s_i, y_i)`` oldest first, ``s_i = u_{i+1} - u_i`` and
+    ``y_i = -(g_{i+1} - g_i)`` (the change of f's gradient), each with ``s_i . y_i > 0``.  The
+    initial matrix is ``gamma I`` with ``gamma = s.y / y.y`` of the newest pair.  With no pairs
+    the direction is g itself.  Vectors are flat numpy arrays."""
+    q = -np.asarray(g, dtype=np.float64)                  # gradient of f
+    if not pairs:
+        return -q
+    rho = [1.0 / float(np.dot(s, y)) for s, y in pairs]
+    alpha = [0.0] * len(pairs)
+    for i in range(len(pairs) - 1, -1, -1):
+        s, y = pairs[i]
+        alpha[i] = rho[i] * float(np.dot(s, q))
+        q = q - alpha[i] * y
+    s, y = pairs[-1]
+    r = (float(np.dot(s, y)) / float(np.dot(y, y))) * q
+    for i in range(len(pairs)):
+        s, y = pairs[i]
+        beta = rho[i] * float(np.dot(y, r))
+        r = r + (alpha[i] - beta) * s
+    return -r                                              # descent for f = ascent for F
+
+
+def grape_lbfgs_step(u_trial, g_trial, F_trial, state, lo, hi, history=8, step0=0.05, c1=1e-4,
+                     first=False):
+    """One step of projected L-BFGS ascent with Armijo backtracking for one pulse (the GRAPE
+    update read as a quasi-Newton method; the paper leaves the rule open).
+
+    ``u_trial`` (M, K) is the point just evaluated, with fidelity ``F_trial`` and gradient
+    ``g_trial``; ``state`` (a dict, empty on the first call) holds the accepted point ``u``,
+    its ``g`` and ``F``, the direction ``d``, the step length ``alpha`` and the pair list.
+    Rules, in order:
+      * first call: accept the trial point outright;
+      * otherwise accept when ``F_trial >= F + c1 * g . (u_trial - u)`` (Armijo, projected step),
+        store the pair (s, y) when ``s . y > 0`` (at most ``history``, oldest dropped);
+        else halve ``alpha``, and below ``alpha = 1e-3`` drop every pair and restart from the
+        gradient;
+      * after an accept (or a restart) the direction is :func:`lbfgs_direction`, replaced by the
+        gradient (dropping the pairs) when it is not an ascent direction (``g . d <= 0``); a
+        gradient direction is scaled so that its largest entry is ``step0`` times the widest
+        grid span ``max_k(hi_k - lo_k) / 2``; ``alpha`` restarts at 1;
+      * the next trial point is ``clip(u + alpha d, lo_k, hi_k)``.
+    Returns ``(u_next, state)``.
+    """
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    ut = np.asarray(u_trial, dtype=np.float64)
+    gt = np.asarray(g_trial, dtype=np.float64)
+    span = 0.5 * float(np.max(hi - lo))
+
+    def grad_dir(g):
+        m = float(np.max(np.abs(g)))
+        return g * (step0 * span / m) if m > 0 else np.zeros_like(g)
+
+    new_dir = False
+    if first:
+        state = {"u": ut.copy(), "g": gt.copy(), "F": float(F_trial), "pairs": []}
+        new_dir = True
+    else:
+        u, g, F = state["u"], state["g"], state["F"]
+        p = ut - u
+        if float(F_trial) >= F + c1 * float(np.sum(g * p)):
+            s = p.ravel()
+            y = -(gt - g).ravel()
+            if float(np.dot(s, y)) > 0.0:
+                state["pairs"] = (state["pairs"] + [(s, y)])[-history:]
+            state["u"], state["g"], state["F"] = ut.copy(), gt.copy(), float(F_trial)
+            new_dir = True
+        else:
+            state["alpha"] *= 0.5
+            if state["alpha"] < 1e-3:
+                state["pairs"] = []
+                new_dir = True
+    if new_dir:
+        g = state["g"]
+        if state["pairs"]:
+            d = lbfgs_direction(g.ravel(), state["pairs"]).reshape(g.shape)
+            if float(np.sum(g * d)) <= 0.0:
+                state["pairs"] = []
+                d = grad_dir(g)
+        else:
+            d = grad_dir(g)
+        state["d"] = d
+        state["alpha"] = 1.0
+    x = state["u"] + state["alpha"] * state["d"]
+    u_next = np.empty_like(x)
+    for k in range(x.shape[-1]):
+        u_next[..., k] = np.minimum(np.maximum(x[..., k], lo[k]), hi[k])
+    return u_next, state
 
 
 # ---------------------------------------------------------------------------

@@ -1139,11 +1139,15 @@ redo_status redo_fidelity_grad_drift_workspace(const redo_table* t, int64_t B, i
 
 redo_status redo_fidelity_grad_drift(const redo_table* t, const int32_t* q, const double* h, int64_t B, int64_t M,
                                      const void* U_target, int32_t target_batched, redo_precision prec,
-                                     int32_t checkpoint_every, double* F_out, double* grad, void* workspace,
-                                     size_t workspace_bytes, int64_t* dev_status, void* stream) {
+                                     int32_t checkpoint_every, int32_t reunit_every, double* F_out, double* grad,
+                                     void* workspace, size_t workspace_bytes, int64_t* dev_status, void* stream) {
   redo_status st = check_drift_grad(t, prec);
   if (st != REDO_OK) return st;
-  if (B < 0 || M < 0 || checkpoint_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
+  if (B < 0 || M < 0 || checkpoint_every < 0 || reunit_every < 0)
+    return set_error(REDO_ERR_INVALID, "negative size");
+  if (reunit_every > 0 && reunit_every != checkpoint_every)
+    return set_error(REDO_ERR_INVALID, "reunit_every (%d) must equal checkpoint_every (%d)", reunit_every,
+                     checkpoint_every);
   if (B == 0) return REDO_OK;
   if (!U_target) return set_error(REDO_ERR_INVALID, "U_target is NULL");
   if (M > 0 && (!q || !h || !grad)) return set_error(REDO_ERR_INVALID, "q, h or grad is NULL");
@@ -1163,14 +1167,17 @@ redo_status redo_fidelity_grad_drift(const redo_table* t, const int32_t* q, cons
     return cuda_error(e, "drift diagonals");
   L.g.p.pd = pd;
   if (t->N > kSmallN) {
-    if ((e = large_grad(t, q, L.g.p, prec, ut, target_batched, F_out, grad, workspace, dev_status, s)) !=
-        cudaSuccess)
+    if ((e = large_grad(t, q, L.g.p, prec, ut, target_batched, F_out, grad, workspace, dev_status, s, nullptr,
+                        nullptr, reunit_every > 0)) != cudaSuccess)
       return cuda_error(e, "large-N drift gradient");
     return REDO_OK;
   }
   void* keep = L.g.keep ? w + L.g.keep_off : nullptr;
   if ((e = launch_chain_segments(t, q, L.g.p, prec, w + L.g.seg_off, dev_status, s, keep)) != cudaSuccess)
     return cuda_error(e, "gradient segments");
+  if (reunit_every > 0 && M > 0 &&
+      (e = launch_polar(t, prec, prec, w + L.g.seg_off, w + L.g.seg_off, B * L.g.p.S, 1, s)) != cudaSuccess)
+    return cuda_error(e, "segment re-unitarisation");
   if ((e = launch_grad_scan(t, B, L.g.p.S, prec, w + L.g.seg_off, ut, target_batched, w + L.g.pck_off,
                             w + L.g.rck_off, tau, F_out, s)) != cudaSuccess)
     return cuda_error(e, "gradient checkpoints");
@@ -1382,6 +1389,33 @@ redo_status redo_mlp_adam(int64_t count, float* params, const float* grads, floa
   cudaError_t e = mlp_adam(count, params, grads, m, v, step, lr, beta1, beta2, eps,
                            (cudaStream_t)stream);
   return e == cudaSuccess ? REDO_OK : cuda_error(e, "adam");
+}
+
+redo_status redo_grape_lbfgs_workspace(const redo_table* t, int64_t B, int64_t M, int32_t history, size_t* bytes) {
+  if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
+  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
+  if (history < 1 || history > 64) return set_error(REDO_ERR_INVALID, "history must be 1..64");
+  *bytes = lbfgs_state_bytes(B, M * t->K, history);
+  return REDO_OK;
+}
+
+redo_status redo_grape_lbfgs_step(const redo_table* t, double* u, const double* grad, const double* F, int64_t B,
+                                  int64_t M, int32_t history, int32_t first, double step0, double c1, void* state,
+                                  size_t state_bytes, double* u_best, double* F_best, void* stream) {
+  if (!t) return set_error(REDO_ERR_INVALID, "table is NULL");
+  if (B < 0 || M < 0) return set_error(REDO_ERR_INVALID, "negative B or M");
+  if (history < 1 || history > 64) return set_error(REDO_ERR_INVALID, "history must be 1..64");
+  if (!(step0 > 0.0) || !std::isfinite(step0) || !(c1 > 0.0 && c1 < 1.0))
+    return set_error(REDO_ERR_INVALID, "step0 > 0 and 0 < c1 < 1 required");
+  if (B == 0 || M == 0) return REDO_OK;
+  if (!u || !grad || !F || !state) return set_error(REDO_ERR_INVALID, "null pointer");
+  const size_t need = lbfgs_state_bytes(B, M * t->K, history);
+  if (state_bytes < need) return set_error(REDO_ERR_INVALID, "state of %zu bytes needed", need);
+  if (((uintptr_t)state & 255) != 0) return set_error(REDO_ERR_INVALID, "state not 256-byte aligned");
+  cudaError_t e = launch_lbfgs_step(t, u, grad, F, B, M, history, first ? 1 : 0, step0, c1, state, u_best, F_best,
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "grape L-BFGS step");
+  return REDO_OK;
 }
 
 redo_status redo_grape_adam_step(const redo_table* t, double* u, const double* grad, double* m,

@@ -163,6 +163,18 @@ cudaError_t launch_grape_adam(double* u, const double* g, double* m, double* v, 
                               const double* lo, const double* delta, int64_t levels, int step, double lr,
                               double b1, double b2, double eps, cudaStream_t s);
 
+// Projected L-BFGS ascent step of the GRAPE loop (kernels_lbfgs.cu): per pulse the accepted
+// point, its gradient, the direction, a ring of `hist` (s, y) pairs and the scalars.
+struct LbfgsState {
+  double *u, *g, *d, *S, *Y, *rho, *F, *alpha;
+  int *count, *head;
+};
+size_t lbfgs_state_bytes(int64_t B, int64_t n, int hist);
+LbfgsState lbfgs_state_layout(void* base, int64_t B, int64_t n, int hist);
+cudaError_t launch_lbfgs_step(const redo_table* t, double* u, const double* g, const double* F, int64_t B,
+                              int64_t M, int hist, int first, double step0, double c1, void* state,
+                              double* u_best, double* F_best, cudaStream_t s);
+
 // GRAPE gradient (kernels_grad.cu).
 cudaError_t launch_grad_scan(const redo_table* t, int64_t B, int64_t S, int prec, const void* seg,
                              const double2* U_target, int target_batched, void* Pck, void* Rck,

@@ -91,14 +91,17 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
     step of a pulse is halved whenever its fidelity decreased and grown by 1.1
     otherwise.  ``optimizer="adam"``: Adam moments per coefficient, ``step`` is
     then the learning rate in rad/s, decayed as step / (1 + it / lr_decay).
+    ``optimizer="lbfgs"``: projected L-BFGS with Armijo backtracking (redo_grape_lbfgs_step,
+    8 pairs), ``step`` the size of a gradient step as a fraction of half the widest grid; every
+    iteration is one fidelity and gradient evaluation, and the result is the accepted point.
     Stops early once every pulse reached ``threshold``.  With ``psi0`` given, ``target`` is a
     state ([N] or [B][N]) and the objective is the state fidelity |<target| U |psi0>|^2
     (redo_state_grad: matrix-vector sweeps instead of propagators).  With ``drift`` ([B][N], rad/s)
     every pulse carries its own diagonal drift (redo_fidelity_grad_drift; the table's own drift,
     usually zero then, is applied as well).  ``on_iter(it, u, F)``, if given, is called after each
     update with the iteration index, the updated coefficients (device, not copied) and that
-    iteration's fidelities (host).  ``reunit_every`` (unitary fidelity without a per-pulse drift; equal
-    to ``checkpoint_every``) re-unitarises every checkpoint segment of the reduced-precision chains.
+    iteration's fidelities (host).  ``reunit_every`` (unitary fidelities; equal to ``checkpoint_every``)
+    re-unitarises every checkpoint segment of the reduced-precision chains.
     """
     u = u0.clone().contiguous()
     B, M, K = u.shape
@@ -126,15 +129,38 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
     if optimizer == "adam":
         m_ = torch.zeros_like(u)
         v_ = torch.zeros_like(u)
+    elif optimizer == "lbfgs":
+        lb_state = torch.empty(max(redo.redo_grape_lbfgs_workspace(table.handle, B, M, 8), 256),
+                               dtype=torch.uint8, device=u.device)
+        u_best = u.clone()
+        F_best = torch.empty(B, dtype=torch.float64, device=u.device)
+    elif optimizer != "gd":
+        raise ValueError(f"unknown optimizer {optimizer!r}")
     for it in range(iters):
         redo.redo_quantize(table.handle, u, q)
         if state:
             redo.redo_state_grad(table.handle, q, prec, psi0, target, F, g, ws)
         elif drift is not None:
-            redo.redo_fidelity_grad_drift(table.handle, q, drift, target, prec, checkpoint_every, F, g, ws)
+            redo.redo_fidelity_grad_drift(table.handle, q, drift, target, prec, checkpoint_every, F, g, ws,
+                                          reunit_every=reunit_every)
         else:
             redo.redo_fidelity_grad(table.handle, q, target, prec, checkpoint_every, F, g, ws,
                                     reunit_every=reunit_every)
+        if optimizer == "lbfgs":
+            # the accepted point's F (it never falls) is the iteration's fidelity
+            redo.redo_grape_lbfgs_step(table.handle, u, g, F, lb_state, it == 0, 8, step, u_best=u_best,
+                                       F_best=F_best)
+            Fh = F_best.cpu()
+            res.F_history.append(Fh.clone())
+            res.iterations = it + 1
+            if on_iter is not None:
+                on_iter(it, u, Fh)
+            if threshold is not None:
+                newly = (Fh >= threshold) & (reached < 0)
+                reached[newly] = it
+                if bool((reached >= 0).all()):
+                    break
+            continue
         Fh = F.cpu()
         res.F_history.append(Fh.clone())
         if threshold is not None:
@@ -157,6 +183,6 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
         res.iterations = it + 1
         if on_iter is not None:
             on_iter(it, u, Fh)
-    res.u = u
+    res.u = u_best if optimizer == "lbfgs" else u
     res.reached = reached
     return res

@@ -33,7 +33,8 @@ EXPORTS = [
     "redo_propagate_phase_workspace", "redo_batched_product", "redo_fidelity_grad_phase",
     "redo_fidelity_grad_phase_workspace", "redo_propagate_drift", "redo_propagate_drift_workspace",
     "redo_fidelity_grad_drift", "redo_fidelity_grad_drift_workspace", "redo_propagate_steps",
-    "redo_propagate_steps_workspace", "redo_reunitarize", "redo_plan",
+    "redo_propagate_steps_workspace", "redo_reunitarize", "redo_plan", "redo_grape_lbfgs_workspace",
+    "redo_grape_lbfgs_step",
 ]
 PROFILE_PHASES = 11
 PHASE_NAMES = ["quantize", "table", "chain_segments", "chain_combine", "finalize", "chain_tc", "reunitarize",
@@ -74,8 +75,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_propagate_phase_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_drift.argtypes = [vp, vp, vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.redo_propagate_drift_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
-    L.redo_fidelity_grad_drift.argtypes = [vp, vp, vp, i64, i64, vp, i32, i32, i32, vp, vp, vp, ctypes.c_size_t, vp,
-                                           vp]
+    L.redo_fidelity_grad_drift.argtypes = [vp, vp, vp, i64, i64, vp, i32, i32, i32, i32, vp, vp, vp, ctypes.c_size_t,
+                                           vp, vp]
     L.redo_fidelity_grad_drift_workspace.argtypes = [vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
     L.redo_propagate_noalloc.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp, vp, vp]
     L.redo_fidelity_grad.argtypes = [vp, vp, i64, i64, vp, i32, i32, i32, i32, vp, vp, vp, ctypes.c_size_t, vp, vp]
@@ -97,6 +98,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.redo_reunitarize.argtypes = [i32, i64, i32, vp, vp, i32, vp]
     L.redo_plan.argtypes = [dbl, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                             ctypes.POINTER(i64)]
+    L.redo_grape_lbfgs_workspace.argtypes = [vp, i64, i64, i32, ctypes.POINTER(ctypes.c_size_t)]
+    L.redo_grape_lbfgs_step.argtypes = [vp, vp, vp, vp, i64, i64, i32, i32, dbl, dbl, vp, ctypes.c_size_t, vp, vp,
+                                        vp]
     L.redo_profile_enable.argtypes = [i32]
     L.redo_profile_read.argtypes = [vp, vp, i32]
     L.redo_last_error.restype = ctypes.c_char_p
@@ -299,14 +303,16 @@ def redo_fidelity_grad_drift_workspace(handle: int, B: int, M: int, prec, checkp
 
 def redo_fidelity_grad_drift(handle: int, q: torch.Tensor, h: torch.Tensor, U_target: torch.Tensor, prec,
                              checkpoint_every: int, F_out: torch.Tensor | None, grad: torch.Tensor,
-                             workspace: torch.Tensor, status: torch.Tensor | None = None, stream=None):
+                             workspace: torch.Tensor, status: torch.Tensor | None = None, stream=None,
+                             reunit_every: int = 0):
     """redo_fidelity_grad with pulse b's diagonal drift h[b] (device float64 [B][N], rad/s)."""
     B, M = q.shape[0], q.shape[1]
     batched = 1 if U_target.dim() == 3 else 0
     _check(load_library().redo_fidelity_grad_drift(ctypes.c_void_p(handle), _ptr(q), _ptr(h), B, M, _ptr(U_target),
-                                                   batched, _prec(prec), checkpoint_every, _ptr(F_out), _ptr(grad),
-                                                   _ptr(workspace), workspace.numel() * workspace.element_size(),
-                                                   _ptr(status), _stream(stream)))
+                                                   batched, _prec(prec), checkpoint_every, int(reunit_every),
+                                                   _ptr(F_out), _ptr(grad), _ptr(workspace),
+                                                   workspace.numel() * workspace.element_size(), _ptr(status),
+                                                   _stream(stream)))
 
 
 def redo_grape_step(handle: int, u: torch.Tensor, grad: torch.Tensor, step: float,
@@ -399,6 +405,22 @@ def redo_grape_adam_step(handle: int, u, grad, m, v, step: int, lr: float, beta1
     _check(load_library().redo_grape_adam_step(ctypes.c_void_p(handle), _ptr(u), _ptr(grad), _ptr(m), _ptr(v), B, M,
                                                int(step), float(lr), float(beta1), float(beta2), float(eps),
                                                _stream(stream)))
+
+
+def redo_grape_lbfgs_workspace(handle: int, B: int, M: int, history: int = 8) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().redo_grape_lbfgs_workspace(ctypes.c_void_p(handle), B, M, history, ctypes.byref(n)))
+    return n.value
+
+
+def redo_grape_lbfgs_step(handle: int, u, grad, F, state, first: bool, history: int = 8, step0: float = 0.05,
+                          c1: float = 1e-4, u_best=None, F_best=None, stream=None):
+    """In place: u (the point just evaluated) becomes the next point of projected L-BFGS ascent."""
+    B, M = u.shape[0], u.shape[1]
+    _check(load_library().redo_grape_lbfgs_step(ctypes.c_void_p(handle), _ptr(u), _ptr(grad), _ptr(F), B, M,
+                                                int(history), 1 if first else 0, float(step0), float(c1),
+                                                _ptr(state), state.numel() * state.element_size(), _ptr(u_best),
+                                                _ptr(F_best), _stream(stream)))
 
 
 def redo_profile_enable(enable: bool):
@@ -553,7 +575,7 @@ def _table_propagate_drift(self, q, h, prec="fp64", target=None, want_U=True, st
     return U, F, tau
 
 
-def _table_fidelity_grad_drift(self, q, h, target, prec="fp64", checkpoint_every=0, status=None):
+def _table_fidelity_grad_drift(self, q, h, target, prec="fp64", checkpoint_every=0, status=None, reunit_every=0):
     """(F [B], dF/du [B][M][K]) with a diagonal drift per pulse (h [B][N], rad/s)."""
     B, M = q.shape[0], q.shape[1]
     h = torch.as_tensor(h, dtype=torch.float64, device=self.device).contiguous()
@@ -562,7 +584,8 @@ def _table_fidelity_grad_drift(self, q, h, target, prec="fp64", checkpoint_every
     g = torch.empty((B, M, self.K), dtype=torch.float64, device=self.device)
     nbytes = redo_fidelity_grad_drift_workspace(self.handle, B, M, prec, checkpoint_every)
     ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
-    redo_fidelity_grad_drift(self.handle, q, h, target, prec, checkpoint_every, F, g, ws, status)
+    redo_fidelity_grad_drift(self.handle, q, h, target, prec, checkpoint_every, F, g, ws, status,
+                             reunit_every=reunit_every)
     return F, g
 
 

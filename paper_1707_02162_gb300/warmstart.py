@@ -93,12 +93,24 @@ class WarmStartReport:
 
 
 def converge(table: redo.Table, targets: np.ndarray, u0: np.ndarray, iters: int, step: float, threshold: float,
-             prec="fp64", optimizer="gd", drift=None):
+             prec="fp64", optimizer="gd", drift=None, chunk: int = 256, reunit_every: int = 0):
     """Batched GRAPE on per-instance targets (and, with ``drift`` [B][N], per-instance diagonal
-    drifts); returns (u, first iteration reaching threshold per instance, the GRAPE result)."""
-    res = grape(table, torch.as_tensor(targets, device=table.device), torch.as_tensor(u0, device=table.device),
-                iters=iters, step=step, prec=prec, threshold=threshold, optimizer=optimizer, drift=drift)
-    return res.u, res.reached.tolist(), res
+    drifts), ``chunk`` instances per batch (so that every forward state of a batch stays kept);
+    returns (u, first iteration reaching threshold per instance, fidelity history [iters][B])."""
+    us, reached, hist = [], [], []
+    for a in range(0, len(u0), chunk):
+        b = min(a + chunk, len(u0))
+        res = grape(table, torch.as_tensor(targets[a:b], device=table.device),
+                    torch.as_tensor(u0[a:b], device=table.device), iters=iters, step=step, prec=prec,
+                    threshold=threshold, optimizer=optimizer, drift=None if drift is None else drift[a:b],
+                    checkpoint_every=reunit_every, reunit_every=reunit_every)
+        us.append(res.u)
+        reached += res.reached.tolist()
+        F = torch.stack(res.F_history)
+        if F.shape[0] < iters:                 # stopped early: every instance reached; hold the last values
+            F = torch.cat([F, F[-1:].expand(iters - F.shape[0], -1)])
+        hist.append(F)
+    return torch.cat(us), reached, torch.cat(hist, dim=1)
 
 
 def local_pauli_family(n_qubits: int, n_strings: int, rng: np.random.Generator) -> list[str]:
@@ -117,8 +129,9 @@ def local_pauli_family(n_qubits: int, n_strings: int, rng: np.random.Generator) 
 
 def study(table: redo.Table, n_qubits: int, M: int, K: int, Omega: float, features_const: np.ndarray | None = None,
           n_train: int = 512, n_test: int = 64, threshold: float = 0.99, iters: int = 400, step: float = 0.0,
-          theta_max: float = np.pi / 2, train_steps: int = 1500, hidden=(512, 512, 512), seed: int = 4,
-          prec: str = "fp32", per_instance_drift: bool = False) -> WarmStartReport:
+          theta_max: float = np.pi, train_steps: int = 1500, hidden=(512, 512, 512), seed: int = 4,
+          prec: str = "fp32", per_instance_drift: bool = False, optimizer: str = "lbfgs",
+          reunit_every: int = 50) -> WarmStartReport:
     """Learned warm start: targets exp(-i sum_k theta_k P_k) over a fixed set of Pauli strings;
     MLP input = (system constants, theta); output = M*K normalised amplitudes.
 
@@ -126,12 +139,17 @@ def study(table: redo.Table, n_qubits: int, M: int, K: int, Omega: float, featur
     ``features_const`` head every input.  ``per_instance_drift=True``: the table must be built
     with H0 = 0; every instance draws its own offsets nu ~ U[-5, 5] kHz and couplings
     J ~ U[-200, 200] Hz (i < j), GRAPE runs with that diagonal drift per instance, and the input
-    is (nu / 5 kHz, J / 200 Hz, theta): for 5 qubits 5 + 10 + 8 = 23 numbers."""
+    is (nu / 5 kHz, J / 200 Hz, theta): for 5 qubits 5 + 10 + 8 = 23 numbers.
+
+    ``optimizer``: "lbfgs" (``step`` = size of a gradient step as a fraction of half the grid,
+    default 0.05) or "adam" (``step`` = learning rate in rad/s, default 0.01 Omega).  Reduced
+    precision chains are re-unitarised every ``reunit_every`` steps (their checkpoint segments)."""
     from scipy.linalg import expm as _expm   # target construction only (problem input)
     from .inputs import drift_zz, pauli_generator
     rng = np.random.default_rng(seed)
     strings = local_pauli_family(n_qubits, 8, rng)
-    lr = step if step > 0 else 0.01 * Omega          # Adam learning rate in rad/s
+    lr = step if step > 0 else (0.05 if optimizer == "lbfgs" else 0.01 * Omega)
+    ru = reunit_every if prec != "fp64" else 0
     iu = np.triu_indices(n_qubits, 1)
 
     def targets(count):
@@ -160,7 +178,7 @@ def study(table: redo.Table, n_qubits: int, M: int, K: int, Omega: float, featur
     # every training instance starts from the same pulse, so that the converged pulses
     # follow one smooth branch of solutions in theta (what the network can learn)
     u0 = np.broadcast_to(rng.uniform(-0.3 * Omega, 0.3 * Omega, size=(1, M, K)), (n_train, M, K)).copy()
-    u_tr, reached, _ = converge(table, T_tr, u0, iters, lr, threshold, prec, "adam", drift=h_tr)
+    u_tr, reached, _ = converge(table, T_tr, u0, iters, lr, threshold, prec, optimizer, drift=h_tr, reunit_every=ru)
     ok = np.array(reached) >= 0
     if not ok.any():
         raise RuntimeError("no training instance reached the threshold; raise iters or lr")
@@ -175,17 +193,16 @@ def study(table: redo.Table, n_qubits: int, M: int, K: int, Omega: float, featur
     u_mlp = net.forward(feats(sys_te, th_te)).cpu().numpy().reshape(n_test, M, K).astype(np.float64) * Omega
     u_rnd = rng.uniform(-0.3 * Omega, 0.3 * Omega, size=(n_test, M, K))
     # threshold=None keeps every run to the full budget so the final fidelities compare
-    _, _, r_mlp = converge(table, T_te, u_mlp, iters, lr, None, prec, "adam", drift=h_te)
-    _, _, r_rnd = converge(table, T_te, u_rnd, iters, lr, None, prec, "adam", drift=h_te)
+    _, _, F_mlp = converge(table, T_te, u_mlp, iters, lr, None, prec, optimizer, drift=h_te, reunit_every=ru)
+    _, _, F_rnd = converge(table, T_te, u_rnd, iters, lr, None, prec, optimizer, drift=h_te, reunit_every=ru)
 
-    def first_reach(res):
-        F = torch.stack(res.F_history)                      # [iters][B]
-        hit = F >= threshold
+    def first_reach(F):
+        hit = F >= threshold                                # F: [iters][B]
         out = []
         for b in range(F.shape[1]):
             idx = torch.nonzero(hit[:, b])
             out.append(int(idx[0]) if idx.numel() else -1)
         return out, float(F[0].median()), float(F[-1].median())
-    it_mlp, f0m, fem = first_reach(r_mlp)
-    it_rnd, f0r, fer = first_reach(r_rnd)
+    it_mlp, f0m, fem = first_reach(F_mlp)
+    it_rnd, f0r, fer = first_reach(F_rnd)
     return WarmStartReport(int(ok.sum()), n_test, threshold, it_rnd, it_mlp, loss, f0r, f0m, fer, fem)

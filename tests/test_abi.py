@@ -67,7 +67,11 @@ def test_host_validation_without_device(lib):
     n = ctypes.c_size_t()
     assert lib.redo_propagate_drift(None, None, None, 1, 1, 0, 0, None, None, None, None, None, 0, None, None) == 1
     assert lib.redo_propagate_drift_workspace(None, 1, 1, 0, 0, ctypes.byref(n)) == 1
-    assert lib.redo_fidelity_grad_drift(None, None, None, 1, 1, None, 0, 0, 0, None, None, None, 0, None, None) == 1
+    assert lib.redo_fidelity_grad_drift(None, None, None, 1, 1, None, 0, 0, 0, 0, None, None, None, 0, None,
+                                        None) == 1
+    assert lib.redo_fidelity_grad(None, None, 1, 1, None, 0, 0, 0, 0, None, None, None, 0, None, None) == 1
+    assert lib.redo_grape_lbfgs_workspace(None, 1, 1, 8, ctypes.byref(n)) == 1
+    assert lib.redo_grape_lbfgs_step(None, None, None, None, 1, 1, 8, 1, 0.05, 1e-4, None, 0, None, None, None) == 1
     assert lib.redo_fidelity_grad_drift_workspace(None, 1, 1, 0, 0, ctypes.byref(n)) == 1
     assert lib.redo_propagate_phase(None, None, None, 1, 1, 0, 0, None, None, None, None, None, 0, None, None) == 1
     assert lib.redo_fidelity_grad_phase(None, None, None, 1, 1, None, 0, 0, 0, None, None, None, None, 0, None,

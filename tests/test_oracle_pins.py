@@ -731,6 +731,117 @@ def test_grape_ascent_reaches_a_one_qubit_target():
     assert hist[0] < 0.01 and hist[-1] > 0.9999
 
 
+def _bfgs_inverse(pairs, n):
+    """Explicit inverse-Hessian BFGS recursion H <- V^T H V + rho s s^T, V = I - rho y s^T,
+    from H0 = gamma I (gamma from the newest pair), as matrices."""
+    s, y = pairs[-1]
+    H = (s @ y) / (y @ y) * np.eye(n)
+    for s, y in pairs:
+        rho = 1.0 / (s @ y)
+        V = np.eye(n) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    return H
+
+
+def test_lbfgs_two_loop_equals_the_explicit_bfgs_matrix():
+    rng = np.random.default_rng(13)
+    n = 7
+    A = rng.standard_normal((n, n))
+    A = A @ A.T + n * np.eye(n)                      # f's Hessian (F = -f is concave)
+    pairs = []
+    for _ in range(4):
+        s = rng.standard_normal(n)
+        pairs.append((s, A @ s))
+        g = rng.standard_normal(n)
+        H = _bfgs_inverse(pairs, n)
+        assert np.allclose(O.lbfgs_direction(g, pairs), H @ g, rtol=1e-12, atol=1e-12)
+    # no pairs: the gradient itself; the newest secant pair is reproduced exactly
+    assert np.array_equal(O.lbfgs_direction(g, []), g)
+    s, y = pairs[-1]
+    assert np.allclose(O.lbfgs_direction(y, pairs), s, rtol=1e-12, atol=1e-12)
+
+
+def _lbfgs_run(Fg, u0, lo, hi, iters, **kw):
+    u, state, hist = u0.copy(), {}, []
+    for it in range(iters):
+        F, g = Fg(u)
+        hist.append(F)
+        u, state = O.grape_lbfgs_step(u, g, F, state, lo, hi, first=(it == 0), **kw)
+    return state, hist
+
+
+def test_lbfgs_step_maximises_a_concave_quadratic():
+    rng = np.random.default_rng(14)
+    M, K = 4, 3
+    n = M * K
+    A = rng.standard_normal((n, n))
+    A = A @ A.T / n + 0.5 * np.eye(n)
+    ustar = rng.uniform(-0.5, 0.5, size=(M, K))
+    lo, hi = np.full(K, -1.0), np.full(K, 1.0)
+
+    def Fg(u):
+        e = (u - ustar).ravel()
+        return -0.5 * e @ A @ e, -(A @ e).reshape(M, K)
+
+    state, hist = _lbfgs_run(Fg, np.zeros((M, K)), lo, hi, 60)
+    assert np.abs(state["u"] - ustar).max() < 1e-7
+    # accepted fidelities never fall
+    Fs, u, st = [], np.zeros((M, K)), {}
+    for it in range(30):
+        F, g = Fg(u)
+        u, st = O.grape_lbfgs_step(u, g, F, st, lo, hi, first=(it == 0))
+        Fs.append(st["F"])
+    assert all(b >= a for a, b in zip(Fs, Fs[1:]))
+
+
+def test_lbfgs_step_respects_the_grid_and_reaches_a_corner():
+    # separable quadratic whose maximiser lies outside the box: the box corner is the answer
+    M, K = 3, 2
+    lo, hi = np.array([-1.0, -2.0]), np.array([1.0, 2.0])
+    ustar = np.tile(np.array([3.0, -5.0]), (M, 1))
+
+    def Fg(u):
+        e = u - ustar
+        return -0.5 * float(np.sum(e * e)), -e
+
+    state, _ = _lbfgs_run(Fg, np.zeros((M, K)), lo, hi, 40)
+    assert np.allclose(state["u"], np.tile(np.array([1.0, -2.0]), (M, 1)), atol=1e-12)
+
+
+def test_lbfgs_backtracks_and_restarts():
+    # a rejected trial halves alpha; after ten halvings the pairs are dropped
+    lo, hi = np.array([-10.0]), np.array([10.0])
+    u0 = np.zeros((1, 1))
+    st = {}
+    _, st = O.grape_lbfgs_step(u0, np.array([[1.0]]), 0.0, st, lo, hi, first=True)
+    assert st["alpha"] == 1.0 and np.allclose(st["d"], [[0.05 * 10.0]])
+    st["pairs"] = [(np.array([1.0]), np.array([1.0]))]
+    ut = u0 + st["d"]
+    for i in range(1, 11):
+        ut, st = O.grape_lbfgs_step(ut, np.array([[1.0]]), -1.0, st, lo, hi)     # F fell: reject
+        if i < 10:
+            assert st["alpha"] == 0.5 ** i and st["pairs"]
+    assert st["alpha"] == 1.0 and st["pairs"] == []
+
+
+def test_lbfgs_grape_reaches_a_one_qubit_target():
+    H0 = 2 * np.pi * 300.0 * SZ / 2
+    Hk = np.stack([SX / 2, SY / 2])
+    dt, L, M = 1e-5, 4096, 10
+    Om = 2 * np.pi * 1e4
+    lo, hi = np.array([-Om, -Om]), np.array([Om, Om])
+    T, D = O.build_table(H0, Hk, dt, lo, hi, L, 64, 2)
+    UT = O.expm_hermitian((SX + SZ) / math.sqrt(2), math.pi / 2)
+
+    def Fg(u):
+        q, _, _ = O.quantize(u[None], lo, hi, L)
+        return O.grape_gradient(T, D, Hk, dt, O.level_digits(q, 64, 2)[0], UT)
+
+    u0 = np.random.default_rng(3).uniform(-Om, Om, size=(M, 2)) * 0.3
+    state, hist = _lbfgs_run(Fg, u0, lo, hi, 30)
+    assert hist[0] < 0.01 and state["F"] > 0.9999
+
+
 # ---------------------------------------------------------------- amplitude/phase controls
 
 def _two_species():
