@@ -83,15 +83,15 @@ def test_grape_adam_kernel_matches_oracle_three_steps():
     rng = np.random.default_rng(6)
     ud = torch.tensor(u, device="cuda")
     md, vd = torch.zeros_like(ud), torch.zeros_like(ud)
-    uo, mo, vo = u.copy(), np.zeros_like(u), np.zeros_like(u)
     lr = 2e3
     b1, b2 = 0.9, 0.999
     for step in (1, 2, 3):
         g = rng.standard_normal(u.shape) * 1e-7
         g[0, :5] = 0.0                             # zero gradients stay put (eps guards the division)
+        # each step is compared from the same state: the kernel's moments and coefficients so far
+        u_prev, m_prev, v_prev = ud.cpu().numpy(), md.cpu().numpy(), vd.cpu().numpy()
         redo.redo_grape_adam_step(t.handle, ud, torch.tensor(g, device="cuda"), md, vd, step, lr)
-        u_prev, m_prev, v_prev = uo, mo, vo
-        uo, mo, vo = O.grape_adam_update(uo, g, mo, vo, step, lr, w.lo, w.hi)
+        uo, mo, vo = O.grape_adam_update(u_prev, g, m_prev, v_prev, step, lr, w.lo, w.hi)
         # b1 m + (1 - b1) g can cancel: bound by the size of its terms, not of the result
         assert (np.abs(md.cpu().numpy() - mo) <= 4 * ULP * (b1 * np.abs(m_prev) + (1 - b1) * np.abs(g))).all()
         assert (np.abs(vd.cpu().numpy() - vo) <= 4 * ULP * (b2 * v_prev + (1 - b2) * g * g)).all()
