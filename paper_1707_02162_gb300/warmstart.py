@@ -131,7 +131,7 @@ def study(table: redo.Table, n_qubits: int, M: int, K: int, Omega: float, featur
           n_train: int = 512, n_test: int = 64, threshold: float = 0.99, iters: int = 400, step: float = 0.0,
           theta_max: float = np.pi, train_steps: int = 1500, hidden=(512, 512, 512), seed: int = 4,
           prec: str = "fp32", per_instance_drift: bool = False, optimizer: str = "lbfgs",
-          reunit_every: int = 50) -> WarmStartReport:
+          reunit_every: int = 50, train_threshold: float | None = None) -> WarmStartReport:
     """Learned warm start: targets exp(-i sum_k theta_k P_k) over a fixed set of Pauli strings;
     MLP input = (system constants, theta); output = M*K normalised amplitudes.
 
@@ -143,7 +143,10 @@ def study(table: redo.Table, n_qubits: int, M: int, K: int, Omega: float, featur
 
     ``optimizer``: "lbfgs" (``step`` = size of a gradient step as a fraction of half the grid,
     default 0.05) or "adam" (``step`` = learning rate in rad/s, default 0.01 Omega).  Reduced
-    precision chains are re-unitarised every ``reunit_every`` steps (their checkpoint segments)."""
+    precision chains are re-unitarised every ``reunit_every`` steps (their checkpoint segments).
+    The training pulses are converged to ``train_threshold`` (default: ``threshold``) and the
+    ones that reach it are the training set; the test instances run the whole budget from both
+    starts and report the first iteration at ``threshold``."""
     from scipy.linalg import expm as _expm   # target construction only (problem input)
     from .inputs import drift_zz, pauli_generator
     rng = np.random.default_rng(seed)
@@ -178,7 +181,8 @@ def study(table: redo.Table, n_qubits: int, M: int, K: int, Omega: float, featur
     # every training instance starts from the same pulse, so that the converged pulses
     # follow one smooth branch of solutions in theta (what the network can learn)
     u0 = np.broadcast_to(rng.uniform(-0.3 * Omega, 0.3 * Omega, size=(1, M, K)), (n_train, M, K)).copy()
-    u_tr, reached, _ = converge(table, T_tr, u0, iters, lr, threshold, prec, optimizer, drift=h_tr, reunit_every=ru)
+    thr_tr = threshold if train_threshold is None else train_threshold
+    u_tr, reached, _ = converge(table, T_tr, u0, iters, lr, thr_tr, prec, optimizer, drift=h_tr, reunit_every=ru)
     ok = np.array(reached) >= 0
     if not ok.any():
         raise RuntimeError("no training instance reached the threshold; raise iters or lr")
