@@ -977,14 +977,23 @@ def run_workload(args):
         ms = _events_time(it_drift, args.steps)
         res["fp32_per_instance_drift"] = {"instance_iters_per_s": B * 1e3 / ms, "ms_per_batched_iter": ms}
         from paper_1707_02162_gb300.warmstart import MLP
-        net = MLP([23, 512, 512, 512, w.M * w.K])
-        x = torch.randn(1024, 23)
-        y = torch.rand(1024, w.M * w.K) * 2 - 1
-        net.train_step(x, y, 1e-3)
-        ms = _events_time(lambda: net.train_step(x, y, 1e-3), 5)
+        sizes = [23, 512, 512, 512, w.M * w.K]
+        net = MLP(sizes)
+        # forward + backward GEMM flop per sample: 2 in*out for z, 2 for dW, 2 for dh (no dh into x)
+        fl = sum(2 * a * b for a, b in zip(sizes[:-1], sizes[1:])) * 3 - 2 * sizes[0] * sizes[1]
+        mlp = {}
+        for nb in (1024, 8192):
+            x = torch.randn(nb, 23)
+            y = torch.rand(nb, w.M * w.K) * 2 - 1
+            net.train_step(x, y, 1e-3)
+            ms = _events_time(lambda: net.train_step(x, y, 1e-3), 5)
+            tf = fl * nb / (ms / 1e3) / 1e12
+            mlp[f"batch_{nb}"] = {"samples_per_s": nb / (ms / 1e3), "ms_per_step": ms, "gemm_tflops": tf,
+                                  "frac_of_bf16_burst": tf / _peaks().get("bf16_tflops", 1908.8),
+                                  "hardware_frac_x3": 3 * tf / _peaks().get("bf16_tflops", 1908.8)}
         out.update({"metric": "GRAPE iters/s (batched instances, N=32)", "unit": "instance-iterations/s",
                     "value": res["fp32"]["instance_iters_per_s"], "results": res,
-                    "mlp_train_samples_per_s": 1024 / (ms / 1e3),
+                    "mlp_train_samples_per_s": mlp["batch_1024"]["samples_per_s"], "mlp_training": mlp,
                     "config": {"N": w.N, "K": w.K, "M": w.M, "instances": B, "mlp": "23-512-512-512-5000"}})
     print(json.dumps(out))
 

@@ -411,8 +411,9 @@ redo_status redo_grape_step(const redo_table* t, double* u, const double* grad, 
  * flat array holding W_0 (sizes[1] x sizes[0], row-major), b_0, W_1, b_1, ...
  *
  * redo_mlp_sizes: float counts of params, of the activation buffer `acts`
- *   (z and h of every layer for `batch` samples) and of the backward `work`
- *   buffer.  Host only.
+ *   (z and h of every layer for `batch` samples, then scratch for the forward
+ *   GEMMs' split BF16 operand planes) and of the backward `work` buffer (two
+ *   gradient buffers, then the backward GEMMs' plane scratch).  Host only.
  * redo_mlp_forward: x [batch][sizes[0]] -> y [batch][sizes[layers]], filling acts.
  * redo_mlp_backward: gradients of loss = mean over all entries of
  *   (y - y_target)^2 into grads (same layout as params), using the acts of the

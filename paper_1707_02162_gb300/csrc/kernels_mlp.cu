@@ -9,10 +9,13 @@
 // The GEMMs run on the tensor cores (tcgen05, kind::f16 with BF16 operands): every FP32
 // operand value is split as hi = bf16(v), lo = bf16(v - hi) and a product takes
 // hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory (about 16 significant bits
-// per operand, the FP32 exponent range).  A CTA computes one 128 x 128 tile of C: its threads
-// stage 64-wide K slices of A and B (any strides, converted and split on the way) into
-// 128-byte-swizzled K-major tiles, one thread issues the MMAs of a slice while the next slice
-// is staged, and eight warps read the accumulator back for the bias and activation.
+// per operand, the FP32 exponent range).  Each operand of a GEMM is split once, by one CTA per
+// 128-row x 64-K tile, into 128-byte-swizzled K-major hi/lo planes in a scratch buffer (a weight
+// or activation tile is otherwise converted again by every CTA that reads it: 40 times for the
+// 5000-wide output layer).  A CTA then computes one 128 x 128 tile of C: one thread streams
+// the A and B plane tiles of each 64-wide K slice through a three-stage ring of bulk copies,
+// one thread issues the MMAs, and eight warps read the accumulator back for the bias and
+// activation.
 #include <cuda_bf16.h>
 
 #include "redo_internal.cuh"
@@ -47,8 +50,6 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 
 constexpr int kMT = 128, kNT = 128, kKT = 64;                 // C tile, K slice (bf16)
 constexpr uint32_t kMPlane = kMT * kKT * 2;                      // 16 KB: 128 rows x 64 bf16
-constexpr uint32_t kMStage = 4 * kMPlane;                        // A hi, A lo, B hi, B lo
-constexpr uint32_t kMSmem = 2 * kMStage + 1024 + 64;
 constexpr uint32_t kMLimit = 1u << 24;
 // kind::f16 instruction descriptor: D f32, A and B bf16, K-major, N = 128, M = 128
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kNT >> 3) << 17) |
@@ -58,7 +59,7 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) 
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// Stage a 128-row x 64-K tile of a strided operand (element (r, k) at X[r * s_r + k * s_k],
+// Split a 128-row x 64-K tile of a strided operand (element (r, k) at X[r * s_r + k * s_k],
 // zero outside rows x K) into hi / lo planes; groups of 8 consecutive k per thread, threads
 // laid along whichever index is contiguous in memory.
 __device__ __forceinline__ void stage_tile(const float* __restrict__ X, int64_t s_r, int64_t s_k, int rows, int K,
@@ -88,17 +89,40 @@ __device__ __forceinline__ void stage_tile(const float* __restrict__ X, int64_t 
   }
 }
 
-__global__ void __launch_bounds__(256, 1) gemm_tc_kernel(GemmArgs g, int64_t* status) {
+// One 128-row x 64-K tile (rt, kt) of a strided FP32 operand per CTA, split into its hi and lo
+// planes (16 KB each, the layout stage_tile writes) at planes + (rt * KT + kt) * 32 KB.
+__global__ void __launch_bounds__(256) split_planes_kernel(const float* __restrict__ X, int64_t s_r, int64_t s_k,
+                                                           int rows, int K, int KT, uint8_t* __restrict__ planes) {
+  const int rt = blockIdx.y, kt = blockIdx.x;
+  uint8_t* hi = planes + ((size_t)rt * KT + kt) * (2 * kMPlane);
+  stage_tile(X, s_r, s_k, rows, K, rt * kMT, kt * kKT, hi, hi + kMPlane, threadIdx.x);
+}
+
+constexpr int kPStages = 3;
+constexpr uint32_t kPStage = 4 * kMPlane;                        // A hi, A lo, B hi, B lo (64 KB)
+constexpr uint32_t kPSmem = kPStages * kPStage + 1024 + 128;
+
+// C tile from pre-split planes: A planes [ceil(M/128)][KT], B planes [ceil(N/128)][KT].  With
+// split > 1 CTA z takes K slices [z KT / split, (z + 1) KT / split) and writes its partial tile,
+// without bias or activation, to part + z M N (row-major, ldc = N).
+__global__ void __launch_bounds__(256, 1) gemm_planes_kernel(GemmArgs g, const uint8_t* __restrict__ pa,
+                                                             const uint8_t* __restrict__ pb, int KT, int split,
+                                                             float* __restrict__ part, int64_t* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint64_t* done = reinterpret_cast<uint64_t*>(smem + 2 * kMStage);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kPStages * kPStage);
+  uint64_t* empty = full + kPStages;
+  uint64_t* done = empty + kPStages;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = blockIdx.y * kMT, j0 = blockIdx.x * kNT;
   if (tid == 0) {
-    mbar_init(&done[0], 1);
-    mbar_init(&done[1], 1);
+    for (int st = 0; st < kPStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    mbar_init(done, 1);
     *abort_flag = 0;
     fence_mbarrier_init();
   }
@@ -107,23 +131,34 @@ __global__ void __launch_bounds__(256, 1) gemm_tc_kernel(GemmArgs g, int64_t* st
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int nk = (g.K + kKT - 1) / kKT;
-  bool ok = true;
-  int issued = 0;                                   // slices whose MMAs were committed
-  for (int kt = 0; kt < nk; ++kt) {
-    const int st = kt & 1;
-    uint8_t* base = smem + st * kMStage;
-    // the MMAs that read this stage two slices ago are done
-    if (kt >= 2 && !mbar_wait_bounded_n(&done[st], (uint32_t)(((kt - 2) >> 1) & 1), kMLimit)) ok = false;
-    ok = __syncthreads_and(ok && !*abort_flag);
-    if (!ok) break;
-    stage_tile(g.A, g.sa0, g.sa1, g.M, g.K, i0, kt * kKT, base, base + kMPlane, tid);
-    stage_tile(g.B, g.sb1, g.sb0, g.N, g.K, j0, kt * kKT, base + 2 * kMPlane, base + 3 * kMPlane, tid);
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
+  const int z = blockIdx.z;
+  const int k0 = (int)((int64_t)z * KT / split), k1 = (int)((int64_t)(z + 1) * KT / split);
+  const int NK = k1 - k0;                                // K slices of this CTA
+  const uint8_t* a_tiles = pa + ((size_t)blockIdx.y * KT + k0) * (2 * kMPlane);
+  const uint8_t* b_tiles = pb + ((size_t)blockIdx.x * KT + k0) * (2 * kMPlane);
+  if (tid == 0) {
+    // producer: the A and B plane tiles of every K slice, kPStages slices ahead
+    for (int kt = 0; kt < NK && !*abort_flag; ++kt) {
+      const int st = kt % kPStages;
+      if (kt >= kPStages && !mbar_wait_bounded_n(&empty[st], (uint32_t)(((kt / kPStages) - 1) & 1), kMLimit)) {
+        *abort_flag = 1;
+        break;
+      }
+      uint8_t* base = smem + st * kPStage;
+      mbar_arrive_expect_tx(&full[st], kPStage);
+      bulk_load(base, a_tiles + (size_t)kt * (2 * kMPlane), 2 * kMPlane, &full[st]);
+      bulk_load(base + 2 * kMPlane, b_tiles + (size_t)kt * (2 * kMPlane), 2 * kMPlane, &full[st]);
+    }
+  } else if (tid == 32) {
+    // MMA issuer
+    for (int kt = 0; kt < NK; ++kt) {
+      const int st = kt % kPStages;
+      if (*abort_flag || !mbar_wait_bounded_n(&full[st], (uint32_t)((kt / kPStages) & 1), kMLimit)) {
+        *abort_flag = 1;
+        break;
+      }
       tc::tc_fence_after();
-      const uint32_t a_hi = smem_u32(base), a_lo = a_hi + kMPlane;
+      const uint32_t a_hi = smem_u32(smem + st * kPStage), a_lo = a_hi + kMPlane;
       const uint32_t b_hi = a_hi + 2 * kMPlane, b_lo = a_hi + 3 * kMPlane;
 #pragma unroll
       for (int kk = 0; kk < kKT / 16; ++kk) {
@@ -133,16 +168,14 @@ __global__ void __launch_bounds__(256, 1) gemm_tc_kernel(GemmArgs g, int64_t* st
         tc::mma_f16(tmem, tc::smem_desc_sw128(a_hi + o), tc::smem_desc_sw128(b_lo + o), kIdescBf16, 1u);
         tc::mma_f16(tmem, tc::smem_desc_sw128(a_lo + o), tc::smem_desc_sw128(b_hi + o), kIdescBf16, 1u);
       }
-      tc::mma_commit(&done[st]);
+      tc::mma_commit(&empty[st]);
+      if (kt == NK - 1) tc::mma_commit(done);
     }
-    ++issued;
   }
-  // the last committed slice's MMAs (and with them every earlier one) are done
-  if (issued > 0) {
-    const int last = issued - 1;
-    if (!mbar_wait_bounded_n(&done[last & 1], (uint32_t)((last >> 1) & 1), kMLimit)) ok = false;
-  }
-  ok = __syncthreads_and(ok);
+  __syncthreads();                     // the other threads wait here, not spinning, while the two work
+  bool ok = true;
+  if (NK > 0) ok = mbar_wait_bounded_n(done, 0u, kMLimit);
+  ok = __syncthreads_and(ok && !*abort_flag);
   tc::tc_fence_after();
   if (!ok) {
     if (tid == 0 && status) atomicAdd((unsigned long long*)&status[REDO_STATUS_TIMEOUT], 1ull);
@@ -154,7 +187,7 @@ __global__ void __launch_bounds__(256, 1) gemm_tc_kernel(GemmArgs g, int64_t* st
     for (int c0 = 0; c0 < 64; c0 += 32) {
       uint32_t r[32];
       const int jb = 64 * hcol + c0;
-      if (nk > 0) {
+      if (NK > 0) {
         tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)jb, r);
         tc::tmem_wait_ld();
       } else {
@@ -166,6 +199,10 @@ __global__ void __launch_bounds__(256, 1) gemm_tc_kernel(GemmArgs g, int64_t* st
         for (int c = 0; c < 32; ++c) {
           const int j = j0 + jb + c;
           if (j < g.N) {
+            if (split > 1) {
+              part[((int64_t)z * g.M + i) * g.N + j] = __uint_as_float(r[c]);
+              continue;
+            }
             const float v = __uint_as_float(r[c]) + (g.bias ? g.bias[j] : 0.f);
             g.C[(int64_t)i * g.ldc + j] = v;
             if (g.Cact) g.Cact[(int64_t)i * g.ldc + j] = g.act == 1 ? gelu_f(v) : (g.act == 2 ? tanhf(v) : v);
@@ -179,12 +216,65 @@ __global__ void __launch_bounds__(256, 1) gemm_tc_kernel(GemmArgs g, int64_t* st
   if (warp == 0) tc::tmem_dealloc(tmem, kNT);
 }
 
-static cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
+// C = sum_z part[z] (+ bias) in a fixed order, optional activation into Cact.
+__global__ void splitk_reduce_kernel(GemmArgs g, const float* __restrict__ part, int split) {
+  const int64_t n = (int64_t)g.M * g.N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / g.N;
+    const int j = (int)(idx - i * g.N);
+    float v = 0.f;
+    for (int z = 0; z < split; ++z) v += part[(int64_t)z * n + idx];
+    if (g.bias) v += g.bias[j];
+    g.C[i * g.ldc + j] = v;
+    if (g.Cact) g.Cact[i * g.ldc + j] = g.act == 1 ? gelu_f(v) : (g.act == 2 ? tanhf(v) : v);
+  }
+}
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// K splits of one GEMM: when its C tiles fill less than half the GPU and its K loop is long,
+// enough splits (of at least 8 K slices each) to give about one CTA per SM.
+static int gemm_splits(int64_t M, int64_t N, int64_t K) {
+  const int64_t tiles = ceil_div(M, kMT) * ceil_div(N, kNT), KT = ceil_div(K, kKT);
+  if (tiles >= 76 || KT < 16) return 1;
+  int64_t sp = ceil_div(152, tiles);
+  if (sp > KT / 8) sp = KT / 8;
+  return sp < 1 ? 1 : (int)sp;
+}
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch bytes of one GEMM: split planes (A: M x K, B: N x K in tiles of 128 x 64) and, with K
+// split, the partial C tiles.
+size_t gemm_plane_bytes(int64_t M, int64_t N, int64_t K) {
+  const int sp = gemm_splits(M, N, K);
+  return up256((size_t)(ceil_div(M, kMT) + ceil_div(N, kNT)) * ceil_div(K, kKT) * (2 * kMPlane)) +
+         (sp > 1 ? up256((size_t)sp * M * N * sizeof(float)) : 0);
+}
+
+// planes: scratch of gemm_plane_bytes(M, N, K) bytes, 256-byte aligned.
+static cudaError_t gemm(const GemmArgs& g, cudaStream_t s, uint8_t* planes) {
   if (g.M == 0 || g.N == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMSmem);
+  const int KT = (int)ceil_div(g.K, kKT);
+  const int sp = gemm_splits(g.M, g.N, g.K);
+  dim3 grid((g.N + kNT - 1) / kNT, (g.M + kMT - 1) / kMT, sp);
+  uint8_t* pa = planes;
+  uint8_t* pb = planes + (size_t)ceil_div(g.M, kMT) * KT * (2 * kMPlane);
+  float* part = (float*)(planes + up256((size_t)(ceil_div(g.M, kMT) + ceil_div(g.N, kNT)) * KT * (2 * kMPlane)));
+  if (KT > 0) {
+    split_planes_kernel<<<dim3(KT, (unsigned)ceil_div(g.M, kMT)), 256, 0, s>>>(g.A, g.sa0, g.sa1, g.M, g.K, KT, pa);
+    split_planes_kernel<<<dim3(KT, (unsigned)ceil_div(g.N, kNT)), 256, 0, s>>>(g.B, g.sb1, g.sb0, g.N, g.K, KT, pb);
+  }
+  cudaError_t e = cudaFuncSetAttribute(gemm_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kPSmem);
   if (e != cudaSuccess) return e;
-  dim3 grid((g.N + kNT - 1) / kNT, (g.M + kMT - 1) / kMT);
-  gemm_tc_kernel<<<grid, 256, kMSmem, s>>>(g, nullptr);
+  gemm_planes_kernel<<<grid, 256, kPSmem, s>>>(g, pa, pb, KT, sp, part, nullptr);
+  if (sp > 1) {
+    int64_t blocks = ceil_div((int64_t)g.M * g.N, 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, part, sp);
+  }
   return cudaGetLastError();
 }
 
@@ -200,8 +290,15 @@ __global__ void mse_tanh_grad_kernel(const float* __restrict__ y, const float* _
     dz[i] = inv * e * (1.0f - y[i] * y[i]);
   }
   if (loss) {
+    __shared__ double red[8];
     for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, part / (double)count);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      atomicAdd(loss, t / (double)count);
+    }
   }
 }
 
@@ -211,13 +308,36 @@ __global__ void gelu_back_kernel(float* __restrict__ dz, const float* __restrict
     dz[i] *= gelu_grad_f(z[i]);
 }
 
-// db[j] = sum_b dz[b][j]
-__global__ void colsum_kernel(const float* __restrict__ dz, int64_t rows, int cols, float* __restrict__ db) {
+// db[j] = sum_b dz[b][j] in two passes of fixed order.  Pass 1: CTA (column block of 32, row
+// chunk y) has its 8 warps read interleaved rows of the chunk (one coalesced 128-byte piece each)
+// and writes the chunk's sums to part[y][j]; pass 2 adds the chunks' sums.
+constexpr int kColChunks = 32;
+
+__global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ dz, int64_t rows, int cols,
+                                                     float* __restrict__ part) {
+  __shared__ float red[8][32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int j = blockIdx.x * 32 + l;
+  const int64_t r0 = blockIdx.y * rows / kColChunks, r1 = (blockIdx.y + 1) * rows / kColChunks;
+  float s = 0.f;
+  if (j < cols)
+    for (int64_t b = r0 + w; b < r1; b += 8) s += dz[b * cols + j];
+  red[w][l] = s;
+  __syncthreads();
+  if (w == 0 && j < cols) {
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t += red[i][l];
+    part[(int64_t)blockIdx.y * cols + j] = t;
+  }
+}
+
+__global__ void colsum_finish_kernel(const float* __restrict__ part, int cols, float* __restrict__ db) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= cols) return;
-  float s = 0.f;
-  for (int64_t b = 0; b < rows; ++b) s += dz[b * cols + j];
-  db[j] = s;
+  float t = 0.f;
+  for (int y = 0; y < kColChunks; ++y) t += part[(int64_t)y * cols + j];
+  db[j] = t;
 }
 
 __global__ void adam_kernel(int64_t count, float* __restrict__ p, const float* __restrict__ g,
@@ -246,11 +366,44 @@ int64_t mlp_param_count(int L, const int32_t* sizes) {
   return n;
 }
 
+// Scratch (bytes) for the split operand planes of the forward GEMMs and of the backward GEMMs.
+size_t mlp_forward_plane_bytes(int L, const int32_t* sizes, int64_t batch) {
+  size_t m = 0;
+  for (int l = 0; l < L; ++l) {
+    const size_t b = gemm_plane_bytes(batch, sizes[l + 1], sizes[l]);
+    m = b > m ? b : m;
+  }
+  return m;
+}
+
+size_t mlp_backward_plane_bytes(int L, const int32_t* sizes, int64_t batch) {
+  size_t m = 0;
+  for (int l = 0; l < L; ++l) {
+    const size_t b1 = gemm_plane_bytes(sizes[l + 1], sizes[l], batch);   // dW = dz^T h
+    const size_t b2 = gemm_plane_bytes(batch, sizes[l], sizes[l + 1]);   // dh = dz W
+    m = b1 > m ? b1 : m;
+    m = b2 > m ? b2 : m;
+  }
+  return m;
+}
+
+static int64_t activation_floats(int L, const int32_t* sizes, int64_t batch) {
+  int64_t a = 0;
+  for (int l = 1; l <= L; ++l) a += 2 * batch * sizes[l];
+  return a;
+}
+
+static uint8_t* planes_after(float* base, int64_t floats) {
+  uintptr_t p = (uintptr_t)(base + floats);
+  return (uint8_t*)((p + 255) & ~(uintptr_t)255);
+}
+
 cudaError_t mlp_forward(int L, const int32_t* sizes, const float* params, const float* x,
                         int64_t batch, float* acts, float* y, cudaStream_t s) {
   const float* h = x;
   const float* p = params;
   float* a = acts;
+  uint8_t* planes = planes_after(acts, activation_floats(L, sizes, batch));
   for (int l = 0; l < L; ++l) {
     const int in = sizes[l], out = sizes[l + 1];
     GemmArgs g{};
@@ -261,7 +414,7 @@ cudaError_t mlp_forward(int L, const int32_t* sizes, const float* params, const 
     g.bias = p + (int64_t)out * in;
     g.act = l == L - 1 ? 2 : 1;
     g.Cact = a + batch * out;
-    cudaError_t e = gemm(g, s);
+    cudaError_t e = gemm(g, s, planes);
     if (e != cudaSuccess) return e;
     h = a + batch * out;
     p += (int64_t)out * in + out;
@@ -278,6 +431,8 @@ cudaError_t mlp_backward(int L, const int32_t* sizes, const float* params, const
   for (int l = 0; l <= L; ++l) maxw = sizes[l] > maxw ? sizes[l] : maxw;
   float* dz = work;
   float* dh = work + batch * maxw;
+  float* colpart = work + 2 * batch * maxw;              // kColChunks x maxw partial column sums
+  uint8_t* planes = planes_after(work, 2 * batch * maxw + (int64_t)kColChunks * maxw);
   // offsets of every layer's parameters and activations
   int64_t poff[64], aoff[64];
   int64_t po = 0, ao = 0;
@@ -305,16 +460,17 @@ cudaError_t mlp_backward(int L, const int32_t* sizes, const float* params, const
     g.B = h; g.sb0 = in; g.sb1 = 1;              // B(k,j) = h[k][j]
     g.C = dW; g.ldc = in;
     g.M = out; g.N = in; g.K = (int)batch;
-    cudaError_t e = gemm(g, s);
+    cudaError_t e = gemm(g, s, planes);
     if (e != cudaSuccess) return e;
-    colsum_kernel<<<(out + 255) / 256, 256, 0, s>>>(dz, batch, out, db);
+    colsum_kernel<<<dim3((out + 31) / 32, kColChunks), 256, 0, s>>>(dz, batch, out, colpart);
+    colsum_finish_kernel<<<(out + 255) / 256, 256, 0, s>>>(colpart, out, db);
     if (l > 0) {
       GemmArgs h2{};
       h2.A = dz; h2.sa0 = out; h2.sa1 = 1;
       h2.B = W; h2.sb0 = in; h2.sb1 = 1;          // B(k,j) = W[k][j]
       h2.C = dh; h2.ldc = in;
       h2.M = (int)batch; h2.N = in; h2.K = out;
-      e = gemm(h2, s);
+      e = gemm(h2, s, planes);
       if (e != cudaSuccess) return e;
       const float* zprev = acts + aoff[l - 1];
       gelu_back_kernel<<<blocks_for(batch * in), 256, 0, s>>>(dh, zprev, batch * in);

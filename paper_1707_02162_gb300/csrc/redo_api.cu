@@ -1349,9 +1349,12 @@ redo_status redo_mlp_sizes(int32_t layers, const int32_t* sizes, int64_t batch,
     if (l > 0) a += 2 * batch * sizes[l];
     if (sizes[l] > mw) mw = sizes[l];
   }
+  // plus the split operand planes of the GEMMs, 256-byte aligned after the float buffers
+  const int64_t slack = 256 / sizeof(float);
   if (params) *params = mlp_param_count(layers, sizes);
-  if (acts) *acts = a;
-  if (work) *work = 2 * batch * mw;
+  if (acts) *acts = a + slack + (int64_t)((mlp_forward_plane_bytes(layers, sizes, batch) + 3) / 4);
+  // the backward buffer also holds 32 rows of partial column sums for the bias gradients
+  if (work) *work = 2 * batch * mw + 32 * mw + slack + (int64_t)((mlp_backward_plane_bytes(layers, sizes, batch) + 3) / 4);
   return REDO_OK;
 }
 

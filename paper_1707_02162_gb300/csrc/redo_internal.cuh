@@ -203,8 +203,12 @@ cudaError_t launch_sim_state(const redo_table* t, const int32_t* q, int64_t B, i
                              int prec, const double2* psi0, int psi0_batched, const double* obs,
                              double* expect, int64_t* status, cudaStream_t s);
 
-// Warm-start MLP (kernels_mlp.cu).
+// Warm-start MLP (kernels_mlp.cu).  `acts` and `work` end with scratch for the GEMMs' split
+// operand planes (256-byte aligned after the activations / the two gradient buffers).
 int64_t mlp_param_count(int L, const int32_t* sizes);
+size_t gemm_plane_bytes(int64_t M, int64_t N, int64_t K);
+size_t mlp_forward_plane_bytes(int L, const int32_t* sizes, int64_t batch);
+size_t mlp_backward_plane_bytes(int L, const int32_t* sizes, int64_t batch);
 cudaError_t mlp_forward(int L, const int32_t* sizes, const float* params, const float* x,
                         int64_t batch, float* acts, float* y, cudaStream_t s);
 cudaError_t mlp_backward(int L, const int32_t* sizes, const float* params, const float* x,

@@ -26,8 +26,13 @@ def _flat(params):
 @pytest.mark.parametrize("sizes,batch", [([23, 64, 64, 64, 100], 8), ([5, 33, 17, 70], 65),
                                          ([23, 512, 512, 512, 5000], 200)])
 def test_mlp_forward_backward_match_oracle(sizes, batch):
-    # the GEMMs are split-BF16 tensor-core products (about 16 significant bits per operand,
-    # FP32 accumulation): outputs within 1e-4, gradients within 1e-3 of their largest entry
+    # The GEMMs are split-BF16 tensor-core products: an operand v is carried as hi + lo with
+    # |v - hi - lo| <= 2^-16 |v| (bf16 keeps 8 significant bits), and a product drops lo*lo'
+    # (<= 2^-16 |a b|), so every term of a sum is exact to 3 * 2^-16 = 4.6e-5 of itself; the
+    # FP32 accumulation adds ~2^-24 per addition.  Term errors of random sign add like a random
+    # walk, so a sum -- and, layer after layer, each gradient -- stays within about the per-term
+    # bound of its own size (measured on a GB300: 3.6e-6 absolute on outputs in [-1, 1], 1.7e-5
+    # of the largest gradient entry).  Bars: outputs 2e-5, gradients 1e-4 of their largest entry.
     from paper_1707_02162_gb300.warmstart import MLP
     from paper_1707_02162_gb300 import redo
     rng = np.random.default_rng(0)
@@ -40,7 +45,7 @@ def test_mlp_forward_backward_match_oracle(sizes, batch):
     loss_o, grads_o = O.mlp_backward(params, cache, yt)
     net = MLP(sizes, params=_flat(params))
     y = net.forward(torch.tensor(x)).cpu().numpy()
-    assert np.abs(y - y_o).max() < 1e-4
+    assert np.abs(y - y_o).max() < 2e-5
     _, na, nw = redo.redo_mlp_sizes(sizes, batch)
     acts = torch.empty(na, dtype=torch.float32, device="cuda")
     work = torch.empty(nw, dtype=torch.float32, device="cuda")
@@ -53,7 +58,7 @@ def test_mlp_forward_backward_match_oracle(sizes, batch):
     g = net.grads.cpu().numpy()
     go = _flat(grads_o)
     assert abs(loss.item() - loss_o) < 1e-5 * max(1.0, loss_o)
-    assert np.abs(g - go).max() < 1e-3 * np.abs(go).max()
+    assert np.abs(g - go).max() < 1e-4 * np.abs(go).max()
 
 
 def test_adam_matches_oracle():
