@@ -81,11 +81,19 @@ class WarmStartReport:
     mlp_Fend: float = float("nan")
 
     def summary(self) -> dict:
-        def med(v):
+        def med(v, q=50):
             a = np.array([x if x >= 0 else np.inf for x in v], dtype=float)
-            return float(np.median(a))
+            # an element of the list (instances that never reached the threshold count as infinite)
+            return float(np.percentile(a, q, method="higher")) if a.size else float("nan")
+
+        def med_reached(v):
+            a = np.array([x for x in v if x >= 0], dtype=float)
+            return float(np.median(a)) if a.size else float("nan")
         return {"threshold": self.threshold, "train": self.train_instances, "test": self.test_instances,
                 "median_iters_random_init": med(self.random_iters), "median_iters_mlp_init": med(self.mlp_iters),
+                "p25_iters_random_init": med(self.random_iters, 25), "p25_iters_mlp_init": med(self.mlp_iters, 25),
+                "median_iters_among_reached_random": med_reached(self.random_iters),
+                "median_iters_among_reached_mlp": med_reached(self.mlp_iters),
                 "reached_random": int(sum(x >= 0 for x in self.random_iters)),
                 "reached_mlp": int(sum(x >= 0 for x in self.mlp_iters)), "final_train_loss": self.final_loss,
                 "median_F_initial_random": self.random_F0, "median_F_initial_mlp": self.mlp_F0,

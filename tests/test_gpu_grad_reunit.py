@@ -13,6 +13,8 @@ optimum the gradient is small against its natural scale 2 dt ||H_k|| |tau| / N (
 |dF/du| any pulse can have at this |tau|), so its error is bounded against that scale: 1e-5 (split
 FP16) or 2e-5 (FP32) of it, ~1e-3 of the largest oracle entry here.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -71,4 +73,36 @@ def test_reunitarised_gradient_keeps_fidelity_near_one(case):
     from paper_1707_02162_gb300 import redo as R
     with pytest.raises(R.RedoError):
         t.fidelity_grad(q, target, prec, checkpoint_every=ck, reunit_every=ck + 1)
+    t.close()
+
+
+def test_reunitarised_drift_gradient_at_the_warm_start_shape():
+    """The warm-start study's call: N=32, K=10, M=500, every pulse its own diagonal drift, FP32
+    chains re-unitarised every 50 steps, targets near each pulse's own propagator."""
+    w = inputs.config(4, B=2, M=500)
+    h = inputs.drift_diagonals(w)
+    from paper_1707_02162_gb300 import redo
+    t = redo.Table(np.zeros_like(w.H0), w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+    T, _ = _ref.oracle_table(dataclasses.replace(w, H0=np.zeros_like(w.H0)), method="eig")   # drift-free table
+    qo, dig, _, _ = _ref.oracle_levels(w)
+    rng = np.random.default_rng(9)
+    targets, Fo, go = [], [], []
+    for b in range(w.B):
+        Db = O.expm_hermitian(np.diag(h[b]).astype(np.complex128), w.dt)
+        Ub = O.propagate(T, Db, dig[b])
+        targets.append(_near_target(rng, Ub, 0.15))
+        F_b, g_b = O.grape_gradient(T, Db, w.Hk, w.dt, dig[b], targets[-1])
+        Fo.append(F_b)
+        go.append(g_b)
+    targets = np.stack(targets)
+    q = t.quantize(w.u)
+    assert np.array_equal(q.cpu().numpy(), qo)
+    F_re, g_re = t.fidelity_grad_drift(q, h, targets, "fp32", checkpoint_every=50, reunit_every=50)
+    F_no, _ = t.fidelity_grad_drift(q, h, targets, "fp32", checkpoint_every=50)
+    for b in range(w.B):
+        assert 0.9 < Fo[b] < 0.9999
+        assert abs(F_re.cpu().numpy()[b] - Fo[b]) <= 1e-6
+        assert abs(F_re.cpu().numpy()[b] - Fo[b]) <= abs(F_no.cpu().numpy()[b] - Fo[b]) + 1e-9
+        scale = 2 * w.dt * 0.5 * np.sqrt(Fo[b])
+        assert np.abs(g_re.cpu().numpy()[b] - go[b]).max() <= 2e-5 * scale
     t.close()
