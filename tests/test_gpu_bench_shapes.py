@@ -132,3 +132,93 @@ def test_grape_gradient_benchmark_plan_n256_matches_oracle():
         assert abs(fd - go[n, k]) <= 1e-6 * np.abs(go).max()
         assert abs(fd - g[n, k]) <= 1e-3 * np.abs(go).max()
     t.close()
+
+
+def test_plain_n8_replicas_sampled_against_oracle():
+    """The plain-REDO key: 3 qubits, M=1000, 4096 replica pulses, FP64 and FP32, in one call each;
+    three sampled pulses against the oracle, unitarity and F in [0, 1] for every pulse."""
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(0, B=4096)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+    q = t.quantize(w.u)
+    picks = [0, 2047, 4095]
+    qo, dig, _, _ = _ref.oracle_levels(w, w.u[picks])
+    assert np.array_equal(q[picks].cpu().numpy(), qo)
+    T, D = _ref.oracle_table(w)
+    Uo = np.stack([O.propagate(T, D, dig[i]) for i in range(len(picks))])
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-4)):
+        U, F, _ = t.propagate(q, prec, target=w.target)
+        Ug, Fg = U.cpu().numpy(), F.cpu().numpy()
+        assert np.abs(Ug[picks] - Uo).max() < tol
+        for i, b in enumerate(picks):
+            assert abs(Fg[b] - O.fidelity(w.target, Uo[i])) < (1e-12 if prec == "fp64" else 1e-6)
+        G = np.einsum("bji,bjk->bik", Ug.conj(), Ug)
+        assert np.abs(G - np.eye(w.N)).max() < (1e-12 if prec == "fp64" else 1e-4)
+        assert ((Fg >= 0) & (Fg <= 1 + 1e-9)).all()
+    t.close()
+
+
+def test_warm_start_batched_drift_gradient_sampled_against_oracle():
+    """The batched warm-start GRAPE call: N=32, K=10, M=500, 256 instances each with its own
+    diagonal drift, FP32 chains with every forward state kept; three instances against the oracle."""
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(4, B=256)
+    h = inputs.drift_diagonals(w)
+    rng = np.random.default_rng(0)
+    targets = np.stack([inputs.haar_unitary(rng, w.N) for _ in range(w.B)])
+    t = redo.Table(np.zeros_like(w.H0), w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True)
+    q = t.quantize(w.u)
+    F, g = t.fidelity_grad_drift(q, h, targets, "fp32")
+    picks = [0, 128, 255]
+    T, _ = O.build_table(np.zeros_like(w.H0), w.Hk, w.dt, w.lo, w.hi, w.levels, w.base, w.digits, method="eig")
+    qo, dig, _, _ = _ref.oracle_levels(w, w.u[picks])
+    assert np.array_equal(q[picks].cpu().numpy(), qo)
+    for i, b in enumerate(picks):
+        Db = O.expm_hermitian(np.diag(h[b]).astype(np.complex128), w.dt)
+        Fo, go = O.grape_gradient(T, Db, w.Hk, w.dt, dig[i], targets[b])
+        assert abs(F.cpu().numpy()[b] - Fo) < 1e-6
+        assert np.abs(g.cpu().numpy()[b] - go).max() <= 2e-4 * np.abs(go).max()
+    t.close()
+
+
+def test_ensemble_n1024_full_length_properties():
+    """The N=1024 ensemble key at full length (64 realisations x 2000 steps, level table, split
+    FP16 propagators and the FP32 state path), checked through properties and the FP64 path, as
+    the oracle cannot run 2000 products of 1024 x 1024 operators per realisation here:
+      * <Z_1>(t) of the reduced path against the FP64 state path (|d| <= 1e-4), and 1 at t = 0;
+      * the final propagator of one realisation against the FP64 propagator; without
+        re-unitarisation the split-FP16 chain loses norm coherently (~4e-6 per 1024 x 1024
+        product, so U^dag U = (1 - 0.008) I after 2000), bounded below 2e-2, and every entry
+        (modulus <= 1) moves by at most half that beyond the 5e-4 rounding bar;
+      * <Z_1> at the last step recomputed from the propagator's first column (U |0...0>);
+      * with reunit_every = 500 the same propagator is unitary to 1e-4."""
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(3)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=False, fp16x3=True, levels=True)
+    q = t.quantize(w.u)
+    e16, U = t.simulate(q, w.psi0, w.obs_diag, "fp16x3", want_U=True)
+    e64, _ = t.simulate(q, w.psi0, w.obs_diag, "fp64", want_U=False)
+    e16, e64 = e16.cpu().numpy(), e64.cpu().numpy()
+    assert e16.shape == (w.B, w.M + 1)
+    assert np.abs(e16 - e64).max() < 1e-4
+    assert np.abs(e16[:, 0] - 1.0).max() < 1e-6             # <Z_1> of |0...0> before any step
+    q0 = q[:1].contiguous()
+    _, U64 = t.simulate(q0, w.psi0, w.obs_diag, "fp64", want_U=True)
+    U0, U64 = U[0].cpu().numpy(), U64[0].cpu().numpy()
+    # FP64: each of the n = 2000 products moves the norm by up to N u (length-N inner products,
+    # u = 1.1e-16), coherently along the diagonal, so the bar is n N u = 2.3e-10, doubled.
+    assert np.abs(U64.conj().T @ U64 - np.eye(w.N)).max() < 2 * w.M * w.N * 1.12e-16
+    drift = np.abs(np.diag(U0.conj().T @ U0) - 1.0).max()
+    assert drift < 2e-2
+    assert np.abs(U0 - U64).max() < 5e-4 + drift           # |entries| <= 1 lose at most drift / 2
+    for b in (0, 31, 63):
+        Ub = U[b].cpu().numpy()
+        db = np.abs(np.diag(Ub.conj().T @ Ub) - 1.0).max()
+        assert db < 2e-2
+        col = Ub[:, 0]                                       # U |0...0>
+        assert abs(float(np.sum(w.obs_diag * np.abs(col) ** 2)) - e64[b, -1]) < 2 * db + 1e-4
+    _, Ur = t.simulate(q0, w.psi0, w.obs_diag, "fp16x3", reunit_every=500, want_U=True)
+    Ur = Ur[0].cpu().numpy()
+    assert np.abs(Ur.conj().T @ Ur - np.eye(w.N)).max() < 1e-4
+    assert np.abs(Ur - U64).max() < 5e-4
+    t.close()
