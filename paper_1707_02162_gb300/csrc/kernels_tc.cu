@@ -24,8 +24,9 @@
 // Warp roles per CTA (CH chains, EW epilogue warps per chain): warps
 // 0..CH*EW-1 epilogue -- warp w serves TMEM lanes 32(w mod 4).. and, when
 // EW = 8, one 32-column half of the accumulator -- then one bulk-copy
-// producer warp and one MMA-issuing warp.  Two chains per CTA let one
-// chain's MMAs run while the other chain's epilogue rewrites its state.
+// producer warp and one MMA-issuing warp (two in the default three-block
+// kernel).  Two chains per CTA let one chain's MMAs run while the other
+// chain's epilogue rewrites its state.
 // Every wait is bounded; a timeout sets REDO_STATUS_TIMEOUT and the CTA
 // drains, frees its tensor memory and exits.
 #include <cuda_fp16.h>
@@ -590,6 +591,16 @@ __global__ void __launch_bounds__(Tc2Layout<STAGES>::kThreads, 1) chain_tc2_kern
 // The epilogue writes 48 KB of state per step instead of 64 KB, and the saved
 // shared memory deepens the operand ring to four stages.  (A third chain per CTA
 // fits as well, but with a two-stage ring it measured slower.)
+//
+// A single thread issues a tcgen05.mma only every ~80 cycles, more than the 48-64
+// cycles these MMAs execute in, so each product's MMAs are split over two issuing
+// threads: A_hi [B_hi; B_lo] (N = 128, into D1 | D2) and A_lo B_hi (N = 64, into a
+// third accumulator D3, so the two threads never accumulate into the same columns);
+// the epilogue forms Z = D1 + 2^-11 (D2 + D3).  Both threads take the two chains'
+// products in the same stream order and commit each stage and each product once
+// (the barriers count two arrivals).  The producer warp looks the table entries up
+// 32 products at a time, a batch ahead of the copies it issues, so the level-index
+// loads do not delay the operand stream.
 // --------------------------------------------------------------------------
 template <int CH, int STAGES>
 struct Tc3Layout {
@@ -601,8 +612,12 @@ struct Tc3Layout {
   static constexpr uint32_t kMisc = kBars + (2 * STAGES + 2 * CH) * 8;
   static constexpr uint32_t kPhase = kMisc + 16;         // per chain: the next step diagonal, 64 float2
   static constexpr uint32_t kAlloc = kPhase + CH * 64 * 8 + 1024;
-  static constexpr int kThreads = 32 * (EW * CH + 2);
+  // warps: EW per chain (epilogue), one producer, two MMA issuers (hi and lo state planes)
+  static constexpr int kThreads = 32 * (EW * CH + 3);
+  static constexpr uint32_t kTmemPerChain = 192;         // D1 = hi.hi, D2 = hi.lo, D3 = lo.hi
   static_assert(kAlloc <= 232448, "shared memory budget");
+  static_assert(CH * kTmemPerChain <= 512, "tensor memory budget");
+  static_assert(CH == 2, "the operand stream interleaves exactly two chains");
 };
 
 // PH: amplitude/phase call (a.pd non-null), the step diagonals applied by the epilogue.
@@ -622,7 +637,6 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t G = a.units * a.segs;
   int64_t len[CH], f0[CH], unit[CH];
-  int64_t maxlen = 0;
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
     const int64_t g = (int64_t)blockIdx.x * CH + c;
@@ -636,15 +650,14 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
       if (f1 > a.F) f1 = a.F;
       len[c] = f1 > f0[c] ? f1 - f0[c] : 0;
     }
-    if (len[c] > maxlen) maxlen = len[c];
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], 2);                             // both issuers commit
     }
     for (int c = 0; c < CH; ++c) {
-      mbar_init(&mma_done[c], 1);
+      mbar_init(&mma_done[c], 2);
       mbar_init(&state_ready[c], 32 * EW);
     }
     *abort_flag = 0;
@@ -664,8 +677,8 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
     uint8_t* st_lo = st_hi + L::kPlane;
     const int64_t g = (int64_t)blockIdx.x * CH + c;
     float* out = g < G ? reinterpret_cast<float*>(a.out + g * (kN * kN)) : nullptr;
-    const uint32_t d1 = tmem_base + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(c * 128);
-    const uint32_t d2 = d1 + 64;
+    const uint32_t d1 = tmem_base + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(c * L::kTmemPerChain);
+    const uint32_t d2 = d1 + 64, d3 = d1 + 128;
     const int m = r & 63, comp = r >> 6;
     // destinations: r < 64 (Zr row r) -> block 1 row 64+r ; r >= 64 (Zi row r-64) -> block 2
     // row 128+(r-64) and, negated, block 0 row r-64
@@ -770,21 +783,18 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
           break;
         }
         tc_fence_after();
-        // issue all four accumulator loads before waiting once
-        uint32_t ra0[16], rb0[16], ra1[16], rb1[16];
-        tmem_ld16(d1 + 32 * j, ra0);
-        tmem_ld16(d2 + 32 * j, rb0);
-        tmem_ld16(d1 + 32 * j + 16, ra1);
-        tmem_ld16(d2 + 32 * j + 16, rb1);
-        tmem_wait_ld();
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int cb = 32 * j + 16 * h;                  // 16 accumulator columns
-          const uint32_t* ra = h == 0 ? ra0 : ra1;
-          const uint32_t* rb = h == 0 ? rb0 : rb1;
+          uint32_t ra[16], rb[16], rc[16];
+          tmem_ld16(d1 + cb, ra);
+          tmem_ld16(d2 + cb, rb);
+          tmem_ld16(d3 + cb, rc);
+          tmem_wait_ld();
           float z[16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) z[i] = fmaf(__uint_as_float(rb[i]), kLoInv, __uint_as_float(ra[i]));
+          for (int i = 0; i < 16; ++i)
+            z[i] = fmaf(__uint_as_float(rb[i]) + __uint_as_float(rc[i]), kLoInv, __uint_as_float(ra[i]));
           if (!last) {
             store16(z, cb);
           } else if (out) {
@@ -821,61 +831,117 @@ __global__ void __launch_bounds__(Tc3Layout<CH, STAGES>::kThreads, 1) chain_tc3_
       }
     }
   } else if (warp == EW * CH) {
-    if (lane == 0) {
-      uint32_t idx = 0;
-      for (int64_t t = 0; t < maxlen && !*abort_flag; ++t) {
-        for (int c = 0; c < CH; ++c) {
-          if (t >= len[c]) continue;
-          const uint32_t s = idx % STAGES, u = idx / STAGES;
+    // Producer: the warp's lanes look up the table entries of 32 consecutive products of the
+    // stream at once (one level-index load each, issued a batch ahead), and lane 0 issues the
+    // bulk copies in stream order.
+    const uint32_t n0 = (uint32_t)len[0], n1 = (uint32_t)len[1];
+    const uint32_t mn = n0 < n1 ? n0 : n1, total = n0 + n1;
+    const uint32_t clong = n0 > n1 ? 0u : 1u;
+    // stage 1 (a batch ahead): the level index and the operand slot k*d + j, digit j
+    auto fetch = [&](uint32_t idx, int32_t& qv, int32_t& kd, int32_t& jd) {
+      qv = 0;
+      kd = 0;
+      jd = 0;
+      if (idx >= total) return;
+      uint32_t t, c;
+      if (idx < 2u * mn) {
+        t = idx >> 1;
+        c = idx & 1u;
+      } else {
+        t = idx - mn;
+        c = clong;
+      }
+      const int64_t f = f0[c] + (int64_t)t;
+      const int64_t n = f / a.fps;
+      const int r = (int)(f - n * a.fps);
+      const int kq = r / a.d;
+      jd = r - kq * a.d;
+      kd = r;
+      qv = a.q[(unit[c] * a.M + n) * a.K + kq];
+    };
+    // stage 2 (after the current batch's copies are issued): the table entry
+    auto entry = [&](int32_t qv, int32_t kd, int32_t jd) -> int64_t {
+      if (qv < 0 || qv >= a.levels) {
+        if (a.status) atomicAdd((unsigned long long*)&a.status[REDO_STATUS_BADINDEX], 1ull);
+        qv = 0;
+      }
+      for (int i = 0; i < jd; ++i) qv /= a.base;
+      return (int64_t)kd * a.base + qv % a.base;
+    };
+    int32_t qn, kn, jn;
+    fetch((uint32_t)lane, qn, kn, jn);
+    int64_t e_cur = (uint32_t)lane < total ? entry(qn, kn, jn) : 0;
+    for (uint32_t i0 = 0; i0 < total && !*abort_flag; i0 += 32) {
+      fetch(i0 + 32u + (uint32_t)lane, qn, kn, jn);
+      const uint32_t nb = total - i0 < 32u ? total - i0 : 32u;
+      int ok = 1;
+      for (uint32_t i = 0; i < nb; ++i) {
+        const int64_t ei = __shfl_sync(0xffffffffu, e_cur, (int)i);
+        if (lane == 0 && ok) {
+          const uint32_t id = i0 + i;
+          const uint32_t s = id % STAGES, u = id / STAGES;
           if (u > 0 && !mbar_wait_bounded_n(&empty[s], (u - 1) & 1, kTcWaitLimit)) {
             *abort_flag = 1;
-            break;
+            ok = 0;
+          } else {
+            uint8_t* dst = smem + L::kRing + s * kEntryBytes;
+            const uint8_t* src = a.planes + ei * kEntryBytes;
+            mbar_arrive_expect_tx(&full[s], kEntryBytes);
+            bulk_load(dst, src, kEntryBytes / 2, &full[s]);
+            bulk_load(dst + kEntryBytes / 2, src + kEntryBytes / 2, kEntryBytes / 2, &full[s]);
           }
-          const int64_t e = tc_entry(a, unit[c], f0[c] + t);
-          uint8_t* dst = smem + L::kRing + s * kEntryBytes;
-          const uint8_t* src = a.planes + e * kEntryBytes;
-          mbar_arrive_expect_tx(&full[s], kEntryBytes);
-          bulk_load(dst, src, kEntryBytes / 2, &full[s]);
-          bulk_load(dst + kEntryBytes / 2, src + kEntryBytes / 2, kEntryBytes / 2, &full[s]);
-          ++idx;
         }
       }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      e_cur = i0 + 32u + (uint32_t)lane < total ? entry(qn, kn, jn) : 0;
     }
   } else {
+    // Two MMA-issuing threads share every product: `hi` issues A_hi [B_hi; B_lo] (N = 128, into
+    // D1 | D2) and `lo` issues A_lo B_hi (N = 64, into D3); each commits the stage and the chain's
+    // accumulators once, so both barriers complete when both halves of the product are done.
+    // The two chains' products are taken in stream order (32-bit counters throughout).
+    const bool hi = warp == EW * CH + 1;
     if (lane == 0) {
-      uint32_t idx = 0;
-      for (int64_t t = 0; t < maxlen && !*abort_flag; ++t) {
-        for (int c = 0; c < CH; ++c) {
-          if (t >= len[c]) continue;
-          const uint32_t s = idx % STAGES, u = idx / STAGES;
-          if (!mbar_wait_bounded_n(&full[s], u & 1, kTcWaitLimit) ||
-              !mbar_wait_bounded_n(&state_ready[c], (uint32_t)(t & 1), kTcWaitLimit)) {
-            *abort_flag = 1;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t a_hi = smem_u32(smem + c * L::kState);
-          const uint32_t a_lo = a_hi + L::kPlane;
-          const uint32_t b0 = smem_u32(smem + L::kRing + s * kEntryBytes);
-          const uint32_t dd1 = tmem_base + (uint32_t)(c * 128);
-          const uint32_t dd2 = dd1 + 64;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t arow = h == 0 ? 64u * 128u : 0u;   // [Yr; Yi] for Cr, [-Yi; Yr] for Ci
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t ao = arow + (uint32_t)kk * 32u;
-              const uint32_t bo = (uint32_t)h * kEntryAtom + (uint32_t)kk * 32u;
-              const uint64_t ah = smem_desc_sw128(a_hi + ao), al = smem_desc_sw128(a_lo + ao);
-              const uint64_t bb = smem_desc_sw128(b0 + bo);
-              mma_f16(dd1, ah, bb, kIdesc128, (h | kk) ? 1u : 0u);
-              mma_f16(dd2, al, bb, kIdesc64, 1u);
-            }
-          }
-          mma_commit(&empty[s]);
-          mma_commit(&mma_done[c]);
-          ++idx;
+      const uint32_t n0 = (uint32_t)len[0], n1 = (uint32_t)len[1];
+      const uint32_t mn = n0 < n1 ? n0 : n1, total = n0 + n1;
+      const uint32_t clong = n0 > n1 ? 0u : 1u;
+      const uint32_t st0 = smem_u32(smem) + (hi ? 0u : L::kPlane);
+      const uint32_t ring = smem_u32(smem + L::kRing);
+      const uint32_t dd0 = tmem_base + (hi ? 0u : 128u);
+      const uint32_t idesc = hi ? kIdesc128 : kIdesc64;
+      const uint64_t dst0 = smem_desc_sw128(st0), dring = smem_desc_sw128(ring);
+      for (uint32_t idx = 0; idx < total; ++idx) {
+        uint32_t t, c;
+        if (idx < 2u * mn) {
+          t = idx >> 1;
+          c = idx & 1u;
+        } else {
+          t = idx - mn;
+          c = clong;
         }
+        const uint32_t s = idx % STAGES, par = (idx / STAGES) & 1u;
+        if (!mbar_wait_bounded_n(&full[s], par, kTcWaitLimit) ||
+            !mbar_wait_bounded_n(&state_ready[c], t & 1u, kTcWaitLimit)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dd = dd0 + c * L::kTmemPerChain;
+        const uint32_t a_pl = st0 + c * L::kState;
+        const uint32_t b0 = ring + s * kEntryBytes;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t arow = h == 0 ? 64u * 128u : 0u;   // [Yr; Yi] for Cr, [-Yi; Yr] for Ci
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t ao = arow + (uint32_t)kk * 32u;
+            const uint32_t bo = (uint32_t)h * kEntryAtom + (uint32_t)kk * 32u;
+            mma_f16(dd, smem_desc_sw128(a_pl + ao), smem_desc_sw128(b0 + bo), idesc, (h | kk) ? 1u : 0u);
+          }
+        }
+        mma_commit(&empty[s]);
+        mma_commit(&mma_done[c]);
+        if (*abort_flag) break;
       }
     }
   }
@@ -931,12 +997,14 @@ ChainPlan plan_chain_tc(const redo_table* t, int64_t B, int64_t M) {
 }
 
 // Which chain kernel runs (all exact alternatives):
-//   3 (default) three-block state in shared memory, 2 chains, 4-stage ring: 35.4 ms
+//   3 (default) three-block state in shared memory, 2 chains, 4-stage ring,
+//     two MMA issuers, batched operand lookups:                              33.0 ms
+//     (one issuer and per-product lookups: 35.1 ms)
 //   1 embedded state in shared memory, 2 chains, 3-stage ring:               37.3 ms
 //   2 embedded state in tensor memory, 2 chains, 4-stage ring:               39.1 ms
-// (GB300, 256 pulses x 2000 steps x 12 products).  The per-step epilogue latency on the
-// chains' serial dependency bounds all three; variant 3 writes the least state per step
-// and has the deepest operand ring.
+// (GB300, 256 pulses x 2000 steps x 12 products).  Each chain's step is serial: MMAs,
+// then the epilogue that rewrites the state; at 33.0 ms the default's operand stream
+// reads the level table at ~0.9 of the measured HBM copy bandwidth.
 static int tc_variant() {
   const char* v = getenv("REDO_TC_VARIANT");
   if (v && v[0] == '1') return 1;
