@@ -48,6 +48,7 @@ constexpr uint32_t kSpin = 1u << 22;  // counter polls before a dependency wait 
 constexpr float kScale = 2048.0f, kInv = 1.0f / 2048.0f;
 constexpr uint32_t kNegB = 1u << 14;  // instruction descriptor: negate B
 constexpr int kQ = 4;                 // depth of the in-CTA unit queue
+constexpr int kSweepThreads = 352;    // 4 epilogue, producer, MMA, 4 trace warps, scheduler
 
 __host__ __device__ inline size_t state_bytes(int N) { return (size_t)8 * N * N; }
 __host__ __device__ inline size_t entry_bytes(int N) { return (size_t)8 * N * N; }
@@ -488,7 +489,7 @@ __device__ __forceinline__ void trace_xor(const uint8_t* Vs, const uint8_t* Rs, 
 }
 
 template <int NB>
-__global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
   using Gm = Geo<NB>;
   constexpr int kStages = Gm::kStages, kBufs = Gm::kBufs;
   const int N = a.N;
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
     }
     for (int i = 0; i < kQ; ++i) {
       mbar_init(&uq_full[i], 1);
-      mbar_init(&uq_empty[i], 9);     // MMA thread + 4 epilogue warps + 4 trace warps
+      mbar_init(&uq_empty[i], 10);    // producer + MMA thread + 4 epilogue warps + 4 trace warps
     }
     mbar_init(drain, 1);
     *abort_local = 0;
@@ -542,45 +543,28 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
     atomicExch(a.abort, 1);
   };
 
-  if (warp == 4) {
-    // ------------------------------------------------------------------ producer
+  if (warp == 10) {
+    // ------------------------------------------------------------------ scheduler
+    // Claims units in ticket (step) order, waits until the previous step of the unit's row
+    // block is written, and queues it; up to kQ units run ahead of the stages below, so the
+    // claim and the dependency wait of the next units overlap the current unit's copies.
     if (lane == 0) {
-      uint32_t kit = 0, ui = 0;
+      uint32_t ui = 0;
       for (;;) {
         int32_t tk = -1, e = -1, trk = -1;
-        Unit u{};
         if (!*abort_local && !ld_relaxed(a.abort)) {
           const uint32_t got = atomicAdd(a.ticket, 1u);
           if ((int64_t)got < total) tk = (int32_t)got;
         }
-        uint32_t pre = 0;                 // ring stages armed with their operand tile only
-        const uint8_t* Bb = nullptr;
         if (tk >= 0) {
-          u = decode(a, tk, RT, TNB);
+          const Unit u = decode(a, tk, RT, TNB);
           int k;
           bool last;
           e = (int32_t)factor_entry(a, u.c % a.gmod, u.t, k, last);
           if (a.trace && e >= 0 && last) trk = k;
-          if (e >= 0) {
-            // the operand tiles do not depend on the previous step: start the first ones now
-            Bb = a.planes + (size_t)e * entry_bytes(N) + (size_t)u.nb * KT * Gm::kB;
-            for (; pre < (uint32_t)kStages && pre < (uint32_t)KT; ++pre) {
-              const uint32_t it = kit + pre, s = it % kStages;
-              if (it >= (uint32_t)kStages && !wait_bar(&empty[s], ((it / kStages) - 1) & 1, abort_local, a.abort)) {
-                fail();
-                break;
-              }
-              uint8_t* dst = ring + s * Gm::kStage;
-              mbar_arrive_expect_tx(&full[s], Gm::kStage);
-              bulk_load(dst + kTile, Bb + (size_t)pre * Gm::kB, Gm::kB, &full[s]);
-            }
-          }
-          // the previous step of this row block is written
-          const bool ok = !*abort_local && wait_count(&a.cnt[u.c * RT + u.rt], (uint32_t)(u.t * 2 * TNB), a.abort);
-          if (!ok) {
+          if (*abort_local || !wait_count(&a.cnt[u.c * RT + u.rt], (uint32_t)(u.t * 2 * TNB), a.abort)) {
             fail();
             tk = -1;
-            kit += pre;                   // stages with copies in flight, drained below
           }
         }
         const uint32_t slot = ui % kQ;
@@ -592,26 +576,44 @@ __global__ void __launch_bounds__(320, 1) sweep_kernel(SweepArgs a) {
         mbar_arrive(&uq_full[slot]);
         ++ui;
         if (tk < 0) break;
-        if (e < 0) continue;
+      }
+    }
+  } else if (warp == 4) {
+    // ------------------------------------------------------------------ producer
+    // Streams the state (A) and operand (B) tiles of the queued units through the ring,
+    // one K tile of each per stage, back to back across units.
+    if (lane == 0) {
+      uint32_t kit = 0, ui = 0;
+      for (;;) {
+        const uint32_t slot = ui % kQ;
+        if (!wait_bar(&uq_full[slot], (ui / kQ) & 1, abort_local, a.abort)) {
+          fail();
+          break;
+        }
+        const int4 m = uq[slot];
+        mbar_arrive(&uq_empty[slot]);
+        ++ui;
+        if (m.x < 0) break;
+        if (m.y < 0) continue;
+        const Unit u = decode(a, m.x, RT, TNB);
+        const uint8_t* Bb = a.planes + (size_t)m.y * entry_bytes(N) + (size_t)u.nb * KT * Gm::kB;
+        // the states written by other CTAs (generic proxy) are read by bulk copies
         fence_proxy_async_global();
         const uint8_t* Sc = state_in(a, u.c, u.t, sb);
         bool ok = true;
-        for (int kt = 0; kt < KT && ok; ++kt, ++kit) {
+        for (int kt = 0; kt < KT; ++kt, ++kit) {
           const uint32_t s = kit % kStages;
           uint8_t* dst = ring + s * Gm::kStage;
-          if ((uint32_t)kt >= pre) {
-            if (kit >= (uint32_t)kStages &&
-                !wait_bar(&empty[s], ((kit / kStages) - 1) & 1, abort_local, a.abort)) {
-              fail();
-              ok = false;
-              break;
-            }
-            mbar_arrive_expect_tx(&full[s], Gm::kStage);
-            bulk_load(dst + kTile, Bb + (size_t)kt * Gm::kB, Gm::kB, &full[s]);
+          if (kit >= (uint32_t)kStages &&
+              !wait_bar(&empty[s], ((kit / kStages) - 1) & 1, abort_local, a.abort)) {
+            fail();
+            ok = false;
+            break;
           }
+          mbar_arrive_expect_tx(&full[s], Gm::kStage);
+          bulk_load(dst + kTile, Bb + (size_t)kt * Gm::kB, Gm::kB, &full[s]);
           const int kta = u.h ? (kt + KT / 2) % KT : kt;
-          const uint8_t* sa = Sc + ((size_t)u.rt * KT + kta) * kTile;
-          bulk_load(dst, sa, kTile, &full[s]);
+          bulk_load(dst, Sc + ((size_t)u.rt * KT + kta) * kTile, kTile, &full[s]);
         }
         if (!ok) break;
       }
@@ -961,11 +963,11 @@ static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan&
   if (NB == 256) {
     if ((e = cudaFuncSetAttribute(sweep_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
       return e;
-    sweep_kernel<256><<<(unsigned)grid, 320, smem, s>>>(a);
+    sweep_kernel<256><<<(unsigned)grid, kSweepThreads, smem, s>>>(a);
   } else {
     if ((e = cudaFuncSetAttribute(sweep_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
       return e;
-    sweep_kernel<128><<<(unsigned)grid, 320, smem, s>>>(a);
+    sweep_kernel<128><<<(unsigned)grid, kSweepThreads, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
