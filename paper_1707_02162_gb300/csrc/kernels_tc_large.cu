@@ -54,19 +54,28 @@ __host__ __device__ inline size_t state_bytes(int N) { return (size_t)8 * N * N;
 __host__ __device__ inline size_t entry_bytes(int N) { return (size_t)8 * N * N; }
 __host__ __device__ inline int trace_warps(int N) { return N >= 1024 ? 2 : 4; }
 
-template <int NB>
+template <int NB, int ST = (NB == 256 ? 2 : 3)>
 struct Geo {
   static constexpr uint32_t kB = (uint32_t)NB * 256u;      // NB rows hi + NB rows lo, 128 B each
   static constexpr uint32_t kStage = kTile + kB;
-  static constexpr int kStages = NB == 256 ? 2 : 3;
+  static constexpr int kStages = ST;
   static constexpr int kAcc = 2 * NB;                       // TMEM columns of D1 | D2
   static constexpr int kBufs = 512 / kAcc;
   static constexpr uint32_t kRing = kStages * kStage;
 };
 
-inline size_t sweep_smem(int NB, int N) {
-  const size_t ring = NB == 256 ? Geo<256>::kRing : Geo<128>::kRing;
-  return ring + (size_t)trace_warps(N) * 16 * N + 2048;
+// Shared memory per trace warp for rows staged by cp.async (the reverse sweep of a gradient
+// with one-nonzero-per-row operators at N <= 256): SL rows of eight 16-byte granules per lane.
+__host__ __device__ constexpr uint32_t trace_stage_bytes(int SL) { return (uint32_t)SL * 8 * 32 * 16; }
+
+constexpr int kTraceRows = 6;         // staged rows in flight per trace warp
+
+// staged: the trace rows go through shared memory (two ring stages; the row buffers of the
+// general trace path are not needed then)
+inline size_t sweep_smem(int NB, int N, bool staged) {
+  const size_t ring = NB == 256 ? Geo<256>::kRing : (staged ? Geo<128, 2>::kRing : Geo<128>::kRing);
+  const size_t rows = staged ? (size_t)trace_warps(N) * trace_stage_bytes(kTraceRows) : (size_t)trace_warps(N) * 16 * N;
+  return ring + rows + 2048;
 }
 
 // byte offset of the hi element (row, kcol) of a state; lo at +kHalf
@@ -418,6 +427,31 @@ __device__ __forceinline__ void xor_perm8(float (&v)[8], int m7) {
   }
 }
 
+// One row's granule of the compact trace: ld = R Re hi, lo, R Im hi, lo, V Re hi, lo, V Im hi, lo
+// (V's granule already the one at column i ^ m), h = the operator's values on the granule.
+__device__ __forceinline__ void trace_row(const uint4 (&ld)[8], const float2 (&h)[8], int m7, bool conjV,
+                                          float& tr, float& ti) {
+  float rr[8], ri[8], vr[8], vi[8];
+  unpack8(ld[0], ld[1], rr);
+  unpack8(ld[2], ld[3], ri);
+  unpack8(ld[4], ld[5], vr);
+  unpack8(ld[6], ld[7], vi);
+  if (conjV) {
+#pragma unroll
+    for (int w = 0; w < 8; ++w) vi[w] = -vi[w];
+  }
+  xor_perm8(vr, m7);
+  xor_perm8(vi, m7);
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    // conj(V[x][i ^ m]) R[x][i]
+    const float pr = fmaf(vr[w], rr[w], vi[w] * ri[w]);
+    const float pi = fmaf(vr[w], ri[w], -vi[w] * rr[w]);
+    tr = fmaf(h[w].x, pr, fmaf(-h[w].y, pi, tr));
+    ti = fmaf(h[w].x, pi, fmaf(h[w].y, pr, ti));
+  }
+}
+
 // The same part of the trace when H_k has one nonzero per row, h_i = H_k[i][i ^ m]:
 // sum_x sum_i h_i conj(V[x][i ^ m]) R[x][i].  A lane takes the complex granules
 // q = lane + 32 j (columns 8q .. 8q+7) of a row: R's own granule and V's granule q ^ (m >> 3),
@@ -463,34 +497,89 @@ __device__ __forceinline__ void trace_xor(const uint8_t* Vs, const uint8_t* Rs, 
         }
       }
 #pragma unroll
-      for (int b = 0; b < kRB; ++b) {
-        float rr[8], ri[8], vr[8], vi[8];
-        unpack8(ld[b][0], ld[b][1], rr);
-        unpack8(ld[b][2], ld[b][3], ri);
-        unpack8(ld[b][4], ld[b][5], vr);
-        unpack8(ld[b][6], ld[b][7], vi);
-        if (conjV) {
-#pragma unroll
-          for (int w = 0; w < 8; ++w) vi[w] = -vi[w];
-        }
-        xor_perm8(vr, m7);
-        xor_perm8(vi, m7);
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-          // conj(V[x][i ^ m]) R[x][i]
-          const float pr = fmaf(vr[w], rr[w], vi[w] * ri[w]);
-          const float pi = fmaf(vr[w], ri[w], -vi[w] * rr[w]);
-          tr = fmaf(h[w].x, pr, fmaf(-h[w].y, pi, tr));
-          ti = fmaf(h[w].x, pi, fmaf(h[w].y, pr, ti));
-        }
-      }
+      for (int b = 0; b < kRB; ++b) trace_row(ld[b], h, m7, conjV, tr, ti);
     }
   }
 }
 
-template <int NB>
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory");
+}
+
+// trace_xor for N <= 256 (one granule per lane) with the granules of SL rows in flight through
+// the warp's shared-memory stage (trace_stage_bytes(SL)) instead of registers: rows are fetched
+// two at a time by cp.async, a pair is consumed while the next pairs are on their way.  A lane
+// reads back only the granules it fetched itself.
+template <int SL>
+__device__ __forceinline__ void trace_xor_staged(const uint8_t* Vs, const uint8_t* Rs, int N, int x0, int nrows,
+                                                 int stride, int m, const float2* __restrict__ hv, int lane,
+                                                 bool conjV, float& tr, float& ti, uint8_t* stage) {
+  const int NG = N / 8, mq = m >> 3, m7 = m & 7;
+  const bool active = lane < NG;
+  const int q = active ? lane : 0, qv = q ^ mq;
+  float2 h[8];
+#pragma unroll
+  for (int w = 0; w < 8; ++w) h[w] = active ? __ldg(hv + 8 * q + w) : make_float2(0.f, 0.f);
+  const uint32_t orr = s_off(N, 0, 8 * q), ori = s_off(N, 0, N + 8 * q);
+  const uint32_t ovr = s_off(N, 0, 8 * qv), ovi = s_off(N, 0, N + 8 * qv);
+  const uint32_t sbase = smem_u32(stage);
+  auto slot_off = [&](int s, int z) -> uint32_t { return (uint32_t)(((s * 8 + z) * 32 + lane) * 16); };
+  auto issue = [&](int r) {
+    if (active && r < nrows) {
+      const int x = x0 + r * stride;
+      const uint32_t ro = (uint32_t)((x >> 7) * (2 * N / 64)) * kTile + (uint32_t)(x & 127) * 128u;
+      const uint32_t sw = (uint32_t)((x & 7) << 4);
+      const uint8_t* pr = Rs + ro + (orr ^ sw);
+      const uint8_t* pi = Rs + ro + (ori ^ sw);
+      const uint8_t* vr = Vs + ro + (ovr ^ sw);
+      const uint8_t* vi = Vs + ro + (ovi ^ sw);
+      const int s = r % SL;
+      cp_async16(sbase + slot_off(s, 0), pr);
+      cp_async16(sbase + slot_off(s, 1), pr + kHalf);
+      cp_async16(sbase + slot_off(s, 2), pi);
+      cp_async16(sbase + slot_off(s, 3), pi + kHalf);
+      cp_async16(sbase + slot_off(s, 4), vr);
+      cp_async16(sbase + slot_off(s, 5), vr + kHalf);
+      cp_async16(sbase + slot_off(s, 6), vi);
+      cp_async16(sbase + slot_off(s, 7), vi + kHalf);
+    }
+  };
+  auto consume = [&](int r) {
+    if (active && r < nrows) {
+      uint4 ld[8];
+      const int s = r % SL;
+#pragma unroll
+      for (int z = 0; z < 8; ++z) ld[z] = *reinterpret_cast<const uint4*>(stage + slot_off(s, z));
+      trace_row(ld, h, m7, conjV, tr, ti);
+    }
+  };
+#pragma unroll
+  for (int g = 0; g < SL / 2; ++g) {
+    issue(2 * g);
+    issue(2 * g + 1);
+    cp_async_commit();
+  }
+  for (int r = 0; r < nrows; r += 2) {
+    cp_async_wait<SL / 2 - 1>();                          // rows r, r + 1 have landed
+    consume(r);
+    consume(r + 1);
+    __syncwarp();                                         // their slots are read before refilling
+    issue(r + SL);
+    issue(r + SL + 1);
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
+}
+
+// STG: the trace rows staged in shared memory by cp.async (compact operators only)
+template <int NB, int ST, bool STG>
 __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
-  using Gm = Geo<NB>;
+  using Gm = Geo<NB, ST>;
   constexpr int kStages = Gm::kStages, kBufs = Gm::kBufs;
   const int N = a.N;
   const int KT = 2 * N / 64, RT = N / 128, TNB = N / NB;
@@ -501,8 +590,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* ring = smem;
-  float* trace_rows = reinterpret_cast<float*>(smem + Gm::kRing);
-  uint8_t* ctrl = smem + Gm::kRing + (size_t)TW * 16 * N;  // 1024-byte aligned
+  float* trace_rows = reinterpret_cast<float*>(smem + Gm::kRing);      // general trace path
+  uint8_t* trace_stage = smem + Gm::kRing;                               // staged path
+  uint8_t* ctrl = smem + Gm::kRing + (STG ? (size_t)TW * trace_stage_bytes(kTraceRows) : (size_t)TW * 16 * N);
   int4* uq = reinterpret_cast<int4*>(ctrl);                  // {ticket, entry, trace k, -}
   uint64_t* full = reinterpret_cast<uint64_t*>(ctrl + kQ * sizeof(int4));
   uint64_t* empty = full + kStages;
@@ -824,7 +914,11 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
           float tr = 0.0f, ti = 0.0f;
           const float2* hv = a.xval + (size_t)k * N;
           const int mk = a.xmask[k];
-          trace_xor(Vs, Rs, N, x0, nrows, TW, mk, hv, lane, conjV, tr, ti);
+          if (STG)
+            trace_xor_staged<kTraceRows>(Vs, Rs, N, x0, nrows, TW, mk, hv, lane, conjV, tr, ti,
+                                         trace_stage + (size_t)tw * trace_stage_bytes(kTraceRows));
+          else
+            trace_xor(Vs, Rs, N, x0, nrows, TW, mk, hv, lane, conjV, tr, ti);
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) {
             tr += __shfl_xor_sync(0xffffffffu, tr, off);
@@ -958,16 +1052,24 @@ static cudaError_t sweep(const redo_table* t, const int32_t* q, const ChainPlan&
   a.status = status;
   a.store = store;
   a.vstore = vstore;
-  const size_t smem = sweep_smem(NB, N);
+  // The gradient's reverse sweep with compact operators at N <= 256 stages its trace rows in
+  // shared memory, taken from the operand ring (two stages instead of three): the traces, not
+  // the MMAs, set its pace, and their loads need more bytes in flight than registers hold.
+  const bool staged = trace && t->hk_xval && NB == 128 && N <= 256;
+  const size_t smem = sweep_smem(NB, N, staged);
   int64_t grid = total < t->num_sms ? total : t->num_sms;
   if (NB == 256) {
-    if ((e = cudaFuncSetAttribute(sweep_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-      return e;
-    sweep_kernel<256><<<(unsigned)grid, kSweepThreads, smem, s>>>(a);
+    auto k = sweep_kernel<256, 2, false>;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    k<<<(unsigned)grid, kSweepThreads, smem, s>>>(a);
+  } else if (staged) {
+    auto k = sweep_kernel<128, 2, true>;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    k<<<(unsigned)grid, kSweepThreads, smem, s>>>(a);
   } else {
-    if ((e = cudaFuncSetAttribute(sweep_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-      return e;
-    sweep_kernel<128><<<(unsigned)grid, kSweepThreads, smem, s>>>(a);
+    auto k = sweep_kernel<128, 3, false>;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    k<<<(unsigned)grid, kSweepThreads, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
