@@ -47,7 +47,7 @@ constexpr uint32_t kLimit = 1u << 24; // mbarrier polls before a wait gives up
 constexpr uint32_t kSpin = 1u << 22;  // counter polls before a dependency wait gives up
 constexpr float kScale = 2048.0f, kInv = 1.0f / 2048.0f;
 constexpr uint32_t kNegB = 1u << 14;  // instruction descriptor: negate B
-constexpr int kQ = 4;                 // depth of the in-CTA unit queue
+constexpr int kQ = 2;                 // depth of the in-CTA unit queue (1, 3, 4 and 8 measured slower)
 constexpr int kSweepThreads = 352;    // 4 epilogue, producer, MMA, 4 trace warps, scheduler
 
 __host__ __device__ inline size_t state_bytes(int N) { return (size_t)8 * N * N; }
