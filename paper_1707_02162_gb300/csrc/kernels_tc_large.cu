@@ -312,6 +312,13 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Counter increment with release semantics at GPU scope: after the CTA barrier that precedes it,
+// every write of the CTA's threads before that barrier is visible to a reader that acquires the
+// new value (ld_acquire in wait_count).
+__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // false on time-out or when the sweep was aborted
 __device__ bool wait_count(const uint32_t* cnt, uint32_t target, const int* abort) {
   for (uint32_t i = 0; i < kSpin; ++i) {
@@ -856,8 +863,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
       fence_proxy_async_global();
       named_barrier(1, 128);
       if (threadIdx.x == 0 && !*abort_local) {
-        __threadfence();
-        atomicAdd(&a.cnt[u.c * RT + u.rt], 1u);
+        red_release_add(&a.cnt[u.c * RT + u.rt], 1u);
       }
     }
   } else {
@@ -957,8 +963,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
       if (threadIdx.x == 192 && !*abort_local) {
         uint32_t* tc = &a.tcnt[(u.c % a.gmod) * RT + u.rt];
         if (u.t == 0 || wait_count(tc, (uint32_t)(u.t * (a.vstore ? 2 : 4) * TNB), a.abort)) {
-          __threadfence();
-          atomicAdd(tc, 1u);
+          red_release_add(tc, 1u);
         } else {
           fail();
         }
