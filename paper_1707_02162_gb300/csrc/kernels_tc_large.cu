@@ -324,7 +324,7 @@ __device__ bool wait_count(const uint32_t* cnt, uint32_t target, const int* abor
   for (uint32_t i = 0; i < kSpin; ++i) {
     if (ld_acquire(cnt) >= target) return true;
     if ((i & 63) == 63 && ld_relaxed(abort)) return false;
-    __nanosleep(64);
+    __nanosleep(16);
   }
   return false;
 }
