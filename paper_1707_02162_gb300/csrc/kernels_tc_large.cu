@@ -48,7 +48,7 @@ constexpr uint32_t kSpin = 1u << 22;  // counter polls before a dependency wait 
 constexpr float kScale = 2048.0f, kInv = 1.0f / 2048.0f;
 constexpr uint32_t kNegB = 1u << 14;  // instruction descriptor: negate B
 constexpr int kQ = 2;                 // depth of the in-CTA unit queue (1, 3, 4 and 8 measured slower)
-constexpr int kSweepThreads = 352;    // 4 epilogue, producer, MMA, 4 trace warps, scheduler
+constexpr int kSweepThreads = 384;    // 4 epilogue, producer, MMA, 4 trace warps, scheduler, publisher
 
 __host__ __device__ inline size_t state_bytes(int N) { return (size_t)8 * N * N; }
 __host__ __device__ inline size_t entry_bytes(int N) { return (size_t)8 * N * N; }
@@ -608,7 +608,14 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
   uint64_t* uq_full = tmem_empty + kBufs;
   uint64_t* uq_empty = uq_full + kQ;
   uint64_t* drain = uq_empty + kQ;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* pub_full = drain + 1;           // publisher mailboxes: two slots of a counter address
+  uint64_t* pub_empty = pub_full + 2;       // (outputs) and two of a counter address and the
+  uint64_t* pub_ptr = pub_empty + 2;        // count it has to reach first (traces)
+  uint64_t* tpub_full = pub_ptr + 2;
+  uint64_t* tpub_empty = tpub_full + 2;
+  uint64_t* tpub_ptr = tpub_empty + 2;
+  uint32_t* tpub_target = reinterpret_cast<uint32_t*>(tpub_ptr + 2);
+  uint32_t* tmem_slot = tpub_target + 2;
   volatile int* abort_local = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -626,6 +633,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
       mbar_init(&uq_empty[i], 10);    // producer + MMA thread + 4 epilogue warps + 4 trace warps
     }
     mbar_init(drain, 1);
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(&pub_full[j], 128);     // the epilogue's threads
+      mbar_init(&pub_empty[j], 1);
+      mbar_init(&tpub_full[j], 128);    // the trace warps' threads
+      mbar_init(&tpub_empty[j], 1);
+    }
     *abort_local = 0;
     fence_mbarrier_init();
   }
@@ -640,7 +653,46 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
     atomicExch(a.abort, 1);
   };
 
-  if (warp == 10) {
+  if (warp == 11) {
+    // ------------------------------------------------------------------ publisher
+    // Makes each unit's outputs visible to the other CTAs: a release reduction on the unit's
+    // row-block counter, which has to wait for the unit's stores to be performed, done here so
+    // that the epilogue goes on to its next unit meanwhile.  The epilogue's threads arrive on
+    // the slot's barrier after their stores (CTA-scope release), so this release covers them.
+    if (lane == 0) {
+      for (uint32_t k = 0;; ++k) {
+        const uint32_t j = k & 1u;
+        if (!wait_bar(&pub_full[j], (k >> 1) & 1u, abort_local, a.abort)) {
+          fail();
+          break;
+        }
+        const uint64_t ptr = pub_ptr[j];
+        mbar_arrive(&pub_empty[j]);
+        if (ptr == 0) break;
+        if (!*abort_local) red_release_add(reinterpret_cast<uint32_t*>(ptr), 1u);
+      }
+    } else if (lane == 1 && a.trace) {
+      // the trace warps' counters: a unit's slice of step t is counted only after every slice
+      // of step t-1 of the same rows (so tcnt >= t * slices-per-step means steps < t are done)
+      for (uint32_t k = 0;; ++k) {
+        const uint32_t j = k & 1u;
+        if (!wait_bar(&tpub_full[j], (k >> 1) & 1u, abort_local, a.abort)) {
+          fail();
+          break;
+        }
+        const uint64_t ptr = tpub_ptr[j];
+        const uint32_t target = tpub_target[j];
+        mbar_arrive(&tpub_empty[j]);
+        if (ptr == 0) break;
+        uint32_t* tc = reinterpret_cast<uint32_t*>(ptr);
+        if (*abort_local) continue;
+        if (target == 0 || wait_count(tc, target, a.abort))
+          red_release_add(tc, 1u);
+        else
+          fail();
+      }
+    }
+  } else if (warp == 10) {
     // ------------------------------------------------------------------ scheduler
     // Claims units in ticket (step) order, waits until the previous step of the unit's row
     // block is written, and queues it; up to kQ units run ahead of the stages below, so the
@@ -787,8 +839,18 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
     }
   } else if (warp < 4) {
     // ------------------------------------------------------------------ epilogue (warps 0-3)
-    uint32_t ui = 0, use = 0;
+    uint32_t ui = 0, use = 0, pubs = 0;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    // hand a counter address (0: no more) to the publisher through mailbox slot pubs & 1
+    auto post = [&](uint32_t* cnt) {
+      const uint32_t j = pubs & 1u;
+      if (threadIdx.x == 0) {
+        if (pubs >= 2 && !wait_bar(&pub_empty[j], ((pubs >> 1) - 1) & 1u, abort_local, a.abort)) fail();
+        pub_ptr[j] = (uint64_t)(uintptr_t)cnt;
+      }
+      mbar_arrive(&pub_full[j]);
+      ++pubs;
+    };
     for (;;) {
       const uint32_t slot = ui % kQ;
       if (threadIdx.x == 0 && !wait_bar(&uq_full[slot], (ui / kQ) & 1, abort_local, a.abort)) fail();
@@ -798,7 +860,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&uq_empty[slot]);
       ++ui;
-      if (m.x < 0) break;
+      if (m.x < 0) {
+        post(nullptr);
+        break;
+      }
       const Unit u = decode(a, m.x, RT, TNB);
       const uint8_t* cur = state_in(a, u.c, u.t, sb);
       uint8_t* nxt = state_out(a, u.c, u.t, sb);
@@ -859,17 +924,24 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
           ++use;
         }
       }
-      // publish: this unit's part of step t+1 is written
+      // publish: this unit's part of step t+1 is written (by the publisher thread)
       fence_proxy_async_global();
-      named_barrier(1, 128);
-      if (threadIdx.x == 0 && !*abort_local) {
-        red_release_add(&a.cnt[u.c * RT + u.rt], 1u);
-      }
+      post(&a.cnt[u.c * RT + u.rt]);
     }
   } else {
     // ------------------------------------------------------------------ trace warps (6-9)
     const int tw = warp - 6;
-    uint32_t ui = 0;
+    uint32_t ui = 0, tpubs = 0;
+    auto tpost = [&](uint32_t* cnt, uint32_t target) {
+      const uint32_t j = tpubs & 1u;
+      if (threadIdx.x == 192) {
+        if (tpubs >= 2 && !wait_bar(&tpub_empty[j], ((tpubs >> 1) - 1) & 1u, abort_local, a.abort)) fail();
+        tpub_ptr[j] = (uint64_t)(uintptr_t)cnt;
+        tpub_target[j] = target;
+      }
+      mbar_arrive(&tpub_full[j]);
+      ++tpubs;
+    };
     for (;;) {
       const uint32_t slot = ui % kQ;
       if (threadIdx.x == 192 && !wait_bar(&uq_full[slot], (ui / kQ) & 1, abort_local, a.abort)) fail();
@@ -879,7 +951,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&uq_empty[slot]);
       ++ui;
-      if (m.x < 0) break;
+      if (m.x < 0) {
+        if (a.trace) tpost(nullptr, 0);
+        break;
+      }
       if (!a.trace) continue;
       const Unit u = decode(a, m.x, RT, TNB);
       if (m.z >= 0 && !a.vstore) {
@@ -956,18 +1031,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
           atomicAdd(&slot_acc->y, si);
         }
       }
-      // publish: this unit's reads of the step-t states are over.  A slice of step t is
-      // counted only after every slice of step t-1 of these rows, so tcnt >= t * 4 TNB
-      // means exactly that the slices of steps < t are done (as cnt does for outputs).
-      named_barrier(2, 128);
-      if (threadIdx.x == 192 && !*abort_local) {
-        uint32_t* tc = &a.tcnt[(u.c % a.gmod) * RT + u.rt];
-        if (u.t == 0 || wait_count(tc, (uint32_t)(u.t * (a.vstore ? 2 : 4) * TNB), a.abort)) {
-          red_release_add(tc, 1u);
-        } else {
-          fail();
-        }
-      }
+      // publish: this unit's reads of the step-t states are over (counted by the publisher
+      // thread after every slice of step t-1 of these rows)
+      tpost(&a.tcnt[(u.c % a.gmod) * RT + u.rt], (uint32_t)(u.t * (a.vstore ? 2 : 4) * TNB));
     }
   }
   tc_fence_before();
