@@ -866,15 +866,19 @@ polar_ns_kernel(const cplx<Rin>* __restrict__ in, cplx<Rout>* __restrict__ out, 
   cplx<Rc> Y[TM][TM];
   const int ty = lt / MM::TX, tx = lt % MM::TX;
   for (int it = 0; it < iters; ++it) {
-    MM::run_adj(P, P, lt, Y);                            // G = P^dag P (P read in column order)
+    if constexpr (MM::TY == MM::TX && TM > 1) {
+      MM::ns_half_gram(P, Q, lt);                        // Q = (3I - P^dag P) / 2, half the Gram tiles
+    } else {
+      MM::run_adj(P, P, lt, Y);                          // G = P^dag P (P read in column order)
 #pragma unroll
-    for (int a = 0; a < TM; ++a)
+      for (int a = 0; a < TM; ++a)
 #pragma unroll
-      for (int c = 0; c < TM; ++c) {
-        const int r = ty + MM::TY * a, col = tx + MM::TX * c;
-        Q[r * N + col] = cmake<Rc>((r == col ? Rc(1.5) : Rc(0)) - Rc(0.5) * Y[a][c].x,
-                                   -Rc(0.5) * Y[a][c].y);
-      }
+        for (int c = 0; c < TM; ++c) {
+          const int r = ty + MM::TY * a, col = tx + MM::TX * c;
+          Q[r * N + col] = cmake<Rc>((r == col ? Rc(1.5) : Rc(0)) - Rc(0.5) * Y[a][c].x,
+                                     -Rc(0.5) * Y[a][c].y);
+        }
+    }
     __syncthreads();
     MM::run(P, Q, lt, Y);                                // P (3I - G) / 2
     __syncthreads();
