@@ -20,14 +20,17 @@
 // half, column block); units are handed out in step order from a global ticket counter to
 // persistent CTAs, and a unit waits only until the previous step of its own row block is
 // complete (a counter per chain and row block that every finished unit increments).  In a
-// CTA, one warp claims tickets, waits for the counters and streams the A (state) and B
+// CTA, a scheduler warp claims tickets and waits for the counters, up to two units ahead
+// through an in-CTA unit queue; a producer warp streams the queued units' A (state) and B
 // (operand) tiles through a ring of bulk copies; one thread issues the MMAs into tensor
-// memory; four epilogue warps turn the FP32 accumulators into the next state's split
-// FP16 tiles.  In the reverse sweep of the gradient four more warps evaluate
+// memory; four epilogue warps turn the FP32 accumulators into the next state's split FP16
+// tiles; a publisher warp increments the counters with release semantics once a unit's
+// stores are done.  In the reverse sweep of the gradient four more warps evaluate
 // Tr(H_k V^dag R) for a slice of rows of the current states while the MMAs run; they
-// count their finished slices per row block of a V/R pair, and a unit writes over the
-// states of step t-1 only once all of that step's slices of its rows are added.
-// Every wait is bounded; a timed-out CTA raises a sweep-wide abort flag and leaves.
+// count their finished slices per row block of a V/R pair (through the publisher), and a
+// unit writes over the states of step t-1 only once all of that step's slices of its rows
+// are added.  Every wait is bounded; a timed-out CTA raises a sweep-wide abort flag and
+// leaves.
 #include "redo_internal.cuh"
 #include "device_sync.cuh"
 #include "tcgen05.cuh"
