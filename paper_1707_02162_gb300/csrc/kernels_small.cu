@@ -17,17 +17,60 @@ namespace redo {
 // ============================================================================
 // Quantizer -- Eq. (cgrain): level q = clamp(rint((u - lo_k) / delta_k))
 // ============================================================================
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU, so the FP64 divide
+// decides a level only where an FP32 estimate cannot.  With u = 2^-24, the estimate
+// y = fl32(fl32(fl32(v) - fl32(lo)) * fl32(1/delta)) and the FP64 quotient
+// x = fl64(fl64(v - lo) / delta) differ by at most about 3u|y| + u (|v| + |lo|) / |delta|
+// <= 4u|y| + 2u |lo| / |delta| (first order: three FP32 roundings of the quotient, and the
+// FP32 roundings of v and lo).  The kernel takes twice that plus 2^-40 as the bound e; where y lies more
+// than e from every half-integer, no half-integer lies between y and x, so rint(y) = rint(x).
+// Elsewhere (near ties, non-finite or huge y, terms whose lo, delta are out of the FP32 range)
+// the level comes from the FP64 subtract and divide as before.
+constexpr int kQuantFastK = 256;
+
 __global__ void quantize_kernel(const double* __restrict__ u, int64_t count, int K,
                                 const double* __restrict__ lo, const double* __restrict__ delta,
                                 int64_t levels, int32_t* __restrict__ q, int64_t* status) {
+  // per term: fl32(lo), fl32(1/delta) and the term's part of the bound e (1 disables the screen)
+  __shared__ float s_lo[kQuantFastK], s_rcp[kQuantFastK], s_e0[kQuantFastK];
+  const bool screen = K <= kQuantFastK && levels <= ((int64_t)1 << 24);
+  if (screen) {
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+      const double l = lo[j], d = delta[j];
+      const bool ok = fabs(d) > 1e-30 && fabs(d) < 1e30 && fabs(l) < 1e30;
+      s_lo[j] = ok ? (float)l : 0.0f;
+      s_rcp[j] = ok ? (float)(1.0 / d) : 0.0f;
+      s_e0[j] = ok ? (float)fmin(4.0 * 0x1p-24 * fabs(l) / fabs(d) + 0x1p-40, 1.0) : 1.0f;
+    }
+  }
+  __syncthreads();
   unsigned nonfinite = 0, saturated = 0;
   const double top = (double)(levels - 1);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(i % K);
+  const float topf = (float)(levels - 1);               // exact when the screen is on
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int k = (int)(i % K);                                   // term of element i, advanced below
+  const int kstep = (int)(stride % K);
+  for (; i < count; i += stride) {
     const double v = u[i];
     int32_t r = 0;
-    if (!isfinite(v)) {
+    float y = 0.0f, ry = 0.0f, e = 1.0f;
+    if (screen) {
+      y = __fmul_rn(__fsub_rn((float)v, s_lo[k]), s_rcp[k]);
+      ry = rintf(y);
+      e = fmaf(fabsf(y), 0x1p-21f, s_e0[k]);
+    }
+    if (fabsf(y - ry) < 0.5f - e) {                       // false for NaN or infinite y
+      if (ry < 0.0f) {
+        ++saturated;
+        r = 0;
+      } else if (ry > topf) {
+        ++saturated;
+        r = (int32_t)(levels - 1);
+      } else {
+        r = (int32_t)ry;
+      }
+    } else if (!isfinite(v)) {
       ++nonfinite;
     } else {
       // one IEEE subtract, one IEEE divide (no contraction), round half to even
@@ -43,6 +86,8 @@ __global__ void quantize_kernel(const double* __restrict__ u, int64_t count, int
       }
     }
     q[i] = r;
+    k += kstep;
+    if (k >= K) k -= K;
   }
   if (status) {
     // warp-aggregate the counters, one atomic per warp and word

@@ -71,6 +71,43 @@ def test_quantize_ten_million_random_bit_exact():
     assert np.array_equal(q, q_ref)
 
 
+@pytest.mark.parametrize("base,digits", [(64, 2), (16, 5), (256, 3)])
+def test_quantize_bit_exact_near_ties_offset_grids(base, digits):
+    """Values at every distance from the grid's ties, on grids offset far from zero.
+
+    The quantizer screens each value with an FP32 estimate whose error bound grows with
+    |y| and with |lo| / delta; distances from 1e-10 to 0.3 of a step on both sides of every
+    tie (and of every grid point) cross that bound, for offsets up to 2^17 steps.
+    """
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(1, B=1, M=4)
+    L = base ** digits
+    Om = w.extra["Omega"]
+    offs = np.resize(np.array([-0.5, 0.0, 3.0, 37.5, -250.0, 1e-3, 2.0 ** 17 / (L - 1), -1e4]), w.K)
+    span = np.resize(np.array([2.0, 0.37, 5.0, 1.0]), w.K) * Om
+    lo = offs * span
+    hi = lo + span
+    t = redo.Table(w.H0, w.Hk, w.dt, lo, hi, base, digits, fp32=True)
+    delta = (hi - lo) / (L - 1)
+    rng = np.random.default_rng(7)
+    j = rng.integers(0, L - 1, size=4096)
+    dist = np.concatenate([np.geomspace(1e-10, 0.3, 96), [0.0]])
+    dist = np.concatenate([dist, -dist])
+    parts = []
+    for c in (0.5, 0.0):
+        base_pts = lo[None, :] + (j[:, None] + c) * delta[None, :]
+        parts.append((base_pts[:, None, :] + dist[None, :, None] * delta[None, None, :]).reshape(-1, w.K))
+    parts.append(rng.uniform(lo - 0.1 * span, hi + 0.1 * span, size=(200000, w.K)))
+    u = np.concatenate(parts)[None]
+    st = _status()
+    q = t.quantize(u, st)
+    torch.cuda.synchronize()
+    q_ref, nn, ns = O.quantize(u, lo, hi, L)
+    assert np.array_equal(q.cpu().numpy(), q_ref)
+    s = st.cpu().numpy()
+    assert s[0] == nn and s[1] == ns
+
+
 # ------------------------------------------------------------------ table
 
 @pytest.mark.parametrize("idx,n", [(0, 3), (1, 6), (4, 5), (0, 1), (0, 2)])
