@@ -100,6 +100,35 @@ def _mlp_forward_gelu_output(params, x):
     return h, cache
 
 
+def _mlp_forward_no_bias(params, x):
+    h = np.asarray(x, dtype=np.float64)
+    cache = [h]
+    for li, (W, _) in enumerate(params):
+        z = h @ W.T
+        cache.append(z)
+        h = np.tanh(z) if li == len(params) - 1 else O.gelu(z)
+        cache.append(h)
+    return h, cache
+
+
+def _phase_split_step_no_inverse(H0, Sx, sz, dt, amp_row, phi_row):
+    # Z_n E ... E D: the turn back about z (Z_n^dag) dropped
+    Zd = np.diag(O.phase_rotation(phi_row, sz))
+    E = np.eye(np.asarray(H0).shape[0], dtype=np.complex128)
+    for k in range(Sx.shape[0]):
+        E = O.expm_pade13(-1j * dt * amp_row[k] * Sx[k]) @ E
+    return Zd @ E @ O.expm_pade13(-1j * dt * np.asarray(H0, dtype=np.complex128))
+
+
+def _lbfgs_accepts_every_trial(f):
+    def step(ut, gt, Ft, state, lo, hi, history=8, step0=0.05, c1=1e-4, first=False):
+        if not first:
+            state = dict(state)
+            state["F"] = -np.inf
+        return f(ut, gt, Ft, state, lo, hi, history, step0, c1, first)
+    return step
+
+
 def _eye_like(D):
     return np.eye(D.shape[0], dtype=np.complex128)
 
@@ -174,6 +203,9 @@ CASES = [
     ("Strang chain: time order reversed", "propagate_strang",
      lambda f: lambda T, Dh, dg: f(T, Dh, dg[::-1]),
      [P.test_strang_table_chain_matches_split_steps_at_level_values]),
+    ("Strang expectation: one step late", "simulate_expectation_strang",
+     lambda f: _with_output(f, lambda r: (np.concatenate([r[0][1:], r[0][-1:]]), r[1])),
+     [P.test_strang_expectation_series_closed_form_and_prefix_chains]),
     ("Strang split step: whole drift on one side", "strang_split_step",
      lambda f: lambda H0, Hk, dt, u: O.split_step(H0, Hk, dt, u),
      [P.test_strang_local_error_is_third_order, P.test_strang_step_is_time_reversible]),
@@ -217,6 +249,8 @@ CASES = [
     ("L-BFGS direction: pairs newest first", "lbfgs_direction",
      lambda f: lambda g, pairs: f(g, list(pairs)[::-1]),
      [P.test_lbfgs_two_loop_equals_the_explicit_bfgs_matrix]),
+    ("L-BFGS step: every trial accepted", "grape_lbfgs_step", _lbfgs_accepts_every_trial,
+     [P.test_lbfgs_backtracks_and_restarts]),
     ("polar: inverse instead of inverse root", "polar_unitary", lambda f: _polar_inverse_not_root,
      [P.test_polar_factor]),
     ("polar: Gram root on the wrong side", "polar_unitary", lambda f: _polar_wrong_side,
@@ -232,6 +266,8 @@ CASES = [
     ("MLP backward: weight gradient halved", "mlp_backward",
      lambda f: _with_output(f, lambda r: (r[0], [(0.5 * gw, gb) for gw, gb in r[1]])),
      [P.test_mlp_gradient_finite_difference]),
+    ("MLP forward: bias ignored", "mlp_forward", lambda f: _mlp_forward_no_bias,
+     [P.test_mlp_gradient_finite_difference]),
     ("MLP forward: output layer through GELU", "mlp_forward", lambda f: _mlp_forward_gelu_output,
      [P.test_mlp_gradient_finite_difference]),
     ("Adam: no bias correction", "adam_step", lambda f: _adam_step_no_bias_correction,
@@ -246,6 +282,8 @@ CASES = [
     ("phase chain: time order reversed", "propagate_phase",
      lambda f: lambda T, D, dg, phi, sz: f(T, D, dg[::-1], phi[::-1], sz),
      [P.test_phase_zero_is_the_x_only_chain, P.test_phase_step_at_levels_matches_the_xy_exponential]),
+    ("phase split step: inverse rotation dropped", "phase_split_step", lambda f: _phase_split_step_no_inverse,
+     [P.test_phase_step_at_levels_matches_the_xy_exponential, P.test_phase_gradient_matches_central_differences]),
     ("phase gradient: phase derivative sign", "phase_gradient",
      lambda f: _with_output(f, lambda r: (r[0], r[1], -r[2])),
      [P.test_phase_gradient_matches_central_differences]),

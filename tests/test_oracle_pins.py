@@ -313,6 +313,38 @@ def test_strang_table_chain_matches_split_steps_at_level_values():
     assert np.abs(X - U).max() < 1e-15 and ex[0] == 1.0
 
 
+def test_strang_expectation_series_closed_form_and_prefix_chains():
+    # no drift: D_h = I and the symmetric chain is the Rabi rotation at the quantised amplitude,
+    # <Z>(t_n) = cos(n dt u_hat) for every n (the whole series, not only its ends)
+    H0 = np.zeros((2, 2), dtype=complex)
+    Hk = np.stack([SX / 2])
+    lo, hi, L, b, d, dt = np.array([-6e4]), np.array([6e4]), 4096, 64, 2, 1e-6
+    T, D = O.build_table(H0, Hk, dt, lo, hi, L, b, d)
+    Dh = O.half_drift(H0, dt)
+    M = 40
+    q, _, _ = O.quantize(np.full((1, M, 1), 3.3e4), lo, hi, L)
+    uh = O.level_values(q[0, 0], lo, hi, L)[0]
+    ex, _ = O.simulate_expectation_strang(T, Dh, O.level_digits(q, b, d)[0], np.array([1, 0], dtype=complex),
+                                          np.array([1.0, -1.0]))
+    assert np.abs(ex - np.cos(np.arange(M + 1) * dt * uh)).max() < 1e-12
+    # with a drift: <O>(t_n) is the expectation in the state of the first n symmetric steps
+    rng = np.random.default_rng(14)
+    n = 2
+    H0 = inputs.drift_zz(n, rng.uniform(-5e3, 5e3, n), np.array([[0, 150.0], [0, 0]]))
+    Hk = inputs.controls_global_xy(n)
+    lo2, hi2 = np.array([-6e4, -6e4]), np.array([6e4, 6e4])
+    T, D = O.build_table(H0, Hk, dt, lo2, hi2, L, b, d)
+    Dh = O.half_drift(H0, dt)
+    q, _, _ = O.quantize(rng.uniform(-6e4, 6e4, size=(1, 9, 2)), lo2, hi2, L)
+    dig = O.level_digits(q, b, d)[0]
+    psi0 = np.array([0.6, 0.8j, 0, 0], dtype=complex)
+    obs = np.array([1.0, 0.3, -0.5, -1.0])
+    ex, _ = O.simulate_expectation_strang(T, Dh, dig, psi0, obs)
+    for m in range(10):
+        psi = O.propagate_strang(T, Dh, dig[:m]) @ psi0
+        assert abs(ex[m] - float(np.sum(obs * np.abs(psi) ** 2))) < 1e-13
+
+
 def test_strang_commuting_case_has_no_splitting_error():
     n = 2
     rng = np.random.default_rng(13)
