@@ -152,9 +152,12 @@ redo_status redo_table_copy(const redo_table* t, void* table_out, void* drift_ou
  * q[b][n][k] = clamp(rint((u[b][n][k] - lo[k]) / delta_k), 0, levels - 1),
  * computed with one IEEE FP64 subtract and one IEEE FP64 divide (no fused
  * multiply-add) and round-half-to-even, so the result is bit-identical to any
- * IEEE implementation of the same formula.  NaN/Inf coefficients give q = 0
- * and count in dev_status[REDO_STATUS_NONFINITE]; out-of-range coefficients
- * are clamped and counted in dev_status[REDO_STATUS_SATURATED].
+ * IEEE implementation of the same formula.  (Values farther from a tie than
+ * the error bound of an FP32 estimate of the quotient are decided by that
+ * estimate, which gives the same level; the FP64 arithmetic decides the rest.)
+ * NaN/Inf coefficients give q = 0 and count in dev_status[REDO_STATUS_NONFINITE];
+ * out-of-range coefficients are clamped and counted in
+ * dev_status[REDO_STATUS_SATURATED].
  *
  *  u    device double [B][M][K];  q  device int32 [B][M][K] (may not alias u).
  *  dev_status  device int64 [REDO_STATUS_WORDS] or NULL.
