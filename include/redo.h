@@ -88,8 +88,9 @@ typedef struct redo_table redo_table;
  * folded into the digit-0 operators of term 0 (T[0][0][c] <- T[0][0][c] D).
  * Exponentials are FP64 scaling-and-squaring Taylor series on the GPU.
  *
- *  N        Hilbert-space dimension, a power of two, 2 <= N <= 1024 (N > 64 uses
- *           the global-memory path: batched GEMMs, one launch per chain step).
+ *  N        Hilbert-space dimension, a power of two, 2 <= N <= 1024 (N > 64: FP64
+ *           and FP32 chains run as batched GEMMs, one launch per chain step;
+ *           REDO_FP16X3 chains as persistent tensor-core sweeps).
  *  K        number of control terms, 1 <= K <= 64.
  *  dt       time step in seconds (> 0).
  *  H0       device, complex128 [N][N], Hermitian drift (rad/s).
