@@ -316,9 +316,13 @@ redo_status redo_propagate_noalloc(const redo_table* t, const int32_t* q, int64_
  *  F_out         device double [B] or NULL;  grad  device double [B][M][K].
  *  workspace     >= redo_fidelity_grad_workspace() bytes, 256-byte aligned.
  * Method: segment products (one per C steps), prefix checkpoints and suffix
- * costates per segment, then one backward sweep per segment that undoes each
- * factor with its adjoint (the table operators are unitary) and evaluates the
- * traces with the sparse (CSR) form of H_k captured at table build time.
+ * costates per segment, then one backward sweep per segment that evaluates the
+ * traces with the sparse (CSR) form of H_k captured at table build time.  When
+ * every forward partial product of the segment chains fits in 24 GiB (N <= 64,
+ * and the tensor-core sweeps at N >= 128), the workspace holds them
+ * (redo_fidelity_grad_workspace counts them) and the backward sweep reads them;
+ * otherwise it undoes each factor with its adjoint (the table operators are
+ * unitary), which needs memory only per segment.
  */
 redo_status redo_fidelity_grad(const redo_table* t, const int32_t* q, int64_t B, int64_t M,
                                const void* U_target, int32_t target_batched, redo_precision prec,
