@@ -729,7 +729,8 @@ ChainPlan plan_chain_large(const redo_table* t, int64_t B, int64_t M) {
   p.F = M * (int64_t)t->K * t->digits;
   // enough chains to give every SM a few tiles per step
   const int64_t tiles = (int64_t)(t->N / kT) * (t->N / kT);
-  int64_t S = (4 * (int64_t)t->num_sms + B * tiles - 1) / (B * tiles);
+  const int64_t bt = B * tiles;                         // 0 for an empty batch: one segment
+  int64_t S = bt > 0 ? (4 * (int64_t)t->num_sms + bt - 1) / bt : 1;
   const int64_t max_s = (p.F + 15) / 16;
   if (S > max_s) S = max_s;
   if (S > 256) S = 256;

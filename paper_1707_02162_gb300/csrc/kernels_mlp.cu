@@ -237,7 +237,7 @@ __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + 
 // enough splits (of at least 8 K slices each) to give about one CTA per SM.
 static int gemm_splits(int64_t M, int64_t N, int64_t K) {
   const int64_t tiles = ceil_div(M, kMT) * ceil_div(N, kNT), KT = ceil_div(K, kKT);
-  if (tiles >= 76 || KT < 16) return 1;
+  if (tiles == 0 || tiles >= 76 || KT < 16) return 1;       // an empty GEMM takes no split
   int64_t sp = ceil_div(152, tiles);
   if (sp > KT / 8) sp = KT / 8;
   return sp < 1 ? 1 : (int)sp;

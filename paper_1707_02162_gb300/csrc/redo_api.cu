@@ -1191,6 +1191,7 @@ redo_status redo_simulate_workspace(const redo_table* t, int64_t B, int64_t M,
                                     redo_precision prec, int32_t reunit_every, int32_t want_U,
                                     size_t* bytes) {
   if (!t || !bytes) return set_error(REDO_ERR_INVALID, "null argument");
+  if (B < 0 || M < 0 || reunit_every < 0) return set_error(REDO_ERR_INVALID, "negative size");
   redo_status st = check_prec(t, prec);
   if (st != REDO_OK) return st;
   // the lockstep state simulation (N > 64 with fewer pulses than SMs) needs two state vectors

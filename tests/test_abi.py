@@ -126,3 +126,30 @@ def test_new_entry_points_validate_without_device(lib):
     assert lib.redo_reunitarize(8, 1, 4, dummy, dummy, 1, None) == 5          # FP64 / FP32 arithmetic only
     assert lib.redo_reunitarize(8, -1, 0, dummy, dummy, 1, None) == 1
     assert lib.redo_reunitarize(8, 0, 0, None, None, 1, None) == 0            # nothing to do
+
+
+def test_mlp_sizes_through_the_binding(lib):
+    # the warm-start network 23 -> 3 x 512 GELU -> 5000: params = sum of W (out x in) and b (out)
+    sizes = [23, 512, 512, 512, 5000]
+    want = sum(a * b + b for a, b in zip(sizes[:-1], sizes[1:]))
+    assert want == 3_102_600                               # the 3.10 M parameters of the warm-start network
+    for batch in (0, 1, 256):
+        p, a, w = redo.redo_mlp_sizes(sizes, batch)
+        assert p == want
+        # z and h of every layer for `batch` samples come first in acts; two gradient buffers of
+        # the widest layer in work
+        assert a >= 2 * batch * sum(sizes[1:])
+        assert w >= 2 * batch * max(sizes)
+    with pytest.raises(redo.RedoError):
+        redo.redo_mlp_sizes([23], 4)                      # no layer
+    with pytest.raises(redo.RedoError):
+        redo.redo_mlp_sizes([23, 0, 5], 4)                # empty layer
+    with pytest.raises(redo.RedoError):
+        redo.redo_mlp_sizes([23, 5], -1)                  # negative batch
+
+
+def test_binding_rejects_host_tensors():
+    import torch
+    with pytest.raises(ValueError, match="device tensor"):
+        redo._ptr(torch.zeros(4))
+    assert redo._ptr(None) is None

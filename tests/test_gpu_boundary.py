@@ -97,6 +97,25 @@ def test_propagate_steps_rejects_large_n_and_tensor_core_precision():
     t.close()
 
 
+def test_workspace_queries_for_an_empty_batch_at_large_n():
+    # B = 0 is a valid request: the N > 64 segment plans divide the GPU among B pulses, and the
+    # queries must answer (not divide by zero) for every precision and checkpoint choice
+    from paper_1707_02162_gb300 import redo
+    w = inputs.config(2, B=1, M=4, n_qubits=7, base=16, digits=2)
+    t = redo.Table(w.H0, w.Hk, w.dt, w.lo, w.hi, w.base, w.digits, fp32=True, fp16x3=True)
+    assert t.N == 128
+    for prec in ("fp64", "fp32", "fp16x3"):
+        for reunit in (0, 2):
+            assert redo.redo_propagate_workspace(t.handle, 0, 10, prec, reunit) >= 0
+        for ck in (0, 2):
+            assert redo.redo_fidelity_grad_workspace(t.handle, 0, 10, prec, ck) >= 0
+        assert redo.redo_simulate_workspace(t.handle, 0, 10, prec, 0, want_U=True) >= 0
+    with pytest.raises(redo.RedoError) as e:
+        redo.redo_simulate_workspace(t.handle, -1, 10, "fp32")
+    assert e.value.status == 1
+    t.close()
+
+
 def _perturbed(rng, N, count, eps, hermitian):
     Us = np.stack([inputs.haar_unitary(rng, N) for _ in range(count)])
     P = np.empty_like(Us)
