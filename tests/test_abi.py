@@ -153,3 +153,43 @@ def test_binding_rejects_host_tensors():
     with pytest.raises(ValueError, match="device tensor"):
         redo._ptr(torch.zeros(4))
     assert redo._ptr(None) is None
+
+
+_HOST_FUZZ = r'''
+import ctypes, itertools, math, sys
+sys.path.insert(0, sys.argv[1])
+from paper_1707_02162_gb300 import redo
+L = redo.load_library()
+vals = [0.0, -1.0, 1e-320, 1e-300, 1e-12, 0.5, 1.0, 64.0, 2.6e5, 1e300, math.inf, -math.inf, math.nan]
+bases = [-5, 0, 1, 2, 3, 64, 100, 2 ** 31 - 1]
+out = [ctypes.c_int32() for _ in range(3)] + [ctypes.c_int64()]
+seen = set()
+for om, eps, b in itertools.product(vals, vals, bases):
+    st = L.redo_plan(om, eps, b, *[ctypes.byref(o) for o in out])
+    seen.add(st)
+    if st == 0:
+        l, m, p, s = (o.value for o in out)
+        assert p == m - l >= -1 and s == (b - 1) * (m - l + 1), (om, eps, b, l, m, p, s)
+        assert b ** l <= eps * (1 + 1e-12) < b ** (l + 1) * (1 + 1e-9) or eps < 1e-300
+    else:
+        assert st == 1, st
+for sizes in ([23], [23, 512, 5000], [1] * 34, [4, 1 << 20, 3], [0, 2], [5, -1, 2]):
+    arr = (ctypes.c_int32 * len(sizes))(*sizes)
+    for batch in (-1, 0, 1, 1 << 20):
+        p, a, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        st = L.redo_mlp_sizes(len(sizes) - 1, ctypes.cast(arr, ctypes.c_void_p), batch,
+                              ctypes.byref(p), ctypes.byref(a), ctypes.byref(w))
+        assert st in (0, 1), st
+        if st == 0:
+            assert p.value > 0 and a.value >= 0 and w.value >= 0
+print("ok", sorted(seen))
+'''
+
+
+def test_host_only_entry_points_survive_edge_inputs(lib):
+    # run in a child process: a crash on some input fails this test instead of the whole session
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", _HOST_FUZZ, ROOT], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.startswith("ok")
