@@ -124,6 +124,12 @@ def test_autograd_function_and_grape_loop_improve_fidelity():
     q = t.quantize(w.u)
     _, g = t.fidelity_grad(q, w.target, "fp64")
     assert torch.equal(u.grad, g)
+    # the chain rule through the Function with an upstream gradient that differs per pulse
+    wts = torch.tensor([0.5, -2.0, 3.0, 0.0], dtype=torch.float64, device="cuda")
+    u.grad = None
+    F = RedoFidelity.apply(u, t, w.target, "fp64", 0)
+    (F * wts).sum().backward()
+    assert torch.equal(u.grad, wts[:, None, None] * g)
     res = grape(t, w.target, torch.tensor(w.u, device="cuda"), iters=60, step=2e10, prec="fp64")
     F0, F1 = res.F_history[0], res.F_history[-1]
     assert (F1 > F0).all() and F1.mean() > F0.mean() + 0.02
