@@ -79,12 +79,36 @@ class GrapeResult:
     F_history: list = field(default_factory=list)
     iterations: int = 0
     reached: torch.Tensor | None = None        # per pulse: first iteration with F >= threshold (-1 if never)
+    state: dict | None = None                  # everything a later grape(..., resume=state) continues from
+
+
+_STATE_TENSORS = ("u", "scale", "prev_F", "reached", "F_history", "m", "v", "lbfgs_state", "u_best", "F_best")
+
+
+def save_state(path: str, state: dict) -> None:
+    """Write a GRAPE run's state (``GrapeResult.state``) to an ``.npz`` file."""
+    import numpy as np
+    arrays = {"optimizer": np.array(state["optimizer"]), "iteration": np.array(state["iteration"])}
+    for k in _STATE_TENSORS:
+        if state.get(k) is not None:
+            arrays[k] = state[k].detach().cpu().numpy()
+    np.savez(path, **arrays)
+
+
+def load_state(path: str) -> dict:
+    """Read a state written by :func:`save_state` (host tensors; ``grape`` moves them)."""
+    import numpy as np
+    with np.load(path) as z:
+        state = {"optimizer": str(z["optimizer"]), "iteration": int(z["iteration"])}
+        for k in _STATE_TENSORS:
+            state[k] = torch.from_numpy(z[k].copy()) if k in z.files else None
+    return state
 
 
 def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, prec="fp64",
           checkpoint_every=0, threshold: float | None = None, adaptive: bool = True,
           optimizer: str = "gd", lr_decay: float = 150.0, psi0=None, drift=None,
-          on_iter=None, reunit_every: int = 0) -> GrapeResult:
+          on_iter=None, reunit_every: int = 0, resume: dict | None = None) -> GrapeResult:
     """Gradient ascent on the fidelity (the paper does not specify the update rule).
 
     ``optimizer="gd"``: ``u <- clamp(u + step * dF/du)``; with ``adaptive`` the
@@ -102,14 +126,33 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
     update with the iteration index, the updated coefficients (device, not copied) and that
     iteration's fidelities (host).  ``reunit_every`` (unitary fidelities; equal to ``checkpoint_every``)
     re-unitarises every checkpoint segment of the reduced-precision chains.
+
+    The result's ``state`` holds the run's position: coefficients, iteration count, fidelity
+    history, first-reached iterations and the optimizer's own state (step factors, Adam moments,
+    or the L-BFGS pair ring and best point).  ``grape(..., resume=state)`` (``u0`` may then be
+    None) continues that run for ``iters`` more iterations with the same ``optimizer``, ``step``
+    and ``lr_decay``, exactly as an uninterrupted run would; :func:`save_state` and
+    :func:`load_state` keep it in an ``.npz`` file between processes.
     """
-    u = u0.clone().contiguous()
+    if resume is not None and resume["optimizer"] != optimizer:
+        raise ValueError(f"state of a {resume['optimizer']!r} run resumed with optimizer {optimizer!r}")
+    dev = u0.device if u0 is not None else table.device
+    u = (resume["u"].to(dev) if resume is not None else u0).clone().contiguous()
     B, M, K = u.shape
     scale_h = torch.ones(B, dtype=torch.float64)               # per-pulse step factors (host)
     scale_d = torch.ones(B, dtype=torch.float64, device=u.device)
     prev_F = None
     reached = torch.full((B,), -1, dtype=torch.int64)
     res = GrapeResult(u=u)
+    it0 = 0
+    if resume is not None:
+        it0 = res.iterations = resume["iteration"]
+        reached = resume["reached"].clone()
+        res.F_history = [f.clone() for f in resume["F_history"]]
+        if resume.get("scale") is not None:
+            scale_h = resume["scale"].clone()
+            scale_d.copy_(scale_h)
+        prev_F = resume["prev_F"].clone() if resume.get("prev_F") is not None else None
     state = psi0 is not None
     if state and drift is not None:
         raise ValueError("per-pulse drift is supported for the unitary fidelity only")
@@ -129,14 +172,22 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
     if optimizer == "adam":
         m_ = torch.zeros_like(u)
         v_ = torch.zeros_like(u)
+        if resume is not None:
+            m_.copy_(resume["m"])
+            v_.copy_(resume["v"])
     elif optimizer == "lbfgs":
         lb_state = torch.empty(max(redo.redo_grape_lbfgs_workspace(table.handle, B, M, 8), 256),
                                dtype=torch.uint8, device=u.device)
         u_best = u.clone()
         F_best = torch.empty(B, dtype=torch.float64, device=u.device)
+        if resume is not None:
+            lb_state.copy_(resume["lbfgs_state"])
+            u_best.copy_(resume["u_best"])
+            F_best.copy_(resume["F_best"])
     elif optimizer != "gd":
         raise ValueError(f"unknown optimizer {optimizer!r}")
-    for it in range(iters):
+    done = it0                                  # iterations completed (evaluation and update)
+    for it in range(it0, it0 + iters):
         redo.redo_quantize(table.handle, u, q)
         if state:
             redo.redo_state_grad(table.handle, q, prec, psi0, target, F, g, ws)
@@ -152,7 +203,7 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
                                        F_best=F_best)
             Fh = F_best.cpu()
             res.F_history.append(Fh.clone())
-            res.iterations = it + 1
+            res.iterations = done = it + 1
             if on_iter is not None:
                 on_iter(it, u, Fh)
             if threshold is not None:
@@ -170,7 +221,7 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
                 break
         if optimizer == "adam":
             redo.redo_grape_adam_step(table.handle, u, g, m_, v_, it + 1, step / (1.0 + it / lr_decay))
-            res.iterations = it + 1
+            res.iterations = done = it + 1
             if on_iter is not None:
                 on_iter(it, u, Fh)
             continue
@@ -180,9 +231,20 @@ def grape(table: redo.Table, target, u0: torch.Tensor, iters: int, step: float, 
             scale_d.copy_(scale_h, non_blocking=True)
         prev_F = Fh
         redo.redo_grape_step(table.handle, u, g, step, scale_d if adaptive else None)
-        res.iterations = it + 1
+        res.iterations = done = it + 1
         if on_iter is not None:
             on_iter(it, u, Fh)
     res.u = u_best if optimizer == "lbfgs" else u
     res.reached = reached
+    B_ = u.shape[0]
+    res.state = {"optimizer": optimizer, "iteration": done, "u": u.clone(), "reached": reached.clone(),
+                 # completed iterations only: an iteration stopped by the threshold before its
+                 # update is evaluated again on resume
+                 "F_history": (torch.stack(res.F_history[:done]) if done > 0
+                               else torch.empty((0, B_), dtype=torch.float64)),
+                 "scale": scale_h.clone(), "prev_F": None if prev_F is None else prev_F.clone()}
+    if optimizer == "adam":
+        res.state.update(m=m_.clone(), v=v_.clone())
+    elif optimizer == "lbfgs":
+        res.state.update(lbfgs_state=lb_state.clone(), u_best=u_best.clone(), F_best=F_best.clone())
     return res

@@ -41,6 +41,21 @@ class MLP:
         self.step_count = 0
         self._buf = {}
 
+    def save(self, path: str) -> None:
+        """Weights, Adam moments and step count to an ``.npz`` file (training resumes from it)."""
+        np.savez(path, sizes=np.array(self.sizes, dtype=np.int64), params=self.params.cpu().numpy(),
+                 m=self.m.cpu().numpy(), v=self.v.cpu().numpy(), step_count=np.array(self.step_count))
+
+    @classmethod
+    def load(cls, path: str, device="cuda") -> "MLP":
+        """The network saved by :meth:`save`, ready to continue training where it stopped."""
+        with np.load(path) as z:
+            net = cls([int(s) for s in z["sizes"]], params=z["params"].astype(np.float64), device=device)
+            net.m.copy_(torch.from_numpy(z["m"]))
+            net.v.copy_(torch.from_numpy(z["v"]))
+            net.step_count = int(z["step_count"])
+        return net
+
     def _buffers(self, batch):
         if batch not in self._buf:
             _, na, nw = redo.redo_mlp_sizes(self.sizes, batch)
