@@ -541,7 +541,16 @@ def run_gpu(args):
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     if rank == 0:
-        print(json.dumps(out))
+        emit(out, args)
+
+
+def emit(out: dict, args) -> None:
+    """Print the run's JSON line; with ``--jsonl PATH`` also append it to that file."""
+    line = json.dumps(out)
+    print(line)
+    if getattr(args, "jsonl", None):
+        with open(args.jsonl, "a") as f:
+            f.write(line + "\n")
 
 
 def run_reference(args):
@@ -566,7 +575,7 @@ def run_reference(args):
            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": info["cores"],
                             "sample": info["sample"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(out))
+    emit(out, args)
 
 
 # ----------------------------------------------------------------------------- other workloads
@@ -996,7 +1005,7 @@ def run_workload(args):
                     "value": res["fp32"]["instance_iters_per_s"], "results": res,
                     "mlp_train_samples_per_s": mlp["batch_1024"]["samples_per_s"], "mlp_training": mlp,
                     "config": {"N": w.N, "K": w.K, "M": w.M, "instances": B, "mlp": "23-512-512-512-5000"}})
-    print(json.dumps(out))
+    emit(out, args)
 
 
 def main():
@@ -1022,6 +1031,7 @@ def main():
                     help="warmstart_study: fidelity the training pulses are converged to")
     ap.add_argument("--ws-test", type=int, default=1000, help="warmstart_study: held-out test instances")
     ap.add_argument("--ws-iters", type=int, default=600, help="warmstart_study: GRAPE iteration budget")
+    ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file (one record per run)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")

@@ -20,12 +20,12 @@ if ROOT not in sys.path:
 import bench  # noqa: E402
 
 
-def _run(monkeypatch, env):
+def _run(monkeypatch, env, jsonl=None):
     real = bench.oracle_throughput
     monkeypatch.setattr(bench, "oracle_throughput", lambda M_sample=200: real(cores=2, M_sample=4))
     for k, v in env.items():
         monkeypatch.setenv(k, v)
-    args = argparse.Namespace(steps=2, warmup=1)
+    args = argparse.Namespace(steps=2, warmup=1, jsonl=jsonl)
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
         bench.run_reference(args)
@@ -57,3 +57,12 @@ def test_reference_line_keys_and_consistency(monkeypatch):
 
 def test_reference_line_only_on_rank_zero(monkeypatch):
     assert _run(monkeypatch, {"WORLD_SIZE": "2", "RANK": "1"}) == ""
+
+
+def test_reference_line_appended_to_a_jsonl_file(monkeypatch, tmp_path):
+    path = tmp_path / "runs.jsonl"
+    path.write_text('{"earlier": 1}\n')
+    out = _run(monkeypatch, {"WORLD_SIZE": "1", "RANK": "0"}, jsonl=str(path))
+    lines = path.read_text().splitlines()
+    assert len(lines) == 2 and json.loads(lines[0]) == {"earlier": 1}
+    assert json.loads(lines[1]) == json.loads(out)
