@@ -127,6 +127,41 @@ def _ptr(t: torch.Tensor | None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+# (N, K) of every live table handle: the C ABI takes plain pointers, so the binding checks here
+# that each array holds what the library will read or write for that table.
+_TABLE_NK: dict = {}
+
+
+def _table_nk(handle: int) -> tuple[int, int]:
+    nk = _TABLE_NK.get(handle)
+    if nk is None:
+        info = redo_table_info(handle)
+        nk = _TABLE_NK[handle] = (info["N"], info["K"])
+    return nk
+
+
+def _exact(t: torch.Tensor, name: str, dtype, count: int):
+    """An input the library reads ``count`` elements of: that dtype and exactly that many elements."""
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: {dtype} expected, got {t.dtype}")
+    if t.numel() != count:
+        raise ValueError(f"{name}: {count} elements expected for this table and shape, got {t.numel()}")
+
+
+def _room(t: torch.Tensor | None, name: str, nbytes: int):
+    """An array the library writes (or reads) ``nbytes`` of: at least that many bytes."""
+    if t is not None and t.numel() * t.element_size() < nbytes:
+        raise ValueError(f"{name}: {nbytes} bytes needed, got {t.numel() * t.element_size()}")
+
+
+def _levels(handle: int, q: torch.Tensor) -> tuple[int, int, int, int]:
+    """(B, M, N, K) of a level-index array q [B][M][K] (int32) for this table, checked."""
+    B, M = q.shape[0], q.shape[1]
+    N, K = _table_nk(handle)
+    _exact(q, "q", torch.int32, B * M * K)
+    return B, M, N, K
+
+
 def _stream(stream=None):
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
@@ -152,6 +187,7 @@ def redo_build_table(H0: torch.Tensor, Hk: torch.Tensor, dt: float, lo, hi, base
 
 
 def redo_table_free(handle: int):
+    _TABLE_NK.pop(handle, None)
     _check(load_library().redo_table_free(ctypes.c_void_p(handle)))
 
 
@@ -171,6 +207,9 @@ def redo_table_copy(handle: int, table_out: torch.Tensor | None, drift_out: torc
 
 def redo_quantize(handle: int, u: torch.Tensor, q: torch.Tensor, status: torch.Tensor | None = None, stream=None):
     B, M = u.shape[0], u.shape[1]
+    N, K = _table_nk(handle)
+    _exact(u, "u", torch.float64, B * M * K)
+    _exact(q, "q", torch.int32, B * M * K)
     _check(load_library().redo_quantize(ctypes.c_void_p(handle), _ptr(u), B, M, _ptr(q), _ptr(status),
                                         _stream(stream)))
 
@@ -185,7 +224,11 @@ def redo_propagate_workspace(handle: int, B: int, M: int, prec, reunit_every: in
 def redo_propagate(handle: int, q: torch.Tensor, prec, U_out: torch.Tensor | None, U_target: torch.Tensor | None,
                    F_out: torch.Tensor | None, tau_out: torch.Tensor | None, workspace: torch.Tensor,
                    status: torch.Tensor | None = None, reunit_every: int = 0, stream=None):
-    B, M = q.shape[0], q.shape[1]
+    B, M, N, K = _levels(handle, q)
+    _room(U_out, "U_out", B * N * N * 16)
+    _room(U_target, "U_target", N * N * 16)
+    _room(F_out, "F_out", B * 8)
+    _room(tau_out, "tau_out", B * 16)
     _check(load_library().redo_propagate(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), reunit_every,
                                          _ptr(U_out), _ptr(U_target), _ptr(F_out), _ptr(tau_out),
                                          _ptr(workspace), workspace.numel() * workspace.element_size(),
@@ -223,7 +266,10 @@ def redo_propagate_phase(handle: int, q: torch.Tensor, phi: torch.Tensor, prec, 
                          workspace: torch.Tensor, status: torch.Tensor | None = None, reunit_every: int = 0,
                          stream=None):
     """Amplitude/phase controls: q the quantised amplitudes, phi [B][M][K] the phases (radians)."""
-    B, M = q.shape[0], q.shape[1]
+    B, M, N, K = _levels(handle, q)
+    _room(phi, "phi", B * M * K * 8)
+    _room(U_out, "U_out", B * N * N * 16)
+    _room(F_out, "F_out", B * 8)
     _check(load_library().redo_propagate_phase(ctypes.c_void_p(handle), _ptr(q), _ptr(phi), B, M, _prec(prec),
                                                reunit_every, _ptr(U_out), _ptr(U_target), _ptr(F_out),
                                                _ptr(tau_out), _ptr(workspace),
@@ -236,7 +282,10 @@ def redo_propagate_noalloc(handle: int, q: torch.Tensor, prec, U_out: torch.Tens
                            status: torch.Tensor | None = None, stream=None):
     """redo_propagate without a workspace: scratch is the library's fixed device array
     (for callers that cannot allocate device memory)."""
-    B, M = q.shape[0], q.shape[1]
+    B, M, N, K = _levels(handle, q)
+    _room(U_out, "U_out", B * N * N * 16)
+    _room(F_out, "F_out", B * 8)
+    _room(tau_out, "tau_out", B * 16)
     _check(load_library().redo_propagate_noalloc(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), _ptr(U_out),
                                                  _ptr(U_target), _ptr(F_out), _ptr(tau_out), _ptr(status),
                                                  _stream(stream)))
@@ -252,7 +301,8 @@ def redo_propagate_steps_workspace(handle: int, B: int, M: int, prec) -> int:
 def redo_propagate_steps(handle: int, q: torch.Tensor, prec, U_steps: torch.Tensor,
                          workspace: torch.Tensor | None = None, status: torch.Tensor | None = None, stream=None):
     """U_steps[b][n] = the step propagator of step n of pulse b (complex128 [B][M][N][N])."""
-    B, M = q.shape[0], q.shape[1]
+    B, M, N, K = _levels(handle, q)
+    _room(U_steps, "U_steps", B * M * N * N * 16)
     nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(load_library().redo_propagate_steps(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), _ptr(U_steps),
                                                _ptr(workspace), nbytes, _ptr(status), _stream(stream)))
@@ -286,8 +336,11 @@ def redo_fidelity_grad(handle: int, q: torch.Tensor, U_target: torch.Tensor, pre
                        F_out: torch.Tensor | None, grad: torch.Tensor, workspace: torch.Tensor,
                        status: torch.Tensor | None = None, stream=None, reunit_every: int = 0):
     """F and dF/du; reunit_every > 0 (equal to checkpoint_every) re-unitarises every checkpoint segment."""
-    B, M = q.shape[0], q.shape[1]
+    B, M, N, K = _levels(handle, q)
     batched = 1 if U_target.dim() == 3 else 0
+    _room(U_target, "U_target", (B if batched else 1) * N * N * 16)
+    _room(grad, "grad", B * M * K * 8)
+    _room(F_out, "F_out", B * 8)
     _check(load_library().redo_fidelity_grad(ctypes.c_void_p(handle), _ptr(q), B, M, _ptr(U_target), batched,
                                              _prec(prec), checkpoint_every, int(reunit_every), _ptr(F_out),
                                              _ptr(grad), _ptr(workspace), workspace.numel() * workspace.element_size(),
@@ -306,8 +359,12 @@ def redo_fidelity_grad_drift(handle: int, q: torch.Tensor, h: torch.Tensor, U_ta
                              workspace: torch.Tensor, status: torch.Tensor | None = None, stream=None,
                              reunit_every: int = 0):
     """redo_fidelity_grad with pulse b's diagonal drift h[b] (device float64 [B][N], rad/s)."""
-    B, M = q.shape[0], q.shape[1]
+    B, M, N, K = _levels(handle, q)
     batched = 1 if U_target.dim() == 3 else 0
+    _room(h, "h", B * N * 8)
+    _room(U_target, "U_target", (B if batched else 1) * N * N * 16)
+    _room(grad, "grad", B * M * K * 8)
+    _room(F_out, "F_out", B * 8)
     _check(load_library().redo_fidelity_grad_drift(ctypes.c_void_p(handle), _ptr(q), _ptr(h), B, M, _ptr(U_target),
                                                    batched, _prec(prec), checkpoint_every, int(reunit_every),
                                                    _ptr(F_out), _ptr(grad), _ptr(workspace),
@@ -319,6 +376,10 @@ def redo_grape_step(handle: int, u: torch.Tensor, grad: torch.Tensor, step: floa
                     step_scale: torch.Tensor | None = None, stream=None):
     """In place: u <- clamp(u + step * s_b * grad, lo_k, hi_k) (gradient ascent on the fidelity)."""
     B, M = u.shape[0], u.shape[1]
+    N, K = _table_nk(handle)
+    _exact(u, "u", torch.float64, B * M * K)
+    _room(grad, "grad", B * M * K * 8)
+    _room(step_scale, "step_scale", B * 8)
     _check(load_library().redo_grape_step(ctypes.c_void_p(handle), _ptr(u), _ptr(grad), B, M, float(step),
                                           _ptr(step_scale), _stream(stream)))
 
@@ -333,8 +394,12 @@ def redo_simulate_workspace(handle: int, B: int, M: int, prec, reunit_every: int
 def redo_simulate(handle: int, q: torch.Tensor, prec, reunit_every: int, psi0: torch.Tensor, obs_diag: torch.Tensor,
                   expect: torch.Tensor, U_final: torch.Tensor | None, workspace: torch.Tensor | None,
                   status: torch.Tensor | None = None, stream=None):
-    B, M = q.shape[0], q.shape[1]
+    B, M, N, K = _levels(handle, q)
     batched = 1 if psi0.dim() == 2 else 0
+    _room(psi0, "psi0", (B if batched else 1) * N * 16)
+    _room(obs_diag, "obs_diag", N * 8)
+    _room(expect, "expect", B * (M + 1) * 8)
+    _room(U_final, "U_final", B * N * N * 16)
     nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(load_library().redo_simulate(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), reunit_every,
                                         _ptr(psi0), batched, _ptr(obs_diag), _ptr(expect), _ptr(U_final),
@@ -344,7 +409,7 @@ def redo_simulate(handle: int, q: torch.Tensor, prec, reunit_every: int, psi0: t
 def redo_expect_diag(handle: int, q: torch.Tensor, prec, rho_diag: torch.Tensor, obs_diag: torch.Tensor,
                      expect: torch.Tensor | None, expect_mean: torch.Tensor | None,
                      status: torch.Tensor | None = None, stream=None):
-    B, M = q.shape[0], q.shape[1]
+    B, M, N, K = _levels(handle, q)
     _check(load_library().redo_expect_diag(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), _ptr(rho_diag),
                                            _ptr(obs_diag), _ptr(expect), _ptr(expect_mean), _ptr(status),
                                            _stream(stream)))
@@ -359,8 +424,12 @@ def redo_state_grad_workspace(handle: int, B: int) -> int:
 def redo_state_grad(handle: int, q: torch.Tensor, prec, psi0: torch.Tensor, psi_target: torch.Tensor,
                     F: torch.Tensor | None, grad: torch.Tensor | None, workspace: torch.Tensor | None,
                     status: torch.Tensor | None = None, stream=None):
-    B, M = q.shape[0], q.shape[1]
+    B, M, N, K = _levels(handle, q)
     batched = 1 if psi0.dim() == 2 else 0
+    _room(psi0, "psi0", (B if batched else 1) * N * 16)
+    _room(psi_target, "psi_target", (B if batched else 1) * N * 16)
+    _room(grad, "grad", B * M * K * 8)
+    _room(F, "F", B * 8)
     nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(load_library().redo_state_grad(ctypes.c_void_p(handle), _ptr(q), B, M, _prec(prec), _ptr(psi0),
                                           _ptr(psi_target), batched, _ptr(F), _ptr(grad), _ptr(workspace), nbytes,
@@ -402,6 +471,10 @@ def redo_grape_adam_step(handle: int, u, grad, m, v, step: int, lr: float, beta1
                          stream=None):
     """In place Adam ascent on the coefficients u (clamped to each term's grid)."""
     B, M = u.shape[0], u.shape[1]
+    N, K = _table_nk(handle)
+    _exact(u, "u", torch.float64, B * M * K)
+    for t, name in ((grad, "grad"), (m, "m"), (v, "v")):
+        _room(t, name, B * M * K * 8)
     _check(load_library().redo_grape_adam_step(ctypes.c_void_p(handle), _ptr(u), _ptr(grad), _ptr(m), _ptr(v), B, M,
                                                int(step), float(lr), float(beta1), float(beta2), float(eps),
                                                _stream(stream)))
@@ -417,6 +490,12 @@ def redo_grape_lbfgs_step(handle: int, u, grad, F, state, first: bool, history: 
                           c1: float = 1e-4, u_best=None, F_best=None, stream=None):
     """In place: u (the point just evaluated) becomes the next point of projected L-BFGS ascent."""
     B, M = u.shape[0], u.shape[1]
+    N, K = _table_nk(handle)
+    _exact(u, "u", torch.float64, B * M * K)
+    _room(grad, "grad", B * M * K * 8)
+    _room(u_best, "u_best", B * M * K * 8)
+    _room(F, "F", B * 8)
+    _room(F_best, "F_best", B * 8)
     _check(load_library().redo_grape_lbfgs_step(ctypes.c_void_p(handle), _ptr(u), _ptr(grad), _ptr(F), B, M,
                                                 int(history), 1 if first else 0, float(step0), float(c1),
                                                 _ptr(state), state.numel() * state.element_size(), _ptr(u_best),
@@ -531,7 +610,7 @@ def _table_propagate_phase(self, q, phi, prec="fp64", target=None, want_U=True, 
 
 def _table_fidelity_grad_phase(self, q, phi, target, prec="fp64", checkpoint_every=0, status=None):
     """(F [B], dF/dA [B][M][K], dF/dphi [B][M][K]) for amplitude/phase controls."""
-    B, M = q.shape[0], q.shape[1]
+    B, M, _, _ = _levels(self.handle, q)
     phi = torch.as_tensor(phi, dtype=torch.float64, device=self.device).contiguous()
     target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
     F = torch.empty(B, dtype=torch.float64, device=self.device)
@@ -556,7 +635,7 @@ Table.propagate_phase = _table_propagate_phase
 def _table_propagate_drift(self, q, h, prec="fp64", target=None, want_U=True, status=None, reunit_every=0):
     """(U [B][N][N] or None, F or None, tau or None) with a diagonal drift per pulse: h [B][N] the
     drift energies (rad/s) applied each step as diag(exp(-i dt h_b)) before the table factors."""
-    B, M = q.shape[0], q.shape[1]
+    B, M, _, _ = _levels(self.handle, q)
     h = torch.as_tensor(h, dtype=torch.float64, device=self.device).contiguous()
     U = torch.empty((B, self.N, self.N), dtype=torch.complex128, device=self.device) if want_U else None
     F = tau = None

@@ -193,3 +193,67 @@ def test_host_only_entry_points_survive_edge_inputs(lib):
     r = subprocess.run([sys.executable, "-c", _HOST_FUZZ, ROOT], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.startswith("ok")
+
+
+@pytest.fixture
+def fake_table():
+    """A handle whose (N, K) = (4, 3) sits in the binding's cache; no library table behind it."""
+    h = 987654321
+    redo._TABLE_NK[h] = (4, 3)
+    yield h
+    redo._TABLE_NK.pop(h, None)
+
+
+def _past_checks(fn, *a, **kw):
+    # correct sizes reach the device check, which host tensors then fail
+    with pytest.raises(ValueError, match="device tensor expected"):
+        fn(*a, **kw)
+
+
+def test_binding_checks_sizes_against_the_table(fake_table):
+    import torch
+    h, B, M, N, K = fake_table, 2, 5, 4, 3
+    u = torch.zeros((B, M, K), dtype=torch.float64)
+    q = torch.zeros((B, M, K), dtype=torch.int32)
+    _past_checks(redo.redo_quantize, h, u, q)
+    with pytest.raises(ValueError, match="elements expected"):
+        redo.redo_quantize(h, torch.zeros((B, M, K + 1), dtype=torch.float64), q)
+    with pytest.raises(ValueError, match="int32 expected"):
+        redo.redo_quantize(h, u, q.to(torch.int64))
+    with pytest.raises(ValueError, match="float64 expected"):
+        redo.redo_quantize(h, u.float(), q)
+    ws = torch.zeros(256, dtype=torch.uint8)
+    U = torch.zeros((B, N, N), dtype=torch.complex128)
+    _past_checks(redo.redo_propagate, h, q, "fp64", U, None, None, None, ws)
+    with pytest.raises(ValueError, match="elements expected"):
+        redo.redo_propagate(h, q[:, :, :2].contiguous(), "fp64", U, None, None, None, ws)
+    with pytest.raises(ValueError, match="U_out"):
+        redo.redo_propagate(h, q, "fp64", U[:1], None, None, None, ws)
+    with pytest.raises(ValueError, match="F_out"):
+        redo.redo_propagate(h, q, "fp64", U, torch.zeros((N, N), dtype=torch.complex128),
+                            torch.zeros(1, dtype=torch.float64), None, ws)
+    g = torch.zeros((B, M, K), dtype=torch.float64)
+    T = torch.zeros((N, N), dtype=torch.complex128)
+    F = torch.zeros(B, dtype=torch.float64)
+    _past_checks(redo.redo_fidelity_grad, h, q, T, "fp64", 0, F, g, ws)
+    with pytest.raises(ValueError, match="grad"):
+        redo.redo_fidelity_grad(h, q, T, "fp64", 0, F, g[:, :2], ws)
+    with pytest.raises(ValueError, match="U_target"):
+        redo.redo_fidelity_grad(h, q, torch.zeros((1, N, N), dtype=torch.complex128), "fp64", 0, F, g, ws)
+    _past_checks(redo.redo_grape_step, h, u, g, 0.1)
+    with pytest.raises(ValueError, match="step_scale"):
+        redo.redo_grape_step(h, u, g, 0.1, torch.ones(1, dtype=torch.float64))
+    _past_checks(redo.redo_grape_adam_step, h, u, g, torch.zeros_like(u), torch.zeros_like(u), 1, 0.01)
+    with pytest.raises(ValueError, match="elements expected"):
+        redo.redo_grape_adam_step(h, torch.zeros((B, M, K + 2), dtype=torch.float64), g, g, g, 1, 0.01)
+    psi = torch.zeros(N, dtype=torch.complex128)
+    _past_checks(redo.redo_simulate, h, q, "fp64", 0, psi, torch.zeros(N, dtype=torch.float64),
+                 torch.zeros((B, M + 1), dtype=torch.float64), None, None)
+    with pytest.raises(ValueError, match="expect"):
+        redo.redo_simulate(h, q, "fp64", 0, psi, torch.zeros(N, dtype=torch.float64),
+                           torch.zeros((B, M), dtype=torch.float64), None, None)
+    # an empty pulse (M = 0) of a K = 1 table may drop its last axis
+    redo._TABLE_NK[h] = (4, 1)
+    _past_checks(redo.redo_quantize, h, torch.zeros((3, 7), dtype=torch.float64), torch.zeros((3, 7), dtype=torch.int32))
+    _past_checks(redo.redo_propagate, h, torch.zeros((3, 0, 1), dtype=torch.int32), "fp64",
+                 torch.zeros((3, N, N), dtype=torch.complex128), None, None, None, ws)
