@@ -201,6 +201,9 @@ def redo_table_info(handle: int) -> dict:
 
 
 def redo_table_copy(handle: int, table_out: torch.Tensor | None, drift_out: torch.Tensor | None, stream=None):
+    i = redo_table_info(handle)
+    _room(table_out, "table_out", i["entries"] * i["N"] * i["N"] * 16)
+    _room(drift_out, "drift_out", i["N"] * i["N"] * 16)
     _check(load_library().redo_table_copy(ctypes.c_void_p(handle), _ptr(table_out), _ptr(drift_out),
                                           _stream(stream)))
 
@@ -242,6 +245,13 @@ def redo_batched_product(A: torch.Tensor, B: torch.Tensor, adjA: bool = False, a
     count = max(A.shape[0] if A.dim() == 3 else 1, B.shape[0] if B.dim() == 3 else 1)
     if out is None:
         out = torch.empty((count, N, N), dtype=torch.complex128, device=A.device)
+    for t, name in ((A, "A"), (B, "B")):
+        if t.dtype != torch.complex128 or t.dim() not in (2, 3) or tuple(t.shape[-2:]) != (N, N):
+            raise ValueError(f"{name}: complex128 [N][N] or [count][N][N] with N = {N} expected, got "
+                             f"{t.dtype} {tuple(t.shape)}")
+    if A.dim() == 3 and B.dim() == 3 and A.shape[0] != B.shape[0]:
+        raise ValueError(f"A and B batches differ: {A.shape[0]} and {B.shape[0]}")
+    _room(out, "out", count * N * N * 16)
     A, B = A.contiguous(), B.contiguous()
     _check(load_library().redo_batched_product(N, count, _ptr(A), int(adjA), int(A.dim() == 3), _ptr(B), int(adjB),
                                                int(B.dim() == 3), _ptr(out), _stream(stream)))
@@ -312,6 +322,9 @@ def redo_reunitarize(P_in: torch.Tensor, U_out: torch.Tensor, prec="fp64", iters
     """Newton-Schulz steps P <- P (3I - P^dag P)/2 on complex128 [count][N][N] matrices."""
     N = P_in.shape[-1]
     count = P_in.numel() // (N * N)
+    if P_in.dtype != torch.complex128 or P_in.numel() != count * N * N:
+        raise ValueError(f"P_in: complex128 [count][N][N] expected, got {P_in.dtype} {tuple(P_in.shape)}")
+    _room(U_out, "U_out", count * N * N * 16)
     _check(load_library().redo_reunitarize(N, count, _prec(prec), _ptr(P_in), _ptr(U_out), int(iters),
                                            _stream(stream)))
 
@@ -449,20 +462,41 @@ def redo_mlp_sizes(sizes, batch: int) -> tuple[int, int, int]:
     return p.value, a.value, w.value
 
 
+def _mlp_check(sizes, params, x, acts):
+    """params, x and acts of a network of these widths for x.shape[0] samples; returns the
+    (params, acts, work) float counts of redo_mlp_sizes."""
+    p, a, w = redo_mlp_sizes(sizes, x.shape[0])
+    _exact(params, "params", torch.float32, p)
+    _exact(x, "x", torch.float32, x.shape[0] * int(sizes[0]))
+    _room(acts, "acts", a * 4)
+    return p, a, w
+
+
 def redo_mlp_forward(sizes, params, x, acts, y, stream=None):
     arr, L = _sizes_arg(sizes)
+    _mlp_check(sizes, params, x, acts)
+    _room(y, "y", x.shape[0] * int(sizes[-1]) * 4)
     _check(load_library().redo_mlp_forward(L, ctypes.cast(arr, ctypes.c_void_p), _ptr(params), _ptr(x), x.shape[0],
                                            _ptr(acts), _ptr(y), _stream(stream)))
 
 
 def redo_mlp_backward(sizes, params, x, acts, y_target, grads, loss, work, stream=None):
     arr, L = _sizes_arg(sizes)
+    p, _, w = _mlp_check(sizes, params, x, acts)
+    _exact(y_target, "y_target", torch.float32, x.shape[0] * int(sizes[-1]))
+    _room(grads, "grads", p * 4)
+    _room(work, "work", w * 4)
+    _room(loss, "loss", 8)
     _check(load_library().redo_mlp_backward(L, ctypes.cast(arr, ctypes.c_void_p), _ptr(params), _ptr(x), x.shape[0],
                                             _ptr(acts), _ptr(y_target), _ptr(grads), _ptr(loss), _ptr(work),
                                             _stream(stream)))
 
 
 def redo_mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    if params.dtype != torch.float32:
+        raise ValueError(f"params: torch.float32 expected, got {params.dtype}")
+    for t, name in ((grads, "grads"), (m, "m"), (v, "v")):
+        _room(t, name, params.numel() * 4)
     _check(load_library().redo_mlp_adam(params.numel(), _ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(step),
                                         float(lr), float(beta1), float(beta2), float(eps), _stream(stream)))
 

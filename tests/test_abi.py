@@ -257,3 +257,43 @@ def test_binding_checks_sizes_against_the_table(fake_table):
     _past_checks(redo.redo_quantize, h, torch.zeros((3, 7), dtype=torch.float64), torch.zeros((3, 7), dtype=torch.int32))
     _past_checks(redo.redo_propagate, h, torch.zeros((3, 0, 1), dtype=torch.int32), "fp64",
                  torch.zeros((3, N, N), dtype=torch.complex128), None, None, None, ws)
+
+
+def test_binding_checks_products_reunitarisation_and_mlp_arrays(lib):
+    import torch
+    N = 4
+    A = torch.zeros((3, N, N), dtype=torch.complex128)
+    _past_checks(redo.redo_batched_product, A, torch.zeros((N, N), dtype=torch.complex128))
+    with pytest.raises(ValueError, match="batches differ"):
+        redo.redo_batched_product(A, torch.zeros((2, N, N), dtype=torch.complex128))
+    with pytest.raises(ValueError, match="complex128"):
+        redo.redo_batched_product(A, torch.zeros((3, N, N + 1), dtype=torch.complex128))
+    with pytest.raises(ValueError, match="complex128"):
+        redo.redo_batched_product(A, torch.zeros((3, N, N), dtype=torch.complex64))
+    with pytest.raises(ValueError, match="out"):
+        redo.redo_batched_product(A, A, out=torch.zeros((2, N, N), dtype=torch.complex128))
+    _past_checks(redo.redo_reunitarize, A, torch.empty_like(A))
+    with pytest.raises(ValueError, match="P_in"):
+        redo.redo_reunitarize(A.to(torch.complex64), torch.empty_like(A))
+    with pytest.raises(ValueError, match="U_out"):
+        redo.redo_reunitarize(A, torch.empty((2, N, N), dtype=torch.complex128))
+    sizes, batch = [5, 7, 3], 4
+    p, a, w = redo.redo_mlp_sizes(sizes, batch)
+    params = torch.zeros(p, dtype=torch.float32)
+    x = torch.zeros((batch, 5), dtype=torch.float32)
+    acts = torch.zeros(a, dtype=torch.float32)
+    y = torch.zeros((batch, 3), dtype=torch.float32)
+    _past_checks(redo.redo_mlp_forward, sizes, params, x, acts, y)
+    with pytest.raises(ValueError, match="params"):
+        redo.redo_mlp_forward(sizes, params[:-1], x, acts, y)
+    with pytest.raises(ValueError, match="x"):
+        redo.redo_mlp_forward(sizes, params, torch.zeros((batch, 6), dtype=torch.float32), acts, y)
+    with pytest.raises(ValueError, match="acts"):
+        redo.redo_mlp_forward(sizes, params, x, acts[:-1], y)
+    work, grads = torch.zeros(w, dtype=torch.float32), torch.zeros(p, dtype=torch.float32)
+    _past_checks(redo.redo_mlp_backward, sizes, params, x, acts, y, grads, None, work)
+    with pytest.raises(ValueError, match="work"):
+        redo.redo_mlp_backward(sizes, params, x, acts, y, grads, None, work[:-1])
+    _past_checks(redo.redo_mlp_adam, params, grads, grads.clone(), grads.clone(), 1, 1e-3)
+    with pytest.raises(ValueError, match="float32"):
+        redo.redo_mlp_adam(params.double(), grads, grads, grads, 1, 1e-3)
