@@ -179,6 +179,12 @@ def redo_build_table(H0: torch.Tensor, Hk: torch.Tensor, dt: float, lo, hi, base
     K = Hk.shape[0]
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     hi = np.ascontiguousarray(hi, dtype=np.float64)
+    if tuple(H0.shape) != (N, N) or tuple(Hk.shape) != (K, N, N):
+        raise ValueError(f"H0 [N][N] and Hk [K][N][N] expected, got {tuple(H0.shape)} and {tuple(Hk.shape)}")
+    if H0.dtype != torch.complex128 or Hk.dtype != torch.complex128:
+        raise ValueError("H0 and Hk: torch.complex128 expected")
+    if lo.size != K or hi.size != K:
+        raise ValueError(f"lo and hi: {K} values expected (one per control term), got {lo.size} and {hi.size}")
     out = ctypes.c_void_p()
     _check(L.redo_build_table(N, K, float(dt), _ptr(H0), _ptr(Hk), lo.ctypes.data_as(ctypes.c_void_p),
                               hi.ctypes.data_as(ctypes.c_void_p), base, digits, flags, _stream(stream),
@@ -261,6 +267,9 @@ def redo_batched_product(A: torch.Tensor, B: torch.Tensor, adjA: bool = False, a
 def redo_table_set_phase_axes(handle: int, sz: np.ndarray):
     """Attach the diagonals of the species' S_kz ([K][N], host) for amplitude/phase calls."""
     sz = np.ascontiguousarray(sz, dtype=np.float64)
+    N, K = _table_nk(handle)
+    if sz.size != K * N:
+        raise ValueError(f"sz: [K][N] = {K * N} values expected, got {sz.size}")
     _check(load_library().redo_table_set_phase_axes(ctypes.c_void_p(handle), sz.ctypes.data))
 
 
@@ -647,6 +656,8 @@ def _table_fidelity_grad_phase(self, q, phi, target, prec="fp64", checkpoint_eve
     B, M, _, _ = _levels(self.handle, q)
     phi = torch.as_tensor(phi, dtype=torch.float64, device=self.device).contiguous()
     target = torch.as_tensor(target, dtype=torch.complex128, device=self.device).contiguous()
+    _room(phi, "phi", B * M * self.K * 8)
+    _room(target, "target", (B if target.dim() == 3 else 1) * self.N * self.N * 16)
     F = torch.empty(B, dtype=torch.float64, device=self.device)
     gA = torch.empty((B, M, self.K), dtype=torch.float64, device=self.device)
     gP = torch.empty((B, M, self.K), dtype=torch.float64, device=self.device)
@@ -671,6 +682,7 @@ def _table_propagate_drift(self, q, h, prec="fp64", target=None, want_U=True, st
     drift energies (rad/s) applied each step as diag(exp(-i dt h_b)) before the table factors."""
     B, M, _, _ = _levels(self.handle, q)
     h = torch.as_tensor(h, dtype=torch.float64, device=self.device).contiguous()
+    _room(h, "h", B * self.N * 8)
     U = torch.empty((B, self.N, self.N), dtype=torch.complex128, device=self.device) if want_U else None
     F = tau = None
     if target is not None:

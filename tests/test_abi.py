@@ -297,3 +297,24 @@ def test_binding_checks_products_reunitarisation_and_mlp_arrays(lib):
     _past_checks(redo.redo_mlp_adam, params, grads, grads.clone(), grads.clone(), 1, 1e-3)
     with pytest.raises(ValueError, match="float32"):
         redo.redo_mlp_adam(params.double(), grads, grads, grads, 1, 1e-3)
+
+
+def test_binding_checks_table_build_inputs():
+    import torch
+    N, K = 4, 2
+    H0 = torch.zeros((N, N), dtype=torch.complex128)
+    Hk = torch.zeros((K, N, N), dtype=torch.complex128)
+    with pytest.raises(ValueError, match="device tensor expected"):
+        redo.redo_build_table(H0, Hk, 1e-6, [-1.0, -1.0], [1.0, 1.0], 64, 2)
+    with pytest.raises(ValueError, match="one per control term"):
+        redo.redo_build_table(H0, Hk, 1e-6, [-1.0], [1.0], 64, 2)
+    with pytest.raises(ValueError, match=r"Hk \[K\]\[N\]\[N\]"):
+        redo.redo_build_table(H0, torch.zeros((K, N, N + 1), dtype=torch.complex128), 1e-6, [-1.0] * 2, [1.0] * 2, 64, 2)
+    with pytest.raises(ValueError, match="complex128"):
+        redo.redo_build_table(H0.to(torch.complex64), Hk, 1e-6, [-1.0] * 2, [1.0] * 2, 64, 2)
+
+
+def test_binding_checks_phase_axes(fake_table):
+    import numpy as np
+    with pytest.raises(ValueError, match="sz"):
+        redo.redo_table_set_phase_axes(fake_table, np.zeros((3, 3)))
