@@ -1,5 +1,4 @@
 """GPU state simulation (Section IV) against the oracle and a closed form."""
-import math
 
 import numpy as np
 import pytest
