@@ -162,6 +162,11 @@ CASES = [
      [P.test_table_thetas_sum_to_level_value]),
     ("Pade exponential: sign of the exponent", "expm_pade13", lambda f: lambda A: f(-A),
      [lambda: P.test_expm_pauli_closed_form(0.3)]),
+    ("Pade exponential: coefficient b_3 off by 1e-6", "_B13",
+     lambda f: [c * (1 + 1e-6) if j == 3 else c for j, c in enumerate(f)],
+     [lambda: P.test_expm_pauli_closed_form(1.7), P.test_expm_against_scipy_and_eig]),
+    ("Pade exponential: no scaling before squaring", "_THETA13", lambda f: 1e9,
+     [lambda: P.test_expm_pauli_closed_form(250.0), P.test_expm_against_scipy_and_eig]),
     ("Pade exponential: transposed", "expm_pade13", lambda f: lambda A: f(A).T,
      [P.test_expm_against_scipy_and_eig]),
     ("eigen exponential: sign of t", "expm_hermitian", lambda f: lambda H, t, eig=None: f(H, -t, eig),
