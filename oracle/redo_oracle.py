@@ -117,7 +117,8 @@ def level_digits(q, base, digits):
 
 
 def level_values(q, lo, hi, levels):
-    """Quantised coefficient ``u_hat = lo + q*delta`` (the coarse-grained value)."""
+    """Quantised coefficient ``u_hat = lo + q*delta``: the coarse-grained value of Eq. (cgrain),
+    Section II."""
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     delta = (hi - lo) / np.float64(levels - 1)
@@ -159,7 +160,9 @@ def plan_digits(omega_max, eps, base):
 # ---------------------------------------------------------------------------
 
 def _pade13_coefficients():
-    # [13/13] Pade approximant of exp: b_j = (26 - j)! 13! / (26! j! (13 - j)!)
+    """Coefficients b_j of the [13/13] Pade approximant of exp, the numerator polynomial of
+    Higham (2005) for the Pade method the paper compares with (Section II)."""
+    # b_j = (26 - j)! 13! / (26! j! (13 - j)!)
     m = 13
     out = []
     for j in range(m + 1):
@@ -203,7 +206,8 @@ def expm_pade13(A):
 
 
 def expm_hermitian(H, t, eig=None):
-    """``exp(-i t H)`` for Hermitian H by eigen-decomposition ``H = V diag(w) V^dag``.
+    """``exp(-i t H)`` for Hermitian H by eigen-decomposition ``H = V diag(w) V^dag`` (the "ED"
+    method among the paper's comparison methods, Section II).
 
     ``eig`` may pass ``(w, V) = numpy.linalg.eigh(H)`` computed once for many ``t``."""
     if eig is None:
@@ -290,7 +294,9 @@ def exact_step(H0, Hk, dt, u_row):
 
 
 def split_step(H0, Hk, dt, u_row):
-    """Split but unquantised step ``exp(-i dt u_{K-1} H_{K-1}) ... exp(-i dt u_0 H_0) exp(-i dt H0)``."""
+    """Split but unquantised step ``exp(-i dt u_{K-1} H_{K-1}) ... exp(-i dt u_0 H_0) exp(-i dt H0)``:
+    the Section III step formula at continuous coefficients (what the table evaluates at the
+    quantised ones)."""
     U = expm_pade13(-1j * dt * np.asarray(H0, dtype=np.complex128))
     for k in range(Hk.shape[0]):
         U = expm_pade13(-1j * dt * u_row[k] * Hk[k]) @ U
@@ -309,14 +315,16 @@ def split_step(H0, Hk, dt, u_row):
 # step by step here, with no use of the identity prod_n S_n = D_h (prod_n E_n D) D_h^dag.
 
 def half_drift(H0, dt, method="pade"):
-    """``D_h = exp(-i (dt/2) H0)``."""
+    """``D_h = exp(-i (dt/2) H0)``: half of the Section III drift step, for the symmetric variant
+    of the step that splits the drift evenly around the control factors."""
     if method == "pade":
         return expm_pade13(-0.5j * dt * np.asarray(H0, dtype=np.complex128))
     return expm_hermitian(H0, 0.5 * dt)
 
 
 def strang_step_propagator(T, Dh, digit_row):
-    """One symmetric step ``S_n = D_h E_{K-1} ... E_0 D_h`` (T not folded with the drift)."""
+    """One symmetric step ``S_n = D_h E_{K-1} ... E_0 D_h`` (T not folded with the drift): the
+    Section III step with the drift split evenly, products of Eq. (exp2prod) as in process 2."""
     U = Dh
     for E in step_factors(T, Dh, digit_row):
         U = E @ U
@@ -324,7 +332,8 @@ def strang_step_propagator(T, Dh, digit_row):
 
 
 def propagate_strang(T, Dh, digits_bm):
-    """Chained symmetric propagator ``S_M ... S_1`` for one pulse."""
+    """Chained symmetric propagator ``S_M ... S_1`` for one pulse (the Section III chain of
+    symmetric steps)."""
     U = np.eye(Dh.shape[0], dtype=np.complex128)
     for n in range(digits_bm.shape[0]):
         U = strang_step_propagator(T, Dh, digits_bm[n]) @ U
@@ -332,7 +341,8 @@ def propagate_strang(T, Dh, digits_bm):
 
 
 def strang_split_step(H0, Hk, dt, u_row):
-    """Symmetric split, unquantised step ``D_h exp(-i dt u_{K-1} H_{K-1}) ... exp(-i dt u_0 H_0) D_h``."""
+    """Symmetric split, unquantised step ``D_h exp(-i dt u_{K-1} H_{K-1}) ... exp(-i dt u_0 H_0) D_h``
+    (the Section III step with the drift split evenly, at continuous coefficients)."""
     Dh = expm_pade13(-0.5j * dt * np.asarray(H0, dtype=np.complex128))
     U = Dh
     for k in range(Hk.shape[0]):
@@ -341,7 +351,8 @@ def strang_split_step(H0, Hk, dt, u_row):
 
 
 def simulate_expectation_strang(T, Dh, digits_bm, psi0, obs_diag):
-    """``<O>(t_n)`` along the symmetric chain, ``psi_n = S_n ... S_1 psi0``; returns (expect, U_final)."""
+    """``<O>(t_n)`` along the symmetric chain, ``psi_n = S_n ... S_1 psi0`` (Section IV's
+    expectation values on the chain of symmetric steps); returns (expect, U_final)."""
     N = Dh.shape[0]
     X = np.eye(N, dtype=np.complex128)
     out = np.empty(digits_bm.shape[0] + 1, dtype=np.float64)
@@ -366,12 +377,14 @@ def simulate_expectation_strang(T, Dh, digits_bm, psi0, obs_diag):
 # per basis state, exp(-i sum_k phi_kn sz[k][a]).
 
 def phase_rotation(phi_row, sz):
-    """Diagonal of ``Z_n = exp(-i sum_k phi_kn S_kz)``; ``sz[k]`` is the diagonal of ``S_kz``."""
+    """Diagonal of ``Z_n = exp(-i sum_k phi_kn S_kz)``; ``sz[k]`` is the diagonal of ``S_kz``
+    (the phase turn of the drive of Section III, Eq. vn)."""
     return np.exp(-1j * (np.asarray(phi_row, dtype=np.float64) @ np.asarray(sz, dtype=np.float64)))
 
 
 def phase_step_propagator(T, D, digit_row, phi_row, sz):
-    """One amplitude/phase step ``U_n = Z_n E_{K-1} ... E_0 Z_n^dag D`` (T not folded with the drift)."""
+    """One amplitude/phase step ``U_n = Z_n E_{K-1} ... E_0 Z_n^dag D`` (T not folded with the drift):
+    Section III, Eq. vn and the Dirac-frame step that follows Eq. vnd."""
     Z = np.diag(phase_rotation(phi_row, sz))
     E = np.eye(D.shape[0], dtype=np.complex128)
     for Ek in step_factors(T, D, digit_row):
@@ -380,7 +393,8 @@ def phase_step_propagator(T, D, digit_row, phi_row, sz):
 
 
 def propagate_phase(T, D, digits_bm, phi_bm, sz):
-    """Chained amplitude/phase propagator ``U_M ... U_1`` for one pulse; ``phi_bm`` is (M, K)."""
+    """Chained amplitude/phase propagator ``U_M ... U_1`` for one pulse (Section III);
+    ``phi_bm`` is (M, K)."""
     U = np.eye(D.shape[0], dtype=np.complex128)
     for n in range(digits_bm.shape[0]):
         U = phase_step_propagator(T, D, digits_bm[n], phi_bm[n], sz) @ U
@@ -389,7 +403,7 @@ def propagate_phase(T, D, digits_bm, phi_bm, sz):
 
 def phase_split_step(H0, Sx, sz, dt, amp_row, phi_row):
     """Unquantised amplitude/phase step ``Z_n exp(-i dt A_{K-1} S_x,K-1) ... exp(-i dt A_0 S_x0) Z_n^dag
-    exp(-i dt H0)``."""
+    exp(-i dt H0)``: the step of Section III's Eq. vn drive at continuous amplitudes."""
     Z = np.diag(phase_rotation(phi_row, sz))
     E = np.eye(H0.shape[0], dtype=np.complex128)
     for k in range(Sx.shape[0]):
@@ -456,12 +470,14 @@ def phase_gradient(T, D, Sx, sz, dt, digits_bm, phi_bm, U_target):
 # ---------------------------------------------------------------------------
 
 def trace_overlap(U_target, U):
-    """``tau = Tr(U_T^dag U) = sum_ab conj(U_T[a,b]) U[a,b]``."""
+    """``tau = Tr(U_T^dag U) = sum_ab conj(U_T[a,b]) U[a,b]``, the overlap inside the unitary
+    fidelity of Section III."""
     return complex(np.sum(np.conj(U_target) * U))
 
 
 def fidelity(U_target, U):
-    """``F_U = |Tr(U_T^dag U)|^2 / N^2`` (``Tr(U_T^dag U_T) = N`` for unitary U_T)."""
+    """``F_U = |Tr(U_T^dag U)|^2 / N^2`` (``Tr(U_T^dag U_T) = N`` for unitary U_T), the unitary
+    fidelity of Section III."""
     N = U.shape[0]
     tau = trace_overlap(U_target, U)
     return (tau.real * tau.real + tau.imag * tau.imag) / float(N * N)
@@ -576,7 +592,8 @@ def state_transfer_gradient(T, D, Hk, dt, digits_bm, psi0, psiT):
 # hi_k] of its level grid, so that it always has a level.
 
 def grape_update(u, g, step, scale, lo, hi):
-    """One ascent step ``u_bnk <- clip(u_bnk + step * s_b * g_bnk, lo_k, hi_k)``.
+    """One ascent step ``u_bnk <- clip(u_bnk + step * s_b * g_bnk, lo_k, hi_k)``: the update box
+    of the GRAPE flowchart (Section III, Fig. fc), whose rule the paper leaves open.
 
     ``u``, ``g``: (B, M, K); ``scale``: (B,) per-pulse factors s_b (None: all 1);
     ``lo``, ``hi``: (K,).  Returns the new array (the input is not modified).
@@ -593,7 +610,8 @@ def grape_update(u, g, step, scale, lo, hi):
 
 
 def grape_step_scale(scale, F, F_prev):
-    """Per-pulse step factors for the next ascent step: ``s_b / 2`` where the
+    """Per-pulse step factors of the GRAPE update (Section III, Fig. fc; rule read here):
+    ``s_b / 2`` where the
     fidelity fell (``F_b < F_prev_b``), else ``min(1.1 s_b, 8)``; unchanged before
     the first comparison (``F_prev`` None)."""
     scale = np.asarray(scale, dtype=np.float64)
@@ -722,7 +740,9 @@ def grape_lbfgs_step(u_trial, g_trial, F_trial, state, lo, hi, history=8, step0=
 # ---------------------------------------------------------------------------
 
 def polar_unitary(P):
-    """Unitary polar factor ``P (P^dag P)^(-1/2)`` via eigen-decomposition of P^dag P."""
+    """Unitary polar factor ``P (P^dag P)^(-1/2)`` via eigen-decomposition of P^dag P: the unitary
+    nearest P, which re-unitarisation of finite-precision chains approaches (the paper's chains
+    are exact products of unitary operators, Section III; it has no such step)."""
     P = np.asarray(P, dtype=np.complex128)
     w, V = np.linalg.eigh(P.conj().T @ P)
     return P @ ((V * (1.0 / np.sqrt(w))[None, :]) @ V.conj().T)
@@ -772,14 +792,15 @@ def expect_mixed(T, D, digits_bm, rho0, obs):
 # ---------------------------------------------------------------------------
 
 def gelu(x):
-    """Exact GELU ``0.5 x (1 + erf(x / sqrt 2))``."""
+    """Exact GELU ``0.5 x (1 + erf(x / sqrt 2))``, the activation of the warm-start network (an
+    extension of the Section III GRAPE application; the paper has no network)."""
     from math import erf
     v = np.vectorize(erf, otypes=[np.float64])
     return 0.5 * x * (1.0 + v(x / math.sqrt(2.0)))
 
 
 def gelu_grad(x):
-    """Derivative of the exact GELU: ``Phi(x) + x phi(x)``."""
+    """Derivative of the exact GELU: ``Phi(x) + x phi(x)`` (warm-start network, as :func:`gelu`)."""
     from math import erf
     v = np.vectorize(erf, otypes=[np.float64])
     Phi = 0.5 * (1.0 + v(x / math.sqrt(2.0)))
@@ -788,7 +809,8 @@ def gelu_grad(x):
 
 
 def mlp_init(sizes, rng):
-    """Weights ``W_l`` (out, in) ~ U[-1/sqrt(in), 1/sqrt(in)], biases zero."""
+    """Weights ``W_l`` (out, in) ~ U[-1/sqrt(in), 1/sqrt(in)], biases zero (warm-start network,
+    as :func:`gelu`)."""
     params = []
     for a, b in zip(sizes[:-1], sizes[1:]):
         lim = 1.0 / math.sqrt(a)
@@ -797,7 +819,8 @@ def mlp_init(sizes, rng):
 
 
 def mlp_forward(params, x):
-    """Hidden layers ``h = GELU(W h + b)``, output ``tanh(W h + b)``; x is (batch, in).
+    """Hidden layers ``h = GELU(W h + b)``, output ``tanh(W h + b)``; x is (batch, in) (the
+    warm-start network of the GRAPE extension, as :func:`gelu`).
 
     Returns ``(y, cache)`` with the pre-activations needed by :func:`mlp_backward`.
     """
@@ -812,7 +835,8 @@ def mlp_forward(params, x):
 
 
 def mlp_backward(params, cache, y_target):
-    """Gradients of the loss ``mean((y - y_target)^2)`` (mean over all entries)."""
+    """Gradients of the loss ``mean((y - y_target)^2)`` (mean over all entries) by the chain rule
+    through :func:`mlp_forward` (warm-start network, as :func:`gelu`)."""
     nl = len(params)
     y = cache[-1]
     dh = 2.0 * (y - y_target) / y.size
