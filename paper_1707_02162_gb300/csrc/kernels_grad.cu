@@ -1,4 +1,6 @@
 // GRAPE fidelity gradient of the REDO split model (SIMT, N <= 64, FP64/FP32).
+// (Section III: the gradient that GRAPE, Fig. fc, ascends; the paper prints no formula, so it is
+// derived here from the split model's definitions.)
 //
 // With the chain of table factors A_0 ... A_{F-1} of one pulse (A_0 applied
 // first), forward partial products P_f = A_f ... A_0 and backward costates

@@ -1,6 +1,8 @@
 // Large-N path (N = 128 ... 1024, powers of two): operators and states live in
 // global memory and every product is a batched complex GEMM, one launch per
 // chain step over all chains at once ("lockstep" chains).  SIMT FP64/FP32.
+// (Section II processes 1 and 2 -- the table and the products of Eq. exp2prod -- and the
+// Section III chain U = U_M ... U_1, gradient and Section IV dynamics for large N.)
 //
 // Everything the N <= 64 path does in shared memory is expressed here with
 // one GEMM kernel, templated on a small functor that names the three

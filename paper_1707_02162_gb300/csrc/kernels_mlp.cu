@@ -1,5 +1,6 @@
 // Multilayer perceptron for the learned warm start of GRAPE: forward,
 // backward (mean-squared error) and Adam, FP32 master weights.
+// (No paper counterpart: the learned warm start extends the GRAPE application of Section III.)
 //
 // Network: h_0 = x; z_l = h_l W_l^T + b_l; h_{l+1} = GELU(z_l) for hidden
 // layers (exact erf form) and tanh(z_l) for the output layer, whose entries are

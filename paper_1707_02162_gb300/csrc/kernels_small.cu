@@ -1,5 +1,7 @@
 // SIMT kernels of libredo for N <= 64: quantizer, FP64 operator table,
 // segmented product chains (FP64 / FP32) and the FP64 fidelity epilogue.
+// (Section II: Eq. cgrain for the quantizer, process 1 for the table, process 2 and Eq. exp2prod
+// for the products; Section III: the chain U = U_M ... U_1 and the unitary fidelity F_U.)
 //
 // Every product here is a complex N x N matrix product held in shared memory;
 // table operators are streamed in with bulk asynchronous copies

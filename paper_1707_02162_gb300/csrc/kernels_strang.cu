@@ -1,4 +1,6 @@
 // Symmetric (Strang) split of a step: S_n = D_h E_{K-1} ... E_0 D_h, D_h = exp(-i dt/2 H0).
+// (The Section III step with the drift split evenly around the control factors: a second-order
+// variant of the paper's step.)
 //
 // With the drift folded into every step (U_n = E_{K-1} ... E_0 D), the symmetric chain is
 // a conjugation of the folded one:

@@ -1,4 +1,5 @@
 // Tensor-core (tcgen05) product chains for N = 64 in split-FP16 arithmetic.
+// (Section II process 2, Eq. exp2prod, and the Section III chain, on the tensor cores.)
 //
 // One chain multiplies a segment of gathered table operators,
 //     X <- A_f X,   f = f0 .. f0+len-1,

@@ -1,4 +1,6 @@
 // Tensor-core (tcgen05, split-FP16) sweeps for 128 <= N <= 1024.
+// (Section II process 2, Eq. exp2prod, the Section III chain and its GRAPE gradient (Fig. fc), and
+// the Section IV dynamics, on the tensor cores at large N.)
 //
 // State layout.  A chain state Y (N x N complex) is stored as the real N x 2N matrix
 // S = [Re Y | Im Y] in split FP16 (hi = fp16(v), lo = fp16((v - hi) 2^11)), cut into tiles

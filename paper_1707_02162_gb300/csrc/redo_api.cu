@@ -1,4 +1,5 @@
 // Host side of the libredo C ABI: argument checks, table ownership, launch order.
+// (Each entry point is declared with the passage it implements -- Sections II to IV -- in redo.h.)
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
