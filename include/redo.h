@@ -186,9 +186,9 @@ redo_status redo_quantize(const redo_table* t, const double* u, int64_t B, int64
  *              the norm drift of reduced-precision chains; R > M acts as R = M.
  *  U_out       device complex128 [B][N][N]; receives U_b.  May be NULL if F is wanted only.
  *  U_target    device complex128 [N][N] or NULL.
- *  F_out       device double [B]: |Tr(U_target^dag U_b)|^2 / N^2 (FP64 reduction);
- *              required iff U_target is given.
- *  tau_out     device complex128 [B] (Tr(U_target^dag U_b)) or NULL.
+ *  F_out       device double [B] or NULL: |Tr(U_target^dag U_b)|^2 / N^2 (FP64 reduction).
+ *  tau_out     device complex128 [B] (Tr(U_target^dag U_b)) or NULL.  With U_target, at
+ *              least one of F_out and tau_out is required; without it both are left untouched.
  *  workspace   device scratch of at least redo_propagate_workspace() bytes,
  *              256-byte aligned; contents are overwritten.
  *  dev_status  device int64 [REDO_STATUS_WORDS] or NULL.
